@@ -1,0 +1,320 @@
+"""Benchmark: exhaustive PIFS range-domain search on one 512x512 12-bit CT-like slice.
+
+One step = one complete fic_encode of the slice (prep, search, exact
+re-score, fallback, map output): 4096 ranges x 15625 domains x 8 symmetries
+= 5.12e8 range-domain comparisons.  Metric: comparisons/s (and ms per slice).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun (N > 1) every rank encodes its own slice (weak scaling, no
+collective on the data path); the time is the max over ranks.  The reference
+arm (--impl reference) times the FP64 CPU oracle on a bounded sample of the
+same workload on this machine's host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import fic_synth  # noqa: E402
+
+N_PIX, RANGE, STRIDE, BITS = 512, 8, 4, 12
+WORKLOAD = ("512x512 12-bit CT-like synthetic slice; 8x8 ranges (4096); 16x16 domains at stride 4 "
+            "(15625) x 8 symmetries; s 5-bit, o 7-bit")
+METRIC = "range-domain comparisons/s"
+
+
+def comparisons():
+    R = (N_PIX // RANGE) ** 2
+    D = ((N_PIX - 2 * RANGE) // STRIDE + 1) ** 2
+    return R, D, R * D * 8
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            return json.load(fh), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, \
+        "fallback"
+
+
+def cpu_oracle_sample(img, target_s=12.0, min_ranges=64):
+    """Time the FP64 oracle on an evenly spaced sample of ranges (~target_s seconds)."""
+    import oracle
+
+    oracle.build()
+    R, D, _ = comparisons()
+    cores = os.cpu_count() or 1
+    n = min_ranges
+    t0 = time.perf_counter()
+    oracle.encode(img, n=RANGE, t=STRIDE, bit_depth=BITS, ranges=np.linspace(0, R - 1, n).astype(np.int32),
+                  threads=cores)
+    dt = time.perf_counter() - t0
+    n2 = int(min(R, max(n, n * target_s / max(dt, 1e-3))))
+    sel = np.linspace(0, R - 1, n2).astype(np.int32)
+    t0 = time.perf_counter()
+    oracle.encode(img, n=RANGE, t=STRIDE, bit_depth=BITS, ranges=sel, threads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": n2 * D * 8 / dt, "unit": "comparisons/s", "cores": cores, "kind": "oracle",
+            "sample": f"{n2} evenly spaced ranges of the 512x512 slice, all 125000 candidates each, "
+                      f"{dt:.1f} s wall on {cores} threads"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    img = fic_synth.ct_slice()
+    R, D, comps = comparisons()
+    import oracle
+
+    oracle.build()
+    cores = os.cpu_count() or 1
+    per_step = 64  # ranges per step (bounded sample)
+    times = []
+    for s in range(args.warmup + args.steps):
+        sel = ((np.arange(per_step) * 61 + s * 7) % R).astype(np.int32)
+        t0 = time.perf_counter()
+        oracle.encode(img, n=RANGE, t=STRIDE, bit_depth=BITS, ranges=sel, threads=cores)
+        if s >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    t = float(np.sum(times))
+    value = args.steps * per_step * D * 8 / t
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "comparisons/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps * R / per_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample_ranges_per_step": per_step},
+            "cpu_baseline": {"value": value, "unit": "comparisons/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{per_step} ranges x 125000 candidates per step"},
+            "e2e": {"value": value, "unit": "comparisons/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300")
+    ap.add_argument("--search", default="auto", choices=["auto", "tc", "simt"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+
+    import __graft_entry__
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if rank == 0 or ws == 1:
+        __graft_entry__.build()
+    if ws > 1:
+        dist.barrier()
+    __graft_entry__.build()
+    from paper_1404_0774_gb300 import fic
+
+    R, D, comps = comparisons()
+    img_np = fic_synth.ct_slice(fic_synth.CT_SEED + rank)
+    search = {"auto": fic.FIC_SEARCH_AUTO, "tc": fic.FIC_SEARCH_TC, "simt": fic.FIC_SEARCH_SIMT}[args.search]
+    p = fic.params(range_size=RANGE, domain_stride=STRIDE, bit_depth=BITS, search=search)
+    img = torch.from_numpy(img_np.astype(np.int16)).to(dev)
+    wsb = fic.encode_workspace_size(N_PIX, N_PIX, p)
+    work = torch.empty(wsb, dtype=torch.uint8, device=dev)
+    maps = torch.empty(R * 40, dtype=torch.uint8, device=dev)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 129 MB L2
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        fic.encode(img, p, maps=maps, workspace=work, stream=stream)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    launches_per_step = 7
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for i in range(args.steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            step()
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    t_total = float(np.sum(step_ms)) / 1e3
+    if ws > 1:
+        tt = torch.tensor([t_total], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_total = float(tt.item())
+    value = ws * args.steps * comps / t_total
+
+    # dominant kernel: the search, timed alone with events on the launching stream
+    stats = fic.last_encode_stats()
+    used = {fic.FIC_SEARCH_TC: "tc", fic.FIC_SEARCH_SIMT: "simt"}.get(stats[2], "?")
+
+    # end to end through the C ABI with pinned host buffers
+    h_img = torch.from_numpy(img_np.astype(np.int16)).pin_memory()
+    h_maps = torch.empty(R * 40, dtype=torch.uint8).pin_memory()
+    lib = fic.lib()
+    import ctypes
+
+    nm = ctypes.c_int()
+
+    def e2e_step():
+        rc = lib.fic_encode(h_img.data_ptr(), N_PIX, N_PIX, N_PIX, ctypes.byref(p), h_maps.data_ptr(), R,
+                            ctypes.byref(nm), work.data_ptr(), wsb, stream.cuda_stream)
+        assert rc == 0, rc
+
+    for _ in range(3):
+        e2e_step()
+    torch.cuda.synchronize()
+    e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for i in range(args.steps):
+        flush.zero_()
+        e_ev[i][0].record(stream)
+        e2e_step()
+        e_ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    e2e_t = float(np.sum([a.elapsed_time(b) for a, b in e_ev])) / 1e3
+    if ws > 1:
+        tt = torch.tensor([e2e_t], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_t = float(tt.item())
+    e2e_value = ws * args.steps * comps / e2e_t
+
+    # dominant kernel (the search) timed alone: events recorded by the library
+    # around each phase on the launching stream, L2 flushed before each step
+    pt = fic.params(range_size=RANGE, domain_stride=STRIDE, bit_depth=BITS, search=search,
+                    flags=fic.FIC_FLAG_PHASE_TIMING)
+    phases = []
+    for i in range(max(5, min(args.steps, 20))):
+        flush.zero_()
+        fic.encode(img, pt, maps=maps, workspace=work, stream=stream)
+        phases.append(fic.last_encode_phase_ms())
+    phases = np.array(phases)
+    phase_med = {k: float(v) for k, v in zip(["prep", "search", "rescore", "fallback", "output"],
+                                               np.median(phases, axis=0))}
+    peaks, peak_kind = load_peaks()
+    clocks = clk.summary()
+    kern_ms = phase_med["search"]
+    if used == "tc":
+        flops = comps * (2 * (2 * 64 + 16))  # executed FP16 MMA flops (hi/lo halves + extra columns)
+        roof = {"bound": "tensor", "achieved": flops / (kern_ms * 1e-3) / 1e12, "peak": peaks["bf16_tflops"],
+                "unit": "TFLOP/s"}
+    else:
+        fp32_peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        flops = comps * 2 * 64
+        roof = {"bound": "alu", "achieved": flops / (kern_ms * 1e-3) / 1e12, "peak": fp32_peak,
+                "unit": "TFLOP/s"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = None
+    roof["peak_source"] = peak_kind
+    roof["kernel"] = "search"
+    roof["phase_ms"] = phase_med
+
+    line = {"metric": METRIC, "value": value, "unit": "comparisons/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": 1e3 * t_total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "fp16+fp32" if used == "tc" else "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "search": used, "l2": "flushed (256 MB write) between steps",
+                       "comparisons_per_step": comps},
+            "e2e": {"value": e2e_value, "unit": "comparisons/s",
+                    "h2d_bytes_per_step": N_PIX * N_PIX * 2, "d2h_bytes_per_step": R * 40},
+            "gpu_launches": launches_per_step * args.steps, "clocks": clocks, "roofline": roof}
+    if rank == 0:
+        if ws == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_oracle_sample(img_np)
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,162 @@
+/*
+ * fic.h -- C ABI of the GB300 PIFS fractal-encoding library (libfic.so).
+ *
+ * The library implements the hot path of partitioned-iterated-function-system
+ * (PIFS) fractal image encoding after Haque et al., "GPU Accelerated Fractal
+ * Image Compression for Medical Imaging in Parallel Computing Platform"
+ * (arXiv 1404.0774): the exhaustive range-domain search of Section V
+ * (Algorithm 2, parallelised per range as in Algorithm 3), and the decoder
+ * that iterates the resulting maps (the "decoding" of the abstract and
+ * Section VI).  Everything runs on one CUDA GPU; there is no CPU fallback.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Image: row-major, `pitch_px` elements per row (pitch_px >= w).  Pixel type
+ *    is uint8_t when bit_depth <= 8 and uint16_t when 8 < bit_depth <= 12;
+ *    values must lie in [0, 2^bit_depth - 1].
+ *  - Ranges (Section V, Section VI): non-overlapping n x n blocks; range
+ *    r = j*(w/n) + i has its top-left pixel at row n*j, column n*i.
+ *  - Domains (Section V, Algorithm 1): 2n x 2n blocks on a grid of spacing t
+ *    (the paper's STEP); domain d = v*U + u, U = (w-2n)/t + 1, has its top-left
+ *    pixel at row t*v, column t*u.  They are contracted by the 2x2 mean.
+ *  - Symmetries (Section V: rotations and mirroring), k = 0..7: identity,
+ *    rotate 90 cw, rotate 180, rotate 270 cw, mirror left-right, mirror
+ *    top-bottom, transpose, anti-transpose.  Output pixel (y, x) of S_k(A)
+ *    reads A at (y,x), (n-1-x,y), (n-1-y,n-1-x), (x,n-1-y), (y,n-1-x),
+ *    (n-1-y,x), (x,y), (n-1-x,n-1-y) respectively.
+ *  - Candidate index = 8*d + k; the search order is d-major, k-minor and the
+ *    first of equal minima wins (Algorithm 2, strict comparison).
+ *  - Contrast s by least squares (eq 9, with the domain-variance denominator
+ *    n*sum(a^2) - (sum a)^2 stated after eq 10; s = 0 for a flat domain,
+ *    eq 11), clamped to [-1, 1] and rounded half away from zero to c/Ls,
+ *    Ls = 2^(s_bits-1) - 1.  Brightness o = (sum b - s_hat*sum a)/m (eq 10
+ *    with the quantised s), clamped to [-P, P], P = 2^bit_depth - 1, rounded
+ *    half away from zero to e*P/Lo, Lo = 2^(o_bits-1) - 1.  Collage error
+ *    R = sum (s_hat*a_i + o_hat - b_i)^2 (eq 8).
+ *  - Pointers may be host or device memory; the library detects which
+ *    (cudaPointerGetAttributes) and copies host data itself.  The caller owns
+ *    every buffer.  `stream` is a cudaStream_t (NULL = legacy default stream).
+ *    Calls on one stream are ordered; the host-pointer variants synchronise
+ *    the stream before returning.
+ *  - Errors: every call returns FIC_OK (0) or a negative FIC_ERR_* code and
+ *    never aborts; fic_status_str() gives a message.
+ */
+#ifndef FIC_H
+#define FIC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    FIC_OK = 0,
+    FIC_ERR_BAD_ARG = -1,   /* null pointer, bad parameter value              */
+    FIC_ERR_SIZE = -2,      /* w/h not multiples of n, smaller than 2n, ...  */
+    FIC_ERR_BITDEPTH = -3,  /* bit_depth outside 1..12, bad s_bits/o_bits     */
+    FIC_ERR_CAPACITY = -4,  /* output or workspace buffer too small           */
+    FIC_ERR_CUDA = -5,      /* a CUDA runtime call failed                     */
+    FIC_ERR_TIMEOUT = -6,   /* a bounded device-side wait ran out             */
+    FIC_ERR_UNSUPPORTED = -7 /* valid parameters this build does not handle   */
+};
+
+/* Search implementation. */
+enum {
+    FIC_SEARCH_AUTO = 0, /* tensor-core search where supported, else SIMT     */
+    FIC_SEARCH_TC = 1,   /* FP16 tcgen05 tensor-core cross term + FP32 epilogue */
+    FIC_SEARCH_SIMT = 2  /* plain FP32 CUDA-core search (the speedup baseline) */
+};
+
+typedef struct {
+    int32_t range_size;    /* n: 4, 8 or 16                                   */
+    int32_t domain_stride; /* t >= 1 (the paper's STEP)                       */
+    int32_t bit_depth;     /* B: 1..12                                        */
+    int32_t s_bits;        /* contrast code bits, 2..8 (5 in the workloads)   */
+    int32_t o_bits;        /* brightness code bits, 2..10 (7)                 */
+    int32_t decode_iters;  /* Jacobi iterations of fic_decode (10)            */
+    int32_t search;        /* FIC_SEARCH_*                                    */
+    int32_t n_split;       /* candidate-dimension splits, 0 = automatic       */
+    uint32_t flags;        /* FIC_FLAG_* bits                                 */
+} fic_params;
+
+/* fic_params.flags: record CUDA events around each encode phase on the
+ * caller's stream (read them back with fic_last_encode_phase_ms). */
+#define FIC_FLAG_PHASE_TIMING 0x1u
+
+/* One map per range: range -> (domain, symmetry, s, o) and its collage error. */
+typedef struct {
+    uint32_t range_idx;  /* r                                                 */
+    uint32_t domain_idx; /* d                                                 */
+    int32_t iso;         /* k in 0..7                                         */
+    int32_t s_code;      /* c in [-Ls, Ls]; s_hat = c / Ls                    */
+    int32_t o_code;      /* e in [-Lo, Lo]; o_hat = e * P / Lo                */
+    float s;             /* s_hat                                             */
+    float o;             /* o_hat                                             */
+    uint32_t info;       /* FIC_MAP_* bits                                    */
+    double err;          /* eq 8 residual, FP64, summed over pixels in order  */
+} fic_map;
+
+#define FIC_MAP_FALLBACK 0x1u /* resolved by the exact full rescan           */
+
+/* Fill `p` with the defaults of the workloads (n=8, t=8, B=8, 5/7 bits,
+ * 10 decode iterations, automatic search). */
+void fic_default_params(fic_params *p);
+
+/* Number of ranges and domains of a w x h image under `p`; returns FIC_OK or
+ * an error for invalid sizes.  Either output pointer may be NULL. */
+int fic_counts(int w, int h, const fic_params *p, int64_t *n_ranges, int64_t *n_domains);
+
+/* Device workspace bytes that fic_encode needs for a w x h image. */
+int fic_encode_workspace_size(int w, int h, const fic_params *p, size_t *bytes);
+
+/*
+ * fic_encode -- exhaustive range-domain search (Section V, Algorithms 1-3).
+ *   img        w x h image (pitch_px elements per row), host or device.
+ *   maps       output, one fic_map per range in range order (host or device);
+ *              maps_cap >= number of ranges.
+ *   n_maps     output (host), number of maps written; may be NULL.
+ *   workspace  device buffer of at least fic_encode_workspace_size() bytes,
+ *              or NULL to let the library allocate (cudaMallocAsync) and free
+ *              it on `stream`.
+ * Every map is the exact minimiser of eq 8 over all 8*D candidates with the
+ * lowest-index tie-break; codes are decided in FP64 as described above.
+ */
+int fic_encode(const void *img, int w, int h, int pitch_px, const fic_params *p, fic_map *maps,
+               int maps_cap, int *n_maps, void *workspace, size_t workspace_bytes, void *stream);
+
+/*
+ * fic_decode -- iterate the maps (decoding, abstract and Section VI).
+ *   Starts from a flat image of value `init`, applies p->decode_iters Jacobi
+ *   steps x <- s_hat * S_k(tau(x[domain])) + o_hat over all ranges (FP32, no
+ *   clamping inside the iteration), then clamps to [0, P] into `out`
+ *   (w*h floats, row-major, host or device).  `maps` (n_maps = number of
+ *   ranges, host or device) is read-only; host maps are validated (domain and
+ *   symmetry in range), device maps must come from fic_encode with the same
+ *   w, h and parameters.  `workspace` as in fic_encode, of
+ *   fic_decode_workspace_size() bytes (NULL = allocate).
+ */
+int fic_decode(const fic_map *maps, int n_maps, int w, int h, const fic_params *p, float init,
+               float *out, void *workspace, size_t workspace_bytes, void *stream);
+
+/* Device workspace bytes that fic_decode needs for a w x h image. */
+int fic_decode_workspace_size(int w, int h, const fic_params *p, size_t *bytes);
+
+/* Human-readable message for a status code. */
+const char *fic_status_str(int status);
+
+/* Counters of the last fic_encode on this host thread (diagnostics):
+ * out[0] = ranges resolved by the exact full rescan, out[1] = number of
+ * candidate lists, out[2] = search implementation used (FIC_SEARCH_*). */
+int fic_last_encode_stats(int64_t out[4]);
+
+/* Phase durations (ms) of the last fic_encode on this host thread that ran
+ * with FIC_FLAG_PHASE_TIMING: out[0] prep, out[1] search, out[2] re-score,
+ * out[3] fallback, out[4] map output.  Waits for those events. */
+int fic_last_encode_phase_ms(double out[5]);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FIC_H */

@@ -1,0 +1,427 @@
+// Host side of the C ABI declared in include/fic.h.
+//
+// fic_encode runs, on one stream: (host image -> device copy) -> prep
+// (ranges, domain pool) -> search (tensor-core or SIMT screening) -> exact
+// re-score + certification -> exact fallback for uncertified ranges ->
+// final FP64 codes and residuals -> (device -> host maps copy).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "fic_internal.cuh"
+
+using namespace fic;
+
+namespace {
+
+thread_local int64_t g_stats[4] = {0, 0, 0, 0};
+
+// Phase events of the last timed encode (per host thread).
+struct PhaseEvents {
+    cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    bool valid = false;
+    bool ensure()
+    {
+        for (auto &e : ev)
+            if (!e && cudaEventCreate(&e) != cudaSuccess) {
+                cudaGetLastError();
+                return false;
+            }
+        return true;
+    }
+};
+thread_local PhaseEvents g_phase;
+
+constexpr size_t kAlign = 256;
+size_t align_up(size_t v) { return (v + kAlign - 1) & ~(kAlign - 1); }
+
+int check_params(const fic_params *p)
+{
+    if (!p) return FIC_ERR_BAD_ARG;
+    if (p->flags & ~FIC_FLAG_PHASE_TIMING) return FIC_ERR_BAD_ARG;
+    if (p->range_size != 4 && p->range_size != 8 && p->range_size != 16) return FIC_ERR_BAD_ARG;
+    if (p->domain_stride < 1) return FIC_ERR_BAD_ARG;
+    if (p->bit_depth < 1 || p->bit_depth > 12) return FIC_ERR_BITDEPTH;
+    if (p->s_bits < 2 || p->s_bits > 8 || p->o_bits < 2 || p->o_bits > 10) return FIC_ERR_BITDEPTH;
+    if (p->decode_iters < 0 || p->decode_iters > 100000) return FIC_ERR_BAD_ARG;
+    if (p->search < FIC_SEARCH_AUTO || p->search > FIC_SEARCH_SIMT) return FIC_ERR_BAD_ARG;
+    if (p->n_split < 0) return FIC_ERR_BAD_ARG;
+    return FIC_OK;
+}
+
+int make_geometry(int w, int h, int pitch, const fic_params *p, Geometry &g)
+{
+    int rc = check_params(p);
+    if (rc != FIC_OK) return rc;
+    const int n = p->range_size;
+    if (w <= 0 || h <= 0 || w % n || h % n || w < 2 * n || h < 2 * n) return FIC_ERR_SIZE;
+    if (pitch < w) return FIC_ERR_BAD_ARG;
+    if ((long long)w * h > (1LL << 30)) return FIC_ERR_SIZE;
+    std::memset(&g, 0, sizeof g);
+    g.w = w;
+    g.h = h;
+    g.pitch = pitch;
+    g.n = n;
+    g.t = p->domain_stride;
+    g.m = n * n;
+    g.nx = w / n;
+    g.ny = h / n;
+    g.R = g.nx * g.ny;
+    g.U = (w - 2 * n) / g.t + 1;
+    g.V = (h - 2 * n) / g.t + 1;
+    if ((long long)g.U * g.V * 8 >= (1LL << 31)) return FIC_ERR_SIZE;
+    g.D = g.U * g.V;
+    g.N = 8 * g.D;
+    g.B = p->bit_depth;
+    g.P = (1 << g.B) - 1;
+    g.s_bits = p->s_bits;
+    g.o_bits = p->o_bits;
+    g.Ls = (1 << (g.s_bits - 1)) - 1;
+    g.Lo = (1 << (g.o_bits - 1)) - 1;
+    g.split_hilo = 4 * g.P > 2048 ? 1 : 0;
+    g.KP = (g.split_hilo ? 2 * g.m : g.m) + 16;
+    const long long Gnum = 4LL * g.Ls * g.m * g.P;
+    g.mod_g = (Gnum % g.Lo) == 0 ? 1 : 0;
+    g.G = (double)Gnum / g.Lo;
+    return FIC_OK;
+}
+
+EpiConst make_epi(const Geometry &g)
+{
+    EpiConst ec;
+    ec.two_ls = 2.0f * g.Ls;
+    ec.ls = (float)g.Ls;
+    ec.G = (float)g.G;
+    ec.invG = (float)(1.0 / g.G);
+    const double pl = (double)g.P / g.Lo;
+    ec.lambda = (float)(2.0 * g.Ls * g.m * pl * pl / (g.G * g.G));
+    return ec;
+}
+
+int sm_count()
+{
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 148;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 148;
+    return n > 0 ? n : 148;
+}
+
+int choose_search(const Geometry &g, const fic_params *p)
+{
+    (void)g;
+    if (p->search == FIC_SEARCH_TC) return -1;  // not available in this build
+    return FIC_SEARCH_SIMT;
+}
+
+int choose_split(const Geometry &g, const fic_params *p, int search)
+{
+    (void)search;
+    const int tiles = (g.N + 63) / 64;
+    const int mt = (g.R + 127) / 128;
+    int s = p->n_split;
+    if (s == 0) s = std::max(1, (2 * 2 * sm_count() + mt - 1) / mt);
+    return std::max(1, std::min(s, tiles));
+}
+
+struct EncLayout {
+    size_t img, ri, di, dconst, bblk, qblk, rs32, cb32, ra16, cb16, lists, winner, fb_list, fb_count,
+        qp2max, maps, total;
+};
+
+EncLayout enc_layout(const Geometry &g, int search, int n_lists)
+{
+    EncLayout L;
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        const size_t at = o;
+        o = align_up(o + bytes);
+        return at;
+    };
+    const size_t elem = g.B <= 8 ? 1 : 2;
+    L.img = take((size_t)g.w * g.h * elem);
+    L.ri = take(sizeof(RangeInfo) * g.R);
+    L.di = take(sizeof(DomainInfo) * g.D);
+    L.dconst = take(sizeof(float4) * g.D);
+    L.bblk = take(sizeof(uint16_t) * (size_t)g.R * g.m);
+    L.qblk = take(sizeof(uint16_t) * (size_t)g.D * g.m);
+    const bool simt = search == FIC_SEARCH_SIMT;
+    L.rs32 = simt ? take(sizeof(float) * (size_t)g.R * g.m) : 0;
+    L.cb32 = simt ? take(sizeof(float) * (size_t)g.N * g.m) : 0;
+    L.ra16 = simt ? 0 : take(sizeof(__half) * (size_t)g.R * g.KP);
+    L.cb16 = simt ? 0 : take(sizeof(__half) * (size_t)g.N * g.KP);
+    L.lists = take(sizeof(ListEntry) * (size_t)g.R * n_lists * kListK);
+    L.winner = take(sizeof(uint32_t) * g.R);
+    L.fb_list = take(sizeof(int) * g.R);
+    L.fb_count = take(sizeof(int) * 2);
+    L.qp2max = take(sizeof(float) * 2);
+    L.maps = take(sizeof(fic_map) * g.R);
+    L.total = o;
+    return L;
+}
+
+bool is_device_ptr(const void *ptr)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+#define FIC_CUDA(call)                      \
+    do {                                    \
+        cudaError_t e_ = (call);            \
+        if (e_ != cudaSuccess) {            \
+            cudaGetLastError();             \
+            rc = FIC_ERR_CUDA;              \
+            goto done;                      \
+        }                                   \
+    } while (0)
+
+}  // namespace
+
+extern "C" {
+
+void fic_default_params(fic_params *p)
+{
+    if (!p) return;
+    p->range_size = 8;
+    p->domain_stride = 8;
+    p->bit_depth = 8;
+    p->s_bits = 5;
+    p->o_bits = 7;
+    p->decode_iters = 10;
+    p->search = FIC_SEARCH_AUTO;
+    p->n_split = 0;
+    p->flags = 0;
+}
+
+int fic_counts(int w, int h, const fic_params *p, int64_t *n_ranges, int64_t *n_domains)
+{
+    Geometry g;
+    const int rc = make_geometry(w, h, w, p, g);
+    if (rc != FIC_OK) return rc;
+    if (n_ranges) *n_ranges = g.R;
+    if (n_domains) *n_domains = g.D;
+    return FIC_OK;
+}
+
+int fic_encode_workspace_size(int w, int h, const fic_params *p, size_t *bytes)
+{
+    if (!bytes) return FIC_ERR_BAD_ARG;
+    Geometry g;
+    const int rc = make_geometry(w, h, w, p, g);
+    if (rc != FIC_OK) return rc;
+    const int search = choose_search(g, p);
+    if (search < 0) return FIC_ERR_UNSUPPORTED;
+    const int lps = search == FIC_SEARCH_SIMT ? search_simt_lists_per_split() : 1;
+    *bytes = enc_layout(g, search, choose_split(g, p, search) * lps).total;
+    return FIC_OK;
+}
+
+int fic_encode(const void *img, int w, int h, int pitch_px, const fic_params *p, fic_map *maps,
+               int maps_cap, int *n_maps, void *workspace, size_t workspace_bytes, void *stream)
+{
+    if (!img || !maps) return FIC_ERR_BAD_ARG;
+    Geometry g;
+    int rc = make_geometry(w, h, pitch_px, p, g);
+    if (rc != FIC_OK) return rc;
+    if (maps_cap < g.R) return FIC_ERR_CAPACITY;
+    const int search = choose_search(g, p);
+    if (search < 0) return FIC_ERR_UNSUPPORTED;
+    const int n_split = choose_split(g, p, search);
+    const int lps = search == FIC_SEARCH_SIMT ? search_simt_lists_per_split() : 1;
+    const int n_lists = n_split * lps;
+    const EncLayout L = enc_layout(g, search, n_lists);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    char *ws = static_cast<char *>(workspace);
+    bool owned = false;
+    if (ws) {
+        if (workspace_bytes < L.total) return FIC_ERR_CAPACITY;
+    } else {
+        if (cudaMallocAsync(reinterpret_cast<void **>(&ws), L.total, st) != cudaSuccess) {
+            cudaGetLastError();
+            return FIC_ERR_CUDA;
+        }
+        owned = true;
+    }
+    {
+        const bool img_dev = is_device_ptr(img);
+        const bool maps_dev = is_device_ptr(maps);
+        const size_t elem = g.B <= 8 ? 1 : 2;
+        const void *dimg = img;
+        Geometry gd = g;
+        if (!img_dev) {
+            FIC_CUDA(cudaMemcpy2DAsync(ws + L.img, (size_t)w * elem, img, (size_t)pitch_px * elem,
+                                       (size_t)w * elem, h, cudaMemcpyHostToDevice, st));
+            dimg = ws + L.img;
+            gd.pitch = w;
+        }
+        RangeInfo *ri = reinterpret_cast<RangeInfo *>(ws + L.ri);
+        DomainInfo *di = reinterpret_cast<DomainInfo *>(ws + L.di);
+        float4 *dconst = reinterpret_cast<float4 *>(ws + L.dconst);
+        uint16_t *bblk = reinterpret_cast<uint16_t *>(ws + L.bblk);
+        uint16_t *qblk = reinterpret_cast<uint16_t *>(ws + L.qblk);
+        float *rs32 = L.rs32 ? reinterpret_cast<float *>(ws + L.rs32) : nullptr;
+        float *cb32 = L.cb32 ? reinterpret_cast<float *>(ws + L.cb32) : nullptr;
+        __half *ra16 = L.ra16 ? reinterpret_cast<__half *>(ws + L.ra16) : nullptr;
+        __half *cb16 = L.cb16 ? reinterpret_cast<__half *>(ws + L.cb16) : nullptr;
+        ListEntry *lists = reinterpret_cast<ListEntry *>(ws + L.lists);
+        uint32_t *winner = reinterpret_cast<uint32_t *>(ws + L.winner);
+        int *fb_list = reinterpret_cast<int *>(ws + L.fb_list);
+        int *fb_count = reinterpret_cast<int *>(ws + L.fb_count);
+        float *qp2max = reinterpret_cast<float *>(ws + L.qp2max);
+        fic_map *dmaps = maps_dev ? maps : reinterpret_cast<fic_map *>(ws + L.maps);
+        const EpiConst ec = make_epi(g);
+        const bool timed = (p->flags & FIC_FLAG_PHASE_TIMING) && g_phase.ensure();
+        g_phase.valid = false;
+#define FIC_MARK(i) \
+    if (timed) FIC_CUDA(cudaEventRecord(g_phase.ev[i], st))
+
+        FIC_CUDA(cudaMemsetAsync(fb_count, 0, sizeof(int), st));
+        FIC_MARK(0);
+        FIC_CUDA(launch_prep(gd, dimg, ri, di, dconst, bblk, qblk, rs32, cb32, ra16, cb16, st));
+        FIC_CUDA(launch_qp2max(gd, di, qp2max, st));
+        FIC_MARK(1);
+        FIC_CUDA(launch_search_simt(gd, ec, ri, di, dconst, rs32, cb32, lists, n_split, st));
+        FIC_MARK(2);
+        FIC_CUDA(launch_rescore(gd, ec, ri, di, bblk, qblk, lists, n_lists, qp2max, winner, fb_list,
+                                fb_count, st));
+        FIC_MARK(3);
+        FIC_CUDA(launch_fallback(gd, ri, di, bblk, qblk, fb_list, fb_count, winner, st));
+        FIC_MARK(4);
+        FIC_CUDA(launch_finalize(gd, ri, di, bblk, qblk, winner, dmaps, st));
+        FIC_MARK(5);
+#undef FIC_MARK
+        g_phase.valid = timed;
+        if (!maps_dev) {
+            FIC_CUDA(cudaMemcpyAsync(maps, dmaps, sizeof(fic_map) * g.R, cudaMemcpyDeviceToHost, st));
+        }
+        if (!maps_dev || !img_dev) FIC_CUDA(cudaStreamSynchronize(st));
+        g_stats[0] = -1;
+        g_stats[1] = n_lists;
+        g_stats[2] = search;
+        g_stats[3] = n_split;
+        if (n_maps) *n_maps = g.R;
+    }
+done:
+    if (owned) {
+        if (cudaFreeAsync(ws, st) != cudaSuccess) {
+            cudaGetLastError();
+            if (rc == FIC_OK) rc = FIC_ERR_CUDA;
+        }
+    }
+    return rc;
+}
+
+int fic_decode(const fic_map *maps, int n_maps, int w, int h, const fic_params *p, float init,
+               float *out, void *workspace, size_t workspace_bytes, void *stream)
+{
+    if (!maps || !out) return FIC_ERR_BAD_ARG;
+    Geometry g;
+    int rc = make_geometry(w, h, w, p, g);
+    if (rc != FIC_OK) return rc;
+    if (n_maps != g.R) return FIC_ERR_CAPACITY;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const size_t dws = align_up(decode_workspace_bytes(g));
+    const size_t maps_b = align_up(sizeof(fic_map) * g.R);
+    const size_t out_b = align_up(sizeof(float) * (size_t)w * h);
+    const size_t total = dws + maps_b + out_b;
+    char *ws = static_cast<char *>(workspace);
+    bool owned = false;
+    const bool maps_dev = is_device_ptr(maps);
+    const bool out_dev = is_device_ptr(out);
+    if (!maps_dev) {
+        // host maps are validated here; device maps are trusted to come from fic_encode
+        for (int r = 0; r < g.R; ++r)
+            if (maps[r].domain_idx >= (uint32_t)g.D || maps[r].iso < 0 || maps[r].iso > 7)
+                return FIC_ERR_BAD_ARG;
+    }
+    if (ws) {
+        if (workspace_bytes < total) return FIC_ERR_CAPACITY;
+    } else {
+        if (cudaMallocAsync(reinterpret_cast<void **>(&ws), total, st) != cudaSuccess) {
+            cudaGetLastError();
+            return FIC_ERR_CUDA;
+        }
+        owned = true;
+    }
+    {
+        const fic_map *dmaps = maps;
+        float *dout = out_dev ? out : reinterpret_cast<float *>(ws + dws + maps_b);
+        if (!maps_dev) {
+            FIC_CUDA(cudaMemcpyAsync(ws + dws, maps, sizeof(fic_map) * g.R, cudaMemcpyHostToDevice, st));
+            dmaps = reinterpret_cast<const fic_map *>(ws + dws);
+        }
+        FIC_CUDA(launch_decode(g, dmaps, init, p->decode_iters, ws, dout, st));
+        if (!out_dev) {
+            FIC_CUDA(cudaMemcpyAsync(out, dout, sizeof(float) * (size_t)w * h, cudaMemcpyDeviceToHost, st));
+            FIC_CUDA(cudaStreamSynchronize(st));
+        } else if (!maps_dev) {
+            FIC_CUDA(cudaStreamSynchronize(st));
+        }
+    }
+done:
+    if (owned) {
+        if (cudaFreeAsync(ws, st) != cudaSuccess) {
+            cudaGetLastError();
+            if (rc == FIC_OK) rc = FIC_ERR_CUDA;
+        }
+    }
+    return rc;
+}
+
+int fic_decode_workspace_size(int w, int h, const fic_params *p, size_t *bytes)
+{
+    if (!bytes) return FIC_ERR_BAD_ARG;
+    Geometry g;
+    const int rc = make_geometry(w, h, w, p, g);
+    if (rc != FIC_OK) return rc;
+    *bytes = align_up(decode_workspace_bytes(g)) + align_up(sizeof(fic_map) * g.R) +
+             align_up(sizeof(float) * (size_t)w * h);
+    return FIC_OK;
+}
+
+const char *fic_status_str(int status)
+{
+    switch (status) {
+    case FIC_OK: return "ok";
+    case FIC_ERR_BAD_ARG: return "invalid argument";
+    case FIC_ERR_SIZE: return "image size must be a multiple of the range size and at least two ranges";
+    case FIC_ERR_BITDEPTH: return "unsupported bit depth or code width";
+    case FIC_ERR_CAPACITY: return "output or workspace buffer too small";
+    case FIC_ERR_CUDA: return "CUDA runtime error";
+    case FIC_ERR_TIMEOUT: return "device-side wait timed out";
+    case FIC_ERR_UNSUPPORTED: return "parameters not supported by this build";
+    default: return "unknown status";
+    }
+}
+
+int fic_last_encode_phase_ms(double out[5])
+{
+    if (!out) return FIC_ERR_BAD_ARG;
+    if (!g_phase.valid) return FIC_ERR_BAD_ARG;
+    if (cudaEventSynchronize(g_phase.ev[5]) != cudaSuccess) {
+        cudaGetLastError();
+        return FIC_ERR_CUDA;
+    }
+    for (int i = 0; i < 5; ++i) {
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, g_phase.ev[i], g_phase.ev[i + 1]) != cudaSuccess) {
+            cudaGetLastError();
+            return FIC_ERR_CUDA;
+        }
+        out[i] = ms;
+    }
+    return FIC_OK;
+}
+
+int fic_last_encode_stats(int64_t out[4])
+{
+    if (!out) return FIC_ERR_BAD_ARG;
+    for (int i = 0; i < 4; ++i) out[i] = g_stats[i];
+    return FIC_OK;
+}
+
+}  // extern "C"

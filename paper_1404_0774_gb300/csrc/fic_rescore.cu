@@ -1,0 +1,349 @@
+// Exact re-scoring of the screened candidates, certification, exact fallback,
+// and map output.
+//
+// The screening epilogue ranks candidates in FP32.  Here each range's list
+// entries whose key lies within 2*beta of the best key are re-scored exactly:
+//   - the cross term X = sum q_i b_i is recomputed in integers,
+//   - the s and o codes are decided in FP64 with the operation sequence of the
+//     least squares of eq 9-12 (so they are identical to an FP64 evaluation of
+//     the same formulas), and
+//   - the residual of eq 8 is evaluated exactly in integer arithmetic:
+//       R * D^2 = sum_i (c*Lo*q_i + 4*Ls*e*P - D*b_i)^2,  D = 4*Ls*Lo,
+//     expanded into the exact integer statistics.
+// The winner is the smallest exact residual, ties to the lowest candidate
+// index (Algorithm 2's strict comparison).  A range is certified when every
+// full candidate list's worst key lies beyond the re-scoring window, so no
+// candidate outside the lists can beat or tie the winner; otherwise it goes
+// to the exact fallback, which scans all of its candidates with exact
+// integer decisions.
+#include "fic_internal.cuh"
+
+namespace fic {
+
+namespace {
+
+struct Stats {
+    long long Sq, Sqq, Sb, Sbb, X;
+};
+
+// FP64 least squares + quantisation, in the evaluation order of eq 9-12.
+__device__ void fp64_codes(const Geometry &g, const Stats &st, int &c, int &e, double &s_hat,
+                           double &o_hat)
+{
+    const double md = (double)g.m;
+    const double Sa = __dmul_rn((double)st.Sq, 0.25);
+    const double Sb = (double)st.Sb;
+    const double Saa = __dmul_rn((double)st.Sqq, 0.0625);
+    const double Sab = __dmul_rn((double)st.X, 0.25);
+    const double den = __dsub_rn(__dmul_rn(md, Saa), __dmul_rn(Sa, Sa));
+    const double s =
+        (den == 0.0) ? 0.0 : __ddiv_rn(__dsub_rn(__dmul_rn(md, Sab), __dmul_rn(Sa, Sb)), den);
+    const double Ls = (double)g.Ls;
+    const double sc = s < -1.0 ? -1.0 : (s > 1.0 ? 1.0 : s);
+    c = (int)round(__dmul_rn(sc, Ls));
+    s_hat = __ddiv_rn((double)c, Ls);
+    const double o = __ddiv_rn(__dsub_rn(Sb, __dmul_rn(s_hat, Sa)), md);
+    const double P = (double)g.P, Lo = (double)g.Lo;
+    const double oc = o < -P ? -P : (o > P ? P : o);
+    e = (int)round(__ddiv_rn(__dmul_rn(oc, Lo), P));
+    o_hat = __ddiv_rn(__dmul_rn((double)e, P), Lo);
+}
+
+// Exact residual times D^2 for codes (c, e).
+__device__ __int128 exact_err(const Geometry &g, const Stats &st, int c, int e)
+{
+    const __int128 A = (__int128)c * g.Lo;
+    const __int128 Bo = (__int128)4 * g.Ls * e * g.P;
+    const __int128 Dd = (__int128)4 * g.Ls * g.Lo;
+    return A * A * st.Sqq + (__int128)g.m * Bo * Bo + Dd * Dd * st.Sbb + 2 * A * Bo * st.Sq -
+           2 * A * Dd * st.X - 2 * Bo * Dd * st.Sb;
+}
+
+__device__ __forceinline__ bool better(unsigned __int128 e1, uint32_t i1, unsigned __int128 e2,
+                                       uint32_t i2)
+{
+    return e1 < e2 || (e1 == e2 && i1 < i2);
+}
+
+__device__ __forceinline__ unsigned long long shfl64(unsigned long long v, int src)
+{
+    return __shfl_sync(0xffffffffu, v, src);
+}
+
+// Warp argmin over (err, idx).
+__device__ void warp_argmin(unsigned __int128 &err, uint32_t &idx)
+{
+    for (int off = 16; off > 0; off >>= 1) {
+        const unsigned long long lo = shfl64((unsigned long long)err, (threadIdx.x & 31) ^ off);
+        const unsigned long long hi = shfl64((unsigned long long)(err >> 64), (threadIdx.x & 31) ^ off);
+        const uint32_t oi = __shfl_xor_sync(0xffffffffu, idx, off);
+        const unsigned __int128 oe = ((unsigned __int128)hi << 64) | lo;
+        if (better(oe, oi, err, idx)) {
+            err = oe;
+            idx = oi;
+        }
+    }
+}
+
+// Exact X of candidate idx for a range whose pixels are b[] (lane-distributed:
+// lane l holds pixels l, l+32, ...).
+__device__ long long warp_cross(const Geometry &g, const uint16_t *qblk, uint32_t idx,
+                                const int (&b)[kMaxM / 32])
+{
+    const int d = idx >> 3, k = idx & 7;
+    const int lane = threadIdx.x & 31;
+    long long acc = 0;
+#pragma unroll
+    for (int j = 0; j < kMaxM / 32; ++j) {
+        const int i = lane + 32 * j;
+        if (i < g.m) {
+            int sy, sx;
+            sym_src(k, g.n, i / g.n, i % g.n, sy, sx);
+            acc += (long long)qblk[(size_t)d * g.m + sy * g.n + sx] * b[j];
+        }
+    }
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    return acc;
+}
+
+}  // namespace
+
+// One warp per range.
+__global__ void k_rescore(Geometry g, EpiConst ec, const RangeInfo *ri, const DomainInfo *di,
+                          const uint16_t *bblk, const uint16_t *qblk, const ListEntry *lists,
+                          int n_lists, const float *qp2max, uint32_t *winner, int *fb_list,
+                          int *fb_count)
+{
+    const int warps = blockDim.x >> 5;
+    const int r = blockIdx.x * warps + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (r >= g.R) return;
+    const RangeInfo rin = ri[r];
+    int b[kMaxM / 32];
+#pragma unroll
+    for (int j = 0; j < kMaxM / 32; ++j) {
+        const int i = lane + 32 * j;
+        b[j] = i < g.m ? (int)bblk[(size_t)r * g.m + i] : 0;
+    }
+    const ListEntry *L = lists + (size_t)r * n_lists * kListK;
+    const int nent = n_lists * kListK;
+    // best screening key
+    float kbest = __int_as_float(0x7f800000);
+    for (int f = lane; f < nent; f += 32) kbest = fminf(kbest, L[f].key);
+    for (int off = 16; off > 0; off >>= 1) kbest = fminf(kbest, __shfl_xor_sync(0xffffffffu, kbest, off));
+    // screening error allowance in key units (2*Ls*R units)
+    const float two_ls = ec.two_ls;
+    const float delta_o = (float)g.m * 0.25f * ((float)g.P / g.Lo) * ((float)g.P / g.Lo);
+    const float mag = two_ls * (rin.sbbc + delta_o) + fabsf(kbest);
+    const float beta = 1.0f / 65536.0f * mag +
+                       ec.ls * (1.0f / 262144.0f) * sqrtf(*qp2max * rin.bp2) +
+                       ec.lambda * ec.G * 2.0f + 1e-3f;
+    const float kthr = kbest + 2.0f * beta;
+    // certification: every full list must end beyond the window
+    bool cert = true;
+    for (int l = lane; l < n_lists; l += 32) {
+        const ListEntry last = L[l * kListK + kListK - 1];
+        if (last.idx != 0xffffffffu && !(last.key > kthr)) cert = false;
+    }
+    cert = __all_sync(0xffffffffu, cert);
+
+    Stats st;
+    st.Sb = rin.Sb;
+    st.Sbb = rin.Sbb;
+    unsigned __int128 best_e = ~(unsigned __int128)0;
+    uint32_t best_i = 0xffffffffu;
+    for (int f0 = 0; f0 < nent; f0 += 32) {
+        const int f = f0 + lane;
+        ListEntry ent = f < nent ? L[f] : ListEntry{__int_as_float(0x7f800000), 0xffffffffu};
+        const bool fin = ent.idx != 0xffffffffu && ent.key <= kthr;
+        unsigned mask = __ballot_sync(0xffffffffu, fin);
+        while (mask) {
+            const int src = __ffs(mask) - 1;
+            mask &= mask - 1;
+            const uint32_t idx = __shfl_sync(0xffffffffu, ent.idx, src);
+            const long long X = warp_cross(g, qblk, idx, b);
+            if (lane == src) {
+                const DomainInfo dd = di[idx >> 3];
+                st.Sq = dd.Sq;
+                st.Sqq = dd.Sqq;
+                st.X = X;
+                int c, e;
+                double sh, oh;
+                fp64_codes(g, st, c, e, sh, oh);
+                const unsigned __int128 er = (unsigned __int128)exact_err(g, st, c, e);
+                if (better(er, idx, best_e, best_i)) {
+                    best_e = er;
+                    best_i = idx;
+                }
+            }
+        }
+    }
+    warp_argmin(best_e, best_i);
+    if (lane == 0) {
+        winner[r] = best_i;
+        if (!cert || best_i == 0xffffffffu) {
+            const int slot = atomicAdd(fb_count, 1);
+            fb_list[slot] = r;
+        }
+    }
+}
+
+// Exact code decisions in integer arithmetic (round half away from zero of
+// the exact rational values), used by the fallback scan.
+__device__ __forceinline__ int round_div_away(long long num, long long den)  // den > 0
+{
+    const long long a = num < 0 ? -num : num;
+    long long q = (long long)((double)a / (double)den + 0.5);
+    // correct the estimate: want q = floor((2a + den) / (2 den))
+    while (q > 0 && 2 * a + den < 2 * den * q) --q;
+    while (2 * a + den >= 2 * den * (q + 1)) ++q;
+    return (int)(num < 0 ? -q : q);
+}
+
+// One CTA per range that failed certification: exhaustive exact scan.
+__global__ void __launch_bounds__(256) k_fallback(Geometry g, const RangeInfo *ri, const DomainInfo *di,
+                                                  const uint16_t *bblk, const uint16_t *qblk,
+                                                  const int *fb_list, const int *fb_count,
+                                                  uint32_t *winner)
+{
+    __shared__ int b_s[kMaxM];
+    __shared__ unsigned long long e_s[2][8];
+    __shared__ uint32_t i_s[8];
+    const int count = *fb_count;
+    for (int slot = blockIdx.x; slot < count; slot += gridDim.x) {
+        const int r = fb_list[slot];
+        __syncthreads();
+        for (int i = threadIdx.x; i < g.m; i += blockDim.x) b_s[i] = bblk[(size_t)r * g.m + i];
+        __syncthreads();
+        const RangeInfo rin = ri[r];
+        Stats st;
+        st.Sb = rin.Sb;
+        st.Sbb = rin.Sbb;
+        unsigned __int128 best_e = ~(unsigned __int128)0;
+        uint32_t best_i = 0xffffffffu;
+        const long long Q = 4LL * g.Ls * g.m * g.P;  // o grid: e = round(z*Lo/Q)
+        for (int idx = threadIdx.x; idx < g.N; idx += blockDim.x) {
+            const int d = idx >> 3, k = idx & 7;
+            long long X = 0;
+            for (int i = 0; i < g.m; ++i) {
+                int sy, sx;
+                sym_src(k, g.n, i / g.n, i % g.n, sy, sx);
+                X += (long long)qblk[(size_t)d * g.m + sy * g.n + sx] * b_s[i];
+            }
+            const DomainInfo dd = di[d];
+            st.Sq = dd.Sq;
+            st.Sqq = dd.Sqq;
+            st.X = X;
+            const long long den = (long long)g.m * dd.Sqq - dd.Sq * dd.Sq;
+            const long long num = (long long)g.m * X - dd.Sq * rin.Sb;
+            int c = 0;
+            if (den != 0) {
+                // c = round(Ls * clamp(4 num / den, -1, 1))
+                const long long v = 4LL * num;
+                if (v >= den) c = g.Ls;
+                else if (-v >= den) c = -g.Ls;
+                else c = round_div_away((long long)g.Ls * v, den);
+            }
+            const long long z = 4LL * g.Ls * rin.Sb - (long long)c * dd.Sq;
+            int e = round_div_away(z * g.Lo, Q);
+            if (e > g.Lo) e = g.Lo;  // o is never below -P, clamp above only
+            const unsigned __int128 er = (unsigned __int128)exact_err(g, st, c, e);
+            if (better(er, (uint32_t)idx, best_e, best_i)) {
+                best_e = er;
+                best_i = (uint32_t)idx;
+            }
+        }
+        warp_argmin(best_e, best_i);
+        const int w = threadIdx.x >> 5;
+        if ((threadIdx.x & 31) == 0) {
+            e_s[0][w] = (unsigned long long)best_e;
+            e_s[1][w] = (unsigned long long)(best_e >> 64);
+            i_s[w] = best_i;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned __int128 be = ((unsigned __int128)e_s[1][0] << 64) | e_s[0][0];
+            uint32_t bi = i_s[0];
+            for (int j = 1; j < (int)(blockDim.x >> 5); ++j) {
+                const unsigned __int128 ej = ((unsigned __int128)e_s[1][j] << 64) | e_s[0][j];
+                if (better(ej, i_s[j], be, bi)) {
+                    be = ej;
+                    bi = i_s[j];
+                }
+            }
+            winner[r] = bi | 0x80000000u;  // high bit: resolved by the fallback
+        }
+    }
+}
+
+// One thread per range: FP64 codes and the eq 8 residual summed over the
+// pixels in order, written as the output map.
+__global__ void k_finalize(Geometry g, const RangeInfo *ri, const DomainInfo *di, const uint16_t *bblk,
+                           const uint16_t *qblk, const uint32_t *winner, fic_map *maps)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= g.R) return;
+    const uint32_t wv = winner[r];
+    uint32_t idx = wv & 0x7fffffffu;
+    if (idx >= (uint32_t)g.N) idx = 0;  // unreachable: every range has a winner
+    const int d = idx >> 3, k = idx & 7;
+    const RangeInfo rin = ri[r];
+    const DomainInfo dd = di[d];
+    long long X = 0;
+    for (int i = 0; i < g.m; ++i) {
+        int sy, sx;
+        sym_src(k, g.n, i / g.n, i % g.n, sy, sx);
+        X += (long long)qblk[(size_t)d * g.m + sy * g.n + sx] * bblk[(size_t)r * g.m + i];
+    }
+    Stats st{dd.Sq, dd.Sqq, rin.Sb, rin.Sbb, X};
+    int c, e;
+    double sh, oh;
+    fp64_codes(g, st, c, e, sh, oh);
+    double R = 0.0;
+    for (int i = 0; i < g.m; ++i) {
+        int sy, sx;
+        sym_src(k, g.n, i / g.n, i % g.n, sy, sx);
+        const double a = __dmul_rn(0.25, (double)qblk[(size_t)d * g.m + sy * g.n + sx]);
+        const double t = __dsub_rn(__dadd_rn(__dmul_rn(sh, a), oh), (double)bblk[(size_t)r * g.m + i]);
+        R = __dadd_rn(R, __dmul_rn(t, t));
+    }
+    fic_map mp;
+    mp.range_idx = (uint32_t)r;
+    mp.domain_idx = (uint32_t)d;
+    mp.iso = k;
+    mp.s_code = c;
+    mp.o_code = e;
+    mp.s = (float)sh;
+    mp.o = (float)oh;
+    mp.info = (wv & 0x80000000u) ? FIC_MAP_FALLBACK : 0u;
+    mp.err = R;
+    maps[r] = mp;
+}
+
+cudaError_t launch_rescore(const Geometry &g, const EpiConst &ec, const RangeInfo *ri,
+                           const DomainInfo *di, const uint16_t *bblk, const uint16_t *qblk,
+                           const ListEntry *lists, int n_lists, const float *qp2max, uint32_t *winner,
+                           int *fb_list, int *fb_count, cudaStream_t st)
+{
+    k_rescore<<<(g.R + 3) / 4, 128, 0, st>>>(g, ec, ri, di, bblk, qblk, lists, n_lists, qp2max, winner,
+                                             fb_list, fb_count);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fallback(const Geometry &g, const RangeInfo *ri, const DomainInfo *di,
+                            const uint16_t *bblk, const uint16_t *qblk, const int *fb_list,
+                            const int *fb_count, uint32_t *winner, cudaStream_t st)
+{
+    k_fallback<<<304, 256, 0, st>>>(g, ri, di, bblk, qblk, fb_list, fb_count, winner);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(const Geometry &g, const RangeInfo *ri, const DomainInfo *di,
+                            const uint16_t *bblk, const uint16_t *qblk, const uint32_t *winner,
+                            fic_map *maps, cudaStream_t st)
+{
+    k_finalize<<<(g.R + 127) / 128, 128, 0, st>>>(g, ri, di, bblk, qblk, winner, maps);
+    return cudaGetLastError();
+}
+
+}  // namespace fic

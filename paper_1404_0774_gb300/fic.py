@@ -1,0 +1,209 @@
+"""Thin ctypes binding of libfic.so (include/fic.h).
+
+Argument marshalling only: every step of encoding and decoding runs in the
+library's CUDA kernels.  Device buffers are torch CUDA tensors (torch is used
+for device memory and streams only); host buffers are numpy arrays.  If the
+compiled library is missing this module raises on import of any entry point:
+there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "_lib", "libfic.so")
+
+FIC_OK = 0
+FIC_SEARCH_AUTO, FIC_SEARCH_TC, FIC_SEARCH_SIMT = 0, 1, 2
+FIC_MAP_FALLBACK = 0x1
+FIC_FLAG_PHASE_TIMING = 0x1
+STATUS = {0: "ok", -1: "bad argument", -2: "bad size", -3: "bad bit depth", -4: "capacity",
+          -5: "cuda error", -6: "timeout", -7: "unsupported"}
+
+
+class FicError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {STATUS.get(code, code)} ({code})")
+        self.code = code
+
+
+class fic_params(ctypes.Structure):
+    _fields_ = [("range_size", ctypes.c_int32), ("domain_stride", ctypes.c_int32),
+                ("bit_depth", ctypes.c_int32), ("s_bits", ctypes.c_int32), ("o_bits", ctypes.c_int32),
+                ("decode_iters", ctypes.c_int32), ("search", ctypes.c_int32), ("n_split", ctypes.c_int32),
+                ("flags", ctypes.c_uint32)]
+
+
+MAP_DTYPE = np.dtype([("range_idx", np.uint32), ("domain_idx", np.uint32), ("iso", np.int32),
+                      ("s_code", np.int32), ("o_code", np.int32), ("s", np.float32), ("o", np.float32),
+                      ("info", np.uint32), ("err", np.float64)])
+assert MAP_DTYPE.itemsize == 40
+
+_lib = None
+
+
+def lib():
+    """Load libfic.so (build it first with paper_1404_0774_gb300.build.build())."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_LIB_PATH):
+            raise ImportError(f"libfic.so not built: {_LIB_PATH} is missing (run __graft_entry__.build())")
+        L = ctypes.CDLL(_LIB_PATH)
+        vp, sz, i64p = ctypes.c_void_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_int64)
+        pp = ctypes.POINTER(fic_params)
+        L.fic_default_params.argtypes = [pp]
+        L.fic_default_params.restype = None
+        L.fic_counts.argtypes = [ctypes.c_int, ctypes.c_int, pp, i64p, i64p]
+        L.fic_encode_workspace_size.argtypes = [ctypes.c_int, ctypes.c_int, pp, ctypes.POINTER(sz)]
+        L.fic_decode_workspace_size.argtypes = [ctypes.c_int, ctypes.c_int, pp, ctypes.POINTER(sz)]
+        L.fic_encode.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, pp, vp, ctypes.c_int,
+                                 ctypes.POINTER(ctypes.c_int), vp, sz, vp]
+        L.fic_decode.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, pp, ctypes.c_float, vp, vp,
+                                 sz, vp]
+        L.fic_status_str.argtypes = [ctypes.c_int]
+        L.fic_status_str.restype = ctypes.c_char_p
+        L.fic_last_encode_stats.argtypes = [i64p]
+        L.fic_last_encode_phase_ms.argtypes = [ctypes.POINTER(ctypes.c_double)]
+        _lib = L
+    return _lib
+
+
+def params(range_size=8, domain_stride=8, bit_depth=8, s_bits=5, o_bits=7, decode_iters=10,
+           search=FIC_SEARCH_AUTO, n_split=0, flags=0) -> fic_params:
+    return fic_params(range_size, domain_stride, bit_depth, s_bits, o_bits, decode_iters, search, n_split,
+                      flags)
+
+
+def _check(rc: int, what: str):
+    if rc != FIC_OK:
+        raise FicError(rc, what)
+
+
+def counts(w: int, h: int, p: fic_params):
+    r, d = ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().fic_counts(w, h, ctypes.byref(p), ctypes.byref(r), ctypes.byref(d)), "fic_counts")
+    return r.value, d.value
+
+
+def encode_workspace_size(w: int, h: int, p: fic_params) -> int:
+    b = ctypes.c_size_t()
+    _check(lib().fic_encode_workspace_size(w, h, ctypes.byref(p), ctypes.byref(b)), "fic_encode_workspace_size")
+    return b.value
+
+
+def decode_workspace_size(w: int, h: int, p: fic_params) -> int:
+    b = ctypes.c_size_t()
+    _check(lib().fic_decode_workspace_size(w, h, ctypes.byref(p), ctypes.byref(b)), "fic_decode_workspace_size")
+    return b.value
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+
+        return torch.cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def encode(img, p: fic_params, maps=None, workspace=None, stream=None):
+    """Encode one image.
+
+    img: torch CUDA tensor (uint8, or int16/uint16 holding values < 2^12) or a
+    numpy array (host).  Returns maps: for a CUDA image a torch uint8 tensor of
+    R*40 bytes on the same device (view with ``maps_to_numpy``), for a host
+    image a numpy MAP_DTYPE array.  ``workspace`` is an optional device byte
+    tensor of at least ``encode_workspace_size`` bytes.
+    """
+    h, w = int(img.shape[0]), int(img.shape[1])
+    R, _ = counts(w, h, p)
+    if _is_torch(img):
+        import torch
+
+        if not img.is_cuda:
+            raise ValueError("torch image must be on a CUDA device")
+        pitch = int(img.stride(0))
+        if img.stride(1) != 1:
+            raise ValueError("image rows must be contiguous")
+        if maps is None:
+            maps = torch.empty(R * MAP_DTYPE.itemsize, dtype=torch.uint8, device=img.device)
+        img_ptr, maps_ptr = img.data_ptr(), maps.data_ptr()
+        st = _stream_ptr(stream)
+    else:
+        a = np.ascontiguousarray(img, dtype=np.uint8 if p.bit_depth <= 8 else np.uint16)
+        img = a
+        pitch = w
+        if maps is None:
+            maps = np.zeros(R, MAP_DTYPE)
+        img_ptr, maps_ptr = a.ctypes.data, maps.ctypes.data
+        st = 0 if stream is None else _stream_ptr(stream)
+    ws_ptr, ws_bytes = (None, 0)
+    if workspace is not None:
+        ws_ptr, ws_bytes = workspace.data_ptr(), workspace.numel() * workspace.element_size()
+    n = ctypes.c_int()
+    _check(lib().fic_encode(img_ptr, w, h, pitch, ctypes.byref(p), maps_ptr, R, ctypes.byref(n), ws_ptr,
+                            ws_bytes, st), "fic_encode")
+    return maps
+
+
+def decode(maps, w: int, h: int, p: fic_params, init: float | None = None, out=None, workspace=None,
+           stream=None):
+    """Decode maps (device tensor or host MAP_DTYPE array) into a w x h float32 image."""
+    R, _ = counts(w, h, p)
+    if init is None:
+        init = float(1 << (p.bit_depth - 1))
+    if _is_torch(maps):
+        import torch
+
+        if out is None:
+            out = torch.empty((h, w), dtype=torch.float32, device=maps.device)
+        maps_ptr, out_ptr, st = maps.data_ptr(), out.data_ptr(), _stream_ptr(stream)
+    else:
+        maps = np.ascontiguousarray(maps, MAP_DTYPE)
+        if out is None:
+            out = np.zeros((h, w), np.float32)
+        maps_ptr, out_ptr = maps.ctypes.data, out.ctypes.data
+        st = 0 if stream is None else _stream_ptr(stream)
+    ws_ptr, ws_bytes = (None, 0)
+    if workspace is not None:
+        ws_ptr, ws_bytes = workspace.data_ptr(), workspace.numel() * workspace.element_size()
+    _check(lib().fic_decode(maps_ptr, R, w, h, ctypes.byref(p), ctypes.c_float(init), out_ptr, ws_ptr, ws_bytes,
+                            st), "fic_decode")
+    return out
+
+
+def maps_to_numpy(maps) -> np.ndarray:
+    """View a device maps tensor (uint8, R*40 bytes) as a host MAP_DTYPE array."""
+    if _is_torch(maps):
+        return maps.detach().cpu().numpy().view(MAP_DTYPE)
+    return np.asarray(maps, MAP_DTYPE)
+
+
+def last_encode_stats():
+    out = (ctypes.c_int64 * 4)()
+    lib().fic_last_encode_stats(out)
+    return list(out)
+
+
+def last_encode_phase_ms():
+    """[prep, search, rescore, fallback, output] ms of the last encode run with
+    FIC_FLAG_PHASE_TIMING (waits for its events)."""
+    out = (ctypes.c_double * 5)()
+    _check(lib().fic_last_encode_phase_ms(out), "fic_last_encode_phase_ms")
+    return list(out)
+
+
+def header_symbols() -> list[str]:
+    """Function names declared in include/fic.h (for the ABI-export test)."""
+    import re
+
+    hdr = os.path.join(os.path.dirname(_HERE), "include", "fic.h")
+    with open(hdr) as fh:
+        text = fh.read()
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(fic_\w+)\s*\(", text, re.M)))

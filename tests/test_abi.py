@@ -1,0 +1,60 @@
+"""The C ABI library loads and exports every entry point include/fic.h
+declares; host-side validation works without a GPU (no compute calls)."""
+import ctypes
+
+import pytest
+
+
+@pytest.fixture(scope="module")
+def fic():
+    from paper_1404_0774_gb300 import build
+
+    build.build()
+    from paper_1404_0774_gb300 import fic
+
+    return fic
+
+
+def test_exports_every_declared_symbol(fic):
+    names = fic.header_symbols()
+    assert "fic_encode" in names and "fic_decode" in names
+    lib = fic.lib()
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def test_counts_and_validation(fic):
+    p = fic.params(range_size=8, domain_stride=4, bit_depth=12)
+    assert fic.counts(512, 512, p) == (4096, 15625)
+    p1 = fic.params(range_size=8, domain_stride=8, bit_depth=8)
+    assert fic.counts(256, 256, p1) == (1024, 961)
+    for bad in [(250, 256, p1), (8, 256, p1), (256, 0, p1)]:
+        with pytest.raises(fic.FicError) as ei:
+            fic.counts(*bad)
+        assert ei.value.code == -2
+    with pytest.raises(fic.FicError) as ei:
+        fic.counts(256, 256, fic.params(bit_depth=13))
+    assert ei.value.code == -3
+    with pytest.raises(fic.FicError) as ei:
+        fic.counts(256, 256, fic.params(range_size=6))
+    assert ei.value.code == -1
+
+
+def test_status_strings(fic):
+    lib = fic.lib()
+    for code in range(-7, 1):
+        assert lib.fic_status_str(code)
+
+
+def test_encode_rejects_bad_arguments_before_any_gpu_work(fic):
+    lib = fic.lib()
+    p = fic.params()
+    n = ctypes.c_int()
+    # null image / maps
+    assert lib.fic_encode(None, 64, 64, 64, ctypes.byref(p), None, 64, ctypes.byref(n), None, 0, None) == -1
+    buf = (ctypes.c_uint8 * 4096)()
+    maps = (ctypes.c_uint8 * (40 * 64))()
+    # maps capacity below the range count
+    assert lib.fic_encode(buf, 64, 64, 64, ctypes.byref(p), maps, 10, ctypes.byref(n), None, 0, None) == -4
+    # pitch smaller than width
+    assert lib.fic_encode(buf, 64, 64, 32, ctypes.byref(p), maps, 64, ctypes.byref(n), None, 0, None) == -1

@@ -1,0 +1,149 @@
+"""Parity of the CUDA encoder/decoder (through the C ABI) with the FP64 oracle.
+
+For every checked range:
+  * the map the GPU returns, re-scored by the oracle for the same
+    (domain, symmetry), has identical s/o codes and an identical FP64
+    residual (both sides evaluate eq 8-12 with the same operation order);
+  * its residual is within 1e-5 relative (plus 1e-9*m*P^2 absolute, for exact
+    zeros) of the oracle's per-range minimum over all candidates;
+  * index agreement with the oracle's choice is reported; it is not required,
+    because equal residuals admit several correct maps.
+Decoding: GPU FP32 decode of the same maps as the FP64 oracle decode, pixel
+by pixel, and the decoded PSNR within 0.01 dB.
+"""
+import numpy as np
+import pytest
+
+import fic_synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+REL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def fic():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_1404_0774_gb300 import fic
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return fic
+
+
+def gpu_encode(fic, img, p):
+    dev = torch.device("cuda:0")
+    t = torch.from_numpy(img.astype(np.int16) if img.dtype == np.uint16 else img).to(dev)
+    maps = fic.encode(t, p)
+    torch.cuda.synchronize()
+    return fic.maps_to_numpy(maps)
+
+
+def check_against_oracle(orc, img, got, n, t, B, sb=5, ob=7, ranges=None):
+    m, P = n * n, (1 << B) - 1
+    h, w = img.shape
+    R = (h // n) * (w // n)
+    assert len(got) == R
+    assert np.array_equal(got["range_idx"], np.arange(R))
+    # every map is a valid, self-consistent candidate: oracle re-score agrees exactly
+    for r in range(R):
+        f = orc.fit_candidate(img, r, int(got["domain_idx"][r]), int(got["iso"][r]), n=n, t=t,
+                              bit_depth=B, s_bits=sb, o_bits=ob)
+        assert (f["c"], f["e"]) == (got["s_code"][r], got["o_code"][r]), r
+        assert f["err"] == got["err"][r], (r, f["err"], got["err"][r])
+        assert np.float32(f["s_hat"]) == got["s"][r] and np.float32(f["o_hat"]) == got["o"][r]
+    sel = np.arange(R) if ranges is None else np.asarray(ranges)
+    ref = orc.encode(img, n=n, t=t, bit_depth=B, s_bits=sb, o_bits=ob, ranges=sel)
+    e_gpu = got["err"][sel]
+    bound = ref["err"] * (1 + REL) + 1e-9 * m * P * P
+    bad = np.nonzero(e_gpu > bound)[0]
+    assert bad.size == 0, f"ranges {sel[bad][:10]} worse than the oracle minimum"
+    same = np.mean((got["domain_idx"][sel] == ref["d"]) & (got["iso"][sel] == ref["k"]))
+    return same
+
+
+CASES = [
+    # (name, image factory, n, t, B)
+    ("mr64_t4", lambda: fic_synth.mr_slice(5, 64), 8, 4, 8),
+    ("ct64_t4", lambda: fic_synth.ct_slice(6, 64), 8, 4, 12),
+    ("rand12_96x64", lambda: fic_synth.random_image(7, 64, 96, 12), 8, 8, 12),
+    ("rand8_n4", lambda: fic_synth.random_image(8, 32, 32, 8), 4, 2, 8),
+    ("ct_n16", lambda: fic_synth.ct_slice(9, 64), 16, 8, 12),
+    ("min_size", lambda: fic_synth.random_image(10, 16, 16, 8), 8, 8, 8),
+    ("constant", lambda: np.full((48, 48), 1234, np.uint16), 8, 4, 12),
+    ("flat_regions", lambda: np.where(fic_synth.random_image(11, 64, 64, 8) > 128, 200, 10).astype(np.uint8), 8, 4, 8),
+    ("b10_rand", lambda: fic_synth.random_image(12, 48, 48, 10).astype(np.uint16), 8, 4, 10),
+]
+
+
+@pytest.mark.parametrize("name,make,n,t,B", CASES, ids=[c[0] for c in CASES])
+@pytest.mark.parametrize("search", ["simt"])
+def test_encode_parity_small(fic, orc, name, make, n, t, B, search):
+    img = make()
+    p = fic.params(range_size=n, domain_stride=t, bit_depth=B,
+                   search={"simt": fic.FIC_SEARCH_SIMT, "tc": fic.FIC_SEARCH_TC}[search])
+    got = gpu_encode(fic, img, p)
+    check_against_oracle(orc, img, got, n, t, B)
+
+
+@pytest.mark.parametrize("n_split", [1, 3, 0])
+def test_encode_parity_splits(fic, orc, n_split):
+    img = fic_synth.ct_slice(13, 96)
+    p = fic.params(range_size=8, domain_stride=4, bit_depth=12, search=fic.FIC_SEARCH_SIMT, n_split=n_split)
+    check_against_oracle(orc, img, gpu_encode(fic, img, p), 8, 4, 12)
+
+
+def test_mr_slice_256_full(fic, orc):
+    """256x256 8-bit MR-like slice, 8x8 ranges, domains at stride 8: every range."""
+    img = fic_synth.mr_slice()
+    p = fic.params(range_size=8, domain_stride=8, bit_depth=8)
+    same = check_against_oracle(orc, img, gpu_encode(fic, img, p), 8, 8, 8)
+    assert same > 0.99
+
+
+def test_ct_slice_512_sampled(fic, orc):
+    """512x512 12-bit CT-like slice, 8x8 ranges, domains at stride 4 (5.12e8
+    comparisons): every map re-scored, minimum checked on sampled ranges."""
+    img = fic_synth.ct_slice()
+    p = fic.params(range_size=8, domain_stride=4, bit_depth=12)
+    got = gpu_encode(fic, img, p)
+    rng = np.random.default_rng(0)
+    sample = np.sort(rng.choice(4096, 96, replace=False))
+    check_against_oracle(orc, img, got, 8, 4, 12, ranges=sample)
+
+
+def test_host_and_device_pointers_agree(fic):
+    img = fic_synth.ct_slice(14, 64)
+    p = fic.params(range_size=8, domain_stride=4, bit_depth=12)
+    dev = gpu_encode(fic, img, p)
+    host = fic.encode(img, p)
+    assert np.array_equal(dev, host)
+
+
+@pytest.mark.parametrize("B,n,t", [(8, 8, 8), (12, 8, 4)])
+def test_decode_parity(fic, orc, B, n, t):
+    img = fic_synth.mr_slice(size=128) if B == 8 else fic_synth.ct_slice(15, 128)
+    p = fic.params(range_size=n, domain_stride=t, bit_depth=B, decode_iters=10)
+    maps = fic.encode(torch.from_numpy(img.astype(np.int16) if B > 8 else img).cuda(), p)
+    out = fic.decode(maps, 128, 128, p)
+    torch.cuda.synchronize()
+    got = fic.maps_to_numpy(maps)
+    ref = orc.decode(got["domain_idx"], got["iso"], got["s_code"] / ((1 << 4) - 1),
+                     got["o_code"] * ((1 << B) - 1) / 63.0, 128, 128, n=n, t=t, bit_depth=B, iters=10)
+    diff = np.abs(out.cpu().numpy().astype(np.float64) - ref)
+    assert diff.max() < 2e-6 * (1 << B) * 10
+    assert abs(orc.psnr(img, out.cpu().numpy(), B) - orc.psnr(img, ref, B)) < 0.01
+    # host maps / host output path
+    host = fic.decode(got, 128, 128, p)
+    assert np.array_equal(host, out.cpu().numpy())
+
+
+def test_decode_rejects_invalid_host_maps(fic):
+    p = fic.params(range_size=8, domain_stride=8, bit_depth=8)
+    maps = np.zeros(16, fic.MAP_DTYPE)
+    maps["domain_idx"][3] = 10 ** 6
+    with pytest.raises(fic.FicError):
+        fic.decode(maps, 32, 32, p)
