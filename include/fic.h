@@ -99,6 +99,7 @@ typedef struct {
 } fic_map;
 
 #define FIC_MAP_FALLBACK 0x1u /* resolved by the exact full rescan           */
+#define FIC_MAP_ERROR 0x2u    /* a bounded device wait timed out: invalid    */
 
 /* Fill `p` with the defaults of the workloads (n=8, t=8, B=8, 5/7 bits,
  * 10 decode iterations, automatic search). */
@@ -150,6 +151,19 @@ const char *fic_status_str(int status);
  * out[0] = ranges resolved by the exact full rescan, out[1] = number of
  * candidate lists, out[2] = search implementation used (FIC_SEARCH_*). */
 int fic_last_encode_stats(int64_t out[4]);
+
+/*
+ * fic_cross_terms -- the contraction alone, for testing: runs the encode's
+ *   prep and the selected search path's cross-term stage and writes
+ *   Xt[r][c] = sum_i q'_i b'_i - e_r f_d / m = (m*X - Sq*Sb)/m as FP32 for
+ *   every range r and candidate c (row-major, R x 8D floats, DEVICE memory
+ *   `out`), where X = sum_i q_i b_i is the eq 9 cross term (q the 2x2 sums of
+ *   S_k(domain d), b the range pixels), Sq = sum q, Sb = sum b.  `img` as in
+ *   fic_encode (device); workspace as fic_encode (NULL = allocate).
+ *   Returns FIC_ERR_TIMEOUT if a bounded device wait expired.
+ */
+int fic_cross_terms(const void *img, int w, int h, int pitch_px, const fic_params *p, float *out,
+                    void *workspace, size_t workspace_bytes, void *stream);
 
 /* Phase durations (ms) of the last fic_encode on this host thread that ran
  * with FIC_FLAG_PHASE_TIMING: out[0] prep, out[1] search, out[2] re-score,

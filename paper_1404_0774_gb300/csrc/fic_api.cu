@@ -108,20 +108,27 @@ int sm_count()
 
 int choose_search(const Geometry &g, const fic_params *p)
 {
-    (void)g;
-    if (p->search == FIC_SEARCH_TC) return -1;  // not available in this build
-    return FIC_SEARCH_SIMT;
+    if (p->search == FIC_SEARCH_SIMT) return FIC_SEARCH_SIMT;
+    if (search_tc_supported(g)) return FIC_SEARCH_TC;
+    return p->search == FIC_SEARCH_TC ? -1 : FIC_SEARCH_SIMT;
 }
 
+// Split of the candidate dimension: enough CTAs for whole waves over the SMs.
 int choose_split(const Geometry &g, const fic_params *p, int search)
 {
-    (void)search;
-    const int tiles = (g.N + 63) / 64;
+    const int tile = search == FIC_SEARCH_TC ? search_tc_tile() : 64;
+    const int tiles = (g.N + tile - 1) / tile;
     const int mt = (g.R + 127) / 128;
     int s = p->n_split;
-    if (s == 0) s = std::max(1, (2 * 2 * sm_count() + mt - 1) / mt);
-    return std::max(1, std::min(s, tiles));
+    if (s == 0) {
+        const int per_sm = search == FIC_SEARCH_TC ? 1 : 2;
+        const int target = 4 * per_sm * sm_count();  // four waves
+        s = std::max(1, (target + mt - 1) / mt);
+    }
+    return std::max(1, std::min(std::min(s, tiles), 64));
 }
+
+int lists_per_split(int search) { return search == FIC_SEARCH_SIMT ? search_simt_lists_per_split() : 1; }
 
 struct EncLayout {
     size_t img, ri, di, dconst, bblk, qblk, rs32, cb32, ra16, cb16, lists, winner, fb_list, fb_count,
@@ -147,8 +154,8 @@ EncLayout enc_layout(const Geometry &g, int search, int n_lists)
     const bool simt = search == FIC_SEARCH_SIMT;
     L.rs32 = simt ? take(sizeof(float) * (size_t)g.R * g.m) : 0;
     L.cb32 = simt ? take(sizeof(float) * (size_t)g.N * g.m) : 0;
-    L.ra16 = simt ? 0 : take(sizeof(__half) * (size_t)g.R * g.KP);
-    L.cb16 = simt ? 0 : take(sizeof(__half) * (size_t)g.N * g.KP);
+    L.ra16 = simt ? 0 : take(sizeof(__half) * (size_t)search_tc_rows(g.R) * g.KP);
+    L.cb16 = simt ? 0 : take(sizeof(__half) * (size_t)search_tc_rows(g.N) * g.KP);
     L.lists = take(sizeof(ListEntry) * (size_t)g.R * n_lists * kListK);
     L.winner = take(sizeof(uint32_t) * g.R);
     L.fb_list = take(sizeof(int) * g.R);
@@ -215,24 +222,28 @@ int fic_encode_workspace_size(int w, int h, const fic_params *p, size_t *bytes)
     if (rc != FIC_OK) return rc;
     const int search = choose_search(g, p);
     if (search < 0) return FIC_ERR_UNSUPPORTED;
-    const int lps = search == FIC_SEARCH_SIMT ? search_simt_lists_per_split() : 1;
-    *bytes = enc_layout(g, search, choose_split(g, p, search) * lps).total;
+    *bytes = enc_layout(g, search, choose_split(g, p, search) * lists_per_split(search)).total;
     return FIC_OK;
 }
 
-int fic_encode(const void *img, int w, int h, int pitch_px, const fic_params *p, fic_map *maps,
-               int maps_cap, int *n_maps, void *workspace, size_t workspace_bytes, void *stream)
+}  // extern "C"
+
+namespace {
+
+// Shared pipeline of fic_encode and fic_cross_terms (dump != nullptr: stop
+// after the contraction and write the raw cross terms there).
+int run_encode(const void *img, int w, int h, int pitch_px, const fic_params *p, fic_map *maps, int maps_cap,
+               int *n_maps, void *workspace, size_t workspace_bytes, void *stream, float *dump)
 {
-    if (!img || !maps) return FIC_ERR_BAD_ARG;
+    if (!img || (!maps && !dump)) return FIC_ERR_BAD_ARG;
     Geometry g;
     int rc = make_geometry(w, h, pitch_px, p, g);
     if (rc != FIC_OK) return rc;
-    if (maps_cap < g.R) return FIC_ERR_CAPACITY;
+    if (!dump && maps_cap < g.R) return FIC_ERR_CAPACITY;
     const int search = choose_search(g, p);
     if (search < 0) return FIC_ERR_UNSUPPORTED;
     const int n_split = choose_split(g, p, search);
-    const int lps = search == FIC_SEARCH_SIMT ? search_simt_lists_per_split() : 1;
-    const int n_lists = n_split * lps;
+    const int n_lists = n_split * lists_per_split(search);
     const EncLayout L = enc_layout(g, search, n_lists);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     char *ws = static_cast<char *>(workspace);
@@ -248,7 +259,7 @@ int fic_encode(const void *img, int w, int h, int pitch_px, const fic_params *p,
     }
     {
         const bool img_dev = is_device_ptr(img);
-        const bool maps_dev = is_device_ptr(maps);
+        const bool maps_dev = dump ? true : is_device_ptr(maps);
         const size_t elem = g.B <= 8 ? 1 : 2;
         const void *dimg = img;
         Geometry gd = g;
@@ -271,34 +282,50 @@ int fic_encode(const void *img, int w, int h, int pitch_px, const fic_params *p,
         uint32_t *winner = reinterpret_cast<uint32_t *>(ws + L.winner);
         int *fb_list = reinterpret_cast<int *>(ws + L.fb_list);
         int *fb_count = reinterpret_cast<int *>(ws + L.fb_count);
+        int *err = fb_count + 1;
         float *qp2max = reinterpret_cast<float *>(ws + L.qp2max);
         fic_map *dmaps = maps_dev ? maps : reinterpret_cast<fic_map *>(ws + L.maps);
         const EpiConst ec = make_epi(g);
-        const bool timed = (p->flags & FIC_FLAG_PHASE_TIMING) && g_phase.ensure();
+        const bool timed = !dump && (p->flags & FIC_FLAG_PHASE_TIMING) && g_phase.ensure();
         g_phase.valid = false;
 #define FIC_MARK(i) \
     if (timed) FIC_CUDA(cudaEventRecord(g_phase.ev[i], st))
 
-        FIC_CUDA(cudaMemsetAsync(fb_count, 0, sizeof(int), st));
+        FIC_CUDA(cudaMemsetAsync(fb_count, 0, 2 * sizeof(int), st));
+        if (ra16) {  // zero the padding rows that complete the last TMA boxes
+            const size_t row = sizeof(__half) * g.KP;
+            FIC_CUDA(cudaMemsetAsync(ws + L.ra16 + row * g.R, 0, row * (search_tc_rows(g.R) - g.R), st));
+            FIC_CUDA(cudaMemsetAsync(ws + L.cb16 + row * g.N, 0, row * (search_tc_rows(g.N) - g.N), st));
+        }
         FIC_MARK(0);
         FIC_CUDA(launch_prep(gd, dimg, ri, di, dconst, bblk, qblk, rs32, cb32, ra16, cb16, st));
         FIC_CUDA(launch_qp2max(gd, di, qp2max, st));
         FIC_MARK(1);
-        FIC_CUDA(launch_search_simt(gd, ec, ri, di, dconst, rs32, cb32, lists, n_split, st));
+        if (search == FIC_SEARCH_TC)
+            FIC_CUDA(launch_search_tc(gd, ec, ri, dconst, ra16, cb16, lists, n_split, dump, err, st));
+        else
+            FIC_CUDA(launch_search_simt(gd, ec, ri, di, dconst, rs32, cb32, lists, n_split, dump, st));
         FIC_MARK(2);
-        FIC_CUDA(launch_rescore(gd, ec, ri, di, bblk, qblk, lists, n_lists, qp2max, winner, fb_list,
-                                fb_count, st));
-        FIC_MARK(3);
-        FIC_CUDA(launch_fallback(gd, ri, di, bblk, qblk, fb_list, fb_count, winner, st));
-        FIC_MARK(4);
-        FIC_CUDA(launch_finalize(gd, ri, di, bblk, qblk, winner, dmaps, st));
-        FIC_MARK(5);
+        if (!dump) {
+            FIC_CUDA(launch_rescore(gd, ec, ri, di, bblk, qblk, lists, n_lists, qp2max, winner, fb_list,
+                                    fb_count, st));
+            FIC_MARK(3);
+            FIC_CUDA(launch_fallback(gd, ri, di, bblk, qblk, fb_list, fb_count, winner, st));
+            FIC_MARK(4);
+            FIC_CUDA(launch_finalize(gd, ri, di, bblk, qblk, winner, err, dmaps, st));
+            FIC_MARK(5);
+        }
 #undef FIC_MARK
         g_phase.valid = timed;
-        if (!maps_dev) {
+        const bool sync = dump || !maps_dev || !img_dev;
+        if (!dump && !maps_dev)
             FIC_CUDA(cudaMemcpyAsync(maps, dmaps, sizeof(fic_map) * g.R, cudaMemcpyDeviceToHost, st));
+        if (sync) {
+            int herr = 0;
+            FIC_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+            FIC_CUDA(cudaStreamSynchronize(st));
+            if (herr) rc = FIC_ERR_TIMEOUT;
         }
-        if (!maps_dev || !img_dev) FIC_CUDA(cudaStreamSynchronize(st));
         g_stats[0] = -1;
         g_stats[1] = n_lists;
         g_stats[2] = search;
@@ -313,6 +340,25 @@ done:
         }
     }
     return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fic_encode(const void *img, int w, int h, int pitch_px, const fic_params *p, fic_map *maps,
+               int maps_cap, int *n_maps, void *workspace, size_t workspace_bytes, void *stream)
+{
+    if (!maps) return FIC_ERR_BAD_ARG;
+    return run_encode(img, w, h, pitch_px, p, maps, maps_cap, n_maps, workspace, workspace_bytes, stream,
+                      nullptr);
+}
+
+int fic_cross_terms(const void *img, int w, int h, int pitch_px, const fic_params *p, float *out,
+                    void *workspace, size_t workspace_bytes, void *stream)
+{
+    if (!out) return FIC_ERR_BAD_ARG;
+    return run_encode(img, w, h, pitch_px, p, nullptr, 0, nullptr, workspace, workspace_bytes, stream, out);
 }
 
 int fic_decode(const fic_map *maps, int n_maps, int w, int h, const fic_params *p, float init,

@@ -228,7 +228,15 @@ cudaError_t launch_prep(const Geometry &g, const void *img, RangeInfo *ri, Domai
                         __half *ra16, __half *cb16, cudaStream_t st);
 cudaError_t launch_search_simt(const Geometry &g, const EpiConst &ec, const RangeInfo *ri,
                                const DomainInfo *di, const float4 *dconst, const float *rs32,
-                               const float *cb32, ListEntry *lists, int n_split, cudaStream_t st);
+                               const float *cb32, ListEntry *lists, int n_split, float *dump,
+                               cudaStream_t st);
+bool search_tc_supported(const Geometry &g);
+size_t search_tc_smem(const Geometry &g);
+int search_tc_tile();
+int search_tc_rows(int rows);  // operand rows allocated (multiple of the TMA box)
+cudaError_t launch_search_tc(const Geometry &g, const EpiConst &ec, const RangeInfo *ri, const float4 *dconst,
+                             const __half *ra16, const __half *cb16, ListEntry *lists, int n_split, float *dump,
+                             int *err, cudaStream_t st);
 int search_simt_lists_per_split();
 cudaError_t launch_rescore(const Geometry &g, const EpiConst &ec, const RangeInfo *ri,
                            const DomainInfo *di, const uint16_t *bblk, const uint16_t *qblk,
@@ -239,7 +247,7 @@ cudaError_t launch_fallback(const Geometry &g, const RangeInfo *ri, const Domain
                             const int *fb_count, uint32_t *winner, cudaStream_t st);
 cudaError_t launch_finalize(const Geometry &g, const RangeInfo *ri, const DomainInfo *di,
                             const uint16_t *bblk, const uint16_t *qblk, const uint32_t *winner,
-                            fic_map *maps, cudaStream_t st);
+                            const int *err, fic_map *maps, cudaStream_t st);
 size_t decode_workspace_bytes(const Geometry &g);
 cudaError_t launch_decode(const Geometry &g, const fic_map *maps, float init, int iters, void *ws,
                           float *out, cudaStream_t st);

@@ -108,7 +108,34 @@ __device__ long long warp_cross(const Geometry &g, const uint16_t *qblk, uint32_
 
 }  // namespace
 
+__device__ __forceinline__ double u128_to_double(unsigned __int128 v)
+{
+    return (double)(unsigned long long)(v >> 64) * 18446744073709551616.0 + (double)(unsigned long long)v;
+}
+
+// Exact residual (times D^2) of one candidate whose cross term is X.
+__device__ unsigned __int128 exact_candidate(const Geometry &g, Stats st, const DomainInfo *di, uint32_t idx,
+                                             long long X)
+{
+    const DomainInfo dd = di[idx >> 3];
+    st.Sq = dd.Sq;
+    st.Sqq = dd.Sqq;
+    st.X = X;
+    int c, e;
+    double sh, oh;
+    fp64_codes(g, st, c, e, sh, oh);
+    return (unsigned __int128)exact_err(g, st, c, e);
+}
+
 // One warp per range.
+//  1. U = exact residual of the entry with the best screening key.
+//  2. Finalists: entries whose key, less the screening error allowance,
+//     does not exceed U (keys may underestimate, never overestimate by more
+//     than the allowance).  Each is re-scored exactly; the winner is the
+//     smallest exact residual, ties to the lowest index.
+//  3. Certified when every full list's last key, less the allowance, is
+//     strictly above the winner's residual: then no candidate outside the
+//     lists can beat or tie it.
 __global__ void k_rescore(Geometry g, EpiConst ec, const RangeInfo *ri, const DomainInfo *di,
                           const uint16_t *bblk, const uint16_t *qblk, const ListEntry *lists,
                           int n_lists, const float *qp2max, uint32_t *winner, int *fb_list,
@@ -117,7 +144,7 @@ __global__ void k_rescore(Geometry g, EpiConst ec, const RangeInfo *ri, const Do
     const int warps = blockDim.x >> 5;
     const int r = blockIdx.x * warps + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
-    if (r >= g.R) return;
+    if (r >= g.R) return;  // warp-uniform
     const RangeInfo rin = ri[r];
     int b[kMaxM / 32];
 #pragma unroll
@@ -127,64 +154,83 @@ __global__ void k_rescore(Geometry g, EpiConst ec, const RangeInfo *ri, const Do
     }
     const ListEntry *L = lists + (size_t)r * n_lists * kListK;
     const int nent = n_lists * kListK;
-    // best screening key
-    float kbest = __int_as_float(0x7f800000);
-    for (int f = lane; f < nent; f += 32) kbest = fminf(kbest, L[f].key);
-    for (int off = 16; off > 0; off >>= 1) kbest = fminf(kbest, __shfl_xor_sync(0xffffffffu, kbest, off));
-    // screening error allowance in key units (2*Ls*R units)
-    const float two_ls = ec.two_ls;
-    const float delta_o = (float)g.m * 0.25f * ((float)g.P / g.Lo) * ((float)g.P / g.Lo);
-    const float mag = two_ls * (rin.sbbc + delta_o) + fabsf(kbest);
-    const float beta = 1.0f / 65536.0f * mag +
-                       ec.ls * (1.0f / 262144.0f) * sqrtf(*qp2max * rin.bp2) +
-                       ec.lambda * ec.G * 2.0f + 1e-3f;
-    const float kthr = kbest + 2.0f * beta;
-    // certification: every full list must end beyond the window
-    bool cert = true;
-    for (int l = lane; l < n_lists; l += 32) {
-        const ListEntry last = L[l * kListK + kListK - 1];
-        if (last.idx != 0xffffffffu && !(last.key > kthr)) cert = false;
+    // best screening key (ties to the lowest index)
+    float kb = __int_as_float(0x7f800000);
+    uint32_t ib = 0xffffffffu;
+    for (int f = lane; f < nent; f += 32) {
+        const ListEntry e = L[f];
+        if (e.idx != 0xffffffffu && (e.key < kb || (e.key == kb && e.idx < ib))) {
+            kb = e.key;
+            ib = e.idx;
+        }
     }
-    cert = __all_sync(0xffffffffu, cert);
-
+    for (int off = 16; off > 0; off >>= 1) {
+        const float ok = __shfl_xor_sync(0xffffffffu, kb, off);
+        const uint32_t oi = __shfl_xor_sync(0xffffffffu, ib, off);
+        if (ok < kb || (ok == kb && oi < ib)) {
+            kb = ok;
+            ib = oi;
+        }
+    }
+    if (ib == 0xffffffffu) {  // no candidate was listed: exact rescan
+        if (lane == 0) {
+            winner[r] = 0xffffffffu;
+            fb_list[atomicAdd(fb_count, 1)] = r;
+        }
+        return;
+    }
     Stats st;
     st.Sb = rin.Sb;
     st.Sbb = rin.Sbb;
+    const double invD2 = 1.0 / ((double)(4 * g.Ls * g.Lo) * (double)(4 * g.Ls * g.Lo));
+    const double inv2ls = 1.0 / (2.0 * g.Ls);
+    double U;
+    {
+        const long long X = warp_cross(g, qblk, ib, b);
+        U = u128_to_double(exact_candidate(g, st, di, ib, X)) * invD2;  // same on every lane
+    }
+    // screening error allowance, converted to residual units
+    const float delta_o = (float)g.m * 0.25f * ((float)g.P / g.Lo) * ((float)g.P / g.Lo);
+    const float beta_k = (ec.two_ls * (rin.sbbc + delta_o) + fabsf(kb)) * (1.0f / 65536.0f) +
+                         ec.ls * (1.0f / 262144.0f) * sqrtf(*qp2max * rin.bp2) + 2.0f * ec.lambda * ec.G + 1e-3f;
+    const double betaE = (double)beta_k * inv2ls;
+    const double sbbc = (double)rin.sbbc;
+
     unsigned __int128 best_e = ~(unsigned __int128)0;
     uint32_t best_i = 0xffffffffu;
     for (int f0 = 0; f0 < nent; f0 += 32) {
         const int f = f0 + lane;
-        ListEntry ent = f < nent ? L[f] : ListEntry{__int_as_float(0x7f800000), 0xffffffffu};
-        const bool fin = ent.idx != 0xffffffffu && ent.key <= kthr;
+        const ListEntry ent = f < nent ? L[f] : ListEntry{__int_as_float(0x7f800000), 0xffffffffu};
+        const bool fin = ent.idx != 0xffffffffu && sbbc + (double)ent.key * inv2ls - betaE <= U;
         unsigned mask = __ballot_sync(0xffffffffu, fin);
+        long long myX = 0;
         while (mask) {
             const int src = __ffs(mask) - 1;
             mask &= mask - 1;
             const uint32_t idx = __shfl_sync(0xffffffffu, ent.idx, src);
             const long long X = warp_cross(g, qblk, idx, b);
-            if (lane == src) {
-                const DomainInfo dd = di[idx >> 3];
-                st.Sq = dd.Sq;
-                st.Sqq = dd.Sqq;
-                st.X = X;
-                int c, e;
-                double sh, oh;
-                fp64_codes(g, st, c, e, sh, oh);
-                const unsigned __int128 er = (unsigned __int128)exact_err(g, st, c, e);
-                if (better(er, idx, best_e, best_i)) {
-                    best_e = er;
-                    best_i = idx;
-                }
+            if (lane == src) myX = X;
+        }
+        if (fin) {  // lanes re-score their own finalists in parallel
+            const unsigned __int128 er = exact_candidate(g, st, di, ent.idx, myX);
+            if (better(er, ent.idx, best_e, best_i)) {
+                best_e = er;
+                best_i = ent.idx;
             }
         }
     }
     warp_argmin(best_e, best_i);
+    const double Estar = u128_to_double(best_e) * invD2;
+    bool cert = true;
+    for (int l = lane; l < n_lists; l += 32) {
+        const ListEntry last = L[l * kListK + kListK - 1];
+        if (last.idx != 0xffffffffu && !(sbbc + (double)last.key * inv2ls - betaE > Estar * (1.0 + 1e-12) + 1e-12))
+            cert = false;
+    }
+    cert = __all_sync(0xffffffffu, cert);
     if (lane == 0) {
         winner[r] = best_i;
-        if (!cert || best_i == 0xffffffffu) {
-            const int slot = atomicAdd(fb_count, 1);
-            fb_list[slot] = r;
-        }
+        if (!cert) fb_list[atomicAdd(fb_count, 1)] = r;
     }
 }
 
@@ -279,7 +325,7 @@ __global__ void __launch_bounds__(256) k_fallback(Geometry g, const RangeInfo *r
 // One thread per range: FP64 codes and the eq 8 residual summed over the
 // pixels in order, written as the output map.
 __global__ void k_finalize(Geometry g, const RangeInfo *ri, const DomainInfo *di, const uint16_t *bblk,
-                           const uint16_t *qblk, const uint32_t *winner, fic_map *maps)
+                           const uint16_t *qblk, const uint32_t *winner, const int *err, fic_map *maps)
 {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= g.R) return;
@@ -315,7 +361,7 @@ __global__ void k_finalize(Geometry g, const RangeInfo *ri, const DomainInfo *di
     mp.o_code = e;
     mp.s = (float)sh;
     mp.o = (float)oh;
-    mp.info = (wv & 0x80000000u) ? FIC_MAP_FALLBACK : 0u;
+    mp.info = ((wv & 0x80000000u) ? FIC_MAP_FALLBACK : 0u) | (*err ? FIC_MAP_ERROR : 0u);
     mp.err = R;
     maps[r] = mp;
 }
@@ -340,9 +386,9 @@ cudaError_t launch_fallback(const Geometry &g, const RangeInfo *ri, const Domain
 
 cudaError_t launch_finalize(const Geometry &g, const RangeInfo *ri, const DomainInfo *di,
                             const uint16_t *bblk, const uint16_t *qblk, const uint32_t *winner,
-                            fic_map *maps, cudaStream_t st)
+                            const int *err, fic_map *maps, cudaStream_t st)
 {
-    k_finalize<<<(g.R + 127) / 128, 128, 0, st>>>(g, ri, di, bblk, qblk, winner, maps);
+    k_finalize<<<(g.R + 127) / 128, 128, 0, st>>>(g, ri, di, bblk, qblk, winner, err, maps);
     return cudaGetLastError();
 }
 

@@ -22,7 +22,7 @@ constexpr int XS = BN + 1;
 __global__ void __launch_bounds__(256) k_search_simt(Geometry g, EpiConst ec, const RangeInfo *ri,
                                                      const DomainInfo *di, const float4 *dconst,
                                                      const float *rs32, const float *cb32,
-                                                     ListEntry *lists, int n_split)
+                                                     ListEntry *lists, int n_split, float *dump)
 {
     extern __shared__ float smem[];
     float *As = smem;              // [KC][BM]
@@ -113,7 +113,11 @@ __global__ void __launch_bounds__(256) k_search_simt(Geometry g, EpiConst ec, co
                 Xs[(tr * 8 + i) * XS + tc * 4 + j] =
                     fmaf(-er_s[tr * 8 + i], fdm_s[tc * 4 + j], acc[i][j]);
         __syncthreads();
-        if (my_r < g.R) {
+        if (my_r < g.R && dump) {
+            const int c0 = n0 + er_half * 32;
+            for (int j = 0; j < 32 && c0 + j < g.N; ++j)
+                dump[(size_t)my_r * g.N + c0 + j] = Xs[er_row * XS + er_half * 32 + j];
+        } else if (my_r < g.R) {
             const int c0 = n0 + er_half * 32;
             const int nvalid = min(32, g.N - c0);
             if (nvalid > 0) {
@@ -130,7 +134,7 @@ __global__ void __launch_bounds__(256) k_search_simt(Geometry g, EpiConst ec, co
             }
         }
     }
-    if (my_r < g.R) {
+    if (my_r < g.R && !dump) {
         const int n_lists = n_split * 2;
         ListEntry *dst = lists + ((size_t)my_r * n_lists + split * 2 + er_half) * kListK;
 #pragma unroll
@@ -142,18 +146,14 @@ int search_simt_lists_per_split() { return 2; }
 
 cudaError_t launch_search_simt(const Geometry &g, const EpiConst &ec, const RangeInfo *ri,
                                const DomainInfo *di, const float4 *dconst, const float *rs32,
-                               const float *cb32, ListEntry *lists, int n_split, cudaStream_t st)
+                               const float *cb32, ListEntry *lists, int n_split, float *dump,
+                               cudaStream_t st)
 {
     const size_t smem = sizeof(float) * (KC * BM + KC * BN + BM * XS);
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_search_simt, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    cudaError_t e = cudaFuncSetAttribute(k_search_simt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
     dim3 grid((g.R + BM - 1) / BM, n_split);
-    k_search_simt<<<grid, 256, smem, st>>>(g, ec, ri, di, dconst, rs32, cb32, lists, n_split);
+    k_search_simt<<<grid, 256, smem, st>>>(g, ec, ri, di, dconst, rs32, cb32, lists, n_split, dump);
     return cudaGetLastError();
 }
 

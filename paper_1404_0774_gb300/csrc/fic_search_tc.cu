@@ -1,0 +1,428 @@
+// Tensor-core range-domain search for sm_103a (tcgen05 + TMA + TMEM).
+//
+// The cross term of eq 9, X = sum_i q_i b_i over all ranges x all candidates
+// (domain d, symmetry k), is a dense contraction M = ranges, N = candidates,
+// K = pixels.  Operands are centred integers in FP16 (exact):
+//   A row (range r):      [ b'_1..b'_m | b'_1..b'_m (12-bit only) | e_hi e_lo 0.. ]
+//   B row (candidate):    [ 128*hi_i   | lo_i       (12-bit only) | -16 f_d  -f_d/m 0.. ]
+// with q'_i = 128*hi_i + lo_i (8-bit: a single q' block), so that the FP32
+// accumulator is Xt = sum q'b' - e_r f_d / m = (m X - Sq Sb) / m.  The K
+// dimension is laid out as 64-element SWIZZLE_128B blocks plus one
+// 16-element SWIZZLE_32B tail block carrying the centring terms.
+//
+// CTA = 128 ranges (one per TMEM lane), streaming a contiguous slice of the
+// candidate dimension in tiles of 128:
+//   warp 0        TMA producer (one thread): A once, B tiles into a 4-stage ring
+//   warp 1        TMEM allocator + MMA issuer (one thread): 9 (12-bit) or 5
+//                 (8-bit) tcgen05.mma kind::f16 128x128x16 per tile into one
+//                 of two TMEM accumulators
+//   warps 2..5    epilogue: tcgen05.ld 32 columns at a time, FP32 screening
+//                 (eq 8-12 with quantisation), per-range top-4 list
+// Every mbarrier wait is bounded by a wall-clock limit; on expiry the CTA sets
+// an error flag, stops, drains its outstanding TMA loads (bounded), frees its
+// TMEM and exits.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include "fic_internal.cuh"
+
+namespace fic {
+namespace {
+
+constexpr int BM = 128;
+constexpr int BN = 128;
+constexpr int STAGES = 4;
+constexpr int NACC = 2;
+constexpr int THREADS = 192;
+constexpr uint32_t TMEM_COLS = BN * NACC;  // 256
+constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s per wait
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ unsigned long long gtimer()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for the phase of `parity` to complete.  Returns false when the
+// CTA is aborting (another role timed out) or this wait timed out.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_s, int *err)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = gtimer();
+    for (uint32_t i = 1;; ++i) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((i & 63) == 0) {
+            if (*abort_s) return false;
+            if (gtimer() - t0 > kWaitNs) {
+                *abort_s = 1;
+                atomicExch(err, 1);
+                return false;
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// SM100 shared-memory matrix descriptor, K-major, swizzled.
+// layout: 2 = SWIZZLE_128B (SBO 1024), 6 = SWIZZLE_32B (SBO 256)
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t sbo, uint32_t layout)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)1u << 16;                         // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;     // stride byte offset: 8-row group pitch
+    d |= (uint64_t)1u << 46;                         // descriptor version (sm_100 family)
+    d |= (uint64_t)layout << 61;
+    return d;
+}
+
+// Instruction descriptor: kind::f16, A = B = F16, D = F32, both K-major.
+__host__ __device__ constexpr uint32_t instr_desc(int M, int N)
+{
+    return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
+{
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+          "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+          "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+          "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+struct TcMaps {
+    CUtensorMap a128, a32, b128, b32;
+};
+
+}  // namespace
+
+// nblk: number of 64-element SWIZZLE_128B K blocks (1 for 8-bit, 2 for 12-bit).
+// dump != nullptr: write the raw accumulators Xt[r][c] instead of screening.
+template <int NBLK>
+__global__ void __launch_bounds__(THREADS, 1)
+    k_search_tc(const __grid_constant__ TcMaps maps, Geometry g, EpiConst ec, const RangeInfo *ri,
+                const float4 *dconst, ListEntry *lists, int n_split, float *dump, int *err)
+{
+    constexpr uint32_t A_BLK = BM * 128;                 // bytes of one 64-col block, A
+    constexpr uint32_t B_BLK = BN * 128;
+    constexpr uint32_t A_BYTES = NBLK * A_BLK + BM * 32;  // + SW32 tail
+    constexpr uint32_t B_BYTES = NBLK * B_BLK + BN * 32;
+    constexpr int KSTEPS = NBLK * 4 + 1;
+    constexpr uint32_t IDESC = instr_desc(BM, BN);
+
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint8_t *sA = smem;
+    uint8_t *sB = smem + A_BYTES;  // A_BYTES is a multiple of 1024
+    __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], a_bar, tfull_bar[NACC], tempty_bar[NACC];
+    __shared__ uint32_t tmem_base_s;
+    __shared__ int abort_s;
+
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const int r0 = blockIdx.x * BM;
+    const int split = blockIdx.y;
+    const int tiles = (g.N + BN - 1) / BN;
+    const int t_begin = (int)((long long)tiles * split / n_split);
+    const int t_end = (int)((long long)tiles * (split + 1) / n_split);
+    const int ntile = t_end - t_begin;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full_bar[s], 1);
+            mbar_init(&empty_bar[s], 1);
+        }
+        mbar_init(&a_bar, 1);
+        for (int a = 0; a < NACC; ++a) {
+            mbar_init(&tfull_bar[a], 1);
+            mbar_init(&tempty_bar[a], 4);  // one arrival per epilogue warp
+        }
+        abort_s = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&tmem_base_s)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = tmem_base_s;
+
+    if (warp == 0) {
+        // ------------------------------------------------------ TMA producer
+        if (lane == 0) {
+            int issued = 0;
+            mbar_expect_tx(&a_bar, A_BYTES);
+#pragma unroll
+            for (int b = 0; b < NBLK; ++b) tma_load_2d(sA + b * A_BLK, &maps.a128, 64 * b, r0, &a_bar);
+            tma_load_2d(sA + NBLK * A_BLK, &maps.a32, 64 * NBLK, r0, &a_bar);
+            for (int it = 0; it < ntile; ++it) {
+                const int s = it % STAGES;
+                if (!mbar_wait(&empty_bar[s], ((it / STAGES) & 1) ^ 1, &abort_s, err)) break;
+                uint8_t *dst = sB + s * B_BYTES;
+                const int y = (t_begin + it) * BN;
+                mbar_expect_tx(&full_bar[s], B_BYTES);
+#pragma unroll
+                for (int b = 0; b < NBLK; ++b) tma_load_2d(dst + b * B_BLK, &maps.b128, 64 * b, y, &full_bar[s]);
+                tma_load_2d(dst + NBLK * B_BLK, &maps.b32, 64 * NBLK, y, &full_bar[s]);
+                issued = it + 1;
+            }
+            // drain: every issued load must land before the CTA may exit
+            mbar_wait(&a_bar, 0, &abort_s, err);
+            for (int it = (issued > STAGES ? issued - STAGES : 0); it < issued; ++it) {
+                const int s = it % STAGES;
+                if (mbar_try_wait(&full_bar[s], (it / STAGES) & 1)) continue;
+                const unsigned long long t0 = gtimer();
+                while (!mbar_try_wait(&full_bar[s], (it / STAGES) & 1) && gtimer() - t0 < kWaitNs) {
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            const uint32_t a_base = smem_u32(sA);
+            const uint32_t b_base0 = smem_u32(sB);
+            bool ok = mbar_wait(&a_bar, 0, &abort_s, err);
+            for (int it = 0; ok && it < ntile; ++it) {
+                const int s = it % STAGES;
+                const int acc = it % NACC;
+                if (!mbar_wait(&tempty_bar[acc], ((it / NACC) & 1) ^ 1, &abort_s, err)) break;
+                if (!mbar_wait(&full_bar[s], (it / STAGES) & 1, &abort_s, err)) break;
+                tc_fence_after();
+                const uint32_t b_base = b_base0 + s * B_BYTES;
+                const uint32_t d_tmem = tmem_base + acc * BN;
+#pragma unroll
+                for (int k = 0; k < KSTEPS; ++k) {
+                    uint64_t ad, bd;
+                    if (k < NBLK * 4) {
+                        const uint32_t off_a = (k >> 2) * A_BLK + (k & 3) * 32;
+                        const uint32_t off_b = (k >> 2) * B_BLK + (k & 3) * 32;
+                        ad = smem_desc(a_base + off_a, 1024, 2);
+                        bd = smem_desc(b_base + off_b, 1024, 2);
+                    } else {
+                        ad = smem_desc(a_base + NBLK * A_BLK, 256, 6);
+                        bd = smem_desc(b_base + NBLK * B_BLK, 256, 6);
+                    }
+                    umma_f16(d_tmem, ad, bd, IDESC, k > 0 ? 1u : 0u);
+                }
+                umma_commit(&empty_bar[s]);      // smem stage free once these MMAs finish
+                umma_commit(&tfull_bar[acc]);    // accumulator ready for the epilogue
+            }
+        }
+    } else {
+        // ------------------------------------------------------ epilogue
+        const int quad = warp & 3;  // TMEM lane quadrant this warp may access
+        const int row = quad * 32 + lane;
+        const int r = r0 + row;
+        const bool live = r < g.R;
+        float zb = 0.0f, rho_lim = 0.5f;
+        if (live) {
+            zb = ri[r].zb;
+            rho_lim = ri[r].rho_lim;
+        }
+        ListState L;
+        list_init(L);
+        for (int it = 0; it < ntile; ++it) {
+            const int acc = it % NACC;
+            // warp-uniform decision: tcgen05.ld below is .sync.aligned
+            if (!__all_sync(0xffffffffu, mbar_wait(&tfull_bar[acc], (it / NACC) & 1, &abort_s, err))) break;
+            tc_fence_after();
+            const int n0 = (t_begin + it) * BN;
+#pragma unroll 1
+            for (int ch = 0; ch < BN / 32; ++ch) {
+                float X[32];
+                tmem_ld32(tmem_base + ((uint32_t)(quad * 32) << 16) + acc * BN + ch * 32, X);
+                const int c0 = n0 + ch * 32;
+                const int nvalid = min(32, g.N - c0);
+                if (dump) {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j)
+                        if (live && j < nvalid) dump[(size_t)r * g.N + c0 + j] = X[j];
+                } else if (live && nvalid > 0) {
+                    float4 dc[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int d = (c0 >> 3) + q;
+                        dc[q] = d < g.D ? __ldg(dconst + d) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    }
+                    epi_chunk32(X, (uint32_t)c0, dc, zb, rho_lim, ec, L, nvalid);
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty_bar[acc]);
+        }
+        if (live && !dump) {
+            ListEntry *dst = lists + ((size_t)r * n_split + split) * kListK;
+#pragma unroll
+            for (int i = 0; i < kListK; ++i) dst[i] = ListEntry{L.key[i], L.idx[i]};
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        __syncwarp();
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS)
+                     : "memory");
+    }
+}
+
+namespace {
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+bool make_map(CUtensorMap *m, const void *base, int rows, int kp, int x_box, int y_box, CUtensorMapSwizzle sw)
+{
+    auto fn = encode_fn();
+    if (!fn) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)kp, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)kp * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)x_box, (cuuint32_t)y_box};
+    const cuuint32_t estr[2] = {1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<void *>(base), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+bool search_tc_supported(const Geometry &g)
+{
+    // one 64-element K block per copy of the pixels: n = 8 (m = 64)
+    return g.m == 64 && g.KP == (g.split_hilo ? 2 : 1) * 64 + 16;
+}
+
+size_t search_tc_smem(const Geometry &g)
+{
+    const int nblk = g.split_hilo ? 2 : 1;
+    return 1024 + (size_t)(nblk * BM * 128 + BM * 32) + (size_t)STAGES * (nblk * BN * 128 + BN * 32);
+}
+
+int search_tc_tile() { return BN; }
+
+int search_tc_rows(int rows) { return (rows + 127) / 128 * 128; }
+
+cudaError_t launch_search_tc(const Geometry &g, const EpiConst &ec, const RangeInfo *ri, const float4 *dconst,
+                             const __half *ra16, const __half *cb16, ListEntry *lists, int n_split, float *dump,
+                             int *err, cudaStream_t st)
+{
+    if (!search_tc_supported(g)) return cudaErrorInvalidValue;
+    TcMaps mp;
+    const int nblk = g.split_hilo ? 2 : 1;
+    // operand buffers hold whole boxes (rows padded with zeros to a multiple of 128)
+    const int rpad = search_tc_rows(g.R), npad = search_tc_rows(g.N);
+    if (!make_map(&mp.a128, ra16, rpad, g.KP, 64, BM, CU_TENSOR_MAP_SWIZZLE_128B) ||
+        !make_map(&mp.a32, ra16, rpad, g.KP, 16, BM, CU_TENSOR_MAP_SWIZZLE_32B) ||
+        !make_map(&mp.b128, cb16, npad, g.KP, 64, BN, CU_TENSOR_MAP_SWIZZLE_128B) ||
+        !make_map(&mp.b32, cb16, npad, g.KP, 16, BN, CU_TENSOR_MAP_SWIZZLE_32B))
+        return cudaErrorInvalidValue;
+    const size_t smem = search_tc_smem(g);
+    dim3 grid((g.R + BM - 1) / BM, n_split);
+    cudaError_t e;
+    if (nblk == 2) {
+        e = cudaFuncSetAttribute(k_search_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_search_tc<2><<<grid, THREADS, smem, st>>>(mp, g, ec, ri, dconst, lists, n_split, dump, err);
+    } else {
+        e = cudaFuncSetAttribute(k_search_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_search_tc<1><<<grid, THREADS, smem, st>>>(mp, g, ec, ri, dconst, lists, n_split, dump, err);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace fic
