@@ -6,6 +6,8 @@
 // final FP64 codes and residuals -> (device -> host maps copy).
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 
 #include "fic_internal.cuh"
@@ -176,14 +178,34 @@ bool is_device_ptr(const void *ptr)
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-#define FIC_CUDA(call)                      \
-    do {                                    \
-        cudaError_t e_ = (call);            \
-        if (e_ != cudaSuccess) {            \
-            cudaGetLastError();             \
-            rc = FIC_ERR_CUDA;              \
-            goto done;                      \
-        }                                   \
+// FIC_DEBUG=1 in the environment: synchronise after every call on the
+// encode/decode paths and report the first failing one on stderr.
+bool debug_mode()
+{
+    static int v = -1;
+    if (v < 0) {
+        const char *e = getenv("FIC_DEBUG");
+        v = (e && e[0] == '1') ? 1 : 0;
+    }
+    return v == 1;
+}
+
+cudaError_t debug_check(cudaError_t e, const char *what, int line, cudaStream_t st)
+{
+    if (e == cudaSuccess && debug_mode()) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess && debug_mode())
+        fprintf(stderr, "libfic: %s failed at fic_api.cu:%d: %s\n", what, line, cudaGetErrorString(e));
+    return e;
+}
+
+#define FIC_CUDA(call)                                              \
+    do {                                                            \
+        cudaError_t e_ = debug_check((call), #call, __LINE__, st);  \
+        if (e_ != cudaSuccess) {                                    \
+            cudaGetLastError();                                     \
+            rc = FIC_ERR_CUDA;                                      \
+            goto done;                                              \
+        }                                                           \
     } while (0)
 
 }  // namespace
@@ -317,14 +339,17 @@ int run_encode(const void *img, int w, int h, int pitch_px, const fic_params *p,
         }
 #undef FIC_MARK
         g_phase.valid = timed;
-        const bool sync = dump || !maps_dev || !img_dev;
+        const bool sync = dump || !maps_dev || !img_dev || debug_mode();
         if (!dump && !maps_dev)
             FIC_CUDA(cudaMemcpyAsync(maps, dmaps, sizeof(fic_map) * g.R, cudaMemcpyDeviceToHost, st));
         if (sync) {
             int herr = 0;
             FIC_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
             FIC_CUDA(cudaStreamSynchronize(st));
-            if (herr) rc = FIC_ERR_TIMEOUT;
+            if (herr) {
+                rc = FIC_ERR_TIMEOUT;
+                if (debug_mode()) fprintf(stderr, "libfic: device error flag %d\n", herr);
+            }
         }
         g_stats[0] = -1;
         g_stats[1] = n_lists;

@@ -175,7 +175,8 @@ struct TcMaps {
 template <int NBLK>
 __global__ void __launch_bounds__(THREADS, 1)
     k_search_tc(const __grid_constant__ TcMaps maps, Geometry g, EpiConst ec, const RangeInfo *ri,
-                const float4 *dconst, ListEntry *lists, int n_split, float *dump, int *err)
+                const float4 *dconst, ListEntry *lists, int n_split, float *dump, int *err,
+                uint32_t smem_bytes, int rpad, int npad)
 {
     constexpr uint32_t A_BLK = BM * 128;                 // bytes of one 64-col block, A
     constexpr uint32_t B_BLK = BN * 128;
@@ -202,6 +203,15 @@ __global__ void __launch_bounds__(THREADS, 1)
     const int ntile = t_end - t_begin;
 
     if (threadIdx.x == 0) {
+        // self-checks: every TMA box and MMA operand must lie inside this CTA's
+        // dynamic shared memory, and every box inside the padded operands
+        const uint32_t used = (uint32_t)(smem - smem_raw) + A_BYTES + STAGES * B_BYTES;
+        int bad = 0;
+        if (used > smem_bytes) bad = 2;
+        if (r0 + BM > rpad || t_end * BN > npad) bad = 3;
+        if (smem_u32(smem) & 1023u) bad = 4;
+        abort_s = bad;
+        if (bad) atomicExch(err, bad);
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&full_bar[s], 1);
             mbar_init(&empty_bar[s], 1);
@@ -211,7 +221,6 @@ __global__ void __launch_bounds__(THREADS, 1)
             mbar_init(&tfull_bar[a], 1);
             mbar_init(&tempty_bar[a], 4);  // one arrival per epilogue warp
         }
-        abort_s = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
@@ -225,8 +234,17 @@ __global__ void __launch_bounds__(THREADS, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem_base = tmem_base_s;
+    // TMEM: lane field 0, columns [base, base + 256) within the 512 of the SM
+    if (threadIdx.x == 0 && ((tmem_base >> 16) != 0 || (tmem_base & 0xFFFFu) + TMEM_COLS > 512)) {
+        abort_s = 5;
+        atomicExch(err, 5);
+    }
+    __syncthreads();
+    const bool run = abort_s == 0;
 
-    if (warp == 0) {
+    if (!run) {
+        // skip all work; fall through to the TMEM release
+    } else if (warp == 0) {
         // ------------------------------------------------------ TMA producer
         if (lane == 0) {
             int issued = 0;
@@ -416,11 +434,13 @@ cudaError_t launch_search_tc(const Geometry &g, const EpiConst &ec, const RangeI
     if (nblk == 2) {
         e = cudaFuncSetAttribute(k_search_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        k_search_tc<2><<<grid, THREADS, smem, st>>>(mp, g, ec, ri, dconst, lists, n_split, dump, err);
+        k_search_tc<2><<<grid, THREADS, smem, st>>>(mp, g, ec, ri, dconst, lists, n_split, dump, err,
+                                                    (uint32_t)smem, rpad, npad);
     } else {
         e = cudaFuncSetAttribute(k_search_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        k_search_tc<1><<<grid, THREADS, smem, st>>>(mp, g, ec, ri, dconst, lists, n_split, dump, err);
+        k_search_tc<1><<<grid, THREADS, smem, st>>>(mp, g, ec, ri, dconst, lists, n_split, dump, err,
+                                                    (uint32_t)smem, rpad, npad);
     }
     return cudaGetLastError();
 }

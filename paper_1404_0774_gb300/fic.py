@@ -67,6 +67,7 @@ def lib():
         L.fic_status_str.restype = ctypes.c_char_p
         L.fic_last_encode_stats.argtypes = [i64p]
         L.fic_last_encode_phase_ms.argtypes = [ctypes.POINTER(ctypes.c_double)]
+        L.fic_cross_terms.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, pp, vp, vp, sz, vp]
         _lib = L
     return _lib
 
@@ -175,6 +176,20 @@ def decode(maps, w: int, h: int, p: fic_params, init: float | None = None, out=N
         ws_ptr, ws_bytes = workspace.data_ptr(), workspace.numel() * workspace.element_size()
     _check(lib().fic_decode(maps_ptr, R, w, h, ctypes.byref(p), ctypes.c_float(init), out_ptr, ws_ptr, ws_bytes,
                             st), "fic_decode")
+    return out
+
+
+def cross_terms(img, p: fic_params, out=None, stream=None):
+    """Raw cross terms Xt[r, c] = (m*X - Sq*Sb)/m of the selected search path
+    (testing aid).  img: torch CUDA tensor; returns a (R, 8D) float32 tensor."""
+    import torch
+
+    h, w = int(img.shape[0]), int(img.shape[1])
+    R, D = counts(w, h, p)
+    if out is None:
+        out = torch.empty((R, 8 * D), dtype=torch.float32, device=img.device)
+    _check(lib().fic_cross_terms(img.data_ptr(), w, h, int(img.stride(0)), ctypes.byref(p), out.data_ptr(), None,
+                                 0, _stream_ptr(stream)), "fic_cross_terms")
     return out
 
 

@@ -23,6 +23,20 @@ def test_exports_every_declared_symbol(fic):
         assert hasattr(lib, name), name
 
 
+def test_binding_declares_argument_types_for_every_entry_point(fic):
+    """ctypes passes undeclared integer arguments as 32-bit ints, which would
+    truncate 64-bit device pointers: every entry point must declare its types."""
+    import re
+
+    lib = fic.lib()
+    hdr = open(fic.os.path.join(fic.os.path.dirname(fic._HERE), "include", "fic.h")).read()
+    for name in fic.header_symbols():
+        decl = re.search(r"^\s*(?:const\s+)?\w+\s*\*?\s*" + name + r"\s*\(([^)]*)\)", hdr, re.M).group(1).strip()
+        n_args = 0 if decl in ("", "void") else decl.count(",") + 1
+        fn = getattr(lib, name)
+        assert fn.argtypes is not None and len(fn.argtypes) == n_args, name
+
+
 def test_counts_and_validation(fic):
     p = fic.params(range_size=8, domain_stride=4, bit_depth=12)
     assert fic.counts(512, 512, p) == (4096, 15625)

@@ -55,15 +55,8 @@ def fic():
 
 
 def gpu_xt(fic, img, p):
-    import ctypes
-
-    h, w = img.shape
-    R, D = fic.counts(w, h, p)
     t = torch.from_numpy(img.astype(np.int16) if img.dtype == np.uint16 else img).cuda()
-    out = torch.zeros((R, 8 * D), dtype=torch.float32, device="cuda")
-    rc = fic.lib().fic_cross_terms(t.data_ptr(), w, h, w, ctypes.byref(p), out.data_ptr(), None, 0,
-                                   torch.cuda.current_stream().cuda_stream)
-    assert rc == 0, rc
+    out = fic.cross_terms(t, p)
     torch.cuda.synchronize()
     return out.cpu().numpy().astype(np.float64)
 
