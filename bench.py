@@ -212,7 +212,7 @@ def main():
     for _ in range(max(3, args.warmup)):
         step()
     torch.cuda.synchronize()
-    launches_per_step = 7
+    launches_per_step = 8  # range prep, domain prep, seed, search, re-score, fallback scan + reduce, output
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     if ws > 1:
@@ -269,6 +269,9 @@ def main():
         e2e_t = float(tt.item())
     e2e_value = ws * args.steps * comps / e2e_t
 
+    mnp = fic.maps_to_numpy(maps)
+    n_fallback = int((mnp["info"] & fic.FIC_MAP_FALLBACK).sum())
+
     # dominant kernel (the search) timed alone: events recorded by the library
     # around each phase on the launching stream, L2 flushed before each step
     pt = fic.params(range_size=RANGE, domain_stride=STRIDE, bit_depth=BITS, search=search,
@@ -304,7 +307,7 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "fp16+fp32" if used == "tc" else "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "search": used, "l2": "flushed (256 MB write) between steps",
-                       "comparisons_per_step": comps},
+                       "comparisons_per_step": comps, "ranges_resolved_by_exact_rescan": n_fallback},
             "e2e": {"value": e2e_value, "unit": "comparisons/s",
                     "h2d_bytes_per_step": N_PIX * N_PIX * 2, "d2h_bytes_per_step": R * 40},
             "gpu_launches": launches_per_step * args.steps, "clocks": clocks, "roofline": roof}

@@ -93,10 +93,25 @@ EpiConst make_epi(const Geometry &g)
     EpiConst ec;
     ec.two_ls = 2.0f * g.Ls;
     ec.ls = (float)g.Ls;
+    ec.inv2ls = (float)(0.5 / g.Ls);
     ec.G = (float)g.G;
     ec.invG = (float)(1.0 / g.G);
     const double pl = (double)g.P / g.Lo;
-    ec.lambda = (float)(2.0 * g.Ls * g.m * pl * pl / (g.G * g.G));
+    const double lambda = 2.0 * g.Ls * g.m * pl * pl / (g.G * g.G);
+    ec.lambda = (float)lambda;
+    ec.delta_o = (float)(g.m * 0.25 * pl * pl);
+    // o code decided next to its rounding boundary: z/G is off by at most
+    // eps (z units) -> the residue w moves by eps and lambda*w^2 by
+    // lambda*(G*eps + eps^2) around |w| = G/2; eps covers the FP32 rounding of
+    // z*invG and of the residue (z spans up to 16*G when reduced mod G, else
+    // 8*Ls*m*P)
+    const double zmax = g.mod_g ? 16.0 * g.G : 8.0 * g.Ls * g.m * g.P;
+    const double eps = zmax * 2.384185791015625e-07 + (g.mod_g ? 0.0 : g.Lo * g.G * 1.2e-7);  // 2^-22
+    ec.beta_o = (float)(2.0 * lambda * (g.G * eps + eps * eps) + 1e-3);
+    ec.sqrtm4 = (float)(0.25 * sqrt((double)g.m));
+    ec.inv4ls = (float)(0.25 / g.Ls);
+    ec.invm = (float)(1.0 / g.m);
+    ec.pmax = (float)g.P - 0.5f;
     return ec;
 }
 
@@ -134,7 +149,7 @@ int lists_per_split(int search) { return search == FIC_SEARCH_SIMT ? search_simt
 
 struct EncLayout {
     size_t img, ri, di, dconst, bblk, qblk, rs32, cb32, ra16, cb16, lists, winner, fb_list, fb_count,
-        qp2max, maps, total;
+        tbest, partial, maps, total;
 };
 
 EncLayout enc_layout(const Geometry &g, int search, int n_lists)
@@ -162,7 +177,8 @@ EncLayout enc_layout(const Geometry &g, int search, int n_lists)
     L.winner = take(sizeof(uint32_t) * g.R);
     L.fb_list = take(sizeof(int) * g.R);
     L.fb_count = take(sizeof(int) * 2);
-    L.qp2max = take(sizeof(float) * 2);
+    L.tbest = take(sizeof(int) * g.R);
+    L.partial = take(fallback_partial_bytes(g));
     L.maps = take(sizeof(fic_map) * g.R);
     L.total = o;
     return L;
@@ -305,7 +321,8 @@ int run_encode(const void *img, int w, int h, int pitch_px, const fic_params *p,
         int *fb_list = reinterpret_cast<int *>(ws + L.fb_list);
         int *fb_count = reinterpret_cast<int *>(ws + L.fb_count);
         int *err = fb_count + 1;
-        float *qp2max = reinterpret_cast<float *>(ws + L.qp2max);
+        int *tbest = reinterpret_cast<int *>(ws + L.tbest);
+        void *partial = ws + L.partial;
         fic_map *dmaps = maps_dev ? maps : reinterpret_cast<fic_map *>(ws + L.maps);
         const EpiConst ec = make_epi(g);
         const bool timed = !dump && (p->flags & FIC_FLAG_PHASE_TIMING) && g_phase.ensure();
@@ -320,19 +337,18 @@ int run_encode(const void *img, int w, int h, int pitch_px, const fic_params *p,
             FIC_CUDA(cudaMemsetAsync(ws + L.cb16 + row * g.N, 0, row * (search_tc_rows(g.N) - g.N), st));
         }
         FIC_MARK(0);
-        FIC_CUDA(launch_prep(gd, dimg, ri, di, dconst, bblk, qblk, rs32, cb32, ra16, cb16, st));
-        FIC_CUDA(launch_qp2max(gd, di, qp2max, st));
+        FIC_CUDA(launch_prep(gd, dimg, ec, ri, di, dconst, bblk, qblk, rs32, cb32, ra16, cb16, tbest, st));
+        if (!dump) FIC_CUDA(launch_seed(gd, ec, ri, di, dconst, bblk, qblk, tbest, st));
         FIC_MARK(1);
         if (search == FIC_SEARCH_TC)
-            FIC_CUDA(launch_search_tc(gd, ec, ri, dconst, ra16, cb16, lists, n_split, dump, err, st));
+            FIC_CUDA(launch_search_tc(gd, ec, ri, dconst, ra16, cb16, lists, n_split, tbest, dump, err, st));
         else
-            FIC_CUDA(launch_search_simt(gd, ec, ri, di, dconst, rs32, cb32, lists, n_split, dump, st));
+            FIC_CUDA(launch_search_simt(gd, ec, ri, di, dconst, rs32, cb32, lists, n_split, tbest, dump, st));
         FIC_MARK(2);
         if (!dump) {
-            FIC_CUDA(launch_rescore(gd, ec, ri, di, bblk, qblk, lists, n_lists, qp2max, winner, fb_list,
-                                    fb_count, st));
+            FIC_CUDA(launch_rescore(gd, ec, ri, di, bblk, qblk, lists, n_lists, winner, fb_list, fb_count, st));
             FIC_MARK(3);
-            FIC_CUDA(launch_fallback(gd, ri, di, bblk, qblk, fb_list, fb_count, winner, st));
+            FIC_CUDA(launch_fallback(gd, ri, di, bblk, qblk, fb_list, fb_count, partial, winner, st));
             FIC_MARK(4);
             FIC_CUDA(launch_finalize(gd, ri, di, bblk, qblk, winner, err, dmaps, st));
             FIC_MARK(5);

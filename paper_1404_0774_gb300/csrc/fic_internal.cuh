@@ -56,6 +56,10 @@ struct RangeInfo {
     float zb;           // 4*Ls*Sb (reduced mod G when mod_g)
     float bp2;          // sum (b - c_r)^2
     float rho_lim;      // |rho| above this: the s code may differ from FP64's
+    float beta_a;       // key rounding allowance (see beta_key)
+    float beta_q;       // cross-term accumulation allowance factor (0: exact)
+    int shadow;         // constant block: every candidate has s = 0 and one residual
+    int pad;
 };
 
 struct DomainInfo {
@@ -69,11 +73,24 @@ struct DomainInfo {
 //   x: alpha = 2*m/den (0 for a flat domain) so that Ls*clamp(s) = 2*Ls*sat(Xt*alpha+1/2) - Ls
 //   y: sqz   = Sq (reduced mod G when mod_g)
 //   z: kappa = den/(8*m*Ls)
-//   w: g     = sqrt(m/den) (0 for a flat domain): |Xt|*g = sqrt(explained variance)
+//   w: Sq as float (exact)
 struct EpiConst {
-    float two_ls, ls;
+    float two_ls, ls, inv2ls;
     float G, invG;
     float lambda;
+    float delta_o;      // m*(P/(2*Lo))^2: largest offset-rounding term of the residual
+    float beta_o;       // key error from an o code decided next to its rounding boundary
+    float sqrtm4;       // sqrt(m)/4
+    float inv4ls, invm, pmax;  // 1/(4*Ls), 1/m, P (offset clamp detection)
+};
+
+// Per-thread constants of the range the thread screens.
+struct RangeEpi {
+    float zb, rho_lim;
+    float sbbc, sqrt_sbbc;
+    float bA, bQ;       // error allowance terms, see beta_key
+    float Sb;           // sum b (exact as float)
+    int shadow;
 };
 
 struct ListEntry {
@@ -86,7 +103,30 @@ struct ListState {
     float key[kListK];
     uint32_t idx[kListK];
     int has_zero;       // an s-code-0 candidate is (or was) in the list
+    float T;            // best clean key seen for this range (own or shared)
+    float tw;           // T + 3*beta(T): larger keys cannot reach the winner
+    float Tpub;         // value last published to (or read from) the shared per-range best
 };
+
+__device__ __forceinline__ int f2ord(float f)
+{
+    const int i = __float_as_int(f);
+    return i >= 0 ? i : i ^ 0x7fffffff;
+}
+
+__device__ __forceinline__ float ord2f(int o) { return __int_as_float(o >= 0 ? o : o ^ 0x7fffffff); }
+
+// Allowance (key units, key = 2*Ls*(R - Sbb_c)) for |key - exact| of any
+// candidate whose residual is within reach of key T:
+//   FP32 rounding of the key terms, the cross-term accumulation error (zero
+//   unless centred products can exceed 2^23, see bQ), and the o-code decision
+//   next to its rounding boundary.
+__device__ __forceinline__ float beta_key(const RangeEpi &re, float T, const EpiConst &ec)
+{
+    const float ET = fmaxf(0.0f, fmaf(T, ec.inv2ls, re.sbbc));
+    return re.bA + ec.beta_o + 3.814697265625e-6f * (fabsf(T) + 2.0f * ec.two_ls * ET) +
+           re.bQ * (re.sqrt_sbbc + sqrtf(ET + ec.delta_o) + ec.sqrtm4);
+}
 
 __device__ __forceinline__ void list_init(ListState &L)
 {
@@ -96,6 +136,18 @@ __device__ __forceinline__ void list_init(ListState &L)
         L.idx[i] = 0xffffffffu;
     }
     L.has_zero = 0;
+    L.T = __int_as_float(0x7f800000);
+    L.tw = __int_as_float(0x7f800000);
+    L.Tpub = __int_as_float(0x7f800000);
+}
+
+// Adopt a better shared best key.
+__device__ __forceinline__ void list_adopt(ListState &L, float T, const RangeEpi &re, const EpiConst &ec)
+{
+    if (T < L.T) {
+        L.T = T;
+        L.tw = T + 3.0f * beta_key(re, T, ec);
+    }
 }
 
 // Sorted insertion; equal keys keep the earlier (lower-index) entry first.
@@ -139,64 +191,69 @@ __device__ __forceinline__ float epi_key(float X, float c, float zb, float4 dc, 
     return fmaf(__fmul_rn(wv, ec.lambda), wv, cy);
 }
 
-// Process 32 consecutive candidates idx0..idx0+31 (4 domains x 8 symmetries)
-// of one range.  X[] holds Xt per candidate and is overwritten by the keys.
-// Only the first `nvalid` candidates are real (a ragged tail of the
-// candidate dimension); the rest get an infinite key.
-__device__ __forceinline__ void epi_chunk32(float (&X)[32], uint32_t idx0, const float4 (&dc)[4],
-                                            float zb, float rho_lim, const EpiConst &ec,
-                                            ListState &L, int nvalid = 32)
+// Main pass over 32 consecutive candidates (4 domains x 8 symmetries):
+// X[] (cross terms) is overwritten by the keys.  Branch-free.  Returns whether
+// this thread needs the rare pass: a key below `thr`, or a code decided next
+// to its rounding boundary.  Lanes beyond the ragged end carry X = NaN (their
+// keys are NaN and compare false everywhere).
+// zpen: added to the key of s-code-0 candidates (their residual is one value
+// per range; once the list holds one, the others need never be looked at).
+__device__ __forceinline__ bool epi_keys32(float (&X)[32], const float4 (&dc)[4], float zb, float rho_lim,
+                                           const EpiConst &ec, float thr, float zpen)
 {
     float kmin = __int_as_float(0x7f800000);
     float rmax = 0.0f;
-    float xs[32];
 #pragma unroll
     for (int j = 0; j < 32; ++j) {
         const float4 c4 = dc[j >> 3];
         float rho;
         const float c = epi_code(X[j], c4.x, ec, rho);
-        xs[j] = X[j];
-        float k = epi_key(X[j], c, zb, c4, ec);
-        if (j >= nvalid) {
-            k = __int_as_float(0x7f800000);
-            rho = 0.0f;
-        }
-        rmax = fmaxf(rmax, fabsf(rho));
+        const float zero = __saturatef(fmaf(c, -c, 1.0f));  // 1 for c = 0, else 0 (c is an integer)
+        const float k = fmaf(zero, zpen, epi_key(X[j], c, zb, c4, ec));
         X[j] = k;
         kmin = fminf(kmin, k);
+        rmax = fmaxf(rmax, fabsf(rho));
     }
-    if (rmax > rho_lim) {
-        // near a rounding boundary of s: the code FP64 picks may be the other
-        // neighbour, so rank by the smaller of the two keys
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-            const float4 c4 = dc[j >> 3];
-            float rho;
-            const float c = epi_code(xs[j], c4.x, ec, rho);
-            if (j < nvalid && fabsf(rho) > rho_lim) {
-                float c2 = c + (rho > 0.0f ? 1.0f : -1.0f);
-                c2 = fminf(fmaxf(c2, -ec.ls), ec.ls);
-                const float k2 = epi_key(xs[j], c2, zb, c4, ec);
-                X[j] = fminf(X[j], k2);
-                kmin = fminf(kmin, X[j]);
-            }
+    return kmin < thr || rmax > rho_lim;
+}
+
+__device__ __forceinline__ float4 pick4(const float4 (&dc)[4], int q)
+{
+    return q == 0 ? dc[0] : (q == 1 ? dc[1] : (q == 2 ? dc[2] : dc[3]));
+}
+
+// Rare pass for one thread: keys and cross terms staged in shared memory at
+// krow[j*stride], xrow[j*xstride].  Handles codes next to a rounding boundary
+// (the key becomes the smaller of the two neighbouring codes' keys: a lower
+// bound of the residual FP64 decides) and list insertion with s-code-0
+// de-duplication (all such candidates of a range have one residual).
+static __device__ __noinline__ void epi_rare(const float *krow, int stride, const float *xrow, int xstride,
+                                      uint32_t idx0, const float4 (&dc)[4], const RangeEpi &re,
+                                      const EpiConst &ec, ListState &L, int nvalid)
+{
+#pragma unroll 1
+    for (int j = 0; j < nvalid; ++j) {
+        float k = krow[j * stride];
+        const float x = xrow[j * xstride];
+        const float4 c4 = pick4(dc, j >> 3);
+        float rho;
+        const float c = epi_code(x, c4.x, ec, rho);
+        const bool near = fabsf(rho) > re.rho_lim;
+        if (near) {
+            const float c2 = fminf(fmaxf(c + (rho > 0.0f ? 1.0f : -1.0f), -ec.ls), ec.ls);
+            k = fminf(k, epi_key(x, c2, re.zb, c4, ec));
         }
-    }
-    if (kmin < L.key[kListK - 1]) {
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-            float kj = X[j];
-            if (kj < L.key[kListK - 1]) {
-                float rho;
-                const float c = epi_code(xs[j], dc[j >> 3].x, ec, rho);
-                if (c == 0.0f && fabsf(rho) <= rho_lim) {
-                    // every s-code-0 candidate of a range has the same residual
-                    // (Sbb_c plus the offset term): keep only the first
-                    if (L.has_zero) continue;
-                    L.has_zero = 1;
-                }
-                list_insert(L, kj, idx0 + j);
-            }
+        if (!(k < fminf(L.key[kListK - 1], L.tw))) continue;
+        if (c == 0.0f && !near) {
+            if (L.has_zero) continue;
+            L.has_zero = 1;  // later s-code-0 keys carry the penalty in the main pass
+        }
+        list_insert(L, k, idx0 + j);
+        if (k < L.T && !near) {
+            // a clean key (code not near a boundary, offset not clamped) is an
+            // upper bound of the residual up to beta: it may tighten the window
+            const float ostar = (re.Sb - c * c4.w * ec.inv4ls) * ec.invm;
+            if (ostar < ec.pmax) list_adopt(L, k, re, ec);
         }
     }
 }
@@ -223,34 +280,53 @@ __device__ __forceinline__ int load_px(const void *img, int B, size_t off)
 
 // ---------------------------------------------------------------- launches
 // (host-side wrappers, each returns cudaError_t of the launch)
-cudaError_t launch_prep(const Geometry &g, const void *img, RangeInfo *ri, DomainInfo *di,
-                        float4 *dconst, uint16_t *bblk, uint16_t *qblk, float *rs32, float *cb32,
-                        __half *ra16, __half *cb16, cudaStream_t st);
 cudaError_t launch_search_simt(const Geometry &g, const EpiConst &ec, const RangeInfo *ri,
                                const DomainInfo *di, const float4 *dconst, const float *rs32,
-                               const float *cb32, ListEntry *lists, int n_split, float *dump,
+                               const float *cb32, ListEntry *lists, int n_split, int *tbest, float *dump,
                                cudaStream_t st);
 bool search_tc_supported(const Geometry &g);
 size_t search_tc_smem(const Geometry &g);
 int search_tc_tile();
 int search_tc_rows(int rows);  // operand rows allocated (multiple of the TMA box)
 cudaError_t launch_search_tc(const Geometry &g, const EpiConst &ec, const RangeInfo *ri, const float4 *dconst,
-                             const __half *ra16, const __half *cb16, ListEntry *lists, int n_split, float *dump,
-                             int *err, cudaStream_t st);
+                             const __half *ra16, const __half *cb16, ListEntry *lists, int n_split, int *tbest,
+                             float *dump, int *err, cudaStream_t st);
 int search_simt_lists_per_split();
 cudaError_t launch_rescore(const Geometry &g, const EpiConst &ec, const RangeInfo *ri,
                            const DomainInfo *di, const uint16_t *bblk, const uint16_t *qblk,
-                           const ListEntry *lists, int n_lists, const float *qp2max, uint32_t *winner,
-                           int *fb_list, int *fb_count, cudaStream_t st);
+                           const ListEntry *lists, int n_lists, uint32_t *winner, int *fb_list,
+                           int *fb_count, cudaStream_t st);
+size_t fallback_partial_bytes(const Geometry &g);
 cudaError_t launch_fallback(const Geometry &g, const RangeInfo *ri, const DomainInfo *di,
                             const uint16_t *bblk, const uint16_t *qblk, const int *fb_list,
-                            const int *fb_count, uint32_t *winner, cudaStream_t st);
+                            const int *fb_count, void *partial, uint32_t *winner, cudaStream_t st);
 cudaError_t launch_finalize(const Geometry &g, const RangeInfo *ri, const DomainInfo *di,
                             const uint16_t *bblk, const uint16_t *qblk, const uint32_t *winner,
                             const int *err, fic_map *maps, cudaStream_t st);
 size_t decode_workspace_bytes(const Geometry &g);
 cudaError_t launch_decode(const Geometry &g, const fic_map *maps, float init, int iters, void *ws,
                           float *out, cudaStream_t st);
-cudaError_t launch_qp2max(const Geometry &g, const DomainInfo *di, float *qp2max, cudaStream_t st);
+// Per-thread epilogue constants of range r.
+__device__ __forceinline__ RangeEpi range_epi(const RangeInfo &ri, const EpiConst &ec)
+{
+    RangeEpi re;
+    re.zb = ri.zb;
+    re.rho_lim = ri.rho_lim;
+    re.sbbc = ri.sbbc;
+    re.sqrt_sbbc = sqrtf(fmaxf(ri.sbbc, 0.0f));
+    re.bA = ri.beta_a;
+    re.bQ = ri.beta_q;
+    re.Sb = (float)ri.Sb;
+    re.shadow = ri.shadow;
+    return re;
+}
+cudaError_t launch_prep(const Geometry &g, const void *img, const EpiConst &ec, RangeInfo *ri, DomainInfo *di,
+                        float4 *dconst, uint16_t *bblk, uint16_t *qblk, float *rs32, float *cb32,
+                        __half *ra16, __half *cb16, int *tbest, cudaStream_t st);
+cudaError_t launch_seed(const Geometry &g, const EpiConst &ec, const RangeInfo *ri, const DomainInfo *di,
+                        const float4 *dconst, const uint16_t *bblk, const uint16_t *qblk, int *tbest,
+                        cudaStream_t st);
+// Key-space value that excludes s-code-0 candidates once a list holds one.
+constexpr float kZeroPenalty = 1e30f;
 
 }  // namespace fic

@@ -11,8 +11,8 @@
 namespace fic {
 
 // One thread per range: statistics, centre, operand rows.
-__global__ void k_range_prep(Geometry g, const void *img, RangeInfo *ri, uint16_t *bblk,
-                             float *rs32, __half *ra16)
+__global__ void k_range_prep(Geometry g, EpiConst ec, const void *img, RangeInfo *ri, uint16_t *bblk,
+                             float *rs32, __half *ra16, int *tbest)
 {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= g.R) return;
@@ -66,6 +66,24 @@ __global__ void k_range_prep(Geometry g, const void *img, RangeInfo *ri, uint16_
     // accumulation error of high-variance pairs (grows with sum (b-c_r)^2)
     const double eta = 1e-5 + 12.0 * g.Ls * 64.0 * bp2 * 3.552713678800501e-15;  // 2^-48
     info.rho_lim = (float)(0.5 - fmin(eta, 0.25));
+    // Screening allowance.  A candidate within reach of the winner has
+    // |c| * sqrt(sum (q-q_mean)^2) <= 4*Ls*(sqrt(Sbb_c) + sqrt(R)), R <= Eb; its
+    // centred products (hi/lo split included) then sum to at most S.  Below
+    // 2^23 every FP32 partial sum of integers is exact and the cross term
+    // carries no error; otherwise allow 2^-15 relative.
+    const double sbbc = fmax((double)info.sbbc, 0.0);
+    const double Eb = 4.0 * (sbbc + ec.delta_o);
+    const double sb = sqrt(bp2);
+    const double S = (4.0 * g.Ls * (sqrt(sbbc) + sqrt(Eb)) + sqrt((double)g.m)) * sb +
+                     (g.split_hilo ? 128.0 * sqrt((double)g.m) * sb : 0.0);
+    const bool exact = S < 8388608.0;
+    const double gam = 3.0517578125e-05;  // 2^-15
+    info.beta_q = exact ? 0.0f : (float)(4.0 * g.Ls * gam * sb);
+    info.beta_a = (float)(3.814697265625e-06 * 2.0 * g.Ls * (sbbc + ec.delta_o) + 1e-3 +
+                          (exact ? 0.0 : gam * g.Ls * 128.0 * sqrt((double)g.m) * sb));
+    info.shadow = bmin == bmax ? 1 : 0;
+    info.pad = 0;
+    tbest[r] = 0x7f800000;  // +inf in the ordered-integer encoding of floats
     ri[r] = info;
 }
 
@@ -124,7 +142,7 @@ __global__ void k_domain_prep(Geometry g, const void *img, DomainInfo *di, float
         c4.x = den > 0 ? (float)(2.0 * m / (double)den) : 0.0f;
         c4.y = (float)(g.mod_g ? fmod((double)Sq, g.G) : (double)Sq);
         c4.z = (float)((double)den / (8.0 * m * g.Ls));
-        c4.w = den > 0 ? (float)sqrt((double)m / (double)den) : 0.0f;
+        c4.w = (float)Sq;
         dconst[d] = c4;
     }
     __syncthreads();
@@ -171,31 +189,66 @@ __global__ void k_domain_prep(Geometry g, const void *img, DomainInfo *di, float
     }
 }
 
-cudaError_t launch_prep(const Geometry &g, const void *img, RangeInfo *ri, DomainInfo *di,
+cudaError_t launch_prep(const Geometry &g, const void *img, const EpiConst &ec, RangeInfo *ri, DomainInfo *di,
                         float4 *dconst, uint16_t *bblk, uint16_t *qblk, float *rs32, float *cb32,
-                        __half *ra16, __half *cb16, cudaStream_t st)
+                        __half *ra16, __half *cb16, int *tbest, cudaStream_t st)
 {
-    k_range_prep<<<(g.R + 127) / 128, 128, 0, st>>>(g, img, ri, bblk, rs32, ra16);
+    k_range_prep<<<(g.R + 127) / 128, 128, 0, st>>>(g, ec, img, ri, bblk, rs32, ra16, tbest);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_domain_prep<<<g.D, g.m < 32 ? 32 : g.m, 0, st>>>(g, img, di, dconst, qblk, cb32, cb16);
     return cudaGetLastError();
 }
 
-__global__ void k_qp2max(int D, const DomainInfo *di, float *out)
+// Seed of the per-range best key: before the search, every range scores 256
+// candidates -- the 8 symmetries of the 5 x 5 domains around it and of 7
+// domains spread over the image -- from their exact cross terms, with the
+// same code decision and key as the search epilogue.  Only clean keys (code
+// not next to a rounding boundary, offset not clamped) are published: each is
+// within the screening allowance of a real candidate's residual, which is all
+// the search's insertion window needs.
+__global__ void k_seed(Geometry g, EpiConst ec, const RangeInfo *ri, const DomainInfo *di, const float4 *dconst,
+                       const uint16_t *bblk, const uint16_t *qblk, int *tbest)
 {
-    float v = 0.0f;
-    for (int d = blockIdx.x * blockDim.x + threadIdx.x; d < D; d += gridDim.x * blockDim.x)
-        v = fmaxf(v, di[d].qp2);
-    for (int off = 16; off > 0; off >>= 1) v = fmaxf(v, __shfl_down_sync(0xffffffffu, v, off));
-    if ((threadIdx.x & 31) == 0) atomicMax((int *)out, __float_as_int(v));  // v >= 0
+    const int r = blockIdx.x;
+    const int s = threadIdx.x;  // 256 seed slots
+    const RangeInfo rin = ri[r];
+    if (rin.shadow) return;
+    const int slot_d = s >> 3, k = s & 7;
+    int d;
+    if (slot_d < 25) {
+        const int ry = (r / g.nx) * g.n, rx = (r % g.nx) * g.n;
+        const int v0 = min(max((ry - g.n / 2) / g.t, 0), g.V - 1);
+        const int u0 = min(max((rx - g.n / 2) / g.t, 0), g.U - 1);
+        const int v = min(max(v0 + slot_d / 5 - 2, 0), g.V - 1);
+        const int u = min(max(u0 + slot_d % 5 - 2, 0), g.U - 1);
+        d = v * g.U + u;
+    } else {
+        d = (int)(((long long)r * 2654435761LL + (long long)(slot_d - 25) * 40503LL) % g.D);
+    }
+    long long X = 0;
+    for (int i = 0; i < g.m; ++i) {
+        int sy, sx;
+        sym_src(k, g.n, i / g.n, i % g.n, sy, sx);
+        X += (long long)qblk[(size_t)d * g.m + sy * g.n + sx] * bblk[(size_t)r * g.m + i];
+    }
+    const DomainInfo dd = di[d];
+    const float Xt = (float)((double)((long long)g.m * X - dd.Sq * rin.Sb) / g.m);
+    const float4 c4 = dconst[d];
+    const RangeEpi re = range_epi(rin, ec);
+    float rho;
+    const float c = epi_code(Xt, c4.x, ec, rho);
+    if (fabsf(rho) > re.rho_lim) return;
+    const float ostar = (re.Sb - c * c4.w * ec.inv4ls) * ec.invm;
+    if (!(ostar < ec.pmax)) return;
+    atomicMin(tbest + r, f2ord(epi_key(Xt, c, re.zb, c4, ec)));
 }
 
-cudaError_t launch_qp2max(const Geometry &g, const DomainInfo *di, float *qp2max, cudaStream_t st)
+cudaError_t launch_seed(const Geometry &g, const EpiConst &ec, const RangeInfo *ri, const DomainInfo *di,
+                        const float4 *dconst, const uint16_t *bblk, const uint16_t *qblk, int *tbest,
+                        cudaStream_t st)
 {
-    cudaError_t e = cudaMemsetAsync(qp2max, 0, sizeof(float), st);
-    if (e != cudaSuccess) return e;
-    k_qp2max<<<64, 256, 0, st>>>(g.D, di, qp2max);
+    k_seed<<<g.R, 256, 0, st>>>(g, ec, ri, di, dconst, bblk, qblk, tbest);
     return cudaGetLastError();
 }
 

@@ -16,6 +16,8 @@
 // candidate outside the lists can beat or tie the winner; otherwise it goes
 // to the exact fallback, which scans all of its candidates with exact
 // integer decisions.
+#include <algorithm>
+
 #include "fic_internal.cuh"
 
 namespace fic {
@@ -138,14 +140,19 @@ __device__ unsigned __int128 exact_candidate(const Geometry &g, Stats st, const 
 //     lists can beat or tie it.
 __global__ void k_rescore(Geometry g, EpiConst ec, const RangeInfo *ri, const DomainInfo *di,
                           const uint16_t *bblk, const uint16_t *qblk, const ListEntry *lists,
-                          int n_lists, const float *qp2max, uint32_t *winner, int *fb_list,
-                          int *fb_count)
+                          int n_lists, uint32_t *winner, int *fb_list, int *fb_count)
 {
     const int warps = blockDim.x >> 5;
     const int r = blockIdx.x * warps + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (r >= g.R) return;  // warp-uniform
     const RangeInfo rin = ri[r];
+    if (rin.shadow) {
+        // constant range: num = 0 for every candidate, so s = 0, one offset and
+        // one residual for all; the first candidate wins (Algorithm 2)
+        if (lane == 0) winner[r] = 0;
+        return;
+    }
     int b[kMaxM / 32];
 #pragma unroll
     for (int j = 0; j < kMaxM / 32; ++j) {
@@ -189,10 +196,11 @@ __global__ void k_rescore(Geometry g, EpiConst ec, const RangeInfo *ri, const Do
         const long long X = warp_cross(g, qblk, ib, b);
         U = u128_to_double(exact_candidate(g, st, di, ib, X)) * invD2;  // same on every lane
     }
-    // screening error allowance, converted to residual units
-    const float delta_o = (float)g.m * 0.25f * ((float)g.P / g.Lo) * ((float)g.P / g.Lo);
-    const float beta_k = (ec.two_ls * (rin.sbbc + delta_o) + fabsf(kb)) * (1.0f / 65536.0f) +
-                         ec.ls * (1.0f / 262144.0f) * sqrtf(*qp2max * rin.bp2) + 2.0f * ec.lambda * ec.G + 1e-3f;
+    // screening error allowance (the epilogue's), converted to residual units;
+    // evaluated at the largest key that can still matter
+    const RangeEpi re = range_epi(rin, ec);
+    const float kreach = (float)((U - (double)rin.sbbc) * 2.0 * g.Ls);
+    const float beta_k = fmaxf(beta_key(re, kb, ec), beta_key(re, fmaxf(kb, kreach), ec));
     const double betaE = (double)beta_k * inv2ls;
     const double sbbc = (double)rin.sbbc;
 
@@ -223,9 +231,12 @@ __global__ void k_rescore(Geometry g, EpiConst ec, const RangeInfo *ri, const Do
     const double Estar = u128_to_double(best_e) * invD2;
     bool cert = true;
     for (int l = lane; l < n_lists; l += 32) {
+        // a full list's unlisted candidates have residual >= its last key less
+        // the allowance at that key; that bound must clear the winner strictly
         const ListEntry last = L[l * kListK + kListK - 1];
-        if (last.idx != 0xffffffffu && !(sbbc + (double)last.key * inv2ls - betaE > Estar * (1.0 + 1e-12) + 1e-12))
-            cert = false;
+        if (last.idx == 0xffffffffu) continue;
+        const double bl = (double)beta_key(re, last.key, ec) * inv2ls;
+        if (!(sbbc + (double)last.key * inv2ls - bl > Estar * (1.0 + 1e-12) + 1e-12)) cert = false;
     }
     cert = __all_sync(0xffffffffu, cert);
     if (lane == 0) {
@@ -234,29 +245,60 @@ __global__ void k_rescore(Geometry g, EpiConst ec, const RangeInfo *ri, const Do
     }
 }
 
-// Exact code decisions in integer arithmetic (round half away from zero of
-// the exact rational values), used by the fallback scan.
-__device__ __forceinline__ int round_div_away(long long num, long long den)  // den > 0
+// round half away from zero of num/den (den > 0), exactly: an FP32 estimate
+// corrected with exact integer comparisons.
+__device__ __forceinline__ long long round_div_away(long long num, long long den)
 {
     const long long a = num < 0 ? -num : num;
-    long long q = (long long)((double)a / (double)den + 0.5);
-    // correct the estimate: want q = floor((2a + den) / (2 den))
+    long long q = (long long)(__fdividef((float)a, (float)den) + 0.5f);
+    // want q = floor((2a + den) / (2 den))
     while (q > 0 && 2 * a + den < 2 * den * q) --q;
     while (2 * a + den >= 2 * den * (q + 1)) ++q;
-    return (int)(num < 0 ? -q : q);
+    return num < 0 ? -q : q;
 }
 
-// One CTA per range that failed certification: exhaustive exact scan.
+// Exact residual (times D^2) of candidate idx for range statistics st, with
+// the s and o codes decided exactly from the rational least-squares values.
+__device__ unsigned __int128 exact_rational(const Geometry &g, Stats st, const DomainInfo &dd, long long X)
+{
+    st.Sq = dd.Sq;
+    st.Sqq = dd.Sqq;
+    st.X = X;
+    const long long den = (long long)g.m * dd.Sqq - dd.Sq * dd.Sq;
+    const long long num = (long long)g.m * X - dd.Sq * st.Sb;
+    int c = 0;
+    if (den != 0) {
+        const long long v = 4LL * num;  // s = v / den
+        if (v >= den) c = g.Ls;
+        else if (-v >= den) c = -g.Ls;
+        else c = (int)round_div_away((long long)g.Ls * v, den);
+    }
+    const long long Q = 4LL * g.Ls * g.m * g.P;  // o * Lo / P = z * Lo / Q
+    const long long z = 4LL * g.Ls * st.Sb - (long long)c * dd.Sq;
+    int e = (int)round_div_away(z * g.Lo, Q);
+    if (e > g.Lo) e = g.Lo;  // o is never below -P; clamp above only
+    return (unsigned __int128)exact_err(g, st, c, e);
+}
+
+struct Partial {
+    unsigned long long lo, hi;
+    uint32_t idx, pad;
+};
+
+// Exhaustive exact scan of the ranges that failed certification.  Each range
+// is split over gridDim.x CTAs (blockIdx.x = candidate chunk); each CTA writes
+// its best (residual, index) to part[slot][chunk].
 __global__ void __launch_bounds__(256) k_fallback(Geometry g, const RangeInfo *ri, const DomainInfo *di,
                                                   const uint16_t *bblk, const uint16_t *qblk,
-                                                  const int *fb_list, const int *fb_count,
-                                                  uint32_t *winner)
+                                                  const int *fb_list, const int *fb_count, Partial *part)
 {
     __shared__ int b_s[kMaxM];
-    __shared__ unsigned long long e_s[2][8];
-    __shared__ uint32_t i_s[8];
+    __shared__ Partial w_s[8];
     const int count = *fb_count;
-    for (int slot = blockIdx.x; slot < count; slot += gridDim.x) {
+    const int nch = gridDim.x;
+    const int lo = (int)((long long)g.N * blockIdx.x / nch);
+    const int hi = (int)((long long)g.N * (blockIdx.x + 1) / nch);
+    for (int slot = blockIdx.y; slot < count; slot += gridDim.y) {
         const int r = fb_list[slot];
         __syncthreads();
         for (int i = threadIdx.x; i < g.m; i += blockDim.x) b_s[i] = bblk[(size_t)r * g.m + i];
@@ -267,33 +309,15 @@ __global__ void __launch_bounds__(256) k_fallback(Geometry g, const RangeInfo *r
         st.Sbb = rin.Sbb;
         unsigned __int128 best_e = ~(unsigned __int128)0;
         uint32_t best_i = 0xffffffffu;
-        const long long Q = 4LL * g.Ls * g.m * g.P;  // o grid: e = round(z*Lo/Q)
-        for (int idx = threadIdx.x; idx < g.N; idx += blockDim.x) {
+        for (int idx = lo + threadIdx.x; idx < hi; idx += blockDim.x) {
             const int d = idx >> 3, k = idx & 7;
-            long long X = 0;
+            unsigned long long X = 0;
             for (int i = 0; i < g.m; ++i) {
                 int sy, sx;
                 sym_src(k, g.n, i / g.n, i % g.n, sy, sx);
-                X += (long long)qblk[(size_t)d * g.m + sy * g.n + sx] * b_s[i];
+                X += (unsigned long long)((unsigned)qblk[(size_t)d * g.m + sy * g.n + sx] * (unsigned)b_s[i]);
             }
-            const DomainInfo dd = di[d];
-            st.Sq = dd.Sq;
-            st.Sqq = dd.Sqq;
-            st.X = X;
-            const long long den = (long long)g.m * dd.Sqq - dd.Sq * dd.Sq;
-            const long long num = (long long)g.m * X - dd.Sq * rin.Sb;
-            int c = 0;
-            if (den != 0) {
-                // c = round(Ls * clamp(4 num / den, -1, 1))
-                const long long v = 4LL * num;
-                if (v >= den) c = g.Ls;
-                else if (-v >= den) c = -g.Ls;
-                else c = round_div_away((long long)g.Ls * v, den);
-            }
-            const long long z = 4LL * g.Ls * rin.Sb - (long long)c * dd.Sq;
-            int e = round_div_away(z * g.Lo, Q);
-            if (e > g.Lo) e = g.Lo;  // o is never below -P, clamp above only
-            const unsigned __int128 er = (unsigned __int128)exact_err(g, st, c, e);
+            const unsigned __int128 er = exact_rational(g, st, di[d], (long long)X);
             if (better(er, (uint32_t)idx, best_e, best_i)) {
                 best_e = er;
                 best_i = (uint32_t)idx;
@@ -301,24 +325,33 @@ __global__ void __launch_bounds__(256) k_fallback(Geometry g, const RangeInfo *r
         }
         warp_argmin(best_e, best_i);
         const int w = threadIdx.x >> 5;
-        if ((threadIdx.x & 31) == 0) {
-            e_s[0][w] = (unsigned long long)best_e;
-            e_s[1][w] = (unsigned long long)(best_e >> 64);
-            i_s[w] = best_i;
-        }
+        if ((threadIdx.x & 31) == 0) w_s[w] = Partial{(unsigned long long)best_e, (unsigned long long)(best_e >> 64), best_i, 0};
         __syncthreads();
         if (threadIdx.x == 0) {
-            unsigned __int128 be = ((unsigned __int128)e_s[1][0] << 64) | e_s[0][0];
-            uint32_t bi = i_s[0];
+            Partial b = w_s[0];
             for (int j = 1; j < (int)(blockDim.x >> 5); ++j) {
-                const unsigned __int128 ej = ((unsigned __int128)e_s[1][j] << 64) | e_s[0][j];
-                if (better(ej, i_s[j], be, bi)) {
-                    be = ej;
-                    bi = i_s[j];
-                }
+                const unsigned __int128 ej = ((unsigned __int128)w_s[j].hi << 64) | w_s[j].lo;
+                const unsigned __int128 eb = ((unsigned __int128)b.hi << 64) | b.lo;
+                if (better(ej, w_s[j].idx, eb, b.idx)) b = w_s[j];
             }
-            winner[r] = bi | 0x80000000u;  // high bit: resolved by the fallback
+            part[(size_t)slot * nch + blockIdx.x] = b;
         }
+    }
+}
+
+__global__ void k_fallback_reduce(int nch, const int *fb_list, const int *fb_count, const Partial *part,
+                                  uint32_t *winner)
+{
+    const int count = *fb_count;
+    for (int slot = blockIdx.x * blockDim.x + threadIdx.x; slot < count; slot += gridDim.x * blockDim.x) {
+        Partial b = part[(size_t)slot * nch];
+        for (int j = 1; j < nch; ++j) {
+            const Partial pj = part[(size_t)slot * nch + j];
+            const unsigned __int128 ej = ((unsigned __int128)pj.hi << 64) | pj.lo;
+            const unsigned __int128 eb = ((unsigned __int128)b.hi << 64) | b.lo;
+            if (better(ej, pj.idx, eb, b.idx)) b = pj;
+        }
+        winner[fb_list[slot]] = b.idx | 0x80000000u;  // high bit: resolved by the fallback
     }
 }
 
@@ -368,19 +401,31 @@ __global__ void k_finalize(Geometry g, const RangeInfo *ri, const DomainInfo *di
 
 cudaError_t launch_rescore(const Geometry &g, const EpiConst &ec, const RangeInfo *ri,
                            const DomainInfo *di, const uint16_t *bblk, const uint16_t *qblk,
-                           const ListEntry *lists, int n_lists, const float *qp2max, uint32_t *winner,
-                           int *fb_list, int *fb_count, cudaStream_t st)
+                           const ListEntry *lists, int n_lists, uint32_t *winner, int *fb_list,
+                           int *fb_count, cudaStream_t st)
 {
-    k_rescore<<<(g.R + 3) / 4, 128, 0, st>>>(g, ec, ri, di, bblk, qblk, lists, n_lists, qp2max, winner,
-                                             fb_list, fb_count);
+    k_rescore<<<(g.R + 3) / 4, 128, 0, st>>>(g, ec, ri, di, bblk, qblk, lists, n_lists, winner, fb_list,
+                                             fb_count);
     return cudaGetLastError();
+}
+
+int fallback_chunks(const Geometry &g) { return std::min(64, std::max(1, g.N / 1024)); }
+
+size_t fallback_partial_bytes(const Geometry &g)
+{
+    return sizeof(Partial) * (size_t)g.R * fallback_chunks(g);
 }
 
 cudaError_t launch_fallback(const Geometry &g, const RangeInfo *ri, const DomainInfo *di,
                             const uint16_t *bblk, const uint16_t *qblk, const int *fb_list,
-                            const int *fb_count, uint32_t *winner, cudaStream_t st)
+                            const int *fb_count, void *partial, uint32_t *winner, cudaStream_t st)
 {
-    k_fallback<<<304, 256, 0, st>>>(g, ri, di, bblk, qblk, fb_list, fb_count, winner);
+    const int nch = fallback_chunks(g);
+    Partial *part = reinterpret_cast<Partial *>(partial);
+    k_fallback<<<dim3(nch, 16), 256, 0, st>>>(g, ri, di, bblk, qblk, fb_list, fb_count, part);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_fallback_reduce<<<4, 256, 0, st>>>(nch, fb_list, fb_count, part, winner);
     return cudaGetLastError();
 }
 

@@ -22,12 +22,13 @@ constexpr int XS = BN + 1;
 __global__ void __launch_bounds__(256) k_search_simt(Geometry g, EpiConst ec, const RangeInfo *ri,
                                                      const DomainInfo *di, const float4 *dconst,
                                                      const float *rs32, const float *cb32,
-                                                     ListEntry *lists, int n_split, float *dump)
+                                                     ListEntry *lists, int n_split, int *tbest, float *dump)
 {
     extern __shared__ float smem[];
     float *As = smem;              // [KC][BM]
     float *Bs = As + KC * BM;      // [KC][BN]
     float *Xs = Bs + KC * BN;      // [BM][XS]
+    float *Ks = Xs + BM * XS;      // [32][256]: keys staged for the rare pass
     __shared__ float er_s[BM];
     __shared__ float fdm_s[BN];
 
@@ -45,11 +46,8 @@ __global__ void __launch_bounds__(256) k_search_simt(Geometry g, EpiConst ec, co
     const int er_row = tid & (BM - 1);
     const int er_half = tid >> 7;
     const int my_r = r0 + er_row;
-    float zb = 0.0f, rho_lim = 0.5f;
-    if (my_r < g.R) {
-        zb = ri[my_r].zb;
-        rho_lim = ri[my_r].rho_lim;
-    }
+    RangeEpi re{};
+    if (my_r < g.R) re = range_epi(ri[my_r], ec);
     ListState L;
     list_init(L);
 
@@ -117,24 +115,37 @@ __global__ void __launch_bounds__(256) k_search_simt(Geometry g, EpiConst ec, co
             const int c0 = n0 + er_half * 32;
             for (int j = 0; j < 32 && c0 + j < g.N; ++j)
                 dump[(size_t)my_r * g.N + c0 + j] = Xs[er_row * XS + er_half * 32 + j];
-        } else if (my_r < g.R) {
+        } else if (my_r < g.R && !re.shadow) {
+            const float Tg = ord2f(__ldcg(tbest + my_r));  // best key other CTAs found
+            list_adopt(L, Tg, re, ec);
+            L.Tpub = fminf(L.Tpub, Tg);
             const int c0 = n0 + er_half * 32;
             const int nvalid = min(32, g.N - c0);
             if (nvalid > 0) {
+                const float *xrow = Xs + er_row * XS + er_half * 32;
                 float X[32];
 #pragma unroll
-                for (int j = 0; j < 32; ++j) X[j] = Xs[er_row * XS + er_half * 32 + j];
+                for (int j = 0; j < 32; ++j) X[j] = j < nvalid ? xrow[j] : __int_as_float(0x7fc00000);
                 float4 dc[4];
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     const int d = (c0 >> 3) + q;
                     dc[q] = d < g.D ? dconst[d] : make_float4(0.f, 0.f, 0.f, 0.f);
                 }
-                epi_chunk32(X, (uint32_t)c0, dc, zb, rho_lim, ec, L, nvalid);
+                if (epi_keys32(X, dc, re.zb, re.rho_lim, ec, fminf(L.key[kListK - 1], L.tw),
+                               L.has_zero ? kZeroPenalty : 0.0f)) {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) Ks[j * 256 + tid] = X[j];
+                    epi_rare(Ks + tid, 256, xrow, 1, (uint32_t)c0, dc, re, ec, L, nvalid);
+                    if (L.T < L.Tpub) {
+                        atomicMin(tbest + my_r, f2ord(L.T));
+                        L.Tpub = L.T;
+                    }
+                }
             }
         }
     }
-    if (my_r < g.R && !dump) {
+    if (my_r < g.R && !dump && !re.shadow) {
         const int n_lists = n_split * 2;
         ListEntry *dst = lists + ((size_t)my_r * n_lists + split * 2 + er_half) * kListK;
 #pragma unroll
@@ -146,14 +157,14 @@ int search_simt_lists_per_split() { return 2; }
 
 cudaError_t launch_search_simt(const Geometry &g, const EpiConst &ec, const RangeInfo *ri,
                                const DomainInfo *di, const float4 *dconst, const float *rs32,
-                               const float *cb32, ListEntry *lists, int n_split, float *dump,
+                               const float *cb32, ListEntry *lists, int n_split, int *tbest, float *dump,
                                cudaStream_t st)
 {
-    const size_t smem = sizeof(float) * (KC * BM + KC * BN + BM * XS);
+    const size_t smem = sizeof(float) * (KC * BM + KC * BN + BM * XS + 32 * 256);
     cudaError_t e = cudaFuncSetAttribute(k_search_simt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((g.R + BM - 1) / BM, n_split);
-    k_search_simt<<<grid, 256, smem, st>>>(g, ec, ri, di, dconst, rs32, cb32, lists, n_split, dump);
+    k_search_simt<<<grid, 256, smem, st>>>(g, ec, ri, di, dconst, rs32, cb32, lists, n_split, tbest, dump);
     return cudaGetLastError();
 }
 

@@ -146,9 +146,10 @@ __device__ __forceinline__ void umma_commit(uint64_t *bar)
                  : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
+// 32 lanes x 32 consecutive columns (one FP32 per column) for this warp's
+// lane quadrant.  Asynchronous: the registers are valid after tmem_wait().
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32])
 {
-    uint32_t r[32];
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
         "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
@@ -159,9 +160,20 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
           "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
           "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
         : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Wait for this thread's outstanding tcgen05.ld; the register operands tie
+// every later use of r[] to the wait.
+__device__ __forceinline__ void tmem_wait(uint32_t (&r)[32])
+{
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]),
+                   "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]),
+                   "+r"(r[14]), "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]),
+                   "+r"(r[21]), "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]),
+                   "+r"(r[28]), "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
+                 :
+                 : "memory");
 }
 
 struct TcMaps {
@@ -175,7 +187,7 @@ struct TcMaps {
 template <int NBLK>
 __global__ void __launch_bounds__(THREADS, 1)
     k_search_tc(const __grid_constant__ TcMaps maps, Geometry g, EpiConst ec, const RangeInfo *ri,
-                const float4 *dconst, ListEntry *lists, int n_split, float *dump, int *err,
+                const float4 *dconst, ListEntry *lists, int n_split, int *tbest, float *dump, int *err,
                 uint32_t smem_bytes, int rpad, int npad)
 {
     constexpr uint32_t A_BLK = BM * 128;                 // bytes of one 64-col block, A
@@ -189,6 +201,9 @@ __global__ void __launch_bounds__(THREADS, 1)
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t *sA = smem;
     uint8_t *sB = smem + A_BYTES;  // A_BYTES is a multiple of 1024
+    float *ksm = reinterpret_cast<float *>(sB + STAGES * B_BYTES);  // [32][128] keys (rare pass)
+    float *xsm = ksm + 32 * BM;                                     // [32][128] cross terms (rare pass)
+    float4 *dcs = reinterpret_cast<float4 *>(xsm + 32 * BM);        // [4 warps][16] domain constants
     __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], a_bar, tfull_bar[NACC], tempty_bar[NACC];
     __shared__ uint32_t tmem_base_s;
     __shared__ int abort_s;
@@ -205,7 +220,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     if (threadIdx.x == 0) {
         // self-checks: every TMA box and MMA operand must lie inside this CTA's
         // dynamic shared memory, and every box inside the padded operands
-        const uint32_t used = (uint32_t)(smem - smem_raw) + A_BYTES + STAGES * B_BYTES;
+        const uint32_t used = (uint32_t)(smem - smem_raw) + A_BYTES + STAGES * B_BYTES + 2 * 32 * BM * 4 + 4 * 16 * 16;
         int bad = 0;
         if (used > smem_bytes) bad = 2;
         if (r0 + BM > rpad || t_end * BN > npad) bad = 3;
@@ -311,44 +326,92 @@ __global__ void __launch_bounds__(THREADS, 1)
         const int row = quad * 32 + lane;
         const int r = r0 + row;
         const bool live = r < g.R;
-        float zb = 0.0f, rho_lim = 0.5f;
-        if (live) {
-            zb = ri[r].zb;
-            rho_lim = ri[r].rho_lim;
-        }
+        float4 *wdc = dcs + (warp - 2) * 16;
+        RangeEpi re{};
+        if (live) re = range_epi(ri[r], ec);
+        const bool scr = live && !re.shadow;  // shadow ranges need no screening
         ListState L;
         list_init(L);
+        const uint32_t lane_addr = tmem_base + ((uint32_t)(quad * 32) << 16);
         for (int it = 0; it < ntile; ++it) {
             const int acc = it % NACC;
+            const int n0 = (t_begin + it) * BN;
+            // this tile's 16 domains: staged once per warp
+            if (lane < BN / 8) {
+                const int d = (n0 >> 3) + lane;
+                wdc[lane] = d < g.D ? __ldg(dconst + d) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+            if (scr && !dump) {
+                const float Tg = ord2f(__ldcg(tbest + r));  // best key other CTAs found
+                list_adopt(L, Tg, re, ec);
+                L.Tpub = fminf(L.Tpub, Tg);
+            }
+            __syncwarp();
             // warp-uniform decision: tcgen05.ld below is .sync.aligned
             if (!__all_sync(0xffffffffu, mbar_wait(&tfull_bar[acc], (it / NACC) & 1, &abort_s, err))) break;
             tc_fence_after();
-            const int n0 = (t_begin + it) * BN;
-#pragma unroll 1
-            for (int ch = 0; ch < BN / 32; ++ch) {
-                float X[32];
-                tmem_ld32(tmem_base + ((uint32_t)(quad * 32) << 16) + acc * BN + ch * 32, X);
+            const uint32_t taddr = lane_addr + acc * BN;
+            // one chunk of 32 columns; `nxt` is being filled by a prefetch
+            auto chunk = [&](uint32_t(&cur)[32], int ch) {
                 const int c0 = n0 + ch * 32;
                 const int nvalid = min(32, g.N - c0);
+                float X[32];
+#pragma unroll
+                for (int j = 0; j < 32; ++j) X[j] = __uint_as_float(cur[j]);
                 if (dump) {
 #pragma unroll
                     for (int j = 0; j < 32; ++j)
                         if (live && j < nvalid) dump[(size_t)r * g.N + c0 + j] = X[j];
-                } else if (live && nvalid > 0) {
-                    float4 dc[4];
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const int d = (c0 >> 3) + q;
-                        dc[q] = d < g.D ? __ldg(dconst + d) : make_float4(0.f, 0.f, 0.f, 0.f);
-                    }
-                    epi_chunk32(X, (uint32_t)c0, dc, zb, rho_lim, ec, L, nvalid);
+                    return;
                 }
+                if (nvalid < 32) {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j)
+                        if (j >= nvalid) X[j] = __int_as_float(0x7fc00000);  // NaN: never listed
+                }
+                float4 dc[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) dc[q] = wdc[ch * 4 + q];
+                const bool need = scr && nvalid > 0 &&
+                                  epi_keys32(X, dc, re.zb, re.rho_lim, ec, fminf(L.key[kListK - 1], L.tw),
+                                             L.has_zero ? kZeroPenalty : 0.0f);
+                if (__any_sync(0xffffffffu, need)) {
+                    // stage keys, reload the cross terms (still in TMEM), then each
+                    // thread walks its own row
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) ksm[j * BM + row] = X[j];
+                    uint32_t tx[32];
+                    tmem_ld32(taddr + ch * 32, tx);
+                    tmem_wait(tx);
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) xsm[j * BM + row] = __uint_as_float(tx[j]);
+                    if (need) {
+                        epi_rare(ksm + row, BM, xsm + row, BM, (uint32_t)c0, dc, re, ec, L, nvalid);
+                        if (L.T < L.Tpub) {
+                            atomicMin(tbest + r, f2ord(L.T));
+                            L.Tpub = L.T;
+                        }
+                    }
+                    __syncwarp();
+                }
+            };
+            uint32_t ra[32], rb[32];
+            tmem_ld32(taddr, ra);
+            tmem_wait(ra);
+#pragma unroll 1
+            for (int ch = 0; ch < BN / 32; ch += 2) {
+                tmem_ld32(taddr + (ch + 1) * 32, rb);  // prefetch the odd chunk
+                chunk(ra, ch);
+                tmem_wait(rb);
+                if (ch + 2 < BN / 32) tmem_ld32(taddr + (ch + 2) * 32, ra);  // prefetch the next even chunk
+                chunk(rb, ch + 1);
+                if (ch + 2 < BN / 32) tmem_wait(ra);
             }
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&tempty_bar[acc]);
         }
-        if (live && !dump) {
+        if (scr && !dump) {
             ListEntry *dst = lists + ((size_t)r * n_split + split) * kListK;
 #pragma unroll
             for (int i = 0; i < kListK; ++i) dst[i] = ListEntry{L.key[i], L.idx[i]};
@@ -407,7 +470,8 @@ bool search_tc_supported(const Geometry &g)
 size_t search_tc_smem(const Geometry &g)
 {
     const int nblk = g.split_hilo ? 2 : 1;
-    return 1024 + (size_t)(nblk * BM * 128 + BM * 32) + (size_t)STAGES * (nblk * BN * 128 + BN * 32);
+    return 1024 + (size_t)(nblk * BM * 128 + BM * 32) + (size_t)STAGES * (nblk * BN * 128 + BN * 32) +
+           2 * 32 * BM * 4 + 4 * 16 * 16;
 }
 
 int search_tc_tile() { return BN; }
@@ -415,8 +479,8 @@ int search_tc_tile() { return BN; }
 int search_tc_rows(int rows) { return (rows + 127) / 128 * 128; }
 
 cudaError_t launch_search_tc(const Geometry &g, const EpiConst &ec, const RangeInfo *ri, const float4 *dconst,
-                             const __half *ra16, const __half *cb16, ListEntry *lists, int n_split, float *dump,
-                             int *err, cudaStream_t st)
+                             const __half *ra16, const __half *cb16, ListEntry *lists, int n_split, int *tbest,
+                             float *dump, int *err, cudaStream_t st)
 {
     if (!search_tc_supported(g)) return cudaErrorInvalidValue;
     TcMaps mp;
@@ -434,12 +498,12 @@ cudaError_t launch_search_tc(const Geometry &g, const EpiConst &ec, const RangeI
     if (nblk == 2) {
         e = cudaFuncSetAttribute(k_search_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        k_search_tc<2><<<grid, THREADS, smem, st>>>(mp, g, ec, ri, dconst, lists, n_split, dump, err,
+        k_search_tc<2><<<grid, THREADS, smem, st>>>(mp, g, ec, ri, dconst, lists, n_split, tbest, dump, err,
                                                     (uint32_t)smem, rpad, npad);
     } else {
         e = cudaFuncSetAttribute(k_search_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        k_search_tc<1><<<grid, THREADS, smem, st>>>(mp, g, ec, ri, dconst, lists, n_split, dump, err,
+        k_search_tc<1><<<grid, THREADS, smem, st>>>(mp, g, ec, ri, dconst, lists, n_split, tbest, dump, err,
                                                     (uint32_t)smem, rpad, npad);
     }
     return cudaGetLastError();
