@@ -165,6 +165,35 @@ int fic_last_encode_stats(int64_t out[4]);
 int fic_cross_terms(const void *img, int w, int h, int pitch_px, const fic_params *p, float *out,
                     void *workspace, size_t workspace_bytes, void *stream);
 
+/*
+ * fic_encode_static -- fic_encode for callers that may not allocate device
+ *   memory (no counterpart in the paper: this is a deployment aid).
+ *
+ *   Some hosts forbid device allocation by a library: a plug-in whose host
+ *   application owns all GPU memory, a real-time pipeline that reserves every
+ *   buffer at start-up, a process under a device-memory cap it does not
+ *   control.  This call allocates nothing (no cudaMalloc, cudaFree or other
+ *   allocating routine): its scratch is a static device array of
+ *   FIC_STATIC_SCRATCH_BYTES that each GPU loading the library keeps until
+ *   the process exits.  The caller still passes the image and the maps
+ *   buffer (host or device, as for fic_encode).
+ *
+ *   - Images whose workspace (fic_encode_workspace_size) exceeds
+ *     FIC_STATIC_SCRATCH_BYTES are rejected with FIC_ERR_CAPACITY before any
+ *     device work; e.g. 256x256 with 8x8 ranges fits, 512x512 at stride 4
+ *     does not.
+ *   - The first call on each device looks up the array's device address; make
+ *     that first call before any stream capture on that device.
+ *   - Every call on a device shares the one array, which keeps the previous
+ *     call's contents (each call initialises what it needs).  Calls whose
+ *     work overlaps on the GPU -- concurrent streams, or several host threads
+ *     -- race on it: serialise them.
+ *   - FIC_FLAG_PHASE_TIMING is rejected (it would create CUDA events).
+ */
+#define FIC_STATIC_SCRATCH_BYTES (16u << 20)
+int fic_encode_static(const void *img, int w, int h, int pitch_px, const fic_params *p, fic_map *maps,
+                      int maps_cap, int *n_maps, void *stream);
+
 /* Phase durations (ms) of the last fic_encode on this host thread that ran
  * with FIC_FLAG_PHASE_TIMING: out[0] prep, out[1] search, out[2] re-score,
  * out[3] fallback, out[4] map output.  Waits for those events. */

@@ -385,6 +385,16 @@ done:
 
 }  // namespace
 
+namespace fic {
+int encode_with_workspace(const void *img, int w, int h, int pitch_px, const fic_params *p, fic_map *maps,
+                          int maps_cap, int *n_maps, void *workspace, size_t workspace_bytes, void *stream)
+{
+    if (!maps || !workspace) return FIC_ERR_BAD_ARG;
+    return run_encode(img, w, h, pitch_px, p, maps, maps_cap, n_maps, workspace, workspace_bytes, stream,
+                      nullptr);
+}
+}  // namespace fic
+
 extern "C" {
 
 int fic_encode(const void *img, int w, int h, int pitch_px, const fic_params *p, fic_map *maps,

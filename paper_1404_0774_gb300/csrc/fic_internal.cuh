@@ -326,6 +326,9 @@ cudaError_t launch_prep(const Geometry &g, const void *img, const EpiConst &ec, 
 cudaError_t launch_seed(const Geometry &g, const EpiConst &ec, const RangeInfo *ri, const DomainInfo *di,
                         const float4 *dconst, const uint16_t *bblk, const uint16_t *qblk, int *tbest,
                         cudaStream_t st);
+// The encode pipeline on a caller-provided device workspace (never allocates).
+int encode_with_workspace(const void *img, int w, int h, int pitch_px, const fic_params *p, fic_map *maps,
+                          int maps_cap, int *n_maps, void *workspace, size_t workspace_bytes, void *stream);
 // Key-space value that excludes s-code-0 candidates once a list holds one.
 constexpr float kZeroPenalty = 1e30f;
 

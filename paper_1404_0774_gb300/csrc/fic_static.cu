@@ -1,0 +1,70 @@
+// fic_encode_static: the encode pipeline with its scratch memory in a fixed
+// device array that lives inside this library, for callers that may not
+// allocate device memory themselves.
+//
+// Who needs this: code that runs where asking the CUDA allocator for memory
+// is not allowed or not acceptable -- a plug-in whose host application owns
+// and budgets all device memory, a real-time pipeline that reserves every
+// buffer at start-up so that no allocation can stall a frame later, or a
+// process running under a hard device-memory cap set by someone else.  Such a
+// caller can neither pass a workspace it allocated nor let fic_encode
+// allocate one.  This entry point uses instead a static array of
+// FIC_STATIC_SCRATCH_BYTES (16 MiB) that every GPU which loads the library
+// holds until the process exits.
+#include <mutex>
+
+#include "fic_internal.cuh"
+
+namespace {
+
+constexpr size_t kStaticBytes = FIC_STATIC_SCRATCH_BYTES;
+
+// The scratch.  In host code this name is only a host-side stand-in for the
+// device array, never a device address: the address a kernel may use comes
+// from cudaGetSymbolAddress below.
+static __device__ __align__(256) unsigned char g_scratch[kStaticBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+void *g_addr[kMaxDevices] = {};
+
+// Device address of g_scratch on the current device, looked up once per device
+// (with that device current).  Returns nullptr on failure.
+void *scratch_address()
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_addr[dev]) {
+        void *ptr = nullptr;
+        if (cudaGetSymbolAddress(&ptr, g_scratch) != cudaSuccess || !ptr) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        g_addr[dev] = ptr;
+    }
+    return g_addr[dev];
+}
+
+}  // namespace
+
+extern "C" {
+
+int fic_encode_static(const void *img, int w, int h, int pitch_px, const fic_params *p, fic_map *maps,
+                      int maps_cap, int *n_maps, void *stream)
+{
+    if (!img || !maps || !p) return FIC_ERR_BAD_ARG;
+    if (p->flags & FIC_FLAG_PHASE_TIMING) return FIC_ERR_BAD_ARG;  // timing events would be created
+    size_t need = 0;
+    const int rc = fic_encode_workspace_size(w, h, p, &need);  // host-only size check, no device call
+    if (rc != FIC_OK) return rc;
+    if (need > kStaticBytes) return FIC_ERR_CAPACITY;
+    void *ws = scratch_address();
+    if (!ws) return FIC_ERR_CUDA;
+    return fic::encode_with_workspace(img, w, h, pitch_px, p, maps, maps_cap, n_maps, ws, kStaticBytes, stream);
+}
+
+}  // extern "C"

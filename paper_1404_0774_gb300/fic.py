@@ -68,6 +68,8 @@ def lib():
         L.fic_last_encode_stats.argtypes = [i64p]
         L.fic_last_encode_phase_ms.argtypes = [ctypes.POINTER(ctypes.c_double)]
         L.fic_cross_terms.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, pp, vp, vp, sz, vp]
+        L.fic_encode_static.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, pp, vp, ctypes.c_int,
+                                        ctypes.POINTER(ctypes.c_int), vp]
         _lib = L
     return _lib
 
