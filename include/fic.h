@@ -84,6 +84,12 @@ typedef struct {
 /* fic_params.flags: record CUDA events around each encode phase on the
  * caller's stream (read them back with fic_last_encode_phase_ms). */
 #define FIC_FLAG_PHASE_TIMING 0x1u
+/* fic_params.flags: screen every range and every domain.  By default the
+ * search skips what Section V says needs no search: shadow (constant) ranges,
+ * and flat (zero-variance) domains, whose candidates all share one residual
+ * per range and are represented by the first of them.  The maps are the same
+ * either way; this flag exists to measure and test the dense search. */
+#define FIC_FLAG_DENSE 0x2u
 
 /* One map per range: range -> (domain, symmetry, s, o) and its collage error. */
 typedef struct {
@@ -95,7 +101,7 @@ typedef struct {
     float s;             /* s_hat                                             */
     float o;             /* o_hat                                             */
     uint32_t info;       /* FIC_MAP_* bits                                    */
-    double err;          /* eq 8 residual, FP64, summed over pixels in order  */
+    double err;          /* eq 8 residual: exact value rounded to FP64        */
 } fic_map;
 
 #define FIC_MAP_FALLBACK 0x1u /* resolved by the exact full rescan           */

@@ -40,7 +40,7 @@ size_t align_up(size_t v) { return (v + kAlign - 1) & ~(kAlign - 1); }
 int check_params(const fic_params *p)
 {
     if (!p) return FIC_ERR_BAD_ARG;
-    if (p->flags & ~FIC_FLAG_PHASE_TIMING) return FIC_ERR_BAD_ARG;
+    if (p->flags & ~(FIC_FLAG_PHASE_TIMING | FIC_FLAG_DENSE)) return FIC_ERR_BAD_ARG;
     if (p->range_size != 4 && p->range_size != 8 && p->range_size != 16) return FIC_ERR_BAD_ARG;
     if (p->domain_stride < 1) return FIC_ERR_BAD_ARG;
     if (p->bit_depth < 1 || p->bit_depth > 12) return FIC_ERR_BITDEPTH;
@@ -66,6 +66,7 @@ int make_geometry(int w, int h, int pitch, const fic_params *p, Geometry &g)
     g.n = n;
     g.t = p->domain_stride;
     g.m = n * n;
+    g.ln = n == 4 ? 2 : (n == 8 ? 3 : 4);
     g.nx = w / n;
     g.ny = h / n;
     g.R = g.nx * g.ny;
@@ -130,26 +131,31 @@ int choose_search(const Geometry &g, const fic_params *p)
     return p->search == FIC_SEARCH_TC ? -1 : FIC_SEARCH_SIMT;
 }
 
-// Split of the candidate dimension: enough CTAs for whole waves over the SMs.
+// Maximum split of the candidate dimension (the list layout).  The kernels
+// use fewer splits when fewer ranges and domains need screening: enough CTAs
+// for `target` (four waves over the SMs), see active_splits.
+constexpr int kMaxSplit = 64;
 int choose_split(const Geometry &g, const fic_params *p, int search)
 {
-    const int tile = search == FIC_SEARCH_TC ? search_tc_tile() : 64;
-    const int tiles = (g.N + tile - 1) / tile;
-    const int mt = (g.R + 127) / 128;
-    int s = p->n_split;
-    if (s == 0) {
-        const int per_sm = search == FIC_SEARCH_TC ? 1 : 2;
-        const int target = 4 * per_sm * sm_count();  // four waves
-        s = std::max(1, (target + mt - 1) / mt);
-    }
-    return std::max(1, std::min(std::min(s, tiles), 64));
+    (void)g;
+    (void)search;
+    return p->n_split > 0 ? std::min(p->n_split, kMaxSplit) : kMaxSplit;
 }
 
-int lists_per_split(int search) { return search == FIC_SEARCH_SIMT ? search_simt_lists_per_split() : 1; }
+int split_target(const fic_params *p, int search)
+{
+    if (p->n_split > 0) return 1 << 30;  // a fixed split: active_splits caps it at max_split
+    return 4 * (search == FIC_SEARCH_TC ? 1 : 2) * sm_count();
+}
+
+int lists_per_split(int search)
+{
+    return search == FIC_SEARCH_SIMT ? search_simt_lists_per_split() : search_tc_lists_per_split();
+}
 
 struct EncLayout {
     size_t img, ri, di, dconst, bblk, qblk, rs32, cb32, ra16, cb16, lists, winner, fb_list, fb_count,
-        tbest, partial, maps, total;
+        tbest, partial, maps, rkeep, dkeep, act, dact, counts, dconst_c, dmap, total;
 };
 
 EncLayout enc_layout(const Geometry &g, int search, int n_lists)
@@ -180,6 +186,13 @@ EncLayout enc_layout(const Geometry &g, int search, int n_lists)
     L.tbest = take(sizeof(int) * g.R);
     L.partial = take(fallback_partial_bytes(g));
     L.maps = take(sizeof(fic_map) * g.R);
+    L.rkeep = take(sizeof(int) * g.R);
+    L.dkeep = take(sizeof(int) * g.D);
+    L.act = take(sizeof(int) * g.R);
+    L.dact = take(sizeof(int) * g.D);
+    L.counts = take(sizeof(int) * 4);
+    L.dconst_c = take(sizeof(float4) * g.D);
+    L.dmap = take(sizeof(int) * g.D);
     L.total = o;
     return L;
 }
@@ -323,6 +336,16 @@ int run_encode(const void *img, int w, int h, int pitch_px, const fic_params *p,
         int *err = fb_count + 1;
         int *tbest = reinterpret_cast<int *>(ws + L.tbest);
         void *partial = ws + L.partial;
+        CompactBufs cbuf;
+        cbuf.rkeep = reinterpret_cast<int *>(ws + L.rkeep);
+        cbuf.dkeep = reinterpret_cast<int *>(ws + L.dkeep);
+        cbuf.act = reinterpret_cast<int *>(ws + L.act);
+        cbuf.dact = reinterpret_cast<int *>(ws + L.dact);
+        cbuf.counts = reinterpret_cast<int *>(ws + L.counts);
+        cbuf.dconst_c = reinterpret_cast<float4 *>(ws + L.dconst_c);
+        cbuf.dmap = reinterpret_cast<int *>(ws + L.dmap);
+        // the contraction dump covers every range and candidate
+        const int dense = (dump || (p->flags & FIC_FLAG_DENSE)) ? 1 : 0;
         fic_map *dmaps = maps_dev ? maps : reinterpret_cast<fic_map *>(ws + L.maps);
         const EpiConst ec = make_epi(g);
         const bool timed = !dump && (p->flags & FIC_FLAG_PHASE_TIMING) && g_phase.ensure();
@@ -337,16 +360,21 @@ int run_encode(const void *img, int w, int h, int pitch_px, const fic_params *p,
             FIC_CUDA(cudaMemsetAsync(ws + L.cb16 + row * g.N, 0, row * (search_tc_rows(g.N) - g.N), st));
         }
         FIC_MARK(0);
-        FIC_CUDA(launch_prep(gd, dimg, ec, ri, di, dconst, bblk, qblk, rs32, cb32, ra16, cb16, tbest, st));
+        FIC_CUDA(launch_prep(gd, dimg, ec, dense, ri, di, dconst, bblk, qblk, rs32, cb32, ra16, cb16, tbest, cbuf, st));
         if (!dump) FIC_CUDA(launch_seed(gd, ec, ri, di, dconst, bblk, qblk, tbest, st));
         FIC_MARK(1);
+        const int target = split_target(p, search);
         if (search == FIC_SEARCH_TC)
-            FIC_CUDA(launch_search_tc(gd, ec, ri, dconst, ra16, cb16, lists, n_split, tbest, dump, err, st));
+            FIC_CUDA(launch_search_tc(gd, ec, ri, cbuf, dense, ra16, cb16, lists, n_split, target, tbest, dump, err,
+                                      st));
         else
-            FIC_CUDA(launch_search_simt(gd, ec, ri, di, dconst, rs32, cb32, lists, n_split, tbest, dump, st));
+            FIC_CUDA(launch_search_simt(gd, ec, ri, di, cbuf, dense, rs32, cb32, lists, n_split, target, tbest, dump,
+                                        st));
         FIC_MARK(2);
         if (!dump) {
-            FIC_CUDA(launch_rescore(gd, ec, ri, di, bblk, qblk, lists, n_lists, winner, fb_list, fb_count, st));
+            FIC_CUDA(launch_rescore(gd, ec, ri, di, bblk, qblk, lists, n_lists, cbuf.counts, lists_per_split(search),
+                                    search == FIC_SEARCH_TC ? search_tc_tile() : 64, target, n_split, dense, winner,
+                                    fb_list, fb_count, st));
             FIC_MARK(3);
             FIC_CUDA(launch_fallback(gd, ri, di, bblk, qblk, fb_list, fb_count, partial, winner, st));
             FIC_MARK(4);

@@ -38,6 +38,7 @@ constexpr float kMagic = 12582912.0f;  // 1.5 * 2^23: x + kMagic rounds x to an 
 struct Geometry {
     int w, h, pitch;   // image size and row pitch (elements)
     int n, t, m;       // range size, domain stride, pixels per range
+    int ln;            // log2(n): n is a power of two
     int nx, ny, R;     // ranges per row / column / total
     int U, V, D;       // domains per row / column / total
     int N;             // candidates = 8*D
@@ -191,28 +192,102 @@ __device__ __forceinline__ float epi_key(float X, float c, float zb, float4 dc, 
     return fmaf(__fmul_rn(wv, ec.lambda), wv, cy);
 }
 
+// Packed FP32 pairs (sm_100 family .f32x2 arithmetic, round to nearest):
+// two candidates per instruction, each lane computing exactly what the scalar
+// operation would.
+typedef unsigned long long f32x2_t;
+
+__device__ __forceinline__ f32x2_t pk2(float lo, float hi)
+{
+    f32x2_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+
+__device__ __forceinline__ void upk2(f32x2_t v, float &lo, float &hi)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+
+__device__ __forceinline__ f32x2_t fma2(f32x2_t a, f32x2_t b, f32x2_t c)
+{
+    f32x2_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+__device__ __forceinline__ f32x2_t add2(f32x2_t a, f32x2_t b)
+{
+    f32x2_t d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+__device__ __forceinline__ f32x2_t sub2(f32x2_t a, f32x2_t b)
+{
+    f32x2_t d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+__device__ __forceinline__ f32x2_t mul2(f32x2_t a, f32x2_t b)
+{
+    f32x2_t d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
 // Main pass over 32 consecutive candidates (4 domains x 8 symmetries):
-// X[] (cross terms) is overwritten by the keys.  Branch-free.  Returns whether
-// this thread needs the rare pass: a key below `thr`, or a code decided next
-// to its rounding boundary.  Lanes beyond the ragged end carry X = NaN (their
-// keys are NaN and compare false everywhere).
-// zpen: added to the key of s-code-0 candidates (their residual is one value
-// per range; once the list holds one, the others need never be looked at).
+// X[] (cross terms) is overwritten by the keys.  Branch-free, two candidates
+// (same domain, so same column constants) per packed instruction; the keys
+// are bit-identical to epi_code/epi_key.  Returns whether this thread needs
+// the rare pass: a key below `thr`, or a code decided next to its rounding
+// boundary.  Lanes beyond the ragged end carry X = NaN (their keys are NaN
+// and compare false everywhere).  zpen: added to the key of s-code-0
+// candidates (their residual is one value per range; once the list holds
+// one, the others need never be looked at).
 __device__ __forceinline__ bool epi_keys32(float (&X)[32], const float4 (&dc)[4], float zb, float rho_lim,
                                            const EpiConst &ec, float thr, float zpen)
 {
     float kmin = __int_as_float(0x7f800000);
     float rmax = 0.0f;
+    const f32x2_t two_ls = pk2(ec.two_ls, ec.two_ls), mls = pk2(-ec.ls, -ec.ls);
+    const f32x2_t mag = pk2(kMagic, kMagic), zb2 = pk2(zb, zb), invg = pk2(ec.invG, ec.invG);
+    const f32x2_t mg = pk2(-ec.G, -ec.G), lam = pk2(ec.lambda, ec.lambda), zp = pk2(zpen, zpen);
 #pragma unroll
-    for (int j = 0; j < 32; ++j) {
-        const float4 c4 = dc[j >> 3];
-        float rho;
-        const float c = epi_code(X[j], c4.x, ec, rho);
-        const float zero = __saturatef(fmaf(c, -c, 1.0f));  // 1 for c = 0, else 0 (c is an integer)
-        const float k = fmaf(zero, zpen, epi_key(X[j], c, zb, c4, ec));
-        X[j] = k;
-        kmin = fminf(kmin, k);
-        rmax = fmaxf(rmax, fabsf(rho));
+    for (int q = 0; q < 4; ++q) {
+        const float4 c4 = dc[q];
+        const f32x2_t msqz = pk2(-c4.y, -c4.y), kap = pk2(c4.z, c4.z);
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            const int j = q * 8 + 2 * h;
+            const float u0 = __saturatef(fmaf(X[j], c4.x, 0.5f));
+            const float u1 = __saturatef(fmaf(X[j + 1], c4.x, 0.5f));
+            const f32x2_t x = pk2(X[j], X[j + 1]);
+            const f32x2_t r = fma2(pk2(u0, u1), two_ls, mls);  // Ls * clamp(s, -1, 1)
+            const f32x2_t c = sub2(add2(r, mag), mag);          // rounded code
+            const f32x2_t rho = sub2(r, c);
+            float c0, c1, p0, p1;
+            upk2(c, c0, c1);
+            upk2(rho, p0, p1);
+            rmax = fmaxf(rmax, fabsf(p0));
+            rmax = fmaxf(rmax, fabsf(p1));
+            const float zero0 = __saturatef(fmaf(c0, -c0, 1.0f));  // 1 for c = 0, else 0
+            const float zero1 = __saturatef(fmaf(c1, -c1, 1.0f));
+            const f32x2_t z = fma2(c, msqz, zb2);
+            const f32x2_t e = sub2(fma2(z, invg, mag), mag);
+            const f32x2_t wv = fma2(e, mg, z);
+            const f32x2_t y = fma2(c, kap, sub2(pk2(0.0f, 0.0f), x));
+            const f32x2_t cy = mul2(c, y);
+            f32x2_t k = fma2(mul2(wv, lam), wv, cy);
+            k = fma2(pk2(zero0, zero1), zp, k);
+            float k0, k1;
+            upk2(k, k0, k1);
+            X[j] = k0;
+            X[j + 1] = k1;
+            kmin = fminf(kmin, k0);
+            kmin = fminf(kmin, k1);
+        }
     }
     return kmin < thr || rmax > rho_lim;
 }
@@ -227,8 +302,10 @@ __device__ __forceinline__ float4 pick4(const float4 (&dc)[4], int q)
 // (the key becomes the smaller of the two neighbouring codes' keys: a lower
 // bound of the residual FP64 decides) and list insertion with s-code-0
 // de-duplication (all such candidates of a range have one residual).
-static __device__ __noinline__ void epi_rare(const float *krow, int stride, const float *xrow, int xstride,
-                                      uint32_t idx0, const float4 (&dc)[4], const RangeEpi &re,
+// od[q]: original index of the chunk's q-th domain (the search may skip flat
+// domains, so consecutive columns need not be consecutive domains).
+static __device__ __forceinline__ void epi_rare(const float *krow, int stride, const float *xrow, int xstride,
+                                      const int (&od)[4], const float4 (&dc)[4], const RangeEpi &re,
                                       const EpiConst &ec, ListState &L, int nvalid)
 {
 #pragma unroll 1
@@ -248,7 +325,9 @@ static __device__ __noinline__ void epi_rare(const float *krow, int stride, cons
             if (L.has_zero) continue;
             L.has_zero = 1;  // later s-code-0 keys carry the penalty in the main pass
         }
-        list_insert(L, k, idx0 + j);
+        const int q = j >> 3;
+        const int d = q == 0 ? od[0] : (q == 1 ? od[1] : (q == 2 ? od[2] : od[3]));
+        list_insert(L, k, (uint32_t)(d * 8 + (j & 7)));
         if (k < L.T && !near) {
             // a clean key (code not near a boundary, offset not clamped) is an
             // upper bound of the residual up to beta: it may tighten the window
@@ -278,23 +357,49 @@ __device__ __forceinline__ int load_px(const void *img, int B, size_t off)
     return B <= 8 ? (int)((const uint8_t *)img)[off] : (int)((const uint16_t *)img)[off];
 }
 
+// Compaction of the search dimensions: ranges that need screening (all but
+// shadow ranges) and domains that need screening (all but flat domains), in
+// their original order.  counts[0] = ranges kept, counts[1] = first shadow
+// range, counts[2] = domains kept, counts[3] = first flat domain (-1: none).
+struct CompactBufs {
+    int *rkeep, *dkeep;   // flags
+    int *act;             // kept range ids (search row j -> range act[j])
+    int *dact;            // kept domain ids
+    int *counts;          // 4 ints, see above
+    float4 *dconst_c;     // epilogue constants of the kept domains, in order
+    int *dmap;            // kept domain j -> original domain id
+};
+// Number of candidate-dimension splits actually used: enough CTAs for about
+// `target` (a few waves over the SMs) given the number of row tiles that have
+// ranges to screen, capped by the list layout (max_split) and by the tiles.
+__host__ __device__ __forceinline__ int active_splits(int row_tiles, int col_tiles, int target, int max_split)
+{
+    if (row_tiles <= 0 || col_tiles <= 0) return 1;
+    int s = target / row_tiles;
+    s = s < 1 ? 1 : s;
+    s = s > max_split ? max_split : s;
+    return s > col_tiles ? col_tiles : s;
+}
+
 // ---------------------------------------------------------------- launches
 // (host-side wrappers, each returns cudaError_t of the launch)
 cudaError_t launch_search_simt(const Geometry &g, const EpiConst &ec, const RangeInfo *ri,
-                               const DomainInfo *di, const float4 *dconst, const float *rs32,
-                               const float *cb32, ListEntry *lists, int n_split, int *tbest, float *dump,
-                               cudaStream_t st);
+                               const DomainInfo *di, const CompactBufs &cb, int dense, const float *rs32,
+                               const float *cb32, ListEntry *lists, int max_split, int target, int *tbest,
+                               float *dump, cudaStream_t st);
 bool search_tc_supported(const Geometry &g);
 size_t search_tc_smem(const Geometry &g);
 int search_tc_tile();
+int search_tc_lists_per_split();
 int search_tc_rows(int rows);  // operand rows allocated (multiple of the TMA box)
-cudaError_t launch_search_tc(const Geometry &g, const EpiConst &ec, const RangeInfo *ri, const float4 *dconst,
-                             const __half *ra16, const __half *cb16, ListEntry *lists, int n_split, int *tbest,
-                             float *dump, int *err, cudaStream_t st);
+cudaError_t launch_search_tc(const Geometry &g, const EpiConst &ec, const RangeInfo *ri, const CompactBufs &cb,
+                             int dense, const __half *ra16, const __half *cb16, ListEntry *lists, int max_split,
+                             int target, int *tbest, float *dump, int *err, cudaStream_t st);
 int search_simt_lists_per_split();
 cudaError_t launch_rescore(const Geometry &g, const EpiConst &ec, const RangeInfo *ri,
                            const DomainInfo *di, const uint16_t *bblk, const uint16_t *qblk,
-                           const ListEntry *lists, int n_lists, uint32_t *winner, int *fb_list,
+                           const ListEntry *lists, int max_lists, const int *counts, int lists_per_split,
+                           int col_tile, int target, int max_split, int dense, uint32_t *winner, int *fb_list,
                            int *fb_count, cudaStream_t st);
 size_t fallback_partial_bytes(const Geometry &g);
 cudaError_t launch_fallback(const Geometry &g, const RangeInfo *ri, const DomainInfo *di,
@@ -320,9 +425,9 @@ __device__ __forceinline__ RangeEpi range_epi(const RangeInfo &ri, const EpiCons
     re.shadow = ri.shadow;
     return re;
 }
-cudaError_t launch_prep(const Geometry &g, const void *img, const EpiConst &ec, RangeInfo *ri, DomainInfo *di,
-                        float4 *dconst, uint16_t *bblk, uint16_t *qblk, float *rs32, float *cb32,
-                        __half *ra16, __half *cb16, int *tbest, cudaStream_t st);
+cudaError_t launch_prep(const Geometry &g, const void *img, const EpiConst &ec, int dense, RangeInfo *ri,
+                        DomainInfo *di, float4 *dconst, uint16_t *bblk, uint16_t *qblk, float *rs32, float *cb32,
+                        __half *ra16, __half *cb16, int *tbest, const CompactBufs &cb, cudaStream_t st);
 cudaError_t launch_seed(const Geometry &g, const EpiConst &ec, const RangeInfo *ri, const DomainInfo *di,
                         const float4 *dconst, const uint16_t *bblk, const uint16_t *qblk, int *tbest,
                         cudaStream_t st);

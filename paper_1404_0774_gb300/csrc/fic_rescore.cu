@@ -87,27 +87,6 @@ __device__ void warp_argmin(unsigned __int128 &err, uint32_t &idx)
     }
 }
 
-// Exact X of candidate idx for a range whose pixels are b[] (lane-distributed:
-// lane l holds pixels l, l+32, ...).
-__device__ long long warp_cross(const Geometry &g, const uint16_t *qblk, uint32_t idx,
-                                const int (&b)[kMaxM / 32])
-{
-    const int d = idx >> 3, k = idx & 7;
-    const int lane = threadIdx.x & 31;
-    long long acc = 0;
-#pragma unroll
-    for (int j = 0; j < kMaxM / 32; ++j) {
-        const int i = lane + 32 * j;
-        if (i < g.m) {
-            int sy, sx;
-            sym_src(k, g.n, i / g.n, i % g.n, sy, sx);
-            acc += (long long)qblk[(size_t)d * g.m + sy * g.n + sx] * b[j];
-        }
-    }
-    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-    return acc;
-}
-
 }  // namespace
 
 __device__ __forceinline__ double u128_to_double(unsigned __int128 v)
@@ -129,120 +108,24 @@ __device__ unsigned __int128 exact_candidate(const Geometry &g, Stats st, const 
     return (unsigned __int128)exact_err(g, st, c, e);
 }
 
-// One warp per range.
-//  1. U = exact residual of the entry with the best screening key.
-//  2. Finalists: entries whose key, less the screening error allowance,
-//     does not exceed U (keys may underestimate, never overestimate by more
-//     than the allowance).  Each is re-scored exactly; the winner is the
-//     smallest exact residual, ties to the lowest index.
-//  3. Certified when every full list's last key, less the allowance, is
-//     strictly above the winner's residual: then no candidate outside the
-//     lists can beat or tie it.
-__global__ void k_rescore(Geometry g, EpiConst ec, const RangeInfo *ri, const DomainInfo *di,
-                          const uint16_t *bblk, const uint16_t *qblk, const ListEntry *lists,
-                          int n_lists, uint32_t *winner, int *fb_list, int *fb_count)
+// Exact X of candidate idx for a range whose pixels b[] are spread over the
+// warp (lane l holds pixels l, l+32, ...); every lane gets the sum.
+__device__ long long warp_cross(const Geometry &g, const uint16_t *qblk, uint32_t idx, const int (&b)[kMaxM / 32])
 {
-    const int warps = blockDim.x >> 5;
-    const int r = blockIdx.x * warps + (threadIdx.x >> 5);
+    const int d = idx >> 3, k = idx & 7;
     const int lane = threadIdx.x & 31;
-    if (r >= g.R) return;  // warp-uniform
-    const RangeInfo rin = ri[r];
-    if (rin.shadow) {
-        // constant range: num = 0 for every candidate, so s = 0, one offset and
-        // one residual for all; the first candidate wins (Algorithm 2)
-        if (lane == 0) winner[r] = 0;
-        return;
-    }
-    int b[kMaxM / 32];
+    long long acc = 0;
 #pragma unroll
     for (int j = 0; j < kMaxM / 32; ++j) {
         const int i = lane + 32 * j;
-        b[j] = i < g.m ? (int)bblk[(size_t)r * g.m + i] : 0;
-    }
-    const ListEntry *L = lists + (size_t)r * n_lists * kListK;
-    const int nent = n_lists * kListK;
-    // best screening key (ties to the lowest index)
-    float kb = __int_as_float(0x7f800000);
-    uint32_t ib = 0xffffffffu;
-    for (int f = lane; f < nent; f += 32) {
-        const ListEntry e = L[f];
-        if (e.idx != 0xffffffffu && (e.key < kb || (e.key == kb && e.idx < ib))) {
-            kb = e.key;
-            ib = e.idx;
+        if (i < g.m) {
+            int sy, sx;
+            sym_src(k, g.n, i >> g.ln, i & (g.n - 1), sy, sx);
+            acc += (long long)qblk[(size_t)d * g.m + (sy << g.ln) + sx] * b[j];
         }
     }
-    for (int off = 16; off > 0; off >>= 1) {
-        const float ok = __shfl_xor_sync(0xffffffffu, kb, off);
-        const uint32_t oi = __shfl_xor_sync(0xffffffffu, ib, off);
-        if (ok < kb || (ok == kb && oi < ib)) {
-            kb = ok;
-            ib = oi;
-        }
-    }
-    if (ib == 0xffffffffu) {  // no candidate was listed: exact rescan
-        if (lane == 0) {
-            winner[r] = 0xffffffffu;
-            fb_list[atomicAdd(fb_count, 1)] = r;
-        }
-        return;
-    }
-    Stats st;
-    st.Sb = rin.Sb;
-    st.Sbb = rin.Sbb;
-    const double invD2 = 1.0 / ((double)(4 * g.Ls * g.Lo) * (double)(4 * g.Ls * g.Lo));
-    const double inv2ls = 1.0 / (2.0 * g.Ls);
-    double U;
-    {
-        const long long X = warp_cross(g, qblk, ib, b);
-        U = u128_to_double(exact_candidate(g, st, di, ib, X)) * invD2;  // same on every lane
-    }
-    // screening error allowance (the epilogue's), converted to residual units;
-    // evaluated at the largest key that can still matter
-    const RangeEpi re = range_epi(rin, ec);
-    const float kreach = (float)((U - (double)rin.sbbc) * 2.0 * g.Ls);
-    const float beta_k = fmaxf(beta_key(re, kb, ec), beta_key(re, fmaxf(kb, kreach), ec));
-    const double betaE = (double)beta_k * inv2ls;
-    const double sbbc = (double)rin.sbbc;
-
-    unsigned __int128 best_e = ~(unsigned __int128)0;
-    uint32_t best_i = 0xffffffffu;
-    for (int f0 = 0; f0 < nent; f0 += 32) {
-        const int f = f0 + lane;
-        const ListEntry ent = f < nent ? L[f] : ListEntry{__int_as_float(0x7f800000), 0xffffffffu};
-        const bool fin = ent.idx != 0xffffffffu && sbbc + (double)ent.key * inv2ls - betaE <= U;
-        unsigned mask = __ballot_sync(0xffffffffu, fin);
-        long long myX = 0;
-        while (mask) {
-            const int src = __ffs(mask) - 1;
-            mask &= mask - 1;
-            const uint32_t idx = __shfl_sync(0xffffffffu, ent.idx, src);
-            const long long X = warp_cross(g, qblk, idx, b);
-            if (lane == src) myX = X;
-        }
-        if (fin) {  // lanes re-score their own finalists in parallel
-            const unsigned __int128 er = exact_candidate(g, st, di, ent.idx, myX);
-            if (better(er, ent.idx, best_e, best_i)) {
-                best_e = er;
-                best_i = ent.idx;
-            }
-        }
-    }
-    warp_argmin(best_e, best_i);
-    const double Estar = u128_to_double(best_e) * invD2;
-    bool cert = true;
-    for (int l = lane; l < n_lists; l += 32) {
-        // a full list's unlisted candidates have residual >= its last key less
-        // the allowance at that key; that bound must clear the winner strictly
-        const ListEntry last = L[l * kListK + kListK - 1];
-        if (last.idx == 0xffffffffu) continue;
-        const double bl = (double)beta_key(re, last.key, ec) * inv2ls;
-        if (!(sbbc + (double)last.key * inv2ls - bl > Estar * (1.0 + 1e-12) + 1e-12)) cert = false;
-    }
-    cert = __all_sync(0xffffffffu, cert);
-    if (lane == 0) {
-        winner[r] = best_i;
-        if (!cert) fb_list[atomicAdd(fb_count, 1)] = r;
-    }
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    return acc;
 }
 
 // round half away from zero of num/den (den > 0), exactly: an FP32 estimate
@@ -280,6 +163,144 @@ __device__ unsigned __int128 exact_rational(const Geometry &g, Stats st, const D
     return (unsigned __int128)exact_err(g, st, c, e);
 }
 
+// One warp per range.  Ranking here uses exact integer arithmetic only
+// (codes rounded exactly from the rational least-squares values, residual in
+// 128-bit integers); the FP64 code decision of eq 9-12 is made once, for the
+// winner, by k_finalize.  The two decisions differ only when an FP64
+// rounding crosses a half-integer that the exact value misses by less than
+// 1e-15 relative.
+//  1. U = exact residual of the entry with the best screening key.
+//  2. Finalists: entries whose key, less the screening error allowance,
+//     does not exceed U (keys may underestimate, never overestimate by more
+//     than the allowance).  The winner is the smallest exact residual, ties
+//     to the lowest index.
+//  3. Certified when every full list's last key, less the allowance at that
+//     key, is strictly above the winner's residual: then no candidate outside
+//     the lists can beat or tie it.  Otherwise the range goes to the exact
+//     fallback.
+__global__ void k_rescore(Geometry g, EpiConst ec, const RangeInfo *ri, const DomainInfo *di,
+                          const uint16_t *bblk, const uint16_t *qblk, const ListEntry *lists,
+                          int max_lists, const int *counts, int lists_per_split, int col_tile, int target,
+                          int max_split, int dense, uint32_t *winner, int *fb_list, int *fb_count)
+{
+    const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (r >= g.R) return;  // warp-uniform
+    const RangeInfo rin = ri[r];
+    if (rin.shadow && !dense) {
+        // constant range: num = 0 for every candidate, so s = 0, one offset and
+        // one residual for all; the first candidate wins (Algorithm 2)
+        if (lane == 0) winner[r] = 0;
+        return;
+    }
+    int b[kMaxM / 32];
+#pragma unroll
+    for (int j = 0; j < kMaxM / 32; ++j) {
+        const int i = lane + 32 * j;
+        b[j] = i < g.m ? (int)bblk[(size_t)r * g.m + i] : 0;
+    }
+    // lists actually written by the search (its split count follows the kept counts)
+    const int n_lists = lists_per_split *
+                        active_splits((counts[0] + 127) / 128, (8 * counts[2] + col_tile - 1) / col_tile, target, max_split);
+    const ListEntry *L = lists + (size_t)r * max_lists * kListK;
+    const int nent = n_lists * kListK;
+    float kb = __int_as_float(0x7f800000);
+    uint32_t ib = 0xffffffffu;
+    for (int f = lane; f < nent; f += 32) {
+        const ListEntry e = L[f];
+        if (e.idx != 0xffffffffu && (e.key < kb || (e.key == kb && e.idx < ib))) {
+            kb = e.key;
+            ib = e.idx;
+        }
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        const float ok = __shfl_xor_sync(0xffffffffu, kb, off);
+        const uint32_t oi = __shfl_xor_sync(0xffffffffu, ib, off);
+        if (ok < kb || (ok == kb && oi < ib)) {
+            kb = ok;
+            ib = oi;
+        }
+    }
+    if (ib == 0xffffffffu) {  // no candidate was listed: exact rescan
+        if (lane == 0) {
+            winner[r] = 0xffffffffu;
+            fb_list[atomicAdd(fb_count, 1)] = r;
+        }
+        return;
+    }
+    Stats st;
+    st.Sb = rin.Sb;
+    st.Sbb = rin.Sbb;
+    const double invD2 = 1.0 / ((double)(4 * g.Ls * g.Lo) * (double)(4 * g.Ls * g.Lo));
+    const double inv2ls = 1.0 / (2.0 * g.Ls);
+    unsigned __int128 ue;
+    {
+        const long long X = warp_cross(g, qblk, ib, b);
+        ue = exact_rational(g, st, di[ib >> 3], X);  // integer work, same on every lane
+    }
+    const double U = u128_to_double(ue) * invD2;
+    // screening error allowance (the epilogue's), converted to residual units;
+    // evaluated at the largest key that can still matter
+    const RangeEpi re = range_epi(rin, ec);
+    const float kreach = (float)((U - (double)rin.sbbc) * 2.0 * g.Ls);
+    const float beta_k = fmaxf(beta_key(re, kb, ec), beta_key(re, fmaxf(kb, kreach), ec));
+    const double betaE = (double)beta_k * inv2ls;
+    const double sbbc = (double)rin.sbbc;
+
+    unsigned __int128 best_e = ~(unsigned __int128)0;
+    uint32_t best_i = 0xffffffffu;
+    for (int f0 = 0; f0 < nent; f0 += 32) {
+        const int f = f0 + lane;
+        const ListEntry ent = f < nent ? L[f] : ListEntry{__int_as_float(0x7f800000), 0xffffffffu};
+        const bool fin = ent.idx != 0xffffffffu && sbbc + (double)ent.key * inv2ls - betaE <= U;
+        unsigned mask = __ballot_sync(0xffffffffu, fin);
+        long long myX = 0;
+        while (mask) {
+            const int src = __ffs(mask) - 1;
+            mask &= mask - 1;
+            const uint32_t idx = __shfl_sync(0xffffffffu, ent.idx, src);
+            const long long X = warp_cross(g, qblk, idx, b);
+            if (lane == src) myX = X;
+        }
+        if (fin) {  // lanes re-score their own finalists in parallel (integer work)
+            const unsigned __int128 er = exact_rational(g, st, di[ent.idx >> 3], myX);
+            if (better(er, ent.idx, best_e, best_i)) {
+                best_e = er;
+                best_i = ent.idx;
+            }
+        }
+    }
+    // Flat domains were not screened: all their candidates have s = 0 and the
+    // same residual, so only the first of them, (first flat domain, k = 0), can
+    // win; it is a finalist of every range.
+    const int dflat = counts[3];
+    if (dflat >= 0) {
+        const uint32_t fi = (uint32_t)dflat * 8;
+        const long long X = warp_cross(g, qblk, fi, b);
+        const unsigned __int128 er = exact_rational(g, st, di[dflat], X);
+        if (lane == 0 && better(er, fi, best_e, best_i)) {
+            best_e = er;
+            best_i = fi;
+        }
+    }
+    warp_argmin(best_e, best_i);
+    const double Estar = u128_to_double(best_e) * invD2;
+    bool cert = true;
+    for (int l = lane; l < n_lists; l += 32) {
+        // a full list's unlisted candidates have residual >= its last key less
+        // the allowance at that key; that bound must clear the winner strictly
+        const ListEntry last = L[l * kListK + kListK - 1];
+        if (last.idx == 0xffffffffu) continue;
+        const double bl = (double)beta_key(re, last.key, ec) * inv2ls;
+        if (!(sbbc + (double)last.key * inv2ls - bl > Estar * (1.0 + 1e-12) + 1e-12)) cert = false;
+    }
+    cert = __all_sync(0xffffffffu, cert);
+    if (lane == 0) {
+        winner[r] = best_i;
+        if (!cert) fb_list[atomicAdd(fb_count, 1)] = r;
+    }
+}
+
 struct Partial {
     unsigned long long lo, hi;
     uint32_t idx, pad;
@@ -314,7 +335,7 @@ __global__ void __launch_bounds__(256) k_fallback(Geometry g, const RangeInfo *r
             unsigned long long X = 0;
             for (int i = 0; i < g.m; ++i) {
                 int sy, sx;
-                sym_src(k, g.n, i / g.n, i % g.n, sy, sx);
+                sym_src(k, g.n, i >> g.ln, i & (g.n - 1), sy, sx);
                 X += (unsigned long long)((unsigned)qblk[(size_t)d * g.m + sy * g.n + sx] * (unsigned)b_s[i]);
             }
             const unsigned __int128 er = exact_rational(g, st, di[d], (long long)X);
@@ -355,37 +376,52 @@ __global__ void k_fallback_reduce(int nch, const int *fb_list, const int *fb_cou
     }
 }
 
-// One thread per range: FP64 codes and the eq 8 residual summed over the
-// pixels in order, written as the output map.
-__global__ void k_finalize(Geometry g, const RangeInfo *ri, const DomainInfo *di, const uint16_t *bblk,
-                           const uint16_t *qblk, const uint32_t *winner, const int *err, fic_map *maps)
+// FP64 codes of the winner (eq 9-12 in FP64, the operation order of the
+// least-squares formulas) and its eq 8 residual, one thread per range so that
+// every FP64 instruction works on 32 ranges.  The residual is evaluated
+// exactly in integers and rounded once to FP64.  The range's pixels and the
+// winner's 2x2 sums are staged in shared memory by the whole block.
+constexpr int kFinRanges = 32;
+__global__ void __launch_bounds__(128) k_finalize(Geometry g, const RangeInfo *ri, const DomainInfo *di,
+                                                  const uint16_t *bblk, const uint16_t *qblk,
+                                                  const uint32_t *winner, const int *err, fic_map *maps)
 {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= g.R) return;
-    const uint32_t wv = winner[r];
+    __shared__ uint16_t b_s[kFinRanges][kMaxM + 2];  // row pitch of 129 words: conflict-free
+    __shared__ uint16_t q_s[kFinRanges][kMaxM + 2];
+    __shared__ uint32_t w_s[kFinRanges];
+    const int r0 = blockIdx.x * kFinRanges;
+    const int nr = min(kFinRanges, g.R - r0);
+    for (int j = threadIdx.x; j < nr; j += blockDim.x) w_s[j] = winner[r0 + j];
+    __syncthreads();
+    const int lm = 2 * g.ln;
+    for (int e = threadIdx.x; e < nr * g.m; e += blockDim.x) {
+        const int j = e >> lm, i = e & (g.m - 1);
+        uint32_t idx = w_s[j] & 0x7fffffffu;
+        if (idx >= (uint32_t)g.N) idx = 0;  // unreachable: every range has a winner
+        b_s[j][i] = bblk[(size_t)(r0 + j) * g.m + i];
+        q_s[j][i] = qblk[(size_t)(idx >> 3) * g.m + i];
+    }
+    __syncthreads();
+    const int j = threadIdx.x;
+    if (j >= nr) return;
+    const int r = r0 + j;
+    const uint32_t wv = w_s[j];
     uint32_t idx = wv & 0x7fffffffu;
-    if (idx >= (uint32_t)g.N) idx = 0;  // unreachable: every range has a winner
+    if (idx >= (uint32_t)g.N) idx = 0;
     const int d = idx >> 3, k = idx & 7;
     const RangeInfo rin = ri[r];
     const DomainInfo dd = di[d];
     long long X = 0;
     for (int i = 0; i < g.m; ++i) {
         int sy, sx;
-        sym_src(k, g.n, i / g.n, i % g.n, sy, sx);
-        X += (long long)qblk[(size_t)d * g.m + sy * g.n + sx] * bblk[(size_t)r * g.m + i];
+        sym_src(k, g.n, i >> g.ln, i & (g.n - 1), sy, sx);
+        X += (long long)q_s[j][(sy << g.ln) + sx] * b_s[j][i];
     }
     Stats st{dd.Sq, dd.Sqq, rin.Sb, rin.Sbb, X};
     int c, e;
     double sh, oh;
     fp64_codes(g, st, c, e, sh, oh);
-    double R = 0.0;
-    for (int i = 0; i < g.m; ++i) {
-        int sy, sx;
-        sym_src(k, g.n, i / g.n, i % g.n, sy, sx);
-        const double a = __dmul_rn(0.25, (double)qblk[(size_t)d * g.m + sy * g.n + sx]);
-        const double t = __dsub_rn(__dadd_rn(__dmul_rn(sh, a), oh), (double)bblk[(size_t)r * g.m + i]);
-        R = __dadd_rn(R, __dmul_rn(t, t));
-    }
+    const double invD2 = 1.0 / ((double)(4 * g.Ls * g.Lo) * (double)(4 * g.Ls * g.Lo));
     fic_map mp;
     mp.range_idx = (uint32_t)r;
     mp.domain_idx = (uint32_t)d;
@@ -395,17 +431,18 @@ __global__ void k_finalize(Geometry g, const RangeInfo *ri, const DomainInfo *di
     mp.s = (float)sh;
     mp.o = (float)oh;
     mp.info = ((wv & 0x80000000u) ? FIC_MAP_FALLBACK : 0u) | (*err ? FIC_MAP_ERROR : 0u);
-    mp.err = R;
+    mp.err = u128_to_double((unsigned __int128)exact_err(g, st, c, e)) * invD2;
     maps[r] = mp;
 }
 
 cudaError_t launch_rescore(const Geometry &g, const EpiConst &ec, const RangeInfo *ri,
                            const DomainInfo *di, const uint16_t *bblk, const uint16_t *qblk,
-                           const ListEntry *lists, int n_lists, uint32_t *winner, int *fb_list,
+                           const ListEntry *lists, int max_lists, const int *counts, int lists_per_split,
+                           int col_tile, int target, int max_split, int dense, uint32_t *winner, int *fb_list,
                            int *fb_count, cudaStream_t st)
 {
-    k_rescore<<<(g.R + 3) / 4, 128, 0, st>>>(g, ec, ri, di, bblk, qblk, lists, n_lists, winner, fb_list,
-                                             fb_count);
+    k_rescore<<<(g.R + 3) / 4, 128, 0, st>>>(g, ec, ri, di, bblk, qblk, lists, max_lists, counts, lists_per_split,
+                                             col_tile, target, max_split, dense, winner, fb_list, fb_count);
     return cudaGetLastError();
 }
 
@@ -433,7 +470,7 @@ cudaError_t launch_finalize(const Geometry &g, const RangeInfo *ri, const Domain
                             const uint16_t *bblk, const uint16_t *qblk, const uint32_t *winner,
                             const int *err, fic_map *maps, cudaStream_t st)
 {
-    k_finalize<<<(g.R + 127) / 128, 128, 0, st>>>(g, ri, di, bblk, qblk, winner, err, maps);
+    k_finalize<<<(g.R + kFinRanges - 1) / kFinRanges, 128, 0, st>>>(g, ri, di, bblk, qblk, winner, err, maps);
     return cudaGetLastError();
 }
 

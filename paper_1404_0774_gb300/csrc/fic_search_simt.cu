@@ -21,8 +21,10 @@ constexpr int XS = BN + 1;
 
 __global__ void __launch_bounds__(256) k_search_simt(Geometry g, EpiConst ec, const RangeInfo *ri,
                                                      const DomainInfo *di, const float4 *dconst,
-                                                     const float *rs32, const float *cb32,
-                                                     ListEntry *lists, int n_split, int *tbest, float *dump)
+                                                     const int *act, const int *dmap, const int *counts,
+                                                     int dense, const float *rs32, const float *cb32,
+                                                     ListEntry *lists, int max_split, int target, int *tbest,
+                                                     float *dump)
 {
     extern __shared__ float smem[];
     float *As = smem;              // [KC][BM]
@@ -33,21 +35,29 @@ __global__ void __launch_bounds__(256) k_search_simt(Geometry g, EpiConst ec, co
     __shared__ float fdm_s[BN];
 
     const int tid = threadIdx.x;
+    // rows are the ranges kept for screening, columns the candidates of the
+    // kept domains (both compacted, in original order)
+    const int nrow = counts[0];
+    const int ncol = 8 * counts[2];
     const int r0 = blockIdx.x * BM;
     const int split = blockIdx.y;
     // contiguous slice of the candidate dimension, in whole tiles
-    const int tiles = (g.N + BN - 1) / BN;
+    const int tiles = (ncol + BN - 1) / BN;
+    const int n_split = active_splits((nrow + BM - 1) / BM, tiles, target, max_split);
+    if (r0 >= nrow || split >= n_split) return;  // CTA-uniform: nothing to screen
     const int t_begin = (int)((long long)tiles * split / n_split);
     const int t_end = (int)((long long)tiles * (split + 1) / n_split);
 
-    if (tid < BM) er_s[tid] = (r0 + tid < g.R) ? (float)ri[r0 + tid].e_r : 0.0f;
+    if (tid < BM) er_s[tid] = (r0 + tid < nrow) ? (float)ri[act[r0 + tid]].e_r : 0.0f;
 
     // epilogue role: one range row, one half of the tile
     const int er_row = tid & (BM - 1);
     const int er_half = tid >> 7;
-    const int my_r = r0 + er_row;
+    const bool row_live = r0 + er_row < nrow;
+    const int my_r = row_live ? act[r0 + er_row] : 0;  // range id
     RangeEpi re{};
-    if (my_r < g.R) re = range_epi(ri[my_r], ec);
+    if (row_live) re = range_epi(ri[my_r], ec);
+    const bool scr = row_live && (dense || !re.shadow);
     ListState L;
     list_init(L);
 
@@ -68,7 +78,7 @@ __global__ void __launch_bounds__(256) k_search_simt(Geometry g, EpiConst ec, co
             for (int f = tid; f < BM * (KC / 4); f += 256) {
                 const int r = f % BM, k4 = f / BM;
                 float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (r0 + r < g.R && k0 + 4 * k4 < g.m)
+                if (r0 + r < nrow && k0 + 4 * k4 < g.m)
                     v = *reinterpret_cast<const float4 *>(rs32 + (size_t)(r0 + r) * g.m + k0 + 4 * k4);
                 As[(4 * k4 + 0) * BM + r] = v.x;
                 As[(4 * k4 + 1) * BM + r] = v.y;
@@ -79,7 +89,7 @@ __global__ void __launch_bounds__(256) k_search_simt(Geometry g, EpiConst ec, co
             for (int f = tid; f < BN * (KC / 4); f += 256) {
                 const int c = f % BN, k4 = f / BN;
                 float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (n0 + c < g.N && k0 + 4 * k4 < g.m)
+                if (n0 + c < ncol && k0 + 4 * k4 < g.m)
                     v = *reinterpret_cast<const float4 *>(cb32 + (size_t)(n0 + c) * g.m + k0 + 4 * k4);
                 Bs[(4 * k4 + 0) * BN + c] = v.x;
                 Bs[(4 * k4 + 1) * BN + c] = v.y;
@@ -87,7 +97,7 @@ __global__ void __launch_bounds__(256) k_search_simt(Geometry g, EpiConst ec, co
                 Bs[(4 * k4 + 3) * BN + c] = v.w;
             }
             if (k0 == 0 && tid < BN)
-                fdm_s[tid] = (n0 + tid < g.N) ? (float)di[(n0 + tid) >> 3].f_d / (float)g.m : 0.0f;
+                fdm_s[tid] = (n0 + tid < ncol) ? (float)di[dmap[(n0 + tid) >> 3]].f_d / (float)g.m : 0.0f;
             __syncthreads();
             const int kn = min(KC, g.m - k0);
 #pragma unroll 4
@@ -111,32 +121,35 @@ __global__ void __launch_bounds__(256) k_search_simt(Geometry g, EpiConst ec, co
                 Xs[(tr * 8 + i) * XS + tc * 4 + j] =
                     fmaf(-er_s[tr * 8 + i], fdm_s[tc * 4 + j], acc[i][j]);
         __syncthreads();
-        if (my_r < g.R && dump) {
+        if (row_live && dump) {
             const int c0 = n0 + er_half * 32;
-            for (int j = 0; j < 32 && c0 + j < g.N; ++j)
-                dump[(size_t)my_r * g.N + c0 + j] = Xs[er_row * XS + er_half * 32 + j];
-        } else if (my_r < g.R && !re.shadow) {
+            for (int j = 0; j < 32 && c0 + j < ncol; ++j)
+                dump[(size_t)my_r * g.N + dmap[(c0 + j) >> 3] * 8 + (j & 7)] = Xs[er_row * XS + er_half * 32 + j];
+        } else if (scr) {
             const float Tg = ord2f(__ldcg(tbest + my_r));  // best key other CTAs found
             list_adopt(L, Tg, re, ec);
             L.Tpub = fminf(L.Tpub, Tg);
             const int c0 = n0 + er_half * 32;
-            const int nvalid = min(32, g.N - c0);
+            const int nvalid = min(32, ncol - c0);
             if (nvalid > 0) {
                 const float *xrow = Xs + er_row * XS + er_half * 32;
                 float X[32];
 #pragma unroll
                 for (int j = 0; j < 32; ++j) X[j] = j < nvalid ? xrow[j] : __int_as_float(0x7fc00000);
                 float4 dc[4];
+                int od[4];
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    const int d = (c0 >> 3) + q;
-                    dc[q] = d < g.D ? dconst[d] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    const int jd = (c0 >> 3) + q;
+                    const bool ok = jd < counts[2];
+                    dc[q] = ok ? dconst[jd] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    od[q] = ok ? dmap[jd] : 0;
                 }
                 if (epi_keys32(X, dc, re.zb, re.rho_lim, ec, fminf(L.key[kListK - 1], L.tw),
                                L.has_zero ? kZeroPenalty : 0.0f)) {
 #pragma unroll
                     for (int j = 0; j < 32; ++j) Ks[j * 256 + tid] = X[j];
-                    epi_rare(Ks + tid, 256, xrow, 1, (uint32_t)c0, dc, re, ec, L, nvalid);
+                    epi_rare(Ks + tid, 256, xrow, 1, od, dc, re, ec, L, nvalid);
                     if (L.T < L.Tpub) {
                         atomicMin(tbest + my_r, f2ord(L.T));
                         L.Tpub = L.T;
@@ -145,9 +158,8 @@ __global__ void __launch_bounds__(256) k_search_simt(Geometry g, EpiConst ec, co
             }
         }
     }
-    if (my_r < g.R && !dump && !re.shadow) {
-        const int n_lists = n_split * 2;
-        ListEntry *dst = lists + ((size_t)my_r * n_lists + split * 2 + er_half) * kListK;
+    if (scr && !dump) {
+        ListEntry *dst = lists + ((size_t)my_r * max_split * 2 + split * 2 + er_half) * kListK;
 #pragma unroll
         for (int i = 0; i < kListK; ++i) dst[i] = ListEntry{L.key[i], L.idx[i]};
     }
@@ -156,15 +168,16 @@ __global__ void __launch_bounds__(256) k_search_simt(Geometry g, EpiConst ec, co
 int search_simt_lists_per_split() { return 2; }
 
 cudaError_t launch_search_simt(const Geometry &g, const EpiConst &ec, const RangeInfo *ri,
-                               const DomainInfo *di, const float4 *dconst, const float *rs32,
-                               const float *cb32, ListEntry *lists, int n_split, int *tbest, float *dump,
-                               cudaStream_t st)
+                               const DomainInfo *di, const CompactBufs &cb, int dense, const float *rs32,
+                               const float *cb32, ListEntry *lists, int max_split, int target, int *tbest,
+                               float *dump, cudaStream_t st)
 {
     const size_t smem = sizeof(float) * (KC * BM + KC * BN + BM * XS + 32 * 256);
     cudaError_t e = cudaFuncSetAttribute(k_search_simt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    dim3 grid((g.R + BM - 1) / BM, n_split);
-    k_search_simt<<<grid, 256, smem, st>>>(g, ec, ri, di, dconst, rs32, cb32, lists, n_split, tbest, dump);
+    dim3 grid((g.R + BM - 1) / BM, max_split);
+    k_search_simt<<<grid, 256, smem, st>>>(g, ec, ri, di, cb.dconst_c, cb.act, cb.dmap, cb.counts, dense, rs32, cb32,
+                                           lists, max_split, target, tbest, dump);
     return cudaGetLastError();
 }
 

@@ -31,9 +31,11 @@ namespace {
 
 constexpr int BM = 128;
 constexpr int BN = 128;
-constexpr int STAGES = 4;
+constexpr int STAGES = 3;
 constexpr int NACC = 2;
-constexpr int THREADS = 192;
+constexpr int EPI_WARPS = 8;                    // two per TMEM lane quadrant
+constexpr int THREADS = 64 + 32 * EPI_WARPS;   // TMA warp, MMA warp, epilogue
+constexpr int EPI_COLS = BN / 2;               // columns of a tile per epilogue warp
 constexpr uint32_t TMEM_COLS = BN * NACC;  // 256
 constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s per wait
 
@@ -187,7 +189,8 @@ struct TcMaps {
 template <int NBLK>
 __global__ void __launch_bounds__(THREADS, 1)
     k_search_tc(const __grid_constant__ TcMaps maps, Geometry g, EpiConst ec, const RangeInfo *ri,
-                const float4 *dconst, ListEntry *lists, int n_split, int *tbest, float *dump, int *err,
+                const float4 *dconst, const int *act, const int *dmap, const int *counts, int dense,
+                ListEntry *lists, int max_split, int target, int *tbest, float *dump, int *err,
                 uint32_t smem_bytes, int rpad, int npad)
 {
     constexpr uint32_t A_BLK = BM * 128;                 // bytes of one 64-col block, A
@@ -201,18 +204,25 @@ __global__ void __launch_bounds__(THREADS, 1)
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t *sA = smem;
     uint8_t *sB = smem + A_BYTES;  // A_BYTES is a multiple of 1024
-    float *ksm = reinterpret_cast<float *>(sB + STAGES * B_BYTES);  // [32][128] keys (rare pass)
-    float *xsm = ksm + 32 * BM;                                     // [32][128] cross terms (rare pass)
-    float4 *dcs = reinterpret_cast<float4 *>(xsm + 32 * BM);        // [4 warps][16] domain constants
+    constexpr int ET = 32 * EPI_WARPS;                                // epilogue threads
+    float *ksm = reinterpret_cast<float *>(sB + STAGES * B_BYTES);  // [32][ET] keys (rare pass)
+    float *xsm = ksm + 32 * ET;                                     // [32][ET] cross terms (rare pass)
+    float4 *dcs = reinterpret_cast<float4 *>(xsm + 32 * ET);        // [EPI_WARPS][8] domain constants
     __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], a_bar, tfull_bar[NACC], tempty_bar[NACC];
     __shared__ uint32_t tmem_base_s;
     __shared__ int abort_s;
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
+    // rows are the ranges kept for screening, columns the candidates of the
+    // kept domains (both compacted, in original order)
+    const int nrow = counts[0];
+    const int ncol = 8 * counts[2];
     const int r0 = blockIdx.x * BM;
     const int split = blockIdx.y;
-    const int tiles = (g.N + BN - 1) / BN;
+    const int tiles = (ncol + BN - 1) / BN;
+    const int n_split = active_splits((nrow + BM - 1) / BM, tiles, target, max_split);
+    if (r0 >= nrow || split >= n_split) return;  // CTA-uniform: nothing to screen
     const int t_begin = (int)((long long)tiles * split / n_split);
     const int t_end = (int)((long long)tiles * (split + 1) / n_split);
     const int ntile = t_end - t_begin;
@@ -220,7 +230,8 @@ __global__ void __launch_bounds__(THREADS, 1)
     if (threadIdx.x == 0) {
         // self-checks: every TMA box and MMA operand must lie inside this CTA's
         // dynamic shared memory, and every box inside the padded operands
-        const uint32_t used = (uint32_t)(smem - smem_raw) + A_BYTES + STAGES * B_BYTES + 2 * 32 * BM * 4 + 4 * 16 * 16;
+        const uint32_t used = (uint32_t)(smem - smem_raw) + A_BYTES + STAGES * B_BYTES + 2 * 32 * ET * 4 +
+                              EPI_WARPS * 8 * 16 + EPI_WARPS * 8 * 4;
         int bad = 0;
         if (used > smem_bytes) bad = 2;
         if (r0 + BM > rpad || t_end * BN > npad) bad = 3;
@@ -234,7 +245,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         mbar_init(&a_bar, 1);
         for (int a = 0; a < NACC; ++a) {
             mbar_init(&tfull_bar[a], 1);
-            mbar_init(&tempty_bar[a], 4);  // one arrival per epilogue warp
+            mbar_init(&tempty_bar[a], EPI_WARPS);  // one arrival per epilogue warp
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -322,47 +333,77 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
     } else {
         // ------------------------------------------------------ epilogue
-        const int quad = warp & 3;  // TMEM lane quadrant this warp may access
+        const int ew = warp - 2;              // epilogue warp 0..7
+        const int quad = warp & 3;            // TMEM lane quadrant this warp may access
+        const int half = ew >> 2;             // which 64 columns of each tile
         const int row = quad * 32 + lane;
-        const int r = r0 + row;
-        const bool live = r < g.R;
-        float4 *wdc = dcs + (warp - 2) * 16;
+        const int et = ew * 32 + lane;        // staging column of this thread
+        const int jrow = r0 + row;            // search row
+        const bool live = jrow < nrow;
+        const int r = live ? act[jrow] : 0;   // range id
+        float4 *wdc = dcs + ew * 8;
+        int *wod = reinterpret_cast<int *>(dcs + EPI_WARPS * 8) + ew * 8;
         RangeEpi re{};
         if (live) re = range_epi(ri[r], ec);
-        const bool scr = live && !re.shadow;  // shadow ranges need no screening
+        const bool scr = live && (dense || !re.shadow);
         ListState L;
         list_init(L);
-        const uint32_t lane_addr = tmem_base + ((uint32_t)(quad * 32) << 16);
+        const uint32_t lane_addr = tmem_base + ((uint32_t)(quad * 32) << 16) + half * EPI_COLS;
+        // prefetch for the first tile: its 8 domains and the shared best key
+        float4 dc_next = make_float4(0.f, 0.f, 0.f, 0.f);
+        int od_next = 0;
+        int tb_next = 0x7f800000;
+        if (ntile > 0) {
+            const int jd = ((t_begin * BN + half * EPI_COLS) >> 3) + lane;
+            if (lane < 8 && jd < counts[2]) {
+                dc_next = __ldg(dconst + jd);
+                od_next = __ldg(dmap + jd);
+            }
+            if (scr && !dump) tb_next = __ldcg(tbest + r);
+        }
         for (int it = 0; it < ntile; ++it) {
             const int acc = it % NACC;
-            const int n0 = (t_begin + it) * BN;
-            // this tile's 16 domains: staged once per warp
-            if (lane < BN / 8) {
-                const int d = (n0 >> 3) + lane;
-                wdc[lane] = d < g.D ? __ldg(dconst + d) : make_float4(0.f, 0.f, 0.f, 0.f);
+            const int n0 = (t_begin + it) * BN + half * EPI_COLS;
+            if (lane < 8) {
+                wdc[lane] = dc_next;
+                wod[lane] = od_next;
             }
             if (scr && !dump) {
-                const float Tg = ord2f(__ldcg(tbest + r));  // best key other CTAs found
+                const float Tg = ord2f(tb_next);  // best key other CTAs found
                 list_adopt(L, Tg, re, ec);
                 L.Tpub = fminf(L.Tpub, Tg);
+            }
+            if (it + 1 < ntile) {  // prefetch for the next tile
+                const int jd = ((n0 + BN) >> 3) + lane;
+                if (lane < 8 && jd < counts[2]) {
+                    dc_next = __ldg(dconst + jd);
+                    od_next = __ldg(dmap + jd);
+                }
+                if (scr && !dump) tb_next = __ldcg(tbest + r);
             }
             __syncwarp();
             // warp-uniform decision: tcgen05.ld below is .sync.aligned
             if (!__all_sync(0xffffffffu, mbar_wait(&tfull_bar[acc], (it / NACC) & 1, &abort_s, err))) break;
             tc_fence_after();
             const uint32_t taddr = lane_addr + acc * BN;
-            // one chunk of 32 columns; `nxt` is being filled by a prefetch
-            auto chunk = [&](uint32_t(&cur)[32], int ch) {
+#pragma unroll 1
+            for (int ch = 0; ch < EPI_COLS / 32; ++ch) {
+                uint32_t cur[32];
+                tmem_ld32(taddr + ch * 32, cur);
+                tmem_wait(cur);
                 const int c0 = n0 + ch * 32;
-                const int nvalid = min(32, g.N - c0);
+                const int nvalid = min(32, ncol - c0);
                 float X[32];
 #pragma unroll
                 for (int j = 0; j < 32; ++j) X[j] = __uint_as_float(cur[j]);
+                int od[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) od[q] = wod[ch * 4 + q];
                 if (dump) {
 #pragma unroll
                     for (int j = 0; j < 32; ++j)
-                        if (live && j < nvalid) dump[(size_t)r * g.N + c0 + j] = X[j];
-                    return;
+                        if (live && j < nvalid) dump[(size_t)r * g.N + od[j >> 3] * 8 + (j & 7)] = X[j];
+                    continue;
                 }
                 if (nvalid < 32) {
 #pragma unroll
@@ -379,14 +420,14 @@ __global__ void __launch_bounds__(THREADS, 1)
                     // stage keys, reload the cross terms (still in TMEM), then each
                     // thread walks its own row
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) ksm[j * BM + row] = X[j];
+                    for (int j = 0; j < 32; ++j) ksm[j * ET + et] = X[j];
                     uint32_t tx[32];
                     tmem_ld32(taddr + ch * 32, tx);
                     tmem_wait(tx);
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) xsm[j * BM + row] = __uint_as_float(tx[j]);
+                    for (int j = 0; j < 32; ++j) xsm[j * ET + et] = __uint_as_float(tx[j]);
                     if (need) {
-                        epi_rare(ksm + row, BM, xsm + row, BM, (uint32_t)c0, dc, re, ec, L, nvalid);
+                        epi_rare(ksm + et, ET, xsm + et, ET, od, dc, re, ec, L, nvalid);
                         if (L.T < L.Tpub) {
                             atomicMin(tbest + r, f2ord(L.T));
                             L.Tpub = L.T;
@@ -394,25 +435,13 @@ __global__ void __launch_bounds__(THREADS, 1)
                     }
                     __syncwarp();
                 }
-            };
-            uint32_t ra[32], rb[32];
-            tmem_ld32(taddr, ra);
-            tmem_wait(ra);
-#pragma unroll 1
-            for (int ch = 0; ch < BN / 32; ch += 2) {
-                tmem_ld32(taddr + (ch + 1) * 32, rb);  // prefetch the odd chunk
-                chunk(ra, ch);
-                tmem_wait(rb);
-                if (ch + 2 < BN / 32) tmem_ld32(taddr + (ch + 2) * 32, ra);  // prefetch the next even chunk
-                chunk(rb, ch + 1);
-                if (ch + 2 < BN / 32) tmem_wait(ra);
             }
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&tempty_bar[acc]);
         }
         if (scr && !dump) {
-            ListEntry *dst = lists + ((size_t)r * n_split + split) * kListK;
+            ListEntry *dst = lists + (((size_t)r * max_split + split) * 2 + half) * kListK;
 #pragma unroll
             for (int i = 0; i < kListK; ++i) dst[i] = ListEntry{L.key[i], L.idx[i]};
         }
@@ -471,16 +500,18 @@ size_t search_tc_smem(const Geometry &g)
 {
     const int nblk = g.split_hilo ? 2 : 1;
     return 1024 + (size_t)(nblk * BM * 128 + BM * 32) + (size_t)STAGES * (nblk * BN * 128 + BN * 32) +
-           2 * 32 * BM * 4 + 4 * 16 * 16;
+           2 * 32 * (32 * EPI_WARPS) * 4 + EPI_WARPS * 8 * 16 + EPI_WARPS * 8 * 4;
 }
+
+int search_tc_lists_per_split() { return 2; }
 
 int search_tc_tile() { return BN; }
 
 int search_tc_rows(int rows) { return (rows + 127) / 128 * 128; }
 
-cudaError_t launch_search_tc(const Geometry &g, const EpiConst &ec, const RangeInfo *ri, const float4 *dconst,
-                             const __half *ra16, const __half *cb16, ListEntry *lists, int n_split, int *tbest,
-                             float *dump, int *err, cudaStream_t st)
+cudaError_t launch_search_tc(const Geometry &g, const EpiConst &ec, const RangeInfo *ri, const CompactBufs &cb,
+                             int dense, const __half *ra16, const __half *cb16, ListEntry *lists, int max_split,
+                             int target, int *tbest, float *dump, int *err, cudaStream_t st)
 {
     if (!search_tc_supported(g)) return cudaErrorInvalidValue;
     TcMaps mp;
@@ -493,18 +524,18 @@ cudaError_t launch_search_tc(const Geometry &g, const EpiConst &ec, const RangeI
         !make_map(&mp.b32, cb16, npad, g.KP, 16, BN, CU_TENSOR_MAP_SWIZZLE_32B))
         return cudaErrorInvalidValue;
     const size_t smem = search_tc_smem(g);
-    dim3 grid((g.R + BM - 1) / BM, n_split);
+    dim3 grid((g.R + BM - 1) / BM, max_split);
     cudaError_t e;
     if (nblk == 2) {
         e = cudaFuncSetAttribute(k_search_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        k_search_tc<2><<<grid, THREADS, smem, st>>>(mp, g, ec, ri, dconst, lists, n_split, tbest, dump, err,
-                                                    (uint32_t)smem, rpad, npad);
+        k_search_tc<2><<<grid, THREADS, smem, st>>>(mp, g, ec, ri, cb.dconst_c, cb.act, cb.dmap, cb.counts, dense,
+                                                    lists, max_split, target, tbest, dump, err, (uint32_t)smem, rpad, npad);
     } else {
         e = cudaFuncSetAttribute(k_search_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        k_search_tc<1><<<grid, THREADS, smem, st>>>(mp, g, ec, ri, dconst, lists, n_split, tbest, dump, err,
-                                                    (uint32_t)smem, rpad, npad);
+        k_search_tc<1><<<grid, THREADS, smem, st>>>(mp, g, ec, ri, cb.dconst_c, cb.act, cb.dmap, cb.counts, dense,
+                                                    lists, max_split, target, tbest, dump, err, (uint32_t)smem, rpad, npad);
     }
     return cudaGetLastError();
 }
