@@ -125,8 +125,9 @@ int fic_encode_workspace_size(int w, int h, const fic_params *p, size_t *bytes);
  *              maps_cap >= number of ranges.
  *   n_maps     output (host), number of maps written; may be NULL.
  *   workspace  device buffer of at least fic_encode_workspace_size() bytes,
- *              or NULL to let the library allocate (cudaMallocAsync) and free
- *              it on `stream`.
+ *              256-byte aligned (FIC_ERR_BAD_ARG otherwise; cudaMalloc and
+ *              torch allocations are), or NULL to let the library allocate
+ *              (cudaMallocAsync) and free it on `stream`.
  * Every map is the exact minimiser of eq 8 over all 8*D candidates with the
  * lowest-index tie-break; codes are decided in FP64 as described above.
  */

@@ -113,6 +113,7 @@ EpiConst make_epi(const Geometry &g)
     ec.inv4ls = (float)(0.25 / g.Ls);
     ec.invm = (float)(1.0 / g.m);
     ec.pmax = (float)g.P - 0.5f;
+    ec.near_slack = (float)((32.0 * g.Ls * g.Ls + 16.0 * g.Ls) * 5.9604644775390625e-08);  // 2^-24
     return ec;
 }
 
@@ -301,6 +302,7 @@ int run_encode(const void *img, int w, int h, int pitch_px, const fic_params *p,
     bool owned = false;
     if (ws) {
         if (workspace_bytes < L.total) return FIC_ERR_CAPACITY;
+        if (reinterpret_cast<uintptr_t>(ws) & (kAlign - 1)) return FIC_ERR_BAD_ARG;
     } else {
         if (cudaMallocAsync(reinterpret_cast<void **>(&ws), L.total, st) != cudaSuccess) {
             cudaGetLastError();
@@ -372,9 +374,9 @@ int run_encode(const void *img, int w, int h, int pitch_px, const fic_params *p,
                                         st));
         FIC_MARK(2);
         if (!dump) {
-            FIC_CUDA(launch_rescore(gd, ec, ri, di, bblk, qblk, lists, n_lists, cbuf.counts, lists_per_split(search),
-                                    search == FIC_SEARCH_TC ? search_tc_tile() : 64, target, n_split, dense, winner,
-                                    fb_list, fb_count, st));
+            FIC_CUDA(launch_rescore(gd, ec, ri, di, bblk, qblk, lists, n_lists, cbuf.counts, cbuf.act, cbuf.rkeep,
+                                    lists_per_split(search), search == FIC_SEARCH_TC ? search_tc_tile() : 64, target,
+                                    n_split, sm_count(), winner, fb_list, fb_count, st));
             FIC_MARK(3);
             FIC_CUDA(launch_fallback(gd, ri, di, bblk, qblk, fb_list, fb_count, partial, winner, st));
             FIC_MARK(4);
@@ -465,6 +467,7 @@ int fic_decode(const fic_map *maps, int n_maps, int w, int h, const fic_params *
     }
     if (ws) {
         if (workspace_bytes < total) return FIC_ERR_CAPACITY;
+        if (reinterpret_cast<uintptr_t>(ws) & (kAlign - 1)) return FIC_ERR_BAD_ARG;
     } else {
         if (cudaMallocAsync(reinterpret_cast<void **>(&ws), total, st) != cudaSuccess) {
             cudaGetLastError();

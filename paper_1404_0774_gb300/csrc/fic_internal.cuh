@@ -83,6 +83,7 @@ struct EpiConst {
     float beta_o;       // key error from an o code decided next to its rounding boundary
     float sqrtm4;       // sqrt(m)/4
     float inv4ls, invm, pmax;  // 1/(4*Ls), 1/m, P (offset clamp detection)
+    float near_slack;   // kappa * near_slack bounds how far below c*y the key of the other code can fall
 };
 
 // Per-thread constants of the range the thread screens.
@@ -237,20 +238,30 @@ __device__ __forceinline__ f32x2_t mul2(f32x2_t a, f32x2_t b)
     return d;
 }
 
-// Main pass over 32 consecutive candidates (4 domains x 8 symmetries):
-// X[] (cross terms) is overwritten by the keys.  Branch-free, two candidates
-// (same domain, so same column constants) per packed instruction; the keys
-// are bit-identical to epi_code/epi_key.  Returns whether this thread needs
-// the rare pass: a key below `thr`, or a code decided next to its rounding
-// boundary.  Lanes beyond the ragged end carry X = NaN (their keys are NaN
-// and compare false everywhere).  zpen: added to the key of s-code-0
-// candidates (their residual is one value per range; once the list holds
-// one, the others need never be looked at).
-__device__ __forceinline__ bool epi_keys32(float (&X)[32], const float4 (&dc)[4], float zb, float rho_lim,
-                                           const EpiConst &ec, float thr, float zpen)
+// Main pass over 32 consecutive candidates (4 domains x 8 symmetries) with
+// cross terms X[].  Branch-free, two candidates (same domain, so same column
+// constants) per packed instruction; the keys are bit-identical to
+// epi_code/epi_key.  Returns the mask of candidates whose key is below `thr`
+// (bit j for X[j]): the ones a rare pass must visit.  A code decided next to its rounding
+// boundary (|rho| > rho_lim) may be the neighbouring one in FP64; its key is
+// then replaced by a lower bound of both codes' keys (see below), so that
+// such a candidate costs a rare pass only when it could enter the list.
+// Lanes beyond the ragged end carry X = NaN (their keys are NaN and compare
+// false everywhere).  zpen: added to the key of s-code-0 candidates (their
+// residual is one value per range; once the list holds one, the others need
+// never be looked at).
+//
+// Lower bound for a near-boundary candidate.  With r = Xt/(2*kappa) (the
+// unrounded Ls*s) the s part of the key is f(c) = c*(c*kappa - Xt) =
+// kappa*((c - r)^2 - r^2), so for the neighbour c2 = c + sign(rho):
+// f(c2) - f(c) = kappa*(1 - 2|rho|) >= -2*kappa*e, e the FP32 error of rho
+// (at most 7*Ls*2^-24).  The FP32 evaluations of c*y and c2*y2 each carry at
+// most 8*Ls^2*kappa*2^-24, and lambda*w^2 >= 0, so both keys are at least
+// c*y - kappa*near_slack with near_slack = (32*Ls^2 + 16*Ls)*2^-24.
+__device__ __forceinline__ uint32_t epi_keys32(const float (&X)[32], const float4 (&dc)[4], float zb, float rho_lim,
+                                               const EpiConst &ec, float thr, float zpen)
 {
-    float kmin = __int_as_float(0x7f800000);
-    float rmax = 0.0f;
+    uint32_t mask = 0;
     const f32x2_t two_ls = pk2(ec.two_ls, ec.two_ls), mls = pk2(-ec.ls, -ec.ls);
     const f32x2_t mag = pk2(kMagic, kMagic), zb2 = pk2(zb, zb), invg = pk2(ec.invG, ec.invG);
     const f32x2_t mg = pk2(-ec.G, -ec.G), lam = pk2(ec.lambda, ec.lambda), zp = pk2(zpen, zpen);
@@ -258,6 +269,8 @@ __device__ __forceinline__ bool epi_keys32(float (&X)[32], const float4 (&dc)[4]
     for (int q = 0; q < 4; ++q) {
         const float4 c4 = dc[q];
         const f32x2_t msqz = pk2(-c4.y, -c4.y), kap = pk2(c4.z, c4.z);
+        const float sl = -c4.z * ec.near_slack;
+        const f32x2_t msl = pk2(sl, sl);
 #pragma unroll
         for (int h = 0; h < 4; ++h) {
             const int j = q * 8 + 2 * h;
@@ -270,8 +283,6 @@ __device__ __forceinline__ bool epi_keys32(float (&X)[32], const float4 (&dc)[4]
             float c0, c1, p0, p1;
             upk2(c, c0, c1);
             upk2(rho, p0, p1);
-            rmax = fmaxf(rmax, fabsf(p0));
-            rmax = fmaxf(rmax, fabsf(p1));
             const float zero0 = __saturatef(fmaf(c0, -c0, 1.0f));  // 1 for c = 0, else 0
             const float zero1 = __saturatef(fmaf(c1, -c1, 1.0f));
             const f32x2_t z = fma2(c, msqz, zb2);
@@ -281,15 +292,17 @@ __device__ __forceinline__ bool epi_keys32(float (&X)[32], const float4 (&dc)[4]
             const f32x2_t cy = mul2(c, y);
             f32x2_t k = fma2(mul2(wv, lam), wv, cy);
             k = fma2(pk2(zero0, zero1), zp, k);
-            float k0, k1;
+            const f32x2_t lo = add2(cy, msl);
+            float k0, k1, l0, l1;
             upk2(k, k0, k1);
-            X[j] = k0;
-            X[j + 1] = k1;
-            kmin = fminf(kmin, k0);
-            kmin = fminf(kmin, k1);
+            upk2(lo, l0, l1);
+            k0 = fabsf(p0) > rho_lim ? l0 : k0;
+            k1 = fabsf(p1) > rho_lim ? l1 : k1;
+            mask |= (k0 < thr ? 1u : 0u) << j;
+            mask |= (k1 < thr ? 1u : 0u) << (j + 1);
         }
     }
-    return kmin < thr || rmax > rho_lim;
+    return mask;
 }
 
 __device__ __forceinline__ float4 pick4(const float4 (&dc)[4], int q)
@@ -297,25 +310,30 @@ __device__ __forceinline__ float4 pick4(const float4 (&dc)[4], int q)
     return q == 0 ? dc[0] : (q == 1 ? dc[1] : (q == 2 ? dc[2] : dc[3]));
 }
 
-// Rare pass for one thread: keys and cross terms staged in shared memory at
-// krow[j*stride], xrow[j*xstride].  Handles codes next to a rounding boundary
-// (the key becomes the smaller of the two neighbouring codes' keys: a lower
-// bound of the residual FP64 decides) and list insertion with s-code-0
-// de-duplication (all such candidates of a range have one residual).
-// od[q]: original index of the chunk's q-th domain (the search may skip flat
-// domains, so consecutive columns need not be consecutive domains).
-static __device__ __forceinline__ void epi_rare(const float *krow, int stride, const float *xrow, int xstride,
-                                      const int (&od)[4], const float4 (&dc)[4], const RangeEpi &re,
-                                      const EpiConst &ec, ListState &L, int nvalid)
+// Rare pass for one thread: cross terms staged in shared memory at
+// xrow[j*stride]; only the candidates of `mask` (the main pass's keys below
+// its threshold, a superset of what can still enter the list) are visited,
+// their keys recomputed (bit-identical to the main pass).  Handles codes next
+// to a rounding boundary (the key becomes the smaller of the two neighbouring
+// codes' keys: a lower bound of the residual FP64 decides) and list insertion
+// with s-code-0 de-duplication (all such candidates of a range have one
+// residual).  od[q]: original index of the chunk's q-th domain (the search
+// may skip flat domains, so consecutive columns need not be consecutive
+// domains).
+static __device__ __forceinline__ void epi_rare(const float *xrow, int stride, const int (&od)[4],
+                                                const float4 (&dc)[4], const RangeEpi &re, const EpiConst &ec,
+                                                ListState &L, uint32_t mask)
 {
 #pragma unroll 1
-    for (int j = 0; j < nvalid; ++j) {
-        float k = krow[j * stride];
-        const float x = xrow[j * xstride];
+    while (mask) {
+        const int j = __ffs(mask) - 1;
+        mask &= mask - 1;
+        const float x = xrow[j * stride];
         const float4 c4 = pick4(dc, j >> 3);
         float rho;
         const float c = epi_code(x, c4.x, ec, rho);
         const bool near = fabsf(rho) > re.rho_lim;
+        float k = epi_key(x, c, re.zb, c4, ec);
         if (near) {
             const float c2 = fminf(fmaxf(c + (rho > 0.0f ? 1.0f : -1.0f), -ec.ls), ec.ls);
             k = fminf(k, epi_key(x, c2, re.zb, c4, ec));
@@ -350,6 +368,26 @@ __device__ __forceinline__ void sym_src(int k, int n, int y, int x, int &sy, int
     case 6: sy = x; sx = y; break;
     default: sy = n - 1 - x; sx = n - 1 - y; break;
     }
+}
+
+// The same map without branches, for threads whose symmetries differ: with
+// (u, v) = (x, y) when S_k swaps the axes, else (y, x), the source pixel is
+// (u ^ my, v ^ mx), where my, mx are 0 or n-1 (n a power of two, so n-1-u =
+// u ^ (n-1)).  Bit k of 0xCA: axes swapped; of 0xA6: rows flipped; of 0x9C:
+// columns flipped (k numbered as in sym_src).
+struct SymFlags {
+    int swap, my, mx;
+};
+
+__device__ __forceinline__ SymFlags sym_flags(int k, int n)
+{
+    return SymFlags{(0xCA >> k) & 1, ((0xA6 >> k) & 1) * (n - 1), ((0x9C >> k) & 1) * (n - 1)};
+}
+
+__device__ __forceinline__ int sym_src_index(const SymFlags &f, int ln, int y, int x)
+{
+    const int u = f.swap ? x : y, v = f.swap ? y : x;
+    return ((u ^ f.my) << ln) + (v ^ f.mx);
 }
 
 __device__ __forceinline__ int load_px(const void *img, int B, size_t off)
@@ -398,9 +436,9 @@ cudaError_t launch_search_tc(const Geometry &g, const EpiConst &ec, const RangeI
 int search_simt_lists_per_split();
 cudaError_t launch_rescore(const Geometry &g, const EpiConst &ec, const RangeInfo *ri,
                            const DomainInfo *di, const uint16_t *bblk, const uint16_t *qblk,
-                           const ListEntry *lists, int max_lists, const int *counts, int lists_per_split,
-                           int col_tile, int target, int max_split, int dense, uint32_t *winner, int *fb_list,
-                           int *fb_count, cudaStream_t st);
+                           const ListEntry *lists, int max_lists, const int *counts, const int *act,
+                           const int *rkeep, int lists_per_split, int col_tile, int target, int max_split, int n_sm,
+                           uint32_t *winner, int *fb_list, int *fb_count, cudaStream_t st);
 size_t fallback_partial_bytes(const Geometry &g);
 cudaError_t launch_fallback(const Geometry &g, const RangeInfo *ri, const DomainInfo *di,
                             const uint16_t *bblk, const uint16_t *qblk, const int *fb_list,

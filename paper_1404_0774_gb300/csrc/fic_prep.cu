@@ -16,12 +16,11 @@ __device__ __forceinline__ long long warp_sum_ll(long long v)
     return v;
 }
 
-// One warp per range (lanes over pixels): statistics, centre, operand rows.
-__global__ void k_range_prep(Geometry g, EpiConst ec, const void *img, RangeInfo *ri, uint16_t *bblk, int *tbest)
+// One warp per range (lanes over pixels): statistics, centre, allowances,
+// and the keep flag (every range but shadow ranges, or all when dense).
+__device__ __forceinline__ void range_stats(const Geometry &g, const EpiConst &ec, const void *img, int dense, int r,
+                                            int lane, RangeInfo *ri, uint16_t *bblk, int *tbest, int *rkeep)
 {
-    const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
-    if (r >= g.R) return;  // warp-uniform
     const int ry = (r / g.nx) * g.n, rx = (r % g.nx) * g.n;
     constexpr int PPL = kMaxM / 32;  // pixels per lane, upper bound
     int bv[PPL];
@@ -100,137 +99,134 @@ __global__ void k_range_prep(Geometry g, EpiConst ec, const void *img, RangeInfo
     info.pad = 0;
     ri[r] = info;
     tbest[r] = 0x7f800000;  // +inf in the ordered-integer encoding of floats
+    rkeep[r] = dense || !info.shadow;
 }
 
-// One block of m threads per domain.
-__global__ void k_domain_prep(Geometry g, const void *img, DomainInfo *di, float4 *dconst, uint16_t *qblk)
+
+// One warp per domain (lanes over the contracted pixels): the 2x2 sums q
+// (tau as an integer sum, the mean being q/4), Sq, Sqq, centre, the epilogue
+// column constants, and the keep flag (every domain but flat ones, den = 0,
+// or all when dense).
+__device__ __forceinline__ void domain_stats(const Geometry &g, const void *img, int dense, int d, int lane,
+                                             DomainInfo *di, float4 *dconst, uint16_t *qblk, int *dkeep)
 {
-    __shared__ int q_s[kMaxM];
-    __shared__ long long red_s[2][kMaxM / 32];
-    __shared__ int cd_s, fd_s;
-    __shared__ float qp2_s[kMaxM / 32];
-    const int d = blockIdx.x;
-    const int i = threadIdx.x;  // pixel of the contracted block (blockDim = max(m, 32))
-    const int n = g.n, m = g.m;
-    const bool live = i < m;
-    const int dy = (d / g.U) * g.t, dx = (d % g.U) * g.t;
-    const int y = live ? i / n : 0, x = live ? i % n : 0;
-    const size_t o0 = (size_t)(dy + 2 * y) * g.pitch + dx + 2 * x;
-    int q = 0;
-    if (live) {
-        q = load_px(img, g.B, o0) + load_px(img, g.B, o0 + 1) + load_px(img, g.B, o0 + g.pitch) +
-            load_px(img, g.B, o0 + g.pitch + 1);
-        q_s[i] = q;
-        qblk[(size_t)d * m + i] = (uint16_t)q;
+    const int du = d % g.U;
+    const int dy = (d / g.U) * g.t, dx = du * g.t;
+    long long Sq = 0, Sqq = 0;
+    for (int i = lane; i < g.m; i += 32) {
+        const int y = i >> g.ln, x = i & (g.n - 1);
+        const size_t o0 = (size_t)(dy + 2 * y) * g.pitch + dx + 2 * x;
+        const int q = load_px(img, g.B, o0) + load_px(img, g.B, o0 + 1) + load_px(img, g.B, o0 + g.pitch) +
+                      load_px(img, g.B, o0 + g.pitch + 1);
+        qblk[(size_t)d * g.m + i] = (uint16_t)q;
+        Sq += q;
+        Sqq += (long long)q * q;
     }
-    long long s1 = q, s2 = (long long)q * q;
-    for (int off = 16; off > 0; off >>= 1) {
-        s1 += __shfl_down_sync(0xffffffffu, s1, off);
-        s2 += __shfl_down_sync(0xffffffffu, s2, off);
-    }
-    const int lane = i & 31, warp = i >> 5, nw = (m + 31) / 32;
-    if (lane == 0) {
-        red_s[0][warp] = s1;
-        red_s[1][warp] = s2;
-    }
-    __syncthreads();
-    if (i == 0) {
-        long long Sq = 0, Sqq = 0;
-        for (int w = 0; w < nw; ++w) {
-            Sq += red_s[0][w];
-            Sqq += red_s[1][w];
-        }
-        const long long cd = (2 * Sq + m) / (2 * (long long)m);
-        cd_s = (int)cd;
-        fd_s = (int)(Sq - (long long)m * cd);
-        const long long den = (long long)m * Sqq - Sq * Sq;
-        DomainInfo info;
-        info.Sq = Sq;
-        info.Sqq = Sqq;
-        info.c_d = (int)cd;
-        info.f_d = fd_s;
-        info.qp2 = 0.0f;
-        info.pad = 0.0f;
-        di[d] = info;
-        // FP32 from exact integers (no FP64 on this path)
-        float4 c4;
-        const float denf = (float)den;
-        c4.x = den > 0 ? (2.0f * m) / denf : 0.0f;
-        c4.y = (float)(g.mod_g ? Sq % (long long)g.G : Sq);
-        c4.z = denf / (8.0f * m * g.Ls);
-        c4.w = (float)Sq;
-        dconst[d] = c4;
-    }
-    __syncthreads();
-    const int c_d = cd_s;
-    // centred value of this pixel for the variance bound
-    {
-        const float qc = (float)(q - c_d);
-        float v = live ? qc * qc : 0.0f;
-        for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-        if (lane == 0) qp2_s[warp] = v;
-        __syncthreads();
-        if (i == 0) {
-            float t = 0.0f;
-            for (int w = 0; w < nw; ++w) t += qp2_s[w];
-            di[d].qp2 = t;
-        }
+    Sq = warp_sum_ll(Sq);
+    Sqq = warp_sum_ll(Sqq);
+    if (lane != 0) return;
+    const int m = g.m;
+    const long long cd = (2 * Sq + m) / (2 * (long long)m);
+    const long long den = (long long)m * Sqq - Sq * Sq;
+    DomainInfo info;
+    info.Sq = Sq;
+    info.Sqq = Sqq;
+    info.c_d = (int)cd;
+    info.f_d = (int)(Sq - (long long)m * cd);
+    info.qp2 = 0.0f;
+    info.pad = 0.0f;
+    di[d] = info;
+    // FP32 from exact integers (no FP64 on this path)
+    float4 c4;
+    const float denf = (float)den;
+    c4.x = den > 0 ? (2.0f * m) / denf : 0.0f;
+    c4.y = (float)(g.mod_g ? Sq % (long long)g.G : Sq);
+    c4.z = denf / (8.0f * m * g.Ls);
+    c4.w = (float)Sq;
+    dconst[d] = c4;
+    dkeep[d] = dense || den != 0;
+}
+
+// Statistics of every range (blocks [0, rb), a warp each) and every domain
+// (the blocks after), one launch.
+__global__ void __launch_bounds__(256) k_stats(Geometry g, EpiConst ec, const void *img, int dense, int rb,
+                                               RangeInfo *ri, uint16_t *bblk, int *tbest, DomainInfo *di,
+                                               float4 *dconst, uint16_t *qblk, int *rkeep, int *dkeep)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if ((int)blockIdx.x < rb) {
+        const int r = blockIdx.x * 8 + w;
+        if (r < g.R) range_stats(g, ec, img, dense, r, lane, ri, bblk, tbest, rkeep);
+    } else {
+        const int d = (blockIdx.x - rb) * 8 + w;
+        if (d < g.D) domain_stats(g, img, dense, d, lane, di, dconst, qblk, dkeep);
     }
 }
 
-// Stable compaction of the items whose flag is set (one block): keeps the
-// original order, writes the count, and the first unset index (-1 if none).
-__global__ void __launch_bounds__(1024) k_compact(int n, const int *flag, int *list, int *count, int *first_unset)
+// Stable compaction of the flagged items, block 0 over the ranges and block 1
+// over the domains: the kept indices in their original order, cnt[0] = how
+// many, cnt[1] = the first unflagged index (-1 if none).  Rounds of 1024
+// items: warp ballots, a scan of the 32 warp counts, a running base.
+__global__ void __launch_bounds__(1024) k_compact(int nr, const int *rflag, int *ract, int *rcnt, int nd,
+                                                  const int *dflag, int *dact, int *dcnt)
 {
-    __shared__ int cnt_s[1024];
-    __shared__ int first_s[32];
-    const int t = threadIdx.x;
-    const int seg = (n + 1023) / 1024;
-    const int lo = min(n, t * seg), hi = min(n, lo + seg);
-    int c = 0, fu = 0x7fffffff;
-    for (int i = lo; i < hi; ++i) {
-        if (flag[i]) ++c;
-        else fu = min(fu, i);
-    }
-    cnt_s[t] = c;
-    for (int off = 16; off > 0; off >>= 1) fu = min(fu, __shfl_xor_sync(0xffffffffu, fu, off));
-    if ((t & 31) == 0) first_s[t >> 5] = fu;
-    __syncthreads();
-    for (int off = 1; off < 1024; off <<= 1) {  // inclusive scan (Hillis-Steele)
-        const int v = t >= off ? cnt_s[t - off] : 0;
-        __syncthreads();
-        cnt_s[t] += v;
-        __syncthreads();
-    }
-    int pos = cnt_s[t] - c;
-    for (int i = lo; i < hi; ++i)
-        if (flag[i]) list[pos++] = i;
-    if (t == 1023) *count = cnt_s[1023];
+    __shared__ int wsum[32];
+    __shared__ int base_s, first_s;
+    const bool dom = blockIdx.x == 1;
+    const int n = dom ? nd : nr;
+    const int *flag = dom ? dflag : rflag;
+    int *list = dom ? dact : ract;
+    int *cnt = dom ? dcnt : rcnt;
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
     if (t == 0) {
-        int m = 0x7fffffff;
-        for (int w = 0; w < 32; ++w) m = min(m, first_s[w]);
-        *first_unset = m == 0x7fffffff ? -1 : m;
+        base_s = 0;
+        first_s = 0x7fffffff;
+    }
+    int fu = 0x7fffffff;
+    __syncthreads();
+    for (int i0 = 0; i0 < n; i0 += 1024) {
+        const int i = i0 + t;
+        const bool in = i < n;
+        const bool f = in && flag[i] != 0;
+        if (in && !f) fu = min(fu, i);
+        const unsigned b = __ballot_sync(0xffffffffu, f);
+        if (lane == 0) wsum[w] = __popc(b);
+        __syncthreads();
+        if (w == 0) {
+            const int v = wsum[lane];
+            int x = v;
+            for (int off = 1; off < 32; off <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, x, off);
+                if (lane >= off) x += y;
+            }
+            wsum[lane] = x - v;  // exclusive prefix of the warp counts
+        }
+        __syncthreads();
+        const int base = base_s, wbase = wsum[w];
+        if (f) list[base + wbase + __popc(b & ((1u << lane) - 1u))] = i;
+        __syncthreads();  // every thread has read base_s and wsum
+        if (t == 1023) base_s = base + wbase + __popc(b);
+    }
+    for (int off = 16; off > 0; off >>= 1) fu = min(fu, __shfl_xor_sync(0xffffffffu, fu, off));
+    if (lane == 0) atomicMin(&first_s, fu);
+    __syncthreads();
+    if (t == 0) {
+        cnt[0] = base_s;
+        cnt[1] = first_s == 0x7fffffff ? -1 : first_s;
     }
 }
 
-__global__ void k_keep_flags(Geometry g, const RangeInfo *ri, const DomainInfo *di, int dense, int *rkeep, int *dkeep)
+__device__ __forceinline__ uint32_t pack_h2(__half a, __half b)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < g.R) rkeep[i] = dense || !ri[i].shadow;
-    if (i < g.D) {
-        const DomainInfo d = di[i];
-        dkeep[i] = dense || ((long long)g.m * d.Sqq - d.Sq * d.Sq) != 0;  // non-flat domain
-    }
+    return (uint32_t)__half_as_ushort(a) | ((uint32_t)__half_as_ushort(b) << 16);
 }
 
-// Operand row j (j < count) of the range act[j]: centred pixels b - c_r.
-__global__ void k_range_rows(Geometry g, const RangeInfo *ri, const uint16_t *bblk, const int *act, const int *nact,
-                             float *rs32, __half *ra16)
+// Operand row j (j < count) of the range act[j]: centred pixels b - c_r
+// (twice when q is split into hi/lo parts), then e_hi, e_lo (e_r = 1024 e_hi
+// + e_lo) and zeros.
+__device__ __forceinline__ void range_row(const Geometry &g, const RangeInfo *ri, const uint16_t *bblk, int j, int r,
+                                          int lane, float *rs32, __half *ra16)
 {
-    const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
-    if (j >= *nact) return;
-    const int r = act[j];
     const RangeInfo info = ri[r];
     for (int i = lane; i < g.m; i += 32) {
         const int bc = (int)bblk[(size_t)r * g.m + i] - info.c_r;
@@ -252,48 +248,84 @@ __global__ void k_range_rows(Geometry g, const RangeInfo *ri, const uint16_t *bb
     }
 }
 
-// Candidate rows 8j+k of the domain dact[j] (j < count): output pixel (y,x) of
-// S_k(tau(d)) reads q at sym_src; domain constants in the same order.
-__global__ void k_domain_rows(Geometry g, const DomainInfo *di, const uint16_t *qblk, const float4 *dconst,
-                              const int *dact, const int *ndact, float *cb32, __half *cb16, float4 *dconst_c,
-                              int *dmap)
+// Candidate rows 8j+k of the domain dact[j]: output pixel (y,x) of S_k(tau(d))
+// is q at sym_src, centred by c_d.  FP16 row (tensor-core layout):
+// [128*hi | lo (12-bit only) | -1024 f_d/m, -f_d/m, 0...] with q - c_d =
+// 128*hi + lo, written as 16-byte chunks (KP and m are multiples of 8, so a
+// chunk never straddles two parts).  Domain constants in the same order.
+__device__ __forceinline__ void domain_rows_warp(const Geometry &g, const DomainInfo *di, const uint16_t *qblk,
+                                                 const float4 *dconst, int j, int d, int lane, int16_t *qc_s,
+                                                 float *cb32, __half *cb16, float4 *dconst_c, int *dmap)
 {
-    const int j = blockIdx.x;
-    if (j >= *ndact) return;
-    const int d = dact[j];
-    const int i = threadIdx.x;  // blockDim = m
-    const int n = g.n, m = g.m;
+    const int m = g.m;
     const DomainInfo info = di[d];
     const int c_d = info.c_d, fd = info.f_d;
-    if (i == 0) {
+    if (lane == 0) {
         dconst_c[j] = dconst[d];
         dmap[j] = d;
     }
-    const int y = i >> g.ln, x = i & (n - 1);
-    for (int k = 0; k < 8; ++k) {
-        int sy, sx;
-        sym_src(k, n, y, x, sy, sx);
-        const int qc = (int)qblk[(size_t)d * m + (sy << g.ln) + sx] - c_d;
-        const size_t row = (size_t)j * 8 + k;
-        if (cb32) cb32[row * m + i] = (float)qc;
-        if (cb16) {
-            __half *rowp = cb16 + row * g.KP;
-            if (g.split_hilo) {
-                const int hi = (qc + 64) >> 7;  // floor; |hi| <= 128
-                const int lo = qc - 128 * hi;   // in [-64, 63]
-                rowp[i] = __int2half_rn(128 * hi);
-                rowp[m + i] = __int2half_rn(lo);
-            } else {
-                rowp[i] = __int2half_rn(qc);
-            }
-            const int base = g.split_hilo ? 2 * m : m;
-            if (i < g.KP - base) {
-                float v = 0.0f;
-                if (i == 0) v = -1024.0f * (float)fd / (float)m;
-                if (i == 1) v = -(float)fd / (float)m;
-                rowp[base + i] = __float2half_rn(v);
-            }
+    for (int i = lane; i < m; i += 32) qc_s[i] = (int16_t)((int)qblk[(size_t)d * m + i] - c_d);
+    __syncwarp();
+    if (cb32) {
+        for (int k = 0; k < 8; ++k) {
+            const SymFlags sf = sym_flags(k, g.n);
+            for (int i = lane; i < m; i += 32)
+                cb32[((size_t)j * 8 + k) * m + i] = (float)qc_s[sym_src_index(sf, g.ln, i >> g.ln, i & (g.n - 1))];
         }
+    }
+    if (cb16) {
+        const int nch = g.KP >> 3;  // 16-byte chunks per row
+        const int base = g.split_hilo ? 2 * m : m;
+        const __half t0 = __float2half_rn(-1024.0f * (float)fd / (float)m);
+        const __half t1 = __float2half_rn(-(float)fd / (float)m);
+        for (int e = lane; e < 8 * nch; e += 32) {
+            const int k = e / nch, c = e - k * nch;
+            const int col0 = 8 * c;
+            __half h[8];
+            if (col0 >= base) {
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int tc = col0 + u - base;
+                    h[u] = tc == 0 ? t0 : (tc == 1 ? t1 : __float2half_rn(0.0f));
+                }
+            } else {
+                const SymFlags sf = sym_flags(k, g.n);
+                const bool lo_part = col0 >= m;  // second copy (12-bit only)
+                const int p0 = lo_part ? col0 - m : col0;
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int i = p0 + u;
+                    const int qc = qc_s[sym_src_index(sf, g.ln, i >> g.ln, i & (g.n - 1))];
+                    if (g.split_hilo) {
+                        const int hi = (qc + 64) >> 7;  // floor; |hi| <= 128
+                        h[u] = lo_part ? __int2half_rn(qc - 128 * hi) : __int2half_rn(128 * hi);
+                    } else {
+                        h[u] = __int2half_rn(qc);
+                    }
+                }
+            }
+            const uint4 v = make_uint4(pack_h2(h[0], h[1]), pack_h2(h[2], h[3]), pack_h2(h[4], h[5]),
+                                       pack_h2(h[6], h[7]));
+            reinterpret_cast<uint4 *>(cb16 + ((size_t)j * 8 + k) * g.KP)[c] = v;
+        }
+    }
+}
+
+// Operand rows of the kept ranges (blocks [0, rb), a warp per row) and of the
+// kept domains (the blocks after, a warp per domain), one launch.
+__global__ void __launch_bounds__(256) k_rows(Geometry g, int rb, const RangeInfo *ri, const uint16_t *bblk,
+                                              const DomainInfo *di, const uint16_t *qblk, const float4 *dconst,
+                                              const int *act, const int *dact, const int *counts, float *rs32,
+                                              __half *ra16, float *cb32, __half *cb16, float4 *dconst_c, int *dmap)
+{
+    __shared__ int16_t qc_s[8][kMaxM];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if ((int)blockIdx.x < rb) {
+        const int j = blockIdx.x * 8 + w;
+        if (j < counts[0]) range_row(g, ri, bblk, j, act[j], lane, rs32, ra16);
+    } else {
+        const int j = (blockIdx.x - rb) * 8 + w;
+        if (j < counts[2]) domain_rows_warp(g, di, qblk, dconst, j, dact[j], lane, qc_s[w], cb32, cb16, dconst_c, dmap);
     }
 }
 
@@ -301,21 +333,14 @@ cudaError_t launch_prep(const Geometry &g, const void *img, const EpiConst &ec, 
                         DomainInfo *di, float4 *dconst, uint16_t *bblk, uint16_t *qblk, float *rs32, float *cb32,
                         __half *ra16, __half *cb16, int *tbest, const CompactBufs &cb, cudaStream_t st)
 {
-    k_range_prep<<<(g.R + 7) / 8, 256, 0, st>>>(g, ec, img, ri, bblk, tbest);
+    const int rb = (g.R + 7) / 8, db = (g.D + 7) / 8;
+    k_stats<<<rb + db, 256, 0, st>>>(g, ec, img, dense, rb, ri, bblk, tbest, di, dconst, qblk, cb.rkeep, cb.dkeep);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_domain_prep<<<g.D, g.m < 32 ? 32 : g.m, 0, st>>>(g, img, di, dconst, qblk);
+    k_compact<<<2, 1024, 0, st>>>(g.R, cb.rkeep, cb.act, cb.counts + 0, g.D, cb.dkeep, cb.dact, cb.counts + 2);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    const int nmax = g.R > g.D ? g.R : g.D;
-    k_keep_flags<<<(nmax + 255) / 256, 256, 0, st>>>(g, ri, di, dense, cb.rkeep, cb.dkeep);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_compact<<<1, 1024, 0, st>>>(g.R, cb.rkeep, cb.act, cb.counts + 0, cb.counts + 1);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_compact<<<1, 1024, 0, st>>>(g.D, cb.dkeep, cb.dact, cb.counts + 2, cb.counts + 3);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_range_rows<<<(g.R + 7) / 8, 256, 0, st>>>(g, ri, bblk, cb.act, cb.counts + 0, rs32, ra16);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_domain_rows<<<g.D, g.m, 0, st>>>(g, di, qblk, dconst, cb.dact, cb.counts + 2, cb32, cb16, cb.dconst_c, cb.dmap);
+    k_rows<<<rb + db, 256, 0, st>>>(g, rb, ri, bblk, di, qblk, dconst, cb.act, cb.dact, cb.counts, rs32, ra16, cb32,
+                                    cb16, cb.dconst_c, cb.dmap);
     return cudaGetLastError();
 }
 
@@ -326,15 +351,20 @@ cudaError_t launch_prep(const Geometry &g, const void *img, const EpiConst &ec, 
 // not next to a rounding boundary, offset not clamped) are published: each is
 // within the screening allowance of a real candidate's residual, which is all
 // the search's insertion window needs.
-__global__ void k_seed(Geometry g, EpiConst ec, const RangeInfo *ri, const DomainInfo *di, const float4 *dconst,
-                       const uint16_t *bblk, const uint16_t *qblk, int *tbest)
+__global__ void __launch_bounds__(256) k_seed(Geometry g, EpiConst ec, const RangeInfo *ri, const DomainInfo *di,
+                                              const float4 *dconst, const uint16_t *bblk, const uint16_t *qblk,
+                                              int *tbest)
 {
-    __shared__ unsigned b_s[kMaxM];
-    __shared__ uint16_t q_s[kMaxM][32];  // [pixel][domain slot]: lanes read consecutive slots
+    // q2_s[p][slot]: contracted-domain pixels 2p, 2p+1 of the slot's domain
+    // (lanes read consecutive words); bk_s[k][j]: the range pixel that S_k
+    // places over domain pixel j, so X(d, k) = sum_j q_d[j] * bk_s[k][j]
+    __shared__ uint32_t q2_s[kMaxM / 2][32];
+    __shared__ __align__(8) int bk_s[8][kMaxM];
     __shared__ int d_s[32];
     const int r = blockIdx.x;
     const RangeInfo rin = ri[r];  // block-uniform
     if (rin.shadow) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x < 32) {
         const int slot_d = threadIdx.x;
         int d;
@@ -350,22 +380,41 @@ __global__ void k_seed(Geometry g, EpiConst ec, const RangeInfo *ri, const Domai
         }
         d_s[slot_d] = d;
     }
-    for (int i = threadIdx.x; i < g.m; i += blockDim.x) b_s[i] = bblk[(size_t)r * g.m + i];
-    __syncthreads();
-    const int lm = 2 * g.ln;  // log2(m)
-    for (int e = threadIdx.x; e < 32 * g.m; e += blockDim.x) {
-        const int sl = e >> lm, i = e & (g.m - 1);
-        q_s[i][sl] = qblk[(size_t)d_s[sl] * g.m + i];
+    {
+        // one symmetry per warp: no divergence in sym_src
+        const int k = warp;
+        for (int i = lane; i < g.m; i += 32) {
+            int sy, sx;
+            sym_src(k, g.n, i >> g.ln, i & (g.n - 1), sy, sx);
+            bk_s[k][(sy << g.ln) + sx] = bblk[(size_t)r * g.m + i];
+        }
     }
     __syncthreads();
-    const int k = threadIdx.x >> 5;     // one symmetry per warp: no divergence in sym_src
-    const int slot_d = threadIdx.x & 31;
+    // 16-byte loads of the 32 domain rows (m/8 vectors each)
+    const int nv = g.m >> 3;
+    for (int e = threadIdx.x; e < 32 * nv; e += blockDim.x) {
+        const int sl = e & 31, v = e >> 5;
+        const uint4 w = __ldg(reinterpret_cast<const uint4 *>(qblk + (size_t)d_s[sl] * g.m) + v);
+        q2_s[4 * v + 0][sl] = w.x;
+        q2_s[4 * v + 1][sl] = w.y;
+        q2_s[4 * v + 2][sl] = w.z;
+        q2_s[4 * v + 3][sl] = w.w;
+    }
+    __syncthreads();
+    const int k = warp;
+    const int slot_d = lane;
     const int d = d_s[slot_d];
     unsigned long long X = 0;
-    for (int i = 0; i < g.m; ++i) {
-        int sy, sx;
-        sym_src(k, g.n, i >> g.ln, i & (g.n - 1), sy, sx);
-        X += (unsigned)q_s[(sy << g.ln) + sx][slot_d] * b_s[i];
+    for (int p0 = 0; p0 < (g.m >> 1); p0 += 4) {
+        // eight products of at most 4P * P < 2^26: exact in 32 bits
+        uint32_t s = 0;
+#pragma unroll
+        for (int p = p0; p < p0 + 4; ++p) {
+            const uint32_t q2 = q2_s[p][slot_d];
+            const int2 b2 = *reinterpret_cast<const int2 *>(&bk_s[k][2 * p]);
+            s += (q2 & 0xffffu) * (uint32_t)b2.x + (q2 >> 16) * (uint32_t)b2.y;
+        }
+        X += s;
     }
     const DomainInfo dd = di[d];
     const long long num = (long long)g.m * (long long)X - dd.Sq * rin.Sb;  // exact

@@ -108,26 +108,6 @@ __device__ unsigned __int128 exact_candidate(const Geometry &g, Stats st, const 
     return (unsigned __int128)exact_err(g, st, c, e);
 }
 
-// Exact X of candidate idx for a range whose pixels b[] are spread over the
-// warp (lane l holds pixels l, l+32, ...); every lane gets the sum.
-__device__ long long warp_cross(const Geometry &g, const uint16_t *qblk, uint32_t idx, const int (&b)[kMaxM / 32])
-{
-    const int d = idx >> 3, k = idx & 7;
-    const int lane = threadIdx.x & 31;
-    long long acc = 0;
-#pragma unroll
-    for (int j = 0; j < kMaxM / 32; ++j) {
-        const int i = lane + 32 * j;
-        if (i < g.m) {
-            int sy, sx;
-            sym_src(k, g.n, i >> g.ln, i & (g.n - 1), sy, sx);
-            acc += (long long)qblk[(size_t)d * g.m + (sy << g.ln) + sx] * b[j];
-        }
-    }
-    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-    return acc;
-}
-
 // round half away from zero of num/den (den > 0), exactly: an FP32 estimate
 // corrected with exact integer comparisons.
 __device__ __forceinline__ long long round_div_away(long long num, long long den)
@@ -163,6 +143,78 @@ __device__ unsigned __int128 exact_rational(const Geometry &g, Stats st, const D
     return (unsigned __int128)exact_err(g, st, c, e);
 }
 
+// Exact X of two candidates for a range whose pixels b[] are spread over the
+// warp (lane l holds pixels l, l+32, ...); every lane gets both sums.
+__device__ void warp_cross2(const Geometry &g, const uint16_t *qblk, uint32_t i0, uint32_t i1,
+                            const int (&b)[kMaxM / 32], long long &x0, long long &x1)
+{
+    const int d0 = i0 >> 3, k0 = i0 & 7, d1 = i1 >> 3, k1 = i1 & 7;
+    const int lane = threadIdx.x & 31;
+    long long a0 = 0, a1 = 0;
+#pragma unroll
+    for (int j = 0; j < kMaxM / 32; ++j) {
+        const int i = lane + 32 * j;
+        if (i < g.m) {
+            int sy, sx;
+            sym_src(k0, g.n, i >> g.ln, i & (g.n - 1), sy, sx);
+            const int q0 = qblk[(size_t)d0 * g.m + (sy << g.ln) + sx];
+            sym_src(k1, g.n, i >> g.ln, i & (g.n - 1), sy, sx);
+            const int q1 = qblk[(size_t)d1 * g.m + (sy << g.ln) + sx];
+            a0 += (long long)q0 * b[j];
+            a1 += (long long)q1 * b[j];
+        }
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        a0 += __shfl_xor_sync(0xffffffffu, a0, off);
+        a1 += __shfl_xor_sync(0xffffffffu, a1, off);
+    }
+    x0 = a0;
+    x1 = a1;
+}
+
+// The range's pixels permuted for each symmetry: bk[k*(m+1) + j] is the
+// range pixel that S_k places over contracted-domain pixel j, so that
+// X(d, k) = sum_j q_d[j] * bk[k][j] with the domain row read in natural order.
+// Row pitch m+1 words: lanes of different symmetries hit different banks.
+__device__ void stage_sym_pixels(const Geometry &g, const int (&b)[kMaxM / 32], int *bk)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll 1
+    for (int k = 0; k < 8; ++k) {
+#pragma unroll
+        for (int j = 0; j < kMaxM / 32; ++j) {
+            const int i = lane + 32 * j;
+            if (i < g.m) {
+                int sy, sx;
+                sym_src(k, g.n, i >> g.ln, i & (g.n - 1), sy, sx);
+                bk[k * (g.m + 1) + (sy << g.ln) + sx] = b[j];
+            }
+        }
+    }
+    __syncwarp();
+}
+
+// Exact X of candidate idx computed by one lane alone (16-byte loads of the
+// domain row; m is a multiple of 16).
+__device__ long long lane_cross(const Geometry &g, const uint16_t *qblk, uint32_t idx, const int *bk)
+{
+    const int *bkk = bk + (idx & 7) * (g.m + 1);
+    const uint4 *qrow = reinterpret_cast<const uint4 *>(qblk + (size_t)(idx >> 3) * g.m);
+    unsigned long long acc = 0;
+#pragma unroll 4
+    for (int v = 0; v < g.m / 8; ++v) {
+        const uint4 w = __ldg(qrow + v);
+        const int *bb = bkk + 8 * v;
+        // eight products of at most 4P * P < 2^26 each: exact in 32 bits
+        uint32_t s = (w.x & 0xffffu) * (uint32_t)bb[0] + (w.x >> 16) * (uint32_t)bb[1];
+        s += (w.y & 0xffffu) * (uint32_t)bb[2] + (w.y >> 16) * (uint32_t)bb[3];
+        s += (w.z & 0xffffu) * (uint32_t)bb[4] + (w.z >> 16) * (uint32_t)bb[5];
+        s += (w.w & 0xffffu) * (uint32_t)bb[6] + (w.w >> 16) * (uint32_t)bb[7];
+        acc += s;
+    }
+    return (long long)acc;
+}
+
 // One warp per range.  Ranking here uses exact integer arithmetic only
 // (codes rounded exactly from the rational least-squares values, residual in
 // 128-bit integers); the FP64 code decision of eq 9-12 is made once, for the
@@ -178,21 +230,19 @@ __device__ unsigned __int128 exact_rational(const Geometry &g, Stats st, const D
 //     key, is strictly above the winner's residual: then no candidate outside
 //     the lists can beat or tie it.  Otherwise the range goes to the exact
 //     fallback.
-__global__ void k_rescore(Geometry g, EpiConst ec, const RangeInfo *ri, const DomainInfo *di,
-                          const uint16_t *bblk, const uint16_t *qblk, const ListEntry *lists,
-                          int max_lists, const int *counts, int lists_per_split, int col_tile, int target,
-                          int max_split, int dense, uint32_t *winner, int *fb_list, int *fb_count)
+// Both tests compare FP32 keys against thresholds computed once per range in
+// FP64 and rounded outward (up for the finalist bound, so that no finalist
+// is lost; the certification side is rounded down on the key and up on the
+// threshold, so that it never certifies what the exact test would not).
+constexpr int kRescoreWarps = 4;
+__device__ __forceinline__ void rescore_range(const Geometry &g, const EpiConst &ec, const RangeInfo *ri,
+                                              const DomainInfo *di, const uint16_t *bblk, const uint16_t *qblk,
+                                              const ListEntry *lists, int max_lists, const int *counts,
+                                              int lists_per_split, int col_tile, int target, int max_split,
+                                              uint32_t *winner, int *fb_list, int *fb_count, int r, int *bk)
 {
-    const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
-    if (r >= g.R) return;  // warp-uniform
     const RangeInfo rin = ri[r];
-    if (rin.shadow && !dense) {
-        // constant range: num = 0 for every candidate, so s = 0, one offset and
-        // one residual for all; the first candidate wins (Algorithm 2)
-        if (lane == 0) winner[r] = 0;
-        return;
-    }
     int b[kMaxM / 32];
 #pragma unroll
     for (int j = 0; j < kMaxM / 32; ++j) {
@@ -206,6 +256,7 @@ __global__ void k_rescore(Geometry g, EpiConst ec, const RangeInfo *ri, const Do
     const int nent = n_lists * kListK;
     float kb = __int_as_float(0x7f800000);
     uint32_t ib = 0xffffffffu;
+#pragma unroll 4
     for (int f = lane; f < nent; f += 32) {
         const ListEntry e = L[f];
         if (e.idx != 0xffffffffu && (e.key < kb || (e.key == kb && e.idx < ib))) {
@@ -232,35 +283,56 @@ __global__ void k_rescore(Geometry g, EpiConst ec, const RangeInfo *ri, const Do
     st.Sb = rin.Sb;
     st.Sbb = rin.Sbb;
     const double invD2 = 1.0 / ((double)(4 * g.Ls * g.Lo) * (double)(4 * g.Ls * g.Lo));
-    const double inv2ls = 1.0 / (2.0 * g.Ls);
-    unsigned __int128 ue;
+    const double two_ls = 2.0 * g.Ls;
+    // Flat domains were not screened: all their candidates have s = 0 and the
+    // same residual, so only the first of them, (first flat domain, k = 0), can
+    // win; it is a finalist of every range.  Its cross term is computed
+    // together with the best-key entry's.
+    const int dflat = counts[3];
+    const uint32_t fi = dflat >= 0 ? (uint32_t)dflat * 8 : ib;
+    unsigned __int128 ue, fe;
     {
-        const long long X = warp_cross(g, qblk, ib, b);
+        long long X, Xf;
+        warp_cross2(g, qblk, ib, fi, b, X, Xf);
         ue = exact_rational(g, st, di[ib >> 3], X);  // integer work, same on every lane
+        fe = dflat >= 0 ? exact_rational(g, st, di[dflat], Xf) : ~(unsigned __int128)0;
     }
     const double U = u128_to_double(ue) * invD2;
     // screening error allowance (the epilogue's), converted to residual units;
     // evaluated at the largest key that can still matter
     const RangeEpi re = range_epi(rin, ec);
-    const float kreach = (float)((U - (double)rin.sbbc) * 2.0 * g.Ls);
-    const float beta_k = fmaxf(beta_key(re, kb, ec), beta_key(re, fmaxf(kb, kreach), ec));
-    const double betaE = (double)beta_k * inv2ls;
     const double sbbc = (double)rin.sbbc;
+    const float kreach = (float)((U - sbbc) * two_ls);
+    const float beta_k = fmaxf(beta_key(re, kb, ec), beta_key(re, fmaxf(kb, kreach), ec));
+    // finalist: sbbc + key/(2Ls) - beta/(2Ls) <= U  <=>  key <= (U - sbbc)*2Ls + beta
+    const float kfin = __double2float_ru((U - sbbc) * two_ls + (double)beta_k);
 
-    unsigned __int128 best_e = ~(unsigned __int128)0;
-    uint32_t best_i = 0xffffffffu;
+    unsigned __int128 best_e = ue;
+    uint32_t best_i = ib;
+    if (lane == 0 && dflat >= 0 && better(fe, fi, best_e, best_i)) {
+        best_e = fe;
+        best_i = fi;
+    }
+    bool staged = false;
     for (int f0 = 0; f0 < nent; f0 += 32) {
         const int f = f0 + lane;
         const ListEntry ent = f < nent ? L[f] : ListEntry{__int_as_float(0x7f800000), 0xffffffffu};
-        const bool fin = ent.idx != 0xffffffffu && sbbc + (double)ent.key * inv2ls - betaE <= U;
+        const bool fin = ent.idx != 0xffffffffu && ent.idx != ib && ent.key <= kfin;
         unsigned mask = __ballot_sync(0xffffffffu, fin);
+        if (!mask) continue;
         long long myX = 0;
-        while (mask) {
+        if ((mask & (mask - 1)) == 0) {  // one finalist: the whole warp computes it
             const int src = __ffs(mask) - 1;
-            mask &= mask - 1;
             const uint32_t idx = __shfl_sync(0xffffffffu, ent.idx, src);
-            const long long X = warp_cross(g, qblk, idx, b);
-            if (lane == src) myX = X;
+            long long X, Xd;
+            warp_cross2(g, qblk, idx, idx, b, X, Xd);
+            myX = X;
+        } else {  // several: each lane computes its own
+            if (!staged) {
+                stage_sym_pixels(g, b, bk);
+                staged = true;
+            }
+            if (fin) myX = lane_cross(g, qblk, ent.idx, bk);
         }
         if (fin) {  // lanes re-score their own finalists in parallel (integer work)
             const unsigned __int128 er = exact_rational(g, st, di[ent.idx >> 3], myX);
@@ -270,35 +342,43 @@ __global__ void k_rescore(Geometry g, EpiConst ec, const RangeInfo *ri, const Do
             }
         }
     }
-    // Flat domains were not screened: all their candidates have s = 0 and the
-    // same residual, so only the first of them, (first flat domain, k = 0), can
-    // win; it is a finalist of every range.
-    const int dflat = counts[3];
-    if (dflat >= 0) {
-        const uint32_t fi = (uint32_t)dflat * 8;
-        const long long X = warp_cross(g, qblk, fi, b);
-        const unsigned __int128 er = exact_rational(g, st, di[dflat], X);
-        if (lane == 0 && better(er, fi, best_e, best_i)) {
-            best_e = er;
-            best_i = fi;
-        }
-    }
     warp_argmin(best_e, best_i);
     const double Estar = u128_to_double(best_e) * invD2;
+    // certified list: sbbc + (last - beta(last))/(2Ls) > E*(1 + 1e-12) + 1e-12
+    const float kcert = __double2float_ru((Estar * (1.0 + 1e-12) + 1e-12 - sbbc) * two_ls);
     bool cert = true;
     for (int l = lane; l < n_lists; l += 32) {
         // a full list's unlisted candidates have residual >= its last key less
         // the allowance at that key; that bound must clear the winner strictly
         const ListEntry last = L[l * kListK + kListK - 1];
         if (last.idx == 0xffffffffu) continue;
-        const double bl = (double)beta_key(re, last.key, ec) * inv2ls;
-        if (!(sbbc + (double)last.key * inv2ls - bl > Estar * (1.0 + 1e-12) + 1e-12)) cert = false;
+        if (!(__fsub_rd(last.key, beta_key(re, last.key, ec)) > kcert)) cert = false;
     }
     cert = __all_sync(0xffffffffu, cert);
     if (lane == 0) {
         winner[r] = best_i;
         if (!cert) fb_list[atomicAdd(fb_count, 1)] = r;
     }
+}
+
+// Persistent warps over the screened ranges (act[], one warp per range, the
+// grid sized to be resident at once); every other range is a constant one:
+// num = 0 for every candidate, so s = 0, one offset and one residual for
+// all, and the first candidate wins (Algorithm 2).
+__global__ void __launch_bounds__(32 * kRescoreWarps, 4)
+    k_rescore(Geometry g, EpiConst ec, const RangeInfo *ri, const DomainInfo *di, const uint16_t *bblk,
+              const uint16_t *qblk, const ListEntry *lists, int max_lists, const int *counts, const int *act,
+              const int *rkeep, int lists_per_split, int col_tile, int target, int max_split, uint32_t *winner,
+              int *fb_list, int *fb_count)
+{
+    extern __shared__ int bk_all[];  // [warps][8][m+1]
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < g.R; r += gridDim.x * blockDim.x)
+        if (!rkeep[r]) winner[r] = 0;
+    int *bk = bk_all + (threadIdx.x >> 5) * 8 * (g.m + 1);
+    const int nkept = counts[0];
+    for (int j = blockIdx.x * kRescoreWarps + (threadIdx.x >> 5); j < nkept; j += gridDim.x * kRescoreWarps)
+        rescore_range(g, ec, ri, di, bblk, qblk, lists, max_lists, counts, lists_per_split, col_tile, target,
+                      max_split, winner, fb_list, fb_count, act[j], bk);
 }
 
 struct Partial {
@@ -377,46 +457,74 @@ __global__ void k_fallback_reduce(int nch, const int *fb_list, const int *fb_cou
 }
 
 // FP64 codes of the winner (eq 9-12 in FP64, the operation order of the
-// least-squares formulas) and its eq 8 residual, one thread per range so that
-// every FP64 instruction works on 32 ranges.  The residual is evaluated
-// exactly in integers and rounded once to FP64.  The range's pixels and the
-// winner's 2x2 sums are staged in shared memory by the whole block.
+// least-squares formulas) and its eq 8 residual, one thread of warp 0 per
+// range so that every FP64 instruction works on 32 ranges.  The residual is
+// evaluated exactly in integers and rounded once to FP64.  The block stages
+// its 32 ranges' pixels and winners' 2x2 sums in shared memory with 16-byte
+// loads (row pitch m+2 halves: an odd number of words, so lanes walking their
+// own rows hit different banks), and its four warps each sum a quarter of the
+// pixel rows of the exact cross term.
 constexpr int kFinRanges = 32;
-__global__ void __launch_bounds__(128) k_finalize(Geometry g, const RangeInfo *ri, const DomainInfo *di,
-                                                  const uint16_t *bblk, const uint16_t *qblk,
-                                                  const uint32_t *winner, const int *err, fic_map *maps)
+constexpr int kFinWarps = 4;
+__global__ void __launch_bounds__(32 * kFinWarps) k_finalize(Geometry g, const RangeInfo *ri, const DomainInfo *di,
+                                                             const uint16_t *bblk, const uint16_t *qblk,
+                                                             const uint32_t *winner, const int *err, fic_map *maps)
 {
-    __shared__ uint16_t b_s[kFinRanges][kMaxM + 2];  // row pitch of 129 words: conflict-free
-    __shared__ uint16_t q_s[kFinRanges][kMaxM + 2];
+    __shared__ uint32_t b_s[kFinRanges][(kMaxM + 2) / 2];
+    __shared__ uint32_t q_s[kFinRanges][(kMaxM + 2) / 2];
     __shared__ uint32_t w_s[kFinRanges];
+    __shared__ long long x_s[kFinWarps][kFinRanges];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int r0 = blockIdx.x * kFinRanges;
     const int nr = min(kFinRanges, g.R - r0);
-    for (int j = threadIdx.x; j < nr; j += blockDim.x) w_s[j] = winner[r0 + j];
+    const int r = r0 + lane;
+    const bool live = lane < nr;
+    if (warp == 0) w_s[lane] = live ? winner[r] : 0u;
     __syncthreads();
-    const int lm = 2 * g.ln;
-    for (int e = threadIdx.x; e < nr * g.m; e += blockDim.x) {
-        const int j = e >> lm, i = e & (g.m - 1);
-        uint32_t idx = w_s[j] & 0x7fffffffu;
-        if (idx >= (uint32_t)g.N) idx = 0;  // unreachable: every range has a winner
-        b_s[j][i] = bblk[(size_t)(r0 + j) * g.m + i];
-        q_s[j][i] = qblk[(size_t)(idx >> 3) * g.m + i];
-    }
-    __syncthreads();
-    const int j = threadIdx.x;
-    if (j >= nr) return;
-    const int r = r0 + j;
-    const uint32_t wv = w_s[j];
+    const uint32_t wv = w_s[lane];
     uint32_t idx = wv & 0x7fffffffu;
-    if (idx >= (uint32_t)g.N) idx = 0;
+    if (idx >= (uint32_t)g.N) idx = 0;  // unreachable: every range has a winner
     const int d = idx >> 3, k = idx & 7;
-    const RangeInfo rin = ri[r];
-    const DomainInfo dd = di[d];
-    long long X = 0;
-    for (int i = 0; i < g.m; ++i) {
-        int sy, sx;
-        sym_src(k, g.n, i >> g.ln, i & (g.n - 1), sy, sx);
-        X += (long long)q_s[j][(sy << g.ln) + sx] * b_s[j][i];
+    RangeInfo rin{};
+    DomainInfo dd{};
+    if (warp == 0 && live) {  // issued before the staging so that they overlap it
+        rin = ri[r];
+        dd = di[d];
     }
+    const int pw = (g.m + 2) >> 1;  // row pitch in words
+    const int lnv = 2 * g.ln - 3;   // log2 of the 16-byte vectors per row (m >= 16)
+#pragma unroll 4
+    for (int e = threadIdx.x; e < (nr << lnv); e += 32 * kFinWarps) {
+        const int j = e >> lnv, v = e & ((1 << lnv) - 1);
+        uint32_t jd = w_s[j] & 0x7fffffffu;
+        if (jd >= (uint32_t)g.N) jd = 0;
+        const uint4 bw = __ldg(reinterpret_cast<const uint4 *>(bblk + (size_t)(r0 + j) * g.m) + v);
+        const uint4 qw = __ldg(reinterpret_cast<const uint4 *>(qblk + (size_t)(jd >> 3) * g.m) + v);
+        uint32_t *bd = &b_s[0][0] + j * pw + 4 * v;
+        uint32_t *qd = &q_s[0][0] + j * pw + 4 * v;
+        bd[0] = bw.x, bd[1] = bw.y, bd[2] = bw.z, bd[3] = bw.w;
+        qd[0] = qw.x, qd[1] = qw.y, qd[2] = qw.z, qd[3] = qw.w;
+    }
+    __syncthreads();
+    {
+        // rows [warp*n/4, (warp+1)*n/4) of range `lane` (n >= 4)
+        const uint16_t *brow = reinterpret_cast<const uint16_t *>(&b_s[0][0] + lane * pw);
+        const uint16_t *qrow = reinterpret_cast<const uint16_t *>(&q_s[0][0] + lane * pw);
+        const SymFlags sf = sym_flags(k, g.n);
+        const int rows = g.n >> 2;
+        long long X = 0;
+        for (int y = warp * rows; y < (warp + 1) * rows; ++y) {
+            uint32_t acc = 0;  // one row: n products of at most 4P * P, n <= 16
+            for (int x = 0; x < g.n; ++x) acc += (uint32_t)qrow[sym_src_index(sf, g.ln, y, x)] * brow[(y << g.ln) + x];
+            X += acc;
+        }
+        x_s[warp][lane] = X;
+    }
+    __syncthreads();
+    if (warp != 0 || !live) return;
+    long long X = 0;
+#pragma unroll
+    for (int w = 0; w < kFinWarps; ++w) X += x_s[w][lane];
     Stats st{dd.Sq, dd.Sqq, rin.Sb, rin.Sbb, X};
     int c, e;
     double sh, oh;
@@ -437,12 +545,16 @@ __global__ void __launch_bounds__(128) k_finalize(Geometry g, const RangeInfo *r
 
 cudaError_t launch_rescore(const Geometry &g, const EpiConst &ec, const RangeInfo *ri,
                            const DomainInfo *di, const uint16_t *bblk, const uint16_t *qblk,
-                           const ListEntry *lists, int max_lists, const int *counts, int lists_per_split,
-                           int col_tile, int target, int max_split, int dense, uint32_t *winner, int *fb_list,
-                           int *fb_count, cudaStream_t st)
+                           const ListEntry *lists, int max_lists, const int *counts, const int *act,
+                           const int *rkeep, int lists_per_split, int col_tile, int target, int max_split, int n_sm,
+                           uint32_t *winner, int *fb_list, int *fb_count, cudaStream_t st)
 {
-    k_rescore<<<(g.R + 3) / 4, 128, 0, st>>>(g, ec, ri, di, bblk, qblk, lists, max_lists, counts, lists_per_split,
-                                             col_tile, target, max_split, dense, winner, fb_list, fb_count);
+    const size_t smem = sizeof(int) * kRescoreWarps * 8 * (g.m + 1);
+    // at most as many blocks as are resident at once (4 per SM at this size)
+    const int blocks = std::max(1, std::min((g.R + kRescoreWarps - 1) / kRescoreWarps, 4 * n_sm));
+    k_rescore<<<blocks, 32 * kRescoreWarps, smem, st>>>(g, ec, ri, di, bblk, qblk, lists, max_lists, counts, act,
+                                                         rkeep, lists_per_split, col_tile, target, max_split, winner,
+                                                         fb_list, fb_count);
     return cudaGetLastError();
 }
 
@@ -470,7 +582,8 @@ cudaError_t launch_finalize(const Geometry &g, const RangeInfo *ri, const Domain
                             const uint16_t *bblk, const uint16_t *qblk, const uint32_t *winner,
                             const int *err, fic_map *maps, cudaStream_t st)
 {
-    k_finalize<<<(g.R + kFinRanges - 1) / kFinRanges, 128, 0, st>>>(g, ri, di, bblk, qblk, winner, err, maps);
+    k_finalize<<<(g.R + kFinRanges - 1) / kFinRanges, 32 * kFinWarps, 0, st>>>(g, ri, di, bblk, qblk, winner, err,
+                                                                              maps);
     return cudaGetLastError();
 }
 

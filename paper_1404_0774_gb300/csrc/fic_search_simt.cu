@@ -30,7 +30,6 @@ __global__ void __launch_bounds__(256) k_search_simt(Geometry g, EpiConst ec, co
     float *As = smem;              // [KC][BM]
     float *Bs = As + KC * BM;      // [KC][BN]
     float *Xs = Bs + KC * BN;      // [BM][XS]
-    float *Ks = Xs + BM * XS;      // [32][256]: keys staged for the rare pass
     __shared__ float er_s[BM];
     __shared__ float fdm_s[BN];
 
@@ -145,11 +144,10 @@ __global__ void __launch_bounds__(256) k_search_simt(Geometry g, EpiConst ec, co
                     dc[q] = ok ? dconst[jd] : make_float4(0.f, 0.f, 0.f, 0.f);
                     od[q] = ok ? dmap[jd] : 0;
                 }
-                if (epi_keys32(X, dc, re.zb, re.rho_lim, ec, fminf(L.key[kListK - 1], L.tw),
-                               L.has_zero ? kZeroPenalty : 0.0f)) {
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) Ks[j * 256 + tid] = X[j];
-                    epi_rare(Ks + tid, 256, xrow, 1, od, dc, re, ec, L, nvalid);
+                const uint32_t mask = epi_keys32(X, dc, re.zb, re.rho_lim, ec, fminf(L.key[kListK - 1], L.tw),
+                                                 L.has_zero ? kZeroPenalty : 0.0f);
+                if (mask) {
+                    epi_rare(xrow, 1, od, dc, re, ec, L, mask);
                     if (L.T < L.Tpub) {
                         atomicMin(tbest + my_r, f2ord(L.T));
                         L.Tpub = L.T;
@@ -172,7 +170,7 @@ cudaError_t launch_search_simt(const Geometry &g, const EpiConst &ec, const Rang
                                const float *cb32, ListEntry *lists, int max_split, int target, int *tbest,
                                float *dump, cudaStream_t st)
 {
-    const size_t smem = sizeof(float) * (KC * BM + KC * BN + BM * XS + 32 * 256);
+    const size_t smem = sizeof(float) * (KC * BM + KC * BN + BM * XS);
     cudaError_t e = cudaFuncSetAttribute(k_search_simt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((g.R + BM - 1) / BM, max_split);

@@ -178,6 +178,47 @@ __device__ __forceinline__ void tmem_wait(uint32_t (&r)[32])
                  : "memory");
 }
 
+// Wait for this thread's outstanding tcgen05.ld of two 32-column chunks.
+__device__ __forceinline__ void tmem_wait2(uint32_t (&a)[32], uint32_t (&b)[32])
+{
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(a[0]), "+r"(a[1]), "+r"(a[2]), "+r"(a[3]), "+r"(a[4]), "+r"(a[5]), "+r"(a[6]),
+                   "+r"(a[7]), "+r"(a[8]), "+r"(a[9]), "+r"(a[10]), "+r"(a[11]), "+r"(a[12]), "+r"(a[13]),
+                   "+r"(a[14]), "+r"(a[15]), "+r"(a[16]), "+r"(a[17]), "+r"(a[18]), "+r"(a[19]), "+r"(a[20]),
+                   "+r"(a[21]), "+r"(a[22]), "+r"(a[23]), "+r"(a[24]), "+r"(a[25]), "+r"(a[26]), "+r"(a[27]),
+                   "+r"(a[28]), "+r"(a[29]), "+r"(a[30]), "+r"(a[31]), "+r"(b[0]), "+r"(b[1]), "+r"(b[2]),
+                   "+r"(b[3]), "+r"(b[4]), "+r"(b[5]), "+r"(b[6]), "+r"(b[7]), "+r"(b[8]), "+r"(b[9]),
+                   "+r"(b[10]), "+r"(b[11]), "+r"(b[12]), "+r"(b[13]), "+r"(b[14]), "+r"(b[15]), "+r"(b[16]),
+                   "+r"(b[17]), "+r"(b[18]), "+r"(b[19]), "+r"(b[20]), "+r"(b[21]), "+r"(b[22]), "+r"(b[23]),
+                   "+r"(b[24]), "+r"(b[25]), "+r"(b[26]), "+r"(b[27]), "+r"(b[28]), "+r"(b[29]), "+r"(b[30]),
+                   "+r"(b[31])
+                 :
+                 : "memory");
+}
+
+// Rare pass of one 32-column chunk (warp-collective: every lane calls it):
+// reload the cross terms (still in TMEM at taddr) into this thread's column
+// of the staging buffer, then each thread visits its own candidates of
+// `mask`.  Staging is per thread, so no cross-lane ordering is needed.
+__device__ __forceinline__ void rare_chunk(uint32_t taddr, uint32_t mask, const int (&od)[4], const float4 (&dc)[4],
+                                           float *xcol, int stride, const RangeEpi &re, const EpiConst &ec,
+                                           ListState &L, int *tbest_r)
+{
+    uint32_t tx[32];
+    tmem_ld32(taddr, tx);
+    tmem_wait(tx);
+#pragma unroll
+    for (int j = 0; j < 32; ++j) xcol[j * stride] = __uint_as_float(tx[j]);
+    if (mask) {
+        epi_rare(xcol, stride, od, dc, re, ec, L, mask);
+        if (L.T < L.Tpub) {
+            atomicMin(tbest_r, f2ord(L.T));
+            L.Tpub = L.T;
+        }
+    }
+    __syncwarp();
+}
+
 struct TcMaps {
     CUtensorMap a128, a32, b128, b32;
 };
@@ -205,8 +246,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     uint8_t *sA = smem;
     uint8_t *sB = smem + A_BYTES;  // A_BYTES is a multiple of 1024
     constexpr int ET = 32 * EPI_WARPS;                                // epilogue threads
-    float *ksm = reinterpret_cast<float *>(sB + STAGES * B_BYTES);  // [32][ET] keys (rare pass)
-    float *xsm = ksm + 32 * ET;                                     // [32][ET] cross terms (rare pass)
+    float *xsm = reinterpret_cast<float *>(sB + STAGES * B_BYTES);  // [32][ET] cross terms (rare pass)
     float4 *dcs = reinterpret_cast<float4 *>(xsm + 32 * ET);        // [EPI_WARPS][8] domain constants
     __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], a_bar, tfull_bar[NACC], tempty_bar[NACC];
     __shared__ uint32_t tmem_base_s;
@@ -230,7 +270,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     if (threadIdx.x == 0) {
         // self-checks: every TMA box and MMA operand must lie inside this CTA's
         // dynamic shared memory, and every box inside the padded operands
-        const uint32_t used = (uint32_t)(smem - smem_raw) + A_BYTES + STAGES * B_BYTES + 2 * 32 * ET * 4 +
+        const uint32_t used = (uint32_t)(smem - smem_raw) + A_BYTES + STAGES * B_BYTES + 32 * ET * 4 +
                               EPI_WARPS * 8 * 16 + EPI_WARPS * 8 * 4;
         int bad = 0;
         if (used > smem_bytes) bad = 2;
@@ -386,55 +426,57 @@ __global__ void __launch_bounds__(THREADS, 1)
             if (!__all_sync(0xffffffffu, mbar_wait(&tfull_bar[acc], (it / NACC) & 1, &abort_s, err))) break;
             tc_fence_after();
             const uint32_t taddr = lane_addr + acc * BN;
-#pragma unroll 1
-            for (int ch = 0; ch < EPI_COLS / 32; ++ch) {
-                uint32_t cur[32];
-                tmem_ld32(taddr + ch * 32, cur);
-                tmem_wait(cur);
-                const int c0 = n0 + ch * 32;
-                const int nvalid = min(32, ncol - c0);
-                float X[32];
+            // both 32-column chunks of this warp's half tile at once (one load
+            // latency per tile)
+            float Xa[32], Xb[32];
+            {
+                uint32_t ua[32], ub[32];
+                tmem_ld32(taddr, ua);
+                tmem_ld32(taddr + 32, ub);
+                tmem_wait2(ua, ub);
 #pragma unroll
-                for (int j = 0; j < 32; ++j) X[j] = __uint_as_float(cur[j]);
-                int od[4];
+                for (int j = 0; j < 32; ++j) {
+                    Xa[j] = __uint_as_float(ua[j]);
+                    Xb[j] = __uint_as_float(ub[j]);
+                }
+            }
+            const int nva = min(32, ncol - n0), nvb = min(32, ncol - n0 - 32);
+            int oda[4], odb[4];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) od[q] = wod[ch * 4 + q];
-                if (dump) {
+            for (int q = 0; q < 4; ++q) {
+                oda[q] = wod[q];
+                odb[q] = wod[4 + q];
+            }
+            if (dump) {
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    if (live && j < nva) dump[(size_t)r * g.N + oda[j >> 3] * 8 + (j & 7)] = Xa[j];
+                    if (live && j < nvb) dump[(size_t)r * g.N + odb[j >> 3] * 8 + (j & 7)] = Xb[j];
+                }
+            } else {
+                if (nva < 32) {
 #pragma unroll
                     for (int j = 0; j < 32; ++j)
-                        if (live && j < nvalid) dump[(size_t)r * g.N + od[j >> 3] * 8 + (j & 7)] = X[j];
-                    continue;
+                        if (j >= nva) Xa[j] = __int_as_float(0x7fc00000);  // NaN: never listed
                 }
-                if (nvalid < 32) {
+                if (nvb < 32) {
 #pragma unroll
                     for (int j = 0; j < 32; ++j)
-                        if (j >= nvalid) X[j] = __int_as_float(0x7fc00000);  // NaN: never listed
+                        if (j >= nvb) Xb[j] = __int_as_float(0x7fc00000);
                 }
-                float4 dc[4];
+                float4 dca[4], dcb[4];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) dc[q] = wdc[ch * 4 + q];
-                const bool need = scr && nvalid > 0 &&
-                                  epi_keys32(X, dc, re.zb, re.rho_lim, ec, fminf(L.key[kListK - 1], L.tw),
-                                             L.has_zero ? kZeroPenalty : 0.0f);
-                if (__any_sync(0xffffffffu, need)) {
-                    // stage keys, reload the cross terms (still in TMEM), then each
-                    // thread walks its own row
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) ksm[j * ET + et] = X[j];
-                    uint32_t tx[32];
-                    tmem_ld32(taddr + ch * 32, tx);
-                    tmem_wait(tx);
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) xsm[j * ET + et] = __uint_as_float(tx[j]);
-                    if (need) {
-                        epi_rare(ksm + et, ET, xsm + et, ET, od, dc, re, ec, L, nvalid);
-                        if (L.T < L.Tpub) {
-                            atomicMin(tbest + r, f2ord(L.T));
-                            L.Tpub = L.T;
-                        }
-                    }
-                    __syncwarp();
+                for (int q = 0; q < 4; ++q) {
+                    dca[q] = wdc[q];
+                    dcb[q] = wdc[4 + q];
                 }
+                const float thr = fminf(L.key[kListK - 1], L.tw);
+                const float zp = L.has_zero ? kZeroPenalty : 0.0f;
+                const uint32_t ma = scr && nva > 0 ? epi_keys32(Xa, dca, re.zb, re.rho_lim, ec, thr, zp) : 0u;
+                const uint32_t mb = scr && nvb > 0 ? epi_keys32(Xb, dcb, re.zb, re.rho_lim, ec, thr, zp) : 0u;
+                if (__any_sync(0xffffffffu, ma != 0u)) rare_chunk(taddr, ma, oda, dca, xsm + et, ET, re, ec, L, tbest + r);
+                if (__any_sync(0xffffffffu, mb != 0u))
+                    rare_chunk(taddr + 32, mb, odb, dcb, xsm + et, ET, re, ec, L, tbest + r);
             }
             tc_fence_before();
             __syncwarp();
@@ -500,7 +542,7 @@ size_t search_tc_smem(const Geometry &g)
 {
     const int nblk = g.split_hilo ? 2 : 1;
     return 1024 + (size_t)(nblk * BM * 128 + BM * 32) + (size_t)STAGES * (nblk * BN * 128 + BN * 32) +
-           2 * 32 * (32 * EPI_WARPS) * 4 + EPI_WARPS * 8 * 16 + EPI_WARPS * 8 * 4;
+           32 * (32 * EPI_WARPS) * 4 + EPI_WARPS * 8 * 16 + EPI_WARPS * 8 * 4;
 }
 
 int search_tc_lists_per_split() { return 2; }
