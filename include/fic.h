@@ -90,6 +90,12 @@ typedef struct {
  * per range and are represented by the first of them.  The maps are the same
  * either way; this flag exists to measure and test the dense search. */
 #define FIC_FLAG_DENSE 0x2u
+/* fic_params.flags: resolve every screened range by the exact exhaustive
+ * scan (integer cross terms and exact code decisions over all 8*D
+ * candidates) instead of certifying the screened lists.  The maps are the
+ * same, each flagged FIC_MAP_FALLBACK; this flag exists to test that scan and
+ * to time it. */
+#define FIC_FLAG_EXACT_SCAN 0x4u
 
 /* One map per range: range -> (domain, symmetry, s, o) and its collage error. */
 typedef struct {

@@ -40,7 +40,7 @@ size_t align_up(size_t v) { return (v + kAlign - 1) & ~(kAlign - 1); }
 int check_params(const fic_params *p)
 {
     if (!p) return FIC_ERR_BAD_ARG;
-    if (p->flags & ~(FIC_FLAG_PHASE_TIMING | FIC_FLAG_DENSE)) return FIC_ERR_BAD_ARG;
+    if (p->flags & ~(FIC_FLAG_PHASE_TIMING | FIC_FLAG_DENSE | FIC_FLAG_EXACT_SCAN)) return FIC_ERR_BAD_ARG;
     if (p->range_size != 4 && p->range_size != 8 && p->range_size != 16) return FIC_ERR_BAD_ARG;
     if (p->domain_stride < 1) return FIC_ERR_BAD_ARG;
     if (p->bit_depth < 1 || p->bit_depth > 12) return FIC_ERR_BITDEPTH;
@@ -86,6 +86,7 @@ int make_geometry(int w, int h, int pitch, const fic_params *p, Geometry &g)
     const long long Gnum = 4LL * g.Ls * g.m * g.P;
     g.mod_g = (Gnum % g.Lo) == 0 ? 1 : 0;
     g.G = (double)Gnum / g.Lo;
+    g.Gi = g.mod_g ? (int)(Gnum / g.Lo) : 0;
     return FIC_OK;
 }
 
@@ -114,6 +115,8 @@ EpiConst make_epi(const Geometry &g)
     ec.invm = (float)(1.0 / g.m);
     ec.pmax = (float)g.P - 0.5f;
     ec.near_slack = (float)((32.0 * g.Ls * g.Ls + 16.0 * g.Ls) * 5.9604644775390625e-08);  // 2^-24
+    const double dd = 4.0 * g.Ls * g.Lo;
+    ec.invD2_up = std::nextafter((float)(1.0 / (dd * dd)), INFINITY);
     return ec;
 }
 
@@ -376,9 +379,10 @@ int run_encode(const void *img, int w, int h, int pitch_px, const fic_params *p,
         if (!dump) {
             FIC_CUDA(launch_rescore(gd, ec, ri, di, bblk, qblk, lists, n_lists, cbuf.counts, cbuf.act, cbuf.rkeep,
                                     lists_per_split(search), search == FIC_SEARCH_TC ? search_tc_tile() : 64, target,
-                                    n_split, sm_count(), winner, fb_list, fb_count, st));
+                                    n_split, sm_count(), (p->flags & FIC_FLAG_EXACT_SCAN) ? 1 : 0, winner, fb_list,
+                                    fb_count, partial, st));
             FIC_MARK(3);
-            FIC_CUDA(launch_fallback(gd, ri, di, bblk, qblk, fb_list, fb_count, partial, winner, st));
+            FIC_CUDA(launch_fallback(gd, ri, di, bblk, qblk, fb_list, fb_count, partial, winner, sm_count(), st));
             FIC_MARK(4);
             FIC_CUDA(launch_finalize(gd, ri, di, bblk, qblk, winner, err, dmaps, st));
             FIC_MARK(5);

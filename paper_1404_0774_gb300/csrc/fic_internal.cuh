@@ -47,6 +47,7 @@ struct Geometry {
     int split_hilo;    // 1 when q' must be split into two exact FP16 parts
     int KP;            // FP16 operand row length (tensor-core layout)
     int mod_g;         // 1 when G is an integer (z may be reduced mod G)
+    int Gi;            // G when mod_g (< 2^31), else 0
     double G;          // 4*Ls*m*P/Lo
 };
 
@@ -84,6 +85,7 @@ struct EpiConst {
     float sqrtm4;       // sqrt(m)/4
     float inv4ls, invm, pmax;  // 1/(4*Ls), 1/m, P (offset clamp detection)
     float near_slack;   // kappa * near_slack bounds how far below c*y the key of the other code can fall
+    float invD2_up;     // FP32 upper bound of 1/(4*Ls*Lo)^2 (exact residuals are integers / D^2)
 };
 
 // Per-thread constants of the range the thread screens.
@@ -438,11 +440,12 @@ cudaError_t launch_rescore(const Geometry &g, const EpiConst &ec, const RangeInf
                            const DomainInfo *di, const uint16_t *bblk, const uint16_t *qblk,
                            const ListEntry *lists, int max_lists, const int *counts, const int *act,
                            const int *rkeep, int lists_per_split, int col_tile, int target, int max_split, int n_sm,
-                           uint32_t *winner, int *fb_list, int *fb_count, cudaStream_t st);
+                           int exact_scan, uint32_t *winner, int *fb_list, int *fb_count, void *partial,
+                           cudaStream_t st);
 size_t fallback_partial_bytes(const Geometry &g);
 cudaError_t launch_fallback(const Geometry &g, const RangeInfo *ri, const DomainInfo *di,
                             const uint16_t *bblk, const uint16_t *qblk, const int *fb_list,
-                            const int *fb_count, void *partial, uint32_t *winner, cudaStream_t st);
+                            const int *fb_count, void *partial, uint32_t *winner, int n_sm, cudaStream_t st);
 cudaError_t launch_finalize(const Geometry &g, const RangeInfo *ri, const DomainInfo *di,
                             const uint16_t *bblk, const uint16_t *qblk, const uint32_t *winner,
                             const int *err, fic_map *maps, cudaStream_t st);

@@ -48,7 +48,7 @@ __device__ __forceinline__ void range_stats(const Geometry &g, const EpiConst &e
     }
     // centre: nearest integer to the mean, kept within 2048 of every pixel so
     // that b - c_r is an exact FP16 integer
-    long long cr = (2 * Sb + g.m) / (2 * (long long)g.m);
+    long long cr = (2 * Sb + g.m) >> (2 * g.ln + 1);  // m = 2^(2 ln), Sb >= 0
     cr = max((long long)(bmax - 2048), min((long long)(bmin + 2048), cr));
     const int c_r = (int)cr;
     const int e_r = (int)(Sb - (long long)g.m * c_r);
@@ -61,7 +61,7 @@ __device__ __forceinline__ void range_stats(const Geometry &g, const EpiConst &e
             bp2i += (long long)bc * bc;
         }
     }
-    const double bp2 = (double)warp_sum_ll(bp2i);
+    const float bp2f = __ll2float_rn(warp_sum_ll(bp2i));
     if (lane != 0) return;
     // per-range constants: integer arithmetic and FP32 only (the FP64 rate of
     // this part is a small fraction of FP32)
@@ -72,9 +72,8 @@ __device__ __forceinline__ void range_stats(const Geometry &g, const EpiConst &e
     info.e_r = e_r;
     const float invm = 1.0f / (float)g.m;
     info.sbbc = (float)((long long)g.m * Sbb - Sb * Sb) * invm;
-    const long long z = 4LL * g.Ls * Sb;
-    info.zb = (float)(g.mod_g ? z % (long long)g.G : z);
-    const float bp2f = (float)bp2;
+    const int z = 4 * g.Ls * (int)Sb;  // < 2^31 for B <= 12, m <= 256, s_bits <= 8
+    info.zb = (float)(g.mod_g ? z % g.Gi : z);
     info.bp2 = bp2f;
     // FP32 error of Ls*s: ~1e-6 when the cross term is exact, plus the
     // accumulation error of high-variance pairs (grows with sum (b-c_r)^2)
@@ -126,7 +125,7 @@ __device__ __forceinline__ void domain_stats(const Geometry &g, const void *img,
     Sqq = warp_sum_ll(Sqq);
     if (lane != 0) return;
     const int m = g.m;
-    const long long cd = (2 * Sq + m) / (2 * (long long)m);
+    const long long cd = (2 * Sq + m) >> (2 * g.ln + 1);  // m = 2^(2 ln), Sq >= 0
     const long long den = (long long)m * Sqq - Sq * Sq;
     DomainInfo info;
     info.Sq = Sq;
@@ -140,7 +139,7 @@ __device__ __forceinline__ void domain_stats(const Geometry &g, const void *img,
     float4 c4;
     const float denf = (float)den;
     c4.x = den > 0 ? (2.0f * m) / denf : 0.0f;
-    c4.y = (float)(g.mod_g ? Sq % (long long)g.G : Sq);
+    c4.y = (float)(g.mod_g ? (int)Sq % g.Gi : (int)Sq);
     c4.z = denf / (8.0f * m * g.Ls);
     c4.w = (float)Sq;
     dconst[d] = c4;
@@ -165,12 +164,15 @@ __global__ void __launch_bounds__(256) k_stats(Geometry g, EpiConst ec, const vo
 
 // Stable compaction of the flagged items, block 0 over the ranges and block 1
 // over the domains: the kept indices in their original order, cnt[0] = how
-// many, cnt[1] = the first unflagged index (-1 if none).  Rounds of 1024
-// items: warp ballots, a scan of the 32 warp counts, a running base.
+// many, cnt[1] = the first unflagged index (-1 if none).  Passes of
+// 16 x 1024 items: every flag of a pass is loaded up front (one memory
+// latency), warp ballots give per-(round, warp) counts, one warp scans those
+// 512 counts in item order, and every thread scatters its kept items.
+constexpr int kCompactRounds = 16;
 __global__ void __launch_bounds__(1024) k_compact(int nr, const int *rflag, int *ract, int *rcnt, int nd,
                                                   const int *dflag, int *dact, int *dcnt)
 {
-    __shared__ int wsum[32];
+    __shared__ int off_s[kCompactRounds * 32];
     __shared__ int base_s, first_s;
     const bool dom = blockIdx.x == 1;
     const int n = dom ? nd : nr;
@@ -183,31 +185,52 @@ __global__ void __launch_bounds__(1024) k_compact(int nr, const int *rflag, int 
         first_s = 0x7fffffff;
     }
     int fu = 0x7fffffff;
-    __syncthreads();
-    for (int i0 = 0; i0 < n; i0 += 1024) {
-        const int i = i0 + t;
-        const bool in = i < n;
-        const bool f = in && flag[i] != 0;
-        if (in && !f) fu = min(fu, i);
-        const unsigned b = __ballot_sync(0xffffffffu, f);
-        if (lane == 0) wsum[w] = __popc(b);
-        __syncthreads();
-        if (w == 0) {
-            const int v = wsum[lane];
-            int x = v;
-            for (int off = 1; off < 32; off <<= 1) {
-                const int y = __shfl_up_sync(0xffffffffu, x, off);
-                if (lane >= off) x += y;
-            }
-            wsum[lane] = x - v;  // exclusive prefix of the warp counts
+    for (int c0 = 0; c0 < n; c0 += 1024 * kCompactRounds) {
+        bool f[kCompactRounds];
+#pragma unroll
+        for (int q = 0; q < kCompactRounds; ++q) {
+            const int i = c0 + q * 1024 + t;
+            f[q] = i < n && flag[i] != 0;
+            if (i < n && !f[q]) fu = min(fu, i);
+        }
+        unsigned b[kCompactRounds];
+#pragma unroll
+        for (int q = 0; q < kCompactRounds; ++q) {
+            b[q] = __ballot_sync(0xffffffffu, f[q]);
+            if (lane == 0) off_s[q * 32 + w] = __popc(b[q]);
         }
         __syncthreads();
-        const int base = base_s, wbase = wsum[w];
-        if (f) list[base + wbase + __popc(b & ((1u << lane) - 1u))] = i;
-        __syncthreads();  // every thread has read base_s and wsum
-        if (t == 1023) base_s = base + wbase + __popc(b);
+        if (w == 0) {
+            // exclusive scan of the 512 counts in item order; lane l owns
+            // entries [16 l, 16 l + 16)
+            int v[16], sum = 0;
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                v[q] = off_s[16 * lane + q];
+                sum += v[q];
+            }
+            int x = sum;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            const int base = base_s;
+            int run = base + x - sum;
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                off_s[16 * lane + q] = run;
+                run += v[q];
+            }
+            __syncwarp();
+            if (lane == 31) base_s = base + x;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < kCompactRounds; ++q)
+            if (f[q]) list[off_s[q * 32 + w] + __popc(b[q] & ((1u << lane) - 1u))] = c0 + q * 1024 + t;
+        __syncthreads();  // off_s is rewritten by the next pass
     }
-    for (int off = 16; off > 0; off >>= 1) fu = min(fu, __shfl_xor_sync(0xffffffffu, fu, off));
+    for (int o = 16; o > 0; o >>= 1) fu = min(fu, __shfl_xor_sync(0xffffffffu, fu, o));
     if (lane == 0) atomicMin(&first_s, fu);
     __syncthreads();
     if (t == 0) {
@@ -248,14 +271,18 @@ __device__ __forceinline__ void range_row(const Geometry &g, const RangeInfo *ri
     }
 }
 
-// Candidate rows 8j+k of the domain dact[j]: output pixel (y,x) of S_k(tau(d))
-// is q at sym_src, centred by c_d.  FP16 row (tensor-core layout):
-// [128*hi | lo (12-bit only) | -1024 f_d/m, -f_d/m, 0...] with q - c_d =
-// 128*hi + lo, written as 16-byte chunks (KP and m are multiples of 8, so a
-// chunk never straddles two parts).  Domain constants in the same order.
+// Candidate rows 8j+k of the domain dact[j]: output pixel i = (y,x) of
+// S_k(tau(d)) is q at src_s[k][i], centred by c_d.  FP16 row (tensor-core
+// layout): [128*hi | lo (12-bit only) | -1024 f_d/m, -f_d/m, 0...] with
+// q - c_d = 128*hi + lo.  The warp converts the domain's m values once into
+// FP16 bit patterns in shared memory, then assembles 16-byte chunks of the 8
+// rows by gathering (KP and m are multiples of 8, so a chunk never straddles
+// two parts).  Domain constants in the same order.
 __device__ __forceinline__ void domain_rows_warp(const Geometry &g, const DomainInfo *di, const uint16_t *qblk,
-                                                 const float4 *dconst, int j, int d, int lane, int16_t *qc_s,
-                                                 float *cb32, __half *cb16, float4 *dconst_c, int *dmap)
+                                                 const float4 *dconst, int j, int d, int lane,
+                                                 const uint8_t (*src_s)[kMaxM], const uint16_t *kc_s,
+                                                 uint16_t *hi_s, uint16_t *lo_s, float *cb32, __half *cb16,
+                                                 float4 *dconst_c, int *dmap)
 {
     const int m = g.m;
     const DomainInfo info = di[d];
@@ -264,69 +291,84 @@ __device__ __forceinline__ void domain_rows_warp(const Geometry &g, const Domain
         dconst_c[j] = dconst[d];
         dmap[j] = d;
     }
-    for (int i = lane; i < m; i += 32) qc_s[i] = (int16_t)((int)qblk[(size_t)d * m + i] - c_d);
-    __syncwarp();
-    if (cb32) {
-        for (int k = 0; k < 8; ++k) {
-            const SymFlags sf = sym_flags(k, g.n);
-            for (int i = lane; i < m; i += 32)
-                cb32[((size_t)j * 8 + k) * m + i] = (float)qc_s[sym_src_index(sf, g.ln, i >> g.ln, i & (g.n - 1))];
+    for (int i = lane; i < m; i += 32) {
+        const int qc = (int)qblk[(size_t)d * m + i] - c_d;
+        if (cb32) {
+            lo_s[i] = (uint16_t)(qc + 32768);  // SIMT operand: centred value, biased
+        } else if (g.split_hilo) {
+            const int hi = (qc + 64) >> 7;  // floor; |hi| <= 128
+            hi_s[i] = __half_as_ushort(__int2half_rn(128 * hi));
+            lo_s[i] = __half_as_ushort(__int2half_rn(qc - 128 * hi));
+        } else {
+            hi_s[i] = __half_as_ushort(__int2half_rn(qc));
         }
     }
-    if (cb16) {
-        const int nch = g.KP >> 3;  // 16-byte chunks per row
-        const int base = g.split_hilo ? 2 * m : m;
-        const __half t0 = __float2half_rn(-1024.0f * (float)fd / (float)m);
-        const __half t1 = __float2half_rn(-(float)fd / (float)m);
-        for (int e = lane; e < 8 * nch; e += 32) {
-            const int k = e / nch, c = e - k * nch;
-            const int col0 = 8 * c;
-            __half h[8];
-            if (col0 >= base) {
+    __syncwarp();
+    if (cb32) {
+        for (int k = 0; k < 8; ++k)
+            for (int i = lane; i < m; i += 32)
+                cb32[((size_t)j * 8 + k) * m + i] = (float)((int)lo_s[src_s[k][i]] - 32768);
+        return;
+    }
+    const int nch = g.KP >> 3;  // 16-byte chunks per row
+    const int base = g.split_hilo ? 2 * m : m;
+    const uint32_t t0 = __half_as_ushort(__float2half_rn(-1024.0f * (float)fd / (float)m));
+    const uint32_t t1 = __half_as_ushort(__float2half_rn(-(float)fd / (float)m));
+    for (int e = lane; e < 8 * nch; e += 32) {
+        const int kc = kc_s[e];
+        const int k = kc >> 8, c = kc & 255;
+        const int col0 = 8 * c;
+        uint32_t h[8];
+        if (col0 >= base) {
 #pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const int tc = col0 + u - base;
-                    h[u] = tc == 0 ? t0 : (tc == 1 ? t1 : __float2half_rn(0.0f));
-                }
-            } else {
-                const SymFlags sf = sym_flags(k, g.n);
-                const bool lo_part = col0 >= m;  // second copy (12-bit only)
-                const int p0 = lo_part ? col0 - m : col0;
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const int i = p0 + u;
-                    const int qc = qc_s[sym_src_index(sf, g.ln, i >> g.ln, i & (g.n - 1))];
-                    if (g.split_hilo) {
-                        const int hi = (qc + 64) >> 7;  // floor; |hi| <= 128
-                        h[u] = lo_part ? __int2half_rn(qc - 128 * hi) : __int2half_rn(128 * hi);
-                    } else {
-                        h[u] = __int2half_rn(qc);
-                    }
-                }
+            for (int u = 0; u < 8; ++u) {
+                const int tc = col0 + u - base;
+                h[u] = tc == 0 ? t0 : (tc == 1 ? t1 : 0u);
             }
-            const uint4 v = make_uint4(pack_h2(h[0], h[1]), pack_h2(h[2], h[3]), pack_h2(h[4], h[5]),
-                                       pack_h2(h[6], h[7]));
-            reinterpret_cast<uint4 *>(cb16 + ((size_t)j * 8 + k) * g.KP)[c] = v;
+        } else {
+            const bool lo_part = col0 >= m;  // second copy (12-bit only)
+            const uint16_t *vs = lo_part ? lo_s : hi_s;
+            const uint8_t *sk = src_s[k] + (lo_part ? col0 - m : col0);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) h[u] = vs[sk[u]];
         }
+        const uint4 v = make_uint4(h[0] | (h[1] << 16), h[2] | (h[3] << 16), h[4] | (h[5] << 16),
+                                   h[6] | (h[7] << 16));
+        reinterpret_cast<uint4 *>(cb16 + ((size_t)j * 8 + k) * g.KP)[c] = v;
     }
 }
 
 // Operand rows of the kept ranges (blocks [0, rb), a warp per row) and of the
-// kept domains (the blocks after, a warp per domain), one launch.
-__global__ void __launch_bounds__(256) k_rows(Geometry g, int rb, const RangeInfo *ri, const uint16_t *bblk,
+// kept domains (the blocks after, a warp per domain), one launch.  Domain
+// blocks first build the symmetry source table src_s[k][i] and the (row,
+// chunk) table of their 16-byte chunks.
+__global__ void __launch_bounds__(256, 4) k_rows(Geometry g, int rb, const RangeInfo *ri, const uint16_t *bblk,
                                               const DomainInfo *di, const uint16_t *qblk, const float4 *dconst,
                                               const int *act, const int *dact, const int *counts, float *rs32,
                                               __half *ra16, float *cb32, __half *cb16, float4 *dconst_c, int *dmap)
 {
-    __shared__ int16_t qc_s[8][kMaxM];
+    __shared__ uint8_t src_s[8][kMaxM];
+    __shared__ uint16_t kc_s[8 * ((2 * kMaxM + 16) / 8)];
+    __shared__ uint16_t hi_s[8][kMaxM], lo_s[8][kMaxM];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     if ((int)blockIdx.x < rb) {
         const int j = blockIdx.x * 8 + w;
         if (j < counts[0]) range_row(g, ri, bblk, j, act[j], lane, rs32, ra16);
-    } else {
-        const int j = (blockIdx.x - rb) * 8 + w;
-        if (j < counts[2]) domain_rows_warp(g, di, qblk, dconst, j, dact[j], lane, qc_s[w], cb32, cb16, dconst_c, dmap);
+        return;
     }
+    const int j0 = (blockIdx.x - rb) * 8;
+    if (j0 >= counts[2]) return;  // block-uniform
+    for (int e = threadIdx.x; e < 8 * g.m; e += blockDim.x) {
+        const int k = e >> (2 * g.ln), i = e & (g.m - 1);
+        src_s[k][i] = (uint8_t)sym_src_index(sym_flags(k, g.n), g.ln, i >> g.ln, i & (g.n - 1));
+    }
+    const int nch = g.KP >> 3;
+    for (int e = threadIdx.x; e < 8 * nch; e += blockDim.x) kc_s[e] = (uint16_t)(((e / nch) << 8) | (e % nch));
+    __syncthreads();
+    const int j = j0 + w;
+    if (j < counts[2])
+        domain_rows_warp(g, di, qblk, dconst, j, dact[j], lane, src_s, kc_s, hi_s[w], lo_s[w], cb32, cb16, dconst_c,
+                         dmap);
 }
 
 cudaError_t launch_prep(const Geometry &g, const void *img, const EpiConst &ec, int dense, RangeInfo *ri,

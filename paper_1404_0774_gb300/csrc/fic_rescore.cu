@@ -94,18 +94,15 @@ __device__ __forceinline__ double u128_to_double(unsigned __int128 v)
     return (double)(unsigned long long)(v >> 64) * 18446744073709551616.0 + (double)(unsigned long long)v;
 }
 
-// Exact residual (times D^2) of one candidate whose cross term is X.
-__device__ unsigned __int128 exact_candidate(const Geometry &g, Stats st, const DomainInfo *di, uint32_t idx,
-                                             long long X)
+// An FP32 value >= v (v an unsigned 128-bit integer below 2^127): the top 64
+// significant bits, or-ed with 1 so that a discarded remainder always rounds
+// the conversion up past them, converted upward and scaled exactly.
+__device__ __forceinline__ float u128_to_float_ru(unsigned __int128 v)
 {
-    const DomainInfo dd = di[idx >> 3];
-    st.Sq = dd.Sq;
-    st.Sqq = dd.Sqq;
-    st.X = X;
-    int c, e;
-    double sh, oh;
-    fp64_codes(g, st, c, e, sh, oh);
-    return (unsigned __int128)exact_err(g, st, c, e);
+    const unsigned long long hi = (unsigned long long)(v >> 64);
+    if (hi == 0) return __ull2float_ru((unsigned long long)v);
+    const int sh = 64 - __clzll(hi);
+    return ldexpf(__ull2float_ru((unsigned long long)(v >> sh) | 1ull), sh);
 }
 
 // round half away from zero of num/den (den > 0), exactly: an FP32 estimate
@@ -239,7 +236,8 @@ __device__ __forceinline__ void rescore_range(const Geometry &g, const EpiConst 
                                               const DomainInfo *di, const uint16_t *bblk, const uint16_t *qblk,
                                               const ListEntry *lists, int max_lists, const int *counts,
                                               int lists_per_split, int col_tile, int target, int max_split,
-                                              uint32_t *winner, int *fb_list, int *fb_count, int r, int *bk)
+                                              int exact_scan, uint32_t *winner, int *fb_list, int *fb_count, int r,
+                                              int *bk)
 {
     const int lane = threadIdx.x & 31;
     const RangeInfo rin = ri[r];
@@ -272,7 +270,7 @@ __device__ __forceinline__ void rescore_range(const Geometry &g, const EpiConst 
             ib = oi;
         }
     }
-    if (ib == 0xffffffffu) {  // no candidate was listed: exact rescan
+    if (ib == 0xffffffffu || exact_scan) {  // no candidate was listed (or asked): exact scan
         if (lane == 0) {
             winner[r] = 0xffffffffu;
             fb_list[atomicAdd(fb_count, 1)] = r;
@@ -282,8 +280,6 @@ __device__ __forceinline__ void rescore_range(const Geometry &g, const EpiConst 
     Stats st;
     st.Sb = rin.Sb;
     st.Sbb = rin.Sbb;
-    const double invD2 = 1.0 / ((double)(4 * g.Ls * g.Lo) * (double)(4 * g.Ls * g.Lo));
-    const double two_ls = 2.0 * g.Ls;
     // Flat domains were not screened: all their candidates have s = 0 and the
     // same residual, so only the first of them, (first flat domain, k = 0), can
     // win; it is a finalist of every range.  Its cross term is computed
@@ -297,15 +293,15 @@ __device__ __forceinline__ void rescore_range(const Geometry &g, const EpiConst 
         ue = exact_rational(g, st, di[ib >> 3], X);  // integer work, same on every lane
         fe = dflat >= 0 ? exact_rational(g, st, di[dflat], Xf) : ~(unsigned __int128)0;
     }
-    const double U = u128_to_double(ue) * invD2;
-    // screening error allowance (the epilogue's), converted to residual units;
-    // evaluated at the largest key that can still matter
+    // U rounded up; every threshold below is an FP32 bound rounded outward
+    const float U = __fmul_ru(u128_to_float_ru(ue), ec.invD2_up);
+    // screening error allowance (the epilogue's), evaluated at the largest key
+    // that can still matter
     const RangeEpi re = range_epi(rin, ec);
-    const double sbbc = (double)rin.sbbc;
-    const float kreach = (float)((U - sbbc) * two_ls);
+    const float kreach = __fmul_ru(__fsub_ru(U, rin.sbbc), ec.two_ls);
     const float beta_k = fmaxf(beta_key(re, kb, ec), beta_key(re, fmaxf(kb, kreach), ec));
     // finalist: sbbc + key/(2Ls) - beta/(2Ls) <= U  <=>  key <= (U - sbbc)*2Ls + beta
-    const float kfin = __double2float_ru((U - sbbc) * two_ls + (double)beta_k);
+    const float kfin = __fadd_ru(kreach, beta_k);
 
     unsigned __int128 best_e = ue;
     uint32_t best_i = ib;
@@ -343,9 +339,10 @@ __device__ __forceinline__ void rescore_range(const Geometry &g, const EpiConst 
         }
     }
     warp_argmin(best_e, best_i);
-    const double Estar = u128_to_double(best_e) * invD2;
-    // certified list: sbbc + (last - beta(last))/(2Ls) > E*(1 + 1e-12) + 1e-12
-    const float kcert = __double2float_ru((Estar * (1.0 + 1e-12) + 1e-12 - sbbc) * two_ls);
+    // certified list: sbbc + (last - beta(last))/(2Ls) > E*, tested as
+    // round-down(last - beta) > round-up((E* - sbbc) * 2Ls)
+    const float Estar = __fmul_ru(u128_to_float_ru(best_e), ec.invD2_up);
+    const float kcert = __fmul_ru(__fsub_ru(Estar, rin.sbbc), ec.two_ls);
     bool cert = true;
     for (int l = lane; l < n_lists; l += 32) {
         // a full list's unlisted candidates have residual >= its last key less
@@ -368,17 +365,19 @@ __device__ __forceinline__ void rescore_range(const Geometry &g, const EpiConst 
 __global__ void __launch_bounds__(32 * kRescoreWarps, 4)
     k_rescore(Geometry g, EpiConst ec, const RangeInfo *ri, const DomainInfo *di, const uint16_t *bblk,
               const uint16_t *qblk, const ListEntry *lists, int max_lists, const int *counts, const int *act,
-              const int *rkeep, int lists_per_split, int col_tile, int target, int max_split, uint32_t *winner,
-              int *fb_list, int *fb_count)
+              const int *rkeep, int lists_per_split, int col_tile, int target, int max_split, int exact_scan,
+              uint32_t *winner, int *fb_list, int *fb_count, int *fb_done)
 {
     extern __shared__ int bk_all[];  // [warps][8][m+1]
-    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < g.R; r += gridDim.x * blockDim.x)
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < g.R; r += gridDim.x * blockDim.x) {
         if (!rkeep[r]) winner[r] = 0;
+        fb_done[r] = 0;  // completion counters of the exact fallback
+    }
     int *bk = bk_all + (threadIdx.x >> 5) * 8 * (g.m + 1);
     const int nkept = counts[0];
     for (int j = blockIdx.x * kRescoreWarps + (threadIdx.x >> 5); j < nkept; j += gridDim.x * kRescoreWarps)
         rescore_range(g, ec, ri, di, bblk, qblk, lists, max_lists, counts, lists_per_split, col_tile, target,
-                      max_split, winner, fb_list, fb_count, act[j], bk);
+                      max_split, exact_scan, winner, fb_list, fb_count, act[j], bk);
 }
 
 struct Partial {
@@ -386,22 +385,27 @@ struct Partial {
     uint32_t idx, pad;
 };
 
-// Exhaustive exact scan of the ranges that failed certification.  Each range
-// is split over gridDim.x CTAs (blockIdx.x = candidate chunk); each CTA writes
-// its best (residual, index) to part[slot][chunk].
+// Exhaustive exact scan of the ranges that failed certification, as work
+// items (slot, chunk) over a grid of persistent blocks: an item scans one
+// contiguous chunk of the candidates of range fb_list[slot] with exact integer
+// decisions and writes its best (residual, index); the last item of a slot to
+// finish (counted in done[slot], zeroed by the re-score) reduces the chunks
+// and writes the winner, flagged as resolved by the fallback.
 __global__ void __launch_bounds__(256) k_fallback(Geometry g, const RangeInfo *ri, const DomainInfo *di,
-                                                  const uint16_t *bblk, const uint16_t *qblk,
-                                                  const int *fb_list, const int *fb_count, Partial *part)
+                                                  const uint16_t *bblk, const uint16_t *qblk, const int *fb_list,
+                                                  const int *fb_count, int nch, Partial *part, int *done,
+                                                  uint32_t *winner)
 {
     __shared__ int b_s[kMaxM];
     __shared__ Partial w_s[8];
+    __shared__ int last_s;
     const int count = *fb_count;
-    const int nch = gridDim.x;
-    const int lo = (int)((long long)g.N * blockIdx.x / nch);
-    const int hi = (int)((long long)g.N * (blockIdx.x + 1) / nch);
-    for (int slot = blockIdx.y; slot < count; slot += gridDim.y) {
+    for (int item = blockIdx.x; item < count * nch; item += gridDim.x) {
+        const int slot = item / nch, ch = item - slot * nch;
+        const int lo = (int)((long long)g.N * ch / nch);
+        const int hi = (int)((long long)g.N * (ch + 1) / nch);
         const int r = fb_list[slot];
-        __syncthreads();
+        __syncthreads();  // b_s and w_s of the previous item are no longer read
         for (int i = threadIdx.x; i < g.m; i += blockDim.x) b_s[i] = bblk[(size_t)r * g.m + i];
         __syncthreads();
         const RangeInfo rin = ri[r];
@@ -411,12 +415,15 @@ __global__ void __launch_bounds__(256) k_fallback(Geometry g, const RangeInfo *r
         unsigned __int128 best_e = ~(unsigned __int128)0;
         uint32_t best_i = 0xffffffffu;
         for (int idx = lo + threadIdx.x; idx < hi; idx += blockDim.x) {
-            const int d = idx >> 3, k = idx & 7;
+            const int d = idx >> 3;
+            const SymFlags sf = sym_flags(idx & 7, g.n);
+            const uint16_t *qd = qblk + (size_t)d * g.m;
             unsigned long long X = 0;
-            for (int i = 0; i < g.m; ++i) {
-                int sy, sx;
-                sym_src(k, g.n, i >> g.ln, i & (g.n - 1), sy, sx);
-                X += (unsigned long long)((unsigned)qblk[(size_t)d * g.m + sy * g.n + sx] * (unsigned)b_s[i]);
+            for (int y = 0; y < g.n; ++y) {
+                uint32_t acc = 0;  // one row: n products of at most 4P * P, n <= 16
+                for (int x = 0; x < g.n; ++x)
+                    acc += (uint32_t)qd[sym_src_index(sf, g.ln, y, x)] * (uint32_t)b_s[(y << g.ln) + x];
+                X += acc;
             }
             const unsigned __int128 er = exact_rational(g, st, di[d], (long long)X);
             if (better(er, (uint32_t)idx, best_e, best_i)) {
@@ -426,7 +433,8 @@ __global__ void __launch_bounds__(256) k_fallback(Geometry g, const RangeInfo *r
         }
         warp_argmin(best_e, best_i);
         const int w = threadIdx.x >> 5;
-        if ((threadIdx.x & 31) == 0) w_s[w] = Partial{(unsigned long long)best_e, (unsigned long long)(best_e >> 64), best_i, 0};
+        if ((threadIdx.x & 31) == 0)
+            w_s[w] = Partial{(unsigned long long)best_e, (unsigned long long)(best_e >> 64), best_i, 0};
         __syncthreads();
         if (threadIdx.x == 0) {
             Partial b = w_s[0];
@@ -435,24 +443,30 @@ __global__ void __launch_bounds__(256) k_fallback(Geometry g, const RangeInfo *r
                 const unsigned __int128 eb = ((unsigned __int128)b.hi << 64) | b.lo;
                 if (better(ej, w_s[j].idx, eb, b.idx)) b = w_s[j];
             }
-            part[(size_t)slot * nch + blockIdx.x] = b;
+            part[(size_t)slot * nch + ch] = b;
+            __threadfence();  // the partial is visible before the count says so
+            last_s = atomicAdd(done + slot, 1) == nch - 1;
+            if (last_s) {
+                __threadfence();
+                Partial bb{};
+                bb.lo = __ldcg(&part[(size_t)slot * nch].lo);
+                bb.hi = __ldcg(&part[(size_t)slot * nch].hi);
+                bb.idx = __ldcg(&part[(size_t)slot * nch].idx);
+                for (int j = 1; j < nch; ++j) {
+                    const Partial *pj = part + (size_t)slot * nch + j;
+                    const unsigned long long jl = __ldcg(&pj->lo), jh = __ldcg(&pj->hi);
+                    const uint32_t ji = __ldcg(&pj->idx);
+                    const unsigned __int128 ej = ((unsigned __int128)jh << 64) | jl;
+                    const unsigned __int128 eb = ((unsigned __int128)bb.hi << 64) | bb.lo;
+                    if (better(ej, ji, eb, bb.idx)) {
+                        bb.lo = jl;
+                        bb.hi = jh;
+                        bb.idx = ji;
+                    }
+                }
+                winner[r] = bb.idx | 0x80000000u;  // high bit: resolved by the fallback
+            }
         }
-    }
-}
-
-__global__ void k_fallback_reduce(int nch, const int *fb_list, const int *fb_count, const Partial *part,
-                                  uint32_t *winner)
-{
-    const int count = *fb_count;
-    for (int slot = blockIdx.x * blockDim.x + threadIdx.x; slot < count; slot += gridDim.x * blockDim.x) {
-        Partial b = part[(size_t)slot * nch];
-        for (int j = 1; j < nch; ++j) {
-            const Partial pj = part[(size_t)slot * nch + j];
-            const unsigned __int128 ej = ((unsigned __int128)pj.hi << 64) | pj.lo;
-            const unsigned __int128 eb = ((unsigned __int128)b.hi << 64) | b.lo;
-            if (better(ej, pj.idx, eb, b.idx)) b = pj;
-        }
-        winner[fb_list[slot]] = b.idx | 0x80000000u;  // high bit: resolved by the fallback
     }
 }
 
@@ -543,38 +557,45 @@ __global__ void __launch_bounds__(32 * kFinWarps) k_finalize(Geometry g, const R
     maps[r] = mp;
 }
 
+int *fallback_done(const Geometry &g, void *partial);
+
 cudaError_t launch_rescore(const Geometry &g, const EpiConst &ec, const RangeInfo *ri,
                            const DomainInfo *di, const uint16_t *bblk, const uint16_t *qblk,
                            const ListEntry *lists, int max_lists, const int *counts, const int *act,
                            const int *rkeep, int lists_per_split, int col_tile, int target, int max_split, int n_sm,
-                           uint32_t *winner, int *fb_list, int *fb_count, cudaStream_t st)
+                           int exact_scan, uint32_t *winner, int *fb_list, int *fb_count, void *partial,
+                           cudaStream_t st)
 {
     const size_t smem = sizeof(int) * kRescoreWarps * 8 * (g.m + 1);
     // at most as many blocks as are resident at once (4 per SM at this size)
     const int blocks = std::max(1, std::min((g.R + kRescoreWarps - 1) / kRescoreWarps, 4 * n_sm));
     k_rescore<<<blocks, 32 * kRescoreWarps, smem, st>>>(g, ec, ri, di, bblk, qblk, lists, max_lists, counts, act,
-                                                         rkeep, lists_per_split, col_tile, target, max_split, winner,
-                                                         fb_list, fb_count);
+                                                         rkeep, lists_per_split, col_tile, target, max_split,
+                                                         exact_scan, winner, fb_list, fb_count,
+                                                         fallback_done(g, partial));
     return cudaGetLastError();
 }
 
 int fallback_chunks(const Geometry &g) { return std::min(64, std::max(1, g.N / 1024)); }
 
+// Partial results [R][chunks], then one completion counter per slot.
 size_t fallback_partial_bytes(const Geometry &g)
 {
-    return sizeof(Partial) * (size_t)g.R * fallback_chunks(g);
+    return sizeof(Partial) * (size_t)g.R * fallback_chunks(g) + sizeof(int) * (size_t)g.R;
+}
+
+int *fallback_done(const Geometry &g, void *partial)
+{
+    return reinterpret_cast<int *>(reinterpret_cast<Partial *>(partial) + (size_t)g.R * fallback_chunks(g));
 }
 
 cudaError_t launch_fallback(const Geometry &g, const RangeInfo *ri, const DomainInfo *di,
                             const uint16_t *bblk, const uint16_t *qblk, const int *fb_list,
-                            const int *fb_count, void *partial, uint32_t *winner, cudaStream_t st)
+                            const int *fb_count, void *partial, uint32_t *winner, int n_sm, cudaStream_t st)
 {
     const int nch = fallback_chunks(g);
-    Partial *part = reinterpret_cast<Partial *>(partial);
-    k_fallback<<<dim3(nch, 16), 256, 0, st>>>(g, ri, di, bblk, qblk, fb_list, fb_count, part);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    k_fallback_reduce<<<4, 256, 0, st>>>(nch, fb_list, fb_count, part, winner);
+    k_fallback<<<2 * n_sm, 256, 0, st>>>(g, ri, di, bblk, qblk, fb_list, fb_count, nch,
+                                         reinterpret_cast<Partial *>(partial), fallback_done(g, partial), winner);
     return cudaGetLastError();
 }
 

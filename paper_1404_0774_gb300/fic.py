@@ -21,6 +21,7 @@ FIC_SEARCH_AUTO, FIC_SEARCH_TC, FIC_SEARCH_SIMT = 0, 1, 2
 FIC_MAP_FALLBACK = 0x1
 FIC_FLAG_PHASE_TIMING = 0x1
 FIC_FLAG_DENSE = 0x2
+FIC_FLAG_EXACT_SCAN = 0x4
 STATUS = {0: "ok", -1: "bad argument", -2: "bad size", -3: "bad bit depth", -4: "capacity",
           -5: "cuda error", -6: "timeout", -7: "unsupported"}
 

@@ -186,3 +186,33 @@ def test_decode_rejects_invalid_host_maps(fic):
     maps["domain_idx"][3] = 10 ** 6
     with pytest.raises(fic.FicError):
         fic.decode(maps, 32, 32, p)
+
+
+EXACT_CASES = [
+    ("ct64_t4", lambda: fic_synth.ct_slice(19, 64), 8, 4, 12),
+    ("mr64_t4", lambda: fic_synth.mr_slice(20, 64), 8, 4, 8),
+    ("rand8_n4", lambda: fic_synth.random_image(21, 32, 32, 8), 4, 2, 8),
+    ("flat_regions", lambda: np.where(fic_synth.random_image(22, 48, 48, 8) > 100, 200, 10).astype(np.uint8), 8, 4, 8),
+]
+
+
+@pytest.mark.parametrize("name,make,n,t,B", EXACT_CASES, ids=[c[0] for c in EXACT_CASES])
+@pytest.mark.parametrize("search", SEARCH)
+def test_exact_scan_gives_the_screened_maps(fic, orc, name, make, n, t, B, search):
+    """FIC_FLAG_EXACT_SCAN sends every screened range to the exhaustive exact
+    scan (the path uncertified ranges take): the maps must be the screened
+    search's, each flagged as resolved by the scan, and meet the oracle bar."""
+    if search == "tc" and n != 8:
+        pytest.skip("the tensor-core search handles 8x8 ranges")
+    img = make()
+    p = fic.params(range_size=n, domain_stride=t, bit_depth=B, search=search_code(fic, search))
+    px = fic.params(range_size=n, domain_stride=t, bit_depth=B, search=search_code(fic, search),
+                    flags=fic.FIC_FLAG_EXACT_SCAN)
+    a = gpu_encode(fic, img, p)
+    b = gpu_encode(fic, img, px)
+    for f in ("domain_idx", "iso", "s_code", "o_code", "err"):
+        assert np.array_equal(a[f], b[f]), f
+    blocks = img.reshape(img.shape[0] // n, n, img.shape[1] // n, n).transpose(0, 2, 1, 3).reshape(-1, n * n)
+    screened = blocks.max(1) != blocks.min(1)
+    assert np.array_equal((b["info"] & fic.FIC_MAP_FALLBACK) != 0, screened)
+    check_against_oracle(orc, img, b, n, t, B)
