@@ -87,6 +87,17 @@ int make_geometry(int w, int h, int pitch, const fic_params *p, Geometry &g)
     g.mod_g = (Gnum % g.Lo) == 0 ? 1 : 0;
     g.G = (double)Gnum / g.Lo;
     g.Gi = g.mod_g ? (int)(Gnum / g.Lo) : 0;
+    {
+        // magnitude of the exact residual expansion R*D^2 (sum of the absolute
+        // values of its six terms at the largest statistics this bit depth
+        // allows): 64-bit integers suffice below 2^62
+        const double m = g.m, P = g.P, Ls = g.Ls, Lo = g.Lo;
+        const double A = Ls * Lo, Bo = 4.0 * Ls * Lo * P, Dd = 4.0 * Ls * Lo;
+        const double Sq = m * 4.0 * P, Sqq = m * 16.0 * P * P, Sb = m * P, Sbb = m * P * P, X = m * 4.0 * P * P;
+        const double bound = A * A * Sqq + m * Bo * Bo + Dd * Dd * Sbb + 2.0 * A * Bo * Sq + 2.0 * A * Dd * X +
+                             2.0 * Bo * Dd * Sb;
+        g.wide = bound < 4.0e18 ? 0 : 1;  // 2^62 = 4.61e18
+    }
     return FIC_OK;
 }
 

@@ -32,6 +32,12 @@
 namespace fic {
 
 constexpr int kListK = 4;          // entries per candidate list
+// A list entry's idx carries the candidate index (8d + k, < 2^31) and, in bit
+// 31, whether its key is clean: code not next to a rounding boundary and
+// offset not clamped, so that the key bounds the exact residual from above up
+// to the screening allowance.  An empty entry is 0xffffffff.
+constexpr uint32_t kCleanBit = 0x80000000u;
+constexpr uint32_t kIdxMask = 0x7fffffffu;
 constexpr int kMaxM = 256;         // largest range (16 x 16)
 constexpr float kMagic = 12582912.0f;  // 1.5 * 2^23: x + kMagic rounds x to an integer
 
@@ -48,6 +54,7 @@ struct Geometry {
     int KP;            // FP16 operand row length (tensor-core layout)
     int mod_g;         // 1 when G is an integer (z may be reduced mod G)
     int Gi;            // G when mod_g (< 2^31), else 0
+    int wide;          // exact residuals need 128-bit integers (else 64-bit suffice)
     double G;          // 4*Ls*m*P/Lo
 };
 
@@ -347,13 +354,16 @@ static __device__ __forceinline__ void epi_rare(const float *xrow, int stride, c
         }
         const int q = j >> 3;
         const int d = q == 0 ? od[0] : (q == 1 ? od[1] : (q == 2 ? od[2] : od[3]));
-        list_insert(L, k, (uint32_t)(d * 8 + (j & 7)));
-        if (k < L.T && !near) {
-            // a clean key (code not near a boundary, offset not clamped) is an
-            // upper bound of the residual up to beta: it may tighten the window
+        // a clean key (code not near a boundary, offset not clamped) is an
+        // upper bound of the residual up to beta: it may tighten the window,
+        // and the re-score may bound the best residual with it
+        bool clean = false;
+        if (!near) {
             const float ostar = (re.Sb - c * c4.w * ec.inv4ls) * ec.invm;
-            if (ostar < ec.pmax) list_adopt(L, k, re, ec);
+            clean = ostar < ec.pmax;
         }
+        list_insert(L, k, (uint32_t)(d * 8 + (j & 7)) | (clean ? kCleanBit : 0u));
+        if (clean && k < L.T) list_adopt(L, k, re, ec);
     }
 }
 

@@ -51,35 +51,60 @@ __device__ void fp64_codes(const Geometry &g, const Stats &st, int &c, int &e, d
     o_hat = __ddiv_rn(__dmul_rn((double)e, P), Lo);
 }
 
+// Exact integer arithmetic in one of two widths: 64-bit when every term of
+// the residual expansion below stays under 2^62 (Geometry::wide == 0, checked
+// on the host from the largest statistics the bit depth allows), 128-bit
+// otherwise.
+template <bool Wide> struct Exact;
+template <> struct Exact<false> {
+    typedef long long S;
+    typedef unsigned long long U;
+};
+template <> struct Exact<true> {
+    typedef __int128 S;
+    typedef unsigned __int128 U;
+};
+
 // Exact residual times D^2 for codes (c, e).
-__device__ __int128 exact_err(const Geometry &g, const Stats &st, int c, int e)
+template <bool Wide>
+__device__ __forceinline__ typename Exact<Wide>::S exact_err(const Geometry &g, const Stats &st, int c, int e)
 {
-    const __int128 A = (__int128)c * g.Lo;
-    const __int128 Bo = (__int128)4 * g.Ls * e * g.P;
-    const __int128 Dd = (__int128)4 * g.Ls * g.Lo;
-    return A * A * st.Sqq + (__int128)g.m * Bo * Bo + Dd * Dd * st.Sbb + 2 * A * Bo * st.Sq -
-           2 * A * Dd * st.X - 2 * Bo * Dd * st.Sb;
+    typedef typename Exact<Wide>::S S;
+    const S A = (S)c * g.Lo;
+    const S Bo = (S)4 * g.Ls * e * g.P;
+    const S Dd = (S)4 * g.Ls * g.Lo;
+    return A * A * st.Sqq + (S)g.m * Bo * Bo + Dd * Dd * st.Sbb + 2 * A * Bo * st.Sq - 2 * A * Dd * st.X -
+           2 * Bo * Dd * st.Sb;
 }
 
-__device__ __forceinline__ bool better(unsigned __int128 e1, uint32_t i1, unsigned __int128 e2,
-                                       uint32_t i2)
+template <typename U>
+__device__ __forceinline__ bool better(U e1, uint32_t i1, U e2, uint32_t i2)
 {
     return e1 < e2 || (e1 == e2 && i1 < i2);
 }
 
-__device__ __forceinline__ unsigned long long shfl64(unsigned long long v, int src)
+__device__ __forceinline__ unsigned long long shfl_xor64(unsigned long long v, int off)
 {
-    return __shfl_sync(0xffffffffu, v, src);
+    return __shfl_xor_sync(0xffffffffu, v, off);
 }
 
+__device__ __forceinline__ unsigned __int128 shfl_xor128(unsigned __int128 v, int off)
+{
+    const unsigned long long lo = shfl_xor64((unsigned long long)v, off);
+    const unsigned long long hi = shfl_xor64((unsigned long long)(v >> 64), off);
+    return ((unsigned __int128)hi << 64) | lo;
+}
+
+__device__ __forceinline__ unsigned long long shfl_xor_u(unsigned long long v, int off) { return shfl_xor64(v, off); }
+__device__ __forceinline__ unsigned __int128 shfl_xor_u(unsigned __int128 v, int off) { return shfl_xor128(v, off); }
+
 // Warp argmin over (err, idx).
-__device__ void warp_argmin(unsigned __int128 &err, uint32_t &idx)
+template <typename U>
+__device__ __forceinline__ void warp_argmin(U &err, uint32_t &idx)
 {
     for (int off = 16; off > 0; off >>= 1) {
-        const unsigned long long lo = shfl64((unsigned long long)err, (threadIdx.x & 31) ^ off);
-        const unsigned long long hi = shfl64((unsigned long long)(err >> 64), (threadIdx.x & 31) ^ off);
+        const U oe = shfl_xor_u(err, off);
         const uint32_t oi = __shfl_xor_sync(0xffffffffu, idx, off);
-        const unsigned __int128 oe = ((unsigned __int128)hi << 64) | lo;
         if (better(oe, oi, err, idx)) {
             err = oe;
             idx = oi;
@@ -97,13 +122,15 @@ __device__ __forceinline__ double u128_to_double(unsigned __int128 v)
 // An FP32 value >= v (v an unsigned 128-bit integer below 2^127): the top 64
 // significant bits, or-ed with 1 so that a discarded remainder always rounds
 // the conversion up past them, converted upward and scaled exactly.
-__device__ __forceinline__ float u128_to_float_ru(unsigned __int128 v)
+__device__ __forceinline__ float to_float_ru(unsigned __int128 v)
 {
     const unsigned long long hi = (unsigned long long)(v >> 64);
     if (hi == 0) return __ull2float_ru((unsigned long long)v);
     const int sh = 64 - __clzll(hi);
     return ldexpf(__ull2float_ru((unsigned long long)(v >> sh) | 1ull), sh);
 }
+
+__device__ __forceinline__ float to_float_ru(unsigned long long v) { return __ull2float_ru(v); }
 
 // round half away from zero of num/den (den > 0), exactly: an FP32 estimate
 // corrected with exact integer comparisons.
@@ -119,7 +146,9 @@ __device__ __forceinline__ long long round_div_away(long long num, long long den
 
 // Exact residual (times D^2) of candidate idx for range statistics st, with
 // the s and o codes decided exactly from the rational least-squares values.
-__device__ unsigned __int128 exact_rational(const Geometry &g, Stats st, const DomainInfo &dd, long long X)
+template <bool Wide>
+__device__ __forceinline__ typename Exact<Wide>::U exact_rational(const Geometry &g, Stats st, const DomainInfo &dd,
+                                                                 long long X)
 {
     st.Sq = dd.Sq;
     st.Sqq = dd.Sqq;
@@ -137,7 +166,7 @@ __device__ unsigned __int128 exact_rational(const Geometry &g, Stats st, const D
     const long long z = 4LL * g.Ls * st.Sb - (long long)c * dd.Sq;
     int e = (int)round_div_away(z * g.Lo, Q);
     if (e > g.Lo) e = g.Lo;  // o is never below -P; clamp above only
-    return (unsigned __int128)exact_err(g, st, c, e);
+    return (typename Exact<Wide>::U)exact_err<Wide>(g, st, c, e);
 }
 
 // Exact X of two candidates for a range whose pixels b[] are spread over the
@@ -232,6 +261,8 @@ __device__ long long lane_cross(const Geometry &g, const uint16_t *qblk, uint32_
 // is lost; the certification side is rounded down on the key and up on the
 // threshold, so that it never certifies what the exact test would not).
 constexpr int kRescoreWarps = 4;
+constexpr int kRescoreEnt = 16;  // list entries per lane: up to 512 per range
+template <bool Wide>
 __device__ __forceinline__ void rescore_range(const Geometry &g, const EpiConst &ec, const RangeInfo *ri,
                                               const DomainInfo *di, const uint16_t *bblk, const uint16_t *qblk,
                                               const ListEntry *lists, int max_lists, const int *counts,
@@ -239,7 +270,21 @@ __device__ __forceinline__ void rescore_range(const Geometry &g, const EpiConst 
                                               int exact_scan, uint32_t *winner, int *fb_list, int *fb_count, int r,
                                               int *bk)
 {
+    typedef typename Exact<Wide>::U U;
     const int lane = threadIdx.x & 31;
+    // lists actually written by the search (its split count follows the kept counts)
+    const int n_lists = lists_per_split *
+                        active_splits((counts[0] + 127) / 128, (8 * counts[2] + col_tile - 1) / col_tile, target, max_split);
+    const ListEntry *L = lists + (size_t)r * max_lists * kListK;
+    const int nent = n_lists * kListK;
+    // every entry of the range's lists in registers (entry lane + 32 s), the
+    // pixels and statistics loaded alongside: one memory latency
+    ListEntry ent[kRescoreEnt];
+#pragma unroll
+    for (int q = 0; q < kRescoreEnt; ++q) {
+        const int f = lane + 32 * q;
+        ent[q] = f < nent ? L[f] : ListEntry{__int_as_float(0x7f800000), 0xffffffffu};
+    }
     const RangeInfo rin = ri[r];
     int b[kMaxM / 32];
 #pragma unroll
@@ -247,20 +292,19 @@ __device__ __forceinline__ void rescore_range(const Geometry &g, const EpiConst 
         const int i = lane + 32 * j;
         b[j] = i < g.m ? (int)bblk[(size_t)r * g.m + i] : 0;
     }
-    // lists actually written by the search (its split count follows the kept counts)
-    const int n_lists = lists_per_split *
-                        active_splits((counts[0] + 127) / 128, (8 * counts[2] + col_tile - 1) / col_tile, target, max_split);
-    const ListEntry *L = lists + (size_t)r * max_lists * kListK;
-    const int nent = n_lists * kListK;
-    float kb = __int_as_float(0x7f800000);
+    // best key (ties to the lower index) and best clean key
+    float kb = __int_as_float(0x7f800000), kc = __int_as_float(0x7f800000);
     uint32_t ib = 0xffffffffu;
-#pragma unroll 4
-    for (int f = lane; f < nent; f += 32) {
-        const ListEntry e = L[f];
-        if (e.idx != 0xffffffffu && (e.key < kb || (e.key == kb && e.idx < ib))) {
+#pragma unroll
+    for (int q = 0; q < kRescoreEnt; ++q) {
+        const ListEntry e = ent[q];
+        if (e.idx == 0xffffffffu) continue;
+        const uint32_t idx = e.idx & kIdxMask;
+        if (e.key < kb || (e.key == kb && idx < ib)) {
             kb = e.key;
-            ib = e.idx;
+            ib = idx;
         }
+        if ((e.idx & kCleanBit) && e.key < kc) kc = e.key;
     }
     for (int off = 16; off > 0; off >>= 1) {
         const float ok = __shfl_xor_sync(0xffffffffu, kb, off);
@@ -269,6 +313,7 @@ __device__ __forceinline__ void rescore_range(const Geometry &g, const EpiConst 
             kb = ok;
             ib = oi;
         }
+        kc = fminf(kc, __shfl_xor_sync(0xffffffffu, kc, off));
     }
     if (ib == 0xffffffffu || exact_scan) {  // no candidate was listed (or asked): exact scan
         if (lane == 0) {
@@ -280,76 +325,99 @@ __device__ __forceinline__ void rescore_range(const Geometry &g, const EpiConst 
     Stats st;
     st.Sb = rin.Sb;
     st.Sbb = rin.Sbb;
-    // Flat domains were not screened: all their candidates have s = 0 and the
-    // same residual, so only the first of them, (first flat domain, k = 0), can
-    // win; it is a finalist of every range.  Its cross term is computed
-    // together with the best-key entry's.
-    const int dflat = counts[3];
-    const uint32_t fi = dflat >= 0 ? (uint32_t)dflat * 8 : ib;
-    unsigned __int128 ue, fe;
-    {
-        long long X, Xf;
-        warp_cross2(g, qblk, ib, fi, b, X, Xf);
-        ue = exact_rational(g, st, di[ib >> 3], X);  // integer work, same on every lane
-        fe = dflat >= 0 ? exact_rational(g, st, di[dflat], Xf) : ~(unsigned __int128)0;
+    const RangeEpi re = range_epi(rin, ec);
+    U best_e = ~(U)0;
+    uint32_t best_i = 0xffffffffu;
+    // Ub >= the best exact residual, rounded up; every threshold below is an
+    // FP32 bound rounded outward.  A clean entry gives it without exact work:
+    // its residual is at most sbbc + (key + beta(key)) / (2 Ls).  Otherwise
+    // the best-key entry is re-scored exactly first.
+    float Ub;
+    if (kc < __int_as_float(0x7f800000)) {
+        Ub = __fadd_ru(rin.sbbc, __fdiv_ru(__fadd_ru(kc, beta_key(re, kc, ec)), ec.two_ls));
+    } else {
+        long long X, Xd;
+        warp_cross2(g, qblk, ib, ib, b, X, Xd);
+        best_e = exact_rational<Wide>(g, st, di[ib >> 3], X);  // integer work, same on every lane
+        best_i = ib;
+        Ub = __fmul_ru(to_float_ru(best_e), ec.invD2_up);
     }
-    // U rounded up; every threshold below is an FP32 bound rounded outward
-    const float U = __fmul_ru(u128_to_float_ru(ue), ec.invD2_up);
     // screening error allowance (the epilogue's), evaluated at the largest key
     // that can still matter
-    const RangeEpi re = range_epi(rin, ec);
-    const float kreach = __fmul_ru(__fsub_ru(U, rin.sbbc), ec.two_ls);
+    const float kreach = __fmul_ru(__fsub_ru(Ub, rin.sbbc), ec.two_ls);
     const float beta_k = fmaxf(beta_key(re, kb, ec), beta_key(re, fmaxf(kb, kreach), ec));
     // finalist: sbbc + key/(2Ls) - beta/(2Ls) <= U  <=>  key <= (U - sbbc)*2Ls + beta
     const float kfin = __fadd_ru(kreach, beta_k);
-
-    unsigned __int128 best_e = ue;
-    uint32_t best_i = ib;
-    if (lane == 0 && dflat >= 0 && better(fe, fi, best_e, best_i)) {
-        best_e = fe;
-        best_i = fi;
+    // Flat domains were not screened: all their candidates have s = 0 and the
+    // same residual, so only the first of them, (first flat domain, k = 0), can
+    // win; it is a finalist of every range.  With s = 0 its residual needs no
+    // cross term.
+    const int dflat = counts[3];
+    if (lane == 0 && dflat >= 0) {
+        const long long Q = 4LL * g.Ls * g.m * g.P;
+        int e0 = (int)round_div_away(4LL * g.Ls * st.Sb * g.Lo, Q);
+        if (e0 > g.Lo) e0 = g.Lo;
+        Stats s0 = st;
+        s0.Sq = s0.Sqq = s0.X = 0;  // multiplied by c = 0
+        const U fe = (U)exact_err<Wide>(g, s0, 0, e0);
+        const uint32_t fi = (uint32_t)dflat * 8;
+        if (better(fe, fi, best_e, best_i)) {
+            best_e = fe;
+            best_i = fi;
+        }
+    }
+    // finalist slots: bit q of qmask when some lane's entry q is a finalist
+    uint32_t qmask = 0, mine = 0;
+#pragma unroll
+    for (int q = 0; q < kRescoreEnt; ++q) {
+        const bool fin = ent[q].idx != 0xffffffffu && (ent[q].idx & kIdxMask) != best_i && ent[q].key <= kfin;
+        if (__any_sync(0xffffffffu, fin)) qmask |= 1u << q;
+        mine |= (fin ? 1u : 0u) << q;
     }
     bool staged = false;
-    for (int f0 = 0; f0 < nent; f0 += 32) {
-        const int f = f0 + lane;
-        const ListEntry ent = f < nent ? L[f] : ListEntry{__int_as_float(0x7f800000), 0xffffffffu};
-        const bool fin = ent.idx != 0xffffffffu && ent.idx != ib && ent.key <= kfin;
-        unsigned mask = __ballot_sync(0xffffffffu, fin);
-        if (!mask) continue;
+    while (qmask) {
+        const int q = __ffs(qmask) - 1;
+        qmask &= qmask - 1;
+        const bool fin = (mine >> q) & 1u;
+        const unsigned mask = __ballot_sync(0xffffffffu, fin);
+        const uint32_t idx = fin ? (L[lane + 32 * q].idx & kIdxMask) : 0u;  // cached reload
         long long myX = 0;
         if ((mask & (mask - 1)) == 0) {  // one finalist: the whole warp computes it
-            const int src = __ffs(mask) - 1;
-            const uint32_t idx = __shfl_sync(0xffffffffu, ent.idx, src);
+            const uint32_t wi = __shfl_sync(0xffffffffu, idx, __ffs(mask) - 1);
             long long X, Xd;
-            warp_cross2(g, qblk, idx, idx, b, X, Xd);
+            warp_cross2(g, qblk, wi, wi, b, X, Xd);
             myX = X;
         } else {  // several: each lane computes its own
             if (!staged) {
                 stage_sym_pixels(g, b, bk);
                 staged = true;
             }
-            if (fin) myX = lane_cross(g, qblk, ent.idx, bk);
+            if (fin) myX = lane_cross(g, qblk, idx, bk);
         }
         if (fin) {  // lanes re-score their own finalists in parallel (integer work)
-            const unsigned __int128 er = exact_rational(g, st, di[ent.idx >> 3], myX);
-            if (better(er, ent.idx, best_e, best_i)) {
+            const U er = exact_rational<Wide>(g, st, di[idx >> 3], myX);
+            if (better(er, idx, best_e, best_i)) {
                 best_e = er;
-                best_i = ent.idx;
+                best_i = idx;
             }
         }
     }
     warp_argmin(best_e, best_i);
     // certified list: sbbc + (last - beta(last))/(2Ls) > E*, tested as
-    // round-down(last - beta) > round-up((E* - sbbc) * 2Ls)
-    const float Estar = __fmul_ru(u128_to_float_ru(best_e), ec.invD2_up);
+    // round-down(last - beta) > round-up((E* - sbbc) * 2Ls).  A full list's
+    // unlisted candidates have residual >= its last key less the allowance at
+    // that key; that bound must clear the winner strictly.  Entry f is the
+    // last of its list when f % 4 == 3 (lanes 3, 7, ...).
+    const float Estar = __fmul_ru(to_float_ru(best_e), ec.invD2_up);
     const float kcert = __fmul_ru(__fsub_ru(Estar, rin.sbbc), ec.two_ls);
     bool cert = true;
-    for (int l = lane; l < n_lists; l += 32) {
-        // a full list's unlisted candidates have residual >= its last key less
-        // the allowance at that key; that bound must clear the winner strictly
-        const ListEntry last = L[l * kListK + kListK - 1];
-        if (last.idx == 0xffffffffu) continue;
-        if (!(__fsub_rd(last.key, beta_key(re, last.key, ec)) > kcert)) cert = false;
+    if ((lane & (kListK - 1)) == kListK - 1) {
+#pragma unroll
+        for (int q = 0; q < kRescoreEnt; ++q) {
+            const ListEntry last = ent[q];
+            if (last.idx == 0xffffffffu) continue;  // list not full (or past the end)
+            if (!(__fsub_rd(last.key, beta_key(re, last.key, ec)) > kcert)) cert = false;
+        }
     }
     cert = __all_sync(0xffffffffu, cert);
     if (lane == 0) {
@@ -362,6 +430,7 @@ __device__ __forceinline__ void rescore_range(const Geometry &g, const EpiConst 
 // grid sized to be resident at once); every other range is a constant one:
 // num = 0 for every candidate, so s = 0, one offset and one residual for
 // all, and the first candidate wins (Algorithm 2).
+template <bool Wide>
 __global__ void __launch_bounds__(32 * kRescoreWarps, 4)
     k_rescore(Geometry g, EpiConst ec, const RangeInfo *ri, const DomainInfo *di, const uint16_t *bblk,
               const uint16_t *qblk, const ListEntry *lists, int max_lists, const int *counts, const int *act,
@@ -376,8 +445,8 @@ __global__ void __launch_bounds__(32 * kRescoreWarps, 4)
     int *bk = bk_all + (threadIdx.x >> 5) * 8 * (g.m + 1);
     const int nkept = counts[0];
     for (int j = blockIdx.x * kRescoreWarps + (threadIdx.x >> 5); j < nkept; j += gridDim.x * kRescoreWarps)
-        rescore_range(g, ec, ri, di, bblk, qblk, lists, max_lists, counts, lists_per_split, col_tile, target,
-                      max_split, exact_scan, winner, fb_list, fb_count, act[j], bk);
+        rescore_range<Wide>(g, ec, ri, di, bblk, qblk, lists, max_lists, counts, lists_per_split, col_tile, target,
+                            max_split, exact_scan, winner, fb_list, fb_count, act[j], bk);
 }
 
 struct Partial {
@@ -385,12 +454,16 @@ struct Partial {
     uint32_t idx, pad;
 };
 
+__device__ __forceinline__ unsigned long long hi64(unsigned long long) { return 0ull; }
+__device__ __forceinline__ unsigned long long hi64(unsigned __int128 v) { return (unsigned long long)(v >> 64); }
+
 // Exhaustive exact scan of the ranges that failed certification, as work
 // items (slot, chunk) over a grid of persistent blocks: an item scans one
 // contiguous chunk of the candidates of range fb_list[slot] with exact integer
 // decisions and writes its best (residual, index); the last item of a slot to
 // finish (counted in done[slot], zeroed by the re-score) reduces the chunks
 // and writes the winner, flagged as resolved by the fallback.
+template <bool Wide>
 __global__ void __launch_bounds__(256) k_fallback(Geometry g, const RangeInfo *ri, const DomainInfo *di,
                                                   const uint16_t *bblk, const uint16_t *qblk, const int *fb_list,
                                                   const int *fb_count, int nch, Partial *part, int *done,
@@ -412,7 +485,8 @@ __global__ void __launch_bounds__(256) k_fallback(Geometry g, const RangeInfo *r
         Stats st;
         st.Sb = rin.Sb;
         st.Sbb = rin.Sbb;
-        unsigned __int128 best_e = ~(unsigned __int128)0;
+        typedef typename Exact<Wide>::U U;
+        U best_e = ~(U)0;
         uint32_t best_i = 0xffffffffu;
         for (int idx = lo + threadIdx.x; idx < hi; idx += blockDim.x) {
             const int d = idx >> 3;
@@ -425,7 +499,7 @@ __global__ void __launch_bounds__(256) k_fallback(Geometry g, const RangeInfo *r
                     acc += (uint32_t)qd[sym_src_index(sf, g.ln, y, x)] * (uint32_t)b_s[(y << g.ln) + x];
                 X += acc;
             }
-            const unsigned __int128 er = exact_rational(g, st, di[d], (long long)X);
+            const U er = exact_rational<Wide>(g, st, di[d], (long long)X);
             if (better(er, (uint32_t)idx, best_e, best_i)) {
                 best_e = er;
                 best_i = (uint32_t)idx;
@@ -434,7 +508,7 @@ __global__ void __launch_bounds__(256) k_fallback(Geometry g, const RangeInfo *r
         warp_argmin(best_e, best_i);
         const int w = threadIdx.x >> 5;
         if ((threadIdx.x & 31) == 0)
-            w_s[w] = Partial{(unsigned long long)best_e, (unsigned long long)(best_e >> 64), best_i, 0};
+            w_s[w] = Partial{(unsigned long long)best_e, hi64(best_e), best_i, 0};
         __syncthreads();
         if (threadIdx.x == 0) {
             Partial b = w_s[0];
@@ -553,7 +627,7 @@ __global__ void __launch_bounds__(32 * kFinWarps) k_finalize(Geometry g, const R
     mp.s = (float)sh;
     mp.o = (float)oh;
     mp.info = ((wv & 0x80000000u) ? FIC_MAP_FALLBACK : 0u) | (*err ? FIC_MAP_ERROR : 0u);
-    mp.err = u128_to_double((unsigned __int128)exact_err(g, st, c, e)) * invD2;
+    mp.err = u128_to_double((unsigned __int128)exact_err<true>(g, st, c, e)) * invD2;
     maps[r] = mp;
 }
 
@@ -569,10 +643,15 @@ cudaError_t launch_rescore(const Geometry &g, const EpiConst &ec, const RangeInf
     const size_t smem = sizeof(int) * kRescoreWarps * 8 * (g.m + 1);
     // at most as many blocks as are resident at once (4 per SM at this size)
     const int blocks = std::max(1, std::min((g.R + kRescoreWarps - 1) / kRescoreWarps, 4 * n_sm));
-    k_rescore<<<blocks, 32 * kRescoreWarps, smem, st>>>(g, ec, ri, di, bblk, qblk, lists, max_lists, counts, act,
-                                                         rkeep, lists_per_split, col_tile, target, max_split,
-                                                         exact_scan, winner, fb_list, fb_count,
-                                                         fallback_done(g, partial));
+    if (max_lists * kListK > 32 * kRescoreEnt) return cudaErrorInvalidValue;
+    if (g.wide)
+        k_rescore<true><<<blocks, 32 * kRescoreWarps, smem, st>>>(
+            g, ec, ri, di, bblk, qblk, lists, max_lists, counts, act, rkeep, lists_per_split, col_tile, target,
+            max_split, exact_scan, winner, fb_list, fb_count, fallback_done(g, partial));
+    else
+        k_rescore<false><<<blocks, 32 * kRescoreWarps, smem, st>>>(
+            g, ec, ri, di, bblk, qblk, lists, max_lists, counts, act, rkeep, lists_per_split, col_tile, target,
+            max_split, exact_scan, winner, fb_list, fb_count, fallback_done(g, partial));
     return cudaGetLastError();
 }
 
@@ -594,8 +673,13 @@ cudaError_t launch_fallback(const Geometry &g, const RangeInfo *ri, const Domain
                             const int *fb_count, void *partial, uint32_t *winner, int n_sm, cudaStream_t st)
 {
     const int nch = fallback_chunks(g);
-    k_fallback<<<2 * n_sm, 256, 0, st>>>(g, ri, di, bblk, qblk, fb_list, fb_count, nch,
-                                         reinterpret_cast<Partial *>(partial), fallback_done(g, partial), winner);
+    Partial *part = reinterpret_cast<Partial *>(partial);
+    if (g.wide)
+        k_fallback<true><<<2 * n_sm, 256, 0, st>>>(g, ri, di, bblk, qblk, fb_list, fb_count, nch, part,
+                                                   fallback_done(g, partial), winner);
+    else
+        k_fallback<false><<<2 * n_sm, 256, 0, st>>>(g, ri, di, bblk, qblk, fb_list, fb_count, nch, part,
+                                                    fallback_done(g, partial), winner);
     return cudaGetLastError();
 }
 

@@ -216,3 +216,15 @@ def test_exact_scan_gives_the_screened_maps(fic, orc, name, make, n, t, B, searc
     screened = blocks.max(1) != blocks.min(1)
     assert np.array_equal((b["info"] & fic.FIC_MAP_FALLBACK) != 0, screened)
     check_against_oracle(orc, img, b, n, t, B)
+
+
+@pytest.mark.parametrize("search", SEARCH)
+@pytest.mark.parametrize("n,sb,ob", [(8, 8, 10), (16, 6, 9), (8, 3, 4)])
+def test_encode_parity_other_code_widths(fic, orc, search, n, sb, ob):
+    """s and o quantised to other bit widths (the 8/10-bit and 6/9-bit cases
+    need 128-bit exact residuals; 3/4 bits is a coarse grid)."""
+    if search == "tc" and n != 8:
+        pytest.skip("the tensor-core search handles 8x8 ranges")
+    img = fic_synth.ct_slice(23 + n + sb, 64)
+    p = fic.params(range_size=n, domain_stride=4, bit_depth=12, s_bits=sb, o_bits=ob, search=search_code(fic, search))
+    check_against_oracle(orc, img, gpu_encode(fic, img, p), n, 4, 12, sb=sb, ob=ob)
