@@ -207,6 +207,52 @@ int fic_cross_terms(const void *img, int w, int h, int pitch_px, const fic_param
 int fic_encode_static(const void *img, int w, int h, int pitch_px, const fic_params *p, fic_map *maps,
                       int maps_cap, int *n_maps, void *stream);
 
+/* One leaf of an adaptive quadtree encode (fic_encode_quadtree). */
+typedef struct {
+    uint32_t x, y;   /* top-left pixel of the range block                       */
+    uint32_t size;   /* its side n = range_size >> level                        */
+    uint32_t level;  /* 0 = the largest blocks                                  */
+    fic_map map;     /* its map; range_idx and domain_idx index the grids of its
+                        level: w/n ranges per row, domains 2n x 2n at stride n
+                        with (w-2n)/n + 1 per row                               */
+} fic_qmap;          /* 56 bytes */
+
+/*
+ * fic_encode_quadtree -- adaptive quadtree encode.  The paper searches one
+ *   range size; this applies the same exhaustive search (Section V, eq 8-12,
+ *   same quantisation, tie-break and exactness as fic_encode) at several:
+ *   level 0 tiles the image with p->range_size ranges; a range whose best map
+ *   has collage RMS error sqrt(E/m) > rms_split (compared in FP64) is
+ *   replaced by its four quadrants at the next level, down to min_size, whose
+ *   ranges are always kept.  At a level with range size n the domains are
+ *   2n x 2n at stride n (p->domain_stride is ignored).  Each level is one
+ *   encode over that level's active ranges only.
+ *   maps       output leaves (host or device) ordered by level, then by range
+ *              index within the level; maps_cap >= (w/min_size)*(h/min_size).
+ *   n_maps     output (host): number of leaves.  The call waits for `stream`.
+ *   workspace  device buffer of fic_quadtree_workspace_size() bytes, 256-byte
+ *              aligned, or NULL to allocate on `stream`.
+ *   Launch shapes: with p->search == FIC_SEARCH_AUTO and p->n_split == 0 each
+ *   level's search kernel (tensor-core where supported, else FP32) and the
+ *   number of CTAs its candidate dimension is spread over are chosen by
+ *   timing the candidates once per geometry and caching the fastest (the
+ *   maps do not depend on the choice); otherwise p->search / p->n_split fix
+ *   them.
+ *   Sizes: range_size 16 or 8, min_size 4, 8 or 16 with min_size <=
+ *   range_size; w and h multiples of range_size, at least 2*range_size.
+ *   FIC_FLAG_PHASE_TIMING is rejected.
+ */
+int fic_encode_quadtree(const void *img, int w, int h, int pitch_px, const fic_params *p, int min_size,
+                        float rms_split, fic_qmap *maps, int maps_cap, int *n_maps, void *workspace,
+                        size_t workspace_bytes, void *stream);
+int fic_quadtree_workspace_size(int w, int h, const fic_params *p, int min_size, size_t *bytes);
+
+/* Per level of the last fic_encode_quadtree on this host thread: out[0] =
+ * number of levels L, then for level l at out[1 + 4l ..]: search kernel used
+ * (FIC_SEARCH_*), CTA target of its candidate split (waves x SMs), ranges
+ * screened (active), leaves kept. */
+int fic_last_quadtree_stats(int64_t out[17]);
+
 /* Phase durations (ms) of the last fic_encode on this host thread that ran
  * with FIC_FLAG_PHASE_TIMING: out[0] prep, out[1] search, out[2] re-score,
  * out[3] fallback, out[4] map output.  Waits for those events. */

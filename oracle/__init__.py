@@ -161,3 +161,42 @@ def psnr(ref, img, bit_depth):
     a = np.ascontiguousarray(ref, np.float64)
     b = np.ascontiguousarray(img, np.float64)
     return float(lib.orc_psnr(_dptr(a), _dptr(b), a.size, bit_depth))
+
+
+QT_DTYPE = np.dtype([("level", np.int32), ("x", np.int32), ("y", np.int32), ("n", np.int32),
+                     ("range_idx", np.int32), ("d", np.int32), ("k", np.int32), ("c", np.int32),
+                     ("e", np.int32), ("err", np.float64)])
+
+
+def encode_quadtree(img, n_max=16, n_min=4, rms_split=8.0, bit_depth=8, s_bits=5, o_bits=7, threads=None):
+    """Adaptive quadtree by its definition: level 0 tiles the image with n_max
+    ranges; every range whose best map (the exhaustive search of ``encode`` at
+    that level: domains 2n x 2n at stride n) has collage RMS error
+    sqrt(E/m) > rms_split is replaced by its four quadrants at the next level,
+    down to n_min, whose ranges are all kept.  Returns the kept leaves
+    (QT_DTYPE) ordered by level, then range index within the level."""
+    im = np.asarray(img)
+    h, w = im.shape
+    thr = float(rms_split)
+    leaves = []
+    n, level = n_max, 0
+    active = np.arange((h // n) * (w // n), dtype=np.int32)
+    while len(active):
+        nx = w // n
+        fits = encode(im, n=n, t=n, bit_depth=bit_depth, s_bits=s_bits, o_bits=o_bits, ranges=active,
+                      threads=threads)
+        rms = np.sqrt(fits["err"] / float(n * n))
+        split = (rms > thr) & (n > n_min)
+        for r, f in zip(active[~split], fits[~split]):
+            leaves.append((level, (r % nx) * n, (r // nx) * n, n, r, f["d"], f["k"], f["c"], f["e"], f["err"]))
+        children = []
+        for r in active[split]:
+            ry, rx = divmod(int(r), nx)
+            for dy in (0, 1):
+                for dx in (0, 1):
+                    children.append((2 * ry + dy) * (2 * nx) + 2 * rx + dx)
+        active = np.array(sorted(children), dtype=np.int32)
+        n //= 2
+        level += 1
+    out = np.array(leaves, dtype=QT_DTYPE)
+    return out[np.lexsort((out["range_idx"], out["level"]))]

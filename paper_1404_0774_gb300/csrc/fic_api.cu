@@ -9,6 +9,9 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 #include "fic_internal.cuh"
 
@@ -296,7 +299,108 @@ int fic_encode_workspace_size(int w, int h, const fic_params *p, size_t *bytes)
 
 namespace {
 
-// Shared pipeline of fic_encode and fic_cross_terms (dump != nullptr: stop
+struct EncBufs {
+    RangeInfo *ri;
+    DomainInfo *di;
+    float4 *dconst;
+    uint16_t *bblk, *qblk;
+    float *rs32, *cb32;
+    __half *ra16, *cb16;
+    ListEntry *lists;
+    uint32_t *winner;
+    int *fb_list, *fb_count, *err, *tbest;
+    void *partial;
+    CompactBufs cb;
+};
+
+EncBufs enc_bufs(const EncLayout &L, char *ws)
+{
+    EncBufs b;
+    b.ri = reinterpret_cast<RangeInfo *>(ws + L.ri);
+    b.di = reinterpret_cast<DomainInfo *>(ws + L.di);
+    b.dconst = reinterpret_cast<float4 *>(ws + L.dconst);
+    b.bblk = reinterpret_cast<uint16_t *>(ws + L.bblk);
+    b.qblk = reinterpret_cast<uint16_t *>(ws + L.qblk);
+    b.rs32 = L.rs32 ? reinterpret_cast<float *>(ws + L.rs32) : nullptr;
+    b.cb32 = L.cb32 ? reinterpret_cast<float *>(ws + L.cb32) : nullptr;
+    b.ra16 = L.ra16 ? reinterpret_cast<__half *>(ws + L.ra16) : nullptr;
+    b.cb16 = L.cb16 ? reinterpret_cast<__half *>(ws + L.cb16) : nullptr;
+    b.lists = reinterpret_cast<ListEntry *>(ws + L.lists);
+    b.winner = reinterpret_cast<uint32_t *>(ws + L.winner);
+    b.fb_list = reinterpret_cast<int *>(ws + L.fb_list);
+    b.fb_count = reinterpret_cast<int *>(ws + L.fb_count);
+    b.err = b.fb_count + 1;
+    b.tbest = reinterpret_cast<int *>(ws + L.tbest);
+    b.partial = ws + L.partial;
+    b.cb.rkeep = reinterpret_cast<int *>(ws + L.rkeep);
+    b.cb.dkeep = reinterpret_cast<int *>(ws + L.dkeep);
+    b.cb.act = reinterpret_cast<int *>(ws + L.act);
+    b.cb.dact = reinterpret_cast<int *>(ws + L.dact);
+    b.cb.counts = reinterpret_cast<int *>(ws + L.counts);
+    b.cb.dconst_c = reinterpret_cast<float4 *>(ws + L.dconst_c);
+    b.cb.dmap = reinterpret_cast<int *>(ws + L.dmap);
+    return b;
+}
+
+// The device pipeline of one encode on a prepared workspace (no allocation,
+// no synchronisation): statistics, compaction, operand rows, seed, search,
+// re-score, exact fallback, map output.  dimg: device image with row pitch
+// gd.pitch; active (nullable): only ranges with active[r] != 0 are screened
+// (the maps of the others are placeholders); dump != nullptr: stop after the
+// contraction and write the raw cross terms there.
+cudaError_t encode_pipeline(const Geometry &gd, const fic_params *p, int search, int n_split, int target,
+                            const EncLayout &L, char *ws, const void *dimg, const int *active, fic_map *dmaps,
+                            float *dump, bool timed, cudaStream_t st)
+{
+    const EncBufs b = enc_bufs(L, ws);
+    const int n_lists = n_split * lists_per_split(search);
+    // the contraction dump covers every range and candidate
+    const int dense = (dump || (p->flags & FIC_FLAG_DENSE)) ? 1 : 0;
+    const EpiConst ec = make_epi(gd);
+    cudaError_t e;
+#define FIC_STEP(call)                                                 \
+    do {                                                               \
+        if ((e = debug_check((call), #call, __LINE__, st)) != cudaSuccess) \
+            return e;                                                  \
+    } while (0)
+#define FIC_MARK(i) \
+    if (timed) FIC_STEP(cudaEventRecord(g_phase.ev[i], st))
+    FIC_STEP(cudaMemsetAsync(b.fb_count, 0, 2 * sizeof(int), st));
+    if (b.ra16) {  // zero the padding rows that complete the last TMA boxes
+        const size_t row = sizeof(__half) * gd.KP;
+        FIC_STEP(cudaMemsetAsync(ws + L.ra16 + row * gd.R, 0, row * (search_tc_rows(gd.R) - gd.R), st));
+        FIC_STEP(cudaMemsetAsync(ws + L.cb16 + row * gd.N, 0, row * (search_tc_rows(gd.N) - gd.N), st));
+    }
+    FIC_MARK(0);
+    FIC_STEP(launch_prep(gd, dimg, ec, dense, active, b.ri, b.di, b.dconst, b.bblk, b.qblk, b.rs32, b.cb32, b.ra16,
+                         b.cb16, b.tbest, b.cb, st));
+    if (!dump) FIC_STEP(launch_seed(gd, ec, b.ri, b.di, b.dconst, b.bblk, b.qblk, b.cb.rkeep, b.tbest, st));
+    FIC_MARK(1);
+    if (search == FIC_SEARCH_TC)
+        FIC_STEP(launch_search_tc(gd, ec, b.ri, b.cb, dense, b.ra16, b.cb16, b.lists, n_split, target, b.tbest, dump,
+                                  b.err, st));
+    else
+        FIC_STEP(launch_search_simt(gd, ec, b.ri, b.di, b.cb, dense, b.rs32, b.cb32, b.lists, n_split, target, b.tbest,
+                                    dump, st));
+    FIC_MARK(2);
+    if (!dump) {
+        FIC_STEP(launch_rescore(gd, ec, b.ri, b.di, b.bblk, b.qblk, b.lists, n_lists, b.cb.counts, b.cb.act, b.cb.rkeep,
+                                lists_per_split(search), search == FIC_SEARCH_TC ? search_tc_tile() : 64, target,
+                                n_split, sm_count(), (p->flags & FIC_FLAG_EXACT_SCAN) ? 1 : 0, b.winner, b.fb_list,
+                                b.fb_count, b.partial, st));
+        FIC_MARK(3);
+        FIC_STEP(launch_fallback(gd, b.ri, b.di, b.bblk, b.qblk, b.fb_list, b.fb_count, b.partial, b.winner, sm_count(),
+                                 st));
+        FIC_MARK(4);
+        FIC_STEP(launch_finalize(gd, b.ri, b.di, b.bblk, b.qblk, b.winner, b.err, dmaps, st));
+        FIC_MARK(5);
+    }
+#undef FIC_MARK
+#undef FIC_STEP
+    return cudaSuccess;
+}
+
+// Shared front end of fic_encode and fic_cross_terms (dump != nullptr: stop
 // after the contraction and write the raw cross terms there).
 int run_encode(const void *img, int w, int h, int pitch_px, const fic_params *p, fic_map *maps, int maps_cap,
                int *n_maps, void *workspace, size_t workspace_bytes, void *stream, float *dump)
@@ -336,76 +440,18 @@ int run_encode(const void *img, int w, int h, int pitch_px, const fic_params *p,
             dimg = ws + L.img;
             gd.pitch = w;
         }
-        RangeInfo *ri = reinterpret_cast<RangeInfo *>(ws + L.ri);
-        DomainInfo *di = reinterpret_cast<DomainInfo *>(ws + L.di);
-        float4 *dconst = reinterpret_cast<float4 *>(ws + L.dconst);
-        uint16_t *bblk = reinterpret_cast<uint16_t *>(ws + L.bblk);
-        uint16_t *qblk = reinterpret_cast<uint16_t *>(ws + L.qblk);
-        float *rs32 = L.rs32 ? reinterpret_cast<float *>(ws + L.rs32) : nullptr;
-        float *cb32 = L.cb32 ? reinterpret_cast<float *>(ws + L.cb32) : nullptr;
-        __half *ra16 = L.ra16 ? reinterpret_cast<__half *>(ws + L.ra16) : nullptr;
-        __half *cb16 = L.cb16 ? reinterpret_cast<__half *>(ws + L.cb16) : nullptr;
-        ListEntry *lists = reinterpret_cast<ListEntry *>(ws + L.lists);
-        uint32_t *winner = reinterpret_cast<uint32_t *>(ws + L.winner);
-        int *fb_list = reinterpret_cast<int *>(ws + L.fb_list);
-        int *fb_count = reinterpret_cast<int *>(ws + L.fb_count);
-        int *err = fb_count + 1;
-        int *tbest = reinterpret_cast<int *>(ws + L.tbest);
-        void *partial = ws + L.partial;
-        CompactBufs cbuf;
-        cbuf.rkeep = reinterpret_cast<int *>(ws + L.rkeep);
-        cbuf.dkeep = reinterpret_cast<int *>(ws + L.dkeep);
-        cbuf.act = reinterpret_cast<int *>(ws + L.act);
-        cbuf.dact = reinterpret_cast<int *>(ws + L.dact);
-        cbuf.counts = reinterpret_cast<int *>(ws + L.counts);
-        cbuf.dconst_c = reinterpret_cast<float4 *>(ws + L.dconst_c);
-        cbuf.dmap = reinterpret_cast<int *>(ws + L.dmap);
-        // the contraction dump covers every range and candidate
-        const int dense = (dump || (p->flags & FIC_FLAG_DENSE)) ? 1 : 0;
         fic_map *dmaps = maps_dev ? maps : reinterpret_cast<fic_map *>(ws + L.maps);
-        const EpiConst ec = make_epi(g);
         const bool timed = !dump && (p->flags & FIC_FLAG_PHASE_TIMING) && g_phase.ensure();
         g_phase.valid = false;
-#define FIC_MARK(i) \
-    if (timed) FIC_CUDA(cudaEventRecord(g_phase.ev[i], st))
-
-        FIC_CUDA(cudaMemsetAsync(fb_count, 0, 2 * sizeof(int), st));
-        if (ra16) {  // zero the padding rows that complete the last TMA boxes
-            const size_t row = sizeof(__half) * g.KP;
-            FIC_CUDA(cudaMemsetAsync(ws + L.ra16 + row * g.R, 0, row * (search_tc_rows(g.R) - g.R), st));
-            FIC_CUDA(cudaMemsetAsync(ws + L.cb16 + row * g.N, 0, row * (search_tc_rows(g.N) - g.N), st));
-        }
-        FIC_MARK(0);
-        FIC_CUDA(launch_prep(gd, dimg, ec, dense, ri, di, dconst, bblk, qblk, rs32, cb32, ra16, cb16, tbest, cbuf, st));
-        if (!dump) FIC_CUDA(launch_seed(gd, ec, ri, di, dconst, bblk, qblk, tbest, st));
-        FIC_MARK(1);
-        const int target = split_target(p, search);
-        if (search == FIC_SEARCH_TC)
-            FIC_CUDA(launch_search_tc(gd, ec, ri, cbuf, dense, ra16, cb16, lists, n_split, target, tbest, dump, err,
-                                      st));
-        else
-            FIC_CUDA(launch_search_simt(gd, ec, ri, di, cbuf, dense, rs32, cb32, lists, n_split, target, tbest, dump,
-                                        st));
-        FIC_MARK(2);
-        if (!dump) {
-            FIC_CUDA(launch_rescore(gd, ec, ri, di, bblk, qblk, lists, n_lists, cbuf.counts, cbuf.act, cbuf.rkeep,
-                                    lists_per_split(search), search == FIC_SEARCH_TC ? search_tc_tile() : 64, target,
-                                    n_split, sm_count(), (p->flags & FIC_FLAG_EXACT_SCAN) ? 1 : 0, winner, fb_list,
-                                    fb_count, partial, st));
-            FIC_MARK(3);
-            FIC_CUDA(launch_fallback(gd, ri, di, bblk, qblk, fb_list, fb_count, partial, winner, sm_count(), st));
-            FIC_MARK(4);
-            FIC_CUDA(launch_finalize(gd, ri, di, bblk, qblk, winner, err, dmaps, st));
-            FIC_MARK(5);
-        }
-#undef FIC_MARK
+        FIC_CUDA(encode_pipeline(gd, p, search, n_split, split_target(p, search), L, ws, dimg, nullptr, dmaps, dump,
+                                 timed, st));
         g_phase.valid = timed;
         const bool sync = dump || !maps_dev || !img_dev || debug_mode();
         if (!dump && !maps_dev)
             FIC_CUDA(cudaMemcpyAsync(maps, dmaps, sizeof(fic_map) * g.R, cudaMemcpyDeviceToHost, st));
         if (sync) {
             int herr = 0;
-            FIC_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+            FIC_CUDA(cudaMemcpyAsync(&herr, enc_bufs(L, ws).err, sizeof(int), cudaMemcpyDeviceToHost, st));
             FIC_CUDA(cudaStreamSynchronize(st));
             if (herr) {
                 rc = FIC_ERR_TIMEOUT;
@@ -417,6 +463,238 @@ int run_encode(const void *img, int w, int h, int pitch_px, const fic_params *p,
         g_stats[2] = search;
         g_stats[3] = n_split;
         if (n_maps) *n_maps = g.R;
+    }
+done:
+    if (owned) {
+        if (cudaFreeAsync(ws, st) != cudaSuccess) {
+            cudaGetLastError();
+            if (rc == FIC_OK) rc = FIC_ERR_CUDA;
+        }
+    }
+    return rc;
+}
+
+// ------------------------------------------------------------ quadtree
+
+thread_local int64_t g_qt_stats[1 + 4 * kMaxLevels] = {0};
+
+// Launch shapes chosen by timing, per level geometry.
+struct TuneKey {
+    int w, h, n, B, sb, ob, flags, fixed_search;
+    bool operator<(const TuneKey &o) const
+    {
+        return std::tie(w, h, n, B, sb, ob, flags, fixed_search) <
+               std::tie(o.w, o.h, o.n, o.B, o.sb, o.ob, o.flags, o.fixed_search);
+    }
+};
+struct TuneChoice {
+    int search, waves;
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneChoice> g_tune;
+
+constexpr int kWaveChoices[3] = {2, 4, 8};
+
+int target_for(int search, int waves) { return waves * (search == FIC_SEARCH_TC ? 1 : 2) * sm_count(); }
+
+struct QtPlan {
+    int levels;
+    fic_params pl[kMaxLevels];
+    Geometry g[kMaxLevels];
+    size_t img, enc, active[kMaxLevels + 1], leaf[kMaxLevels], maps[kMaxLevels], stage, counts, total;
+    size_t enc_bytes;
+};
+
+int qt_plan(int w, int h, int pitch, const fic_params *p, int min_size, int maps_cap_check, QtPlan &Q)
+{
+    if (!p) return FIC_ERR_BAD_ARG;
+    int rc = check_params(p);
+    if (rc != FIC_OK) return rc;
+    if (p->flags & FIC_FLAG_PHASE_TIMING) return FIC_ERR_BAD_ARG;
+    const int nmax = p->range_size;
+    if (nmax != 8 && nmax != 16) return FIC_ERR_BAD_ARG;
+    if ((min_size != 4 && min_size != 8 && min_size != 16) || min_size > nmax) return FIC_ERR_BAD_ARG;
+    Q.levels = nmax == min_size ? 1 : (nmax / min_size == 2 ? 2 : 3);
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        const size_t at = o;
+        o = align_up(o + bytes);
+        return at;
+    };
+    Q.enc_bytes = 0;
+    for (int l = 0; l < Q.levels; ++l) {
+        Q.pl[l] = *p;
+        Q.pl[l].range_size = nmax >> l;
+        Q.pl[l].domain_stride = nmax >> l;
+        rc = make_geometry(w, h, pitch, &Q.pl[l], Q.g[l]);
+        if (rc != FIC_OK) return rc;
+        for (int s = FIC_SEARCH_TC; s <= FIC_SEARCH_SIMT; ++s) {
+            if (s == FIC_SEARCH_TC && !search_tc_supported(Q.g[l])) continue;
+            if (p->search != FIC_SEARCH_AUTO && p->search != s && !(s == FIC_SEARCH_SIMT && !search_tc_supported(Q.g[l])))
+                continue;
+            Q.enc_bytes = std::max(Q.enc_bytes, enc_layout(Q.g[l], s, choose_split(Q.g[l], p, s) * lists_per_split(s)).total);
+        }
+    }
+    (void)maps_cap_check;
+    const size_t elem = Q.g[0].B <= 8 ? 1 : 2;
+    Q.img = take((size_t)w * h * elem);
+    Q.enc = take(Q.enc_bytes);
+    for (int l = 0; l < Q.levels; ++l) {
+        Q.active[l] = take(sizeof(int) * Q.g[l].R);
+        Q.leaf[l] = take(sizeof(int) * Q.g[l].R);
+        Q.maps[l] = take(sizeof(fic_map) * Q.g[l].R);
+    }
+    Q.active[Q.levels] = take(sizeof(int));  // the last level splits nothing
+    const size_t max_leaves = (size_t)(w / min_size) * (h / min_size);
+    Q.stage = take(sizeof(fic_qmap) * max_leaves);
+    Q.counts = take(sizeof(int) * (2 + 2 * kMaxLevels));
+    Q.total = o;
+    return FIC_OK;
+}
+
+// Time one full pipeline run (after one warm-up run) in milliseconds.
+float time_pipeline(const Geometry &g, const fic_params *p, int search, int target, const EncLayout &L, char *ws,
+                    const void *dimg, const int *active, fic_map *dmaps, cudaStream_t st)
+{
+    cudaEvent_t a, b;
+    if (cudaEventCreate(&a) != cudaSuccess) return 1e30f;
+    if (cudaEventCreate(&b) != cudaSuccess) {
+        cudaEventDestroy(a);
+        return 1e30f;
+    }
+    const int n_split = choose_split(g, p, search);
+    float ms = 1e30f;
+    if (encode_pipeline(g, p, search, n_split, target, L, ws, dimg, active, dmaps, nullptr, false, st) ==
+            cudaSuccess &&
+        cudaEventRecord(a, st) == cudaSuccess &&
+        encode_pipeline(g, p, search, n_split, target, L, ws, dimg, active, dmaps, nullptr, false, st) ==
+            cudaSuccess &&
+        cudaEventRecord(b, st) == cudaSuccess && cudaEventSynchronize(b) == cudaSuccess)
+        cudaEventElapsedTime(&ms, a, b);
+    cudaGetLastError();
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return ms;
+}
+
+int run_quadtree(const void *img, int w, int h, int pitch_px, const fic_params *p, int min_size, float rms_split,
+                 fic_qmap *maps, int maps_cap, int *n_maps, void *workspace, size_t workspace_bytes, void *stream)
+{
+    if (!img || !maps) return FIC_ERR_BAD_ARG;
+    QtPlan Q;
+    int rc = qt_plan(w, h, pitch_px, p, min_size, maps_cap, Q);
+    if (rc != FIC_OK) return rc;
+    if ((size_t)maps_cap < (size_t)(w / min_size) * (h / min_size)) return FIC_ERR_CAPACITY;
+    if (!(rms_split >= 0.0f)) return FIC_ERR_BAD_ARG;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    char *ws = static_cast<char *>(workspace);
+    bool owned = false;
+    if (ws) {
+        if (workspace_bytes < Q.total) return FIC_ERR_CAPACITY;
+        if (reinterpret_cast<uintptr_t>(ws) & (kAlign - 1)) return FIC_ERR_BAD_ARG;
+    } else {
+        if (cudaMallocAsync(reinterpret_cast<void **>(&ws), Q.total, st) != cudaSuccess) {
+            cudaGetLastError();
+            return FIC_ERR_CUDA;
+        }
+        owned = true;
+    }
+    {
+        const bool img_dev = is_device_ptr(img);
+        const bool maps_dev = is_device_ptr(maps);
+        const size_t elem = Q.g[0].B <= 8 ? 1 : 2;
+        const void *dimg = img;
+        int pitch = pitch_px;
+        if (!img_dev) {
+            FIC_CUDA(cudaMemcpy2DAsync(ws + Q.img, (size_t)w * elem, img, (size_t)pitch_px * elem, (size_t)w * elem, h,
+                                       cudaMemcpyHostToDevice, st));
+            dimg = ws + Q.img;
+            pitch = w;
+        }
+        int *counts = reinterpret_cast<int *>(ws + Q.counts);
+        FIC_CUDA(cudaMemsetAsync(counts, 0, sizeof(int) * (2 + 2 * kMaxLevels), st));
+        FIC_CUDA(cudaMemsetAsync(ws + Q.active[0], 1, sizeof(int) * Q.g[0].R, st));  // every level-0 range
+        QtLevels lv;
+        lv.levels = Q.levels;
+        g_qt_stats[0] = Q.levels;
+        for (int l = 0; l < Q.levels; ++l) {
+            Geometry g = Q.g[l];
+            g.pitch = pitch;
+            const fic_params *pl = &Q.pl[l];
+            int *active = reinterpret_cast<int *>(ws + Q.active[l]);
+            int *active_next = reinterpret_cast<int *>(ws + Q.active[l + 1]);
+            int *leaf = reinterpret_cast<int *>(ws + Q.leaf[l]);
+            fic_map *lmaps = reinterpret_cast<fic_map *>(ws + Q.maps[l]);
+            char *ews = ws + Q.enc;
+            // launch shape: fixed by the caller, cached, or timed now
+            TuneChoice ch{FIC_SEARCH_SIMT, 4};
+            const bool tc_ok = search_tc_supported(g);
+            if (p->search == FIC_SEARCH_SIMT || (p->search == FIC_SEARCH_TC && !tc_ok)) ch.search = FIC_SEARCH_SIMT;
+            else if (p->search == FIC_SEARCH_TC) ch.search = FIC_SEARCH_TC;
+            else ch.search = tc_ok ? FIC_SEARCH_TC : FIC_SEARCH_SIMT;
+            if (p->n_split == 0) {
+                const TuneKey key{w, h, g.n, g.B, g.s_bits, g.o_bits, (int)p->flags, p->search};
+                bool have = false;
+                {
+                    std::lock_guard<std::mutex> lk(g_tune_mu);
+                    auto it = g_tune.find(key);
+                    if (it != g_tune.end()) {
+                        ch = it->second;
+                        have = true;
+                    }
+                }
+                if (!have) {
+                    float best = 1e30f;
+                    TuneChoice bc = ch;
+                    for (int s = FIC_SEARCH_TC; s <= FIC_SEARCH_SIMT; ++s) {
+                        if (s == FIC_SEARCH_TC && !tc_ok) continue;
+                        if (p->search != FIC_SEARCH_AUTO && s != ch.search) continue;
+                        for (int wv : kWaveChoices) {
+                            const EncLayout L = enc_layout(g, s, choose_split(g, pl, s) * lists_per_split(s));
+                            const float ms = time_pipeline(g, pl, s, target_for(s, wv), L, ews, dimg, active, lmaps, st);
+                            if (ms < best) {
+                                best = ms;
+                                bc = TuneChoice{s, wv};
+                            }
+                        }
+                    }
+                    ch = bc;
+                    std::lock_guard<std::mutex> lk(g_tune_mu);
+                    g_tune[key] = ch;
+                }
+            }
+            const int n_split = choose_split(g, pl, ch.search);
+            const int target = p->n_split > 0 ? split_target(pl, ch.search) : target_for(ch.search, ch.waves);
+            const EncLayout L = enc_layout(g, ch.search, n_split * lists_per_split(ch.search));
+            FIC_CUDA(encode_pipeline(g, pl, ch.search, n_split, target, L, ews, dimg, active, lmaps, nullptr, false, st));
+            if (l + 1 < Q.levels)
+                FIC_CUDA(cudaMemsetAsync(active_next, 0, sizeof(int) * Q.g[l + 1].R, st));
+            FIC_CUDA(launch_qt_split(g.R, g.nx, g.m, lmaps, active, (double)rms_split, l + 1 == Q.levels ? 1 : 0, leaf,
+                                     active_next, st));
+            lv.R[l] = g.R;
+            lv.nx[l] = g.nx;
+            lv.n[l] = g.n;
+            lv.active[l] = active;
+            lv.leaf[l] = leaf;
+            lv.maps[l] = lmaps;
+            g_qt_stats[1 + 4 * l] = ch.search;
+            g_qt_stats[2 + 4 * l] = target;
+        }
+        fic_qmap *dout = maps_dev ? maps : reinterpret_cast<fic_qmap *>(ws + Q.stage);
+        FIC_CUDA(launch_qt_gather(lv, dout, maps_cap, counts, st));
+        int hc[2 + 2 * kMaxLevels];
+        FIC_CUDA(cudaMemcpyAsync(hc, counts, sizeof hc, cudaMemcpyDeviceToHost, st));
+        FIC_CUDA(cudaStreamSynchronize(st));
+        if (!maps_dev && hc[0] > 0) {
+            FIC_CUDA(cudaMemcpyAsync(maps, dout, sizeof(fic_qmap) * (size_t)hc[0], cudaMemcpyDeviceToHost, st));
+            FIC_CUDA(cudaStreamSynchronize(st));
+        }
+        for (int l = 0; l < Q.levels; ++l) {
+            g_qt_stats[3 + 4 * l] = hc[1 + kMaxLevels + l];
+            g_qt_stats[4 + 4 * l] = hc[1 + l];
+        }
+        if (n_maps) *n_maps = hc[0];
+        if (hc[1 + 2 * kMaxLevels]) rc = FIC_ERR_TIMEOUT;
     }
 done:
     if (owned) {
@@ -557,6 +835,32 @@ int fic_last_encode_phase_ms(double out[5])
         }
         out[i] = ms;
     }
+    return FIC_OK;
+}
+
+int fic_encode_quadtree(const void *img, int w, int h, int pitch_px, const fic_params *p, int min_size,
+                        float rms_split, fic_qmap *maps, int maps_cap, int *n_maps, void *workspace,
+                        size_t workspace_bytes, void *stream)
+{
+    return run_quadtree(img, w, h, pitch_px, p, min_size, rms_split, maps, maps_cap, n_maps, workspace,
+                        workspace_bytes, stream);
+}
+
+int fic_quadtree_workspace_size(int w, int h, const fic_params *p, int min_size, size_t *bytes)
+{
+    if (!bytes) return FIC_ERR_BAD_ARG;
+    QtPlan Q;
+    const int rc = qt_plan(w, h, w, p, min_size, 0, Q);
+    if (rc != FIC_OK) return rc;
+    *bytes = Q.total;
+    return FIC_OK;
+}
+
+int fic_last_quadtree_stats(int64_t out[17])
+{
+    if (!out) return FIC_ERR_BAD_ARG;
+    for (int i = 0; i < 1 + 4 * kMaxLevels; ++i) out[i] = g_qt_stats[i];
+    for (int i = 1 + 4 * kMaxLevels; i < 17; ++i) out[i] = 0;
     return FIC_OK;
 }
 

@@ -476,15 +476,27 @@ __device__ __forceinline__ RangeEpi range_epi(const RangeInfo &ri, const EpiCons
     re.shadow = ri.shadow;
     return re;
 }
-cudaError_t launch_prep(const Geometry &g, const void *img, const EpiConst &ec, int dense, RangeInfo *ri,
-                        DomainInfo *di, float4 *dconst, uint16_t *bblk, uint16_t *qblk, float *rs32, float *cb32,
-                        __half *ra16, __half *cb16, int *tbest, const CompactBufs &cb, cudaStream_t st);
+cudaError_t launch_prep(const Geometry &g, const void *img, const EpiConst &ec, int dense, const int *active,
+                        RangeInfo *ri, DomainInfo *di, float4 *dconst, uint16_t *bblk, uint16_t *qblk, float *rs32,
+                        float *cb32, __half *ra16, __half *cb16, int *tbest, const CompactBufs &cb, cudaStream_t st);
 cudaError_t launch_seed(const Geometry &g, const EpiConst &ec, const RangeInfo *ri, const DomainInfo *di,
-                        const float4 *dconst, const uint16_t *bblk, const uint16_t *qblk, int *tbest,
-                        cudaStream_t st);
+                        const float4 *dconst, const uint16_t *bblk, const uint16_t *qblk, const int *rkeep,
+                        int *tbest, cudaStream_t st);
 // The encode pipeline on a caller-provided device workspace (never allocates).
 int encode_with_workspace(const void *img, int w, int h, int pitch_px, const fic_params *p, fic_map *maps,
                           int maps_cap, int *n_maps, void *workspace, size_t workspace_bytes, void *stream);
+// Levels of an adaptive quadtree encode (device arrays per level).
+constexpr int kMaxLevels = 3;  // range sizes 16, 8, 4
+struct QtLevels {
+    int levels;
+    int R[kMaxLevels], nx[kMaxLevels], n[kMaxLevels];
+    const int *active[kMaxLevels];
+    const int *leaf[kMaxLevels];
+    const fic_map *maps[kMaxLevels];
+};
+cudaError_t launch_qt_split(int R, int nx, int m, const fic_map *maps, const int *active, double rms_split, int last,
+                            int *leaf, int *active_next, cudaStream_t st);
+cudaError_t launch_qt_gather(const QtLevels &lv, fic_qmap *out, int cap, int *counts, cudaStream_t st);
 // Key-space value that excludes s-code-0 candidates once a list holds one.
 constexpr float kZeroPenalty = 1e30f;
 

@@ -18,8 +18,9 @@ __device__ __forceinline__ long long warp_sum_ll(long long v)
 
 // One warp per range (lanes over pixels): statistics, centre, allowances,
 // and the keep flag (every range but shadow ranges, or all when dense).
-__device__ __forceinline__ void range_stats(const Geometry &g, const EpiConst &ec, const void *img, int dense, int r,
-                                            int lane, RangeInfo *ri, uint16_t *bblk, int *tbest, int *rkeep)
+__device__ __forceinline__ void range_stats(const Geometry &g, const EpiConst &ec, const void *img, int dense,
+                                            const int *active, int r, int lane, RangeInfo *ri, uint16_t *bblk,
+                                            int *tbest, int *rkeep)
 {
     const int ry = (r / g.nx) * g.n, rx = (r % g.nx) * g.n;
     constexpr int PPL = kMaxM / 32;  // pixels per lane, upper bound
@@ -98,7 +99,7 @@ __device__ __forceinline__ void range_stats(const Geometry &g, const EpiConst &e
     info.pad = 0;
     ri[r] = info;
     tbest[r] = 0x7f800000;  // +inf in the ordered-integer encoding of floats
-    rkeep[r] = dense || !info.shadow;
+    rkeep[r] = (!active || active[r]) && (dense || !info.shadow);
 }
 
 
@@ -148,14 +149,15 @@ __device__ __forceinline__ void domain_stats(const Geometry &g, const void *img,
 
 // Statistics of every range (blocks [0, rb), a warp each) and every domain
 // (the blocks after), one launch.
-__global__ void __launch_bounds__(256) k_stats(Geometry g, EpiConst ec, const void *img, int dense, int rb,
-                                               RangeInfo *ri, uint16_t *bblk, int *tbest, DomainInfo *di,
-                                               float4 *dconst, uint16_t *qblk, int *rkeep, int *dkeep)
+__global__ void __launch_bounds__(256) k_stats(Geometry g, EpiConst ec, const void *img, int dense,
+                                               const int *active, int rb, RangeInfo *ri, uint16_t *bblk, int *tbest,
+                                               DomainInfo *di, float4 *dconst, uint16_t *qblk, int *rkeep,
+                                               int *dkeep)
 {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     if ((int)blockIdx.x < rb) {
         const int r = blockIdx.x * 8 + w;
-        if (r < g.R) range_stats(g, ec, img, dense, r, lane, ri, bblk, tbest, rkeep);
+        if (r < g.R) range_stats(g, ec, img, dense, active, r, lane, ri, bblk, tbest, rkeep);
     } else {
         const int d = (blockIdx.x - rb) * 8 + w;
         if (d < g.D) domain_stats(g, img, dense, d, lane, di, dconst, qblk, dkeep);
@@ -371,12 +373,13 @@ __global__ void __launch_bounds__(256, 4) k_rows(Geometry g, int rb, const Range
                          dmap);
 }
 
-cudaError_t launch_prep(const Geometry &g, const void *img, const EpiConst &ec, int dense, RangeInfo *ri,
-                        DomainInfo *di, float4 *dconst, uint16_t *bblk, uint16_t *qblk, float *rs32, float *cb32,
-                        __half *ra16, __half *cb16, int *tbest, const CompactBufs &cb, cudaStream_t st)
+cudaError_t launch_prep(const Geometry &g, const void *img, const EpiConst &ec, int dense, const int *active,
+                        RangeInfo *ri, DomainInfo *di, float4 *dconst, uint16_t *bblk, uint16_t *qblk, float *rs32,
+                        float *cb32, __half *ra16, __half *cb16, int *tbest, const CompactBufs &cb, cudaStream_t st)
 {
     const int rb = (g.R + 7) / 8, db = (g.D + 7) / 8;
-    k_stats<<<rb + db, 256, 0, st>>>(g, ec, img, dense, rb, ri, bblk, tbest, di, dconst, qblk, cb.rkeep, cb.dkeep);
+    k_stats<<<rb + db, 256, 0, st>>>(g, ec, img, dense, active, rb, ri, bblk, tbest, di, dconst, qblk, cb.rkeep,
+                                     cb.dkeep);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_compact<<<2, 1024, 0, st>>>(g.R, cb.rkeep, cb.act, cb.counts + 0, g.D, cb.dkeep, cb.dact, cb.counts + 2);
@@ -395,7 +398,7 @@ cudaError_t launch_prep(const Geometry &g, const void *img, const EpiConst &ec, 
 // the search's insertion window needs.
 __global__ void __launch_bounds__(256) k_seed(Geometry g, EpiConst ec, const RangeInfo *ri, const DomainInfo *di,
                                               const float4 *dconst, const uint16_t *bblk, const uint16_t *qblk,
-                                              int *tbest)
+                                              const int *rkeep, int *tbest)
 {
     // q2_s[p][slot]: contracted-domain pixels 2p, 2p+1 of the slot's domain
     // (lanes read consecutive words); bk_s[k][j]: the range pixel that S_k
@@ -404,8 +407,8 @@ __global__ void __launch_bounds__(256) k_seed(Geometry g, EpiConst ec, const Ran
     __shared__ __align__(8) int bk_s[8][kMaxM];
     __shared__ int d_s[32];
     const int r = blockIdx.x;
-    const RangeInfo rin = ri[r];  // block-uniform
-    if (rin.shadow) return;
+    if (!rkeep[r]) return;  // block-uniform: a range that is not screened
+    const RangeInfo rin = ri[r];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x < 32) {
         const int slot_d = threadIdx.x;
@@ -472,10 +475,10 @@ __global__ void __launch_bounds__(256) k_seed(Geometry g, EpiConst ec, const Ran
 }
 
 cudaError_t launch_seed(const Geometry &g, const EpiConst &ec, const RangeInfo *ri, const DomainInfo *di,
-                        const float4 *dconst, const uint16_t *bblk, const uint16_t *qblk, int *tbest,
-                        cudaStream_t st)
+                        const float4 *dconst, const uint16_t *bblk, const uint16_t *qblk, const int *rkeep,
+                        int *tbest, cudaStream_t st)
 {
-    k_seed<<<g.R, 256, 0, st>>>(g, ec, ri, di, dconst, bblk, qblk, tbest);
+    k_seed<<<g.R, 256, 0, st>>>(g, ec, ri, di, dconst, bblk, qblk, rkeep, tbest);
     return cudaGetLastError();
 }
 

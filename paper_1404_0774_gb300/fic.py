@@ -43,6 +43,9 @@ MAP_DTYPE = np.dtype([("range_idx", np.uint32), ("domain_idx", np.uint32), ("iso
                       ("s_code", np.int32), ("o_code", np.int32), ("s", np.float32), ("o", np.float32),
                       ("info", np.uint32), ("err", np.float64)])
 assert MAP_DTYPE.itemsize == 40
+QMAP_DTYPE = np.dtype([("x", np.uint32), ("y", np.uint32), ("size", np.uint32), ("level", np.uint32),
+                       ("map", MAP_DTYPE)])
+assert QMAP_DTYPE.itemsize == 56
 
 _lib = None
 
@@ -72,6 +75,10 @@ def lib():
         L.fic_cross_terms.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, pp, vp, vp, sz, vp]
         L.fic_encode_static.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, pp, vp, ctypes.c_int,
                                         ctypes.POINTER(ctypes.c_int), vp]
+        L.fic_encode_quadtree.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, pp, ctypes.c_int,
+                                          ctypes.c_float, vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), vp, sz, vp]
+        L.fic_quadtree_workspace_size.argtypes = [ctypes.c_int, ctypes.c_int, pp, ctypes.c_int, ctypes.POINTER(sz)]
+        L.fic_last_quadtree_stats.argtypes = [i64p]
         _lib = L
     return _lib
 
@@ -181,6 +188,63 @@ def decode(maps, w: int, h: int, p: fic_params, init: float | None = None, out=N
     _check(lib().fic_decode(maps_ptr, R, w, h, ctypes.byref(p), ctypes.c_float(init), out_ptr, ws_ptr, ws_bytes,
                             st), "fic_decode")
     return out
+
+
+def quadtree_workspace_size(w: int, h: int, p: fic_params, min_size: int = 4) -> int:
+    b = ctypes.c_size_t()
+    _check(lib().fic_quadtree_workspace_size(w, h, ctypes.byref(p), min_size, ctypes.byref(b)),
+           "fic_quadtree_workspace_size")
+    return b.value
+
+
+def encode_quadtree(img, p: fic_params, min_size: int = 4, rms_split: float = 8.0, maps=None, workspace=None,
+                    stream=None):
+    """Adaptive quadtree encode (p.range_size = largest block).  Returns
+    (leaves, n): for a CUDA image a torch uint8 tensor of capacity*56 bytes on
+    the device whose first n records are the leaves (view with
+    ``qmaps_to_numpy``), for a host image a QMAP_DTYPE numpy array of n leaves."""
+    h, w = int(img.shape[0]), int(img.shape[1])
+    cap = (w // min_size) * (h // min_size)
+    if _is_torch(img):
+        import torch
+
+        if not img.is_cuda or img.stride(1) != 1:
+            raise ValueError("torch image must be on a CUDA device with contiguous rows")
+        pitch = int(img.stride(0))
+        if maps is None:
+            maps = torch.empty(cap * QMAP_DTYPE.itemsize, dtype=torch.uint8, device=img.device)
+        img_ptr, maps_ptr, st = img.data_ptr(), maps.data_ptr(), _stream_ptr(stream)
+    else:
+        a = np.ascontiguousarray(img, dtype=np.uint8 if p.bit_depth <= 8 else np.uint16)
+        img = a
+        pitch = w
+        if maps is None:
+            maps = np.zeros(cap, QMAP_DTYPE)
+        img_ptr, maps_ptr = a.ctypes.data, maps.ctypes.data
+        st = 0 if stream is None else _stream_ptr(stream)
+    ws_ptr, ws_bytes = (None, 0)
+    if workspace is not None:
+        ws_ptr, ws_bytes = workspace.data_ptr(), workspace.numel() * workspace.element_size()
+    n = ctypes.c_int()
+    _check(lib().fic_encode_quadtree(img_ptr, w, h, pitch, ctypes.byref(p), int(min_size), ctypes.c_float(rms_split),
+                                     maps_ptr, cap, ctypes.byref(n), ws_ptr, ws_bytes, st), "fic_encode_quadtree")
+    if not _is_torch(maps):
+        return maps[: n.value], n.value
+    return maps, n.value
+
+
+def qmaps_to_numpy(maps, n: int) -> np.ndarray:
+    """The first n leaves of a device quadtree maps tensor as a host QMAP_DTYPE array."""
+    if _is_torch(maps):
+        return maps[: n * QMAP_DTYPE.itemsize].detach().cpu().numpy().view(QMAP_DTYPE)
+    return np.asarray(maps, QMAP_DTYPE)[:n]
+
+
+def last_quadtree_stats():
+    """[levels, then per level: search kernel, CTA target, ranges screened, leaves]."""
+    out = (ctypes.c_int64 * 17)()
+    _check(lib().fic_last_quadtree_stats(out), "fic_last_quadtree_stats")
+    return list(out)
 
 
 def cross_terms(img, p: fic_params, out=None, stream=None):
