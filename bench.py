@@ -196,6 +196,236 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+QT_WORKLOAD = ("512x512 12-bit CT-like synthetic slice; adaptive quadtree: 16x16 ranges split to 8x8 and 4x4 "
+               "while the collage RMS exceeds 8.0; domains 2n x 2n at stride n, 8 symmetries; s 5-bit, o 7-bit")
+
+
+def quadtree_comparisons(fic, stats):
+    """Range-domain comparisons of one quadtree encode: per level, screened
+    ranges x domains x 8 (from the library's per-level statistics)."""
+    total, per_level = 0, []
+    for lvl in range(int(stats[0])):
+        n = 16 >> lvl
+        _, D = fic.counts(N_PIX, N_PIX, fic.params(range_size=n, domain_stride=n, bit_depth=BITS))
+        c = int(stats[3 + 4 * lvl]) * D * 8
+        per_level.append({"range_size": n, "ranges": int(stats[3 + 4 * lvl]), "leaves": int(stats[4 + 4 * lvl]),
+                          "domains": D, "comparisons": c,
+                          "search": {1: "tc", 2: "simt"}.get(int(stats[1 + 4 * lvl]), "?"),
+                          "cta_target": int(stats[2 + 4 * lvl])})
+        total += c
+    return total, per_level
+
+
+def run_quadtree(args):
+    """Adaptive quadtree encode of the 512x512 CT slice: one step = one
+    fic_encode_quadtree (3 levels, each an encode over its active ranges,
+    plus the split and gather kernels; the call waits for its stream)."""
+    import torch
+
+    import __graft_entry__
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    __graft_entry__.build()
+    from paper_1404_0774_gb300 import fic
+
+    img_np = fic_synth.ct_slice(fic_synth.CT_SEED + rank)
+    p = fic.params(range_size=16, domain_stride=16, bit_depth=BITS)
+    img = torch.from_numpy(img_np.astype(np.int16)).to(dev)
+    work = torch.empty(fic.quadtree_workspace_size(N_PIX, N_PIX, p, 4), dtype=torch.uint8, device=dev)
+    cap = (N_PIX // 4) ** 2
+    maps = torch.empty(cap * fic.QMAP_DTYPE.itemsize, dtype=torch.uint8, device=dev)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        return fic.encode_quadtree(img, p, 4, 8.0, maps=maps, workspace=work, stream=stream)[1]
+
+    for _ in range(max(3, args.warmup)):  # the first call also times the launch shapes of each level
+        step()
+    torch.cuda.synchronize()
+    comps, per_level = quadtree_comparisons(fic, fic.last_quadtree_stats())
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t_clk = time.time()
+        for i in range(args.steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            n_leaves = step()
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        while time.time() - t_clk < CLOCK_WINDOW_S:
+            flush.zero_()
+            step()
+        torch.cuda.synchronize()
+        clk_window = time.time() - t_clk
+    t_total = float(np.sum([a.elapsed_time(b) for a, b in ev])) / 1e3
+    if ws > 1:
+        tt = torch.tensor([t_total], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_total = float(tt.item())
+    value = ws * args.steps * comps / t_total
+    # end to end from pinned host memory through the C ABI (image H2D, leaves D2H)
+    h_img = torch.from_numpy(img_np.astype(np.int16)).pin_memory()
+    h_maps = np.zeros(cap, fic.QMAP_DTYPE)
+    for _ in range(2):
+        fic.encode_quadtree(h_img.numpy(), p, 4, 8.0, maps=h_maps, workspace=work, stream=stream)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        flush.zero_()
+        fic.encode_quadtree(h_img.numpy(), p, 4, 8.0, maps=h_maps, workspace=work, stream=stream)
+    torch.cuda.synchronize()
+    e2e_t = time.perf_counter() - t0
+    clocks = clk.summary()
+    clocks["window_s"] = clk_window
+    clocks["note"] = "sampled over the timed steps and the identical steps that follow them"
+    line = {"metric": METRIC, "value": value, "unit": "comparisons/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": 1e3 * t_total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "fp16+fp32", "data": "synthetic",
+            "config": {"workload": QT_WORKLOAD, "leaves": int(n_leaves), "comparisons_per_step": comps,
+                       "levels": per_level, "l2": "flushed (256 MB write) between steps"},
+            "e2e": {"value": ws * args.steps * comps / e2e_t, "unit": "comparisons/s",
+                    "h2d_bytes_per_step": N_PIX * N_PIX * 2, "d2h_bytes_per_step": int(n_leaves) * 56,
+                    "timing": "host wall clock (the call waits for its stream)"},
+            "gpu_launches": None, "clocks": clocks, "roofline": None}
+    if rank == 0:
+        if ws == 1 and not args.no_cpu_baseline:
+            import oracle
+
+            oracle.build()
+            t0 = time.perf_counter()
+            lv = oracle.encode_quadtree(img_np, 16, 4, 8.0, bit_depth=BITS)
+            tc = time.perf_counter() - t0
+            oc = 0
+            for lvl in range(3):
+                n = 16 >> lvl
+                _, D = oracle.counts(N_PIX, N_PIX, n, n)
+                # ranges searched at this level: leaves there plus the split ones (4 children each below)
+                below = sum(int(np.sum(lv["level"] == j)) / 4 ** (j - lvl) for j in range(lvl + 1, 3))
+                oc += int(round(np.sum(lv["level"] == lvl) + below)) * D * 8
+            line["cpu_baseline"] = {"value": oc / tc, "unit": "comparisons/s", "cores": os.cpu_count() or 1,
+                                    "kind": "oracle", "sample": f"the whole quadtree encode of the slice, {tc:.1f} s"}
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+VOL_WORKLOAD = ("12-bit CT-like synthetic stack: 32 slices at 256x256, 32 at 384x384, 32 at 512x512; 8x8 ranges, "
+                "16x16 domains at stride 4, 8 symmetries; s 5-bit, o 7-bit; one batch (one CUDA graph) per step")
+
+
+def run_volume(args):
+    """Batched volume: one step = fic_encode_batch of the whole 96-slice stack
+    (a replay of its CUDA graph).  Reports slices/s and the per-slice
+    completion times within a batch (p50/p99)."""
+    import torch
+
+    import __graft_entry__
+
+    ws_n, rank, local = dist_env()
+    if ws_n > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    __graft_entry__.build()
+    from paper_1404_0774_gb300 import fic
+
+    stack = fic_synth.ct_stack(fic_synth.CT_SEED + 7919 * rank)
+    p = fic.params(range_size=RANGE, domain_stride=STRIDE, bit_depth=BITS)
+    imgs = [torch.from_numpy(a.astype(np.int16)).to(dev) for a in stack]
+    maps = [torch.empty((a.shape[0] // RANGE) ** 2 * 40, dtype=torch.uint8, device=dev) for a in stack]
+    tab = fic.slice_table(imgs, maps)
+    work = torch.empty(fic.batch_workspace_size(tab, p), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    comps = 0
+    for a in stack:
+        R, D = fic.counts(a.shape[1], a.shape[0], p)
+        comps += R * D * 8
+    for _ in range(max(3, args.warmup)):  # the first call runs eagerly and captures the graph
+        fic.encode_batch(tab, p, work, stream)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    lat = []
+    if ws_n > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t_clk = time.time()
+        for i in range(args.steps):
+            ev[i][0].record(stream)
+            fic.encode_batch(tab, p, work, stream)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        while time.time() - t_clk < CLOCK_WINDOW_S:
+            fic.encode_batch(tab, p, work, stream)
+            torch.cuda.synchronize()
+        clk_window = time.time() - t_clk
+    t_total = float(np.sum([a.elapsed_time(b) for a, b in ev])) / 1e3
+    if ws_n > 1:
+        tt = torch.tensor([t_total], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_total = float(tt.item())
+    n_sl = len(stack)
+    value = ws_n * args.steps * n_sl / t_total
+    # per-slice completion times within a batch (separate runs: reading them waits for the batch)
+    for _ in range(args.steps):
+        fic.encode_batch(tab, p, work, stream)
+        lat.extend(fic.last_batch_slice_ms(n_sl))
+    # end to end: pinned host stack -> device, batch, maps -> pinned host
+    h_imgs = [torch.from_numpy(a.astype(np.int16)).pin_memory() for a in stack]
+    h_maps = [torch.empty(m.numel(), dtype=torch.uint8).pin_memory() for m in maps]
+    h2d = sum(h.numel() * 2 for h in h_imgs)
+    d2h = sum(m.numel() for m in maps)
+
+    def e2e_step():
+        for d, h in zip(imgs, h_imgs):
+            d.copy_(h, non_blocking=True)
+        fic.encode_batch(tab, p, work, stream)
+        for h, d in zip(h_maps, maps):
+            h.copy_(d, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_t = e0.elapsed_time(e1) / 1e3
+    clocks = clk.summary()
+    clocks["window_s"] = clk_window
+    clocks["note"] = "sampled over the timed steps and the identical steps that follow them"
+    lat = np.array(lat)
+    line = {"metric": "slices/s", "value": value, "unit": "slices/s", "n_gpus": ws_n, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": 1e3 * t_total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "fp16+fp32", "data": "synthetic",
+            "config": {"workload": VOL_WORKLOAD, "slices": n_sl, "comparisons_per_step": comps,
+                       "comparisons_per_s": ws_n * args.steps * comps / t_total,
+                       "slice_completion_ms": {"p50": float(np.percentile(lat, 50)),
+                                               "p99": float(np.percentile(lat, 99)), "max": float(lat.max()),
+                                               "note": "time from the start of the batch to each slice's maps"},
+                       "l2": "working set of the batch (several GB) is larger than L2"},
+            "e2e": {"value": ws_n * args.steps * n_sl / e2e_t, "unit": "slices/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": None, "clocks": clocks, "roofline": None}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws_n > 1:
+        dist.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -204,9 +434,18 @@ def main():
     ap.add_argument("--impl", default="gb300")
     ap.add_argument("--search", default="auto", choices=["auto", "tc", "simt"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="slice", choices=["slice", "quadtree", "volume"],
+                    help="slice: the 512x512 CT encode (default); quadtree: its adaptive 16->8->4 quadtree "
+                         "encode; volume: a 96-slice CT stack of 256/384/512 slices as one batch")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload == "quadtree":
+        run_quadtree(args)
+        return
+    if args.workload == "volume":
+        run_volume(args)
         return
 
     import torch

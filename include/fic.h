@@ -253,6 +253,39 @@ int fic_quadtree_workspace_size(int w, int h, const fic_params *p, int min_size,
  * screened (active), leaves kept. */
 int fic_last_quadtree_stats(int64_t out[17]);
 
+/* One slice of a batch (fic_encode_batch); every pointer is device memory. */
+typedef struct {
+    const void *img;   /* w x h image, row pitch pitch_px elements; uint8 for
+                          bit_depth <= 8, else uint16                          */
+    int32_t w, h, pitch_px;
+    fic_map *maps;     /* output: one map per range of this slice (in range
+                          order), (w/n)*(h/n) of them                          */
+} fic_slice;
+
+/*
+ * fic_encode_batch -- encode n slices of possibly different sizes with the
+ *   same parameters: for each slice exactly what fic_encode computes.  The
+ *   whole batch is one CUDA graph: the slices' encode pipelines spread over
+ *   parallel branches (largest slices first, each to the least loaded
+ *   branch), captured on the first call for a batch and replayed while the
+ *   slice table, parameters and workspace stay the same (a different batch
+ *   captures a new graph; one graph is kept per host thread).
+ *   workspace  device, fic_batch_workspace_size() bytes, 256-byte aligned
+ *              (required: the graph refers to it).
+ *   Asynchronous on `stream`; the maps are ready when the stream is.  Bounded
+ *   device waits that expire flag the affected maps FIC_MAP_ERROR.
+ *   FIC_FLAG_PHASE_TIMING is rejected.
+ */
+int fic_encode_batch(const fic_slice *slices, int n, const fic_params *p, void *workspace, size_t workspace_bytes,
+                     void *stream);
+int fic_batch_workspace_size(const fic_slice *slices, int n, const fic_params *p, size_t *bytes);
+
+/* Completion time (ms) of each slice of the last graph replay of
+ * fic_encode_batch on this host thread (the first call for a batch runs
+ * eagerly and records none), from the start of the batch: events recorded
+ * inside the graph; waits for them.  out has n entries. */
+int fic_last_batch_slice_ms(float *out, int n);
+
 /* Phase durations (ms) of the last fic_encode on this host thread that ran
  * with FIC_FLAG_PHASE_TIMING: out[0] prep, out[1] search, out[2] re-score,
  * out[3] fallback, out[4] map output.  Waits for those events. */

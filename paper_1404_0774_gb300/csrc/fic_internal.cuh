@@ -493,10 +493,11 @@ struct QtLevels {
     const int *active[kMaxLevels];
     const int *leaf[kMaxLevels];
     const fic_map *maps[kMaxLevels];
+    int list_off[kMaxLevels];  // offset of level l's leaf list in the lists buffer
 };
 cudaError_t launch_qt_split(int R, int nx, int m, const fic_map *maps, const int *active, double rms_split, int last,
                             int *leaf, int *active_next, cudaStream_t st);
-cudaError_t launch_qt_gather(const QtLevels &lv, fic_qmap *out, int cap, int *counts, cudaStream_t st);
+cudaError_t launch_qt_gather(const QtLevels &lv, int *lists, fic_qmap *out, int cap, int *counts, cudaStream_t st);
 // Key-space value that excludes s-code-0 candidates once a list holds one.
 constexpr float kZeroPenalty = 1e30f;
 

@@ -79,6 +79,9 @@ def lib():
                                           ctypes.c_float, vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), vp, sz, vp]
         L.fic_quadtree_workspace_size.argtypes = [ctypes.c_int, ctypes.c_int, pp, ctypes.c_int, ctypes.POINTER(sz)]
         L.fic_last_quadtree_stats.argtypes = [i64p]
+        L.fic_encode_batch.argtypes = [vp, ctypes.c_int, pp, vp, sz, vp]
+        L.fic_batch_workspace_size.argtypes = [vp, ctypes.c_int, pp, ctypes.POINTER(sz)]
+        L.fic_last_batch_slice_ms.argtypes = [ctypes.POINTER(ctypes.c_float), ctypes.c_int]
         _lib = L
     return _lib
 
@@ -244,6 +247,41 @@ def last_quadtree_stats():
     """[levels, then per level: search kernel, CTA target, ranges screened, leaves]."""
     out = (ctypes.c_int64 * 17)()
     _check(lib().fic_last_quadtree_stats(out), "fic_last_quadtree_stats")
+    return list(out)
+
+
+class fic_slice(ctypes.Structure):
+    _fields_ = [("img", ctypes.c_void_p), ("w", ctypes.c_int32), ("h", ctypes.c_int32), ("pitch_px", ctypes.c_int32),
+                ("maps", ctypes.c_void_p)]
+
+
+def slice_table(imgs, maps):
+    """ctypes array of fic_slice for lists of CUDA image tensors and maps tensors."""
+    tab = (fic_slice * len(imgs))()
+    for i, (im, mp) in enumerate(zip(imgs, maps)):
+        if not (im.is_cuda and mp.is_cuda) or im.stride(1) != 1:
+            raise ValueError("batch images and maps must be CUDA tensors with contiguous rows")
+        tab[i] = fic_slice(im.data_ptr(), int(im.shape[1]), int(im.shape[0]), int(im.stride(0)), mp.data_ptr())
+    return tab
+
+
+def batch_workspace_size(table, p: fic_params) -> int:
+    b = ctypes.c_size_t()
+    _check(lib().fic_batch_workspace_size(table, len(table), ctypes.byref(p), ctypes.byref(b)),
+           "fic_batch_workspace_size")
+    return b.value
+
+
+def encode_batch(table, p: fic_params, workspace, stream=None):
+    """Encode every slice of ``table`` (from ``slice_table``); asynchronous on the stream."""
+    _check(lib().fic_encode_batch(table, len(table), ctypes.byref(p), workspace.data_ptr(),
+                                  workspace.numel() * workspace.element_size(), _stream_ptr(stream)),
+           "fic_encode_batch")
+
+
+def last_batch_slice_ms(n: int):
+    out = (ctypes.c_float * n)()
+    _check(lib().fic_last_batch_slice_ms(out, n), "fic_last_batch_slice_ms")
     return list(out)
 
 

@@ -1,0 +1,59 @@
+"""The batched encode (fic_encode_batch through the C ABI): every slice of a
+mixed-size batch must get exactly the maps fic_encode gives that slice alone
+(which the encode parity tests check against the oracle), on the first call
+(run eagerly) and on graph replays."""
+import numpy as np
+import pytest
+
+import fic_synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fic():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_1404_0774_gb300 import fic
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return fic
+
+
+@pytest.mark.parametrize("search", ["auto", "simt"])
+def test_batch_equals_single_slice_encodes(fic, search):
+    sizes = [64, 128, 96, 64, 128, 160]
+    imgs_np = [fic_synth.ct_slice(60 + i, s) for i, s in enumerate(sizes)]
+    code = {"auto": fic.FIC_SEARCH_AUTO, "simt": fic.FIC_SEARCH_SIMT}[search]
+    p = fic.params(range_size=8, domain_stride=4, bit_depth=12, search=code)
+    imgs = [torch.from_numpy(a.astype(np.int16)).cuda() for a in imgs_np]
+    maps = [torch.zeros((s // 8) ** 2 * 40, dtype=torch.uint8, device="cuda") for s in sizes]
+    tab = fic.slice_table(imgs, maps)
+    ws = torch.empty(fic.batch_workspace_size(tab, p), dtype=torch.uint8, device="cuda")
+    ref = [fic.maps_to_numpy(fic.encode(im, p)) for im in imgs]
+    for call in range(3):
+        for m in maps:
+            m.zero_()
+        fic.encode_batch(tab, p, ws)
+        torch.cuda.synchronize()
+        for i, m in enumerate(maps):
+            assert np.array_equal(fic.maps_to_numpy(m), ref[i]), (call, i)
+    t = fic.last_batch_slice_ms(len(sizes))
+    assert all(x > 0 for x in t)
+
+
+def test_batch_rejects_host_pointers_and_short_workspace(fic):
+    p = fic.params(range_size=8, domain_stride=4, bit_depth=12)
+    im = torch.from_numpy(fic_synth.ct_slice(70, 64).astype(np.int16)).cuda()
+    mp = torch.zeros(64 * 40, dtype=torch.uint8, device="cuda")
+    tab = fic.slice_table([im], [mp])
+    need = fic.batch_workspace_size(tab, p)
+    with pytest.raises(fic.FicError):
+        fic.encode_batch(tab, p, torch.empty(need // 2, dtype=torch.uint8, device="cuda"))
+    host = fic.fic_slice(fic_synth.ct_slice(70, 64).astype(np.int16).ctypes.data, 64, 64, 64, mp.data_ptr())
+    bad = (fic.fic_slice * 1)(host)
+    with pytest.raises(fic.FicError):
+        fic.encode_batch(bad, p, torch.empty(need, dtype=torch.uint8, device="cuda"))
