@@ -76,6 +76,8 @@ def _load():
                                           ctypes.c_int, ctypes.c_int, fp]
         lib.orc_decode.argtypes = [ctypes.c_int, ctypes.c_int, pp, ip, ip, dp, dp, ctypes.c_int,
                                    ctypes.c_double, ctypes.c_int, dp, dp]
+        lib.orc_refine_grad.argtypes = [ctypes.c_int, ctypes.c_int, pp, ip, ip, dp, dp, ctypes.c_int,
+                                        ctypes.c_double, dp, dp, dp, dp]
         lib.orc_psnr.argtypes = [dp, dp, ctypes.c_size_t, ctypes.c_int]
         lib.orc_psnr.restype = ctypes.c_double
         lib.orc_num_domains_x.argtypes = [ctypes.c_int, pp]
@@ -200,3 +202,27 @@ def encode_quadtree(img, n_max=16, n_min=4, rms_split=8.0, bit_depth=8, s_bits=5
         level += 1
     out = np.array(leaves, dtype=QT_DTYPE)
     return out[np.lexsort((out["range_idx"], out["level"]))]
+
+
+def refine_grad(dom, sym, s, o, ref, n=8, t=8, bit_depth=8, iters=8, init=None):
+    """Loss (1/N) sum (x_T - ref)^2 of the unrolled unclamped decode with real
+    s, o per range, and its FP64 gradient (dL/ds, dL/do) by the adjoint of
+    the iteration.  Returns (loss, grad_s, grad_o)."""
+    lib = _load()
+    ref = np.ascontiguousarray(ref, np.float64)
+    h, w = ref.shape
+    p = params(n, t, bit_depth, 0, 0)
+    dom = np.ascontiguousarray(dom, np.int32)
+    sym = np.ascontiguousarray(sym, np.int32)
+    s = np.ascontiguousarray(s, np.float64)
+    o = np.ascontiguousarray(o, np.float64)
+    if init is None:
+        init = float(1 << (bit_depth - 1))
+    gs = np.zeros(len(s), np.float64)
+    go = np.zeros(len(s), np.float64)
+    loss = ctypes.c_double()
+    rc = lib.orc_refine_grad(w, h, ctypes.byref(p), _iptr(dom), _iptr(sym), _dptr(s), _dptr(o), int(iters),
+                             float(init), _dptr(ref), ctypes.byref(loss), _dptr(gs), _dptr(go))
+    if rc != 0:
+        raise MemoryError("oracle refine_grad failed")
+    return loss.value, gs, go

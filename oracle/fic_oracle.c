@@ -266,6 +266,79 @@ int orc_decode(int w, int h, const orc_params *p, const int32_t *dom, const int3
     return 0;
 }
 
+/* Differentiable refinement (the decoder with real-valued s and o):
+ * loss L = (1/N) sum_p (x_T[p] - ref[p])^2 of the unrolled, unclamped decode
+ * x_{t+1} = W(x_t) from x_0 = init (W: every range's pixels set to
+ * s_r * S_k(tau(x_t restricted to its domain)) + o_r, as in decode_step), and
+ * its gradient with respect to every s_r and o_r by the adjoint of the
+ * iteration, taken step by step in reverse:
+ *   g_T = 2 (x_T - ref) / N;
+ *   for t = T-1 .. 0:  with a_t[p] the contracted, transformed domain value
+ *   that output pixel p of range r reads from x_t,
+ *     dL/ds_r += sum_{p in r} g_{t+1}[p] a_t[p],   dL/do_r += sum_{p in r} g_{t+1}[p],
+ *     g_t = W'^T g_{t+1}: each output pixel p adds s_r/4 g_{t+1}[p] to each of
+ *     the four source pixels it averages.
+ * Every iterate is kept (plain, no checkpointing). */
+int orc_refine_grad(int w, int h, const orc_params *p, const int32_t *dom, const int32_t *sym, const double *s,
+                    const double *o, int iters, double init, const double *ref, double *loss, double *grad_s,
+                    double *grad_o)
+{
+    const size_t npx = (size_t)w * h;
+    const int n = p->n, nx = w / n, ny = h / n, R = nx * ny;
+    const int U = orc_num_domains_x(w, p);
+    double *x = (double *)malloc(sizeof(double) * npx * (size_t)(iters + 1));
+    double *g = (double *)malloc(sizeof(double) * npx);
+    double *g2 = (double *)malloc(sizeof(double) * npx);
+    if (!x || !g || !g2) {
+        free(x);
+        free(g);
+        free(g2);
+        return -1;
+    }
+    for (size_t i = 0; i < npx; ++i) x[i] = init;
+    for (int t = 0; t < iters; ++t) decode_step(x + npx * t, x + npx * (t + 1), w, h, p, dom, sym, s, o);
+    const double *xT = x + npx * iters;
+    double se = 0.0;
+    for (size_t i = 0; i < npx; ++i) {
+        const double dlt = xT[i] - ref[i];
+        se += dlt * dlt;
+        g[i] = 2.0 * dlt / (double)npx;
+    }
+    *loss = se / (double)npx;
+    for (int r = 0; r < R; ++r) grad_s[r] = grad_o[r] = 0.0;
+    for (int t = iters - 1; t >= 0; --t) {
+        const double *xt = x + npx * t;
+        for (size_t i = 0; i < npx; ++i) g2[i] = 0.0;
+        for (int r = 0; r < R; ++r) {
+            const int ry = (r / nx) * n, rx = (r % nx) * n;
+            const int dy = (dom[r] / U) * p->t, dx = (dom[r] % U) * p->t;
+            for (int y = 0; y < n; ++y)
+                for (int xx = 0; xx < n; ++xx) {
+                    int sy, sx;
+                    sym_src(sym[r], n, y, xx, &sy, &sx);
+                    const size_t q = (size_t)(dy + 2 * sy) * w + (dx + 2 * sx);
+                    const double a = 0.25 * (xt[q] + xt[q + 1] + xt[q + w] + xt[q + w + 1]);
+                    const double gp = g[(size_t)(ry + y) * w + rx + xx];
+                    grad_s[r] += gp * a;
+                    grad_o[r] += gp;
+                    const double back = 0.25 * s[r] * gp;
+                    g2[q] += back;
+                    g2[q + 1] += back;
+                    g2[q + w] += back;
+                    g2[q + w + 1] += back;
+                }
+        }
+        double *tmp = g;
+        g = g2;
+        g2 = tmp;
+    }
+    (void)ny;
+    free(x);
+    free(g);
+    free(g2);
+    return 0;
+}
+
 /* Peak signal-to-noise ratio 10*log10(P^2 / MSE) in dB. */
 double orc_psnr(const double *ref, const double *img, size_t npx, int bit_depth)
 {
