@@ -286,6 +286,40 @@ int fic_batch_workspace_size(const fic_slice *slices, int n, const fic_params *p
  * inside the graph; waits for them.  out has n entries. */
 int fic_last_batch_slice_ms(float *out, int n);
 
+/*
+ * Differentiable refinement (fic_refine*): the decoder with real-valued FP32
+ * contrast s_r and offset o_r per range (each map's domain and symmetry
+ * fixed), unrolled for `iters` Jacobi iterations without clamping from a flat
+ * x_0 = init:  x_{t+1}[p] = s_r * a_t[p] + o_r, where a_t[p] is the 2x2 mean
+ * of x_t that S_k places at pixel p of range r (the maps of eq 6, iterated as
+ * the decoder does).  The adjoint of that iteration gives dL/ds and dL/do for
+ * a loss L of x_T.  The paper decodes with the fitted coefficients; refining
+ * them against the decoded image rather than the collage bound is an
+ * extension of it.  Every pointer is device memory; maps as fic_encode wrote
+ * them for this w, h and parameters.  Iterates are checkpointed every second
+ * step: ckpt holds ceil(iters/2) w x h float images (x_0, x_2, ...), and the
+ * odd ones are recomputed in the reverse sweep.  The adjoint sums in a fixed
+ * order (no atomics): results are deterministic.
+ */
+int fic_refine_workspace_size(int w, int h, const fic_params *p, int iters, size_t *bytes);
+/* x_out = x_T (w x h floats); ckpt as above (filled for fic_refine_backward). */
+int fic_refine_forward(const fic_map *maps, int w, int h, const fic_params *p, const float *s, const float *o,
+                       float init, int iters, float *x_out, float *ckpt, void *workspace, size_t workspace_bytes,
+                       void *stream);
+/* grad_x = dL/dx_T (w x h); writes dL/ds and dL/do (one per range). */
+int fic_refine_backward(const fic_map *maps, int w, int h, const fic_params *p, const float *s, const float *o,
+                        int iters, const float *ckpt, const float *grad_x, float *grad_s, float *grad_o,
+                        void *workspace, size_t workspace_bytes, void *stream);
+/* fic_refine -- the whole refinement: Adam (beta1 0.9, beta2 0.999, eps 1e-8,
+ * step size lr on s and on o/P) for `steps` steps on L = mean((x_T - img)^2),
+ * x_0 = 2^(B-1).  s and o (one per range) are read and updated in place.
+ * loss (optional, steps + 1 floats): L before each step and after the last.
+ * img as in fic_encode but device memory.  One step is a CUDA graph replay;
+ * asynchronous on `stream`. */
+int fic_refine(const void *img, int w, int h, int pitch_px, const fic_params *p, const fic_map *maps, float *s,
+               float *o, int steps, int iters, float lr, float *loss, void *workspace, size_t workspace_bytes,
+               void *stream);
+
 /* Phase durations (ms) of the last fic_encode on this host thread that ran
  * with FIC_FLAG_PHASE_TIMING: out[0] prep, out[1] search, out[2] re-score,
  * out[3] fallback, out[4] map output.  Waits for those events. */

@@ -883,6 +883,154 @@ int run_batch(const fic_slice *slices, int n, const fic_params *p, void *workspa
     return FIC_OK;
 }
 
+// ------------------------------------------------------------ refinement
+
+struct RefineLayout {
+    size_t roff, rsym, dcount, doff, cursor, drng, tmp, g0, g1, partial, step, ds, dof, m, v, C, nitem, ioff, items,
+        ipart, ckpt, xT, total;
+};
+
+int refine_setup(int w, int h, const fic_params *p, int iters, Geometry &g, RefineGeo &rg, RefineLayout &L)
+{
+    if (!p || iters < 1 || iters > 1000) return FIC_ERR_BAD_ARG;
+    int rc = make_geometry(w, h, w, p, g);
+    if (rc != FIC_OK) return rc;
+    rg = RefineGeo{g.w, g.h, g.n, g.ln, g.nx, g.R, g.t, g.U, g.V, g.D};
+    const size_t N = (size_t)w * h;
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        const size_t at = o;
+        o = align_up(o + bytes);
+        return at;
+    };
+    L.roff = take(sizeof(int) * g.R);
+    L.rsym = take(sizeof(int) * g.R);
+    L.dcount = take(sizeof(int) * g.D);
+    L.doff = take(sizeof(int) * (g.D + 1));
+    L.cursor = take(sizeof(int) * g.D);
+    L.drng = take(sizeof(int) * g.R);
+    L.tmp = take(sizeof(float) * N);
+    L.g0 = take(sizeof(float) * N);
+    L.g1 = take(sizeof(float) * N);
+    L.partial = take(sizeof(double) * refine_partials(rg));
+    L.step = take(sizeof(int));
+    L.ds = take(sizeof(float) * g.R);
+    L.dof = take(sizeof(float) * g.R);
+    L.m = take(sizeof(float) * 2 * g.R);
+    L.v = take(sizeof(float) * 2 * g.R);
+    L.C = take(sizeof(float) * (size_t)g.D * g.m);
+    L.nitem = take(sizeof(int) * g.D);
+    L.ioff = take(sizeof(int) * (g.D + 1));
+    L.items = take(sizeof(int4) * g.R);
+    L.ipart = take(sizeof(float) * (size_t)g.R * g.m);
+    L.ckpt = take(sizeof(float) * N * (size_t)((iters + 1) / 2));  // fic_refine only
+    L.xT = take(sizeof(float) * N);
+    L.total = o;
+    return FIC_OK;
+}
+
+RefineBufs refine_bufs(const RefineLayout &L, char *ws)
+{
+    RefineBufs b;
+    b.roff = reinterpret_cast<int *>(ws + L.roff);
+    b.rsym = reinterpret_cast<int *>(ws + L.rsym);
+    b.dcount = reinterpret_cast<int *>(ws + L.dcount);
+    b.doff = reinterpret_cast<int *>(ws + L.doff);
+    b.cursor = reinterpret_cast<int *>(ws + L.cursor);
+    b.drng = reinterpret_cast<int *>(ws + L.drng);
+    b.tmp = reinterpret_cast<float *>(ws + L.tmp);
+    b.g[0] = reinterpret_cast<float *>(ws + L.g0);
+    b.g[1] = reinterpret_cast<float *>(ws + L.g1);
+    b.partial = reinterpret_cast<double *>(ws + L.partial);
+    b.step = reinterpret_cast<int *>(ws + L.step);
+    b.ds = reinterpret_cast<float *>(ws + L.ds);
+    b.dof = reinterpret_cast<float *>(ws + L.dof);
+    b.m = reinterpret_cast<float *>(ws + L.m);
+    b.v = reinterpret_cast<float *>(ws + L.v);
+    b.C = reinterpret_cast<float *>(ws + L.C);
+    b.nitem = reinterpret_cast<int *>(ws + L.nitem);
+    b.ioff = reinterpret_cast<int *>(ws + L.ioff);
+    b.items = reinterpret_cast<int4 *>(ws + L.items);
+    b.ipart = reinterpret_cast<float *>(ws + L.ipart);
+    return b;
+}
+
+int refine_check_ws(void *workspace, size_t bytes, size_t need)
+{
+    if (!workspace) return FIC_ERR_BAD_ARG;
+    if (bytes < need) return FIC_ERR_CAPACITY;
+    if (reinterpret_cast<uintptr_t>(workspace) & (kAlign - 1)) return FIC_ERR_BAD_ARG;
+    return FIC_OK;
+}
+
+int cuda_rc(cudaError_t e)
+{
+    if (e == cudaSuccess) return FIC_OK;
+    cudaGetLastError();
+    return FIC_ERR_CUDA;
+}
+
+thread_local cudaStream_t g_refine_cap = nullptr;
+
+int run_refine(const void *img, int w, int h, int pitch_px, const fic_params *p, const fic_map *maps, float *s,
+               float *o, int steps, int iters, float lr, float *loss, void *workspace, size_t workspace_bytes,
+               void *stream)
+{
+    Geometry g;
+    RefineGeo rg;
+    RefineLayout L;
+    int rc = refine_setup(w, h, p, iters, g, rg, L);
+    if (rc != FIC_OK) return rc;
+    if (!img || !maps || !s || !o || steps < 0 || pitch_px < w || !(lr >= 0.0f)) return FIC_ERR_BAD_ARG;
+    if ((rc = refine_check_ws(workspace, workspace_bytes, L.total)) != FIC_OK) return rc;
+    if (!is_device_ptr(img) || !is_device_ptr(maps) || !is_device_ptr(s) || !is_device_ptr(o) ||
+        (loss && !is_device_ptr(loss)))
+        return FIC_ERR_BAD_ARG;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    char *ws = static_cast<char *>(workspace);
+    const RefineBufs b = refine_bufs(L, ws);
+    float *ckpt = reinterpret_cast<float *>(ws + L.ckpt);
+    float *xT = reinterpret_cast<float *>(ws + L.xT);
+    const float init = (float)(1 << (g.B - 1));
+    const float P = (float)g.P;
+    cudaError_t e = refine_ranges(rg, maps, b, true, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b.step, 0, sizeof(int), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b.m, 0, sizeof(float) * 2 * g.R, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b.v, 0, sizeof(float) * 2 * g.R, st);
+    if (e != cudaSuccess) return cuda_rc(e);
+    // one step: forward, loss and dL/dx_T (counter += 1), reverse sweep, Adam
+    auto one_step = [&](cudaStream_t q) {
+        cudaError_t r = refine_forward(rg, b, s, o, init, iters, ckpt, xT, q);
+        if (r == cudaSuccess) r = refine_loss(rg, b, xT, img, g.B, pitch_px, b.g[0], loss, 1, q);
+        if (r == cudaSuccess) r = refine_backward(rg, b, s, o, iters, ckpt, b.g[0], b.ds, b.dof, q);
+        if (r == cudaSuccess) r = refine_adam(rg, b, s, o, lr, P, q);
+        return r;
+    };
+    if (steps > 0) {
+        if (!g_refine_cap && cudaStreamCreateWithFlags(&g_refine_cap, cudaStreamNonBlocking) != cudaSuccess)
+            return cuda_rc(cudaErrorUnknown);
+        // capture one step from a private stream (the caller's may be the
+        // legacy stream) ordered after the set-up above, then replay it
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        e = cudaStreamBeginCapture(g_refine_cap, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            const cudaError_t es = one_step(g_refine_cap);
+            const cudaError_t ee = cudaStreamEndCapture(g_refine_cap, &graph);
+            e = es != cudaSuccess ? es : ee;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+        for (int i = 0; i < steps && e == cudaSuccess; ++i) e = cudaGraphLaunch(exec, st);
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return cuda_rc(e);
+    }
+    // the loss after the last step
+    e = refine_forward(rg, b, s, o, init, iters, ckpt, xT, st);
+    if (e == cudaSuccess) e = refine_loss(rg, b, xT, img, g.B, pitch_px, b.g[0], loss, 0, st);
+    return cuda_rc(e);
+}
+
 }  // namespace
 
 namespace fic {
@@ -1069,6 +1217,62 @@ int fic_last_batch_slice_ms(float *out, int n)
             return FIC_ERR_CUDA;
         }
     return FIC_OK;
+}
+
+int fic_refine_workspace_size(int w, int h, const fic_params *p, int iters, size_t *bytes)
+{
+    if (!bytes) return FIC_ERR_BAD_ARG;
+    Geometry g;
+    RefineGeo rg;
+    RefineLayout L;
+    const int rc = refine_setup(w, h, p, iters, g, rg, L);
+    if (rc != FIC_OK) return rc;
+    *bytes = L.total;
+    return FIC_OK;
+}
+
+int fic_refine_forward(const fic_map *maps, int w, int h, const fic_params *p, const float *s, const float *o,
+                       float init, int iters, float *x_out, float *ckpt, void *workspace, size_t workspace_bytes,
+                       void *stream)
+{
+    Geometry g;
+    RefineGeo rg;
+    RefineLayout L;
+    int rc = refine_setup(w, h, p, iters, g, rg, L);
+    if (rc != FIC_OK) return rc;
+    if (!maps || !s || !o || !x_out || !ckpt) return FIC_ERR_BAD_ARG;
+    if ((rc = refine_check_ws(workspace, workspace_bytes, L.total)) != FIC_OK) return rc;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const RefineBufs b = refine_bufs(L, static_cast<char *>(workspace));
+    cudaError_t e = refine_ranges(rg, maps, b, false, st);
+    if (e == cudaSuccess) e = refine_forward(rg, b, s, o, init, iters, ckpt, x_out, st);
+    return cuda_rc(e);
+}
+
+int fic_refine_backward(const fic_map *maps, int w, int h, const fic_params *p, const float *s, const float *o,
+                        int iters, const float *ckpt, const float *grad_x, float *grad_s, float *grad_o,
+                        void *workspace, size_t workspace_bytes, void *stream)
+{
+    Geometry g;
+    RefineGeo rg;
+    RefineLayout L;
+    int rc = refine_setup(w, h, p, iters, g, rg, L);
+    if (rc != FIC_OK) return rc;
+    if (!maps || !s || !o || !ckpt || !grad_x || !grad_s || !grad_o) return FIC_ERR_BAD_ARG;
+    if ((rc = refine_check_ws(workspace, workspace_bytes, L.total)) != FIC_OK) return rc;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const RefineBufs b = refine_bufs(L, static_cast<char *>(workspace));
+    cudaError_t e = refine_ranges(rg, maps, b, true, st);
+    if (e == cudaSuccess) e = refine_backward(rg, b, s, o, iters, ckpt, grad_x, grad_s, grad_o, st);
+    return cuda_rc(e);
+}
+
+int fic_refine(const void *img, int w, int h, int pitch_px, const fic_params *p, const fic_map *maps, float *s,
+               float *o, int steps, int iters, float lr, float *loss, void *workspace, size_t workspace_bytes,
+               void *stream)
+{
+    return run_refine(img, w, h, pitch_px, p, maps, s, o, steps, iters, lr, loss, workspace, workspace_bytes,
+                      stream);
 }
 
 int fic_last_encode_stats(int64_t out[4])

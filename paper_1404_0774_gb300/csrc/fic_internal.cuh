@@ -498,6 +498,33 @@ struct QtLevels {
 cudaError_t launch_qt_split(int R, int nx, int m, const fic_map *maps, const int *active, double rms_split, int last,
                             int *leaf, int *active_next, cudaStream_t st);
 cudaError_t launch_qt_gather(const QtLevels &lv, int *lists, fic_qmap *out, int cap, int *counts, cudaStream_t st);
+// Differentiable refinement (the unrolled decoder with FP32 s, o and its adjoint).
+struct RefineGeo {
+    int w, h, n, ln, nx, R, t, U, V, D;
+};
+struct RefineBufs {
+    int *roff, *rsym;                 // per range: domain offset, symmetry
+    int *dcount, *doff, *cursor, *drng;  // domain -> ranges index (CSR, rows sorted)
+    float *tmp, *g[2];                // scratch iterate, adjoint ping-pong
+    double *partial;                  // loss partial sums
+    int *step;                        // Adam step counter (device)
+    float *ds, *dof, *m, *v;          // gradients, Adam moments (2R)
+    float *C;                         // per-domain adjoint sums [D][m]
+    int *nitem, *ioff;                // adjoint work items per domain, offsets (D + 1)
+    int4 *items;                      // (domain, first user, end user) per item, at most R
+    float *ipart;                     // per-item partial sums [R][m]
+};
+cudaError_t refine_ranges(const RefineGeo &rg, const fic_map *maps, const RefineBufs &b, bool with_index,
+                          cudaStream_t st);
+cudaError_t refine_forward(const RefineGeo &rg, const RefineBufs &b, const float *s, const float *o, float init,
+                           int iters, float *ckpt, float *x_out, cudaStream_t st);
+cudaError_t refine_backward(const RefineGeo &rg, const RefineBufs &b, const float *s, const float *o, int iters,
+                            const float *ckpt, const float *grad_x, float *ds, float *dof, cudaStream_t st);
+cudaError_t refine_loss(const RefineGeo &rg, const RefineBufs &b, const float *x, const void *img, int B, int pitch,
+                        float *g, float *loss, int advance, cudaStream_t st);
+cudaError_t refine_adam(const RefineGeo &rg, const RefineBufs &b, float *s, float *o, float lr, float P,
+                        cudaStream_t st);
+size_t refine_partials(const RefineGeo &rg);
 // Key-space value that excludes s-code-0 candidates once a list holds one.
 constexpr float kZeroPenalty = 1e30f;
 

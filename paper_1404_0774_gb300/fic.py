@@ -82,6 +82,13 @@ def lib():
         L.fic_encode_batch.argtypes = [vp, ctypes.c_int, pp, vp, sz, vp]
         L.fic_batch_workspace_size.argtypes = [vp, ctypes.c_int, pp, ctypes.POINTER(sz)]
         L.fic_last_batch_slice_ms.argtypes = [ctypes.POINTER(ctypes.c_float), ctypes.c_int]
+        L.fic_refine_workspace_size.argtypes = [ctypes.c_int, ctypes.c_int, pp, ctypes.c_int, ctypes.POINTER(sz)]
+        L.fic_refine_forward.argtypes = [vp, ctypes.c_int, ctypes.c_int, pp, vp, vp, ctypes.c_float, ctypes.c_int,
+                                         vp, vp, vp, sz, vp]
+        L.fic_refine_backward.argtypes = [vp, ctypes.c_int, ctypes.c_int, pp, vp, vp, ctypes.c_int, vp, vp, vp, vp,
+                                          vp, sz, vp]
+        L.fic_refine.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, pp, vp, vp, vp, ctypes.c_int,
+                                 ctypes.c_int, ctypes.c_float, vp, vp, sz, vp]
         _lib = L
     return _lib
 
@@ -283,6 +290,91 @@ def last_batch_slice_ms(n: int):
     out = (ctypes.c_float * n)()
     _check(lib().fic_last_batch_slice_ms(out, n), "fic_last_batch_slice_ms")
     return list(out)
+
+
+def refine_workspace_size(w: int, h: int, p: fic_params, iters: int) -> int:
+    b = ctypes.c_size_t()
+    _check(lib().fic_refine_workspace_size(w, h, ctypes.byref(p), iters, ctypes.byref(b)),
+           "fic_refine_workspace_size")
+    return b.value
+
+
+def map_coefficients(maps):
+    """(s, o) as float32 CUDA tensors (one per range) from a device maps tensor."""
+    import torch
+
+    f = maps.view(-1, MAP_DTYPE.itemsize)[:, 20:28].contiguous().view(torch.float32)
+    return f[:, 0].clone(), f[:, 1].clone()
+
+
+def _decode_fn():
+    import torch
+
+    class DecodeFn(torch.autograd.Function):
+        """x_T of the unrolled decoder as a function of (s, o); backward runs
+        the library's adjoint kernels (checkpointed every second iterate)."""
+
+        @staticmethod
+        def forward(ctx, s, o, maps, w, h, p, iters, init, ws):
+            x = torch.empty((h, w), dtype=torch.float32, device=s.device)
+            ckpt = torch.empty(((iters + 1) // 2) * h * w, dtype=torch.float32, device=s.device)
+            st = _stream_ptr(None)
+            _check(lib().fic_refine_forward(maps.data_ptr(), w, h, ctypes.byref(p), s.data_ptr(), o.data_ptr(),
+                                            ctypes.c_float(init), iters, x.data_ptr(), ckpt.data_ptr(),
+                                            ws.data_ptr(), ws.numel(), st), "fic_refine_forward")
+            ctx.save_for_backward(s, o, ckpt)
+            ctx.meta = (maps, w, h, p, iters, ws)
+            return x
+
+        @staticmethod
+        def backward(ctx, gx):
+            s, o, ckpt = ctx.saved_tensors
+            maps, w, h, p, iters, ws = ctx.meta
+            gx = gx.contiguous()
+            gs, go = torch.empty_like(s), torch.empty_like(o)
+            _check(lib().fic_refine_backward(maps.data_ptr(), w, h, ctypes.byref(p), s.data_ptr(), o.data_ptr(),
+                                             iters, ckpt.data_ptr(), gx.data_ptr(), gs.data_ptr(), go.data_ptr(),
+                                             ws.data_ptr(), ws.numel(), _stream_ptr(None)), "fic_refine_backward")
+            return gs, go, None, None, None, None, None, None, None
+
+    return DecodeFn
+
+
+_DecodeFn = None
+
+
+def decode_differentiable(s, o, maps, w: int, h: int, p: fic_params, iters: int = 8, init: float | None = None,
+                          workspace=None):
+    """x_T (h x w float32 CUDA tensor) of the unrolled, unclamped decoder with
+    real-valued s, o (CUDA float32, one per range); differentiable in s and o
+    through the library's adjoint (a torch.autograd.Function)."""
+    global _DecodeFn
+    import torch
+
+    if _DecodeFn is None:
+        _DecodeFn = _decode_fn()
+    if init is None:
+        init = float(1 << (p.bit_depth - 1))
+    if workspace is None:
+        workspace = torch.empty(refine_workspace_size(w, h, p, iters), dtype=torch.uint8, device=s.device)
+    return _DecodeFn.apply(s.contiguous(), o.contiguous(), maps, w, h, p, iters, float(init), workspace)
+
+
+def refine(img, maps, s, o, p: fic_params, steps: int = 200, iters: int = 8, lr: float = 1e-3, loss=None,
+           workspace=None, stream=None):
+    """The library's whole refinement loop (Adam on s and o/P, CUDA graph per
+    step); s, o updated in place; returns the loss tensor (steps + 1 values)."""
+    import torch
+
+    h, w = int(img.shape[0]), int(img.shape[1])
+    if loss is None:
+        loss = torch.empty(steps + 1, dtype=torch.float32, device=s.device)
+    if workspace is None:
+        workspace = torch.empty(refine_workspace_size(w, h, p, iters), dtype=torch.uint8, device=s.device)
+    _check(lib().fic_refine(img.data_ptr(), w, h, int(img.stride(0)), ctypes.byref(p), maps.data_ptr(),
+                            s.data_ptr(), o.data_ptr(), steps, iters, ctypes.c_float(lr), loss.data_ptr(),
+                            workspace.data_ptr(), workspace.numel(), _stream_ptr(stream)), "fic_refine")
+    return loss
 
 
 def cross_terms(img, p: fic_params, out=None, stream=None):
