@@ -157,6 +157,23 @@ int fic_decode(const fic_map *maps, int n_maps, int w, int h, const fic_params *
 /* Device workspace bytes that fic_decode needs for a w x h image. */
 int fic_decode_workspace_size(int w, int h, const fic_params *p, size_t *bytes);
 
+/*
+ * fic_decode_scaled -- resolution-independent decoding (the property the
+ *   paper's introduction credits fractal coding with): the maps of a w x h
+ *   encode decoded at 2^scale_log2 times that size.  Every range block and
+ *   domain position and side is scaled (range n*z at (x*z, y*z), domain 2n*z
+ *   at (u*t*z, v*t*z), z = 2^scale_log2) while the 2x2 contraction, the
+ *   symmetries and s, o stay as encoded; iterated as fic_decode does.
+ *   scale_log2 in [-3, 3]; for z < 1 the range side n, the domain stride t,
+ *   w and h must be multiples of 1/z.  out: (w*z) x (h*z) floats.  At z = 1
+ *   this is fic_decode.  Averaging 2x2 blocks of the unclamped decode at 2z
+ *   gives the unclamped decode at z (the contraction commutes with the
+ *   symmetries), so every scale decodes one consistent image.
+ */
+int fic_decode_scaled(const fic_map *maps, int n_maps, int w, int h, const fic_params *p, int scale_log2, float init,
+                      float *out, void *workspace, size_t workspace_bytes, void *stream);
+int fic_decode_scaled_workspace_size(int w, int h, const fic_params *p, int scale_log2, size_t *bytes);
+
 /* Human-readable message for a status code. */
 const char *fic_status_str(int status);
 

@@ -1031,6 +1031,93 @@ int run_refine(const void *img, int w, int h, int pitch_px, const fic_params *p,
     return cuda_rc(e);
 }
 
+// ------------------------------------------------------------ decode
+
+// g: the encode geometry of the maps; gs: the same maps decoded at scale
+// 2^scale_log2 (range and domain sides and positions scaled, the 2x2
+// contraction kept; range and domain counts and indices unchanged).
+int decode_geometry(int w, int h, const fic_params *p, int scale_log2, Geometry &g, Geometry &gs)
+{
+    int rc = make_geometry(w, h, w, p, g);
+    if (rc != FIC_OK) return rc;
+    if (scale_log2 < -3 || scale_log2 > 3) return FIC_ERR_BAD_ARG;
+    gs = g;
+    if (scale_log2 >= 0) {
+        const int z = 1 << scale_log2;
+        if ((long long)w * z * h * z > (1LL << 30)) return FIC_ERR_SIZE;
+        gs.w = w * z, gs.h = h * z, gs.n = g.n * z, gs.t = g.t * z;
+    } else {
+        const int z = 1 << -scale_log2;
+        // positions and sides must stay whole pixels; a range keeps >= 1 pixel
+        if (g.n % z || g.t % z || w % z || h % z) return FIC_ERR_SIZE;
+        gs.w = w / z, gs.h = h / z, gs.n = g.n / z, gs.t = g.t / z;
+    }
+    gs.pitch = gs.w;
+    gs.m = gs.n * gs.n;
+    gs.ln = 0;
+    while ((1 << gs.ln) < gs.n) ++gs.ln;
+    return FIC_OK;
+}
+
+int run_decode(const fic_map *maps, int n_maps, int w, int h, const fic_params *p, int scale_log2, float init,
+               float *out, void *workspace, size_t workspace_bytes, void *stream)
+{
+    if (!maps || !out) return FIC_ERR_BAD_ARG;
+    Geometry g, gs;
+    int rc = decode_geometry(w, h, p, scale_log2, g, gs);
+    if (rc != FIC_OK) return rc;
+    if (n_maps != g.R) return FIC_ERR_CAPACITY;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const size_t npx = (size_t)gs.w * gs.h;
+    const size_t dws = align_up(decode_workspace_bytes(gs));
+    const size_t maps_b = align_up(sizeof(fic_map) * g.R);
+    const size_t out_b = align_up(sizeof(float) * npx);
+    const size_t total = dws + maps_b + out_b;
+    char *ws = static_cast<char *>(workspace);
+    bool owned = false;
+    const bool maps_dev = is_device_ptr(maps);
+    const bool out_dev = is_device_ptr(out);
+    if (!maps_dev) {
+        // host maps are validated here; device maps are trusted to come from fic_encode
+        for (int r = 0; r < g.R; ++r)
+            if (maps[r].domain_idx >= (uint32_t)g.D || maps[r].iso < 0 || maps[r].iso > 7)
+                return FIC_ERR_BAD_ARG;
+    }
+    if (ws) {
+        if (workspace_bytes < total) return FIC_ERR_CAPACITY;
+        if (reinterpret_cast<uintptr_t>(ws) & (kAlign - 1)) return FIC_ERR_BAD_ARG;
+    } else {
+        if (cudaMallocAsync(reinterpret_cast<void **>(&ws), total, st) != cudaSuccess) {
+            cudaGetLastError();
+            return FIC_ERR_CUDA;
+        }
+        owned = true;
+    }
+    {
+        const fic_map *dmaps = maps;
+        float *dout = out_dev ? out : reinterpret_cast<float *>(ws + dws + maps_b);
+        if (!maps_dev) {
+            FIC_CUDA(cudaMemcpyAsync(ws + dws, maps, sizeof(fic_map) * g.R, cudaMemcpyHostToDevice, st));
+            dmaps = reinterpret_cast<const fic_map *>(ws + dws);
+        }
+        FIC_CUDA(launch_decode(gs, dmaps, init, p->decode_iters, ws, dout, st));
+        if (!out_dev) {
+            FIC_CUDA(cudaMemcpyAsync(out, dout, sizeof(float) * npx, cudaMemcpyDeviceToHost, st));
+            FIC_CUDA(cudaStreamSynchronize(st));
+        } else if (!maps_dev) {
+            FIC_CUDA(cudaStreamSynchronize(st));
+        }
+    }
+done:
+    if (owned) {
+        if (cudaFreeAsync(ws, st) != cudaSuccess) {
+            cudaGetLastError();
+            if (rc == FIC_OK) rc = FIC_ERR_CUDA;
+        }
+    }
+    return rc;
+}
+
 }  // namespace
 
 namespace fic {
@@ -1063,69 +1150,28 @@ int fic_cross_terms(const void *img, int w, int h, int pitch_px, const fic_param
 int fic_decode(const fic_map *maps, int n_maps, int w, int h, const fic_params *p, float init,
                float *out, void *workspace, size_t workspace_bytes, void *stream)
 {
-    if (!maps || !out) return FIC_ERR_BAD_ARG;
-    Geometry g;
-    int rc = make_geometry(w, h, w, p, g);
-    if (rc != FIC_OK) return rc;
-    if (n_maps != g.R) return FIC_ERR_CAPACITY;
-    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    const size_t dws = align_up(decode_workspace_bytes(g));
-    const size_t maps_b = align_up(sizeof(fic_map) * g.R);
-    const size_t out_b = align_up(sizeof(float) * (size_t)w * h);
-    const size_t total = dws + maps_b + out_b;
-    char *ws = static_cast<char *>(workspace);
-    bool owned = false;
-    const bool maps_dev = is_device_ptr(maps);
-    const bool out_dev = is_device_ptr(out);
-    if (!maps_dev) {
-        // host maps are validated here; device maps are trusted to come from fic_encode
-        for (int r = 0; r < g.R; ++r)
-            if (maps[r].domain_idx >= (uint32_t)g.D || maps[r].iso < 0 || maps[r].iso > 7)
-                return FIC_ERR_BAD_ARG;
-    }
-    if (ws) {
-        if (workspace_bytes < total) return FIC_ERR_CAPACITY;
-        if (reinterpret_cast<uintptr_t>(ws) & (kAlign - 1)) return FIC_ERR_BAD_ARG;
-    } else {
-        if (cudaMallocAsync(reinterpret_cast<void **>(&ws), total, st) != cudaSuccess) {
-            cudaGetLastError();
-            return FIC_ERR_CUDA;
-        }
-        owned = true;
-    }
-    {
-        const fic_map *dmaps = maps;
-        float *dout = out_dev ? out : reinterpret_cast<float *>(ws + dws + maps_b);
-        if (!maps_dev) {
-            FIC_CUDA(cudaMemcpyAsync(ws + dws, maps, sizeof(fic_map) * g.R, cudaMemcpyHostToDevice, st));
-            dmaps = reinterpret_cast<const fic_map *>(ws + dws);
-        }
-        FIC_CUDA(launch_decode(g, dmaps, init, p->decode_iters, ws, dout, st));
-        if (!out_dev) {
-            FIC_CUDA(cudaMemcpyAsync(out, dout, sizeof(float) * (size_t)w * h, cudaMemcpyDeviceToHost, st));
-            FIC_CUDA(cudaStreamSynchronize(st));
-        } else if (!maps_dev) {
-            FIC_CUDA(cudaStreamSynchronize(st));
-        }
-    }
-done:
-    if (owned) {
-        if (cudaFreeAsync(ws, st) != cudaSuccess) {
-            cudaGetLastError();
-            if (rc == FIC_OK) rc = FIC_ERR_CUDA;
-        }
-    }
-    return rc;
+    return run_decode(maps, n_maps, w, h, p, 0, init, out, workspace, workspace_bytes, stream);
+}
+
+int fic_decode_scaled(const fic_map *maps, int n_maps, int w, int h, const fic_params *p, int scale_log2, float init,
+                      float *out, void *workspace, size_t workspace_bytes, void *stream)
+{
+    return run_decode(maps, n_maps, w, h, p, scale_log2, init, out, workspace, workspace_bytes, stream);
 }
 
 int fic_decode_workspace_size(int w, int h, const fic_params *p, size_t *bytes)
 {
+    return fic_decode_scaled_workspace_size(w, h, p, 0, bytes);
+}
+
+int fic_decode_scaled_workspace_size(int w, int h, const fic_params *p, int scale_log2, size_t *bytes)
+{
     if (!bytes) return FIC_ERR_BAD_ARG;
-    Geometry g;
-    const int rc = make_geometry(w, h, w, p, g);
+    Geometry g, gs;
+    const int rc = decode_geometry(w, h, p, scale_log2, g, gs);
     if (rc != FIC_OK) return rc;
-    *bytes = align_up(decode_workspace_bytes(g)) + align_up(sizeof(fic_map) * g.R) +
-             align_up(sizeof(float) * (size_t)w * h);
+    *bytes = align_up(decode_workspace_bytes(gs)) + align_up(sizeof(fic_map) * g.R) +
+             align_up(sizeof(float) * (size_t)gs.w * gs.h);
     return FIC_OK;
 }
 

@@ -82,6 +82,10 @@ def lib():
         L.fic_encode_batch.argtypes = [vp, ctypes.c_int, pp, vp, sz, vp]
         L.fic_batch_workspace_size.argtypes = [vp, ctypes.c_int, pp, ctypes.POINTER(sz)]
         L.fic_last_batch_slice_ms.argtypes = [ctypes.POINTER(ctypes.c_float), ctypes.c_int]
+        L.fic_decode_scaled.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, pp, ctypes.c_int,
+                                        ctypes.c_float, vp, vp, sz, vp]
+        L.fic_decode_scaled_workspace_size.argtypes = [ctypes.c_int, ctypes.c_int, pp, ctypes.c_int,
+                                                       ctypes.POINTER(sz)]
         L.fic_refine_workspace_size.argtypes = [ctypes.c_int, ctypes.c_int, pp, ctypes.c_int, ctypes.POINTER(sz)]
         L.fic_refine_forward.argtypes = [vp, ctypes.c_int, ctypes.c_int, pp, vp, vp, ctypes.c_float, ctypes.c_int,
                                          vp, vp, vp, sz, vp]
@@ -375,6 +379,32 @@ def refine(img, maps, s, o, p: fic_params, steps: int = 200, iters: int = 8, lr:
                             s.data_ptr(), o.data_ptr(), steps, iters, ctypes.c_float(lr), loss.data_ptr(),
                             workspace.data_ptr(), workspace.numel(), _stream_ptr(stream)), "fic_refine")
     return loss
+
+
+def decode_scaled(maps, w: int, h: int, p: fic_params, scale_log2: int, init: float | None = None, out=None,
+                  stream=None):
+    """Decode maps of a w x h encode at 2^scale_log2 times the size (returns
+    an (h*z) x (w*z) float32 array / tensor, z = 2^scale_log2)."""
+    R, _ = counts(w, h, p)
+    z = 2.0 ** scale_log2
+    ow, oh = int(round(w * z)), int(round(h * z))
+    if init is None:
+        init = float(1 << (p.bit_depth - 1))
+    if _is_torch(maps):
+        import torch
+
+        if out is None:
+            out = torch.empty((oh, ow), dtype=torch.float32, device=maps.device)
+        maps_ptr, out_ptr, st = maps.data_ptr(), out.data_ptr(), _stream_ptr(stream)
+    else:
+        maps = np.ascontiguousarray(maps, MAP_DTYPE)
+        if out is None:
+            out = np.zeros((oh, ow), np.float32)
+        maps_ptr, out_ptr = maps.ctypes.data, out.ctypes.data
+        st = 0 if stream is None else _stream_ptr(stream)
+    _check(lib().fic_decode_scaled(maps_ptr, R, w, h, ctypes.byref(p), int(scale_log2), ctypes.c_float(init), out_ptr,
+                                   None, 0, st), "fic_decode_scaled")
+    return out
 
 
 def cross_terms(img, p: fic_params, out=None, stream=None):

@@ -228,3 +228,31 @@ def test_encode_parity_other_code_widths(fic, orc, search, n, sb, ob):
     img = fic_synth.ct_slice(23 + n + sb, 64)
     p = fic.params(range_size=n, domain_stride=4, bit_depth=12, s_bits=sb, o_bits=ob, search=search_code(fic, search))
     check_against_oracle(orc, img, gpu_encode(fic, img, p), n, 4, 12, sb=sb, ob=ob)
+
+
+@pytest.mark.parametrize("scale_log2", [-1, 1, 2])
+def test_decode_scaled_parity(fic, orc, scale_log2):
+    img = fic_synth.ct_slice(24, 64)
+    p = fic.params(range_size=8, domain_stride=4, bit_depth=12, decode_iters=10)
+    maps = fic.encode(torch.from_numpy(img.astype(np.int16)).cuda(), p)
+    out = fic.decode_scaled(maps, 64, 64, p, scale_log2)
+    torch.cuda.synchronize()
+    got = fic.maps_to_numpy(maps)
+    z = 2.0 ** scale_log2
+    size, n, t = int(64 * z), int(8 * z), int(4 * z)
+    ref = orc.decode(got["domain_idx"], got["iso"], got["s_code"] / 15.0, got["o_code"] * 4095 / 63.0, size, size,
+                     n=n, t=t, bit_depth=12, iters=10)
+    diff = np.abs(out.cpu().numpy().astype(np.float64) - ref)
+    assert out.shape == (size, size)
+    assert diff.max() < 2e-6 * 4096 * 10
+    host = fic.decode_scaled(got, 64, 64, p, scale_log2)
+    assert np.array_equal(host, out.cpu().numpy())
+    if scale_log2 == 1:
+        # 2x2 averages of the 2x decode match the unscaled decode (before the clamp: compare inside [0, P])
+        base = fic.decode(maps, 64, 64, p).cpu().numpy().astype(np.float64)
+        o = out.cpu().numpy().astype(np.float64)
+        down = 0.25 * (o[0::2, 0::2] + o[1::2, 0::2] + o[0::2, 1::2] + o[1::2, 1::2])
+        fine_in = (o > 0) & (o < 4095)
+        inside = (base > 0) & (base < 4095) & fine_in[0::2, 0::2] & fine_in[1::2, 0::2] & fine_in[0::2, 1::2] \
+            & fine_in[1::2, 1::2]
+        assert np.abs(down - base)[inside].max() < 2e-6 * 4096 * 10

@@ -288,3 +288,25 @@ def test_paper_counts(orc):
         R, D = orc.counts(size, size, n, t)
         assert (R, D) == (ranges, domains)
         assert R * D == tests
+
+
+def test_scaled_decode_averages_down_to_the_unscaled_decode(orc):
+    """Resolution-independent decoding: the same maps at twice the size (ranges
+    2n at 2x, domains 4n at stride 2t) average 2x2 down to the decode at the
+    original size, iterate by iterate, because the 2x2 contraction commutes
+    with the symmetries; likewise the original averages down to half size."""
+    img = fic_synth.ct_slice(34, 64)
+    fit = orc.encode(img, n=8, t=4, bit_depth=12)
+    args = (fit["d"], fit["k"], fit["s_hat"], fit["o_hat"])
+
+    def dec(z_num, z_den):
+        n, t, size = 8 * z_num // z_den, 4 * z_num // z_den, 64 * z_num // z_den
+        return orc.decode(*args, size, size, n=n, t=t, bit_depth=12, iters=6, clamp=False)
+
+    def down(x):
+        return 0.25 * (x[0::2, 0::2] + x[1::2, 0::2] + x[0::2, 1::2] + x[1::2, 1::2])
+
+    x1, x2, xh = dec(1, 1), dec(2, 1), dec(1, 2)
+    assert x2.shape == (128, 128) and xh.shape == (32, 32)
+    assert np.allclose(down(x2), x1, rtol=0, atol=1e-9 * 4095)
+    assert np.allclose(down(x1), xh, rtol=0, atol=1e-9 * 4095)
