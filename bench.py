@@ -553,7 +553,7 @@ def main():
     for _ in range(max(3, args.warmup)):
         step()
     torch.cuda.synchronize()
-    launches_per_step = 8  # statistics, compaction, operand rows, seed, search, re-score, exact fallback, output
+    launches_per_step = 8  # statistics, compaction, operand rows, seed, search, re-score, exact scans, output
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     if ws > 1:

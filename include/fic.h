@@ -220,7 +220,7 @@ int fic_cross_terms(const void *img, int w, int h, int pitch_px, const fic_param
  *     -- race on it: serialise them.
  *   - FIC_FLAG_PHASE_TIMING is rejected (it would create CUDA events).
  */
-#define FIC_STATIC_SCRATCH_BYTES (16u << 20)
+#define FIC_STATIC_SCRATCH_BYTES (32u << 20)
 int fic_encode_static(const void *img, int w, int h, int pitch_px, const fic_params *p, fic_map *maps,
                       int maps_cap, int *n_maps, void *stream);
 

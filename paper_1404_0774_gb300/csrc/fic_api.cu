@@ -173,7 +173,7 @@ int lists_per_split(int search)
 }
 
 struct EncLayout {
-    size_t img, ri, di, dconst, bblk, qblk, rs32, cb32, ra16, cb16, lists, winner, fb_list, fb_count,
+    size_t img, ri, di, dconst, bblk, qblk, rs32, cb32, ra16, cb16, lists, winner, fb_list, fb_count, span,
         tbest, partial, maps, rkeep, dkeep, act, dact, counts, dconst_c, dmap, total;
 };
 
@@ -201,7 +201,8 @@ EncLayout enc_layout(const Geometry &g, int search, int n_lists)
     L.lists = take(sizeof(ListEntry) * (size_t)g.R * n_lists * kListK);
     L.winner = take(sizeof(uint32_t) * g.R);
     L.fb_list = take(sizeof(int) * g.R);
-    L.fb_count = take(sizeof(int) * 2);
+    L.fb_count = take(sizeof(int) * 4);  // full-scan count, error flag, list-scan count
+    L.span = take(span_bytes(g, n_lists));
     L.tbest = take(sizeof(int) * g.R);
     L.partial = take(fallback_partial_bytes(g));
     L.maps = take(sizeof(fic_map) * g.R);
@@ -313,7 +314,7 @@ struct EncBufs {
     ListEntry *lists;
     uint32_t *winner;
     int *fb_list, *fb_count, *err, *tbest;
-    void *partial;
+    void *partial, *span;
     CompactBufs cb;
 };
 
@@ -336,6 +337,7 @@ EncBufs enc_bufs(const EncLayout &L, char *ws)
     b.err = b.fb_count + 1;
     b.tbest = reinterpret_cast<int *>(ws + L.tbest);
     b.partial = ws + L.partial;
+    b.span = ws + L.span;
     b.cb.rkeep = reinterpret_cast<int *>(ws + L.rkeep);
     b.cb.dkeep = reinterpret_cast<int *>(ws + L.dkeep);
     b.cb.act = reinterpret_cast<int *>(ws + L.act);
@@ -369,14 +371,14 @@ cudaError_t encode_pipeline(const Geometry &gd, const fic_params *p, int search,
     } while (0)
 #define FIC_MARK(i) \
     if (timed) FIC_STEP(cudaEventRecord(g_phase.ev[i], st))
-    FIC_STEP(cudaMemsetAsync(b.fb_count, 0, 2 * sizeof(int), st));
+    FIC_STEP(cudaMemsetAsync(b.fb_count, 0, 4 * sizeof(int), st));
     if (b.ra16) {  // zero the padding rows that complete the last TMA boxes
         const size_t row = sizeof(__half) * gd.KP;
         FIC_STEP(cudaMemsetAsync(ws + L.ra16 + row * gd.R, 0, row * (search_tc_rows(gd.R) - gd.R), st));
         FIC_STEP(cudaMemsetAsync(ws + L.cb16 + row * gd.N, 0, row * (search_tc_rows(gd.N) - gd.N), st));
     }
     FIC_MARK(0);
-    FIC_STEP(launch_prep(gd, dimg, ec, dense, active, b.ri, b.di, b.dconst, b.bblk, b.qblk, b.rs32, b.cb32, b.ra16,
+    FIC_STEP(launch_prep(gd, dimg, ec, dense, (search == FIC_SEARCH_TC && gd.split_hilo) ? 1 : 0, active, b.ri, b.di, b.dconst, b.bblk, b.qblk, b.rs32, b.cb32, b.ra16,
                          b.cb16, b.tbest, b.cb, st));
     if (!dump) FIC_STEP(launch_seed(gd, ec, b.ri, b.di, b.dconst, b.bblk, b.qblk, b.cb.rkeep, b.tbest, st));
     FIC_MARK(1);
@@ -391,10 +393,11 @@ cudaError_t encode_pipeline(const Geometry &gd, const fic_params *p, int search,
         FIC_STEP(launch_rescore(gd, ec, b.ri, b.di, b.bblk, b.qblk, b.lists, n_lists, b.cb.counts, b.cb.act, b.cb.rkeep,
                                 lists_per_split(search), search == FIC_SEARCH_TC ? search_tc_tile() : 64, target,
                                 n_split, sm_count(), (p->flags & FIC_FLAG_EXACT_SCAN) ? 1 : 0, b.winner, b.fb_list,
-                                b.fb_count, b.partial, st));
+                                b.fb_count, b.partial, b.span, st));
         FIC_MARK(3);
-        FIC_STEP(launch_fallback(gd, b.ri, b.di, b.bblk, b.qblk, b.fb_list, b.fb_count, b.partial, b.winner, sm_count(),
-                                 st));
+        FIC_STEP(launch_exact_scans(gd, b.ri, b.di, b.bblk, b.qblk, b.fb_list, b.fb_count, b.partial, b.cb.counts,
+                                    b.cb.dmap, search == FIC_SEARCH_TC ? search_tc_tile() : 64, target, n_split,
+                                    lists_per_split(search), n_lists, b.span, b.winner, sm_count(), st));
         FIC_MARK(4);
         FIC_STEP(launch_finalize(gd, b.ri, b.di, b.bblk, b.qblk, b.winner, b.err, dmaps, st));
         FIC_MARK(5);

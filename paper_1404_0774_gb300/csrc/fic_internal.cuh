@@ -181,23 +181,34 @@ __device__ __forceinline__ void list_insert(ListState &L, float key, uint32_t id
     }
 }
 
-// Code decision of one candidate: returns c (integer-valued float) and rho.
-__device__ __forceinline__ float epi_code(float X, float alpha, const EpiConst &ec, float &rho)
+// The centring correction of a cross term accumulated without it:
+// Xt = X' + corr, corr = -e_r f_d / m, where f_d / m = Sq/m - round(Sq/m) is
+// recovered exactly from Sq (m a power of two, Sq < 2^24).  With er = 0 (a
+// cross term that already includes it) corr is 0.  Exact in FP32.
+__device__ __forceinline__ float epi_corr(float er, float Sq, const EpiConst &ec)
 {
-    const float u = __saturatef(fmaf(X, alpha, 0.5f));
+    const float a = Sq * ec.invm;
+    return -er * (a - floorf(a + 0.5f));
+}
+
+// Code decision of one candidate from X' (Xt = X' + corr): returns c
+// (integer-valued float) and rho.  bq = 1/2 + corr * alpha.
+__device__ __forceinline__ float epi_code(float X, float alpha, float bq, const EpiConst &ec, float &rho)
+{
+    const float u = __saturatef(fmaf(X, alpha, bq));
     const float r = fmaf(u, ec.two_ls, -ec.ls);  // Ls * clamp(s, -1, 1)
     const float c = __fsub_rn(__fadd_rn(r, kMagic), kMagic);
     rho = __fsub_rn(r, c);
     return c;
 }
 
-// Screening key for a fixed code c.
-__device__ __forceinline__ float epi_key(float X, float c, float zb, float4 dc, const EpiConst &ec)
+// Screening key for a fixed code c, from X' and mcorr = -corr.
+__device__ __forceinline__ float epi_key(float X, float mcorr, float c, float zb, float4 dc, const EpiConst &ec)
 {
     const float z = fmaf(c, -dc.y, zb);
     const float e = __fsub_rn(fmaf(z, ec.invG, kMagic), kMagic);
     const float wv = fmaf(e, -ec.G, z);
-    const float y = fmaf(c, dc.z, -X);
+    const float y = fmaf(c, dc.z, __fsub_rn(mcorr, X));
     const float cy = __fmul_rn(c, y);
     return fmaf(__fmul_rn(wv, ec.lambda), wv, cy);
 }
@@ -248,7 +259,10 @@ __device__ __forceinline__ f32x2_t mul2(f32x2_t a, f32x2_t b)
 }
 
 // Main pass over 32 consecutive candidates (4 domains x 8 symmetries) with
-// cross terms X[].  Branch-free, two candidates (same domain, so same column
+// cross terms X[] = X' (the cross term less the centring correction of
+// epi_corr, er = e_r; er = 0 when X[] already is Xt; the correction is
+// folded into the code's offset and the key's -X' term, so it costs nothing
+// per candidate).  Branch-free, two candidates (same domain, so same column
 // constants) per packed instruction; the keys are bit-identical to
 // epi_code/epi_key.  Returns the mask of candidates whose key is below `thr`
 // (bit j for X[j]): the ones a rare pass must visit.  A code decided next to its rounding
@@ -268,7 +282,7 @@ __device__ __forceinline__ f32x2_t mul2(f32x2_t a, f32x2_t b)
 // most 8*Ls^2*kappa*2^-24, and lambda*w^2 >= 0, so both keys are at least
 // c*y - kappa*near_slack with near_slack = (32*Ls^2 + 16*Ls)*2^-24.
 __device__ __forceinline__ uint32_t epi_keys32(const float (&X)[32], const float4 (&dc)[4], float zb, float rho_lim,
-                                               const EpiConst &ec, float thr, float zpen)
+                                               float er, const EpiConst &ec, float thr, float zpen)
 {
     uint32_t mask = 0;
     const f32x2_t two_ls = pk2(ec.two_ls, ec.two_ls), mls = pk2(-ec.ls, -ec.ls);
@@ -280,11 +294,14 @@ __device__ __forceinline__ uint32_t epi_keys32(const float (&X)[32], const float
         const f32x2_t msqz = pk2(-c4.y, -c4.y), kap = pk2(c4.z, c4.z);
         const float sl = -c4.z * ec.near_slack;
         const f32x2_t msl = pk2(sl, sl);
+        const float corr = epi_corr(er, c4.w, ec);
+        const float bq = fmaf(corr, c4.x, 0.5f);
+        const f32x2_t mcorr = pk2(-corr, -corr);
 #pragma unroll
         for (int h = 0; h < 4; ++h) {
             const int j = q * 8 + 2 * h;
-            const float u0 = __saturatef(fmaf(X[j], c4.x, 0.5f));
-            const float u1 = __saturatef(fmaf(X[j + 1], c4.x, 0.5f));
+            const float u0 = __saturatef(fmaf(X[j], c4.x, bq));
+            const float u1 = __saturatef(fmaf(X[j + 1], c4.x, bq));
             const f32x2_t x = pk2(X[j], X[j + 1]);
             const f32x2_t r = fma2(pk2(u0, u1), two_ls, mls);  // Ls * clamp(s, -1, 1)
             const f32x2_t c = sub2(add2(r, mag), mag);          // rounded code
@@ -297,7 +314,7 @@ __device__ __forceinline__ uint32_t epi_keys32(const float (&X)[32], const float
             const f32x2_t z = fma2(c, msqz, zb2);
             const f32x2_t e = sub2(fma2(z, invg, mag), mag);
             const f32x2_t wv = fma2(e, mg, z);
-            const f32x2_t y = fma2(c, kap, sub2(pk2(0.0f, 0.0f), x));
+            const f32x2_t y = fma2(c, kap, sub2(mcorr, x));
             const f32x2_t cy = mul2(c, y);
             f32x2_t k = fma2(mul2(wv, lam), wv, cy);
             k = fma2(pk2(zero0, zero1), zp, k);
@@ -319,8 +336,8 @@ __device__ __forceinline__ float4 pick4(const float4 (&dc)[4], int q)
     return q == 0 ? dc[0] : (q == 1 ? dc[1] : (q == 2 ? dc[2] : dc[3]));
 }
 
-// Rare pass for one thread: cross terms staged in shared memory at
-// xrow[j*stride]; only the candidates of `mask` (the main pass's keys below
+// Rare pass for one thread: cross terms X' staged in shared memory at
+// xrow[j*stride] (er as for epi_keys32); only the candidates of `mask` (the main pass's keys below
 // its threshold, a superset of what can still enter the list) are visited,
 // their keys recomputed (bit-identical to the main pass).  Handles codes next
 // to a rounding boundary (the key becomes the smaller of the two neighbouring
@@ -330,8 +347,8 @@ __device__ __forceinline__ float4 pick4(const float4 (&dc)[4], int q)
 // may skip flat domains, so consecutive columns need not be consecutive
 // domains).
 static __device__ __forceinline__ void epi_rare(const float *xrow, int stride, const int (&od)[4],
-                                                const float4 (&dc)[4], const RangeEpi &re, const EpiConst &ec,
-                                                ListState &L, uint32_t mask)
+                                                const float4 (&dc)[4], float er, const RangeEpi &re,
+                                                const EpiConst &ec, ListState &L, uint32_t mask)
 {
 #pragma unroll 1
     while (mask) {
@@ -339,13 +356,14 @@ static __device__ __forceinline__ void epi_rare(const float *xrow, int stride, c
         mask &= mask - 1;
         const float x = xrow[j * stride];
         const float4 c4 = pick4(dc, j >> 3);
+        const float corr = epi_corr(er, c4.w, ec);
         float rho;
-        const float c = epi_code(x, c4.x, ec, rho);
+        const float c = epi_code(x, c4.x, fmaf(corr, c4.x, 0.5f), ec, rho);
         const bool near = fabsf(rho) > re.rho_lim;
-        float k = epi_key(x, c, re.zb, c4, ec);
+        float k = epi_key(x, -corr, c, re.zb, c4, ec);
         if (near) {
             const float c2 = fminf(fmaxf(c + (rho > 0.0f ? 1.0f : -1.0f), -ec.ls), ec.ls);
-            k = fminf(k, epi_key(x, c2, re.zb, c4, ec));
+            k = fminf(k, epi_key(x, -corr, c2, re.zb, c4, ec));
         }
         if (!(k < fminf(L.key[kListK - 1], L.tw))) continue;
         if (c == 0.0f && !near) {
@@ -450,12 +468,16 @@ cudaError_t launch_rescore(const Geometry &g, const EpiConst &ec, const RangeInf
                            const DomainInfo *di, const uint16_t *bblk, const uint16_t *qblk,
                            const ListEntry *lists, int max_lists, const int *counts, const int *act,
                            const int *rkeep, int lists_per_split, int col_tile, int target, int max_split, int n_sm,
-                           int exact_scan, uint32_t *winner, int *fb_list, int *fb_count, void *partial,
+                           int exact_scan, uint32_t *winner, int *fb_list, int *fb_count, void *partial, void *span,
                            cudaStream_t st);
+size_t span_bytes(const Geometry &g, int max_lists);
+cudaError_t launch_exact_scans(const Geometry &g, const RangeInfo *ri, const DomainInfo *di, const uint16_t *bblk,
+                               const uint16_t *qblk, const int *fb_list, int *fb_count, void *partial,
+                               const int *counts, const int *dmap, int col_tile, int target, int max_split,
+                               int lists_per_split, int max_lists, void *span, uint32_t *winner, int n_sm,
+                               cudaStream_t st);
 size_t fallback_partial_bytes(const Geometry &g);
-cudaError_t launch_fallback(const Geometry &g, const RangeInfo *ri, const DomainInfo *di,
-                            const uint16_t *bblk, const uint16_t *qblk, const int *fb_list,
-                            const int *fb_count, void *partial, uint32_t *winner, int n_sm, cudaStream_t st);
+
 cudaError_t launch_finalize(const Geometry &g, const RangeInfo *ri, const DomainInfo *di,
                             const uint16_t *bblk, const uint16_t *qblk, const uint32_t *winner,
                             const int *err, fic_map *maps, cudaStream_t st);
@@ -476,7 +498,8 @@ __device__ __forceinline__ RangeEpi range_epi(const RangeInfo &ri, const EpiCons
     re.shadow = ri.shadow;
     return re;
 }
-cudaError_t launch_prep(const Geometry &g, const void *img, const EpiConst &ec, int dense, const int *active,
+cudaError_t launch_prep(const Geometry &g, const void *img, const EpiConst &ec, int dense, int tc_split,
+                        const int *active,
                         RangeInfo *ri, DomainInfo *di, float4 *dconst, uint16_t *bblk, uint16_t *qblk, float *rs32,
                         float *cb32, __half *ra16, __half *cb16, int *tbest, const CompactBufs &cb, cudaStream_t st);
 cudaError_t launch_seed(const Geometry &g, const EpiConst &ec, const RangeInfo *ri, const DomainInfo *di,

@@ -19,8 +19,8 @@ __device__ __forceinline__ long long warp_sum_ll(long long v)
 // One warp per range (lanes over pixels): statistics, centre, allowances,
 // and the keep flag (every range but shadow ranges, or all when dense).
 __device__ __forceinline__ void range_stats(const Geometry &g, const EpiConst &ec, const void *img, int dense,
-                                            const int *active, int r, int lane, RangeInfo *ri, uint16_t *bblk,
-                                            int *tbest, int *rkeep)
+                                            int tc_split, const int *active, int r, int lane, RangeInfo *ri,
+                                            uint16_t *bblk, int *tbest, int *rkeep)
 {
     const int ry = (r / g.nx) * g.n, rx = (r % g.nx) * g.n;
     constexpr int PPL = kMaxM / 32;  // pixels per lane, upper bound
@@ -77,8 +77,14 @@ __device__ __forceinline__ void range_stats(const Geometry &g, const EpiConst &e
     info.zb = (float)(g.mod_g ? z % g.Gi : z);
     info.bp2 = bp2f;
     // FP32 error of Ls*s: ~1e-6 when the cross term is exact, plus the
-    // accumulation error of high-variance pairs (grows with sum (b-c_r)^2)
-    const float eta = 1e-5f + 12.0f * g.Ls * 64.0f * bp2f * 3.552713678800501e-15f;  // 2^-48
+    // accumulation error of high-variance pairs (grows with sum (b-c_r)^2).
+    // With the tensor-core search's separate hi/lo accumulators the cross
+    // term X' is exact but for the rounding of hi + lo and of the folded
+    // correction: relative errors of 2^-23 of (|X'| + |corr|), |corr| <=
+    // |e_r|/2, times alpha <= 2m/(m-1) < 2.1 and 2 Ls.
+    const float er_abs = fabsf((float)e_r);
+    const float eta = tc_split ? 1e-5f + 1.2e-7f * g.Ls * (2.0f + 2.1f * er_abs)
+                               : 1e-5f + 12.0f * g.Ls * 64.0f * bp2f * 3.552713678800501e-15f;  // 2^-48
     info.rho_lim = 0.5f - fminf(eta, 0.25f);
     // Screening allowance.  A candidate within reach of the winner has
     // |c| * sqrt(sum (q-q_mean)^2) <= 4*Ls*(sqrt(Sbb_c) + sqrt(R)), R <= Eb; its
@@ -90,11 +96,12 @@ __device__ __forceinline__ void range_stats(const Geometry &g, const EpiConst &e
     const float sb = sqrtf(bp2f);
     const float sqm = sqrtf((float)g.m);
     const float S = (4.0f * g.Ls * (sqrtf(sbbc) + sqrtf(Eb)) + sqm) * sb + (g.split_hilo ? 128.0f * sqm * sb : 0.0f);
-    const bool exact = S < 8.0e6f;  // < 2^23 with margin
+    const bool exact = tc_split || S < 8.0e6f;  // < 2^23 with margin, or exact partial sums
     const float gam = 3.0517578125e-05f;  // 2^-15
     info.beta_q = exact ? 0.0f : 4.0f * g.Ls * gam * sb;
     info.beta_a = 3.814697265625e-06f * 2.0f * g.Ls * (sbbc + ec.delta_o) + 1e-3f +
-                  (exact ? 0.0f : gam * g.Ls * 128.0f * sqm * sb);
+                  (exact ? (tc_split ? 9.5367431640625e-07f * g.Ls * er_abs : 0.0f)  // 2^-20
+                         : gam * g.Ls * 128.0f * sqm * sb);
     info.shadow = bmin == bmax ? 1 : 0;
     info.pad = 0;
     ri[r] = info;
@@ -149,7 +156,7 @@ __device__ __forceinline__ void domain_stats(const Geometry &g, const void *img,
 
 // Statistics of every range (blocks [0, rb), a warp each) and every domain
 // (the blocks after), one launch.
-__global__ void __launch_bounds__(256) k_stats(Geometry g, EpiConst ec, const void *img, int dense,
+__global__ void __launch_bounds__(256) k_stats(Geometry g, EpiConst ec, const void *img, int dense, int tc_split,
                                                const int *active, int rb, RangeInfo *ri, uint16_t *bblk, int *tbest,
                                                DomainInfo *di, float4 *dconst, uint16_t *qblk, int *rkeep,
                                                int *dkeep)
@@ -157,7 +164,7 @@ __global__ void __launch_bounds__(256) k_stats(Geometry g, EpiConst ec, const vo
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     if ((int)blockIdx.x < rb) {
         const int r = blockIdx.x * 8 + w;
-        if (r < g.R) range_stats(g, ec, img, dense, active, r, lane, ri, bblk, tbest, rkeep);
+        if (r < g.R) range_stats(g, ec, img, dense, tc_split, active, r, lane, ri, bblk, tbest, rkeep);
     } else {
         const int d = (blockIdx.x - rb) * 8 + w;
         if (d < g.D) domain_stats(g, img, dense, d, lane, di, dconst, qblk, dkeep);
@@ -373,13 +380,14 @@ __global__ void __launch_bounds__(256, 4) k_rows(Geometry g, int rb, const Range
                          dmap);
 }
 
-cudaError_t launch_prep(const Geometry &g, const void *img, const EpiConst &ec, int dense, const int *active,
+cudaError_t launch_prep(const Geometry &g, const void *img, const EpiConst &ec, int dense, int tc_split,
+                        const int *active,
                         RangeInfo *ri, DomainInfo *di, float4 *dconst, uint16_t *bblk, uint16_t *qblk, float *rs32,
                         float *cb32, __half *ra16, __half *cb16, int *tbest, const CompactBufs &cb, cudaStream_t st)
 {
     const int rb = (g.R + 7) / 8, db = (g.D + 7) / 8;
-    k_stats<<<rb + db, 256, 0, st>>>(g, ec, img, dense, active, rb, ri, bblk, tbest, di, dconst, qblk, cb.rkeep,
-                                     cb.dkeep);
+    k_stats<<<rb + db, 256, 0, st>>>(g, ec, img, dense, tc_split, active, rb, ri, bblk, tbest, di, dconst, qblk,
+                                     cb.rkeep, cb.dkeep);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_compact<<<2, 1024, 0, st>>>(g.R, cb.rkeep, cb.act, cb.counts + 0, g.D, cb.dkeep, cb.dact, cb.counts + 2);
@@ -467,11 +475,11 @@ __global__ void __launch_bounds__(256) k_seed(Geometry g, EpiConst ec, const Ran
     const float4 c4 = dconst[d];
     const RangeEpi re = range_epi(rin, ec);
     float rho;
-    const float c = epi_code(Xt, c4.x, ec, rho);
+    const float c = epi_code(Xt, c4.x, 0.5f, ec, rho);
     if (fabsf(rho) > re.rho_lim) return;
     const float ostar = (re.Sb - c * c4.w * ec.inv4ls) * ec.invm;
     if (!(ostar < ec.pmax)) return;
-    atomicMin(tbest + r, f2ord(epi_key(Xt, c, re.zb, c4, ec)));
+    atomicMin(tbest + r, f2ord(epi_key(Xt, -0.0f, c, re.zb, c4, ec)));
 }
 
 cudaError_t launch_seed(const Geometry &g, const EpiConst &ec, const RangeInfo *ri, const DomainInfo *di,

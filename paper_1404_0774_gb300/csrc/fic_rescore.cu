@@ -260,6 +260,44 @@ __device__ long long lane_cross(const Geometry &g, const uint16_t *qblk, uint32_
 // FP64 and rounded outward (up for the finalist bound, so that no finalist
 // is lost; the certification side is rounded down on the key and up on the
 // threshold, so that it never certifies what the exact test would not).
+struct Partial {
+    unsigned long long lo, hi;
+    uint32_t idx, pad;
+};
+
+// Re-scan of failed lists: work items (range << 7 | list), per (range, list)
+// partial minima, per range the finalists' best and the items still pending.
+struct SpanBufs {
+    int *items;
+    int *count;
+    Partial *part;   // [R][max_lists]
+    Partial *cert;   // [R]
+    int *pending;    // [R]
+};
+
+SpanBufs span_bufs(const Geometry &g, int max_lists, void *ws, int *count)
+{
+    SpanBufs b;
+    char *p = static_cast<char *>(ws);
+    b.part = reinterpret_cast<Partial *>(p);
+    p += sizeof(Partial) * (size_t)g.R * max_lists;
+    b.cert = reinterpret_cast<Partial *>(p);
+    p += sizeof(Partial) * (size_t)g.R;
+    b.items = reinterpret_cast<int *>(p);
+    p += sizeof(int) * (size_t)g.R * max_lists;
+    b.pending = reinterpret_cast<int *>(p);
+    b.count = count;
+    return b;
+}
+
+size_t span_bytes(const Geometry &g, int max_lists)
+{
+    return (sizeof(Partial) + sizeof(int)) * (size_t)g.R * max_lists + (sizeof(Partial) + sizeof(int)) * (size_t)g.R;
+}
+
+__device__ __forceinline__ unsigned long long hi64(unsigned long long) { return 0ull; }
+__device__ __forceinline__ unsigned long long hi64(unsigned __int128 v) { return (unsigned long long)(v >> 64); }
+
 constexpr int kRescoreWarps = 4;
 constexpr int kRescoreEnt = 16;  // list entries per lane: up to 512 per range
 template <bool Wide>
@@ -268,7 +306,7 @@ __device__ __forceinline__ void rescore_range(const Geometry &g, const EpiConst 
                                               const ListEntry *lists, int max_lists, const int *counts,
                                               int lists_per_split, int col_tile, int target, int max_split,
                                               int exact_scan, uint32_t *winner, int *fb_list, int *fb_count, int r,
-                                              int *bk)
+                                              int *bk, const SpanBufs &sb)
 {
     typedef typename Exact<Wide>::U U;
     const int lane = threadIdx.x & 31;
@@ -410,19 +448,36 @@ __device__ __forceinline__ void rescore_range(const Geometry &g, const EpiConst 
     // last of its list when f % 4 == 3 (lanes 3, 7, ...).
     const float Estar = __fmul_ru(to_float_ru(best_e), ec.invD2_up);
     const float kcert = __fmul_ru(__fsub_ru(Estar, rin.sbbc), ec.two_ls);
-    bool cert = true;
+    // a list that fails the test is re-scanned exactly over its own candidates
+    // (the columns the search gave it); the winner is then the best of those
+    // scans and of the finalists above
+    uint32_t failing = 0;  // bit q: this lane's list (lane/4 + 8q) failed
     if ((lane & (kListK - 1)) == kListK - 1) {
 #pragma unroll
         for (int q = 0; q < kRescoreEnt; ++q) {
             const ListEntry last = ent[q];
             if (last.idx == 0xffffffffu) continue;  // list not full (or past the end)
-            if (!(__fsub_rd(last.key, beta_key(re, last.key, ec)) > kcert)) cert = false;
+            if (!(__fsub_rd(last.key, beta_key(re, last.key, ec)) > kcert)) failing |= 1u << q;
         }
     }
-    cert = __all_sync(0xffffffffu, cert);
+    int nfail = __popc(failing);
+    for (int off = 16; off > 0; off >>= 1) nfail += __shfl_xor_sync(0xffffffffu, nfail, off);
+    if (nfail == 0) {
+        if (lane == 0) winner[r] = best_i;
+        return;
+    }
+    Partial *sp = sb.part + (size_t)r * max_lists;
+    for (int l = lane; l < n_lists; l += 32) sp[l] = Partial{~0ull, ~0ull, 0xffffffffu, 0};
     if (lane == 0) {
-        winner[r] = best_i;
-        if (!cert) fb_list[atomicAdd(fb_count, 1)] = r;
+        sb.cert[r] = Partial{(unsigned long long)best_e, hi64(best_e), best_i, 0};
+        sb.pending[r] = nfail;
+        winner[r] = best_i;  // provisional: the last list scan replaces it
+    }
+    while (failing) {
+        const int q = __ffs(failing) - 1;
+        failing &= failing - 1;
+        const int l = (lane >> 2) + 8 * q;
+        sb.items[atomicAdd(sb.count, 1)] = (r << 7) | l;
     }
 }
 
@@ -435,7 +490,7 @@ __global__ void __launch_bounds__(32 * kRescoreWarps, 4)
     k_rescore(Geometry g, EpiConst ec, const RangeInfo *ri, const DomainInfo *di, const uint16_t *bblk,
               const uint16_t *qblk, const ListEntry *lists, int max_lists, const int *counts, const int *act,
               const int *rkeep, int lists_per_split, int col_tile, int target, int max_split, int exact_scan,
-              uint32_t *winner, int *fb_list, int *fb_count, int *fb_done)
+              uint32_t *winner, int *fb_list, int *fb_count, int *fb_done, SpanBufs sb)
 {
     extern __shared__ int bk_all[];  // [warps][8][m+1]
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < g.R; r += gridDim.x * blockDim.x) {
@@ -446,16 +501,10 @@ __global__ void __launch_bounds__(32 * kRescoreWarps, 4)
     const int nkept = counts[0];
     for (int j = blockIdx.x * kRescoreWarps + (threadIdx.x >> 5); j < nkept; j += gridDim.x * kRescoreWarps)
         rescore_range<Wide>(g, ec, ri, di, bblk, qblk, lists, max_lists, counts, lists_per_split, col_tile, target,
-                            max_split, exact_scan, winner, fb_list, fb_count, act[j], bk);
+                            max_split, exact_scan, winner, fb_list, fb_count, act[j], bk, sb);
 }
 
-struct Partial {
-    unsigned long long lo, hi;
-    uint32_t idx, pad;
-};
 
-__device__ __forceinline__ unsigned long long hi64(unsigned long long) { return 0ull; }
-__device__ __forceinline__ unsigned long long hi64(unsigned __int128 v) { return (unsigned long long)(v >> 64); }
 
 // Exhaustive exact scan of the ranges that failed certification, as work
 // items (slot, chunk) over a grid of persistent blocks: an item scans one
@@ -464,10 +513,9 @@ __device__ __forceinline__ unsigned long long hi64(unsigned __int128 v) { return
 // finish (counted in done[slot], zeroed by the re-score) reduces the chunks
 // and writes the winner, flagged as resolved by the fallback.
 template <bool Wide>
-__global__ void __launch_bounds__(256) k_fallback(Geometry g, const RangeInfo *ri, const DomainInfo *di,
-                                                  const uint16_t *bblk, const uint16_t *qblk, const int *fb_list,
-                                                  const int *fb_count, int nch, Partial *part, int *done,
-                                                  uint32_t *winner)
+__device__ __forceinline__ void full_scans(const Geometry &g, const RangeInfo *ri, const DomainInfo *di,
+                                           const uint16_t *bblk, const uint16_t *qblk, const int *fb_list,
+                                           const int *fb_count, int nch, Partial *part, int *done, uint32_t *winner)
 {
     __shared__ int b_s[kMaxM];
     __shared__ Partial w_s[8];
@@ -542,6 +590,113 @@ __global__ void __launch_bounds__(256) k_fallback(Geometry g, const RangeInfo *r
             }
         }
     }
+}
+
+// Exact scan of the candidates of one failed list (work item (range, list)):
+// list l = split * parts + part of a range holds the columns tile * col_tile
+// + part * seg + [0, seg) of the tiles of its split, exactly as the search
+// assigned them (compacted columns; dmap gives the domain).  Each item writes
+// its best (residual, index); the last item of a range combines them with
+// the finalists' best and writes the winner, flagged as resolved by an exact
+// scan.
+template <bool Wide>
+__device__ __forceinline__ void list_scans(const Geometry &g, const RangeInfo *ri, const DomainInfo *di,
+                                           const uint16_t *bblk, const uint16_t *qblk, const int *counts,
+                                           const int *dmap, int col_tile, int target, int max_split,
+                                           int lists_per_split, int max_lists, const SpanBufs &sb, uint32_t *winner)
+{
+    typedef typename Exact<Wide>::U U;
+    __shared__ int b_s[kMaxM];
+    __shared__ Partial w_s[8];
+    const int count = *sb.count;
+    const int ncol = 8 * counts[2];
+    const int tiles = (ncol + col_tile - 1) / col_tile;
+    const int n_split = active_splits((counts[0] + 127) / 128, tiles, target, max_split);
+    const int n_lists = n_split * lists_per_split;
+    const int seg = col_tile / lists_per_split;
+    for (int item = blockIdx.x; item < count; item += gridDim.x) {
+        const int code = sb.items[item];
+        const int r = code >> 7, l = code & 127;
+        const int sp = l / lists_per_split, part = l - sp * lists_per_split;
+        const int t0 = (int)((long long)tiles * sp / n_split), t1 = (int)((long long)tiles * (sp + 1) / n_split);
+        __syncthreads();  // b_s and w_s of the previous item are no longer read
+        for (int i = threadIdx.x; i < g.m; i += blockDim.x) b_s[i] = bblk[(size_t)r * g.m + i];
+        __syncthreads();
+        const RangeInfo rin = ri[r];
+        Stats st;
+        st.Sb = rin.Sb;
+        st.Sbb = rin.Sbb;
+        U best_e = ~(U)0;
+        uint32_t best_i = 0xffffffffu;
+        for (int i = threadIdx.x; i < (t1 - t0) * seg; i += blockDim.x) {
+            const int ti = i / seg;
+            const int c = (t0 + ti) * col_tile + part * seg + (i - ti * seg);
+            if (c >= ncol) continue;
+            const int d = dmap[c >> 3], k = c & 7;
+            const SymFlags sf = sym_flags(k, g.n);
+            const uint16_t *qd = qblk + (size_t)d * g.m;
+            unsigned long long X = 0;
+            for (int y = 0; y < g.n; ++y) {
+                uint32_t acc = 0;  // one row: n products of at most 4P * P, n <= 16
+                for (int x = 0; x < g.n; ++x)
+                    acc += (uint32_t)qd[sym_src_index(sf, g.ln, y, x)] * (uint32_t)b_s[(y << g.ln) + x];
+                X += acc;
+            }
+            const uint32_t idx = (uint32_t)(d * 8 + k);
+            const U er = exact_rational<Wide>(g, st, di[d], (long long)X);
+            if (better(er, idx, best_e, best_i)) {
+                best_e = er;
+                best_i = idx;
+            }
+        }
+        warp_argmin(best_e, best_i);
+        if ((threadIdx.x & 31) == 0)
+            w_s[threadIdx.x >> 5] = Partial{(unsigned long long)best_e, hi64(best_e), best_i, 0};
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            Partial b = w_s[0];
+            for (int j = 1; j < (int)(blockDim.x >> 5); ++j) {
+                const unsigned __int128 ej = ((unsigned __int128)w_s[j].hi << 64) | w_s[j].lo;
+                const unsigned __int128 eb = ((unsigned __int128)b.hi << 64) | b.lo;
+                if (better(ej, w_s[j].idx, eb, b.idx)) b = w_s[j];
+            }
+            Partial *sp_r = sb.part + (size_t)r * max_lists;
+            sp_r[l] = b;
+            __threadfence();  // the partial is visible before the count says so
+            if (atomicSub(sb.pending + r, 1) == 1) {
+                __threadfence();
+                Partial bb = sb.cert[r];
+                for (int j = 0; j < n_lists; ++j) {
+                    const Partial *pj = sp_r + j;
+                    const unsigned long long jl = __ldcg(&pj->lo), jh = __ldcg(&pj->hi);
+                    const uint32_t ji = __ldcg(&pj->idx);
+                    const unsigned __int128 ej = ((unsigned __int128)jh << 64) | jl;
+                    const unsigned __int128 eb = ((unsigned __int128)bb.hi << 64) | bb.lo;
+                    if (ji != 0xffffffffu && better(ej, ji, eb, bb.idx)) {
+                        bb.lo = jl;
+                        bb.hi = jh;
+                        bb.idx = ji;
+                    }
+                }
+                winner[r] = bb.idx | 0x80000000u;  // high bit: resolved by an exact scan
+            }
+        }
+    }
+}
+
+// One launch for both exact scans (persistent blocks; usually there is no
+// work and every block returns at once).
+template <bool Wide>
+__global__ void __launch_bounds__(256) k_exact_scans(Geometry g, const RangeInfo *ri, const DomainInfo *di,
+                                                     const uint16_t *bblk, const uint16_t *qblk, const int *fb_list,
+                                                     const int *fb_count, int nch, Partial *part, int *done,
+                                                     const int *counts, const int *dmap, int col_tile, int target,
+                                                     int max_split, int lists_per_split, int max_lists, SpanBufs sb,
+                                                     uint32_t *winner)
+{
+    full_scans<Wide>(g, ri, di, bblk, qblk, fb_list, fb_count, nch, part, done, winner);
+    list_scans<Wide>(g, ri, di, bblk, qblk, counts, dmap, col_tile, target, max_split, lists_per_split, max_lists, sb,
+                     winner);
 }
 
 // FP64 codes of the winner (eq 9-12 in FP64, the operation order of the
@@ -637,9 +792,10 @@ cudaError_t launch_rescore(const Geometry &g, const EpiConst &ec, const RangeInf
                            const DomainInfo *di, const uint16_t *bblk, const uint16_t *qblk,
                            const ListEntry *lists, int max_lists, const int *counts, const int *act,
                            const int *rkeep, int lists_per_split, int col_tile, int target, int max_split, int n_sm,
-                           int exact_scan, uint32_t *winner, int *fb_list, int *fb_count, void *partial,
+                           int exact_scan, uint32_t *winner, int *fb_list, int *fb_count, void *partial, void *span,
                            cudaStream_t st)
 {
+    const SpanBufs sb = span_bufs(g, max_lists, span, fb_count + 2);
     const size_t smem = sizeof(int) * kRescoreWarps * 8 * (g.m + 1);
     // at most as many blocks as are resident at once (4 per SM at this size)
     const int blocks = std::max(1, std::min((g.R + kRescoreWarps - 1) / kRescoreWarps, 4 * n_sm));
@@ -647,11 +803,11 @@ cudaError_t launch_rescore(const Geometry &g, const EpiConst &ec, const RangeInf
     if (g.wide)
         k_rescore<true><<<blocks, 32 * kRescoreWarps, smem, st>>>(
             g, ec, ri, di, bblk, qblk, lists, max_lists, counts, act, rkeep, lists_per_split, col_tile, target,
-            max_split, exact_scan, winner, fb_list, fb_count, fallback_done(g, partial));
+            max_split, exact_scan, winner, fb_list, fb_count, fallback_done(g, partial), sb);
     else
         k_rescore<false><<<blocks, 32 * kRescoreWarps, smem, st>>>(
             g, ec, ri, di, bblk, qblk, lists, max_lists, counts, act, rkeep, lists_per_split, col_tile, target,
-            max_split, exact_scan, winner, fb_list, fb_count, fallback_done(g, partial));
+            max_split, exact_scan, winner, fb_list, fb_count, fallback_done(g, partial), sb);
     return cudaGetLastError();
 }
 
@@ -668,18 +824,23 @@ int *fallback_done(const Geometry &g, void *partial)
     return reinterpret_cast<int *>(reinterpret_cast<Partial *>(partial) + (size_t)g.R * fallback_chunks(g));
 }
 
-cudaError_t launch_fallback(const Geometry &g, const RangeInfo *ri, const DomainInfo *di,
-                            const uint16_t *bblk, const uint16_t *qblk, const int *fb_list,
-                            const int *fb_count, void *partial, uint32_t *winner, int n_sm, cudaStream_t st)
+cudaError_t launch_exact_scans(const Geometry &g, const RangeInfo *ri, const DomainInfo *di, const uint16_t *bblk,
+                               const uint16_t *qblk, const int *fb_list, int *fb_count, void *partial,
+                               const int *counts, const int *dmap, int col_tile, int target, int max_split,
+                               int lists_per_split, int max_lists, void *span, uint32_t *winner, int n_sm,
+                               cudaStream_t st)
 {
     const int nch = fallback_chunks(g);
     Partial *part = reinterpret_cast<Partial *>(partial);
+    const SpanBufs sb = span_bufs(g, max_lists, span, fb_count + 2);
     if (g.wide)
-        k_fallback<true><<<2 * n_sm, 256, 0, st>>>(g, ri, di, bblk, qblk, fb_list, fb_count, nch, part,
-                                                   fallback_done(g, partial), winner);
+        k_exact_scans<true><<<2 * n_sm, 256, 0, st>>>(g, ri, di, bblk, qblk, fb_list, fb_count, nch, part,
+                                                       fallback_done(g, partial), counts, dmap, col_tile, target,
+                                                       max_split, lists_per_split, max_lists, sb, winner);
     else
-        k_fallback<false><<<2 * n_sm, 256, 0, st>>>(g, ri, di, bblk, qblk, fb_list, fb_count, nch, part,
-                                                    fallback_done(g, partial), winner);
+        k_exact_scans<false><<<2 * n_sm, 256, 0, st>>>(g, ri, di, bblk, qblk, fb_list, fb_count, nch, part,
+                                                        fallback_done(g, partial), counts, dmap, col_tile, target,
+                                                        max_split, lists_per_split, max_lists, sb, winner);
     return cudaGetLastError();
 }
 

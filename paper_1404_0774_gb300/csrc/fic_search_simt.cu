@@ -144,10 +144,10 @@ __global__ void __launch_bounds__(256) k_search_simt(Geometry g, EpiConst ec, co
                     dc[q] = ok ? dconst[jd] : make_float4(0.f, 0.f, 0.f, 0.f);
                     od[q] = ok ? dmap[jd] : 0;
                 }
-                const uint32_t mask = epi_keys32(X, dc, re.zb, re.rho_lim, ec, fminf(L.key[kListK - 1], L.tw),
+                const uint32_t mask = epi_keys32(X, dc, re.zb, re.rho_lim, 0.0f, ec, fminf(L.key[kListK - 1], L.tw),
                                                  L.has_zero ? kZeroPenalty : 0.0f);
                 if (mask) {
-                    epi_rare(xrow, 1, od, dc, re, ec, L, mask);
+                    epi_rare(xrow, 1, od, dc, 0.0f, re, ec, L, mask);
                     if (L.T < L.Tpub) {
                         atomicMin(tbest + my_r, f2ord(L.T));
                         L.Tpub = L.T;

@@ -36,7 +36,6 @@ constexpr int NACC = 2;
 constexpr int EPI_WARPS = 8;                    // two per TMEM lane quadrant
 constexpr int THREADS = 64 + 32 * EPI_WARPS;   // TMA warp, MMA warp, epilogue
 constexpr int EPI_COLS = BN / 2;               // columns of a tile per epilogue warp
-constexpr uint32_t TMEM_COLS = BN * NACC;  // 256
 constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s per wait
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
@@ -197,20 +196,30 @@ __device__ __forceinline__ void tmem_wait2(uint32_t (&a)[32], uint32_t (&b)[32])
 }
 
 // Rare pass of one 32-column chunk (warp-collective: every lane calls it):
-// reload the cross terms (still in TMEM at taddr) into this thread's column
-// of the staging buffer, then each thread visits its own candidates of
-// `mask`.  Staging is per thread, so no cross-lane ordering is needed.
-__device__ __forceinline__ void rare_chunk(uint32_t taddr, uint32_t mask, const int (&od)[4], const float4 (&dc)[4],
-                                           float *xcol, int stride, const RangeEpi &re, const EpiConst &ec,
-                                           ListState &L, int *tbest_r)
+// reload the cross terms (still in TMEM at taddr, and the lo part at
+// taddr + lo_off when the parts accumulate separately) into this thread's
+// column of the staging buffer, then each thread visits its own candidates
+// of `mask`.  Staging is per thread, so no cross-lane ordering is needed.
+template <int PARTS>
+__device__ __forceinline__ void rare_chunk(uint32_t taddr, uint32_t lo_off, uint32_t mask, const int (&od)[4],
+                                           const float4 (&dc)[4], float er, float *xcol, int stride,
+                                           const RangeEpi &re, const EpiConst &ec, ListState &L, int *tbest_r)
 {
     uint32_t tx[32];
     tmem_ld32(taddr, tx);
-    tmem_wait(tx);
+    if (PARTS == 2) {
+        uint32_t tl[32];
+        tmem_ld32(taddr + lo_off, tl);
+        tmem_wait2(tx, tl);
 #pragma unroll
-    for (int j = 0; j < 32; ++j) xcol[j * stride] = __uint_as_float(tx[j]);
+        for (int j = 0; j < 32; ++j) xcol[j * stride] = __fadd_rn(__uint_as_float(tx[j]), __uint_as_float(tl[j]));
+    } else {
+        tmem_wait(tx);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) xcol[j * stride] = __uint_as_float(tx[j]);
+    }
     if (mask) {
-        epi_rare(xcol, stride, od, dc, re, ec, L, mask);
+        epi_rare(xcol, stride, od, dc, er, re, ec, L, mask);
         if (L.T < L.Tpub) {
             atomicMin(tbest_r, f2ord(L.T));
             L.Tpub = L.T;
@@ -240,6 +249,14 @@ __global__ void __launch_bounds__(THREADS, 1)
     constexpr uint32_t B_BYTES = NBLK * B_BLK + BN * 32;
     constexpr int KSTEPS = NBLK * 4 + 1;
     constexpr uint32_t IDESC = instr_desc(BM, BN);
+    // 12-bit: the hi and lo parts of q' accumulate separately (each sum is
+    // exact in FP32: multiples of 128 below 2^31, integers below 2^23) and the
+    // centring correction is folded into the epilogue, so the only rounding
+    // of the cross term is that of hi + lo.  8-bit: one accumulator, tail
+    // columns included.
+    constexpr uint32_t PARTS = NBLK == 2 ? 2 : 1;
+    constexpr uint32_t ACC_COLS = BN * PARTS;
+    constexpr uint32_t TMEM_COLS = ACC_COLS * NACC;  // 512 or 256
 
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -352,9 +369,10 @@ __global__ void __launch_bounds__(THREADS, 1)
                 if (!mbar_wait(&full_bar[s], (it / STAGES) & 1, &abort_s, err)) break;
                 tc_fence_after();
                 const uint32_t b_base = b_base0 + s * B_BYTES;
-                const uint32_t d_tmem = tmem_base + acc * BN;
+                const uint32_t d_tmem = tmem_base + acc * ACC_COLS;
 #pragma unroll
                 for (int k = 0; k < KSTEPS; ++k) {
+                    if (PARTS == 2 && k == NBLK * 4) break;  // the correction is applied in the epilogue
                     uint64_t ad, bd;
                     if (k < NBLK * 4) {
                         const uint32_t off_a = (k >> 2) * A_BLK + (k & 3) * 32;
@@ -365,7 +383,10 @@ __global__ void __launch_bounds__(THREADS, 1)
                         ad = smem_desc(a_base + NBLK * A_BLK, 256, 6);
                         bd = smem_desc(b_base + NBLK * B_BLK, 256, 6);
                     }
-                    umma_f16(d_tmem, ad, bd, IDESC, k > 0 ? 1u : 0u);
+                    if (PARTS == 2)  // block 0 (hi) -> columns [0, BN), block 1 (lo) -> [BN, 2 BN)
+                        umma_f16(d_tmem + (k >> 2) * BN, ad, bd, IDESC, (k & 3) ? 1u : 0u);
+                    else
+                        umma_f16(d_tmem, ad, bd, IDESC, k > 0 ? 1u : 0u);
                 }
                 umma_commit(&empty_bar[s]);      // smem stage free once these MMAs finish
                 umma_commit(&tfull_bar[acc]);    // accumulator ready for the epilogue
@@ -385,6 +406,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         int *wod = reinterpret_cast<int *>(dcs + EPI_WARPS * 8) + ew * 8;
         RangeEpi re{};
         if (live) re = range_epi(ri[r], ec);
+        const float er = (PARTS == 2 && live) ? (float)ri[r].e_r : 0.0f;  // centring correction factor
         const bool scr = live && (dense || !re.shadow);
         ListState L;
         list_init(L);
@@ -425,33 +447,51 @@ __global__ void __launch_bounds__(THREADS, 1)
             // warp-uniform decision: tcgen05.ld below is .sync.aligned
             if (!__all_sync(0xffffffffu, mbar_wait(&tfull_bar[acc], (it / NACC) & 1, &abort_s, err))) break;
             tc_fence_after();
-            const uint32_t taddr = lane_addr + acc * BN;
-            // both 32-column chunks of this warp's half tile at once (one load
-            // latency per tile)
-            float Xa[32], Xb[32];
-            {
-                uint32_t ua[32], ub[32];
-                tmem_ld32(taddr, ua);
-                tmem_ld32(taddr + 32, ub);
-                tmem_wait2(ua, ub);
-#pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    Xa[j] = __uint_as_float(ua[j]);
-                    Xb[j] = __uint_as_float(ub[j]);
-                }
-            }
+            const uint32_t taddr = lane_addr + acc * ACC_COLS;
             const int nva = min(32, ncol - n0), nvb = min(32, ncol - n0 - 32);
             int oda[4], odb[4];
+            float4 dca[4], dcb[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 oda[q] = wod[q];
                 odb[q] = wod[4 + q];
+                dca[q] = wdc[q];
+                dcb[q] = wdc[4 + q];
+            }
+            // chunk a; with separate parts, chunk b's loads overlap a's main pass
+            float Xa[32], Xb[32];
+            uint32_t hb[32], lb[32];
+            {
+                uint32_t ha[32], la[32];
+                tmem_ld32(taddr, ha);
+                if (PARTS == 2) {  // (chunk b is loaded after a's passes: registers)
+                    tmem_ld32(taddr + BN, la);
+                    tmem_wait2(ha, la);
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) Xa[j] = __fadd_rn(__uint_as_float(ha[j]), __uint_as_float(la[j]));
+                } else {
+                    tmem_ld32(taddr + 32, hb);
+                    tmem_wait2(ha, hb);
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) Xa[j] = __uint_as_float(ha[j]);
+                }
             }
             if (dump) {
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
-                    if (live && j < nva) dump[(size_t)r * g.N + oda[j >> 3] * 8 + (j & 7)] = Xa[j];
-                    if (live && j < nvb) dump[(size_t)r * g.N + odb[j >> 3] * 8 + (j & 7)] = Xb[j];
+                    const float ca = PARTS == 2 ? epi_corr(er, pick4(dca, j >> 3).w, ec) : 0.0f;
+                    if (live && j < nva) dump[(size_t)r * g.N + oda[j >> 3] * 8 + (j & 7)] = Xa[j] + ca;
+                }
+                if (PARTS == 2) {
+                    tmem_ld32(taddr + 32, hb);
+                    tmem_ld32(taddr + BN + 32, lb);
+                    tmem_wait2(hb, lb);
+                }
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    Xb[j] = PARTS == 2 ? __fadd_rn(__uint_as_float(hb[j]), __uint_as_float(lb[j])) : __uint_as_float(hb[j]);
+                    const float cb = PARTS == 2 ? epi_corr(er, pick4(dcb, j >> 3).w, ec) : 0.0f;
+                    if (live && j < nvb) dump[(size_t)r * g.N + odb[j >> 3] * 8 + (j & 7)] = Xb[j] + cb;
                 }
             } else {
                 if (nva < 32) {
@@ -459,24 +499,29 @@ __global__ void __launch_bounds__(THREADS, 1)
                     for (int j = 0; j < 32; ++j)
                         if (j >= nva) Xa[j] = __int_as_float(0x7fc00000);  // NaN: never listed
                 }
+                const float thr = fminf(L.key[kListK - 1], L.tw);
+                const float zp = L.has_zero ? kZeroPenalty : 0.0f;
+                const uint32_t ma = scr && nva > 0 ? epi_keys32(Xa, dca, re.zb, re.rho_lim, er, ec, thr, zp) : 0u;
+                if (__any_sync(0xffffffffu, ma != 0u))
+                    rare_chunk<PARTS>(taddr, BN, ma, oda, dca, er, xsm + et, ET, re, ec, L, tbest + r);
+                if (PARTS == 2) {
+                    tmem_ld32(taddr + 32, hb);
+                    tmem_ld32(taddr + BN + 32, lb);
+                    tmem_wait2(hb, lb);
+                }
+#pragma unroll
+                for (int j = 0; j < 32; ++j)
+                    Xb[j] = PARTS == 2 ? __fadd_rn(__uint_as_float(hb[j]), __uint_as_float(lb[j])) : __uint_as_float(hb[j]);
                 if (nvb < 32) {
 #pragma unroll
                     for (int j = 0; j < 32; ++j)
                         if (j >= nvb) Xb[j] = __int_as_float(0x7fc00000);
                 }
-                float4 dca[4], dcb[4];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    dca[q] = wdc[q];
-                    dcb[q] = wdc[4 + q];
-                }
-                const float thr = fminf(L.key[kListK - 1], L.tw);
-                const float zp = L.has_zero ? kZeroPenalty : 0.0f;
-                const uint32_t ma = scr && nva > 0 ? epi_keys32(Xa, dca, re.zb, re.rho_lim, ec, thr, zp) : 0u;
-                const uint32_t mb = scr && nvb > 0 ? epi_keys32(Xb, dcb, re.zb, re.rho_lim, ec, thr, zp) : 0u;
-                if (__any_sync(0xffffffffu, ma != 0u)) rare_chunk(taddr, ma, oda, dca, xsm + et, ET, re, ec, L, tbest + r);
+                const float thr_b = fminf(L.key[kListK - 1], L.tw);
+                const float zp_b = L.has_zero ? kZeroPenalty : 0.0f;
+                const uint32_t mb = scr && nvb > 0 ? epi_keys32(Xb, dcb, re.zb, re.rho_lim, er, ec, thr_b, zp_b) : 0u;
                 if (__any_sync(0xffffffffu, mb != 0u))
-                    rare_chunk(taddr + 32, mb, odb, dcb, xsm + et, ET, re, ec, L, tbest + r);
+                    rare_chunk<PARTS>(taddr + 32, BN, mb, odb, dcb, er, xsm + et, ET, re, ec, L, tbest + r);
             }
             tc_fence_before();
             __syncwarp();

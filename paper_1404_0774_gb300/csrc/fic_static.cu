@@ -9,7 +9,7 @@
 // process running under a hard device-memory cap set by someone else.  Such a
 // caller can neither pass a workspace it allocated nor let fic_encode
 // allocate one.  This entry point uses instead a static array of
-// FIC_STATIC_SCRATCH_BYTES (16 MiB) that every GPU which loads the library
+// FIC_STATIC_SCRATCH_BYTES (32 MiB) that every GPU which loads the library
 // holds until the process exits.
 #include <mutex>
 

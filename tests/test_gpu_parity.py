@@ -256,3 +256,24 @@ def test_decode_scaled_parity(fic, orc, scale_log2):
         inside = (base > 0) & (base < 4095) & fine_in[0::2, 0::2] & fine_in[1::2, 0::2] & fine_in[0::2, 1::2] \
             & fine_in[1::2, 1::2]
         assert np.abs(down - base)[inside].max() < 2e-6 * 4096 * 10
+
+
+@pytest.mark.parametrize("search", SEARCH)
+def test_failed_lists_rescan_gives_the_exact_maps(fic, orc, search):
+    """High-contrast slices (a smooth bone ring offers many near-equal edge
+    matches) leave some lists uncertified; those lists' candidates are then
+    re-scanned exactly.  The maps must equal the all-exact scan's and meet the
+    oracle bar, and the re-scan path must actually have run."""
+    img = fic_synth.ct_slice(fic_synth.CT_SEED + 1000 + 72, 512)
+    code = search_code(fic, search)
+    p = fic.params(range_size=8, domain_stride=4, bit_depth=12, search=code)
+    px = fic.params(range_size=8, domain_stride=4, bit_depth=12, search=code, flags=fic.FIC_FLAG_EXACT_SCAN)
+    a = gpu_encode(fic, img, p)
+    b = gpu_encode(fic, img, px)
+    assert int((a["info"] & fic.FIC_MAP_FALLBACK).sum()) > 0
+    for f in ("domain_idx", "iso", "s_code", "o_code", "err"):
+        assert np.array_equal(a[f], b[f]), f
+    rng = np.random.default_rng(3)
+    resc = np.nonzero(a["info"] & fic.FIC_MAP_FALLBACK)[0]
+    sample = np.unique(np.concatenate([resc[:24], rng.choice(len(a), 24, replace=False)]))
+    check_against_oracle(orc, img, a, 8, 4, 12, ranges=sample)
