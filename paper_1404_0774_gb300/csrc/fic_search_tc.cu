@@ -7,17 +7,20 @@
 //   B row (candidate):    [ 128*hi_i   | lo_i       (12-bit only) | -16 f_d  -f_d/m 0.. ]
 // with q'_i = 128*hi_i + lo_i (8-bit: a single q' block), so that the FP32
 // accumulator is Xt = sum q'b' - e_r f_d / m = (m X - Sq Sb) / m.  The K
-// dimension is laid out as 64-element SWIZZLE_128B blocks plus one
-// 16-element SWIZZLE_32B tail block carrying the centring terms.
+// dimension is laid out as one block per copy of the pixels (8x8 ranges:
+// 64 elements, SWIZZLE_128B; 4x4 ranges: 16 elements, SWIZZLE_32B) plus one
+// 16-element SWIZZLE_32B tail block carrying the centring terms.  For 12-bit
+// images the hi and lo blocks go to separate TMEM accumulators, whose sums
+// are exact, and the tail's centring term is folded in by the epilogue.
 //
 // CTA = 128 ranges (one per TMEM lane), streaming a contiguous slice of the
 // candidate dimension in tiles of 128:
-//   warp 0        TMA producer (one thread): A once, B tiles into a 4-stage ring
-//   warp 1        TMEM allocator + MMA issuer (one thread): 9 (12-bit) or 5
-//                 (8-bit) tcgen05.mma kind::f16 128x128x16 per tile into one
-//                 of two TMEM accumulators
-//   warps 2..5    epilogue: tcgen05.ld 32 columns at a time, FP32 screening
-//                 (eq 8-12 with quantisation), per-range top-4 list
+//   warp 0        TMA producer (one thread): A once, B tiles into a 3-stage ring
+//   warp 1        TMEM allocator + MMA issuer (one thread): m/16 tcgen05.mma
+//                 kind::f16 128x128x16 per pixel block (+1 tail for 8-bit)
+//                 per tile into one of two TMEM accumulator sets
+//   warps 2..9    epilogue: tcgen05.ld 32 columns at a time, FP32 screening
+//                 (eq 8-12 with quantisation), per-range candidate lists
 // Every mbarrier wait is bounded by a wall-clock limit; on expiry the CTA sets
 // an error flag, stops, drains its outstanding TMA loads (bounded), frees its
 // TMEM and exits.
@@ -234,20 +237,24 @@ struct TcMaps {
 
 }  // namespace
 
-// nblk: number of 64-element SWIZZLE_128B K blocks (1 for 8-bit, 2 for 12-bit).
+// NBLK: number of pixel K blocks (1 for 8-bit, 2 for 12-bit); BW: their width.
 // dump != nullptr: write the raw accumulators Xt[r][c] instead of screening.
-template <int NBLK>
+template <int NBLK, int BW>
 __global__ void __launch_bounds__(THREADS, 1)
     k_search_tc(const __grid_constant__ TcMaps maps, Geometry g, EpiConst ec, const RangeInfo *ri,
                 const float4 *dconst, const int *act, const int *dmap, const int *counts, int dense,
                 ListEntry *lists, int max_split, int target, int *tbest, float *dump, int *err,
                 uint32_t smem_bytes, int rpad, int npad)
 {
-    constexpr uint32_t A_BLK = BM * 128;                 // bytes of one 64-col block, A
-    constexpr uint32_t B_BLK = BN * 128;
+    // BW: K elements per copy of the pixels (64: 128B-swizzled blocks, n = 8;
+    // 16: 32B-swizzled blocks, n = 4); KPB MMAs of K = 16 per block
+    constexpr int KPB = BW / 16;
+    constexpr uint32_t A_BLK = BM * BW * 2;              // bytes of one block, A
+    constexpr uint32_t B_BLK = BN * BW * 2;
     constexpr uint32_t A_BYTES = NBLK * A_BLK + BM * 32;  // + SW32 tail
     constexpr uint32_t B_BYTES = NBLK * B_BLK + BN * 32;
-    constexpr int KSTEPS = NBLK * 4 + 1;
+    constexpr int KSTEPS = NBLK * KPB + 1;
+    constexpr uint32_t SBO = BW == 64 ? 1024 : 256, LAYOUT = BW == 64 ? 2 : 6;
     constexpr uint32_t IDESC = instr_desc(BM, BN);
     // 12-bit: the hi and lo parts of q' accumulate separately (each sum is
     // exact in FP32: multiples of 128 below 2^31, integers below 2^23) and the
@@ -333,8 +340,8 @@ __global__ void __launch_bounds__(THREADS, 1)
             int issued = 0;
             mbar_expect_tx(&a_bar, A_BYTES);
 #pragma unroll
-            for (int b = 0; b < NBLK; ++b) tma_load_2d(sA + b * A_BLK, &maps.a128, 64 * b, r0, &a_bar);
-            tma_load_2d(sA + NBLK * A_BLK, &maps.a32, 64 * NBLK, r0, &a_bar);
+            for (int b = 0; b < NBLK; ++b) tma_load_2d(sA + b * A_BLK, &maps.a128, BW * b, r0, &a_bar);
+            tma_load_2d(sA + NBLK * A_BLK, &maps.a32, BW * NBLK, r0, &a_bar);
             for (int it = 0; it < ntile; ++it) {
                 const int s = it % STAGES;
                 if (!mbar_wait(&empty_bar[s], ((it / STAGES) & 1) ^ 1, &abort_s, err)) break;
@@ -342,8 +349,8 @@ __global__ void __launch_bounds__(THREADS, 1)
                 const int y = (t_begin + it) * BN;
                 mbar_expect_tx(&full_bar[s], B_BYTES);
 #pragma unroll
-                for (int b = 0; b < NBLK; ++b) tma_load_2d(dst + b * B_BLK, &maps.b128, 64 * b, y, &full_bar[s]);
-                tma_load_2d(dst + NBLK * B_BLK, &maps.b32, 64 * NBLK, y, &full_bar[s]);
+                for (int b = 0; b < NBLK; ++b) tma_load_2d(dst + b * B_BLK, &maps.b128, BW * b, y, &full_bar[s]);
+                tma_load_2d(dst + NBLK * B_BLK, &maps.b32, BW * NBLK, y, &full_bar[s]);
                 issued = it + 1;
             }
             // drain: every issued load must land before the CTA may exit
@@ -372,19 +379,18 @@ __global__ void __launch_bounds__(THREADS, 1)
                 const uint32_t d_tmem = tmem_base + acc * ACC_COLS;
 #pragma unroll
                 for (int k = 0; k < KSTEPS; ++k) {
-                    if (PARTS == 2 && k == NBLK * 4) break;  // the correction is applied in the epilogue
+                    if (PARTS == 2 && k == NBLK * KPB) break;  // the correction is applied in the epilogue
                     uint64_t ad, bd;
-                    if (k < NBLK * 4) {
-                        const uint32_t off_a = (k >> 2) * A_BLK + (k & 3) * 32;
-                        const uint32_t off_b = (k >> 2) * B_BLK + (k & 3) * 32;
-                        ad = smem_desc(a_base + off_a, 1024, 2);
-                        bd = smem_desc(b_base + off_b, 1024, 2);
+                    const int blk = k / KPB, sub = k % KPB;
+                    if (k < NBLK * KPB) {
+                        ad = smem_desc(a_base + blk * A_BLK + sub * 32, SBO, LAYOUT);
+                        bd = smem_desc(b_base + blk * B_BLK + sub * 32, SBO, LAYOUT);
                     } else {
                         ad = smem_desc(a_base + NBLK * A_BLK, 256, 6);
                         bd = smem_desc(b_base + NBLK * B_BLK, 256, 6);
                     }
                     if (PARTS == 2)  // block 0 (hi) -> columns [0, BN), block 1 (lo) -> [BN, 2 BN)
-                        umma_f16(d_tmem + (k >> 2) * BN, ad, bd, IDESC, (k & 3) ? 1u : 0u);
+                        umma_f16(d_tmem + blk * BN, ad, bd, IDESC, sub ? 1u : 0u);
                     else
                         umma_f16(d_tmem, ad, bd, IDESC, k > 0 ? 1u : 0u);
                 }
@@ -577,16 +583,20 @@ bool make_map(CUtensorMap *m, const void *base, int rows, int kp, int x_box, int
 
 }  // namespace
 
+// K elements per copy of the pixels: m = 64 (n = 8) in 128B-swizzled blocks,
+// m = 16 (n = 4) in 32B-swizzled ones.
+static int tc_block_width(const Geometry &g) { return g.m == 64 ? 64 : (g.m == 16 ? 16 : 0); }
+
 bool search_tc_supported(const Geometry &g)
 {
-    // one 64-element K block per copy of the pixels: n = 8 (m = 64)
-    return g.m == 64 && g.KP == (g.split_hilo ? 2 : 1) * 64 + 16;
+    const int bw = tc_block_width(g);
+    return bw != 0 && g.KP == (g.split_hilo ? 2 : 1) * bw + 16;
 }
 
 size_t search_tc_smem(const Geometry &g)
 {
-    const int nblk = g.split_hilo ? 2 : 1;
-    return 1024 + (size_t)(nblk * BM * 128 + BM * 32) + (size_t)STAGES * (nblk * BN * 128 + BN * 32) +
+    const int nblk = g.split_hilo ? 2 : 1, bw = tc_block_width(g);
+    return 1024 + (size_t)(nblk * BM * bw * 2 + BM * 32) + (size_t)STAGES * (nblk * BN * bw * 2 + BN * 32) +
            32 * (32 * EPI_WARPS) * 4 + EPI_WARPS * 8 * 16 + EPI_WARPS * 8 * 4;
 }
 
@@ -596,35 +606,45 @@ int search_tc_tile() { return BN; }
 
 int search_tc_rows(int rows) { return (rows + 127) / 128 * 128; }
 
+template <int NBLK, int BW>
+static cudaError_t launch_tc(const TcMaps &mp, dim3 grid, size_t smem, const Geometry &g, const EpiConst &ec,
+                             const RangeInfo *ri, const CompactBufs &cb, int dense, ListEntry *lists, int max_split,
+                             int target, int *tbest, float *dump, int *err, int rpad, int npad, cudaStream_t st)
+{
+    cudaError_t e = cudaFuncSetAttribute(k_search_tc<NBLK, BW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_search_tc<NBLK, BW><<<grid, THREADS, smem, st>>>(mp, g, ec, ri, cb.dconst_c, cb.act, cb.dmap, cb.counts, dense,
+                                                       lists, max_split, target, tbest, dump, err, (uint32_t)smem,
+                                                       rpad, npad);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_search_tc(const Geometry &g, const EpiConst &ec, const RangeInfo *ri, const CompactBufs &cb,
                              int dense, const __half *ra16, const __half *cb16, ListEntry *lists, int max_split,
                              int target, int *tbest, float *dump, int *err, cudaStream_t st)
 {
     if (!search_tc_supported(g)) return cudaErrorInvalidValue;
     TcMaps mp;
-    const int nblk = g.split_hilo ? 2 : 1;
+    const int nblk = g.split_hilo ? 2 : 1, bw = tc_block_width(g);
+    const CUtensorMapSwizzle sw = bw == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_32B;
     // operand buffers hold whole boxes (rows padded with zeros to a multiple of 128)
     const int rpad = search_tc_rows(g.R), npad = search_tc_rows(g.N);
-    if (!make_map(&mp.a128, ra16, rpad, g.KP, 64, BM, CU_TENSOR_MAP_SWIZZLE_128B) ||
+    if (!make_map(&mp.a128, ra16, rpad, g.KP, bw, BM, sw) ||
         !make_map(&mp.a32, ra16, rpad, g.KP, 16, BM, CU_TENSOR_MAP_SWIZZLE_32B) ||
-        !make_map(&mp.b128, cb16, npad, g.KP, 64, BN, CU_TENSOR_MAP_SWIZZLE_128B) ||
+        !make_map(&mp.b128, cb16, npad, g.KP, bw, BN, sw) ||
         !make_map(&mp.b32, cb16, npad, g.KP, 16, BN, CU_TENSOR_MAP_SWIZZLE_32B))
         return cudaErrorInvalidValue;
     const size_t smem = search_tc_smem(g);
-    dim3 grid((g.R + BM - 1) / BM, max_split);
-    cudaError_t e;
-    if (nblk == 2) {
-        e = cudaFuncSetAttribute(k_search_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        k_search_tc<2><<<grid, THREADS, smem, st>>>(mp, g, ec, ri, cb.dconst_c, cb.act, cb.dmap, cb.counts, dense,
-                                                    lists, max_split, target, tbest, dump, err, (uint32_t)smem, rpad, npad);
-    } else {
-        e = cudaFuncSetAttribute(k_search_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        k_search_tc<1><<<grid, THREADS, smem, st>>>(mp, g, ec, ri, cb.dconst_c, cb.act, cb.dmap, cb.counts, dense,
-                                                    lists, max_split, target, tbest, dump, err, (uint32_t)smem, rpad, npad);
-    }
-    return cudaGetLastError();
+    const dim3 grid((g.R + BM - 1) / BM, max_split);
+    if (bw == 64)
+        return nblk == 2 ? launch_tc<2, 64>(mp, grid, smem, g, ec, ri, cb, dense, lists, max_split, target, tbest, dump,
+                                            err, rpad, npad, st)
+                         : launch_tc<1, 64>(mp, grid, smem, g, ec, ri, cb, dense, lists, max_split, target, tbest, dump,
+                                            err, rpad, npad, st);
+    return nblk == 2 ? launch_tc<2, 16>(mp, grid, smem, g, ec, ri, cb, dense, lists, max_split, target, tbest, dump, err,
+                                        rpad, npad, st)
+                     : launch_tc<1, 16>(mp, grid, smem, g, ec, ri, cb, dense, lists, max_split, target, tbest, dump, err,
+                                        rpad, npad, st);
 }
 
 }  // namespace fic

@@ -67,6 +67,8 @@ CASES = [
     ("ct12", lambda: fic_synth.ct_slice(23, 64), 8, 4, 12),
     ("rand12", lambda: fic_synth.random_image(24, 48, 80, 12).astype(np.uint16), 8, 8, 12),
     ("ramp12", lambda: (np.add.outer(np.arange(64) * 40, np.arange(64) * 23) % 4096).astype(np.uint16), 8, 4, 12),
+    ("ct12_n4", lambda: fic_synth.ct_slice(25, 64), 4, 2, 12),
+    ("mr8_n4", lambda: fic_synth.mr_slice(26, 48), 4, 4, 8),
 ]
 
 

@@ -73,6 +73,8 @@ CASES = [
     ("ct64_t4", lambda: fic_synth.ct_slice(6, 64), 8, 4, 12),
     ("rand12_96x64", lambda: fic_synth.random_image(7, 64, 96, 12), 8, 8, 12),
     ("rand8_n4", lambda: fic_synth.random_image(8, 32, 32, 8), 4, 2, 8),
+    ("ct12_n4", lambda: fic_synth.ct_slice(13, 96), 4, 2, 12),
+    ("mr8_n4_t4", lambda: fic_synth.mr_slice(14, 80), 4, 4, 8),
     ("ct_n16", lambda: fic_synth.ct_slice(9, 64), 16, 8, 12),
     ("min_size", lambda: fic_synth.random_image(10, 16, 16, 8), 8, 8, 8),
     ("constant", lambda: np.full((48, 48), 1234, np.uint16), 8, 4, 12),
@@ -91,8 +93,8 @@ def search_code(fic, search):
 @pytest.mark.parametrize("name,make,n,t,B", CASES, ids=[c[0] for c in CASES])
 @pytest.mark.parametrize("search", SEARCH)
 def test_encode_parity_small(fic, orc, name, make, n, t, B, search):
-    if search == "tc" and n != 8:
-        pytest.skip("the tensor-core search handles 8x8 ranges")
+    if search == "tc" and n not in (4, 8):
+        pytest.skip("the tensor-core search handles 4x4 and 8x8 ranges")
     img = make()
     p = fic.params(range_size=n, domain_stride=t, bit_depth=B, search=search_code(fic, search))
     got = gpu_encode(fic, img, p)
@@ -192,6 +194,7 @@ EXACT_CASES = [
     ("ct64_t4", lambda: fic_synth.ct_slice(19, 64), 8, 4, 12),
     ("mr64_t4", lambda: fic_synth.mr_slice(20, 64), 8, 4, 8),
     ("rand8_n4", lambda: fic_synth.random_image(21, 32, 32, 8), 4, 2, 8),
+    ("ct12_n4", lambda: fic_synth.ct_slice(23, 64), 4, 2, 12),
     ("flat_regions", lambda: np.where(fic_synth.random_image(22, 48, 48, 8) > 100, 200, 10).astype(np.uint8), 8, 4, 8),
 ]
 
@@ -202,8 +205,8 @@ def test_exact_scan_gives_the_screened_maps(fic, orc, name, make, n, t, B, searc
     """FIC_FLAG_EXACT_SCAN sends every screened range to the exhaustive exact
     scan (the path uncertified ranges take): the maps must be the screened
     search's, each flagged as resolved by the scan, and meet the oracle bar."""
-    if search == "tc" and n != 8:
-        pytest.skip("the tensor-core search handles 8x8 ranges")
+    if search == "tc" and n not in (4, 8):
+        pytest.skip("the tensor-core search handles 4x4 and 8x8 ranges")
     img = make()
     p = fic.params(range_size=n, domain_stride=t, bit_depth=B, search=search_code(fic, search))
     px = fic.params(range_size=n, domain_stride=t, bit_depth=B, search=search_code(fic, search),
@@ -219,12 +222,12 @@ def test_exact_scan_gives_the_screened_maps(fic, orc, name, make, n, t, B, searc
 
 
 @pytest.mark.parametrize("search", SEARCH)
-@pytest.mark.parametrize("n,sb,ob", [(8, 8, 10), (16, 6, 9), (8, 3, 4)])
+@pytest.mark.parametrize("n,sb,ob", [(8, 8, 10), (16, 6, 9), (8, 3, 4), (4, 8, 10)])
 def test_encode_parity_other_code_widths(fic, orc, search, n, sb, ob):
     """s and o quantised to other bit widths (the 8/10-bit and 6/9-bit cases
     need 128-bit exact residuals; 3/4 bits is a coarse grid)."""
-    if search == "tc" and n != 8:
-        pytest.skip("the tensor-core search handles 8x8 ranges")
+    if search == "tc" and n not in (4, 8):
+        pytest.skip("the tensor-core search handles 4x4 and 8x8 ranges")
     img = fic_synth.ct_slice(23 + n + sb, 64)
     p = fic.params(range_size=n, domain_stride=4, bit_depth=12, s_bits=sb, o_bits=ob, search=search_code(fic, search))
     check_against_oracle(orc, img, gpu_encode(fic, img, p), n, 4, 12, sb=sb, ob=ob)
