@@ -154,11 +154,15 @@ int choose_search(const Geometry &g, const fic_params *p)
 // use fewer splits when fewer ranges and domains need screening: enough CTAs
 // for `target` (four waves over the SMs), see active_splits.
 constexpr int kMaxSplit = 64;
+constexpr int kMaxLists = 128;  // candidate lists per range the re-score takes (and its work-item codes hold)
+
+int lists_per_split(int search);
+
 int choose_split(const Geometry &g, const fic_params *p, int search)
 {
     (void)g;
-    (void)search;
-    return p->n_split > 0 ? std::min(p->n_split, kMaxSplit) : kMaxSplit;
+    const int cap = std::min(kMaxSplit, kMaxLists / lists_per_split(search));
+    return p->n_split > 0 ? std::min(p->n_split, cap) : cap;
 }
 
 int split_target(const fic_params *p, int search)
@@ -197,7 +201,7 @@ EncLayout enc_layout(const Geometry &g, int search, int n_lists)
     L.rs32 = simt ? take(sizeof(float) * (size_t)g.R * g.m) : 0;
     L.cb32 = simt ? take(sizeof(float) * (size_t)g.N * g.m) : 0;
     L.ra16 = simt ? 0 : take(sizeof(__half) * (size_t)search_tc_rows(g.R) * g.KP);
-    L.cb16 = simt ? 0 : take(sizeof(__half) * (size_t)search_tc_rows(g.N) * g.KP);
+    L.cb16 = simt ? 0 : take(sizeof(__half) * (size_t)search_tc_cols(g.N) * g.KP);
     L.lists = take(sizeof(ListEntry) * (size_t)g.R * n_lists * kListK);
     L.winner = take(sizeof(uint32_t) * g.R);
     L.fb_list = take(sizeof(int) * g.R);
@@ -375,7 +379,7 @@ cudaError_t encode_pipeline(const Geometry &gd, const fic_params *p, int search,
     if (b.ra16) {  // zero the padding rows that complete the last TMA boxes
         const size_t row = sizeof(__half) * gd.KP;
         FIC_STEP(cudaMemsetAsync(ws + L.ra16 + row * gd.R, 0, row * (search_tc_rows(gd.R) - gd.R), st));
-        FIC_STEP(cudaMemsetAsync(ws + L.cb16 + row * gd.N, 0, row * (search_tc_rows(gd.N) - gd.N), st));
+        FIC_STEP(cudaMemsetAsync(ws + L.cb16 + row * gd.N, 0, row * (search_tc_cols(gd.N) - gd.N), st));
     }
     FIC_MARK(0);
     FIC_STEP(launch_prep(gd, dimg, ec, dense, (search == FIC_SEARCH_TC && gd.split_hilo) ? 1 : 0, active, b.ri, b.di, b.dconst, b.bblk, b.qblk, b.rs32, b.cb32, b.ra16,

@@ -281,10 +281,19 @@ __device__ __forceinline__ f32x2_t mul2(f32x2_t a, f32x2_t b)
 // (at most 7*Ls*2^-24).  The FP32 evaluations of c*y and c2*y2 each carry at
 // most 8*Ls^2*kappa*2^-24, and lambda*w^2 >= 0, so both keys are at least
 // c*y - kappa*near_slack with near_slack = (32*Ls^2 + 16*Ls)*2^-24.
+//
+// kNearPass: every near-boundary candidate goes to the rare pass instead
+// (the tensor-core search, whose near band is about 3e-4 wide), and the
+// mask is assembled from sign bits: bit (k - thr < 0) | (rho^2 >= lim^2),
+// with lim^2 rounded down so the band holds every |rho| > rho_lim.
+template <bool kNearPass = false>
 __device__ __forceinline__ uint32_t epi_keys32(const float (&X)[32], const float4 (&dc)[4], float zb, float rho_lim,
                                                float er, const EpiConst &ec, float thr, float zpen)
 {
-    uint32_t mask = 0;
+    uint32_t mask = 0, far = 0;  // kNearPass: bit-reversed masks of k < thr, of |rho| below the band
+    const f32x2_t thr2 = pk2(thr, thr);
+    const float mlim2 = -__fmul_rd(rho_lim, rho_lim);
+    const f32x2_t mlim = pk2(mlim2, mlim2);
     const f32x2_t two_ls = pk2(ec.two_ls, ec.two_ls), mls = pk2(-ec.ls, -ec.ls);
     const f32x2_t mag = pk2(kMagic, kMagic), zb2 = pk2(zb, zb), invg = pk2(ec.invG, ec.invG);
     const f32x2_t mg = pk2(-ec.G, -ec.G), lam = pk2(ec.lambda, ec.lambda), zp = pk2(zpen, zpen);
@@ -318,17 +327,27 @@ __device__ __forceinline__ uint32_t epi_keys32(const float (&X)[32], const float
             const f32x2_t cy = mul2(c, y);
             f32x2_t k = fma2(mul2(wv, lam), wv, cy);
             k = fma2(pk2(zero0, zero1), zp, k);
-            const f32x2_t lo = add2(cy, msl);
-            float k0, k1, l0, l1;
-            upk2(k, k0, k1);
-            upk2(lo, l0, l1);
-            k0 = fabsf(p0) > rho_lim ? l0 : k0;
-            k1 = fabsf(p1) > rho_lim ? l1 : k1;
-            mask |= (k0 < thr ? 1u : 0u) << j;
-            mask |= (k1 < thr ? 1u : 0u) << (j + 1);
+            if (kNearPass) {
+                float d0, d1, t0, t1;
+                upk2(sub2(k, thr2), d0, d1);
+                upk2(fma2(rho, rho, mlim), t0, t1);
+                mask = __funnelshift_l(__float_as_uint(d0), mask, 1);  // (mask << 1) | sign bit
+                mask = __funnelshift_l(__float_as_uint(d1), mask, 1);
+                far = __funnelshift_l(__float_as_uint(t0), far, 1);
+                far = __funnelshift_l(__float_as_uint(t1), far, 1);
+            } else {
+                const f32x2_t lo = add2(cy, msl);
+                float k0, k1, l0, l1;
+                upk2(k, k0, k1);
+                upk2(lo, l0, l1);
+                k0 = fabsf(p0) > rho_lim ? l0 : k0;
+                k1 = fabsf(p1) > rho_lim ? l1 : k1;
+                mask |= (k0 < thr ? 1u : 0u) << j;
+                mask |= (k1 < thr ? 1u : 0u) << (j + 1);
+            }
         }
     }
-    return mask;
+    return kNearPass ? __brev(mask | ~far) : mask;
 }
 
 __device__ __forceinline__ float4 pick4(const float4 (&dc)[4], int q)
@@ -459,7 +478,8 @@ bool search_tc_supported(const Geometry &g);
 size_t search_tc_smem(const Geometry &g);
 int search_tc_tile();
 int search_tc_lists_per_split();
-int search_tc_rows(int rows);  // operand rows allocated (multiple of the TMA box)
+int search_tc_rows(int rows);  // range operand rows allocated (multiple of the TMA box)
+int search_tc_cols(int cols);  // candidate operand rows allocated (multiple of the tile)
 cudaError_t launch_search_tc(const Geometry &g, const EpiConst &ec, const RangeInfo *ri, const CompactBufs &cb,
                              int dense, const __half *ra16, const __half *cb16, ListEntry *lists, int max_split,
                              int target, int *tbest, float *dump, int *err, cudaStream_t st);

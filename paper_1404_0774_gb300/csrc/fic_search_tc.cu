@@ -14,13 +14,15 @@
 // are exact, and the tail's centring term is folded in by the epilogue.
 //
 // CTA = 128 ranges (one per TMEM lane), streaming a contiguous slice of the
-// candidate dimension in tiles of 128:
+// candidate dimension in tiles of 96:
 //   warp 0        TMA producer (one thread): A once, B tiles into a 3-stage ring
 //   warp 1        TMEM allocator + MMA issuer (one thread): m/16 tcgen05.mma
-//                 kind::f16 128x128x16 per pixel block (+1 tail for 8-bit)
+//                 kind::f16 128x96x16 per pixel block (+1 tail for 8-bit)
 //                 per tile into one of two TMEM accumulator sets
-//   warps 2..9    epilogue: tcgen05.ld 32 columns at a time, FP32 screening
-//                 (eq 8-12 with quantisation), per-range candidate lists
+//   warps 2..13   epilogue, three per TMEM lane quadrant (three per scheduler
+//                 with the register budget of 14 warps): each takes 32
+//                 columns of every tile, FP32 screening (eq 8-12 with
+//                 quantisation), per-range candidate lists
 // Every mbarrier wait is bounded by a wall-clock limit; on expiry the CTA sets
 // an error flag, stops, drains its outstanding TMA loads (bounded), frees its
 // TMEM and exits.
@@ -33,12 +35,14 @@ namespace fic {
 namespace {
 
 constexpr int BM = 128;
-constexpr int BN = 128;
+constexpr int BN = 96;                          // candidates per tile
 constexpr int STAGES = 3;
 constexpr int NACC = 2;
-constexpr int EPI_WARPS = 8;                    // two per TMEM lane quadrant
-constexpr int THREADS = 64 + 32 * EPI_WARPS;   // TMA warp, MMA warp, epilogue
-constexpr int EPI_COLS = BN / 2;               // columns of a tile per epilogue warp
+constexpr int EPI_COLS = 32;                    // columns of a tile per epilogue warp
+constexpr int LISTS = BN / EPI_COLS;            // epilogue warps per TMEM lane quadrant
+constexpr int EPI_WARPS = 4 * LISTS;
+constexpr int THREADS = 64 + 32 * EPI_WARPS;    // TMA warp, MMA warp, epilogue
+constexpr int DC_WARP = EPI_COLS / 8;           // domains per warp per tile
 constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s per wait
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
@@ -199,29 +203,16 @@ __device__ __forceinline__ void tmem_wait2(uint32_t (&a)[32], uint32_t (&b)[32])
 }
 
 // Rare pass of one 32-column chunk (warp-collective: every lane calls it):
-// reload the cross terms (still in TMEM at taddr, and the lo part at
-// taddr + lo_off when the parts accumulate separately) into this thread's
-// column of the staging buffer, then each thread visits its own candidates
-// of `mask`.  Staging is per thread, so no cross-lane ordering is needed.
-template <int PARTS>
-__device__ __forceinline__ void rare_chunk(uint32_t taddr, uint32_t lo_off, uint32_t mask, const int (&od)[4],
+// stage this thread's cross terms X[] in its column of the staging buffer,
+// then each thread visits its own candidates of `mask`.  Staging is per
+// thread, so no cross-lane ordering is needed.
+__device__ __forceinline__ void rare_chunk(const float (&X)[32], uint32_t mask, const int (&od)[4],
                                            const float4 (&dc)[4], float er, float *xcol, int stride,
                                            const RangeEpi &re, const EpiConst &ec, ListState &L, int *tbest_r)
 {
-    uint32_t tx[32];
-    tmem_ld32(taddr, tx);
-    if (PARTS == 2) {
-        uint32_t tl[32];
-        tmem_ld32(taddr + lo_off, tl);
-        tmem_wait2(tx, tl);
-#pragma unroll
-        for (int j = 0; j < 32; ++j) xcol[j * stride] = __fadd_rn(__uint_as_float(tx[j]), __uint_as_float(tl[j]));
-    } else {
-        tmem_wait(tx);
-#pragma unroll
-        for (int j = 0; j < 32; ++j) xcol[j * stride] = __uint_as_float(tx[j]);
-    }
     if (mask) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) xcol[j * stride] = X[j];
         epi_rare(xcol, stride, od, dc, er, re, ec, L, mask);
         if (L.T < L.Tpub) {
             atomicMin(tbest_r, f2ord(L.T));
@@ -230,6 +221,9 @@ __device__ __forceinline__ void rare_chunk(uint32_t taddr, uint32_t lo_off, uint
     }
     __syncwarp();
 }
+
+// Bits of the first nv (1..32) columns of a 32-column chunk.
+__device__ __forceinline__ uint32_t col_mask(int nv) { return nv >= 32 ? 0xffffffffu : (1u << nv) - 1u; }
 
 struct TcMaps {
     CUtensorMap a128, a32, b128, b32;
@@ -263,7 +257,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     // columns included.
     constexpr uint32_t PARTS = NBLK == 2 ? 2 : 1;
     constexpr uint32_t ACC_COLS = BN * PARTS;
-    constexpr uint32_t TMEM_COLS = ACC_COLS * NACC;  // 512 or 256
+    constexpr uint32_t TMEM_COLS = ACC_COLS * NACC <= 256 ? 256 : 512;  // allocation: a power of two
 
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -271,7 +265,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     uint8_t *sB = smem + A_BYTES;  // A_BYTES is a multiple of 1024
     constexpr int ET = 32 * EPI_WARPS;                                // epilogue threads
     float *xsm = reinterpret_cast<float *>(sB + STAGES * B_BYTES);  // [32][ET] cross terms (rare pass)
-    float4 *dcs = reinterpret_cast<float4 *>(xsm + 32 * ET);        // [EPI_WARPS][8] domain constants
+    float4 *dcs = reinterpret_cast<float4 *>(xsm + 32 * ET);        // [EPI_WARPS][DC_WARP] domain constants
     __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], a_bar, tfull_bar[NACC], tempty_bar[NACC];
     __shared__ uint32_t tmem_base_s;
     __shared__ int abort_s;
@@ -295,7 +289,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         // self-checks: every TMA box and MMA operand must lie inside this CTA's
         // dynamic shared memory, and every box inside the padded operands
         const uint32_t used = (uint32_t)(smem - smem_raw) + A_BYTES + STAGES * B_BYTES + 32 * ET * 4 +
-                              EPI_WARPS * 8 * 16 + EPI_WARPS * 8 * 4;
+                              EPI_WARPS * DC_WARP * (16 + 4);
         int bad = 0;
         if (used > smem_bytes) bad = 2;
         if (r0 + BM > rpad || t_end * BN > npad) bad = 3;
@@ -400,30 +394,30 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
     } else {
         // ------------------------------------------------------ epilogue
-        const int ew = warp - 2;              // epilogue warp 0..7
+        const int ew = warp - 2;              // epilogue warp 0..EPI_WARPS-1
         const int quad = warp & 3;            // TMEM lane quadrant this warp may access
-        const int half = ew >> 2;             // which 64 columns of each tile
+        const int part = ew >> 2;             // which 32 columns of each tile
         const int row = quad * 32 + lane;
         const int et = ew * 32 + lane;        // staging column of this thread
         const int jrow = r0 + row;            // search row
         const bool live = jrow < nrow;
         const int r = live ? act[jrow] : 0;   // range id
-        float4 *wdc = dcs + ew * 8;
-        int *wod = reinterpret_cast<int *>(dcs + EPI_WARPS * 8) + ew * 8;
+        float4 *wdc = dcs + ew * DC_WARP;
+        int *wod = reinterpret_cast<int *>(dcs + EPI_WARPS * DC_WARP) + ew * DC_WARP;
         RangeEpi re{};
         if (live) re = range_epi(ri[r], ec);
         const float er = (PARTS == 2 && live) ? (float)ri[r].e_r : 0.0f;  // centring correction factor
         const bool scr = live && (dense || !re.shadow);
         ListState L;
         list_init(L);
-        const uint32_t lane_addr = tmem_base + ((uint32_t)(quad * 32) << 16) + half * EPI_COLS;
-        // prefetch for the first tile: its 8 domains and the shared best key
+        const uint32_t lane_addr = tmem_base + ((uint32_t)(quad * 32) << 16) + part * EPI_COLS;
+        // prefetch for the first tile: its 4 domains and the shared best key
         float4 dc_next = make_float4(0.f, 0.f, 0.f, 0.f);
         int od_next = 0;
         int tb_next = 0x7f800000;
         if (ntile > 0) {
-            const int jd = ((t_begin * BN + half * EPI_COLS) >> 3) + lane;
-            if (lane < 8 && jd < counts[2]) {
+            const int jd = ((t_begin * BN + part * EPI_COLS) >> 3) + lane;
+            if (lane < DC_WARP && jd < counts[2]) {
                 dc_next = __ldg(dconst + jd);
                 od_next = __ldg(dmap + jd);
             }
@@ -431,8 +425,8 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
         for (int it = 0; it < ntile; ++it) {
             const int acc = it % NACC;
-            const int n0 = (t_begin + it) * BN + half * EPI_COLS;
-            if (lane < 8) {
+            const int n0 = (t_begin + it) * BN + part * EPI_COLS;
+            if (lane < DC_WARP) {
                 wdc[lane] = dc_next;
                 wod[lane] = od_next;
             }
@@ -443,7 +437,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             }
             if (it + 1 < ntile) {  // prefetch for the next tile
                 const int jd = ((n0 + BN) >> 3) + lane;
-                if (lane < 8 && jd < counts[2]) {
+                if (lane < DC_WARP && jd < counts[2]) {
                     dc_next = __ldg(dconst + jd);
                     od_next = __ldg(dmap + jd);
                 }
@@ -454,87 +448,58 @@ __global__ void __launch_bounds__(THREADS, 1)
             if (!__all_sync(0xffffffffu, mbar_wait(&tfull_bar[acc], (it / NACC) & 1, &abort_s, err))) break;
             tc_fence_after();
             const uint32_t taddr = lane_addr + acc * ACC_COLS;
-            const int nva = min(32, ncol - n0), nvb = min(32, ncol - n0 - 32);
-            int oda[4], odb[4];
-            float4 dca[4], dcb[4];
+            const int nv = min(32, ncol - n0);  // may be <= 0 in the last tile
+            int od[4];
+            float4 dc[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                oda[q] = wod[q];
-                odb[q] = wod[4 + q];
-                dca[q] = wdc[q];
-                dcb[q] = wdc[4 + q];
+                od[q] = wod[q];
+                dc[q] = wdc[q];
             }
-            // chunk a; with separate parts, chunk b's loads overlap a's main pass
-            float Xa[32], Xb[32];
-            uint32_t hb[32], lb[32];
+            float X[32];
             {
-                uint32_t ha[32], la[32];
-                tmem_ld32(taddr, ha);
-                if (PARTS == 2) {  // (chunk b is loaded after a's passes: registers)
-                    tmem_ld32(taddr + BN, la);
-                    tmem_wait2(ha, la);
+                uint32_t h[32], l[32];
+                tmem_ld32(taddr, h);
+                if (PARTS == 2) {
+                    tmem_ld32(taddr + BN, l);
+                    tmem_wait2(h, l);
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) Xa[j] = __fadd_rn(__uint_as_float(ha[j]), __uint_as_float(la[j]));
+                    for (int j = 0; j < 32; j += 2)
+                        upk2(add2(pk2(__uint_as_float(h[j]), __uint_as_float(h[j + 1])),
+                                  pk2(__uint_as_float(l[j]), __uint_as_float(l[j + 1]))), X[j], X[j + 1]);
                 } else {
-                    tmem_ld32(taddr + 32, hb);
-                    tmem_wait2(ha, hb);
+                    tmem_wait(h);
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) Xa[j] = __uint_as_float(ha[j]);
+                    for (int j = 0; j < 32; ++j) X[j] = __uint_as_float(h[j]);
                 }
             }
-            if (dump) {
-#pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const float ca = PARTS == 2 ? epi_corr(er, pick4(dca, j >> 3).w, ec) : 0.0f;
-                    if (live && j < nva) dump[(size_t)r * g.N + oda[j >> 3] * 8 + (j & 7)] = Xa[j] + ca;
-                }
-                if (PARTS == 2) {
-                    tmem_ld32(taddr + 32, hb);
-                    tmem_ld32(taddr + BN + 32, lb);
-                    tmem_wait2(hb, lb);
-                }
-#pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    Xb[j] = PARTS == 2 ? __fadd_rn(__uint_as_float(hb[j]), __uint_as_float(lb[j])) : __uint_as_float(hb[j]);
-                    const float cb = PARTS == 2 ? epi_corr(er, pick4(dcb, j >> 3).w, ec) : 0.0f;
-                    if (live && j < nvb) dump[(size_t)r * g.N + odb[j >> 3] * 8 + (j & 7)] = Xb[j] + cb;
-                }
-            } else {
-                if (nva < 32) {
-#pragma unroll
-                    for (int j = 0; j < 32; ++j)
-                        if (j >= nva) Xa[j] = __int_as_float(0x7fc00000);  // NaN: never listed
-                }
-                const float thr = fminf(L.key[kListK - 1], L.tw);
-                const float zp = L.has_zero ? kZeroPenalty : 0.0f;
-                const uint32_t ma = scr && nva > 0 ? epi_keys32(Xa, dca, re.zb, re.rho_lim, er, ec, thr, zp) : 0u;
-                if (__any_sync(0xffffffffu, ma != 0u))
-                    rare_chunk<PARTS>(taddr, BN, ma, oda, dca, er, xsm + et, ET, re, ec, L, tbest + r);
-                if (PARTS == 2) {
-                    tmem_ld32(taddr + 32, hb);
-                    tmem_ld32(taddr + BN + 32, lb);
-                    tmem_wait2(hb, lb);
-                }
-#pragma unroll
-                for (int j = 0; j < 32; ++j)
-                    Xb[j] = PARTS == 2 ? __fadd_rn(__uint_as_float(hb[j]), __uint_as_float(lb[j])) : __uint_as_float(hb[j]);
-                if (nvb < 32) {
-#pragma unroll
-                    for (int j = 0; j < 32; ++j)
-                        if (j >= nvb) Xb[j] = __int_as_float(0x7fc00000);
-                }
-                const float thr_b = fminf(L.key[kListK - 1], L.tw);
-                const float zp_b = L.has_zero ? kZeroPenalty : 0.0f;
-                const uint32_t mb = scr && nvb > 0 ? epi_keys32(Xb, dcb, re.zb, re.rho_lim, er, ec, thr_b, zp_b) : 0u;
-                if (__any_sync(0xffffffffu, mb != 0u))
-                    rare_chunk<PARTS>(taddr + 32, BN, mb, odb, dcb, er, xsm + et, ET, re, ec, L, tbest + r);
-            }
+            // the accumulator is in registers: release it to the MMA warp now,
+            // so that a slow warp holds up the tensor cores only by its load
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&tempty_bar[acc]);
+            if (dump) {
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const float ca = PARTS == 2 ? epi_corr(er, pick4(dc, j >> 3).w, ec) : 0.0f;
+                    if (live && j < nv) dump[(size_t)r * g.N + od[j >> 3] * 8 + (j & 7)] = X[j] + ca;
+                }
+            } else {
+                if (nv < 32) {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j)
+                        if (j >= nv) X[j] = __int_as_float(0x7fc00000);  // NaN: never listed
+                }
+                const float thr = fminf(L.key[kListK - 1], L.tw);
+                const float zp = L.has_zero ? kZeroPenalty : 0.0f;
+                const uint32_t mask =
+                    scr && nv > 0 ? epi_keys32<true>(X, dc, re.zb, re.rho_lim, er, ec, thr, zp) & col_mask(nv) : 0u;
+                if (__any_sync(0xffffffffu, mask != 0u))
+                    rare_chunk(X, mask, od, dc, er, xsm + et, ET, re, ec, L, tbest + r);
+            }
         }
         if (scr && !dump) {
-            ListEntry *dst = lists + (((size_t)r * max_split + split) * 2 + half) * kListK;
+            ListEntry *dst = lists + (((size_t)r * max_split + split) * LISTS + part) * kListK;
 #pragma unroll
             for (int i = 0; i < kListK; ++i) dst[i] = ListEntry{L.key[i], L.idx[i]};
         }
@@ -597,14 +562,16 @@ size_t search_tc_smem(const Geometry &g)
 {
     const int nblk = g.split_hilo ? 2 : 1, bw = tc_block_width(g);
     return 1024 + (size_t)(nblk * BM * bw * 2 + BM * 32) + (size_t)STAGES * (nblk * BN * bw * 2 + BN * 32) +
-           32 * (32 * EPI_WARPS) * 4 + EPI_WARPS * 8 * 16 + EPI_WARPS * 8 * 4;
+           32 * (32 * EPI_WARPS) * 4 + EPI_WARPS * DC_WARP * (16 + 4);
 }
 
-int search_tc_lists_per_split() { return 2; }
+int search_tc_lists_per_split() { return LISTS; }
 
 int search_tc_tile() { return BN; }
 
-int search_tc_rows(int rows) { return (rows + 127) / 128 * 128; }
+int search_tc_rows(int rows) { return (rows + BM - 1) / BM * BM; }
+
+int search_tc_cols(int cols) { return (cols + BN - 1) / BN * BN; }
 
 template <int NBLK, int BW>
 static cudaError_t launch_tc(const TcMaps &mp, dim3 grid, size_t smem, const Geometry &g, const EpiConst &ec,
@@ -628,7 +595,7 @@ cudaError_t launch_search_tc(const Geometry &g, const EpiConst &ec, const RangeI
     const int nblk = g.split_hilo ? 2 : 1, bw = tc_block_width(g);
     const CUtensorMapSwizzle sw = bw == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_32B;
     // operand buffers hold whole boxes (rows padded with zeros to a multiple of 128)
-    const int rpad = search_tc_rows(g.R), npad = search_tc_rows(g.N);
+    const int rpad = search_tc_rows(g.R), npad = search_tc_cols(g.N);
     if (!make_map(&mp.a128, ra16, rpad, g.KP, bw, BM, sw) ||
         !make_map(&mp.a32, ra16, rpad, g.KP, 16, BM, CU_TENSOR_MAP_SWIZZLE_32B) ||
         !make_map(&mp.b128, cb16, npad, g.KP, bw, BN, sw) ||
