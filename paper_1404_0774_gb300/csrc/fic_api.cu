@@ -375,15 +375,12 @@ cudaError_t encode_pipeline(const Geometry &gd, const fic_params *p, int search,
     } while (0)
 #define FIC_MARK(i) \
     if (timed) FIC_STEP(cudaEventRecord(g_phase.ev[i], st))
-    FIC_STEP(cudaMemsetAsync(b.fb_count, 0, 4 * sizeof(int), st));
-    if (b.ra16) {  // zero the padding rows that complete the last TMA boxes
-        const size_t row = sizeof(__half) * gd.KP;
-        FIC_STEP(cudaMemsetAsync(ws + L.ra16 + row * gd.R, 0, row * (search_tc_rows(gd.R) - gd.R), st));
-        FIC_STEP(cudaMemsetAsync(ws + L.cb16 + row * gd.N, 0, row * (search_tc_cols(gd.N) - gd.N), st));
-    }
+    // (operand rows past the kept ones, padding included, are never written:
+    // whatever they hold only reaches accumulator rows and columns that the
+    // epilogue ignores; the exact-scan queue counters are zeroed by k_stats)
     FIC_MARK(0);
     FIC_STEP(launch_prep(gd, dimg, ec, dense, (search == FIC_SEARCH_TC && gd.split_hilo) ? 1 : 0, active, b.ri, b.di, b.dconst, b.bblk, b.qblk, b.rs32, b.cb32, b.ra16,
-                         b.cb16, b.tbest, b.cb, st));
+                         b.cb16, b.tbest, b.cb, b.fb_count, st));
     if (!dump) FIC_STEP(launch_seed(gd, ec, b.ri, b.di, b.dconst, b.bblk, b.qblk, b.cb.rkeep, b.tbest, st));
     FIC_MARK(1);
     if (search == FIC_SEARCH_TC)
@@ -841,6 +838,10 @@ int run_batch(const fic_slice *slices, int n, const fic_params *p, void *workspa
         load[best] += (long long)plan[i].g.R * plan[i].g.D;
     }
     // one eager run first (kernel attributes, first-use work), then capture
+    struct DepLaunchOff {
+        DepLaunchOff() { g_dep_launch = false; }
+        ~DepLaunchOff() { g_dep_launch = true; }
+    } dep_off;
     for (int pass = 0; pass < 2; ++pass) {
         // pass 0 runs on the caller's stream; pass 1 captures from a private
         // stream (the legacy default stream cannot be captured) and the graph

@@ -24,12 +24,44 @@
 #pragma once
 
 #include <cuda_fp16.h>
+#include <utility>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include "fic.h"
 
 namespace fic {
+
+// Programmatic dependent launch: a pipeline kernel may be scheduled while its
+// predecessor in the stream drains.  Each one waits for the predecessor's
+// completion (and memory) before touching global memory, then lets its own
+// successor be scheduled.
+__device__ __forceinline__ void grid_dep_sync()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// Off while the batched encode builds its graph: there, branches that run
+// concurrently make better use of the SMs than early-scheduled CTAs that wait.
+inline thread_local bool g_dep_launch = true;
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_dep(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args &&...args)
+{
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = g_dep_launch ? 1 : 0;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
 
 constexpr int kListK = 4;          // entries per candidate list
 // A list entry's idx carries the candidate index (8d + k, < 2^31) and, in bit
@@ -521,7 +553,8 @@ __device__ __forceinline__ RangeEpi range_epi(const RangeInfo &ri, const EpiCons
 cudaError_t launch_prep(const Geometry &g, const void *img, const EpiConst &ec, int dense, int tc_split,
                         const int *active,
                         RangeInfo *ri, DomainInfo *di, float4 *dconst, uint16_t *bblk, uint16_t *qblk, float *rs32,
-                        float *cb32, __half *ra16, __half *cb16, int *tbest, const CompactBufs &cb, cudaStream_t st);
+                        float *cb32, __half *ra16, __half *cb16, int *tbest, const CompactBufs &cb, int *zero4,
+                        cudaStream_t st);
 cudaError_t launch_seed(const Geometry &g, const EpiConst &ec, const RangeInfo *ri, const DomainInfo *di,
                         const float4 *dconst, const uint16_t *bblk, const uint16_t *qblk, const int *rkeep,
                         int *tbest, cudaStream_t st);

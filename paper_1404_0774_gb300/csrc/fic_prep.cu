@@ -159,8 +159,10 @@ __device__ __forceinline__ void domain_stats(const Geometry &g, const void *img,
 __global__ void __launch_bounds__(256) k_stats(Geometry g, EpiConst ec, const void *img, int dense, int tc_split,
                                                const int *active, int rb, RangeInfo *ri, uint16_t *bblk, int *tbest,
                                                DomainInfo *di, float4 *dconst, uint16_t *qblk, int *rkeep,
-                                               int *dkeep)
+                                               int *dkeep, int *zero4)
 {
+    grid_dep_sync();
+    if (blockIdx.x == 0 && threadIdx.x < 4) zero4[threadIdx.x] = 0;  // exact-scan queue counters
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     if ((int)blockIdx.x < rb) {
         const int r = blockIdx.x * 8 + w;
@@ -181,6 +183,7 @@ constexpr int kCompactRounds = 16;
 __global__ void __launch_bounds__(1024) k_compact(int nr, const int *rflag, int *ract, int *rcnt, int nd,
                                                   const int *dflag, int *dact, int *dcnt)
 {
+    grid_dep_sync();
     __shared__ int off_s[kCompactRounds * 32];
     __shared__ int base_s, first_s;
     const bool dom = blockIdx.x == 1;
@@ -356,6 +359,7 @@ __global__ void __launch_bounds__(256, 4) k_rows(Geometry g, int rb, const Range
                                               const int *act, const int *dact, const int *counts, float *rs32,
                                               __half *ra16, float *cb32, __half *cb16, float4 *dconst_c, int *dmap)
 {
+    grid_dep_sync();
     __shared__ uint8_t src_s[8][kMaxM];
     __shared__ uint16_t kc_s[8 * ((2 * kMaxM + 16) / 8)];
     __shared__ uint16_t hi_s[8][kMaxM], lo_s[8][kMaxM];
@@ -383,18 +387,19 @@ __global__ void __launch_bounds__(256, 4) k_rows(Geometry g, int rb, const Range
 cudaError_t launch_prep(const Geometry &g, const void *img, const EpiConst &ec, int dense, int tc_split,
                         const int *active,
                         RangeInfo *ri, DomainInfo *di, float4 *dconst, uint16_t *bblk, uint16_t *qblk, float *rs32,
-                        float *cb32, __half *ra16, __half *cb16, int *tbest, const CompactBufs &cb, cudaStream_t st)
+                        float *cb32, __half *ra16, __half *cb16, int *tbest, const CompactBufs &cb, int *zero4,
+                        cudaStream_t st)
 {
     const int rb = (g.R + 7) / 8, db = (g.D + 7) / 8;
-    k_stats<<<rb + db, 256, 0, st>>>(g, ec, img, dense, tc_split, active, rb, ri, bblk, tbest, di, dconst, qblk,
-                                     cb.rkeep, cb.dkeep);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = launch_dep(k_stats, dim3(rb + db), dim3(256), 0, st, g, ec, img, dense, tc_split, active, rb, ri,
+                               bblk, tbest, di, dconst, qblk, cb.rkeep, cb.dkeep, zero4);
     if (e != cudaSuccess) return e;
-    k_compact<<<2, 1024, 0, st>>>(g.R, cb.rkeep, cb.act, cb.counts + 0, g.D, cb.dkeep, cb.dact, cb.counts + 2);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_rows<<<rb + db, 256, 0, st>>>(g, rb, ri, bblk, di, qblk, dconst, cb.act, cb.dact, cb.counts, rs32, ra16, cb32,
-                                    cb16, cb.dconst_c, cb.dmap);
-    return cudaGetLastError();
+    e = launch_dep(k_compact, dim3(2), dim3(1024), 0, st, g.R, (const int *)cb.rkeep, cb.act, cb.counts + 0, g.D,
+                   (const int *)cb.dkeep, cb.dact, cb.counts + 2);
+    if (e != cudaSuccess) return e;
+    return launch_dep(k_rows, dim3(rb + db), dim3(256), 0, st, g, rb, (const RangeInfo *)ri, (const uint16_t *)bblk,
+                      (const DomainInfo *)di, (const uint16_t *)qblk, (const float4 *)dconst, (const int *)cb.act,
+                      (const int *)cb.dact, (const int *)cb.counts, rs32, ra16, cb32, cb16, cb.dconst_c, cb.dmap);
 }
 
 // Seed of the per-range best key: before the search, every range scores 256
@@ -408,6 +413,7 @@ __global__ void __launch_bounds__(256) k_seed(Geometry g, EpiConst ec, const Ran
                                               const float4 *dconst, const uint16_t *bblk, const uint16_t *qblk,
                                               const int *rkeep, int *tbest)
 {
+    grid_dep_sync();
     // q2_s[p][slot]: contracted-domain pixels 2p, 2p+1 of the slot's domain
     // (lanes read consecutive words); bk_s[k][j]: the range pixel that S_k
     // places over domain pixel j, so X(d, k) = sum_j q_d[j] * bk_s[k][j]
@@ -486,8 +492,7 @@ cudaError_t launch_seed(const Geometry &g, const EpiConst &ec, const RangeInfo *
                         const float4 *dconst, const uint16_t *bblk, const uint16_t *qblk, const int *rkeep,
                         int *tbest, cudaStream_t st)
 {
-    k_seed<<<g.R, 256, 0, st>>>(g, ec, ri, di, dconst, bblk, qblk, rkeep, tbest);
-    return cudaGetLastError();
+    return launch_dep(k_seed, dim3(g.R), dim3(256), 0, st, g, ec, ri, di, dconst, bblk, qblk, rkeep, tbest);
 }
 
 }  // namespace fic

@@ -493,6 +493,7 @@ __global__ void __launch_bounds__(32 * kRescoreWarps, 4)
               uint32_t *winner, int *fb_list, int *fb_count, int *fb_done, SpanBufs sb)
 {
     extern __shared__ int bk_all[];  // [warps][8][m+1]
+    grid_dep_sync();
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < g.R; r += gridDim.x * blockDim.x) {
         if (!rkeep[r]) winner[r] = 0;
         fb_done[r] = 0;  // completion counters of the exact fallback
@@ -694,6 +695,7 @@ __global__ void __launch_bounds__(256) k_exact_scans(Geometry g, const RangeInfo
                                                      int max_split, int lists_per_split, int max_lists, SpanBufs sb,
                                                      uint32_t *winner)
 {
+    grid_dep_sync();
     full_scans<Wide>(g, ri, di, bblk, qblk, fb_list, fb_count, nch, part, done, winner);
     list_scans<Wide>(g, ri, di, bblk, qblk, counts, dmap, col_tile, target, max_split, lists_per_split, max_lists, sb,
                      winner);
@@ -717,6 +719,7 @@ __global__ void __launch_bounds__(32 * kFinWarps) k_finalize(Geometry g, const R
     __shared__ uint32_t q_s[kFinRanges][(kMaxM + 2) / 2];
     __shared__ uint32_t w_s[kFinRanges];
     __shared__ long long x_s[kFinWarps][kFinRanges];
+    grid_dep_sync();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int r0 = blockIdx.x * kFinRanges;
     const int nr = min(kFinRanges, g.R - r0);
@@ -800,15 +803,9 @@ cudaError_t launch_rescore(const Geometry &g, const EpiConst &ec, const RangeInf
     // at most as many blocks as are resident at once (4 per SM at this size)
     const int blocks = std::max(1, std::min((g.R + kRescoreWarps - 1) / kRescoreWarps, 4 * n_sm));
     if (max_lists * kListK > 32 * kRescoreEnt) return cudaErrorInvalidValue;
-    if (g.wide)
-        k_rescore<true><<<blocks, 32 * kRescoreWarps, smem, st>>>(
-            g, ec, ri, di, bblk, qblk, lists, max_lists, counts, act, rkeep, lists_per_split, col_tile, target,
-            max_split, exact_scan, winner, fb_list, fb_count, fallback_done(g, partial), sb);
-    else
-        k_rescore<false><<<blocks, 32 * kRescoreWarps, smem, st>>>(
-            g, ec, ri, di, bblk, qblk, lists, max_lists, counts, act, rkeep, lists_per_split, col_tile, target,
-            max_split, exact_scan, winner, fb_list, fb_count, fallback_done(g, partial), sb);
-    return cudaGetLastError();
+    return launch_dep(g.wide ? k_rescore<true> : k_rescore<false>, dim3(blocks), dim3(32 * kRescoreWarps), smem, st,
+                      g, ec, ri, di, bblk, qblk, lists, max_lists, counts, act, rkeep, lists_per_split, col_tile,
+                      target, max_split, exact_scan, winner, fb_list, fb_count, fallback_done(g, partial), sb);
 }
 
 int fallback_chunks(const Geometry &g) { return std::min(64, std::max(1, g.N / 1024)); }
@@ -833,24 +830,17 @@ cudaError_t launch_exact_scans(const Geometry &g, const RangeInfo *ri, const Dom
     const int nch = fallback_chunks(g);
     Partial *part = reinterpret_cast<Partial *>(partial);
     const SpanBufs sb = span_bufs(g, max_lists, span, fb_count + 2);
-    if (g.wide)
-        k_exact_scans<true><<<2 * n_sm, 256, 0, st>>>(g, ri, di, bblk, qblk, fb_list, fb_count, nch, part,
-                                                       fallback_done(g, partial), counts, dmap, col_tile, target,
-                                                       max_split, lists_per_split, max_lists, sb, winner);
-    else
-        k_exact_scans<false><<<2 * n_sm, 256, 0, st>>>(g, ri, di, bblk, qblk, fb_list, fb_count, nch, part,
-                                                        fallback_done(g, partial), counts, dmap, col_tile, target,
-                                                        max_split, lists_per_split, max_lists, sb, winner);
-    return cudaGetLastError();
+    return launch_dep(g.wide ? k_exact_scans<true> : k_exact_scans<false>, dim3(2 * n_sm), dim3(256), 0, st, g, ri,
+                      di, bblk, qblk, fb_list, (const int *)fb_count, nch, part, fallback_done(g, partial), counts,
+                      dmap, col_tile, target, max_split, lists_per_split, max_lists, sb, winner);
 }
 
 cudaError_t launch_finalize(const Geometry &g, const RangeInfo *ri, const DomainInfo *di,
                             const uint16_t *bblk, const uint16_t *qblk, const uint32_t *winner,
                             const int *err, fic_map *maps, cudaStream_t st)
 {
-    k_finalize<<<(g.R + kFinRanges - 1) / kFinRanges, 32 * kFinWarps, 0, st>>>(g, ri, di, bblk, qblk, winner, err,
-                                                                              maps);
-    return cudaGetLastError();
+    return launch_dep(k_finalize, dim3((g.R + kFinRanges - 1) / kFinRanges), dim3(32 * kFinWarps), 0, st, g, ri, di,
+                      bblk, qblk, winner, err, maps);
 }
 
 }  // namespace fic

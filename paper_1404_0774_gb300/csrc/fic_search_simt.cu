@@ -26,6 +26,7 @@ __global__ void __launch_bounds__(256) k_search_simt(Geometry g, EpiConst ec, co
                                                      ListEntry *lists, int max_split, int target, int *tbest,
                                                      float *dump)
 {
+    grid_dep_sync();
     extern __shared__ float smem[];
     float *As = smem;              // [KC][BM]
     float *Bs = As + KC * BM;      // [KC][BN]
@@ -174,9 +175,9 @@ cudaError_t launch_search_simt(const Geometry &g, const EpiConst &ec, const Rang
     cudaError_t e = cudaFuncSetAttribute(k_search_simt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((g.R + BM - 1) / BM, max_split);
-    k_search_simt<<<grid, 256, smem, st>>>(g, ec, ri, di, cb.dconst_c, cb.act, cb.dmap, cb.counts, dense, rs32, cb32,
-                                           lists, max_split, target, tbest, dump);
-    return cudaGetLastError();
+    return launch_dep(k_search_simt, grid, dim3(256), smem, st, g, ec, ri, di, (const float4 *)cb.dconst_c,
+                      (const int *)cb.act, (const int *)cb.dmap, (const int *)cb.counts, dense, rs32, cb32, lists,
+                      max_split, target, tbest, dump);
 }
 
 }  // namespace fic

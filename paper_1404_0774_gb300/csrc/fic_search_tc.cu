@@ -270,6 +270,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     __shared__ uint32_t tmem_base_s;
     __shared__ int abort_s;
 
+    grid_dep_sync();
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     // rows are the ranges kept for screening, columns the candidates of the
@@ -580,10 +581,9 @@ static cudaError_t launch_tc(const TcMaps &mp, dim3 grid, size_t smem, const Geo
 {
     cudaError_t e = cudaFuncSetAttribute(k_search_tc<NBLK, BW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_search_tc<NBLK, BW><<<grid, THREADS, smem, st>>>(mp, g, ec, ri, cb.dconst_c, cb.act, cb.dmap, cb.counts, dense,
-                                                       lists, max_split, target, tbest, dump, err, (uint32_t)smem,
-                                                       rpad, npad);
-    return cudaGetLastError();
+    return launch_dep(k_search_tc<NBLK, BW>, grid, dim3(THREADS), smem, st, mp, g, ec, ri,
+                      (const float4 *)cb.dconst_c, (const int *)cb.act, (const int *)cb.dmap, (const int *)cb.counts,
+                      dense, lists, max_split, target, tbest, dump, err, (uint32_t)smem, rpad, npad);
 }
 
 cudaError_t launch_search_tc(const Geometry &g, const EpiConst &ec, const RangeInfo *ri, const CompactBufs &cb,
