@@ -280,18 +280,24 @@ typedef struct {
 } fic_slice;
 
 /*
- * fic_encode_batch -- encode n slices of possibly different sizes with the
- *   same parameters: for each slice exactly what fic_encode computes.  The
- *   whole batch is one CUDA graph: the slices' encode pipelines spread over
- *   parallel branches (largest slices first, each to the least loaded
- *   branch), captured on the first call for a batch and replayed while the
- *   slice table, parameters and workspace stay the same (a different batch
- *   captures a new graph; one graph is kept per host thread).
+ * fic_encode_batch -- encode n slices (1 <= n <= 1024) of possibly different
+ *   sizes with the same parameters: for each slice exactly what fic_encode
+ *   computes.  The slices, sorted by size, are dealt to two halves that run
+ *   as two concurrent pipelines; in each, every stage of the encode is one
+ *   launch over its slices (the slice is the last grid dimension), and the
+ *   search is one persistent kernel that walks a queue of (slice, candidate
+ *   split, range tile) work items.  The launches form one CUDA graph, captured on the first
+ *   call for a batch (which also runs it) and replayed while the slice table,
+ *   parameters and workspace stay the same (a different batch captures a new
+ *   graph; one graph is kept per host thread).
  *   workspace  device, fic_batch_workspace_size() bytes, 256-byte aligned
- *              (required: the graph refers to it).
- *   Asynchronous on `stream`; the maps are ready when the stream is.  Bounded
- *   device waits that expire flag the affected maps FIC_MAP_ERROR.
- *   FIC_FLAG_PHASE_TIMING is rejected.
+ *              (required: the graph refers to it; it also holds the slice
+ *              table the kernels read, written by the first call).
+ *   Asynchronous on `stream` (the first call for a batch waits for its
+ *   stream once, after writing the slice table); the maps are ready when the
+ *   stream is.  Bounded device waits that expire flag the affected maps
+ *   FIC_MAP_ERROR.  FIC_FLAG_PHASE_TIMING is rejected; more than 1024 slices:
+ *   FIC_ERR_CAPACITY.
  */
 int fic_encode_batch(const fic_slice *slices, int n, const fic_params *p, void *workspace, size_t workspace_bytes,
                      void *stream);
@@ -300,7 +306,9 @@ int fic_batch_workspace_size(const fic_slice *slices, int n, const fic_params *p
 /* Completion time (ms) of each slice of the last graph replay of
  * fic_encode_batch on this host thread (the first call for a batch runs
  * eagerly and records none), from the start of the batch: events recorded
- * inside the graph; waits for them.  out has n entries. */
+ * inside the graph; waits for them.  Every stage covers every slice, so all
+ * slices complete with the batch: each entry is the batch's time.  out has n
+ * entries. */
 int fic_last_batch_slice_ms(float *out, int n);
 
 /*

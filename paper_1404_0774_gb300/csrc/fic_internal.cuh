@@ -42,17 +42,13 @@ __device__ __forceinline__ void grid_dep_sync()
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
-// Off while the batched encode builds its graph: there, branches that run
-// concurrently make better use of the SMs than early-scheduled CTAs that wait.
-inline thread_local bool g_dep_launch = true;
-
 template <typename... KArgs, typename... Args>
 inline cudaError_t launch_dep(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
                               Args &&...args)
 {
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = g_dep_launch ? 1 : 0;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = grid;
     cfg.blockDim = block;
@@ -488,6 +484,39 @@ struct CompactBufs {
     float4 *dconst_c;     // epilogue constants of the kept domains, in order
     int *dmap;            // kept domain j -> original domain id
 };
+// Device buffers of one encode (sub-buffers of its workspace).
+struct EncBufs {
+    RangeInfo *ri;
+    DomainInfo *di;
+    float4 *dconst;
+    uint16_t *bblk, *qblk;
+    float *rs32, *cb32;
+    __half *ra16, *cb16;
+    ListEntry *lists;
+    uint32_t *winner;
+    int *fb_list, *fb_count, *err, *tbest;
+    void *partial, *span;
+    CompactBufs cb;
+};
+
+// One slice of a batched encode: everything its kernels need, read by the
+// batched launches from a device array indexed by the slice (the last grid
+// dimension).  abase/bbase: first rows of the slice's operands in the
+// batch's shared operand buffers (tensor-core search).
+constexpr int kMaxBatch = 1024;  // slices in one batched encode
+
+struct SliceCtx {
+    Geometry g;
+    EpiConst ec;
+    EncBufs b;
+    const void *img;
+    fic_map *maps;
+    int n_split, n_lists, target;
+    int rb, db;  // range and domain blocks of the statistics and operand-row kernels
+    int abase, bbase;
+    int r_begin;  // ranges of the slices before this one (context order)
+};
+
 // Number of candidate-dimension splits actually used: enough CTAs for about
 // `target` (a few waves over the SMs) given the number of row tiles that have
 // ranges to screen, capped by the list layout (max_split) and by the tiles.
@@ -514,8 +543,23 @@ int search_tc_rows(int rows);  // range operand rows allocated (multiple of the 
 int search_tc_cols(int cols);  // candidate operand rows allocated (multiple of the tile)
 cudaError_t launch_search_tc(const Geometry &g, const EpiConst &ec, const RangeInfo *ri, const CompactBufs &cb,
                              int dense, const __half *ra16, const __half *cb16, ListEntry *lists, int max_split,
-                             int target, int *tbest, float *dump, int *err, cudaStream_t st);
+                             int target, int *tbest, float *dump, int *err, int *queue, cudaStream_t st);
 int search_simt_lists_per_split();
+// Batched encode of n slices (ctx: device array of their contexts), one
+// launch per stage over the slices (the per-slice stages: once per group of
+// equal slices).
+cudaError_t launch_stats_batch(const SliceCtx *ctx, int n, int blocks, int dense, int tc_split, cudaStream_t st);
+cudaError_t launch_compact_batch(const SliceCtx *ctx, int n, cudaStream_t st);
+cudaError_t launch_rows_batch(const SliceCtx *ctx, int n, int blocks, cudaStream_t st);
+cudaError_t launch_seed_batch(const SliceCtx *ctx, int n, int ranges, cudaStream_t st);
+cudaError_t launch_search_tc_batch(const Geometry &g, const __half *ra16, int arows, const __half *cb16, int brows,
+                                   const SliceCtx *ctx, int n, int dense, int *queue, cudaStream_t st);
+cudaError_t launch_search_simt_batch(const SliceCtx *ctx, int n, int max_ranges, int max_split, int dense,
+                                     cudaStream_t st);
+cudaError_t launch_rescore_batch(const SliceCtx *ctx, int n, int total_ranges, bool any_wide, bool any_narrow,
+                                 int max_m, int lists_per_split, int col_tile, int exact_scan, int n_sm,
+                                 cudaStream_t st);
+cudaError_t launch_finalize_batch(const SliceCtx *ctx, int n, int ranges, cudaStream_t st);
 cudaError_t launch_rescore(const Geometry &g, const EpiConst &ec, const RangeInfo *ri,
                            const DomainInfo *di, const uint16_t *bblk, const uint16_t *qblk,
                            const ListEntry *lists, int max_lists, const int *counts, const int *act,

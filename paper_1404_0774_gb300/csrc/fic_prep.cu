@@ -156,21 +156,41 @@ __device__ __forceinline__ void domain_stats(const Geometry &g, const void *img,
 
 // Statistics of every range (blocks [0, rb), a warp each) and every domain
 // (the blocks after), one launch.
+__device__ __forceinline__ void stats_block(const Geometry &g, const EpiConst &ec, const void *img, int dense,
+                                            int tc_split, const int *active, int rb, RangeInfo *ri, uint16_t *bblk,
+                                            int *tbest, DomainInfo *di, float4 *dconst, uint16_t *qblk, int *rkeep,
+                                            int *dkeep, int *zero4, int bx)
+{
+    if (bx == 0 && threadIdx.x < 4) zero4[threadIdx.x] = 0;  // exact-scan queue counters
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (bx < rb) {
+        const int r = bx * 8 + w;
+        if (r < g.R) range_stats(g, ec, img, dense, tc_split, active, r, lane, ri, bblk, tbest, rkeep);
+    } else {
+        const int d = (bx - rb) * 8 + w;
+        if (d < g.D) domain_stats(g, img, dense, d, lane, di, dconst, qblk, dkeep);
+    }
+}
+
 __global__ void __launch_bounds__(256) k_stats(Geometry g, EpiConst ec, const void *img, int dense, int tc_split,
                                                const int *active, int rb, RangeInfo *ri, uint16_t *bblk, int *tbest,
                                                DomainInfo *di, float4 *dconst, uint16_t *qblk, int *rkeep,
                                                int *dkeep, int *zero4)
 {
     grid_dep_sync();
-    if (blockIdx.x == 0 && threadIdx.x < 4) zero4[threadIdx.x] = 0;  // exact-scan queue counters
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    if ((int)blockIdx.x < rb) {
-        const int r = blockIdx.x * 8 + w;
-        if (r < g.R) range_stats(g, ec, img, dense, tc_split, active, r, lane, ri, bblk, tbest, rkeep);
-    } else {
-        const int d = (blockIdx.x - rb) * 8 + w;
-        if (d < g.D) domain_stats(g, img, dense, d, lane, di, dconst, qblk, dkeep);
-    }
+    stats_block(g, ec, img, dense, tc_split, active, rb, ri, bblk, tbest, di, dconst, qblk, rkeep, dkeep, zero4,
+                blockIdx.x);
+}
+
+// Batched: blockIdx.y = slice.
+__global__ void __launch_bounds__(256) k_stats_batch(const SliceCtx *__restrict__ ctx, int dense, int tc_split)
+{
+    grid_dep_sync();
+    const SliceCtx c = ctx[blockIdx.y];
+    if ((int)blockIdx.x >= c.rb + c.db) return;
+    const EncBufs &b = c.b;
+    stats_block(c.g, c.ec, c.img, dense, tc_split, nullptr, c.rb, b.ri, b.bblk, b.tbest, b.di, b.dconst, b.qblk,
+                b.cb.rkeep, b.cb.dkeep, b.fb_count, blockIdx.x);
 }
 
 // Stable compaction of the flagged items, block 0 over the ranges and block 1
@@ -180,13 +200,11 @@ __global__ void __launch_bounds__(256) k_stats(Geometry g, EpiConst ec, const vo
 // latency), warp ballots give per-(round, warp) counts, one warp scans those
 // 512 counts in item order, and every thread scatters its kept items.
 constexpr int kCompactRounds = 16;
-__global__ void __launch_bounds__(1024) k_compact(int nr, const int *rflag, int *ract, int *rcnt, int nd,
-                                                  const int *dflag, int *dact, int *dcnt)
+__device__ __forceinline__ void compact_block(int nr, const int *rflag, int *ract, int *rcnt, int nd,
+                                              const int *dflag, int *dact, int *dcnt, bool dom)
 {
-    grid_dep_sync();
     __shared__ int off_s[kCompactRounds * 32];
     __shared__ int base_s, first_s;
-    const bool dom = blockIdx.x == 1;
     const int n = dom ? nd : nr;
     const int *flag = dom ? dflag : rflag;
     int *list = dom ? dact : ract;
@@ -249,6 +267,21 @@ __global__ void __launch_bounds__(1024) k_compact(int nr, const int *rflag, int 
         cnt[0] = base_s;
         cnt[1] = first_s == 0x7fffffff ? -1 : first_s;
     }
+}
+
+__global__ void __launch_bounds__(1024) k_compact(int nr, const int *rflag, int *ract, int *rcnt, int nd,
+                                                  const int *dflag, int *dact, int *dcnt)
+{
+    grid_dep_sync();
+    compact_block(nr, rflag, ract, rcnt, nd, dflag, dact, dcnt, blockIdx.x == 1);
+}
+
+__global__ void __launch_bounds__(1024) k_compact_batch(const SliceCtx *__restrict__ ctx)
+{
+    grid_dep_sync();
+    const SliceCtx c = ctx[blockIdx.y];
+    const CompactBufs &cb = c.b.cb;
+    compact_block(c.g.R, cb.rkeep, cb.act, cb.counts + 0, c.g.D, cb.dkeep, cb.dact, cb.counts + 2, blockIdx.x == 1);
 }
 
 __device__ __forceinline__ uint32_t pack_h2(__half a, __half b)
@@ -354,22 +387,21 @@ __device__ __forceinline__ void domain_rows_warp(const Geometry &g, const Domain
 // kept domains (the blocks after, a warp per domain), one launch.  Domain
 // blocks first build the symmetry source table src_s[k][i] and the (row,
 // chunk) table of their 16-byte chunks.
-__global__ void __launch_bounds__(256, 4) k_rows(Geometry g, int rb, const RangeInfo *ri, const uint16_t *bblk,
-                                              const DomainInfo *di, const uint16_t *qblk, const float4 *dconst,
-                                              const int *act, const int *dact, const int *counts, float *rs32,
-                                              __half *ra16, float *cb32, __half *cb16, float4 *dconst_c, int *dmap)
+__device__ __forceinline__ void rows_block(const Geometry &g, int rb, const RangeInfo *ri, const uint16_t *bblk,
+                                           const DomainInfo *di, const uint16_t *qblk, const float4 *dconst,
+                                           const int *act, const int *dact, const int *counts, float *rs32,
+                                           __half *ra16, float *cb32, __half *cb16, float4 *dconst_c, int *dmap, int bx)
 {
-    grid_dep_sync();
     __shared__ uint8_t src_s[8][kMaxM];
     __shared__ uint16_t kc_s[8 * ((2 * kMaxM + 16) / 8)];
     __shared__ uint16_t hi_s[8][kMaxM], lo_s[8][kMaxM];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    if ((int)blockIdx.x < rb) {
-        const int j = blockIdx.x * 8 + w;
+    if (bx < rb) {
+        const int j = bx * 8 + w;
         if (j < counts[0]) range_row(g, ri, bblk, j, act[j], lane, rs32, ra16);
         return;
     }
-    const int j0 = (blockIdx.x - rb) * 8;
+    const int j0 = (bx - rb) * 8;
     if (j0 >= counts[2]) return;  // block-uniform
     for (int e = threadIdx.x; e < 8 * g.m; e += blockDim.x) {
         const int k = e >> (2 * g.ln), i = e & (g.m - 1);
@@ -382,6 +414,26 @@ __global__ void __launch_bounds__(256, 4) k_rows(Geometry g, int rb, const Range
     if (j < counts[2])
         domain_rows_warp(g, di, qblk, dconst, j, dact[j], lane, src_s, kc_s, hi_s[w], lo_s[w], cb32, cb16, dconst_c,
                          dmap);
+}
+
+__global__ void __launch_bounds__(256, 4) k_rows(Geometry g, int rb, const RangeInfo *ri, const uint16_t *bblk,
+                                              const DomainInfo *di, const uint16_t *qblk, const float4 *dconst,
+                                              const int *act, const int *dact, const int *counts, float *rs32,
+                                              __half *ra16, float *cb32, __half *cb16, float4 *dconst_c, int *dmap)
+{
+    grid_dep_sync();
+    rows_block(g, rb, ri, bblk, di, qblk, dconst, act, dact, counts, rs32, ra16, cb32, cb16, dconst_c, dmap,
+               blockIdx.x);
+}
+
+__global__ void __launch_bounds__(256, 4) k_rows_batch(const SliceCtx *__restrict__ ctx)
+{
+    grid_dep_sync();
+    const SliceCtx c = ctx[blockIdx.y];
+    if ((int)blockIdx.x >= c.rb + c.db) return;
+    const EncBufs &b = c.b;
+    rows_block(c.g, c.rb, b.ri, b.bblk, b.di, b.qblk, b.dconst, b.cb.act, b.cb.dact, b.cb.counts, b.rs32, b.ra16,
+               b.cb32, b.cb16, b.cb.dconst_c, b.cb.dmap, blockIdx.x);
 }
 
 cudaError_t launch_prep(const Geometry &g, const void *img, const EpiConst &ec, int dense, int tc_split,
@@ -409,18 +461,16 @@ cudaError_t launch_prep(const Geometry &g, const void *img, const EpiConst &ec, 
 // not next to a rounding boundary, offset not clamped) are published: each is
 // within the screening allowance of a real candidate's residual, which is all
 // the search's insertion window needs.
-__global__ void __launch_bounds__(256) k_seed(Geometry g, EpiConst ec, const RangeInfo *ri, const DomainInfo *di,
-                                              const float4 *dconst, const uint16_t *bblk, const uint16_t *qblk,
-                                              const int *rkeep, int *tbest)
+__device__ __forceinline__ void seed_block(const Geometry &g, const EpiConst &ec, const RangeInfo *ri,
+                                           const DomainInfo *di, const float4 *dconst, const uint16_t *bblk,
+                                           const uint16_t *qblk, const int *rkeep, int *tbest, int r)
 {
-    grid_dep_sync();
     // q2_s[p][slot]: contracted-domain pixels 2p, 2p+1 of the slot's domain
     // (lanes read consecutive words); bk_s[k][j]: the range pixel that S_k
     // places over domain pixel j, so X(d, k) = sum_j q_d[j] * bk_s[k][j]
     __shared__ uint32_t q2_s[kMaxM / 2][32];
     __shared__ __align__(8) int bk_s[8][kMaxM];
     __shared__ int d_s[32];
-    const int r = blockIdx.x;
     if (!rkeep[r]) return;  // block-uniform: a range that is not screened
     const RangeInfo rin = ri[r];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -488,11 +538,50 @@ __global__ void __launch_bounds__(256) k_seed(Geometry g, EpiConst ec, const Ran
     atomicMin(tbest + r, f2ord(epi_key(Xt, -0.0f, c, re.zb, c4, ec)));
 }
 
+__global__ void __launch_bounds__(256) k_seed(Geometry g, EpiConst ec, const RangeInfo *ri, const DomainInfo *di,
+                                              const float4 *dconst, const uint16_t *bblk, const uint16_t *qblk,
+                                              const int *rkeep, int *tbest)
+{
+    grid_dep_sync();
+    seed_block(g, ec, ri, di, dconst, bblk, qblk, rkeep, tbest, blockIdx.x);
+}
+
+__global__ void __launch_bounds__(256) k_seed_batch(const SliceCtx *__restrict__ ctx)
+{
+    grid_dep_sync();
+    const SliceCtx c = ctx[blockIdx.y];
+    if ((int)blockIdx.x >= c.g.R) return;
+    const EncBufs &b = c.b;
+    seed_block(c.g, c.ec, b.ri, b.di, b.dconst, b.bblk, b.qblk, b.cb.rkeep, b.tbest, blockIdx.x);
+}
+
 cudaError_t launch_seed(const Geometry &g, const EpiConst &ec, const RangeInfo *ri, const DomainInfo *di,
                         const float4 *dconst, const uint16_t *bblk, const uint16_t *qblk, const int *rkeep,
                         int *tbest, cudaStream_t st)
 {
     return launch_dep(k_seed, dim3(g.R), dim3(256), 0, st, g, ec, ri, di, dconst, bblk, qblk, rkeep, tbest);
+}
+
+// Batched prep stages of n slices (ctx: device array; blocks / ranges: the
+// largest slice's, so a group of equal slices wastes no blocks).
+cudaError_t launch_stats_batch(const SliceCtx *ctx, int n, int blocks, int dense, int tc_split, cudaStream_t st)
+{
+    return launch_dep(k_stats_batch, dim3(blocks, n), dim3(256), 0, st, ctx, dense, tc_split);
+}
+
+cudaError_t launch_compact_batch(const SliceCtx *ctx, int n, cudaStream_t st)
+{
+    return launch_dep(k_compact_batch, dim3(2, n), dim3(1024), 0, st, ctx);
+}
+
+cudaError_t launch_rows_batch(const SliceCtx *ctx, int n, int blocks, cudaStream_t st)
+{
+    return launch_dep(k_rows_batch, dim3(blocks, n), dim3(256), 0, st, ctx);
+}
+
+cudaError_t launch_seed_batch(const SliceCtx *ctx, int n, int ranges, cudaStream_t st)
+{
+    return launch_dep(k_seed_batch, dim3(ranges, n), dim3(256), 0, st, ctx);
 }
 
 }  // namespace fic

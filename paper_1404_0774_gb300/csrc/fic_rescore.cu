@@ -275,7 +275,7 @@ struct SpanBufs {
     int *pending;    // [R]
 };
 
-SpanBufs span_bufs(const Geometry &g, int max_lists, void *ws, int *count)
+__host__ __device__ SpanBufs span_bufs(const Geometry &g, int max_lists, void *ws, int *count)
 {
     SpanBufs b;
     char *p = static_cast<char *>(ws);
@@ -293,6 +293,14 @@ SpanBufs span_bufs(const Geometry &g, int max_lists, void *ws, int *count)
 size_t span_bytes(const Geometry &g, int max_lists)
 {
     return (sizeof(Partial) + sizeof(int)) * (size_t)g.R * max_lists + (sizeof(Partial) + sizeof(int)) * (size_t)g.R;
+}
+
+__host__ __device__ inline int fallback_chunks(const Geometry &g) { return min(64, max(1, g.N / 1024)); }
+
+// Partial results [R][chunks], then one completion counter per slot.
+__host__ __device__ inline int *fallback_done(const Geometry &g, void *partial)
+{
+    return reinterpret_cast<int *>(reinterpret_cast<Partial *>(partial) + (size_t)g.R * fallback_chunks(g));
 }
 
 __device__ __forceinline__ unsigned long long hi64(unsigned long long) { return 0ull; }
@@ -486,14 +494,14 @@ __device__ __forceinline__ void rescore_range(const Geometry &g, const EpiConst 
 // num = 0 for every candidate, so s = 0, one offset and one residual for
 // all, and the first candidate wins (Algorithm 2).
 template <bool Wide>
-__global__ void __launch_bounds__(32 * kRescoreWarps, 4)
-    k_rescore(Geometry g, EpiConst ec, const RangeInfo *ri, const DomainInfo *di, const uint16_t *bblk,
-              const uint16_t *qblk, const ListEntry *lists, int max_lists, const int *counts, const int *act,
-              const int *rkeep, int lists_per_split, int col_tile, int target, int max_split, int exact_scan,
-              uint32_t *winner, int *fb_list, int *fb_count, int *fb_done, SpanBufs sb)
+__device__ __forceinline__ void rescore_blocks(const Geometry &g, const EpiConst &ec, const RangeInfo *ri,
+                                               const DomainInfo *di, const uint16_t *bblk, const uint16_t *qblk,
+                                               const ListEntry *lists, int max_lists, const int *counts,
+                                               const int *act, const int *rkeep, int lists_per_split, int col_tile,
+                                               int target, int max_split, int exact_scan, uint32_t *winner,
+                                               int *fb_list, int *fb_count, int *fb_done, const SpanBufs &sb)
 {
     extern __shared__ int bk_all[];  // [warps][8][m+1]
-    grid_dep_sync();
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < g.R; r += gridDim.x * blockDim.x) {
         if (!rkeep[r]) winner[r] = 0;
         fb_done[r] = 0;  // completion counters of the exact fallback
@@ -503,6 +511,56 @@ __global__ void __launch_bounds__(32 * kRescoreWarps, 4)
     for (int j = blockIdx.x * kRescoreWarps + (threadIdx.x >> 5); j < nkept; j += gridDim.x * kRescoreWarps)
         rescore_range<Wide>(g, ec, ri, di, bblk, qblk, lists, max_lists, counts, lists_per_split, col_tile, target,
                             max_split, exact_scan, winner, fb_list, fb_count, act[j], bk, sb);
+}
+
+template <bool Wide>
+__global__ void __launch_bounds__(32 * kRescoreWarps, 4)
+    k_rescore(Geometry g, EpiConst ec, const RangeInfo *ri, const DomainInfo *di, const uint16_t *bblk,
+              const uint16_t *qblk, const ListEntry *lists, int max_lists, const int *counts, const int *act,
+              const int *rkeep, int lists_per_split, int col_tile, int target, int max_split, int exact_scan,
+              uint32_t *winner, int *fb_list, int *fb_count, int *fb_done, SpanBufs sb)
+{
+    grid_dep_sync();
+    rescore_blocks<Wide>(g, ec, ri, di, bblk, qblk, lists, max_lists, counts, act, rkeep, lists_per_split, col_tile,
+                         target, max_split, exact_scan, winner, fb_list, fb_count, fb_done, sb);
+}
+
+// Batched: one grid of persistent blocks over the ranges of all slices (in
+// context order, ctx[s].r_begin the first); warp w takes every nw-th range,
+// so the work of every slice is spread over all warps at once.
+template <bool Wide>
+__global__ void __launch_bounds__(32 * kRescoreWarps, 4)
+    k_rescore_batch(const SliceCtx *__restrict__ ctx, int n, int total, int lists_per_split, int col_tile,
+                    int exact_scan)
+{
+    extern __shared__ int bk_all[];  // [warps][8][m+1]
+    grid_dep_sync();
+    // ranges that are not screened: candidate 0 wins; exact-scan completion counters
+    {
+        const int nth = gridDim.x * blockDim.x;
+        int s = 0;
+        for (int gi = blockIdx.x * blockDim.x + threadIdx.x; gi < total; gi += nth) {
+            while (s + 1 < n && gi >= ctx[s + 1].r_begin) ++s;
+            const EncBufs &b = ctx[s].b;
+            const int r = gi - ctx[s].r_begin;
+            if (!b.cb.rkeep[r]) b.winner[r] = 0;
+            fallback_done(ctx[s].g, b.partial)[r] = 0;
+        }
+    }
+    const int nw = gridDim.x * kRescoreWarps;
+    int s = 0;
+    for (int gi = blockIdx.x * kRescoreWarps + (threadIdx.x >> 5); gi < total; gi += nw) {
+        while (s + 1 < n && gi >= ctx[s + 1].r_begin) ++s;
+        const SliceCtx &c = ctx[s];
+        if (c.g.wide != Wide) continue;
+        const int j = gi - c.r_begin;
+        const EncBufs &b = c.b;
+        if (j >= b.cb.counts[0]) continue;  // the screened ranges are the first counts[0]
+        int *bk = bk_all + (threadIdx.x >> 5) * 8 * (c.g.m + 1);
+        rescore_range<Wide>(c.g, c.ec, b.ri, b.di, b.bblk, b.qblk, b.lists, c.n_lists, b.cb.counts, lists_per_split,
+                            col_tile, c.target, c.n_split, exact_scan, b.winner, b.fb_list, b.fb_count,
+                            b.cb.act[j], bk, span_bufs(c.g, c.n_lists, b.span, b.fb_count + 2));
+    }
 }
 
 
@@ -516,13 +574,14 @@ __global__ void __launch_bounds__(32 * kRescoreWarps, 4)
 template <bool Wide>
 __device__ __forceinline__ void full_scans(const Geometry &g, const RangeInfo *ri, const DomainInfo *di,
                                            const uint16_t *bblk, const uint16_t *qblk, const int *fb_list,
-                                           const int *fb_count, int nch, Partial *part, int *done, uint32_t *winner)
+                                           const int *fb_count, int nch, Partial *part, int *done, uint32_t *winner,
+                                           int first, int stride)
 {
     __shared__ int b_s[kMaxM];
     __shared__ Partial w_s[8];
     __shared__ int last_s;
     const int count = *fb_count;
-    for (int item = blockIdx.x; item < count * nch; item += gridDim.x) {
+    for (int item = first; item < count * nch; item += stride) {
         const int slot = item / nch, ch = item - slot * nch;
         const int lo = (int)((long long)g.N * ch / nch);
         const int hi = (int)((long long)g.N * (ch + 1) / nch);
@@ -604,7 +663,8 @@ template <bool Wide>
 __device__ __forceinline__ void list_scans(const Geometry &g, const RangeInfo *ri, const DomainInfo *di,
                                            const uint16_t *bblk, const uint16_t *qblk, const int *counts,
                                            const int *dmap, int col_tile, int target, int max_split,
-                                           int lists_per_split, int max_lists, const SpanBufs &sb, uint32_t *winner)
+                                           int lists_per_split, int max_lists, const SpanBufs &sb, uint32_t *winner,
+                                           int first, int stride)
 {
     typedef typename Exact<Wide>::U U;
     __shared__ int b_s[kMaxM];
@@ -615,7 +675,7 @@ __device__ __forceinline__ void list_scans(const Geometry &g, const RangeInfo *r
     const int n_split = active_splits((counts[0] + 127) / 128, tiles, target, max_split);
     const int n_lists = n_split * lists_per_split;
     const int seg = col_tile / lists_per_split;
-    for (int item = blockIdx.x; item < count; item += gridDim.x) {
+    for (int item = first; item < count; item += stride) {
         const int code = sb.items[item];
         const int r = code >> 7, l = code & 127;
         const int sp = l / lists_per_split, part = l - sp * lists_per_split;
@@ -696,9 +756,66 @@ __global__ void __launch_bounds__(256) k_exact_scans(Geometry g, const RangeInfo
                                                      uint32_t *winner)
 {
     grid_dep_sync();
-    full_scans<Wide>(g, ri, di, bblk, qblk, fb_list, fb_count, nch, part, done, winner);
+    full_scans<Wide>(g, ri, di, bblk, qblk, fb_list, fb_count, nch, part, done, winner, blockIdx.x, gridDim.x);
     list_scans<Wide>(g, ri, di, bblk, qblk, counts, dmap, col_tile, target, max_split, lists_per_split, max_lists, sb,
-                     winner);
+                     winner, blockIdx.x, gridDim.x);
+}
+
+// Batched: the work items of all slices' queues form one sequence (the
+// queue lengths of every slice are read at once, then prefix-summed), spread
+// over the persistent blocks like a single queue.
+template <bool Wide>
+__global__ void __launch_bounds__(256) k_exact_scans_batch(const SliceCtx *__restrict__ ctx, int n,
+                                                           int lists_per_split, int col_tile)
+{
+    __shared__ int fi_s[kMaxBatch + 1], li_s[kMaxBatch + 1];  // item prefixes: full scans, list scans
+    grid_dep_sync();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const SliceCtx &c = ctx[i];
+        const bool mine = c.g.wide == Wide;
+        fi_s[i + 1] = mine ? c.b.fb_count[0] * fallback_chunks(c.g) : 0;
+        li_s[i + 1] = mine ? c.b.fb_count[2] : 0;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {  // inclusive scans, 32 slices at a time
+        const int lane = threadIdx.x;
+        int cf = 0, cl = 0;
+        for (int i0 = 0; i0 < n; i0 += 32) {
+            const int i = i0 + lane;
+            int vf = i < n ? fi_s[i + 1] : 0, vl = i < n ? li_s[i + 1] : 0;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int yf = __shfl_up_sync(0xffffffffu, vf, o), yl = __shfl_up_sync(0xffffffffu, vl, o);
+                if (lane >= o) {
+                    vf += yf;
+                    vl += yl;
+                }
+            }
+            if (i < n) {
+                fi_s[i + 1] = cf + vf;
+                li_s[i + 1] = cl + vl;
+            }
+            cf += __shfl_sync(0xffffffffu, vf, 31);
+            cl += __shfl_sync(0xffffffffu, vl, 31);
+        }
+        if (lane == 0) fi_s[0] = li_s[0] = 0;
+    }
+    __syncthreads();
+    const int b = blockIdx.x, G = gridDim.x;
+    for (int s = 0; s < n; ++s) {
+        const int nf = fi_s[s + 1] - fi_s[s], nl = li_s[s + 1] - li_s[s];
+        // this block's first item of the slice in the global sequence b, b + G, ...
+        const int ff = ((b - fi_s[s]) % G + G) % G, fl = ((b - li_s[s]) % G + G) % G;
+        if (ff >= nf && fl >= nl) continue;  // block-uniform
+        const SliceCtx c = ctx[s];
+        const EncBufs &e = c.b;
+        if (ff < nf)
+            full_scans<Wide>(c.g, e.ri, e.di, e.bblk, e.qblk, e.fb_list, e.fb_count, fallback_chunks(c.g),
+                             reinterpret_cast<Partial *>(e.partial), fallback_done(c.g, e.partial), e.winner, ff, G);
+        if (fl < nl)
+            list_scans<Wide>(c.g, e.ri, e.di, e.bblk, e.qblk, e.cb.counts, e.cb.dmap, col_tile, c.target, c.n_split,
+                             lists_per_split, c.n_lists, span_bufs(c.g, c.n_lists, e.span, e.fb_count + 2), e.winner,
+                             fl, G);
+    }
 }
 
 // FP64 codes of the winner (eq 9-12 in FP64, the operation order of the
@@ -711,17 +828,16 @@ __global__ void __launch_bounds__(256) k_exact_scans(Geometry g, const RangeInfo
 // pixel rows of the exact cross term.
 constexpr int kFinRanges = 32;
 constexpr int kFinWarps = 4;
-__global__ void __launch_bounds__(32 * kFinWarps) k_finalize(Geometry g, const RangeInfo *ri, const DomainInfo *di,
-                                                             const uint16_t *bblk, const uint16_t *qblk,
-                                                             const uint32_t *winner, const int *err, fic_map *maps)
+__device__ __forceinline__ void finalize_block(const Geometry &g, const RangeInfo *ri, const DomainInfo *di,
+                                               const uint16_t *bblk, const uint16_t *qblk, const uint32_t *winner,
+                                               const int *err, fic_map *maps, int bx)
 {
     __shared__ uint32_t b_s[kFinRanges][(kMaxM + 2) / 2];
     __shared__ uint32_t q_s[kFinRanges][(kMaxM + 2) / 2];
     __shared__ uint32_t w_s[kFinRanges];
     __shared__ long long x_s[kFinWarps][kFinRanges];
-    grid_dep_sync();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int r0 = blockIdx.x * kFinRanges;
+    const int r0 = bx * kFinRanges;
     const int nr = min(kFinRanges, g.R - r0);
     const int r = r0 + lane;
     const bool live = lane < nr;
@@ -789,7 +905,23 @@ __global__ void __launch_bounds__(32 * kFinWarps) k_finalize(Geometry g, const R
     maps[r] = mp;
 }
 
-int *fallback_done(const Geometry &g, void *partial);
+__global__ void __launch_bounds__(32 * kFinWarps) k_finalize(Geometry g, const RangeInfo *ri, const DomainInfo *di,
+                                                             const uint16_t *bblk, const uint16_t *qblk,
+                                                             const uint32_t *winner, const int *err, fic_map *maps)
+{
+    grid_dep_sync();
+    finalize_block(g, ri, di, bblk, qblk, winner, err, maps, blockIdx.x);
+}
+
+__global__ void __launch_bounds__(32 * kFinWarps) k_finalize_batch(const SliceCtx *__restrict__ ctx)
+{
+    grid_dep_sync();
+    const SliceCtx c = ctx[blockIdx.y];
+    if ((int)blockIdx.x * kFinRanges >= c.g.R) return;
+    const EncBufs &b = c.b;
+    finalize_block(c.g, b.ri, b.di, b.bblk, b.qblk, b.winner, b.err, c.maps, blockIdx.x);
+}
+
 
 cudaError_t launch_rescore(const Geometry &g, const EpiConst &ec, const RangeInfo *ri,
                            const DomainInfo *di, const uint16_t *bblk, const uint16_t *qblk,
@@ -808,7 +940,6 @@ cudaError_t launch_rescore(const Geometry &g, const EpiConst &ec, const RangeInf
                       target, max_split, exact_scan, winner, fb_list, fb_count, fallback_done(g, partial), sb);
 }
 
-int fallback_chunks(const Geometry &g) { return std::min(64, std::max(1, g.N / 1024)); }
 
 // Partial results [R][chunks], then one completion counter per slot.
 size_t fallback_partial_bytes(const Geometry &g)
@@ -816,10 +947,6 @@ size_t fallback_partial_bytes(const Geometry &g)
     return sizeof(Partial) * (size_t)g.R * fallback_chunks(g) + sizeof(int) * (size_t)g.R;
 }
 
-int *fallback_done(const Geometry &g, void *partial)
-{
-    return reinterpret_cast<int *>(reinterpret_cast<Partial *>(partial) + (size_t)g.R * fallback_chunks(g));
-}
 
 cudaError_t launch_exact_scans(const Geometry &g, const RangeInfo *ri, const DomainInfo *di, const uint16_t *bblk,
                                const uint16_t *qblk, const int *fb_list, int *fb_count, void *partial,
@@ -841,6 +968,36 @@ cudaError_t launch_finalize(const Geometry &g, const RangeInfo *ri, const Domain
 {
     return launch_dep(k_finalize, dim3((g.R + kFinRanges - 1) / kFinRanges), dim3(32 * kFinWarps), 0, st, g, ri, di,
                       bblk, qblk, winner, err, maps);
+}
+
+// Batched re-score and exact scans of n slices (max_m: the pixels per range,
+// common to all slices; total_ranges: the sum over the slices).
+cudaError_t launch_rescore_batch(const SliceCtx *ctx, int n, int total_ranges, bool any_wide, bool any_narrow,
+                                 int max_m, int lists_per_split, int col_tile, int exact_scan, int n_sm,
+                                 cudaStream_t st)
+{
+    const size_t smem = sizeof(int) * kRescoreWarps * 8 * (max_m + 1);
+    const int blocks = 4 * n_sm;  // resident at once (4 per SM at this size)
+    cudaError_t e;
+    if (any_narrow && (e = launch_dep(k_rescore_batch<false>, dim3(blocks), dim3(32 * kRescoreWarps), smem, st, ctx, n,
+                                      total_ranges, lists_per_split, col_tile, exact_scan)) != cudaSuccess)
+        return e;
+    if (any_wide && (e = launch_dep(k_rescore_batch<true>, dim3(blocks), dim3(32 * kRescoreWarps), smem, st, ctx, n,
+                                    total_ranges, lists_per_split, col_tile, exact_scan)) != cudaSuccess)
+        return e;
+    if (any_narrow && (e = launch_dep(k_exact_scans_batch<false>, dim3(2 * n_sm), dim3(256), 0, st, ctx, n,
+                                      lists_per_split, col_tile)) != cudaSuccess)
+        return e;
+    if (any_wide && (e = launch_dep(k_exact_scans_batch<true>, dim3(2 * n_sm), dim3(256), 0, st, ctx, n,
+                                    lists_per_split, col_tile)) != cudaSuccess)
+        return e;
+    return cudaSuccess;
+}
+
+cudaError_t launch_finalize_batch(const SliceCtx *ctx, int n, int ranges, cudaStream_t st)
+{
+    return launch_dep(k_finalize_batch, dim3((ranges + kFinRanges - 1) / kFinRanges, n), dim3(32 * kFinWarps), 0, st,
+                      ctx);
 }
 
 }  // namespace fic

@@ -19,14 +19,12 @@ constexpr int KC = 64;   // pixels per k chunk
 constexpr int XS = BN + 1;
 }  // namespace
 
-__global__ void __launch_bounds__(256) k_search_simt(Geometry g, EpiConst ec, const RangeInfo *ri,
-                                                     const DomainInfo *di, const float4 *dconst,
-                                                     const int *act, const int *dmap, const int *counts,
-                                                     int dense, const float *rs32, const float *cb32,
-                                                     ListEntry *lists, int max_split, int target, int *tbest,
-                                                     float *dump)
+__device__ __forceinline__ void search_simt_cta(const Geometry &g, const EpiConst &ec, const RangeInfo *ri,
+                                                const DomainInfo *di, const float4 *dconst, const int *act,
+                                                const int *dmap, const int *counts, int dense, const float *rs32,
+                                                const float *cb32, ListEntry *lists, int max_split, int target,
+                                                int *tbest, float *dump, int bx, int by)
 {
-    grid_dep_sync();
     extern __shared__ float smem[];
     float *As = smem;              // [KC][BM]
     float *Bs = As + KC * BM;      // [KC][BN]
@@ -39,8 +37,8 @@ __global__ void __launch_bounds__(256) k_search_simt(Geometry g, EpiConst ec, co
     // kept domains (both compacted, in original order)
     const int nrow = counts[0];
     const int ncol = 8 * counts[2];
-    const int r0 = blockIdx.x * BM;
-    const int split = blockIdx.y;
+    const int r0 = bx * BM;
+    const int split = by;
     // contiguous slice of the candidate dimension, in whole tiles
     const int tiles = (ncol + BN - 1) / BN;
     const int n_split = active_splits((nrow + BM - 1) / BM, tiles, target, max_split);
@@ -164,6 +162,29 @@ __global__ void __launch_bounds__(256) k_search_simt(Geometry g, EpiConst ec, co
     }
 }
 
+__global__ void __launch_bounds__(256) k_search_simt(Geometry g, EpiConst ec, const RangeInfo *ri,
+                                                     const DomainInfo *di, const float4 *dconst,
+                                                     const int *act, const int *dmap, const int *counts,
+                                                     int dense, const float *rs32, const float *cb32,
+                                                     ListEntry *lists, int max_split, int target, int *tbest,
+                                                     float *dump)
+{
+    grid_dep_sync();
+    search_simt_cta(g, ec, ri, di, dconst, act, dmap, counts, dense, rs32, cb32, lists, max_split, target, tbest, dump,
+                    blockIdx.x, blockIdx.y);
+}
+
+// Batched: blockIdx.z = slice.
+__global__ void __launch_bounds__(256) k_search_simt_batch(const SliceCtx *__restrict__ ctx, int dense)
+{
+    grid_dep_sync();
+    const SliceCtx c = ctx[blockIdx.z];
+    if ((int)blockIdx.y >= c.n_split || (int)blockIdx.x * BM >= c.g.R) return;  // CTA-uniform
+    const EncBufs &b = c.b;
+    search_simt_cta(c.g, c.ec, b.ri, b.di, b.cb.dconst_c, b.cb.act, b.cb.dmap, b.cb.counts, dense, b.rs32, b.cb32,
+                    b.lists, c.n_split, c.target, b.tbest, nullptr, blockIdx.x, blockIdx.y);
+}
+
 int search_simt_lists_per_split() { return 2; }
 
 cudaError_t launch_search_simt(const Geometry &g, const EpiConst &ec, const RangeInfo *ri,
@@ -178,6 +199,16 @@ cudaError_t launch_search_simt(const Geometry &g, const EpiConst &ec, const Rang
     return launch_dep(k_search_simt, grid, dim3(256), smem, st, g, ec, ri, di, (const float4 *)cb.dconst_c,
                       (const int *)cb.act, (const int *)cb.dmap, (const int *)cb.counts, dense, rs32, cb32, lists,
                       max_split, target, tbest, dump);
+}
+
+cudaError_t launch_search_simt_batch(const SliceCtx *ctx, int n, int max_ranges, int max_split, int dense,
+                                     cudaStream_t st)
+{
+    const size_t smem = sizeof(float) * (KC * BM + KC * BN + BM * XS);
+    cudaError_t e = cudaFuncSetAttribute(k_search_simt_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return launch_dep(k_search_simt_batch, dim3((max_ranges + BM - 1) / BM, max_split, n), dim3(256), smem, st, ctx,
+                      dense);
 }
 
 }  // namespace fic

@@ -233,13 +233,49 @@ struct TcMaps {
 
 // NBLK: number of pixel K blocks (1 for 8-bit, 2 for 12-bit); BW: their width.
 // dump != nullptr: write the raw accumulators Xt[r][c] instead of screening.
-template <int NBLK, int BW>
-__global__ void __launch_bounds__(THREADS, 1)
-    k_search_tc(const __grid_constant__ TcMaps maps, Geometry g, EpiConst ec, const RangeInfo *ri,
-                const float4 *dconst, const int *act, const int *dmap, const int *counts, int dense,
-                ListEntry *lists, int max_split, int target, int *tbest, float *dump, int *err,
-                uint32_t smem_bytes, int rpad, int npad)
+constexpr int kItemQ = 4;  // work items handed from the TMA warp to the other roles
+
+// Work item of the persistent search: row tile `r0` of slice `s` against the
+// candidate tiles [t_begin, t_end) of split `split`.
+struct TcItem {
+    int s, r0, split, t_begin, t_end;
+};
+
+// Work item `item` (ip_s: per-slice prefix of the items, ns_s / rt_s: active
+// splits / row tiles per slice).  Items are numbered slice by slice, split
+// major: the row tiles of a split run side by side, and later splits start
+// from the best keys the earlier ones shared.
+__device__ __forceinline__ TcItem tc_item(const SliceCtx *ctx, const int *ip_s, const int *ns_s, const int *rt_s,
+                                          int n, int item)
 {
+    int lo = 0, hi = n - 1;  // the last slice with ip_s[s] <= item
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (ip_s[mid] <= item) lo = mid;
+        else hi = mid - 1;
+    }
+    TcItem it;
+    it.s = lo;
+    const int local = item - ip_s[lo], ns = ns_s[lo], nrt = rt_s[lo];
+    it.split = local / nrt;
+    it.r0 = (local - it.split * nrt) * BM;
+    const int ncol = 8 * ctx[lo].b.cb.counts[2];
+    const int tiles = (ncol + BN - 1) / BN;
+    it.t_begin = (int)((long long)tiles * it.split / ns);
+    it.t_end = (int)((long long)tiles * (it.split + 1) / ns);
+    return it;
+}
+
+// Persistent tensor-core search over the work items of n slices (n = 1: a
+// single encode); every role (TMA producer, MMA issuer, epilogue warps) walks
+// the same item sequence, so the pipelines run on across item boundaries.
+template <int NBLK, int BW, bool BATCH>
+__device__ __forceinline__ void search_tc_run(const TcMaps &maps, const SliceCtx &one, const SliceCtx *many, int n,
+                                              int dense, float *dump, uint32_t smem_bytes, int *queue)
+{
+    // a single search reads its context from the kernel parameters (constant
+    // bank operands in the epilogue's inner loop)
+    const SliceCtx *ctx = BATCH ? many : &one;
     // BW: K elements per copy of the pixels (64: 128B-swizzled blocks, n = 8;
     // 16: 32B-swizzled blocks, n = 4); KPB MMAs of K = 16 per block
     constexpr int KPB = BW / 16;
@@ -266,48 +302,75 @@ __global__ void __launch_bounds__(THREADS, 1)
     constexpr int ET = 32 * EPI_WARPS;                                // epilogue threads
     float *xsm = reinterpret_cast<float *>(sB + STAGES * B_BYTES);  // [32][ET] cross terms (rare pass)
     float4 *dcs = reinterpret_cast<float4 *>(xsm + 32 * ET);        // [EPI_WARPS][DC_WARP] domain constants
-    __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], a_bar, tfull_bar[NACC], tempty_bar[NACC];
+    __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], a_full, a_empty, tfull_bar[NACC],
+        tempty_bar[NACC];
     __shared__ uint32_t tmem_base_s;
     __shared__ int abort_s;
+    __shared__ int ip_s[kMaxBatch + 1], ns_s[kMaxBatch], rt_s[kMaxBatch];
+    __shared__ int item_q[kItemQ];
+    __shared__ __align__(8) uint64_t q_full[kItemQ], q_empty[kItemQ];
 
-    grid_dep_sync();
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
-    // rows are the ranges kept for screening, columns the candidates of the
-    // kept domains (both compacted, in original order)
-    const int nrow = counts[0];
-    const int ncol = 8 * counts[2];
-    const int r0 = blockIdx.x * BM;
-    const int split = blockIdx.y;
-    const int tiles = (ncol + BN - 1) / BN;
-    const int n_split = active_splits((nrow + BM - 1) / BM, tiles, target, max_split);
-    if (r0 >= nrow || split >= n_split) return;  // CTA-uniform: nothing to screen
-    const int t_begin = (int)((long long)tiles * split / n_split);
-    const int t_end = (int)((long long)tiles * (split + 1) / n_split);
-    const int ntile = t_end - t_begin;
+    int *err0 = ctx[0].b.err;
+
+    // items per slice: row tiles of the kept ranges x active candidate
+    // splits (rows are the ranges kept for screening, columns the candidates
+    // of the kept domains, both compacted in original order)
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const SliceCtx &c = ctx[i];
+        const int nrow = c.b.cb.counts[0], ncol = 8 * c.b.cb.counts[2];
+        const int rt = (nrow + BM - 1) / BM, tiles = (ncol + BN - 1) / BN;
+        const int ns = rt > 0 && tiles > 0 ? active_splits(rt, tiles, c.target, c.n_split) : 0;
+        ns_s[i] = ns;
+        rt_s[i] = rt;
+        ip_s[i + 1] = rt * ns;
+    }
+    __syncthreads();
+    if (warp == 0) {  // inclusive scan of the item counts, 32 slices at a time
+        int carry = 0;
+        for (int i0 = 0; i0 < n; i0 += 32) {
+            const int i = i0 + lane;
+            int v = i < n ? ip_s[i + 1] : 0;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, v, o);
+                if (lane >= o) v += y;
+            }
+            if (i < n) ip_s[i + 1] = carry + v;
+            carry += __shfl_sync(0xffffffffu, v, 31);
+        }
+        if (lane == 0) ip_s[0] = 0;
+    }
 
     if (threadIdx.x == 0) {
-        // self-checks: every TMA box and MMA operand must lie inside this CTA's
-        // dynamic shared memory, and every box inside the padded operands
+        // self-check: every TMA box and MMA operand lies inside this CTA's
+        // dynamic shared memory
         const uint32_t used = (uint32_t)(smem - smem_raw) + A_BYTES + STAGES * B_BYTES + 32 * ET * 4 +
                               EPI_WARPS * DC_WARP * (16 + 4);
         int bad = 0;
         if (used > smem_bytes) bad = 2;
-        if (r0 + BM > rpad || t_end * BN > npad) bad = 3;
         if (smem_u32(smem) & 1023u) bad = 4;
         abort_s = bad;
-        if (bad) atomicExch(err, bad);
+        if (bad) atomicExch(err0, bad);
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&full_bar[s], 1);
             mbar_init(&empty_bar[s], 1);
         }
-        mbar_init(&a_bar, 1);
+        mbar_init(&a_full, 1);
+        mbar_init(&a_empty, 1);
+        for (int q = 0; q < kItemQ; ++q) {
+            mbar_init(&q_full[q], 1);
+            mbar_init(&q_empty[q], 1 + EPI_WARPS);  // the MMA thread and every epilogue warp
+        }
         for (int a = 0; a < NACC; ++a) {
             mbar_init(&tfull_bar[a], 1);
             mbar_init(&tempty_bar[a], EPI_WARPS);  // one arrival per epilogue warp
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+    __syncthreads();
+    const int total = ip_s[n];
+    if ((int)blockIdx.x >= total) return;  // CTA-uniform: no work (nothing allocated yet)
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(&tmem_base_s)),
@@ -319,10 +382,10 @@ __global__ void __launch_bounds__(THREADS, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem_base = tmem_base_s;
-    // TMEM: lane field 0, columns [base, base + 256) within the 512 of the SM
+    // TMEM: lane field 0, columns [base, base + TMEM_COLS) within the 512 of the SM
     if (threadIdx.x == 0 && ((tmem_base >> 16) != 0 || (tmem_base & 0xFFFFu) + TMEM_COLS > 512)) {
         abort_s = 5;
-        atomicExch(err, 5);
+        atomicExch(err0, 5);
     }
     __syncthreads();
     const bool run = abort_s == 0;
@@ -332,29 +395,59 @@ __global__ void __launch_bounds__(THREADS, 1)
     } else if (warp == 0) {
         // ------------------------------------------------------ TMA producer
         if (lane == 0) {
-            int issued = 0;
-            mbar_expect_tx(&a_bar, A_BYTES);
+            uint32_t bseq = 0;  // B tiles issued by this CTA
+            int kitem = 0;      // items started
+            bool a_pending = false;
+            // items are taken from a queue shared by all CTAs (`queue`, a
+            // counter zeroed by the statistics kernel) and handed to the other
+            // roles in order
+            for (int k = 0;; ++k) {
+                const int slot = k % kItemQ;
+                if (!mbar_wait(&q_empty[slot], ((k / kItemQ) & 1) ^ 1, &abort_s, err0)) break;
+                int item = atomicAdd(queue, 1);
+                if (item >= total || *(volatile int *)&abort_s) item = -1;
+                item_q[slot] = item;
+                mbar_arrive(&q_full[slot]);
+                if (item < 0) break;
+                const TcItem w = tc_item(ctx, ip_s, ns_s, rt_s, n, item);
+                const SliceCtx &c = ctx[w.s];
+                int *err = c.b.err;
+                const int rpad = (c.g.R + BM - 1) / BM * BM, npad = (c.g.N + BN - 1) / BN * BN;
+                if (w.r0 + BM > rpad || w.t_end * BN > npad) {  // every box inside the slice's padded operands
+                    abort_s = 3;
+                    atomicExch(err, 3);
+                    break;
+                }
+                // the previous item's MMAs must be done with A
+                if (kitem > 0 && !mbar_wait(&a_empty, (kitem - 1) & 1, &abort_s, err)) break;
+                mbar_expect_tx(&a_full, A_BYTES);
 #pragma unroll
-            for (int b = 0; b < NBLK; ++b) tma_load_2d(sA + b * A_BLK, &maps.a128, BW * b, r0, &a_bar);
-            tma_load_2d(sA + NBLK * A_BLK, &maps.a32, BW * NBLK, r0, &a_bar);
-            for (int it = 0; it < ntile; ++it) {
-                const int s = it % STAGES;
-                if (!mbar_wait(&empty_bar[s], ((it / STAGES) & 1) ^ 1, &abort_s, err)) break;
-                uint8_t *dst = sB + s * B_BYTES;
-                const int y = (t_begin + it) * BN;
-                mbar_expect_tx(&full_bar[s], B_BYTES);
+                for (int b = 0; b < NBLK; ++b) tma_load_2d(sA + b * A_BLK, &maps.a128, BW * b, c.abase + w.r0, &a_full);
+                tma_load_2d(sA + NBLK * A_BLK, &maps.a32, BW * NBLK, c.abase + w.r0, &a_full);
+                a_pending = true;
+                ++kitem;
+                for (int t = w.t_begin; t < w.t_end; ++t, ++bseq) {
+                    const int s = bseq % STAGES;
+                    if (!mbar_wait(&empty_bar[s], ((bseq / STAGES) & 1) ^ 1, &abort_s, err)) break;
+                    uint8_t *dst = sB + s * B_BYTES;
+                    const int y = c.bbase + t * BN;
+                    mbar_expect_tx(&full_bar[s], B_BYTES);
 #pragma unroll
-                for (int b = 0; b < NBLK; ++b) tma_load_2d(dst + b * B_BLK, &maps.b128, BW * b, y, &full_bar[s]);
-                tma_load_2d(dst + NBLK * B_BLK, &maps.b32, BW * NBLK, y, &full_bar[s]);
-                issued = it + 1;
+                    for (int b = 0; b < NBLK; ++b) tma_load_2d(dst + b * B_BLK, &maps.b128, BW * b, y, &full_bar[s]);
+                    tma_load_2d(dst + NBLK * B_BLK, &maps.b32, BW * NBLK, y, &full_bar[s]);
+                }
             }
             // drain: every issued load must land before the CTA may exit
-            mbar_wait(&a_bar, 0, &abort_s, err);
-            for (int it = (issued > STAGES ? issued - STAGES : 0); it < issued; ++it) {
-                const int s = it % STAGES;
-                if (mbar_try_wait(&full_bar[s], (it / STAGES) & 1)) continue;
+            if (a_pending && !mbar_try_wait(&a_full, (kitem - 1) & 1)) {
                 const unsigned long long t0 = gtimer();
-                while (!mbar_try_wait(&full_bar[s], (it / STAGES) & 1) && gtimer() - t0 < kWaitNs) {
+                while (!mbar_try_wait(&a_full, (kitem - 1) & 1) && gtimer() - t0 < kWaitNs) {
+                }
+            }
+            for (uint32_t q = (bseq > STAGES ? bseq - STAGES : 0); q < bseq; ++q) {
+                const int s = q % STAGES;
+                if (mbar_try_wait(&full_bar[s], (q / STAGES) & 1)) continue;
+                const unsigned long long t0 = gtimer();
+                while (!mbar_try_wait(&full_bar[s], (q / STAGES) & 1) && gtimer() - t0 < kWaitNs) {
                 }
             }
         }
@@ -363,34 +456,48 @@ __global__ void __launch_bounds__(THREADS, 1)
         if (lane == 0) {
             const uint32_t a_base = smem_u32(sA);
             const uint32_t b_base0 = smem_u32(sB);
-            bool ok = mbar_wait(&a_bar, 0, &abort_s, err);
-            for (int it = 0; ok && it < ntile; ++it) {
-                const int s = it % STAGES;
-                const int acc = it % NACC;
-                if (!mbar_wait(&tempty_bar[acc], ((it / NACC) & 1) ^ 1, &abort_s, err)) break;
-                if (!mbar_wait(&full_bar[s], (it / STAGES) & 1, &abort_s, err)) break;
-                tc_fence_after();
-                const uint32_t b_base = b_base0 + s * B_BYTES;
-                const uint32_t d_tmem = tmem_base + acc * ACC_COLS;
+            uint32_t bseq = 0, aseq = 0;
+            int kitem = 0;
+            bool ok = true;
+            for (int k = 0; ok; ++k) {
+                const int slot = k % kItemQ;
+                if (!(ok = mbar_wait(&q_full[slot], (k / kItemQ) & 1, &abort_s, err0))) break;
+                const int item = item_q[slot];
+                mbar_arrive(&q_empty[slot]);
+                if (item < 0) break;
+                const TcItem w = tc_item(ctx, ip_s, ns_s, rt_s, n, item);
+                int *err = ctx[w.s].b.err;
+                if (!(ok = mbar_wait(&a_full, kitem & 1, &abort_s, err))) break;
+                ++kitem;
+                for (int t = w.t_begin; t < w.t_end; ++t, ++bseq, ++aseq) {
+                    const int s = bseq % STAGES;
+                    const int acc = aseq % NACC;
+                    if (!(ok = mbar_wait(&tempty_bar[acc], ((aseq / NACC) & 1) ^ 1, &abort_s, err))) break;
+                    if (!(ok = mbar_wait(&full_bar[s], (bseq / STAGES) & 1, &abort_s, err))) break;
+                    tc_fence_after();
+                    const uint32_t b_base = b_base0 + s * B_BYTES;
+                    const uint32_t d_tmem = tmem_base + acc * ACC_COLS;
 #pragma unroll
-                for (int k = 0; k < KSTEPS; ++k) {
-                    if (PARTS == 2 && k == NBLK * KPB) break;  // the correction is applied in the epilogue
-                    uint64_t ad, bd;
-                    const int blk = k / KPB, sub = k % KPB;
-                    if (k < NBLK * KPB) {
-                        ad = smem_desc(a_base + blk * A_BLK + sub * 32, SBO, LAYOUT);
-                        bd = smem_desc(b_base + blk * B_BLK + sub * 32, SBO, LAYOUT);
-                    } else {
-                        ad = smem_desc(a_base + NBLK * A_BLK, 256, 6);
-                        bd = smem_desc(b_base + NBLK * B_BLK, 256, 6);
+                    for (int k = 0; k < KSTEPS; ++k) {
+                        if (PARTS == 2 && k == NBLK * KPB) break;  // the correction is applied in the epilogue
+                        uint64_t ad, bd;
+                        const int blk = k / KPB, sub = k % KPB;
+                        if (k < NBLK * KPB) {
+                            ad = smem_desc(a_base + blk * A_BLK + sub * 32, SBO, LAYOUT);
+                            bd = smem_desc(b_base + blk * B_BLK + sub * 32, SBO, LAYOUT);
+                        } else {
+                            ad = smem_desc(a_base + NBLK * A_BLK, 256, 6);
+                            bd = smem_desc(b_base + NBLK * B_BLK, 256, 6);
+                        }
+                        if (PARTS == 2)  // block 0 (hi) -> columns [0, BN), block 1 (lo) -> [BN, 2 BN)
+                            umma_f16(d_tmem + blk * BN, ad, bd, IDESC, sub ? 1u : 0u);
+                        else
+                            umma_f16(d_tmem, ad, bd, IDESC, k > 0 ? 1u : 0u);
                     }
-                    if (PARTS == 2)  // block 0 (hi) -> columns [0, BN), block 1 (lo) -> [BN, 2 BN)
-                        umma_f16(d_tmem + blk * BN, ad, bd, IDESC, sub ? 1u : 0u);
-                    else
-                        umma_f16(d_tmem, ad, bd, IDESC, k > 0 ? 1u : 0u);
+                    umma_commit(&empty_bar[s]);    // smem stage free once these MMAs finish
+                    umma_commit(&tfull_bar[acc]);  // accumulator ready for the epilogue
                 }
-                umma_commit(&empty_bar[s]);      // smem stage free once these MMAs finish
-                umma_commit(&tfull_bar[acc]);    // accumulator ready for the epilogue
+                umma_commit(&a_empty);  // A free once the item's MMAs finish
             }
         }
     } else {
@@ -400,109 +507,135 @@ __global__ void __launch_bounds__(THREADS, 1)
         const int part = ew >> 2;             // which 32 columns of each tile
         const int row = quad * 32 + lane;
         const int et = ew * 32 + lane;        // staging column of this thread
-        const int jrow = r0 + row;            // search row
-        const bool live = jrow < nrow;
-        const int r = live ? act[jrow] : 0;   // range id
         float4 *wdc = dcs + ew * DC_WARP;
         int *wod = reinterpret_cast<int *>(dcs + EPI_WARPS * DC_WARP) + ew * DC_WARP;
-        RangeEpi re{};
-        if (live) re = range_epi(ri[r], ec);
-        const float er = (PARTS == 2 && live) ? (float)ri[r].e_r : 0.0f;  // centring correction factor
-        const bool scr = live && (dense || !re.shadow);
-        ListState L;
-        list_init(L);
         const uint32_t lane_addr = tmem_base + ((uint32_t)(quad * 32) << 16) + part * EPI_COLS;
-        // prefetch for the first tile: its 4 domains and the shared best key
-        float4 dc_next = make_float4(0.f, 0.f, 0.f, 0.f);
-        int od_next = 0;
-        int tb_next = 0x7f800000;
-        if (ntile > 0) {
-            const int jd = ((t_begin * BN + part * EPI_COLS) >> 3) + lane;
-            if (lane < DC_WARP && jd < counts[2]) {
-                dc_next = __ldg(dconst + jd);
-                od_next = __ldg(dmap + jd);
-            }
-            if (scr && !dump) tb_next = __ldcg(tbest + r);
-        }
-        for (int it = 0; it < ntile; ++it) {
-            const int acc = it % NACC;
-            const int n0 = (t_begin + it) * BN + part * EPI_COLS;
-            if (lane < DC_WARP) {
-                wdc[lane] = dc_next;
-                wod[lane] = od_next;
-            }
-            if (scr && !dump) {
-                const float Tg = ord2f(tb_next);  // best key other CTAs found
-                list_adopt(L, Tg, re, ec);
-                L.Tpub = fminf(L.Tpub, Tg);
-            }
-            if (it + 1 < ntile) {  // prefetch for the next tile
-                const int jd = ((n0 + BN) >> 3) + lane;
-                if (lane < DC_WARP && jd < counts[2]) {
+        uint32_t aseq = 0;
+        bool ok = true;
+        for (int k = 0; ok; ++k) {
+            const int slot = k % kItemQ;
+            if (!(ok = __all_sync(0xffffffffu, mbar_wait(&q_full[slot], (k / kItemQ) & 1, &abort_s, err0)))) break;
+            const int item = item_q[slot];
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&q_empty[slot]);
+            if (item < 0) break;
+            const TcItem w = tc_item(ctx, ip_s, ns_s, rt_s, n, item);
+            const SliceCtx &c = BATCH ? many[w.s] : one;
+            const Geometry &g = c.g;
+            // a single search keeps reading the kernel parameters (constant-bank
+            // operands); a batch copies its slice's constants into registers
+            EpiConst ec_reg;
+            if (BATCH) ec_reg = c.ec;
+            const EpiConst &ec = BATCH ? ec_reg : c.ec;
+            const float4 *dconst = c.b.cb.dconst_c;
+            const int *dmap = c.b.cb.dmap;
+            int *err = c.b.err;
+            int *tbest = c.b.tbest;
+            const int nrow = c.b.cb.counts[0], ndom = c.b.cb.counts[2], ncol = 8 * ndom;
+            const int jrow = w.r0 + row;          // search row
+            const bool live = jrow < nrow;
+            const int r = live ? c.b.cb.act[jrow] : 0;  // range id
+            RangeEpi re{};
+            if (live) re = range_epi(c.b.ri[r], ec);
+            const float er = (PARTS == 2 && live) ? (float)c.b.ri[r].e_r : 0.0f;  // centring correction factor
+            const bool scr = live && (dense || !re.shadow);
+            ListState L;
+            list_init(L);
+            const int ntile = w.t_end - w.t_begin;
+            // prefetch for the first tile: its 4 domains and the shared best key
+            float4 dc_next = make_float4(0.f, 0.f, 0.f, 0.f);
+            int od_next = 0;
+            int tb_next = 0x7f800000;
+            if (ntile > 0) {
+                const int jd = ((w.t_begin * BN + part * EPI_COLS) >> 3) + lane;
+                if (lane < DC_WARP && jd < ndom) {
                     dc_next = __ldg(dconst + jd);
                     od_next = __ldg(dmap + jd);
                 }
                 if (scr && !dump) tb_next = __ldcg(tbest + r);
             }
-            __syncwarp();
-            // warp-uniform decision: tcgen05.ld below is .sync.aligned
-            if (!__all_sync(0xffffffffu, mbar_wait(&tfull_bar[acc], (it / NACC) & 1, &abort_s, err))) break;
-            tc_fence_after();
-            const uint32_t taddr = lane_addr + acc * ACC_COLS;
-            const int nv = min(32, ncol - n0);  // may be <= 0 in the last tile
-            int od[4];
-            float4 dc[4];
+            for (int it = 0; it < ntile; ++it, ++aseq) {
+                const int acc = aseq % NACC;
+                const int n0 = (w.t_begin + it) * BN + part * EPI_COLS;
+                if (lane < DC_WARP) {
+                    wdc[lane] = dc_next;
+                    wod[lane] = od_next;
+                }
+                if (scr && !dump) {
+                    const float Tg = ord2f(tb_next);  // best key other CTAs found
+                    list_adopt(L, Tg, re, ec);
+                    L.Tpub = fminf(L.Tpub, Tg);
+                }
+                if (it + 1 < ntile) {  // prefetch for the next tile
+                    const int jd = ((n0 + BN) >> 3) + lane;
+                    if (lane < DC_WARP && jd < ndom) {
+                        dc_next = __ldg(dconst + jd);
+                        od_next = __ldg(dmap + jd);
+                    }
+                    if (scr && !dump) tb_next = __ldcg(tbest + r);
+                }
+                __syncwarp();
+                // warp-uniform decision: tcgen05.ld below is .sync.aligned
+                if (!(ok = __all_sync(0xffffffffu, mbar_wait(&tfull_bar[acc], (aseq / NACC) & 1, &abort_s, err))))
+                    break;
+                tc_fence_after();
+                const uint32_t taddr = lane_addr + acc * ACC_COLS;
+                const int nv = min(32, ncol - n0);  // may be <= 0 in the last tile
+                int od[4];
+                float4 dc[4];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                od[q] = wod[q];
-                dc[q] = wdc[q];
-            }
-            float X[32];
-            {
-                uint32_t h[32], l[32];
-                tmem_ld32(taddr, h);
-                if (PARTS == 2) {
-                    tmem_ld32(taddr + BN, l);
-                    tmem_wait2(h, l);
+                for (int q = 0; q < 4; ++q) {
+                    od[q] = wod[q];
+                    dc[q] = wdc[q];
+                }
+                float X[32];
+                {
+                    uint32_t h[32], l[32];
+                    tmem_ld32(taddr, h);
+                    if (PARTS == 2) {
+                        tmem_ld32(taddr + BN, l);
+                        tmem_wait2(h, l);
 #pragma unroll
-                    for (int j = 0; j < 32; j += 2)
-                        upk2(add2(pk2(__uint_as_float(h[j]), __uint_as_float(h[j + 1])),
-                                  pk2(__uint_as_float(l[j]), __uint_as_float(l[j + 1]))), X[j], X[j + 1]);
+                        for (int j = 0; j < 32; j += 2)
+                            upk2(add2(pk2(__uint_as_float(h[j]), __uint_as_float(h[j + 1])),
+                                      pk2(__uint_as_float(l[j]), __uint_as_float(l[j + 1]))), X[j], X[j + 1]);
+                    } else {
+                        tmem_wait(h);
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) X[j] = __uint_as_float(h[j]);
+                    }
+                }
+                // the accumulator is in registers: release it to the MMA warp now,
+                // so that a slow warp holds up the tensor cores only by its load
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&tempty_bar[acc]);
+                if (dump) {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const float ca = PARTS == 2 ? epi_corr(er, pick4(dc, j >> 3).w, ec) : 0.0f;
+                        if (live && j < nv) dump[(size_t)r * g.N + od[j >> 3] * 8 + (j & 7)] = X[j] + ca;
+                    }
                 } else {
-                    tmem_wait(h);
+                    if (nv < 32) {
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) X[j] = __uint_as_float(h[j]);
+                        for (int j = 0; j < 32; ++j)
+                            if (j >= nv) X[j] = __int_as_float(0x7fc00000);  // NaN: never listed
+                    }
+                    const float thr = fminf(L.key[kListK - 1], L.tw);
+                    const float zp = L.has_zero ? kZeroPenalty : 0.0f;
+                    const uint32_t mask = scr && nv > 0
+                                              ? epi_keys32<true>(X, dc, re.zb, re.rho_lim, er, ec, thr, zp) & col_mask(nv)
+                                              : 0u;
+                    if (__any_sync(0xffffffffu, mask != 0u))
+                        rare_chunk(X, mask, od, dc, er, xsm + et, ET, re, ec, L, tbest + r);
                 }
             }
-            // the accumulator is in registers: release it to the MMA warp now,
-            // so that a slow warp holds up the tensor cores only by its load
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&tempty_bar[acc]);
-            if (dump) {
+            if (ok && scr && !dump) {
+                ListEntry *dst = c.b.lists + (((size_t)r * c.n_split + w.split) * LISTS + part) * kListK;
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const float ca = PARTS == 2 ? epi_corr(er, pick4(dc, j >> 3).w, ec) : 0.0f;
-                    if (live && j < nv) dump[(size_t)r * g.N + od[j >> 3] * 8 + (j & 7)] = X[j] + ca;
-                }
-            } else {
-                if (nv < 32) {
-#pragma unroll
-                    for (int j = 0; j < 32; ++j)
-                        if (j >= nv) X[j] = __int_as_float(0x7fc00000);  // NaN: never listed
-                }
-                const float thr = fminf(L.key[kListK - 1], L.tw);
-                const float zp = L.has_zero ? kZeroPenalty : 0.0f;
-                const uint32_t mask =
-                    scr && nv > 0 ? epi_keys32<true>(X, dc, re.zb, re.rho_lim, er, ec, thr, zp) & col_mask(nv) : 0u;
-                if (__any_sync(0xffffffffu, mask != 0u))
-                    rare_chunk(X, mask, od, dc, er, xsm + et, ET, re, ec, L, tbest + r);
+                for (int i = 0; i < kListK; ++i) dst[i] = ListEntry{L.key[i], L.idx[i]};
             }
-        }
-        if (scr && !dump) {
-            ListEntry *dst = lists + (((size_t)r * max_split + split) * LISTS + part) * kListK;
-#pragma unroll
-            for (int i = 0; i < kListK; ++i) dst[i] = ListEntry{L.key[i], L.idx[i]};
         }
     }
     tc_fence_before();
@@ -513,6 +646,18 @@ __global__ void __launch_bounds__(THREADS, 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS)
                      : "memory");
     }
+}
+
+// One search (one = its slice context, many = nullptr) or a batch of n
+// slices (many: device array) whose operands share the tensor maps' buffers
+// (rows from abase / bbase on); one CTA per SM, persistent.
+template <int NBLK, int BW, bool BATCH>
+__global__ void __launch_bounds__(THREADS, 1)
+    k_search_tc(const __grid_constant__ TcMaps maps, const __grid_constant__ SliceCtx one, const SliceCtx *many, int n,
+                int dense, float *dump, uint32_t smem_bytes, int *queue)
+{
+    grid_dep_sync();
+    search_tc_run<NBLK, BW, BATCH>(maps, one, many, n, dense, dump, smem_bytes, queue);
 }
 
 namespace {
@@ -574,44 +719,80 @@ int search_tc_rows(int rows) { return (rows + BM - 1) / BM * BM; }
 
 int search_tc_cols(int cols) { return (cols + BN - 1) / BN * BN; }
 
-template <int NBLK, int BW>
-static cudaError_t launch_tc(const TcMaps &mp, dim3 grid, size_t smem, const Geometry &g, const EpiConst &ec,
-                             const RangeInfo *ri, const CompactBufs &cb, int dense, ListEntry *lists, int max_split,
-                             int target, int *tbest, float *dump, int *err, int rpad, int npad, cudaStream_t st)
+static int n_sms()
 {
-    cudaError_t e = cudaFuncSetAttribute(k_search_tc<NBLK, BW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return 1;
+    return n > 0 ? n : 1;
+}
+
+template <int NBLK, int BW, bool BATCH>
+static cudaError_t launch_tc3(const TcMaps &mp, const SliceCtx &one, const SliceCtx *many, int n, int dense,
+                              float *dump, int *queue, size_t smem, cudaStream_t st)
+{
+    cudaError_t e =
+        cudaFuncSetAttribute(k_search_tc<NBLK, BW, BATCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    return launch_dep(k_search_tc<NBLK, BW>, grid, dim3(THREADS), smem, st, mp, g, ec, ri,
-                      (const float4 *)cb.dconst_c, (const int *)cb.act, (const int *)cb.dmap, (const int *)cb.counts,
-                      dense, lists, max_split, target, tbest, dump, err, (uint32_t)smem, rpad, npad);
+    return launch_dep(k_search_tc<NBLK, BW, BATCH>, dim3(n_sms()), dim3(THREADS), smem, st, mp, one, many, n, dense,
+                      dump, (uint32_t)smem, queue);
+}
+
+template <int NBLK, int BW>
+static cudaError_t launch_tc(const TcMaps &mp, const SliceCtx &one, const SliceCtx *many, int n, int dense, float *dump,
+                             int *queue, size_t smem, cudaStream_t st)
+{
+    return many ? launch_tc3<NBLK, BW, true>(mp, one, many, n, dense, dump, queue, smem, st)
+                : launch_tc3<NBLK, BW, false>(mp, one, many, n, dense, dump, queue, smem, st);
+}
+
+// Tensor maps over an operand pair (arows / brows rows of KP halves) and
+// the launch; g: the geometry of any of the slices (pixel and code layout).
+static cudaError_t launch_tc_any(const Geometry &g, const __half *ra16, int arows, const __half *cb16, int brows,
+                                 const SliceCtx &one, const SliceCtx *many, int n, int dense, float *dump,
+                                 int *queue, cudaStream_t st)
+{
+    if (!search_tc_supported(g) || n < 1 || n > kMaxBatch || !queue) return cudaErrorInvalidValue;
+    TcMaps mp;
+    const int nblk = g.split_hilo ? 2 : 1, bw = tc_block_width(g);
+    const CUtensorMapSwizzle sw = bw == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_32B;
+    if (!make_map(&mp.a128, ra16, arows, g.KP, bw, BM, sw) ||
+        !make_map(&mp.a32, ra16, arows, g.KP, 16, BM, CU_TENSOR_MAP_SWIZZLE_32B) ||
+        !make_map(&mp.b128, cb16, brows, g.KP, bw, BN, sw) ||
+        !make_map(&mp.b32, cb16, brows, g.KP, 16, BN, CU_TENSOR_MAP_SWIZZLE_32B))
+        return cudaErrorInvalidValue;
+    const size_t smem = search_tc_smem(g);
+    if (bw == 64)
+        return nblk == 2 ? launch_tc<2, 64>(mp, one, many, n, dense, dump, queue, smem, st)
+                         : launch_tc<1, 64>(mp, one, many, n, dense, dump, queue, smem, st);
+    return nblk == 2 ? launch_tc<2, 16>(mp, one, many, n, dense, dump, queue, smem, st)
+                     : launch_tc<1, 16>(mp, one, many, n, dense, dump, queue, smem, st);
 }
 
 cudaError_t launch_search_tc(const Geometry &g, const EpiConst &ec, const RangeInfo *ri, const CompactBufs &cb,
                              int dense, const __half *ra16, const __half *cb16, ListEntry *lists, int max_split,
-                             int target, int *tbest, float *dump, int *err, cudaStream_t st)
+                             int target, int *tbest, float *dump, int *err, int *queue, cudaStream_t st)
 {
-    if (!search_tc_supported(g)) return cudaErrorInvalidValue;
-    TcMaps mp;
-    const int nblk = g.split_hilo ? 2 : 1, bw = tc_block_width(g);
-    const CUtensorMapSwizzle sw = bw == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_32B;
-    // operand buffers hold whole boxes (rows padded with zeros to a multiple of 128)
-    const int rpad = search_tc_rows(g.R), npad = search_tc_cols(g.N);
-    if (!make_map(&mp.a128, ra16, rpad, g.KP, bw, BM, sw) ||
-        !make_map(&mp.a32, ra16, rpad, g.KP, 16, BM, CU_TENSOR_MAP_SWIZZLE_32B) ||
-        !make_map(&mp.b128, cb16, npad, g.KP, bw, BN, sw) ||
-        !make_map(&mp.b32, cb16, npad, g.KP, 16, BN, CU_TENSOR_MAP_SWIZZLE_32B))
-        return cudaErrorInvalidValue;
-    const size_t smem = search_tc_smem(g);
-    const dim3 grid((g.R + BM - 1) / BM, max_split);
-    if (bw == 64)
-        return nblk == 2 ? launch_tc<2, 64>(mp, grid, smem, g, ec, ri, cb, dense, lists, max_split, target, tbest, dump,
-                                            err, rpad, npad, st)
-                         : launch_tc<1, 64>(mp, grid, smem, g, ec, ri, cb, dense, lists, max_split, target, tbest, dump,
-                                            err, rpad, npad, st);
-    return nblk == 2 ? launch_tc<2, 16>(mp, grid, smem, g, ec, ri, cb, dense, lists, max_split, target, tbest, dump, err,
-                                        rpad, npad, st)
-                     : launch_tc<1, 16>(mp, grid, smem, g, ec, ri, cb, dense, lists, max_split, target, tbest, dump, err,
-                                        rpad, npad, st);
+    SliceCtx one = {};
+    one.g = g;
+    one.ec = ec;
+    one.b.ri = const_cast<RangeInfo *>(ri);
+    one.b.cb = cb;
+    one.b.lists = lists;
+    one.b.tbest = tbest;
+    one.b.err = err;
+    one.n_split = max_split;
+    one.target = target;
+    // operand buffers hold whole boxes (rows padded to the box heights)
+    return launch_tc_any(g, ra16, search_tc_rows(g.R), cb16, search_tc_cols(g.N), one, nullptr, 1, dense, dump, queue,
+                         st);
+}
+
+cudaError_t launch_search_tc_batch(const Geometry &g, const __half *ra16, int arows, const __half *cb16, int brows,
+                                   const SliceCtx *ctx, int n, int dense, int *queue, cudaStream_t st)
+{
+    const SliceCtx none = {};
+    return launch_tc_any(g, ra16, arows, cb16, brows, none, ctx, n, dense, nullptr, queue, st);
 }
 
 }  // namespace fic

@@ -72,3 +72,22 @@ def test_encode_rejects_bad_arguments_before_any_gpu_work(fic):
     assert lib.fic_encode(buf, 64, 64, 64, ctypes.byref(p), maps, 10, ctypes.byref(n), None, 0, None) == -4
     # pitch smaller than width
     assert lib.fic_encode(buf, 64, 64, 32, ctypes.byref(p), maps, 64, ctypes.byref(n), None, 0, None) == -1
+
+
+def test_batch_workspace_size_and_limits(fic):
+    """The batch plan is host arithmetic: sizes grow with the slices, more
+    than 1024 slices is a capacity error, phase timing is rejected."""
+    p = fic.params(range_size=8, domain_stride=4, bit_depth=12)
+
+    def table(sizes):
+        return (fic.fic_slice * len(sizes))(*[fic.fic_slice(None, s, s, s, None) for s in sizes])
+
+    size = ctypes.c_size_t()
+    lib = fic.lib()
+    assert lib.fic_batch_workspace_size(table([64]), 1, ctypes.byref(p), ctypes.byref(size)) == 0
+    one = size.value
+    assert lib.fic_batch_workspace_size(table([64, 128]), 2, ctypes.byref(p), ctypes.byref(size)) == 0
+    assert size.value > one
+    assert lib.fic_batch_workspace_size(table([64] * 1025), 1025, ctypes.byref(p), ctypes.byref(size)) == -4
+    pt = fic.params(range_size=8, domain_stride=4, bit_depth=12, flags=fic.FIC_FLAG_PHASE_TIMING)
+    assert lib.fic_batch_workspace_size(table([64]), 1, ctypes.byref(pt), ctypes.byref(size)) == -1
