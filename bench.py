@@ -296,7 +296,9 @@ def run_quadtree(args):
             "e2e": {"value": ws * args.steps * comps / e2e_t, "unit": "comparisons/s",
                     "h2d_bytes_per_step": N_PIX * N_PIX * 2, "d2h_bytes_per_step": int(n_leaves) * 56,
                     "timing": "host wall clock (the call waits for its stream)"},
-            "gpu_launches": None, "clocks": clocks, "roofline": None}
+            # per level the eight encode kernels and the split test; then the
+            # leaf count and the leaf gather
+            "gpu_launches": args.steps * (9 * len(per_level) + 2), "clocks": clocks, "roofline": None}
     if rank == 0:
         if ws == 1 and not args.no_cpu_baseline:
             import oracle
@@ -321,6 +323,19 @@ def run_quadtree(args):
 
 VOL_WORKLOAD = ("12-bit CT-like synthetic stack: 32 slices at 256x256, 32 at 384x384, 32 at 512x512; 8x8 ranges, "
                 "16x16 domains at stride 4, 8 symmetries; s 5-bit, o 7-bit; one batch (one CUDA graph) per step")
+
+
+def batch_launches(sizes):
+    """Kernel launches of one batched encode: the slices sorted by size are
+    dealt to two halves; per half the statistics, operand-row, seed and output
+    kernels run once per group of equal-sized slices, the compaction, search,
+    re-score and exact scans once."""
+    order = sorted(sizes, reverse=True)
+    total = 0
+    for half in (order[0::2], order[1::2]):
+        if half:
+            total += 4 * len(set(half)) + 4
+    return total
 
 
 def run_volume(args):
@@ -415,11 +430,13 @@ def run_volume(args):
                        "comparisons_per_s": ws_n * args.steps * comps / t_total,
                        "slice_completion_ms": {"p50": float(np.percentile(lat, 50)),
                                                "p99": float(np.percentile(lat, 99)), "max": float(lat.max()),
-                                               "note": "time from the start of the batch to each slice's maps"},
+                                               "note": "time from the start of the batch to each slice's maps "
+                                                       "(every stage covers all slices: they complete together)"},
                        "l2": "working set of the batch (several GB) is larger than L2"},
             "e2e": {"value": ws_n * args.steps * n_sl / e2e_t, "unit": "slices/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
-            "gpu_launches": None, "clocks": clocks, "roofline": None}
+            "gpu_launches": args.steps * batch_launches([a.shape[0] * a.shape[1] for a in stack]), "clocks": clocks,
+            "roofline": None}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws_n > 1:
@@ -487,7 +504,9 @@ def run_refine(args):
             "config": {"workload": REF_WORKLOAD, "decode_iters": T, "adam_lr": lr,
                        "psnr_collage_optimal_db": before, "psnr_refined_db": after, "psnr_gain_db": after - before,
                        "loss_first": float(L[0]), "loss_last": float(L[-1])},
-            "e2e": None, "gpu_launches": None, "clocks": clocks, "roofline": None}
+            # per step: fill + T forward iterations, 2 loss kernels, T/2 recomputed
+            # iterates, T per-range gradients, 3 (T - 1) adjoint kernels, Adam
+            "e2e": None, "gpu_launches": steps * (5 * T + T // 2 + 1), "clocks": clocks, "roofline": None}
     if rank == 0:
         print(json.dumps(line), flush=True)
 

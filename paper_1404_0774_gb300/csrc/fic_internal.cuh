@@ -517,16 +517,24 @@ struct SliceCtx {
     int r_begin;  // ranges of the slices before this one (context order)
 };
 
-// Number of candidate-dimension splits actually used: enough CTAs for about
-// `target` (a few waves over the SMs) given the number of row tiles that have
-// ranges to screen, capped by the list layout (max_split) and by the tiles.
-__host__ __device__ __forceinline__ int active_splits(int row_tiles, int col_tiles, int target, int max_split)
+// Number of candidate-dimension splits actually used: enough work items for
+// about `target` (a few waves over the SMs) given the number of row tiles
+// that have ranges to screen, capped by the list layout (max_split) and by
+// kMinSplitTiles candidate tiles per split (so that a work item amortises its
+// setup and its lists see enough candidates to tighten; the persistent
+// tensor-core search, recognised by its column tile, only: the FP32 search
+// launches one short CTA per item and wants the items).
+constexpr int kMinSplitTiles = 12;
+__host__ __device__ __forceinline__ int active_splits(int row_tiles, int col_tiles, int target, int max_split,
+                                                     int col_tile)
 {
     if (row_tiles <= 0 || col_tiles <= 0) return 1;
     int s = target / row_tiles;
     s = s < 1 ? 1 : s;
     s = s > max_split ? max_split : s;
-    return s > col_tiles ? col_tiles : s;
+    const int by_tiles = col_tile == 96 ? col_tiles / kMinSplitTiles : col_tiles;
+    s = s > by_tiles ? by_tiles : s;
+    return s < 1 ? 1 : s;
 }
 
 // ---------------------------------------------------------------- launches

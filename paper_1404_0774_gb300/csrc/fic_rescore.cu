@@ -320,7 +320,8 @@ __device__ __forceinline__ void rescore_range(const Geometry &g, const EpiConst 
     const int lane = threadIdx.x & 31;
     // lists actually written by the search (its split count follows the kept counts)
     const int n_lists = lists_per_split *
-                        active_splits((counts[0] + 127) / 128, (8 * counts[2] + col_tile - 1) / col_tile, target, max_split);
+                        active_splits((counts[0] + 127) / 128, (8 * counts[2] + col_tile - 1) / col_tile, target, max_split,
+                                      col_tile);
     const ListEntry *L = lists + (size_t)r * max_lists * kListK;
     const int nent = n_lists * kListK;
     // every entry of the range's lists in registers (entry lane + 32 s), the
@@ -672,7 +673,7 @@ __device__ __forceinline__ void list_scans(const Geometry &g, const RangeInfo *r
     const int count = *sb.count;
     const int ncol = 8 * counts[2];
     const int tiles = (ncol + col_tile - 1) / col_tile;
-    const int n_split = active_splits((counts[0] + 127) / 128, tiles, target, max_split);
+    const int n_split = active_splits((counts[0] + 127) / 128, tiles, target, max_split, col_tile);
     const int n_lists = n_split * lists_per_split;
     const int seg = col_tile / lists_per_split;
     for (int item = first; item < count; item += stride) {

@@ -36,6 +36,7 @@ namespace {
 
 constexpr int BM = 128;
 constexpr int BN = 96;                          // candidates per tile
+static_assert(BN == 96, "active_splits recognises the tensor-core search by its 96-column tile");
 constexpr int STAGES = 3;
 constexpr int NACC = 2;
 constexpr int EPI_COLS = 32;                    // columns of a tile per epilogue warp
@@ -321,7 +322,7 @@ __device__ __forceinline__ void search_tc_run(const TcMaps &maps, const SliceCtx
         const SliceCtx &c = ctx[i];
         const int nrow = c.b.cb.counts[0], ncol = 8 * c.b.cb.counts[2];
         const int rt = (nrow + BM - 1) / BM, tiles = (ncol + BN - 1) / BN;
-        const int ns = rt > 0 && tiles > 0 ? active_splits(rt, tiles, c.target, c.n_split) : 0;
+        const int ns = rt > 0 && tiles > 0 ? active_splits(rt, tiles, c.target, c.n_split, BN) : 0;
         ns_s[i] = ns;
         rt_s[i] = rt;
         ip_s[i + 1] = rt * ns;

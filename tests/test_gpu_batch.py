@@ -57,3 +57,37 @@ def test_batch_rejects_host_pointers_and_short_workspace(fic):
     bad = (fic.fic_slice * 1)(host)
     with pytest.raises(fic.FicError):
         fic.encode_batch(bad, p, torch.empty(need, dtype=torch.uint8, device="cuda"))
+
+
+def test_batch_of_stack_slices_equals_single_encodes(fic):
+    """Slices of the CT-like stack at the three sizes of the volume workload
+    (several per size, so the batch forms groups and two half pipelines):
+    every map equals the single-slice encode of that slice."""
+    seed = fic_synth.CT_SEED + 11
+    pick = [0, 1, 2, 32, 33, 34, 64, 65, 66, 95]  # slices of fic_synth.ct_stack(seed)
+    size = {0: 256, 1: 384, 2: 512}
+    p = fic.params(range_size=8, domain_stride=4, bit_depth=12)
+    imgs = [torch.from_numpy(fic_synth.ct_slice(seed + 1000 + k, size[k // 32]).astype(np.int16)).cuda() for k in pick]
+    maps = [torch.zeros((im.shape[0] // 8) ** 2 * 40, dtype=torch.uint8, device="cuda") for im in imgs]
+    tab = fic.slice_table(imgs, maps)
+    ws = torch.empty(fic.batch_workspace_size(tab, p), dtype=torch.uint8, device="cuda")
+    ref = [fic.maps_to_numpy(fic.encode(im, p)) for im in imgs]
+    for call in range(2):  # eager run, then a graph replay
+        for m in maps:
+            m.zero_()
+        fic.encode_batch(tab, p, ws)
+        torch.cuda.synchronize()
+        for i, m in enumerate(maps):
+            got = fic.maps_to_numpy(m)
+            assert np.array_equal(got, ref[i]), (call, pick[i])
+
+
+def test_batch_of_one_slice(fic):
+    im = torch.from_numpy(fic_synth.ct_slice(71, 128).astype(np.int16)).cuda()
+    p = fic.params(range_size=8, domain_stride=4, bit_depth=12)
+    mp = torch.zeros(256 * 40, dtype=torch.uint8, device="cuda")
+    tab = fic.slice_table([im], [mp])
+    ws = torch.empty(fic.batch_workspace_size(tab, p), dtype=torch.uint8, device="cuda")
+    fic.encode_batch(tab, p, ws)
+    torch.cuda.synchronize()
+    assert np.array_equal(fic.maps_to_numpy(mp), fic.maps_to_numpy(fic.encode(im, p)))
