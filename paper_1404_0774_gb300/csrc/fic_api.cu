@@ -369,8 +369,7 @@ cudaError_t encode_pipeline(const Geometry &gd, const fic_params *p, int search,
     // epilogue ignores; the exact-scan queue counters are zeroed by k_stats)
     FIC_MARK(0);
     FIC_STEP(launch_prep(gd, dimg, ec, dense, (search == FIC_SEARCH_TC && gd.split_hilo) ? 1 : 0, active, b.ri, b.di, b.dconst, b.bblk, b.qblk, b.rs32, b.cb32, b.ra16,
-                         b.cb16, b.tbest, b.cb, b.fb_count, st));
-    if (!dump) FIC_STEP(launch_seed(gd, ec, b.ri, b.di, b.dconst, b.bblk, b.qblk, b.cb.rkeep, b.tbest, st));
+                         b.cb16, b.tbest, b.cb, b.fb_count, dump ? 0 : 1, st));
     FIC_MARK(1);
     if (search == FIC_SEARCH_TC)
         FIC_STEP(launch_search_tc(gd, ec, b.ri, b.cb, dense, b.ra16, b.cb16, b.lists, n_split, target, b.tbest, dump,
@@ -880,11 +879,11 @@ cudaError_t batch_pipeline(const BatchPlan &P, const fic_params *p, char *ws, in
         if ((e = launch_stats_batch(dctx + gr.first, gr.second, blocks_of(gr.first), dense,
                                     (tc && g0.split_hilo) ? 1 : 0, st)) != cudaSuccess)
             return e;
-    if ((e = launch_compact_batch(dctx, n, st)) != cudaSuccess) return e;
+    for (auto &gr : groups)
+        if ((e = launch_compact_seed_batch(dctx + gr.first, gr.second, ranges_of(gr.first), st)) != cudaSuccess)
+            return e;
     for (auto &gr : groups)
         if ((e = launch_rows_batch(dctx + gr.first, gr.second, blocks_of(gr.first), st)) != cudaSuccess) return e;
-    for (auto &gr : groups)
-        if ((e = launch_seed_batch(dctx + gr.first, gr.second, ranges_of(gr.first), st)) != cudaSuccess) return e;
     if (tc)
         e = launch_search_tc_batch(g0, reinterpret_cast<const __half *>(ws + P.ra_off), P.arows,
                                    reinterpret_cast<const __half *>(ws + P.cb_off), P.brows, dctx, n, dense,

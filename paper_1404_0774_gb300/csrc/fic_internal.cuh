@@ -557,9 +557,8 @@ int search_simt_lists_per_split();
 // launch per stage over the slices (the per-slice stages: once per group of
 // equal slices).
 cudaError_t launch_stats_batch(const SliceCtx *ctx, int n, int blocks, int dense, int tc_split, cudaStream_t st);
-cudaError_t launch_compact_batch(const SliceCtx *ctx, int n, cudaStream_t st);
+cudaError_t launch_compact_seed_batch(const SliceCtx *ctx, int n, int ranges, cudaStream_t st);
 cudaError_t launch_rows_batch(const SliceCtx *ctx, int n, int blocks, cudaStream_t st);
-cudaError_t launch_seed_batch(const SliceCtx *ctx, int n, int ranges, cudaStream_t st);
 cudaError_t launch_search_tc_batch(const Geometry &g, const __half *ra16, int arows, const __half *cb16, int brows,
                                    const SliceCtx *ctx, int n, int dense, int *queue, cudaStream_t st);
 cudaError_t launch_search_simt_batch(const SliceCtx *ctx, int n, int max_ranges, int max_split, int dense,
@@ -606,10 +605,7 @@ cudaError_t launch_prep(const Geometry &g, const void *img, const EpiConst &ec, 
                         const int *active,
                         RangeInfo *ri, DomainInfo *di, float4 *dconst, uint16_t *bblk, uint16_t *qblk, float *rs32,
                         float *cb32, __half *ra16, __half *cb16, int *tbest, const CompactBufs &cb, int *zero4,
-                        cudaStream_t st);
-cudaError_t launch_seed(const Geometry &g, const EpiConst &ec, const RangeInfo *ri, const DomainInfo *di,
-                        const float4 *dconst, const uint16_t *bblk, const uint16_t *qblk, const int *rkeep,
-                        int *tbest, cudaStream_t st);
+                        int seed, cudaStream_t st);
 // The encode pipeline on a caller-provided device workspace (never allocates).
 int encode_with_workspace(const void *img, int w, int h, int pitch_px, const fic_params *p, fic_map *maps,
                           int maps_cap, int *n_maps, void *workspace, size_t workspace_bytes, void *stream);

@@ -193,17 +193,21 @@ __global__ void __launch_bounds__(256) k_stats_batch(const SliceCtx *__restrict_
                 b.cb.rkeep, b.cb.dkeep, b.fb_count, blockIdx.x);
 }
 
-// Stable compaction of the flagged items, block 0 over the ranges and block 1
-// over the domains: the kept indices in their original order, cnt[0] = how
-// many, cnt[1] = the first unflagged index (-1 if none).  Passes of
-// 16 x 1024 items: every flag of a pass is loaded up front (one memory
-// latency), warp ballots give per-(round, warp) counts, one warp scans those
-// 512 counts in item order, and every thread scatters its kept items.
+// Stable compaction of the flagged items by one block of T threads, over
+// the ranges or over the domains: the kept indices in their original order,
+// cnt[0] = how many, cnt[1] = the first unflagged index (-1 if none).
+// Passes of 16 x T items: every flag of a pass is loaded up front (one
+// memory latency), warp ballots give per-(round, warp) counts, one warp scans
+// those counts in item order, and every thread scatters its kept items.
 constexpr int kCompactRounds = 16;
+template <int T>
 __device__ __forceinline__ void compact_block(int nr, const int *rflag, int *ract, int *rcnt, int nd,
                                               const int *dflag, int *dact, int *dcnt, bool dom)
 {
-    __shared__ int off_s[kCompactRounds * 32];
+    constexpr int W = T / 32;             // warps
+    constexpr int E = kCompactRounds * W / 32;  // counts per lane of the scanning warp
+    static_assert(T % 64 == 0 && T <= 1024, "two or more warps, at most 1024 threads");
+    __shared__ int off_s[kCompactRounds * W];
     __shared__ int base_s, first_s;
     const int n = dom ? nd : nr;
     const int *flag = dom ? dflag : rflag;
@@ -215,11 +219,11 @@ __device__ __forceinline__ void compact_block(int nr, const int *rflag, int *rac
         first_s = 0x7fffffff;
     }
     int fu = 0x7fffffff;
-    for (int c0 = 0; c0 < n; c0 += 1024 * kCompactRounds) {
+    for (int c0 = 0; c0 < n; c0 += T * kCompactRounds) {
         bool f[kCompactRounds];
 #pragma unroll
         for (int q = 0; q < kCompactRounds; ++q) {
-            const int i = c0 + q * 1024 + t;
+            const int i = c0 + q * T + t;
             f[q] = i < n && flag[i] != 0;
             if (i < n && !f[q]) fu = min(fu, i);
         }
@@ -227,16 +231,16 @@ __device__ __forceinline__ void compact_block(int nr, const int *rflag, int *rac
 #pragma unroll
         for (int q = 0; q < kCompactRounds; ++q) {
             b[q] = __ballot_sync(0xffffffffu, f[q]);
-            if (lane == 0) off_s[q * 32 + w] = __popc(b[q]);
+            if (lane == 0) off_s[q * W + w] = __popc(b[q]);
         }
         __syncthreads();
         if (w == 0) {
-            // exclusive scan of the 512 counts in item order; lane l owns
-            // entries [16 l, 16 l + 16)
-            int v[16], sum = 0;
+            // exclusive scan of the 16 W counts in item order; lane l owns
+            // entries [E l, E l + E)
+            int v[E], sum = 0;
 #pragma unroll
-            for (int q = 0; q < 16; ++q) {
-                v[q] = off_s[16 * lane + q];
+            for (int q = 0; q < E; ++q) {
+                v[q] = off_s[E * lane + q];
                 sum += v[q];
             }
             int x = sum;
@@ -247,8 +251,8 @@ __device__ __forceinline__ void compact_block(int nr, const int *rflag, int *rac
             const int base = base_s;
             int run = base + x - sum;
 #pragma unroll
-            for (int q = 0; q < 16; ++q) {
-                off_s[16 * lane + q] = run;
+            for (int q = 0; q < E; ++q) {
+                off_s[E * lane + q] = run;
                 run += v[q];
             }
             __syncwarp();
@@ -257,7 +261,7 @@ __device__ __forceinline__ void compact_block(int nr, const int *rflag, int *rac
         __syncthreads();
 #pragma unroll
         for (int q = 0; q < kCompactRounds; ++q)
-            if (f[q]) list[off_s[q * 32 + w] + __popc(b[q] & ((1u << lane) - 1u))] = c0 + q * 1024 + t;
+            if (f[q]) list[off_s[q * W + w] + __popc(b[q] & ((1u << lane) - 1u))] = c0 + q * T + t;
         __syncthreads();  // off_s is rewritten by the next pass
     }
     for (int o = 16; o > 0; o >>= 1) fu = min(fu, __shfl_xor_sync(0xffffffffu, fu, o));
@@ -269,20 +273,6 @@ __device__ __forceinline__ void compact_block(int nr, const int *rflag, int *rac
     }
 }
 
-__global__ void __launch_bounds__(1024) k_compact(int nr, const int *rflag, int *ract, int *rcnt, int nd,
-                                                  const int *dflag, int *dact, int *dcnt)
-{
-    grid_dep_sync();
-    compact_block(nr, rflag, ract, rcnt, nd, dflag, dact, dcnt, blockIdx.x == 1);
-}
-
-__global__ void __launch_bounds__(1024) k_compact_batch(const SliceCtx *__restrict__ ctx)
-{
-    grid_dep_sync();
-    const SliceCtx c = ctx[blockIdx.y];
-    const CompactBufs &cb = c.b.cb;
-    compact_block(c.g.R, cb.rkeep, cb.act, cb.counts + 0, c.g.D, cb.dkeep, cb.dact, cb.counts + 2, blockIdx.x == 1);
-}
 
 __device__ __forceinline__ uint32_t pack_h2(__half a, __half b)
 {
@@ -436,23 +426,6 @@ __global__ void __launch_bounds__(256, 4) k_rows_batch(const SliceCtx *__restric
                b.cb32, b.cb16, b.cb.dconst_c, b.cb.dmap, blockIdx.x);
 }
 
-cudaError_t launch_prep(const Geometry &g, const void *img, const EpiConst &ec, int dense, int tc_split,
-                        const int *active,
-                        RangeInfo *ri, DomainInfo *di, float4 *dconst, uint16_t *bblk, uint16_t *qblk, float *rs32,
-                        float *cb32, __half *ra16, __half *cb16, int *tbest, const CompactBufs &cb, int *zero4,
-                        cudaStream_t st)
-{
-    const int rb = (g.R + 7) / 8, db = (g.D + 7) / 8;
-    cudaError_t e = launch_dep(k_stats, dim3(rb + db), dim3(256), 0, st, g, ec, img, dense, tc_split, active, rb, ri,
-                               bblk, tbest, di, dconst, qblk, cb.rkeep, cb.dkeep, zero4);
-    if (e != cudaSuccess) return e;
-    e = launch_dep(k_compact, dim3(2), dim3(1024), 0, st, g.R, (const int *)cb.rkeep, cb.act, cb.counts + 0, g.D,
-                   (const int *)cb.dkeep, cb.dact, cb.counts + 2);
-    if (e != cudaSuccess) return e;
-    return launch_dep(k_rows, dim3(rb + db), dim3(256), 0, st, g, rb, (const RangeInfo *)ri, (const uint16_t *)bblk,
-                      (const DomainInfo *)di, (const uint16_t *)qblk, (const float4 *)dconst, (const int *)cb.act,
-                      (const int *)cb.dact, (const int *)cb.counts, rs32, ra16, cb32, cb16, cb.dconst_c, cb.dmap);
-}
 
 // Seed of the per-range best key: before the search, every range scores 256
 // candidates -- the 8 symmetries of the 5 x 5 domains around it and of 7
@@ -538,28 +511,51 @@ __device__ __forceinline__ void seed_block(const Geometry &g, const EpiConst &ec
     atomicMin(tbest + r, f2ord(epi_key(Xt, -0.0f, c, re.zb, c4, ec)));
 }
 
-__global__ void __launch_bounds__(256) k_seed(Geometry g, EpiConst ec, const RangeInfo *ri, const DomainInfo *di,
-                                              const float4 *dconst, const uint16_t *bblk, const uint16_t *qblk,
-                                              const int *rkeep, int *tbest)
+// Compaction (blocks 0 and 1: ranges, domains) and, when seed != 0, the
+// seeds (one block per range after them) in one launch: both need only the
+// statistics, so the seeds run beside the two compaction blocks.
+__global__ void __launch_bounds__(256) k_compact_seed(Geometry g, EpiConst ec, int seed, const RangeInfo *ri,
+                                                      const DomainInfo *di, const float4 *dconst,
+                                                      const uint16_t *bblk, const uint16_t *qblk, const int *rkeep,
+                                                      const int *dkeep, int *act, int *dact, int *counts, int *tbest)
 {
     grid_dep_sync();
-    seed_block(g, ec, ri, di, dconst, bblk, qblk, rkeep, tbest, blockIdx.x);
+    if (blockIdx.x < 2)
+        compact_block<256>(g.R, rkeep, act, counts + 0, g.D, dkeep, dact, counts + 2, blockIdx.x == 1);
+    else if (seed)
+        seed_block(g, ec, ri, di, dconst, bblk, qblk, rkeep, tbest, blockIdx.x - 2);
 }
 
-__global__ void __launch_bounds__(256) k_seed_batch(const SliceCtx *__restrict__ ctx)
+__global__ void __launch_bounds__(256) k_compact_seed_batch(const SliceCtx *__restrict__ ctx)
 {
     grid_dep_sync();
     const SliceCtx c = ctx[blockIdx.y];
-    if ((int)blockIdx.x >= c.g.R) return;
     const EncBufs &b = c.b;
-    seed_block(c.g, c.ec, b.ri, b.di, b.dconst, b.bblk, b.qblk, b.cb.rkeep, b.tbest, blockIdx.x);
+    const CompactBufs &cb = b.cb;
+    if (blockIdx.x < 2)
+        compact_block<256>(c.g.R, cb.rkeep, cb.act, cb.counts + 0, c.g.D, cb.dkeep, cb.dact, cb.counts + 2,
+                           blockIdx.x == 1);
+    else if ((int)blockIdx.x - 2 < c.g.R)
+        seed_block(c.g, c.ec, b.ri, b.di, b.dconst, b.bblk, b.qblk, cb.rkeep, b.tbest, blockIdx.x - 2);
 }
 
-cudaError_t launch_seed(const Geometry &g, const EpiConst &ec, const RangeInfo *ri, const DomainInfo *di,
-                        const float4 *dconst, const uint16_t *bblk, const uint16_t *qblk, const int *rkeep,
-                        int *tbest, cudaStream_t st)
+cudaError_t launch_prep(const Geometry &g, const void *img, const EpiConst &ec, int dense, int tc_split,
+                        const int *active,
+                        RangeInfo *ri, DomainInfo *di, float4 *dconst, uint16_t *bblk, uint16_t *qblk, float *rs32,
+                        float *cb32, __half *ra16, __half *cb16, int *tbest, const CompactBufs &cb, int *zero4,
+                        int seed, cudaStream_t st)
 {
-    return launch_dep(k_seed, dim3(g.R), dim3(256), 0, st, g, ec, ri, di, dconst, bblk, qblk, rkeep, tbest);
+    const int rb = (g.R + 7) / 8, db = (g.D + 7) / 8;
+    cudaError_t e = launch_dep(k_stats, dim3(rb + db), dim3(256), 0, st, g, ec, img, dense, tc_split, active, rb, ri,
+                               bblk, tbest, di, dconst, qblk, cb.rkeep, cb.dkeep, zero4);
+    if (e != cudaSuccess) return e;
+    e = launch_dep(k_compact_seed, dim3(2 + (seed ? g.R : 0)), dim3(256), 0, st, g, ec, seed, (const RangeInfo *)ri,
+                   (const DomainInfo *)di, (const float4 *)dconst, (const uint16_t *)bblk, (const uint16_t *)qblk,
+                   (const int *)cb.rkeep, (const int *)cb.dkeep, cb.act, cb.dact, cb.counts, tbest);
+    if (e != cudaSuccess) return e;
+    return launch_dep(k_rows, dim3(rb + db), dim3(256), 0, st, g, rb, (const RangeInfo *)ri, (const uint16_t *)bblk,
+                      (const DomainInfo *)di, (const uint16_t *)qblk, (const float4 *)dconst, (const int *)cb.act,
+                      (const int *)cb.dact, (const int *)cb.counts, rs32, ra16, cb32, cb16, cb.dconst_c, cb.dmap);
 }
 
 // Batched prep stages of n slices (ctx: device array; blocks / ranges: the
@@ -569,9 +565,10 @@ cudaError_t launch_stats_batch(const SliceCtx *ctx, int n, int blocks, int dense
     return launch_dep(k_stats_batch, dim3(blocks, n), dim3(256), 0, st, ctx, dense, tc_split);
 }
 
-cudaError_t launch_compact_batch(const SliceCtx *ctx, int n, cudaStream_t st)
+// ranges: the largest of the slices (one seed block per range)
+cudaError_t launch_compact_seed_batch(const SliceCtx *ctx, int n, int ranges, cudaStream_t st)
 {
-    return launch_dep(k_compact_batch, dim3(2, n), dim3(1024), 0, st, ctx);
+    return launch_dep(k_compact_seed_batch, dim3(2 + ranges, n), dim3(256), 0, st, ctx);
 }
 
 cudaError_t launch_rows_batch(const SliceCtx *ctx, int n, int blocks, cudaStream_t st)
@@ -579,9 +576,6 @@ cudaError_t launch_rows_batch(const SliceCtx *ctx, int n, int blocks, cudaStream
     return launch_dep(k_rows_batch, dim3(blocks, n), dim3(256), 0, st, ctx);
 }
 
-cudaError_t launch_seed_batch(const SliceCtx *ctx, int n, int ranges, cudaStream_t st)
-{
-    return launch_dep(k_seed_batch, dim3(ranges, n), dim3(256), 0, st, ctx);
-}
+
 
 }  // namespace fic
