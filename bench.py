@@ -296,9 +296,9 @@ def run_quadtree(args):
             "e2e": {"value": ws * args.steps * comps / e2e_t, "unit": "comparisons/s",
                     "h2d_bytes_per_step": N_PIX * N_PIX * 2, "d2h_bytes_per_step": int(n_leaves) * 56,
                     "timing": "host wall clock (the call waits for its stream)"},
-            # per level the eight encode kernels and the split test; then the
+            # per level the seven encode kernels and the split test; then the
             # leaf count and the leaf gather
-            "gpu_launches": args.steps * (9 * len(per_level) + 2), "clocks": clocks, "roofline": None}
+            "gpu_launches": args.steps * (8 * len(per_level) + 2), "clocks": clocks, "roofline": None}
     if rank == 0:
         if ws == 1 and not args.no_cpu_baseline:
             import oracle
@@ -327,14 +327,14 @@ VOL_WORKLOAD = ("12-bit CT-like synthetic stack: 32 slices at 256x256, 32 at 384
 
 def batch_launches(sizes):
     """Kernel launches of one batched encode: the slices sorted by size are
-    dealt to two halves; per half the statistics, operand-row, seed and output
-    kernels run once per group of equal-sized slices, the compaction, search,
-    re-score and exact scans once."""
+    dealt to two halves; per half the statistics, compaction + seed, operand
+    row and output kernels run once per group of equal-sized slices, the
+    search, re-score and exact scans once."""
     order = sorted(sizes, reverse=True)
     total = 0
     for half in (order[0::2], order[1::2]):
         if half:
-            total += 4 * len(set(half)) + 4
+            total += 4 * len(set(half)) + 3
     return total
 
 
@@ -572,7 +572,7 @@ def main():
     for _ in range(max(3, args.warmup)):
         step()
     torch.cuda.synchronize()
-    launches_per_step = 8  # statistics, compaction, operand rows, seed, search, re-score, exact scans, output
+    launches_per_step = 7  # statistics, compaction + seed, operand rows, search, re-score, exact scans, output
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     if ws > 1:
