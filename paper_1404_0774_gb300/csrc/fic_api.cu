@@ -151,8 +151,10 @@ int choose_search(const Geometry &g, const fic_params *p)
 }
 
 // Maximum split of the candidate dimension (the list layout).  The kernels
-// use fewer splits when fewer ranges and domains need screening: enough CTAs
-// for `target` (four waves over the SMs), see active_splits.
+// use fewer splits when fewer ranges and domains need screening: enough work
+// for `target` (three work items per SM for the persistent tensor-core search,
+// measured a little faster than two or four on the 512x512 slice; eight CTAs
+// per SM for the FP32 search), see active_splits.
 constexpr int kMaxSplit = 64;
 constexpr int kMaxLists = 128;  // candidate lists per range the re-score takes (and its work-item codes hold)
 
@@ -168,7 +170,7 @@ int choose_split(const Geometry &g, const fic_params *p, int search)
 int split_target(const fic_params *p, int search)
 {
     if (p->n_split > 0) return 1 << 30;  // a fixed split: active_splits caps it at max_split
-    return 4 * (search == FIC_SEARCH_TC ? 1 : 2) * sm_count();
+    return (search == FIC_SEARCH_TC ? 3 : 8) * sm_count();
 }
 
 int lists_per_split(int search)
