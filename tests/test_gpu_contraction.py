@@ -69,6 +69,8 @@ CASES = [
     ("ramp12", lambda: (np.add.outer(np.arange(64) * 40, np.arange(64) * 23) % 4096).astype(np.uint16), 8, 4, 12),
     ("ct12_n4", lambda: fic_synth.ct_slice(25, 64), 4, 2, 12),
     ("mr8_n4", lambda: fic_synth.mr_slice(26, 48), 4, 4, 8),
+    ("extremes12", lambda: fic_synth.random_image(27, 64, 64, 1).astype(np.uint16) * 4095, 8, 4, 12),
+    ("all4095", lambda: np.full((48, 64), 4095, np.uint16), 8, 4, 12),
 ]
 
 

@@ -80,6 +80,9 @@ CASES = [
     ("constant", lambda: np.full((48, 48), 1234, np.uint16), 8, 4, 12),
     ("flat_regions", lambda: np.where(fic_synth.random_image(11, 64, 64, 8) > 128, 200, 10).astype(np.uint8), 8, 4, 8),
     ("b10_rand", lambda: fic_synth.random_image(12, 48, 48, 10).astype(np.uint16), 8, 4, 10),
+    # extreme magnitudes: every pixel 0 or 4095 (the largest centred products)
+    ("extremes12", lambda: fic_synth.random_image(15, 64, 64, 1).astype(np.uint16) * 4095, 8, 4, 12),
+    ("extremes12_n4", lambda: fic_synth.random_image(16, 48, 48, 1).astype(np.uint16) * 4095, 4, 2, 12),
 ]
 
 
@@ -128,6 +131,20 @@ def test_ct_slice_512_sampled(fic, orc, search):
     got = gpu_encode(fic, img, p)
     rng = np.random.default_rng(0)
     sample = np.sort(rng.choice(4096, 96, replace=False))
+    check_against_oracle(orc, img, got, 8, 4, 12, ranges=sample)
+
+
+@pytest.mark.parametrize("search", SEARCH)
+def test_ct_slice_1024_sampled(fic, orc, search):
+    """The largest size of the paper's experiments (1024x1024), 12-bit CT-like,
+    8x8 ranges, domains at stride 4 (16384 ranges x 64009 domains x 8 =
+    8.4e9 comparisons): every map re-scored, the minimum checked on sampled
+    ranges."""
+    img = fic_synth.ct_slice(fic_synth.CT_SEED + 3, 1024)
+    p = fic.params(range_size=8, domain_stride=4, bit_depth=12, search=search_code(fic, search))
+    got = gpu_encode(fic, img, p)
+    rng = np.random.default_rng(1)
+    sample = np.sort(rng.choice(16384, 40, replace=False))
     check_against_oracle(orc, img, got, 8, 4, 12, ranges=sample)
 
 
