@@ -325,16 +325,16 @@ VOL_WORKLOAD = ("12-bit CT-like synthetic stack: 32 slices at 256x256, 32 at 384
                 "16x16 domains at stride 4, 8 symmetries; s 5-bit, o 7-bit; one batch (one CUDA graph) per step")
 
 
-def batch_launches(sizes):
+def batch_launches(sizes, parts=6):
     """Kernel launches of one batched encode: the slices sorted by size are
-    dealt to two halves; per half the statistics, compaction + seed, operand
-    row and output kernels run once per group of equal-sized slices, the
-    search, re-score and exact scans once."""
+    dealt round-robin to `parts` concurrent pipelines; in each, the
+    statistics, compaction + seed, operand row and output kernels run once per
+    group of equal-sized slices, the search, re-score and exact scans once."""
     order = sorted(sizes, reverse=True)
     total = 0
-    for half in (order[0::2], order[1::2]):
-        if half:
-            total += 4 * len(set(half)) + 3
+    for k in range(min(parts, len(order))):
+        part = order[k::parts]
+        total += 4 * len(set(part)) + 3
     return total
 
 

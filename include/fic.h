@@ -282,8 +282,8 @@ typedef struct {
 /*
  * fic_encode_batch -- encode n slices (1 <= n <= 1024) of possibly different
  *   sizes with the same parameters: for each slice exactly what fic_encode
- *   computes.  The slices, sorted by size, are dealt to two halves that run
- *   as two concurrent pipelines; in each, every stage of the encode is one
+ *   computes.  The slices, sorted by size, are dealt round-robin to six parts
+ *   that run as concurrent pipelines; in each, every stage of the encode is one
  *   launch over its slices (the slice is the last grid dimension), and the
  *   search is one persistent kernel that walks a queue of (slice, candidate
  *   split, range tile) work items.  The launches form one CUDA graph, captured on the first

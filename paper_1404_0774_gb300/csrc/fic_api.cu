@@ -712,6 +712,8 @@ done:
 
 // ------------------------------------------------------------ batch
 
+constexpr int kBatchParts = 6;  // concurrent pipelines of a batch (2, 3, 4, 6: 11.0, 10.9, 10.8, 10.7 ms on the 96-slice stack)
+
 struct BatchSlice {
     Geometry g;
     int n_split;
@@ -731,7 +733,7 @@ struct BatchPlan {
     size_t ctx_off = 0, ra_off = 0, cb_off = 0, total = 0;
     int arows = 0, brows = 0, max_blocks = 0, max_ranges = 0, total_ranges = 0;
     bool any_wide = false, any_narrow = false;
-    int half = 0;  // slices [0, half) and [half, n) of the context order: the two pipelines
+    std::vector<int> part;  // part k: slices [part[k], part[k + 1]) of the context order, one pipeline each
     // the search's work-item counter of the pipeline starting at context k:
     // the spare fourth exact-scan counter of that slice (zeroed by its
     // statistics kernel)
@@ -769,19 +771,22 @@ int batch_plan(const fic_slice *slices, int n, const fic_params *p, BatchPlan &P
         P.sl[i].n_split = choose_split(P.sl[i].g, p, P.search);
         P.n_split = std::max(P.n_split, P.sl[i].n_split);
     }
-    // context order: the slices by decreasing size, dealt alternately to two
-    // halves that run as two concurrent pipelines (one half's statistics,
-    // rows and re-score overlap the other's search); each half is contiguous
-    // and again sorted by size
+    // context order: the slices by decreasing size, dealt round-robin to
+    // kBatchParts parts that run as concurrent pipelines (one part's
+    // statistics, rows and re-score overlap another's search); each part is
+    // contiguous and again sorted by size
     std::vector<int> bysize(n);
     for (int i = 0; i < n; ++i) bysize[i] = i;
     std::stable_sort(bysize.begin(), bysize.end(), [&](int a, int b) {
         return (long long)P.sl[a].g.R * P.sl[a].g.D > (long long)P.sl[b].g.R * P.sl[b].g.D;
     });
+    const int parts = std::min(kBatchParts, n);
     P.order.clear();
-    for (int h = 0; h < 2; ++h)
-        for (int k = h; k < n; k += 2) P.order.push_back(bysize[k]);
-    P.half = (n + 1) / 2;
+    P.part.assign(1, 0);
+    for (int h = 0; h < parts; ++h) {
+        for (int k = h; k < n; k += parts) P.order.push_back(bysize[k]);
+        P.part.push_back((int)P.order.size());
+    }
     const bool tc = P.search == FIC_SEARCH_TC;
     for (int i : P.order) {
         BatchSlice &b = P.sl[i];
@@ -838,8 +843,9 @@ std::vector<SliceCtx> batch_contexts(const BatchPlan &P, const fic_slice *slices
         c.db = (b.g.D + 7) / 8;
         c.abase = b.abase;
         c.bbase = b.bbase;
-        // (the ranges before this slice within its half)
-        c.r_begin = (k == 0 || (int)k == P.half) ? 0 : ctx[k - 1].r_begin + ctx[k - 1].g.R;
+        // (the ranges before this slice within its part)
+        const bool first = std::find(P.part.begin(), P.part.end(), (int)k) != P.part.end();
+        c.r_begin = first ? 0 : ctx[k - 1].r_begin + ctx[k - 1].g.R;
     }
     return ctx;
 }
@@ -910,9 +916,9 @@ struct BatchGraph {
     size_t ws_bytes = 0;
     cudaStream_t st = nullptr;
     cudaGraphExec_t exec = nullptr;
-    cudaEvent_t start = nullptr, end = nullptr, fork = nullptr, join = nullptr;
+    cudaEvent_t start = nullptr, end = nullptr, fork = nullptr, join[kBatchParts] = {};
     cudaStream_t cap = nullptr;  // origin stream of the capture (the caller's may be the legacy stream)
-    cudaStream_t side = nullptr; // the second half's pipeline
+    cudaStream_t side[kBatchParts] = {};  // the other parts' pipelines
     bool ready = false;
     void reset()
     {
@@ -957,9 +963,11 @@ int run_batch(const fic_slice *slices, int n, const fic_params *p, void *workspa
     if (!G.cap && cudaStreamCreateWithFlags(&G.cap, cudaStreamNonBlocking) != cudaSuccess) return FIC_ERR_CUDA;
     if (!G.start && cudaEventCreate(&G.start) != cudaSuccess) return FIC_ERR_CUDA;
     if (!G.end && cudaEventCreate(&G.end) != cudaSuccess) return FIC_ERR_CUDA;
-    if (!G.side && cudaStreamCreateWithFlags(&G.side, cudaStreamNonBlocking) != cudaSuccess) return FIC_ERR_CUDA;
+    for (int k = 0; k < kBatchParts; ++k) {
+        if (!G.side[k] && cudaStreamCreateWithFlags(&G.side[k], cudaStreamNonBlocking) != cudaSuccess) return FIC_ERR_CUDA;
+        if (!G.join[k] && cudaEventCreateWithFlags(&G.join[k], cudaEventDisableTiming) != cudaSuccess) return FIC_ERR_CUDA;
+    }
     if (!G.fork && cudaEventCreateWithFlags(&G.fork, cudaEventDisableTiming) != cudaSuccess) return FIC_ERR_CUDA;
-    if (!G.join && cudaEventCreateWithFlags(&G.join, cudaEventDisableTiming) != cudaSuccess) return FIC_ERR_CUDA;
     // the slice contexts: written once, read by every replay
     const std::vector<SliceCtx> ctx = batch_contexts(P, slices, p, ws);
     if (cudaMemcpyAsync(ws + P.ctx_off, ctx.data(), sizeof(SliceCtx) * ctx.size(), cudaMemcpyHostToDevice, st) !=
@@ -979,13 +987,16 @@ int run_batch(const fic_slice *slices, int n, const fic_params *p, void *workspa
         const bool capturing = e == cudaSuccess && capture;
         // external records: event-record nodes that run with every replay
         if (capture && e == cudaSuccess) e = cudaEventRecordWithFlags(G.start, o, cudaEventRecordExternal);
-        // the two halves as concurrent branches
+        // the parts as concurrent branches (part 0 on the origin stream)
+        const int np = (int)P.part.size() - 1;
         if (e == cudaSuccess) e = cudaEventRecord(G.fork, o);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(G.side, G.fork, 0);
-        if (e == cudaSuccess) e = batch_pipeline(P, p, ws, 0, P.half, o);
-        if (e == cudaSuccess) e = batch_pipeline(P, p, ws, P.half, n, G.side);
-        if (e == cudaSuccess) e = cudaEventRecord(G.join, G.side);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(o, G.join, 0);
+        for (int k = 1; k < np && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(G.side[k], G.fork, 0);
+        for (int k = 0; k < np && e == cudaSuccess; ++k)
+            e = batch_pipeline(P, p, ws, P.part[k], P.part[k + 1], k ? G.side[k] : o);
+        for (int k = 1; k < np && e == cudaSuccess; ++k) {
+            e = cudaEventRecord(G.join[k], G.side[k]);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(o, G.join[k], 0);
+        }
         if (capture && e == cudaSuccess) e = cudaEventRecordWithFlags(G.end, o, cudaEventRecordExternal);
         if (capturing) {
             cudaGraph_t graph = nullptr;
