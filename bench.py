@@ -53,6 +53,29 @@ def dist_env():
     return ws, rank, local
 
 
+def rank_seed(rank):
+    """Every rank encodes its own slice: independent problems, no exchange
+    step (weak scaling; the replicas share nothing but the timing)."""
+    return fic_synth.CT_SEED + rank
+
+
+def max_over_ranks(t, ws, device=None):
+    """The job's time is its slowest rank's: an all-reduce MAX over the ranks."""
+    if ws <= 1:
+        return t
+    import torch
+    import torch.distributed as dist
+
+    tt = torch.tensor([t], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def job_rate(ws, steps, units_per_step, t):
+    """Whole-job throughput: the units all ranks processed over the job's time."""
+    return ws * steps * units_per_step / t
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons, sampled while the timed region runs."""
 
@@ -234,7 +257,7 @@ def run_quadtree(args):
     __graft_entry__.build()
     from paper_1404_0774_gb300 import fic
 
-    img_np = fic_synth.ct_slice(fic_synth.CT_SEED + rank)
+    img_np = fic_synth.ct_slice(rank_seed(rank))
     p = fic.params(range_size=16, domain_stride=16, bit_depth=BITS)
     img = torch.from_numpy(img_np.astype(np.int16)).to(dev)
     work = torch.empty(fic.quadtree_workspace_size(N_PIX, N_PIX, p, 4), dtype=torch.uint8, device=dev)
@@ -268,11 +291,8 @@ def run_quadtree(args):
         torch.cuda.synchronize()
         clk_window = time.time() - t_clk
     t_total = float(np.sum([a.elapsed_time(b) for a, b in ev])) / 1e3
-    if ws > 1:
-        tt = torch.tensor([t_total], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_total = float(tt.item())
-    value = ws * args.steps * comps / t_total
+    t_total = max_over_ranks(t_total, ws, dev)
+    value = job_rate(ws, args.steps, comps, t_total)
     # end to end from pinned host memory through the C ABI (image H2D, leaves D2H)
     h_img = torch.from_numpy(img_np.astype(np.int16)).pin_memory()
     h_maps = np.zeros(cap, fic.QMAP_DTYPE)
@@ -293,7 +313,7 @@ def run_quadtree(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "fp16+fp32", "data": "synthetic",
             "config": {"workload": QT_WORKLOAD, "leaves": int(n_leaves), "comparisons_per_step": comps,
                        "levels": per_level, "l2": "flushed (256 MB write) between steps"},
-            "e2e": {"value": ws * args.steps * comps / e2e_t, "unit": "comparisons/s",
+            "e2e": {"value": job_rate(ws, args.steps, comps, e2e_t), "unit": "comparisons/s",
                     "h2d_bytes_per_step": N_PIX * N_PIX * 2, "d2h_bytes_per_step": int(n_leaves) * 56,
                     "timing": "host wall clock (the call waits for its stream)"},
             # per level the seven encode kernels and the split test; then the
@@ -387,12 +407,9 @@ def run_volume(args):
             torch.cuda.synchronize()
         clk_window = time.time() - t_clk
     t_total = float(np.sum([a.elapsed_time(b) for a, b in ev])) / 1e3
-    if ws_n > 1:
-        tt = torch.tensor([t_total], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_total = float(tt.item())
+    t_total = max_over_ranks(t_total, ws_n, dev)
     n_sl = len(stack)
-    value = ws_n * args.steps * n_sl / t_total
+    value = job_rate(ws_n, args.steps, n_sl, t_total)
     # per-slice completion times within a batch (separate runs: reading them waits for the batch)
     for _ in range(args.steps):
         fic.encode_batch(tab, p, work, stream)
@@ -427,13 +444,13 @@ def run_volume(args):
             "warmup": max(3, args.warmup), "ms_per_step": 1e3 * t_total / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "fp16+fp32", "data": "synthetic",
             "config": {"workload": VOL_WORKLOAD, "slices": n_sl, "comparisons_per_step": comps,
-                       "comparisons_per_s": ws_n * args.steps * comps / t_total,
+                       "comparisons_per_s": job_rate(ws_n, args.steps, comps, t_total),
                        "slice_completion_ms": {"p50": float(np.percentile(lat, 50)),
                                                "p99": float(np.percentile(lat, 99)), "max": float(lat.max()),
                                                "note": "time from the start of the batch to each slice's maps "
                                                        "(every stage covers all slices: they complete together)"},
                        "l2": "working set of the batch (several GB) is larger than L2"},
-            "e2e": {"value": ws_n * args.steps * n_sl / e2e_t, "unit": "slices/s", "h2d_bytes_per_step": h2d,
+            "e2e": {"value": job_rate(ws_n, args.steps, n_sl, e2e_t), "unit": "slices/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": args.steps * batch_launches([a.shape[0] * a.shape[1] for a in stack]), "clocks": clocks,
             "roofline": None}
@@ -461,7 +478,7 @@ def run_refine(args):
     __graft_entry__.build()
     from paper_1404_0774_gb300 import fic
 
-    img_np = fic_synth.ct_slice(fic_synth.CT_SEED + rank)
+    img_np = fic_synth.ct_slice(rank_seed(rank))
     p = fic.params(range_size=RANGE, domain_stride=STRIDE, bit_depth=BITS)
     img = torch.from_numpy(img_np.astype(np.int16)).to(dev)
     maps = fic.encode(img, p)
@@ -556,7 +573,7 @@ def main():
     from paper_1404_0774_gb300 import fic
 
     R, D, comps = comparisons()
-    img_np = fic_synth.ct_slice(fic_synth.CT_SEED + rank)
+    img_np = fic_synth.ct_slice(rank_seed(rank))
     search = {"auto": fic.FIC_SEARCH_AUTO, "tc": fic.FIC_SEARCH_TC, "simt": fic.FIC_SEARCH_SIMT}[args.search]
     p = fic.params(range_size=RANGE, domain_stride=STRIDE, bit_depth=BITS, search=search)
     img = torch.from_numpy(img_np.astype(np.int16)).to(dev)
@@ -599,11 +616,8 @@ def main():
         dist.barrier()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     t_total = float(np.sum(step_ms)) / 1e3
-    if ws > 1:
-        tt = torch.tensor([t_total], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_total = float(tt.item())
-    value = ws * args.steps * comps / t_total
+    t_total = max_over_ranks(t_total, ws, dev)
+    value = job_rate(ws, args.steps, comps, t_total)
 
     # dominant kernel: the search, timed alone with events on the launching stream
     stats = fic.last_encode_stats()
@@ -633,11 +647,8 @@ def main():
         e_ev[i][1].record(stream)
     torch.cuda.synchronize()
     e2e_t = float(np.sum([a.elapsed_time(b) for a, b in e_ev])) / 1e3
-    if ws > 1:
-        tt = torch.tensor([e2e_t], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_t = float(tt.item())
-    e2e_value = ws * args.steps * comps / e2e_t
+    e2e_t = max_over_ranks(e2e_t, ws, dev)
+    e2e_value = job_rate(ws, args.steps, comps, e2e_t)
 
     mnp = fic.maps_to_numpy(maps)
     n_fallback = int((mnp["info"] & fic.FIC_MAP_FALLBACK).sum())
@@ -657,11 +668,8 @@ def main():
         d_ev[i][1].record(stream)
     torch.cuda.synchronize()
     dense_t = float(np.sum([a.elapsed_time(b) for a, b in d_ev])) / 1e3
-    if ws > 1:
-        tt = torch.tensor([dense_t], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        dense_t = float(tt.item())
-    dense_value = ws * args.steps * comps / dense_t
+    dense_t = max_over_ranks(dense_t, ws, dev)
+    dense_value = job_rate(ws, args.steps, comps, dense_t)
     # what the skips leave to screen (host-side count from the image itself)
     n = RANGE
     blocks = img_np.reshape(N_PIX // n, n, N_PIX // n, n).transpose(0, 2, 1, 3).reshape(-1, n * n)
