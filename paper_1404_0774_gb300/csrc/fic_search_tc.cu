@@ -558,6 +558,7 @@ __device__ __forceinline__ void search_tc_run(const TcMaps &maps, const SliceCtx
             for (int it = 0; it < ntile; ++it, ++aseq) {
                 const int acc = aseq % NACC;
                 const int n0 = (w.t_begin + it) * BN + part * EPI_COLS;
+                __syncwarp();  // every lane is done with the previous tile's staged constants
                 if (lane < DC_WARP) {
                     wdc[lane] = dc_next;
                     wod[lane] = od_next;
@@ -582,13 +583,10 @@ __device__ __forceinline__ void search_tc_run(const TcMaps &maps, const SliceCtx
                 tc_fence_after();
                 const uint32_t taddr = lane_addr + acc * ACC_COLS;
                 const int nv = min(32, ncol - n0);  // may be <= 0 in the last tile
-                int od[4];
-                float4 dc[4];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    od[q] = wod[q];
-                    dc[q] = wdc[q];
-                }
+                // the chunk's domain constants stay in shared memory (read where
+                // used, which leaves the registers to the key computation)
+                const int (&od)[4] = *reinterpret_cast<const int (*)[4]>(wod);
+                const float4 (&dc)[4] = *reinterpret_cast<const float4 (*)[4]>(wdc);
                 float X[32];
                 {
                     uint32_t h[32], l[32];
