@@ -523,11 +523,9 @@ __device__ __forceinline__ void search_tc_run(const TcMaps &maps, const SliceCtx
             const TcItem w = tc_item(ctx, ip_s, ns_s, rt_s, n, item);
             const SliceCtx &c = BATCH ? many[w.s] : one;
             const Geometry &g = c.g;
-            // a single search keeps reading the kernel parameters (constant-bank
-            // operands); a batch copies its slice's constants into registers
-            EpiConst ec_reg;
-            if (BATCH) ec_reg = c.ec;
-            const EpiConst &ec = BATCH ? ec_reg : c.ec;
+            // the slice's constants: kernel parameters (constant-bank operands) for
+            // a single search, the context array (cached loads) for a batch
+            const EpiConst &ec = c.ec;
             const float4 *dconst = c.b.cb.dconst_c;
             const int *dmap = c.b.cb.dmap;
             int *err = c.b.err;
