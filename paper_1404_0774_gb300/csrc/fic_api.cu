@@ -888,7 +888,8 @@ cudaError_t batch_pipeline(const BatchPlan &P, const fic_params *p, char *ws, in
                                     (tc && g0.split_hilo) ? 1 : 0, st)) != cudaSuccess)
             return e;
     for (auto &gr : groups)
-        if ((e = launch_compact_seed_batch(dctx + gr.first, gr.second, ranges_of(gr.first), st)) != cudaSuccess)
+        if ((e = launch_compact_seed_batch(dctx + gr.first, gr.second, ranges_of(gr.first),
+                                            P.sl[P.order[k0 + gr.first]].g.m, st)) != cudaSuccess)
             return e;
     for (auto &gr : groups)
         if ((e = launch_rows_batch(dctx + gr.first, gr.second, blocks_of(gr.first), st)) != cudaSuccess) return e;

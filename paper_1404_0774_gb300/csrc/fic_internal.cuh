@@ -467,11 +467,6 @@ __device__ __forceinline__ int sym_src_index(const SymFlags &f, int ln, int y, i
     return ((u ^ f.my) << ln) + (v ^ f.mx);
 }
 
-__device__ __forceinline__ int load_px(const void *img, int B, size_t off)
-{
-    return B <= 8 ? (int)((const uint8_t *)img)[off] : (int)((const uint16_t *)img)[off];
-}
-
 // Compaction of the search dimensions: ranges that need screening (all but
 // shadow ranges) and domains that need screening (all but flat domains), in
 // their original order.  counts[0] = ranges kept, counts[1] = first shadow
@@ -557,7 +552,7 @@ int search_simt_lists_per_split();
 // launch per stage over the slices (the per-slice stages: once per group of
 // equal slices).
 cudaError_t launch_stats_batch(const SliceCtx *ctx, int n, int blocks, int dense, int tc_split, cudaStream_t st);
-cudaError_t launch_compact_seed_batch(const SliceCtx *ctx, int n, int ranges, cudaStream_t st);
+cudaError_t launch_compact_seed_batch(const SliceCtx *ctx, int n, int ranges, int m, cudaStream_t st);
 cudaError_t launch_rows_batch(const SliceCtx *ctx, int n, int blocks, cudaStream_t st);
 cudaError_t launch_search_tc_batch(const Geometry &g, const __half *ra16, int arows, const __half *cb16, int brows,
                                    const SliceCtx *ctx, int n, int dense, int *queue, cudaStream_t st);

@@ -27,13 +27,21 @@ __device__ __forceinline__ void range_stats(const Geometry &g, const EpiConst &e
     int bv[PPL];
     long long Sb = 0, Sbb = 0;
     int bmin = 1 << 30, bmax = -1;
+    // every load issued before the first use (no store between them)
+    const bool b8 = g.B <= 8;
 #pragma unroll
     for (int j = 0; j < PPL; ++j) {
+        if (32 * j >= g.m) break;  // warp-uniform
         const int i = lane + 32 * j;
-        bv[j] = 0;
+        const size_t off = (size_t)(ry + i / g.n) * g.pitch + rx + i % g.n;
+        bv[j] = i < g.m ? (b8 ? (int)((const uint8_t *)img)[off] : (int)((const uint16_t *)img)[off]) : 0;
+    }
+#pragma unroll
+    for (int j = 0; j < PPL; ++j) {
+        if (32 * j >= g.m) break;
+        const int i = lane + 32 * j;
         if (i < g.m) {
-            const int b = load_px(img, g.B, (size_t)(ry + i / g.n) * g.pitch + rx + i % g.n);
-            bv[j] = b;
+            const int b = bv[j];
             Sb += b;
             Sbb += (long long)b * b;
             bmin = min(bmin, b);
@@ -56,6 +64,7 @@ __device__ __forceinline__ void range_stats(const Geometry &g, const EpiConst &e
     long long bp2i = 0;
 #pragma unroll
     for (int j = 0; j < PPL; ++j) {
+        if (32 * j >= g.m) break;
         const int i = lane + 32 * j;
         if (i < g.m) {
             const int bc = bv[j] - c_r;
@@ -120,14 +129,38 @@ __device__ __forceinline__ void domain_stats(const Geometry &g, const void *img,
     const int du = d % g.U;
     const int dy = (d / g.U) * g.t, dx = du * g.t;
     long long Sq = 0, Sqq = 0;
-    for (int i = lane; i < g.m; i += 32) {
+    constexpr int QPL = kMaxM / 32;  // contracted pixels per lane, upper bound
+    int qv[QPL];
+    const bool b8 = g.B <= 8;
+    // every load issued before the first store
+#pragma unroll
+    for (int j = 0; j < QPL; ++j) {
+        if (32 * j >= g.m) break;  // warp-uniform
+        const int i = lane + 32 * j;
         const int y = i >> g.ln, x = i & (g.n - 1);
         const size_t o0 = (size_t)(dy + 2 * y) * g.pitch + dx + 2 * x;
-        const int q = load_px(img, g.B, o0) + load_px(img, g.B, o0 + 1) + load_px(img, g.B, o0 + g.pitch) +
-                      load_px(img, g.B, o0 + g.pitch + 1);
-        qblk[(size_t)d * g.m + i] = (uint16_t)q;
-        Sq += q;
-        Sqq += (long long)q * q;
+        int q = 0;
+        if (i < g.m) {
+            if (b8) {
+                const uint8_t *p8 = (const uint8_t *)img;
+                q = (int)p8[o0] + (int)p8[o0 + 1] + (int)p8[o0 + g.pitch] + (int)p8[o0 + g.pitch + 1];
+            } else {
+                const uint16_t *p16 = (const uint16_t *)img;
+                q = (int)p16[o0] + (int)p16[o0 + 1] + (int)p16[o0 + g.pitch] + (int)p16[o0 + g.pitch + 1];
+            }
+        }
+        qv[j] = q;
+    }
+#pragma unroll
+    for (int j = 0; j < QPL; ++j) {
+        if (32 * j >= g.m) break;
+        const int i = lane + 32 * j;
+        if (i < g.m) {
+            const int q = qv[j];
+            qblk[(size_t)d * g.m + i] = (uint16_t)q;
+            Sq += q;
+            Sqq += (long long)q * q;
+        }
     }
     Sq = warp_sum_ll(Sq);
     Sqq = warp_sum_ll(Sqq);
@@ -220,11 +253,16 @@ __device__ __forceinline__ void compact_block(int nr, const int *rflag, int *rac
     }
     int fu = 0x7fffffff;
     for (int c0 = 0; c0 < n; c0 += T * kCompactRounds) {
+        // all the pass's flag loads in flight at once (clamped index: no
+        // branch between them)
+        int fv[kCompactRounds];
+#pragma unroll
+        for (int q = 0; q < kCompactRounds; ++q) fv[q] = flag[min(c0 + q * T + t, n - 1)];
         bool f[kCompactRounds];
 #pragma unroll
         for (int q = 0; q < kCompactRounds; ++q) {
             const int i = c0 + q * T + t;
-            f[q] = i < n && flag[i] != 0;
+            f[q] = i < n && fv[q] != 0;
             if (i < n && !f[q]) fu = min(fu, i);
         }
         unsigned b[kCompactRounds];
@@ -286,8 +324,19 @@ __device__ __forceinline__ void range_row(const Geometry &g, const RangeInfo *ri
                                           int lane, float *rs32, __half *ra16)
 {
     const RangeInfo info = ri[r];
-    for (int i = lane; i < g.m; i += 32) {
-        const int bc = (int)bblk[(size_t)r * g.m + i] - info.c_r;
+    constexpr int PPL = kMaxM / 32;
+    int bv[PPL];
+#pragma unroll
+    for (int u = 0; u < PPL; ++u) {  // every load before the first store
+        if (32 * u >= g.m) break;  // warp-uniform
+        const int i = lane + 32 * u;
+        bv[u] = i < g.m ? (int)bblk[(size_t)r * g.m + i] : 0;
+    }
+#pragma unroll
+    for (int u = 0; u < PPL; ++u) {
+        const int i = lane + 32 * u;
+        if (i >= g.m) break;
+        const int bc = bv[u] - info.c_r;
         if (rs32) rs32[(size_t)j * g.m + i] = (float)bc;
         if (ra16) {
             ra16[(size_t)j * g.KP + i] = __int2half_rn(bc);
@@ -306,18 +355,56 @@ __device__ __forceinline__ void range_row(const Geometry &g, const RangeInfo *ri
     }
 }
 
+// 8 (4) FP16 bit patterns in reverse order.
+__device__ __forceinline__ uint4 rev8(uint4 v)
+{
+    return make_uint4(__byte_perm(v.w, 0, 0x1032), __byte_perm(v.z, 0, 0x1032), __byte_perm(v.y, 0, 0x1032),
+                      __byte_perm(v.x, 0, 0x1032));
+}
+
+__device__ __forceinline__ uint2 rev4(uint2 v)
+{
+    return make_uint2(__byte_perm(v.y, 0, 0x1032), __byte_perm(v.x, 0, 0x1032));
+}
+
+// Elements i0 .. i0+7 (i0 a multiple of 8) of S_k applied to an n x n block
+// held row-major in s and transposed in t (16-byte aligned).  Output (y, x)
+// reads s at row u ^ my, column v ^ mx with (u, v) = swap ? (x, y) : (y, x);
+// with the axes swapped that is t at row y ^ mx, column x ^ my.  Either way
+// the 8 elements are a run along one row of s or t, reversed when the column
+// mask is set (n >= 8: one run of 8; n = 4: two runs of 4).
+__device__ __forceinline__ uint4 sym_chunk(const uint16_t *s, const uint16_t *t, const SymFlags &f, int n, int ln,
+                                           int i0)
+{
+    const uint16_t *b = f.swap ? t : s;
+    const int rm = f.swap ? f.mx : f.my, cm = f.swap ? f.my : f.mx;
+    if (n >= 8) {
+        const int y = i0 >> ln, x0 = i0 & (n - 1);
+        const uint4 v = *reinterpret_cast<const uint4 *>(b + ((y ^ rm) << ln) + ((x0 ^ cm) & ~7));
+        return cm ? rev8(v) : v;
+    }
+    const int y = i0 >> 2;
+    uint2 r0 = *reinterpret_cast<const uint2 *>(b + ((y ^ rm) << 2));
+    uint2 r1 = *reinterpret_cast<const uint2 *>(b + (((y + 1) ^ rm) << 2));
+    if (cm) {
+        r0 = rev4(r0);
+        r1 = rev4(r1);
+    }
+    return make_uint4(r0.x, r0.y, r1.x, r1.y);
+}
+
 // Candidate rows 8j+k of the domain dact[j]: output pixel i = (y,x) of
-// S_k(tau(d)) is q at src_s[k][i], centred by c_d.  FP16 row (tensor-core
-// layout): [128*hi | lo (12-bit only) | -1024 f_d/m, -f_d/m, 0...] with
-// q - c_d = 128*hi + lo.  The warp converts the domain's m values once into
-// FP16 bit patterns in shared memory, then assembles 16-byte chunks of the 8
-// rows by gathering (KP and m are multiples of 8, so a chunk never straddles
-// two parts).  Domain constants in the same order.
+// S_k(tau(d)) is q at sym_src_index(k, i), centred by c_d.  FP16 row
+// (tensor-core layout): [128*hi | lo (12-bit only) | -1024 f_d/m, -f_d/m,
+// 0...] with q - c_d = 128*hi + lo.  The warp converts the domain's m values
+// once into FP16 bit patterns in shared memory, row-major and transposed, then
+// writes the 16-byte chunks of the 8 rows, each one aligned shared-memory load
+// (KP and m are multiples of 8, so a chunk never straddles two parts).
+// Domain constants in the same order.
 __device__ __forceinline__ void domain_rows_warp(const Geometry &g, const DomainInfo *di, const uint16_t *qblk,
-                                                 const float4 *dconst, int j, int d, int lane,
-                                                 const uint8_t (*src_s)[kMaxM], const uint16_t *kc_s,
-                                                 uint16_t *hi_s, uint16_t *lo_s, float *cb32, __half *cb16,
-                                                 float4 *dconst_c, int *dmap)
+                                                 const float4 *dconst, int j, int d, int lane, const uint16_t *kc_s,
+                                                 uint16_t *hi_s, uint16_t *lo_s, uint16_t *hit_s, uint16_t *lot_s,
+                                                 float *cb32, __half *cb16, float4 *dconst_c, int *dmap)
 {
     const int m = g.m;
     const DomainInfo info = di[d];
@@ -326,23 +413,44 @@ __device__ __forceinline__ void domain_rows_warp(const Geometry &g, const Domain
         dconst_c[j] = dconst[d];
         dmap[j] = d;
     }
-    for (int i = lane; i < m; i += 32) {
-        const int qc = (int)qblk[(size_t)d * m + i] - c_d;
+    constexpr int QPL = kMaxM / 32;
+    int qv[QPL];
+#pragma unroll
+    for (int u = 0; u < QPL; ++u) {  // every load before the first store
+        if (32 * u >= m) break;  // warp-uniform
+        const int i = lane + 32 * u;
+        qv[u] = i < m ? (int)qblk[(size_t)d * m + i] : 0;
+    }
+#pragma unroll
+    for (int u = 0; u < QPL; ++u) {
+        const int i = lane + 32 * u;
+        if (i >= m) break;
+        const int qc = qv[u] - c_d;
+        const int it = ((i & (g.n - 1)) << g.ln) + (i >> g.ln);  // transposed position
         if (cb32) {
             lo_s[i] = (uint16_t)(qc + 32768);  // SIMT operand: centred value, biased
         } else if (g.split_hilo) {
             const int hi = (qc + 64) >> 7;  // floor; |hi| <= 128
-            hi_s[i] = __half_as_ushort(__int2half_rn(128 * hi));
-            lo_s[i] = __half_as_ushort(__int2half_rn(qc - 128 * hi));
+            const uint16_t h = __half_as_ushort(__int2half_rn(128 * hi));
+            const uint16_t l = __half_as_ushort(__int2half_rn(qc - 128 * hi));
+            hi_s[i] = h;
+            hit_s[it] = h;
+            lo_s[i] = l;
+            lot_s[it] = l;
         } else {
-            hi_s[i] = __half_as_ushort(__int2half_rn(qc));
+            const uint16_t h = __half_as_ushort(__int2half_rn(qc));
+            hi_s[i] = h;
+            hit_s[it] = h;
         }
     }
     __syncwarp();
     if (cb32) {
-        for (int k = 0; k < 8; ++k)
+        for (int k = 0; k < 8; ++k) {
+            const SymFlags f = sym_flags(k, g.n);
             for (int i = lane; i < m; i += 32)
-                cb32[((size_t)j * 8 + k) * m + i] = (float)((int)lo_s[src_s[k][i]] - 32768);
+                cb32[((size_t)j * 8 + k) * m + i] =
+                    (float)((int)lo_s[sym_src_index(f, g.ln, i >> g.ln, i & (g.n - 1))] - 32768);
+        }
         return;
     }
     const int nch = g.KP >> 3;  // 16-byte chunks per row
@@ -353,38 +461,28 @@ __device__ __forceinline__ void domain_rows_warp(const Geometry &g, const Domain
         const int kc = kc_s[e];
         const int k = kc >> 8, c = kc & 255;
         const int col0 = 8 * c;
-        uint32_t h[8];
+        uint4 v;
         if (col0 >= base) {
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int tc = col0 + u - base;
-                h[u] = tc == 0 ? t0 : (tc == 1 ? t1 : 0u);
-            }
+            v = make_uint4(col0 == base ? (t0 | (t1 << 16)) : 0u, 0u, 0u, 0u);
         } else {
             const bool lo_part = col0 >= m;  // second copy (12-bit only)
-            const uint16_t *vs = lo_part ? lo_s : hi_s;
-            const uint8_t *sk = src_s[k] + (lo_part ? col0 - m : col0);
-#pragma unroll
-            for (int u = 0; u < 8; ++u) h[u] = vs[sk[u]];
+            v = sym_chunk(lo_part ? lo_s : hi_s, lo_part ? lot_s : hit_s, sym_flags(k, g.n), g.n, g.ln,
+                          lo_part ? col0 - m : col0);
         }
-        const uint4 v = make_uint4(h[0] | (h[1] << 16), h[2] | (h[3] << 16), h[4] | (h[5] << 16),
-                                   h[6] | (h[7] << 16));
         reinterpret_cast<uint4 *>(cb16 + ((size_t)j * 8 + k) * g.KP)[c] = v;
     }
 }
 
 // Operand rows of the kept ranges (blocks [0, rb), a warp per row) and of the
 // kept domains (the blocks after, a warp per domain), one launch.  Domain
-// blocks first build the symmetry source table src_s[k][i] and the (row,
-// chunk) table of their 16-byte chunks.
+// blocks first build the (row, chunk) table of their 16-byte chunks.
 __device__ __forceinline__ void rows_block(const Geometry &g, int rb, const RangeInfo *ri, const uint16_t *bblk,
                                            const DomainInfo *di, const uint16_t *qblk, const float4 *dconst,
                                            const int *act, const int *dact, const int *counts, float *rs32,
                                            __half *ra16, float *cb32, __half *cb16, float4 *dconst_c, int *dmap, int bx)
 {
-    __shared__ uint8_t src_s[8][kMaxM];
     __shared__ uint16_t kc_s[8 * ((2 * kMaxM + 16) / 8)];
-    __shared__ uint16_t hi_s[8][kMaxM], lo_s[8][kMaxM];
+    __shared__ __align__(16) uint16_t hi_s[8][kMaxM], lo_s[8][kMaxM], hit_s[8][kMaxM], lot_s[8][kMaxM];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     if (bx < rb) {
         const int j = bx * 8 + w;
@@ -393,17 +491,13 @@ __device__ __forceinline__ void rows_block(const Geometry &g, int rb, const Rang
     }
     const int j0 = (bx - rb) * 8;
     if (j0 >= counts[2]) return;  // block-uniform
-    for (int e = threadIdx.x; e < 8 * g.m; e += blockDim.x) {
-        const int k = e >> (2 * g.ln), i = e & (g.m - 1);
-        src_s[k][i] = (uint8_t)sym_src_index(sym_flags(k, g.n), g.ln, i >> g.ln, i & (g.n - 1));
-    }
     const int nch = g.KP >> 3;
     for (int e = threadIdx.x; e < 8 * nch; e += blockDim.x) kc_s[e] = (uint16_t)(((e / nch) << 8) | (e % nch));
     __syncthreads();
     const int j = j0 + w;
     if (j < counts[2])
-        domain_rows_warp(g, di, qblk, dconst, j, dact[j], lane, src_s, kc_s, hi_s[w], lo_s[w], cb32, cb16, dconst_c,
-                         dmap);
+        domain_rows_warp(g, di, qblk, dconst, j, dact[j], lane, kc_s, hi_s[w], lo_s[w], hit_s[w], lot_s[w], cb32,
+                         cb16, dconst_c, dmap);
 }
 
 __global__ void __launch_bounds__(256, 4) k_rows(Geometry g, int rb, const RangeInfo *ri, const uint16_t *bblk,
@@ -434,109 +528,185 @@ __global__ void __launch_bounds__(256, 4) k_rows_batch(const SliceCtx *__restric
 // not next to a rounding boundary, offset not clamped) are published: each is
 // within the screening allowance of a real candidate's residual, which is all
 // the search's insertion window needs.
-__device__ __forceinline__ void seed_block(const Geometry &g, const EpiConst &ec, const RangeInfo *ri,
-                                           const DomainInfo *di, const float4 *dconst, const uint16_t *bblk,
-                                           const uint16_t *qblk, const int *rkeep, int *tbest, int r)
+//
+// One warp per range, lane = domain slot, all 8 symmetries per lane: bk[k][j]
+// is the range pixel that S_k places over domain pixel j, so X(d, k) =
+// sum_j q_d[j] * bk[k][j]; q2[p][slot] holds the contracted-domain pixels 2p,
+// 2p+1 of the slot's domain (lanes read consecutive words, the bk reads are
+// broadcasts).  Per warp 96 m bytes of shared memory: 8 m ints of bk, m/2 x
+// 32 words of q2.  The loads of a warp are issued together (one round trip
+// after the keep flag for m <= 64).
+__host__ __device__ constexpr int seed_warps(int m) { return m <= 64 ? 16 : 8; }
+__host__ __device__ constexpr size_t seed_smem(int m) { return (size_t)seed_warps(m) * 96 * (size_t)m; }
+
+template <int PPL>  // range pixels per lane, at least m / 32
+__device__ __forceinline__ void seed_warp(const Geometry &g, const EpiConst &ec, const RangeInfo *ri,
+                                          const DomainInfo *di, const float4 *dconst, const uint16_t *bblk,
+                                          const uint16_t *qblk, const int *rkeep, int *tbest, int r, int lane,
+                                          int *bk, uint32_t *q2)
 {
-    // q2_s[p][slot]: contracted-domain pixels 2p, 2p+1 of the slot's domain
-    // (lanes read consecutive words); bk_s[k][j]: the range pixel that S_k
-    // places over domain pixel j, so X(d, k) = sum_j q_d[j] * bk_s[k][j]
-    __shared__ uint32_t q2_s[kMaxM / 2][32];
-    __shared__ __align__(8) int bk_s[8][kMaxM];
-    __shared__ int d_s[32];
-    if (!rkeep[r]) return;  // block-uniform: a range that is not screened
+    if (!rkeep[r]) return;  // warp-uniform: a range that is not screened
+    int d;
+    if (lane < 25) {
+        const int ry = (r / g.nx) * g.n, rx = (r % g.nx) * g.n;
+        const int v0 = min(max((ry - g.n / 2) / g.t, 0), g.V - 1);
+        const int u0 = min(max((rx - g.n / 2) / g.t, 0), g.U - 1);
+        const int v = min(max(v0 + lane / 5 - 2, 0), g.V - 1);
+        const int u = min(max(u0 + lane % 5 - 2, 0), g.U - 1);
+        d = v * g.U + u;
+    } else {
+        d = (int)(((long long)r * 2654435761LL + (long long)(lane - 25) * 40503LL) % g.D);
+    }
+    int bv[PPL];
+#pragma unroll
+    for (int j = 0; j < PPL; ++j) {
+        const int i = lane + 32 * j;
+        bv[j] = i < g.m ? (int)bblk[(size_t)r * g.m + i] : 0;
+    }
+    const uint4 *qrow = reinterpret_cast<const uint4 *>(qblk + (size_t)d * g.m);
+    const int nv = g.m >> 3;  // 16-byte vectors of the slot's domain row
+    uint4 qv[8];
+#pragma unroll
+    for (int v = 0; v < 8; ++v) qv[v] = v < nv ? __ldg(qrow + v) : make_uint4(0, 0, 0, 0);
     const RangeInfo rin = ri[r];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (threadIdx.x < 32) {
-        const int slot_d = threadIdx.x;
-        int d;
-        if (slot_d < 25) {
-            const int ry = (r / g.nx) * g.n, rx = (r % g.nx) * g.n;
-            const int v0 = min(max((ry - g.n / 2) / g.t, 0), g.V - 1);
-            const int u0 = min(max((rx - g.n / 2) / g.t, 0), g.U - 1);
-            const int v = min(max(v0 + slot_d / 5 - 2, 0), g.V - 1);
-            const int u = min(max(u0 + slot_d % 5 - 2, 0), g.U - 1);
-            d = v * g.U + u;
-        } else {
-            d = (int)(((long long)r * 2654435761LL + (long long)(slot_d - 25) * 40503LL) % g.D);
-        }
-        d_s[slot_d] = d;
-    }
-    {
-        // one symmetry per warp: no divergence in sym_src
-        const int k = warp;
-        for (int i = lane; i < g.m; i += 32) {
-            int sy, sx;
-            sym_src(k, g.n, i >> g.ln, i & (g.n - 1), sy, sx);
-            bk_s[k][(sy << g.ln) + sx] = bblk[(size_t)r * g.m + i];
+    const DomainInfo dd = di[d];
+    const float4 c4 = dconst[d];
+#pragma unroll
+    for (int j = 0; j < PPL; ++j) {
+        const int i = lane + 32 * j;
+        if (i < g.m) {
+            const int y = i >> g.ln, x = i & (g.n - 1);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                int sy, sx;
+                sym_src(k, g.n, y, x, sy, sx);
+                bk[k * g.m + (sy << g.ln) + sx] = bv[j];
+            }
         }
     }
-    __syncthreads();
-    // 16-byte loads of the 32 domain rows (m/8 vectors each)
-    const int nv = g.m >> 3;
-    for (int e = threadIdx.x; e < 32 * nv; e += blockDim.x) {
-        const int sl = e & 31, v = e >> 5;
-        const uint4 w = __ldg(reinterpret_cast<const uint4 *>(qblk + (size_t)d_s[sl] * g.m) + v);
-        q2_s[4 * v + 0][sl] = w.x;
-        q2_s[4 * v + 1][sl] = w.y;
-        q2_s[4 * v + 2][sl] = w.z;
-        q2_s[4 * v + 3][sl] = w.w;
+    for (int v0 = 0; v0 < nv; v0 += 8) {
+        if (v0 > 0) {  // rows longer than 8 vectors (m = 256)
+#pragma unroll
+            for (int v = 0; v < 8; ++v) qv[v] = v0 + v < nv ? __ldg(qrow + v0 + v) : make_uint4(0, 0, 0, 0);
+        }
+#pragma unroll
+        for (int v = 0; v < 8; ++v) {
+            if (v0 + v < nv) {
+                q2[(4 * (v0 + v) + 0) * 32 + lane] = qv[v].x;
+                q2[(4 * (v0 + v) + 1) * 32 + lane] = qv[v].y;
+                q2[(4 * (v0 + v) + 2) * 32 + lane] = qv[v].z;
+                q2[(4 * (v0 + v) + 3) * 32 + lane] = qv[v].w;
+            }
+        }
     }
-    __syncthreads();
-    const int k = warp;
-    const int slot_d = lane;
-    const int d = d_s[slot_d];
-    unsigned long long X = 0;
+    __syncwarp();
+    unsigned long long X[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) X[k] = 0;
     for (int p0 = 0; p0 < (g.m >> 1); p0 += 4) {
-        // eight products of at most 4P * P < 2^26: exact in 32 bits
-        uint32_t s = 0;
+        // eight products of at most 4P * P < 2^26 per partial: exact in 32 bits
+        uint32_t s8[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) s8[k] = 0;
 #pragma unroll
         for (int p = p0; p < p0 + 4; ++p) {
-            const uint32_t q2 = q2_s[p][slot_d];
-            const int2 b2 = *reinterpret_cast<const int2 *>(&bk_s[k][2 * p]);
-            s += (q2 & 0xffffu) * (uint32_t)b2.x + (q2 >> 16) * (uint32_t)b2.y;
+            const uint32_t w = q2[p * 32 + lane];
+            const uint32_t qa = w & 0xffffu, qb = w >> 16;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int2 b2 = *reinterpret_cast<const int2 *>(bk + k * g.m + 2 * p);
+                s8[k] += qa * (uint32_t)b2.x + qb * (uint32_t)b2.y;
+            }
         }
-        X += s;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) X[k] += s8[k];
     }
-    const DomainInfo dd = di[d];
-    const long long num = (long long)g.m * (long long)X - dd.Sq * rin.Sb;  // exact
-    const float Xt = __ll2float_rn(num) * ec.invm;
-    const float4 c4 = dconst[d];
     const RangeEpi re = range_epi(rin, ec);
-    float rho;
-    const float c = epi_code(Xt, c4.x, 0.5f, ec, rho);
-    if (fabsf(rho) > re.rho_lim) return;
-    const float ostar = (re.Sb - c * c4.w * ec.inv4ls) * ec.invm;
-    if (!(ostar < ec.pmax)) return;
-    atomicMin(tbest + r, f2ord(epi_key(Xt, -0.0f, c, re.zb, c4, ec)));
+    const long long sqsb = dd.Sq * rin.Sb;
+    int best = 0x7fffffff;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const long long num = (long long)g.m * (long long)X[k] - sqsb;  // exact
+        const float Xt = __ll2float_rn(num) * ec.invm;
+        float rho;
+        const float c = epi_code(Xt, c4.x, 0.5f, ec, rho);
+        if (fabsf(rho) > re.rho_lim) continue;
+        const float ostar = (re.Sb - c * c4.w * ec.inv4ls) * ec.invm;
+        if (!(ostar < ec.pmax)) continue;
+        best = min(best, f2ord(epi_key(Xt, -0.0f, c, re.zb, c4, ec)));
+    }
+    best = __reduce_min_sync(0xffffffffu, best);
+    if (lane == 0 && best != 0x7fffffff) atomicMin(tbest + r, best);
 }
 
 // Compaction (blocks 0 and 1: ranges, domains) and, when seed != 0, the
-// seeds (one block per range after them) in one launch: both need only the
+// seeds (T/32 ranges per block after them) in one launch: both need only the
 // statistics, so the seeds run beside the two compaction blocks.
-__global__ void __launch_bounds__(256) k_compact_seed(Geometry g, EpiConst ec, int seed, const RangeInfo *ri,
-                                                      const DomainInfo *di, const float4 *dconst,
-                                                      const uint16_t *bblk, const uint16_t *qblk, const int *rkeep,
-                                                      const int *dkeep, int *act, int *dact, int *counts, int *tbest)
+template <int T>
+__device__ __forceinline__ void compact_seed_block(const Geometry &g, const EpiConst &ec, int seed,
+                                                   const RangeInfo *ri, const DomainInfo *di, const float4 *dconst,
+                                                   const uint16_t *bblk, const uint16_t *qblk, const int *rkeep,
+                                                   const int *dkeep, int *act, int *dact, int *counts, int *tbest,
+                                                   int bx)
 {
-    grid_dep_sync();
-    if (blockIdx.x < 2)
-        compact_block<256>(g.R, rkeep, act, counts + 0, g.D, dkeep, dact, counts + 2, blockIdx.x == 1);
-    else if (seed)
-        seed_block(g, ec, ri, di, dconst, bblk, qblk, rkeep, tbest, blockIdx.x - 2);
+    extern __shared__ __align__(16) int seed_sm[];
+    if (bx < 2) {
+        compact_block<T>(g.R, rkeep, act, counts + 0, g.D, dkeep, dact, counts + 2, bx == 1);
+        return;
+    }
+    if (!seed) return;
+    // block b takes ranges b, b + nb, b + 2 nb, ...: the screened ranges
+    // (which cluster in the image) spread evenly over the blocks
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nb = (g.R + T / 32 - 1) / (T / 32);
+    if (bx - 2 >= nb) return;
+    const int r = warp * nb + (bx - 2);
+    if (r >= g.R) return;
+    int *bk = seed_sm + warp * 24 * g.m;
+    seed_warp<T == 512 ? 2 : kMaxM / 32>(g, ec, ri, di, dconst, bblk, qblk, rkeep, tbest, r, lane, bk,
+                                         reinterpret_cast<uint32_t *>(bk + 8 * g.m));
 }
 
-__global__ void __launch_bounds__(256) k_compact_seed_batch(const SliceCtx *__restrict__ ctx)
+template <int T>
+__global__ void __launch_bounds__(T, 1) k_compact_seed(Geometry g, EpiConst ec, int seed, const RangeInfo *ri,
+                                                    const DomainInfo *di, const float4 *dconst,
+                                                    const uint16_t *bblk, const uint16_t *qblk, const int *rkeep,
+                                                    const int *dkeep, int *act, int *dact, int *counts, int *tbest)
 {
     grid_dep_sync();
-    const SliceCtx c = ctx[blockIdx.y];
+    compact_seed_block<T>(g, ec, seed, ri, di, dconst, bblk, qblk, rkeep, dkeep, act, dact, counts, tbest,
+                          blockIdx.x);
+}
+
+template <int T>
+__global__ void __launch_bounds__(T, 1) k_compact_seed_batch(const SliceCtx *__restrict__ ctx)
+{
+    grid_dep_sync();
+    const SliceCtx &c = ctx[blockIdx.y];
     const EncBufs &b = c.b;
     const CompactBufs &cb = b.cb;
-    if (blockIdx.x < 2)
-        compact_block<256>(c.g.R, cb.rkeep, cb.act, cb.counts + 0, c.g.D, cb.dkeep, cb.dact, cb.counts + 2,
-                           blockIdx.x == 1);
-    else if ((int)blockIdx.x - 2 < c.g.R)
-        seed_block(c.g, c.ec, b.ri, b.di, b.dconst, b.bblk, b.qblk, cb.rkeep, b.tbest, blockIdx.x - 2);
+    compact_seed_block<T>(c.g, c.ec, 1, b.ri, b.di, b.dconst, b.bblk, b.qblk, cb.rkeep, cb.dkeep, cb.act, cb.dact,
+                          cb.counts, b.tbest, blockIdx.x);
+}
+
+// Launch shape of the compaction + seed launch: T/32 seeded ranges per block.
+template <typename Launch>
+static cudaError_t with_seed_shape(int m, Launch &&launch)
+{
+    if (seed_warps(m) == 16) {
+        cudaError_t e = cudaFuncSetAttribute(k_compact_seed<512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)seed_smem(m));
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_compact_seed_batch<512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)seed_smem(m));
+        return e != cudaSuccess ? e : launch(k_compact_seed<512>, k_compact_seed_batch<512>, 512);
+    }
+    cudaError_t e = cudaFuncSetAttribute(k_compact_seed<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)seed_smem(m));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_compact_seed_batch<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)seed_smem(m));
+    return e != cudaSuccess ? e : launch(k_compact_seed<256>, k_compact_seed_batch<256>, 256);
 }
 
 cudaError_t launch_prep(const Geometry &g, const void *img, const EpiConst &ec, int dense, int tc_split,
@@ -549,9 +719,13 @@ cudaError_t launch_prep(const Geometry &g, const void *img, const EpiConst &ec, 
     cudaError_t e = launch_dep(k_stats, dim3(rb + db), dim3(256), 0, st, g, ec, img, dense, tc_split, active, rb, ri,
                                bblk, tbest, di, dconst, qblk, cb.rkeep, cb.dkeep, zero4);
     if (e != cudaSuccess) return e;
-    e = launch_dep(k_compact_seed, dim3(2 + (seed ? g.R : 0)), dim3(256), 0, st, g, ec, seed, (const RangeInfo *)ri,
-                   (const DomainInfo *)di, (const float4 *)dconst, (const uint16_t *)bblk, (const uint16_t *)qblk,
-                   (const int *)cb.rkeep, (const int *)cb.dkeep, cb.act, cb.dact, cb.counts, tbest);
+    const int sw = seed_warps(g.m);
+    e = with_seed_shape(g.m, [&](auto one, auto, int threads) {
+        return launch_dep(one, dim3(2 + (seed ? (g.R + sw - 1) / sw : 0)), dim3(threads), seed ? seed_smem(g.m) : 0,
+                          st, g, ec, seed, (const RangeInfo *)ri, (const DomainInfo *)di, (const float4 *)dconst,
+                          (const uint16_t *)bblk, (const uint16_t *)qblk, (const int *)cb.rkeep,
+                          (const int *)cb.dkeep, cb.act, cb.dact, cb.counts, tbest);
+    });
     if (e != cudaSuccess) return e;
     return launch_dep(k_rows, dim3(rb + db), dim3(256), 0, st, g, rb, (const RangeInfo *)ri, (const uint16_t *)bblk,
                       (const DomainInfo *)di, (const uint16_t *)qblk, (const float4 *)dconst, (const int *)cb.act,
@@ -565,10 +739,13 @@ cudaError_t launch_stats_batch(const SliceCtx *ctx, int n, int blocks, int dense
     return launch_dep(k_stats_batch, dim3(blocks, n), dim3(256), 0, st, ctx, dense, tc_split);
 }
 
-// ranges: the largest of the slices (one seed block per range)
-cudaError_t launch_compact_seed_batch(const SliceCtx *ctx, int n, int ranges, cudaStream_t st)
+// ranges, m: the largest of the slices' ranges and their common block size
+cudaError_t launch_compact_seed_batch(const SliceCtx *ctx, int n, int ranges, int m, cudaStream_t st)
 {
-    return launch_dep(k_compact_seed_batch, dim3(2 + ranges, n), dim3(256), 0, st, ctx);
+    const int sw = seed_warps(m);
+    return with_seed_shape(m, [&](auto, auto many, int threads) {
+        return launch_dep(many, dim3(2 + (ranges + sw - 1) / sw, n), dim3(threads), seed_smem(m), st, ctx);
+    });
 }
 
 cudaError_t launch_rows_batch(const SliceCtx *ctx, int n, int blocks, cudaStream_t st)
