@@ -532,6 +532,17 @@ __host__ __device__ __forceinline__ int active_splits(int row_tiles, int col_til
     return s < 1 ? 1 : s;
 }
 
+// First candidate tile of split s of ns over `tiles` tiles.  The tensor-core
+// search (column tile 96) takes its items split-major from a queue shared by
+// all CTAs, so its splits shrink from 1.5x to 0.5x the mean size (boundary
+// tiles * (3 s ns - s^2) / (2 ns^2)): the items that start last are short
+// and the SMs run out of work together.  The FP32 search's splits are equal.
+__host__ __device__ __forceinline__ int split_tile(int tiles, int s, int ns, int col_tile)
+{
+    if (col_tile != 96) return (int)((long long)tiles * s / ns);
+    return (int)((long long)tiles * (3LL * s * ns - (long long)s * s) / (2LL * ns * ns));
+}
+
 // ---------------------------------------------------------------- launches
 // (host-side wrappers, each returns cudaError_t of the launch)
 cudaError_t launch_search_simt(const Geometry &g, const EpiConst &ec, const RangeInfo *ri,

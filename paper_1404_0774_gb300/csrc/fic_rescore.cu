@@ -44,11 +44,62 @@ __device__ void fp64_codes(const Geometry &g, const Stats &st, int &c, int &e, d
     const double sc = s < -1.0 ? -1.0 : (s > 1.0 ? 1.0 : s);
     c = (int)round(__dmul_rn(sc, Ls));
     s_hat = __ddiv_rn((double)c, Ls);
-    const double o = __ddiv_rn(__dsub_rn(Sb, __dmul_rn(s_hat, Sa)), md);
+    // m is a power of two: dividing by it is an exact scaling, the same
+    // result as the multiplication by its exact reciprocal (off the chain)
+    const double o = __dmul_rn(__dsub_rn(Sb, __dmul_rn(s_hat, Sa)), ldexp(1.0, -2 * g.ln));
     const double P = (double)g.P, Lo = (double)g.Lo;
     const double oc = o < -P ? -P : (o > P ? P : o);
     e = (int)round(__ddiv_rn(__dmul_rn(oc, Lo), P));
     o_hat = __ddiv_rn(__dmul_rn((double)e, P), Lo);
+}
+
+// The code decisions of fp64_codes without its chain of dependent FP64
+// divisions (a long latency at the FP64 rate of this part).  s * Ls =
+// 4 Ls (m X - Sq Sb) / (m Sqq - Sq^2) and o * Lo / P = (4 Ls Sb - c Sq) Lo /
+// (4 Ls m P) are formed in FP32 from exact integers (relative error below
+// 4 * 2^-24); fp64_codes forms the same values with numerator and
+// denominator exact in FP64 and an error below 2^-49 * Lo.  Away from a
+// rounding boundary both round to the same code; within 4e-7 * |value| +
+// 1e-6 of one (a few in 10^5 candidates) this returns false and the caller
+// takes fp64_codes itself, so the codes are those of the FP64 sequence bit
+// for bit.  The clamps at +-Ls, +-Lo are integers, never boundaries.
+__device__ __forceinline__ bool round_clear(float v, float lim, int &code)
+{
+    const float a = fminf(fabsf(v), lim);
+    const float fl = floorf(a), fr = a - fl;  // exact
+    if (fabsf(fr - 0.5f) <= fmaf(4e-7f, a, 1e-6f)) return false;
+    const int k = (int)fl + (fr > 0.5f ? 1 : 0);
+    code = v < 0.0f ? -k : k;
+    return true;
+}
+
+__device__ __forceinline__ bool fast_codes(const Geometry &g, const Stats &st, int &c, int &e)
+{
+    const long long NI = (long long)g.m * st.X - st.Sq * st.Sb;
+    const long long DI = (long long)g.m * st.Sqq - st.Sq * st.Sq;
+    c = 0;
+    if (DI != 0 && !round_clear(__fdiv_rn(__ll2float_rn(4LL * g.Ls * NI), __ll2float_rn(DI)), (float)g.Ls, c))
+        return false;
+    const long long NE = (4LL * g.Ls * st.Sb - (long long)c * st.Sq) * g.Lo;
+    return round_clear(__fdiv_rn(__ll2float_rn(NE), __ll2float_rn(4LL * g.Ls * g.m * g.P)), (float)g.Lo, e);
+}
+
+// s_hat = c / Ls and o_hat = e P / Lo as floats: Ls and Lo are 2^k - 1, so
+// a quotient of integers by them is exact or has a binary expansion of
+// period k <= 9, which never holds the 28 equal bits after the float's last
+// place that would make the double quotient a float rounding midpoint; the
+// float rounding of the double quotient is then the correctly rounded float
+// quotient (when the numerator is exact in FP32).
+__device__ __forceinline__ float s_hat_f(const Geometry &g, int c)
+{
+    return __fdiv_rn((float)c, (float)g.Ls);
+}
+
+__device__ __forceinline__ float o_hat_f(const Geometry &g, int e)
+{
+    const long long eP = (long long)e * g.P;
+    if (eP < (1LL << 24) && eP > -(1LL << 24)) return __fdiv_rn((float)eP, (float)g.Lo);
+    return (float)__ddiv_rn((double)eP, (double)g.Lo);
 }
 
 // Exact integer arithmetic in one of two widths: 64-bit when every term of
@@ -680,7 +731,7 @@ __device__ __forceinline__ void list_scans(const Geometry &g, const RangeInfo *r
         const int code = sb.items[item];
         const int r = code >> 7, l = code & 127;
         const int sp = l / lists_per_split, part = l - sp * lists_per_split;
-        const int t0 = (int)((long long)tiles * sp / n_split), t1 = (int)((long long)tiles * (sp + 1) / n_split);
+        const int t0 = split_tile(tiles, sp, n_split, col_tile), t1 = split_tile(tiles, sp + 1, n_split, col_tile);
         __syncthreads();  // b_s and w_s of the previous item are no longer read
         for (int i = threadIdx.x; i < g.m; i += blockDim.x) b_s[i] = bblk[(size_t)r * g.m + i];
         __syncthreads();
@@ -837,6 +888,7 @@ __device__ __forceinline__ void finalize_block(const Geometry &g, const RangeInf
     __shared__ uint32_t q_s[kFinRanges][(kMaxM + 2) / 2];
     __shared__ uint32_t w_s[kFinRanges];
     __shared__ long long x_s[kFinWarps][kFinRanges];
+    __shared__ long long st_s[4][kFinRanges];  // Sq, Sqq of the winner's domain; Sb, Sbb of the range
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int r0 = bx * kFinRanges;
     const int nr = min(kFinRanges, g.R - r0);
@@ -868,6 +920,12 @@ __device__ __forceinline__ void finalize_block(const Geometry &g, const RangeInf
         bd[0] = bw.x, bd[1] = bw.y, bd[2] = bw.z, bd[3] = bw.w;
         qd[0] = qw.x, qd[1] = qw.y, qd[2] = qw.z, qd[3] = qw.w;
     }
+    if (warp == 0 && live) {
+        st_s[0][lane] = dd.Sq;
+        st_s[1][lane] = dd.Sqq;
+        st_s[2][lane] = rin.Sb;
+        st_s[3][lane] = rin.Sbb;
+    }
     __syncthreads();
     {
         // rows [warp*n/4, (warp+1)*n/4) of range `lane` (n >= 4)
@@ -884,26 +942,41 @@ __device__ __forceinline__ void finalize_block(const Geometry &g, const RangeInf
         x_s[warp][lane] = X;
     }
     __syncthreads();
-    if (warp != 0 || !live) return;
+    // The FP64 part, a long dependent chain at the FP64 rate of this part:
+    // spread over all warps of the block, kFinRanges / kFinWarps lanes each.
+    constexpr int kPer = kFinRanges / kFinWarps;
+    const int jr = warp * kPer + lane;  // the range of this lane
+    if (lane >= kPer || jr >= nr) return;
     long long X = 0;
 #pragma unroll
-    for (int w = 0; w < kFinWarps; ++w) X += x_s[w][lane];
-    Stats st{dd.Sq, dd.Sqq, rin.Sb, rin.Sbb, X};
+    for (int w = 0; w < kFinWarps; ++w) X += x_s[w][jr];
+    Stats st{st_s[0][jr], st_s[1][jr], st_s[2][jr], st_s[3][jr], X};
+    const uint32_t wj = w_s[jr];
+    uint32_t ij = wj & 0x7fffffffu;
+    if (ij >= (uint32_t)g.N) ij = 0;
     int c, e;
-    double sh, oh;
-    fp64_codes(g, st, c, e, sh, oh);
+    float sf, of;
+    if (fast_codes(g, st, c, e)) {
+        sf = s_hat_f(g, c);
+        of = o_hat_f(g, e);
+    } else {  // next to a rounding boundary: the FP64 sequence decides
+        double sh, oh;
+        fp64_codes(g, st, c, e, sh, oh);
+        sf = (float)sh;
+        of = (float)oh;
+    }
     const double invD2 = 1.0 / ((double)(4 * g.Ls * g.Lo) * (double)(4 * g.Ls * g.Lo));
     fic_map mp;
-    mp.range_idx = (uint32_t)r;
-    mp.domain_idx = (uint32_t)d;
-    mp.iso = k;
+    mp.range_idx = (uint32_t)(r0 + jr);
+    mp.domain_idx = ij >> 3;
+    mp.iso = ij & 7;
     mp.s_code = c;
     mp.o_code = e;
-    mp.s = (float)sh;
-    mp.o = (float)oh;
-    mp.info = ((wv & 0x80000000u) ? FIC_MAP_FALLBACK : 0u) | (*err ? FIC_MAP_ERROR : 0u);
+    mp.s = sf;
+    mp.o = of;
+    mp.info = ((wj & 0x80000000u) ? FIC_MAP_FALLBACK : 0u) | (*err ? FIC_MAP_ERROR : 0u);
     mp.err = u128_to_double((unsigned __int128)exact_err<true>(g, st, c, e)) * invD2;
-    maps[r] = mp;
+    maps[r0 + jr] = mp;
 }
 
 __global__ void __launch_bounds__(32 * kFinWarps) k_finalize(Geometry g, const RangeInfo *ri, const DomainInfo *di,

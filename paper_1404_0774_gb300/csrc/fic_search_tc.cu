@@ -262,8 +262,9 @@ __device__ __forceinline__ TcItem tc_item(const SliceCtx *ctx, const int *ip_s, 
     it.r0 = (local - it.split * nrt) * BM;
     const int ncol = 8 * ctx[lo].b.cb.counts[2];
     const int tiles = (ncol + BN - 1) / BN;
-    it.t_begin = (int)((long long)tiles * it.split / ns);
-    it.t_end = (int)((long long)tiles * (it.split + 1) / ns);
+    static_assert(BN == 96, "split_tile recognises the tensor-core search by its 96-column tile");
+    it.t_begin = split_tile(tiles, it.split, ns, BN);
+    it.t_end = split_tile(tiles, it.split + 1, ns, BN);
     return it;
 }
 
