@@ -884,7 +884,7 @@ cudaError_t batch_pipeline(const BatchPlan &P, const fic_params *p, char *ws, in
     auto ranges_of = [&](int k) { return P.sl[P.order[k0 + k]].g.R; };
     cudaError_t e = cudaSuccess;
     for (auto &gr : groups)
-        if ((e = launch_stats_batch(dctx + gr.first, gr.second, blocks_of(gr.first), dense,
+        if ((e = launch_stats_batch(dctx + gr.first, gr.second, stats_grid(P.sl[P.order[k0 + gr.first]].g), dense,
                                     (tc && g0.split_hilo) ? 1 : 0, st)) != cudaSuccess)
             return e;
     for (auto &gr : groups)

@@ -562,6 +562,7 @@ int search_simt_lists_per_split();
 // Batched encode of n slices (ctx: device array of their contexts), one
 // launch per stage over the slices (the per-slice stages: once per group of
 // equal slices).
+int stats_grid(const Geometry &g);  // blocks of the statistics launch of one slice
 cudaError_t launch_stats_batch(const SliceCtx *ctx, int n, int blocks, int dense, int tc_split, cudaStream_t st);
 cudaError_t launch_compact_seed_batch(const SliceCtx *ctx, int n, int ranges, int m, cudaStream_t st);
 cudaError_t launch_rows_batch(const SliceCtx *ctx, int n, int blocks, cudaStream_t st);

@@ -10,69 +10,75 @@
 
 namespace fic {
 
-__device__ __forceinline__ long long warp_sum_ll(long long v)
+// Lanes per range or domain in the statistics kernel: G = m / 8 (8 pixels a
+// lane; m = 256 takes the whole warp), so a warp holds 32 / G items whose
+// sums reduce within their lane groups and whose per-item tails run side by
+// side.
+__host__ __device__ __forceinline__ int stats_group(int m) { return m >= 256 ? 32 : m / 8; }
+__host__ __device__ __forceinline__ int stats_items(int m) { return 8 * (32 / stats_group(m)); }  // per block
+__host__ __device__ __forceinline__ int stats_range_blocks(const Geometry &g)
 {
-    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    return (g.R + stats_items(g.m) - 1) / stats_items(g.m);
+}
+__host__ __device__ __forceinline__ int stats_blocks(const Geometry &g)
+{
+    return stats_range_blocks(g) + (g.D + stats_items(g.m) - 1) / stats_items(g.m);
+}
+
+// Sum over the G lanes of a group (G a power of two; every lane of the warp
+// takes part).
+template <typename T>
+__device__ __forceinline__ T group_sum(T v, int G)
+{
+    for (int off = G >> 1; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
     return v;
 }
 
-// One warp per range (lanes over pixels): statistics, centre, allowances,
-// and the keep flag (every range but shadow ranges, or all when dense).
+// G lanes per range (li = lane within the group, 8 pixels each): statistics,
+// centre, allowances, and the keep flag (every range but shadow ranges, or
+// all when dense).  `valid` is false for the lanes of a group past the last
+// range: they take part in the reductions only.
 __device__ __forceinline__ void range_stats(const Geometry &g, const EpiConst &ec, const void *img, int dense,
-                                            int tc_split, const int *active, int r, int lane, RangeInfo *ri,
-                                            uint16_t *bblk, int *tbest, int *rkeep)
+                                            int tc_split, const int *active, int r, bool valid, int li, int G,
+                                            RangeInfo *ri, uint16_t *bblk, int *tbest, int *rkeep)
 {
-    const int ry = (r / g.nx) * g.n, rx = (r % g.nx) * g.n;
-    constexpr int PPL = kMaxM / 32;  // pixels per lane, upper bound
-    int bv[PPL];
+    const int rr = valid ? r : 0;
+    const int ry = (rr / g.nx) * g.n, rx = (rr % g.nx) * g.n;
+    int bv[8];
     long long Sb = 0, Sbb = 0;
     int bmin = 1 << 30, bmax = -1;
     // every load issued before the first use (no store between them)
     const bool b8 = g.B <= 8;
 #pragma unroll
-    for (int j = 0; j < PPL; ++j) {
-        if (32 * j >= g.m) break;  // warp-uniform
-        const int i = lane + 32 * j;
-        const size_t off = (size_t)(ry + i / g.n) * g.pitch + rx + i % g.n;
-        bv[j] = i < g.m ? (b8 ? (int)((const uint8_t *)img)[off] : (int)((const uint16_t *)img)[off]) : 0;
+    for (int j = 0; j < 8; ++j) {
+        const int i = li + G * j;
+        const size_t off = (size_t)(ry + (i >> g.ln)) * g.pitch + rx + (i & (g.n - 1));
+        bv[j] = valid ? (b8 ? (int)((const uint8_t *)img)[off] : (int)((const uint16_t *)img)[off]) : 0;
     }
 #pragma unroll
-    for (int j = 0; j < PPL; ++j) {
-        if (32 * j >= g.m) break;
-        const int i = lane + 32 * j;
-        if (i < g.m) {
-            const int b = bv[j];
-            Sb += b;
-            Sbb += (long long)b * b;
-            bmin = min(bmin, b);
-            bmax = max(bmax, b);
-            bblk[(size_t)r * g.m + i] = (uint16_t)b;
-        }
+    for (int j = 0; j < 8; ++j) {
+        const int b = bv[j];
+        Sb += b;
+        Sbb += (long long)b * b;
+        bmin = min(bmin, b);
+        bmax = max(bmax, b);
+        if (valid) bblk[(size_t)rr * g.m + li + G * j] = (uint16_t)b;
     }
-    Sb = warp_sum_ll(Sb);
-    Sbb = warp_sum_ll(Sbb);
-    for (int off = 16; off > 0; off >>= 1) {
+    Sb = group_sum(Sb, G);
+    Sbb = group_sum(Sbb, G);
+    for (int off = G >> 1; off > 0; off >>= 1) {
         bmin = min(bmin, __shfl_xor_sync(0xffffffffu, bmin, off));
         bmax = max(bmax, __shfl_xor_sync(0xffffffffu, bmax, off));
     }
+    if (!valid || li != 0) return;
     // centre: nearest integer to the mean, kept within 2048 of every pixel so
     // that b - c_r is an exact FP16 integer
     long long cr = (2 * Sb + g.m) >> (2 * g.ln + 1);  // m = 2^(2 ln), Sb >= 0
     cr = max((long long)(bmax - 2048), min((long long)(bmin + 2048), cr));
     const int c_r = (int)cr;
     const int e_r = (int)(Sb - (long long)g.m * c_r);
-    long long bp2i = 0;
-#pragma unroll
-    for (int j = 0; j < PPL; ++j) {
-        if (32 * j >= g.m) break;
-        const int i = lane + 32 * j;
-        if (i < g.m) {
-            const int bc = bv[j] - c_r;
-            bp2i += (long long)bc * bc;
-        }
-    }
-    const float bp2f = __ll2float_rn(warp_sum_ll(bp2i));
-    if (lane != 0) return;
+    // sum (b - c_r)^2, exactly
+    const float bp2f = __ll2float_rn(Sbb - 2 * cr * Sb + (long long)g.m * cr * cr);
     // per-range constants: integer arithmetic and FP32 only (the FP64 rate of
     // this part is a small fraction of FP32)
     RangeInfo info;
@@ -119,28 +125,27 @@ __device__ __forceinline__ void range_stats(const Geometry &g, const EpiConst &e
 }
 
 
-// One warp per domain (lanes over the contracted pixels): the 2x2 sums q
-// (tau as an integer sum, the mean being q/4), Sq, Sqq, centre, the epilogue
-// column constants, and the keep flag (every domain but flat ones, den = 0,
-// or all when dense).
-__device__ __forceinline__ void domain_stats(const Geometry &g, const void *img, int dense, int d, int lane,
-                                             DomainInfo *di, float4 *dconst, uint16_t *qblk, int *dkeep)
+// G lanes per domain (li = lane within the group, 8 contracted pixels
+// each): the 2x2 sums q (tau as an integer sum, the mean being q/4), Sq, Sqq,
+// centre, the epilogue column constants, and the keep flag (every domain but
+// flat ones, den = 0, or all when dense).
+__device__ __forceinline__ void domain_stats(const Geometry &g, const void *img, int dense, int d, bool valid,
+                                             int li, int G, DomainInfo *di, float4 *dconst, uint16_t *qblk,
+                                             int *dkeep)
 {
-    const int du = d % g.U;
-    const int dy = (d / g.U) * g.t, dx = du * g.t;
+    const int dd0 = valid ? d : 0;
+    const int dy = (dd0 / g.U) * g.t, dx = (dd0 % g.U) * g.t;
     long long Sq = 0, Sqq = 0;
-    constexpr int QPL = kMaxM / 32;  // contracted pixels per lane, upper bound
-    int qv[QPL];
+    int qv[8];
     const bool b8 = g.B <= 8;
     // every load issued before the first store
 #pragma unroll
-    for (int j = 0; j < QPL; ++j) {
-        if (32 * j >= g.m) break;  // warp-uniform
-        const int i = lane + 32 * j;
+    for (int j = 0; j < 8; ++j) {
+        const int i = li + G * j;
         const int y = i >> g.ln, x = i & (g.n - 1);
         const size_t o0 = (size_t)(dy + 2 * y) * g.pitch + dx + 2 * x;
         int q = 0;
-        if (i < g.m) {
+        if (valid) {
             if (b8) {
                 const uint8_t *p8 = (const uint8_t *)img;
                 q = (int)p8[o0] + (int)p8[o0 + 1] + (int)p8[o0 + g.pitch] + (int)p8[o0 + g.pitch + 1];
@@ -152,19 +157,15 @@ __device__ __forceinline__ void domain_stats(const Geometry &g, const void *img,
         qv[j] = q;
     }
 #pragma unroll
-    for (int j = 0; j < QPL; ++j) {
-        if (32 * j >= g.m) break;
-        const int i = lane + 32 * j;
-        if (i < g.m) {
-            const int q = qv[j];
-            qblk[(size_t)d * g.m + i] = (uint16_t)q;
-            Sq += q;
-            Sqq += (long long)q * q;
-        }
+    for (int j = 0; j < 8; ++j) {
+        const int q = qv[j];
+        if (valid) qblk[(size_t)d * g.m + li + G * j] = (uint16_t)q;
+        Sq += q;
+        Sqq += (long long)q * q;
     }
-    Sq = warp_sum_ll(Sq);
-    Sqq = warp_sum_ll(Sqq);
-    if (lane != 0) return;
+    Sq = group_sum(Sq, G);
+    Sqq = group_sum(Sqq, G);
+    if (!valid || li != 0) return;
     const int m = g.m;
     const long long cd = (2 * Sq + m) >> (2 * g.ln + 1);  // m = 2^(2 ln), Sq >= 0
     const long long den = (long long)m * Sqq - Sq * Sq;
@@ -187,31 +188,33 @@ __device__ __forceinline__ void domain_stats(const Geometry &g, const void *img,
     dkeep[d] = dense || den != 0;
 }
 
-// Statistics of every range (blocks [0, rb), a warp each) and every domain
-// (the blocks after), one launch.
+// Statistics of every range (the first stats_range_blocks blocks) and every
+// domain (the blocks after), one launch; stats_items per block of 256.
 __device__ __forceinline__ void stats_block(const Geometry &g, const EpiConst &ec, const void *img, int dense,
-                                            int tc_split, const int *active, int rb, RangeInfo *ri, uint16_t *bblk,
+                                            int tc_split, const int *active, RangeInfo *ri, uint16_t *bblk,
                                             int *tbest, DomainInfo *di, float4 *dconst, uint16_t *qblk, int *rkeep,
                                             int *dkeep, int *zero4, int bx)
 {
     if (bx == 0 && threadIdx.x < 4) zero4[threadIdx.x] = 0;  // exact-scan queue counters
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    if (bx < rb) {
-        const int r = bx * 8 + w;
-        if (r < g.R) range_stats(g, ec, img, dense, tc_split, active, r, lane, ri, bblk, tbest, rkeep);
+    const int G = stats_group(g.m), per_block = stats_items(g.m), rbs = stats_range_blocks(g);
+    const int li = threadIdx.x & (G - 1);
+    const int item = threadIdx.x / G;  // (warp, group) in order
+    if (bx < rbs) {
+        const int r = bx * per_block + item;
+        range_stats(g, ec, img, dense, tc_split, active, r, r < g.R, li, G, ri, bblk, tbest, rkeep);
     } else {
-        const int d = (bx - rb) * 8 + w;
-        if (d < g.D) domain_stats(g, img, dense, d, lane, di, dconst, qblk, dkeep);
+        const int d = (bx - rbs) * per_block + item;
+        domain_stats(g, img, dense, d, d < g.D, li, G, di, dconst, qblk, dkeep);
     }
 }
 
 __global__ void __launch_bounds__(256) k_stats(Geometry g, EpiConst ec, const void *img, int dense, int tc_split,
-                                               const int *active, int rb, RangeInfo *ri, uint16_t *bblk, int *tbest,
+                                               const int *active, RangeInfo *ri, uint16_t *bblk, int *tbest,
                                                DomainInfo *di, float4 *dconst, uint16_t *qblk, int *rkeep,
                                                int *dkeep, int *zero4)
 {
     grid_dep_sync();
-    stats_block(g, ec, img, dense, tc_split, active, rb, ri, bblk, tbest, di, dconst, qblk, rkeep, dkeep, zero4,
+    stats_block(g, ec, img, dense, tc_split, active, ri, bblk, tbest, di, dconst, qblk, rkeep, dkeep, zero4,
                 blockIdx.x);
 }
 
@@ -220,9 +223,9 @@ __global__ void __launch_bounds__(256) k_stats_batch(const SliceCtx *__restrict_
 {
     grid_dep_sync();
     const SliceCtx c = ctx[blockIdx.y];
-    if ((int)blockIdx.x >= c.rb + c.db) return;
+    if ((int)blockIdx.x >= stats_blocks(c.g)) return;
     const EncBufs &b = c.b;
-    stats_block(c.g, c.ec, c.img, dense, tc_split, nullptr, c.rb, b.ri, b.bblk, b.tbest, b.di, b.dconst, b.qblk,
+    stats_block(c.g, c.ec, c.img, dense, tc_split, nullptr, b.ri, b.bblk, b.tbest, b.di, b.dconst, b.qblk,
                 b.cb.rkeep, b.cb.dkeep, b.fb_count, blockIdx.x);
 }
 
@@ -716,8 +719,8 @@ cudaError_t launch_prep(const Geometry &g, const void *img, const EpiConst &ec, 
                         int seed, cudaStream_t st)
 {
     const int rb = (g.R + 7) / 8, db = (g.D + 7) / 8;
-    cudaError_t e = launch_dep(k_stats, dim3(rb + db), dim3(256), 0, st, g, ec, img, dense, tc_split, active, rb, ri,
-                               bblk, tbest, di, dconst, qblk, cb.rkeep, cb.dkeep, zero4);
+    cudaError_t e = launch_dep(k_stats, dim3(stats_blocks(g)), dim3(256), 0, st, g, ec, img, dense, tc_split, active,
+                               ri, bblk, tbest, di, dconst, qblk, cb.rkeep, cb.dkeep, zero4);
     if (e != cudaSuccess) return e;
     const int sw = seed_warps(g.m);
     e = with_seed_shape(g.m, [&](auto one, auto, int threads) {
@@ -734,6 +737,8 @@ cudaError_t launch_prep(const Geometry &g, const void *img, const EpiConst &ec, 
 
 // Batched prep stages of n slices (ctx: device array; blocks / ranges: the
 // largest slice's, so a group of equal slices wastes no blocks).
+int stats_grid(const Geometry &g) { return stats_blocks(g); }
+
 cudaError_t launch_stats_batch(const SliceCtx *ctx, int n, int blocks, int dense, int tc_split, cudaStream_t st)
 {
     return launch_dep(k_stats_batch, dim3(blocks, n), dim3(256), 0, st, ctx, dense, tc_split);
