@@ -476,51 +476,58 @@ __device__ __forceinline__ void domain_rows_warp(const Geometry &g, const Domain
     }
 }
 
-// Operand rows of the kept ranges (blocks [0, rb), a warp per row) and of the
-// kept domains (the blocks after, a warp per domain), one launch.  Domain
-// blocks first build the (row, chunk) table of their 16-byte chunks.
-__device__ __forceinline__ void rows_block(const Geometry &g, int rb, const RangeInfo *ri, const uint16_t *bblk,
+// Operand rows of the kept ranges (a warp per row) and of the kept domains
+// (a warp per domain), one launch.  The rows come in groups of 8 (one per
+// warp): first the range groups, then the domain groups, as many as the
+// compaction kept; block `first` takes every stride-th group, so a grid of
+// resident blocks covers them with no block spent on nothing.
+constexpr int kRowsBlocksPerSm = 5;  // resident at 48 registers x 256 threads
+__device__ __forceinline__ void rows_block(const Geometry &g, const RangeInfo *ri, const uint16_t *bblk,
                                            const DomainInfo *di, const uint16_t *qblk, const float4 *dconst,
                                            const int *act, const int *dact, const int *counts, float *rs32,
-                                           __half *ra16, float *cb32, __half *cb16, float4 *dconst_c, int *dmap, int bx)
+                                           __half *ra16, float *cb32, __half *cb16, float4 *dconst_c, int *dmap,
+                                           int first, int stride)
 {
     __shared__ uint16_t kc_s[8 * ((2 * kMaxM + 16) / 8)];
     __shared__ __align__(16) uint16_t hi_s[8][kMaxM], lo_s[8][kMaxM], hit_s[8][kMaxM], lot_s[8][kMaxM];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    if (bx < rb) {
-        const int j = bx * 8 + w;
-        if (j < counts[0]) range_row(g, ri, bblk, j, act[j], lane, rs32, ra16);
-        return;
-    }
-    const int j0 = (bx - rb) * 8;
-    if (j0 >= counts[2]) return;  // block-uniform
     const int nch = g.KP >> 3;
     for (int e = threadIdx.x; e < 8 * nch; e += blockDim.x) kc_s[e] = (uint16_t)(((e / nch) << 8) | (e % nch));
     __syncthreads();
-    const int j = j0 + w;
-    if (j < counts[2])
-        domain_rows_warp(g, di, qblk, dconst, j, dact[j], lane, kc_s, hi_s[w], lo_s[w], hit_s[w], lot_s[w], cb32,
-                         cb16, dconst_c, dmap);
+    const int nr = counts[0], nd = counts[2];
+    const int rgroups = (nr + 7) / 8, groups = rgroups + (nd + 7) / 8;
+    for (int vb = first; vb < groups; vb += stride) {
+        if (vb < rgroups) {
+            const int j = vb * 8 + w;
+            if (j < nr) range_row(g, ri, bblk, j, act[j], lane, rs32, ra16);
+        } else {
+            const int j = (vb - rgroups) * 8 + w;
+            if (j < nd) {
+                __syncwarp();  // the warp's staging arrays of its previous domain are read
+                domain_rows_warp(g, di, qblk, dconst, j, dact[j], lane, kc_s, hi_s[w], lo_s[w], hit_s[w], lot_s[w],
+                                 cb32, cb16, dconst_c, dmap);
+            }
+        }
+    }
 }
 
-__global__ void __launch_bounds__(256, 4) k_rows(Geometry g, int rb, const RangeInfo *ri, const uint16_t *bblk,
+__global__ void __launch_bounds__(256, kRowsBlocksPerSm) k_rows(Geometry g, const RangeInfo *ri, const uint16_t *bblk,
                                               const DomainInfo *di, const uint16_t *qblk, const float4 *dconst,
                                               const int *act, const int *dact, const int *counts, float *rs32,
                                               __half *ra16, float *cb32, __half *cb16, float4 *dconst_c, int *dmap)
 {
     grid_dep_sync();
-    rows_block(g, rb, ri, bblk, di, qblk, dconst, act, dact, counts, rs32, ra16, cb32, cb16, dconst_c, dmap,
-               blockIdx.x);
+    rows_block(g, ri, bblk, di, qblk, dconst, act, dact, counts, rs32, ra16, cb32, cb16, dconst_c, dmap, blockIdx.x,
+               gridDim.x);
 }
 
-__global__ void __launch_bounds__(256, 4) k_rows_batch(const SliceCtx *__restrict__ ctx)
+__global__ void __launch_bounds__(256, kRowsBlocksPerSm) k_rows_batch(const SliceCtx *__restrict__ ctx)
 {
     grid_dep_sync();
-    const SliceCtx c = ctx[blockIdx.y];
-    if ((int)blockIdx.x >= c.rb + c.db) return;
+    const SliceCtx &c = ctx[blockIdx.y];
     const EncBufs &b = c.b;
-    rows_block(c.g, c.rb, b.ri, b.bblk, b.di, b.qblk, b.dconst, b.cb.act, b.cb.dact, b.cb.counts, b.rs32, b.ra16,
-               b.cb32, b.cb16, b.cb.dconst_c, b.cb.dmap, blockIdx.x);
+    rows_block(c.g, b.ri, b.bblk, b.di, b.qblk, b.dconst, b.cb.act, b.cb.dact, b.cb.counts, b.rs32, b.ra16, b.cb32,
+               b.cb16, b.cb.dconst_c, b.cb.dmap, blockIdx.x, gridDim.x);
 }
 
 
@@ -712,6 +719,21 @@ static cudaError_t with_seed_shape(int m, Launch &&launch)
     return e != cudaSuccess ? e : launch(k_compact_seed<256>, k_compact_seed_batch<256>, 256);
 }
 
+// SMs of the current device (queried once).
+static int prep_sms()
+{
+    static int n = 0;
+    if (n <= 0) {
+        int dev = 0, v = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) ==
+                                                     cudaSuccess && v > 0)
+            n = v;
+        else
+            return 1;
+    }
+    return n;
+}
+
 cudaError_t launch_prep(const Geometry &g, const void *img, const EpiConst &ec, int dense, int tc_split,
                         const int *active,
                         RangeInfo *ri, DomainInfo *di, float4 *dconst, uint16_t *bblk, uint16_t *qblk, float *rs32,
@@ -730,7 +752,8 @@ cudaError_t launch_prep(const Geometry &g, const void *img, const EpiConst &ec, 
                           (const int *)cb.dkeep, cb.act, cb.dact, cb.counts, tbest);
     });
     if (e != cudaSuccess) return e;
-    return launch_dep(k_rows, dim3(rb + db), dim3(256), 0, st, g, rb, (const RangeInfo *)ri, (const uint16_t *)bblk,
+    const int blocks = std::max(1, std::min(rb + db, kRowsBlocksPerSm * prep_sms()));
+    return launch_dep(k_rows, dim3(blocks), dim3(256), 0, st, g, (const RangeInfo *)ri, (const uint16_t *)bblk,
                       (const DomainInfo *)di, (const uint16_t *)qblk, (const float4 *)dconst, (const int *)cb.act,
                       (const int *)cb.dact, (const int *)cb.counts, rs32, ra16, cb32, cb16, cb.dconst_c, cb.dmap);
 }
@@ -755,7 +778,8 @@ cudaError_t launch_compact_seed_batch(const SliceCtx *ctx, int n, int ranges, in
 
 cudaError_t launch_rows_batch(const SliceCtx *ctx, int n, int blocks, cudaStream_t st)
 {
-    return launch_dep(k_rows_batch, dim3(blocks, n), dim3(256), 0, st, ctx);
+    const int x = std::max(1, std::min(blocks, kRowsBlocksPerSm * prep_sms() / std::max(1, n)));
+    return launch_dep(k_rows_batch, dim3(x, n), dim3(256), 0, st, ctx);
 }
 
 
