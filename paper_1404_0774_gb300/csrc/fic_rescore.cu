@@ -617,6 +617,43 @@ __global__ void __launch_bounds__(32 * kRescoreWarps, 4)
 
 
 
+// The range's pixels permuted for each symmetry, staged by the whole block:
+// bk[k*(m+1) + j] is the range pixel that S_k places over contracted-domain
+// pixel j (the layout of stage_sym_pixels).
+__device__ __forceinline__ void stage_sym_block(const Geometry &g, const uint16_t *bblk, int r, int *bk)
+{
+    for (int i = threadIdx.x; i < g.m; i += blockDim.x) {
+        const int b = bblk[(size_t)r * g.m + i];
+        const int y = i >> g.ln, x = i & (g.n - 1);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            int sy, sx;
+            sym_src(k, g.n, y, x, sy, sx);
+            bk[k * (g.m + 1) + (sy << g.ln) + sx] = b;
+        }
+    }
+}
+
+// Exact X of one candidate: its contracted-domain row qd read in natural
+// order, 16 bytes at a time, against the staged row bkk = bk + k*(m+1).
+// Eight products of at most 4P * P < 2^26 per partial: exact in 32 bits.
+__device__ __forceinline__ unsigned long long cand_cross(const Geometry &g, const uint16_t *qd, const int *bkk)
+{
+    const uint4 *q4 = reinterpret_cast<const uint4 *>(qd);
+    unsigned long long X = 0;
+#pragma unroll 4
+    for (int v = 0; v < (g.m >> 3); ++v) {
+        const uint4 w = __ldg(q4 + v);
+        const int *b = bkk + 8 * v;
+        uint32_t acc = (w.x & 0xffffu) * (uint32_t)b[0] + (w.x >> 16) * (uint32_t)b[1];
+        acc += (w.y & 0xffffu) * (uint32_t)b[2] + (w.y >> 16) * (uint32_t)b[3];
+        acc += (w.z & 0xffffu) * (uint32_t)b[4] + (w.z >> 16) * (uint32_t)b[5];
+        acc += (w.w & 0xffffu) * (uint32_t)b[6] + (w.w >> 16) * (uint32_t)b[7];
+        X += acc;
+    }
+    return X;
+}
+
 // Exhaustive exact scan of the ranges that failed certification, as work
 // items (slot, chunk) over a grid of persistent blocks: an item scans one
 // contiguous chunk of the candidates of range fb_list[slot] with exact integer
@@ -629,7 +666,7 @@ __device__ __forceinline__ void full_scans(const Geometry &g, const RangeInfo *r
                                            const int *fb_count, int nch, Partial *part, int *done, uint32_t *winner,
                                            int first, int stride)
 {
-    __shared__ int b_s[kMaxM];
+    __shared__ int bk_s[8 * (kMaxM + 1)];
     __shared__ Partial w_s[8];
     __shared__ int last_s;
     const int count = *fb_count;
@@ -638,8 +675,8 @@ __device__ __forceinline__ void full_scans(const Geometry &g, const RangeInfo *r
         const int lo = (int)((long long)g.N * ch / nch);
         const int hi = (int)((long long)g.N * (ch + 1) / nch);
         const int r = fb_list[slot];
-        __syncthreads();  // b_s and w_s of the previous item are no longer read
-        for (int i = threadIdx.x; i < g.m; i += blockDim.x) b_s[i] = bblk[(size_t)r * g.m + i];
+        __syncthreads();  // bk_s and w_s of the previous item are no longer read
+        stage_sym_block(g, bblk, r, bk_s);
         __syncthreads();
         const RangeInfo rin = ri[r];
         Stats st;
@@ -650,15 +687,7 @@ __device__ __forceinline__ void full_scans(const Geometry &g, const RangeInfo *r
         uint32_t best_i = 0xffffffffu;
         for (int idx = lo + threadIdx.x; idx < hi; idx += blockDim.x) {
             const int d = idx >> 3;
-            const SymFlags sf = sym_flags(idx & 7, g.n);
-            const uint16_t *qd = qblk + (size_t)d * g.m;
-            unsigned long long X = 0;
-            for (int y = 0; y < g.n; ++y) {
-                uint32_t acc = 0;  // one row: n products of at most 4P * P, n <= 16
-                for (int x = 0; x < g.n; ++x)
-                    acc += (uint32_t)qd[sym_src_index(sf, g.ln, y, x)] * (uint32_t)b_s[(y << g.ln) + x];
-                X += acc;
-            }
+            const unsigned long long X = cand_cross(g, qblk + (size_t)d * g.m, bk_s + (idx & 7) * (g.m + 1));
             const U er = exact_rational<Wide>(g, st, di[d], (long long)X);
             if (better(er, (uint32_t)idx, best_e, best_i)) {
                 best_e = er;
@@ -719,7 +748,7 @@ __device__ __forceinline__ void list_scans(const Geometry &g, const RangeInfo *r
                                            int first, int stride)
 {
     typedef typename Exact<Wide>::U U;
-    __shared__ int b_s[kMaxM];
+    __shared__ int bk_s[8 * (kMaxM + 1)];
     __shared__ Partial w_s[8];
     const int count = *sb.count;
     const int ncol = 8 * counts[2];
@@ -732,8 +761,8 @@ __device__ __forceinline__ void list_scans(const Geometry &g, const RangeInfo *r
         const int r = code >> 7, l = code & 127;
         const int sp = l / lists_per_split, part = l - sp * lists_per_split;
         const int t0 = split_tile(tiles, sp, n_split, col_tile), t1 = split_tile(tiles, sp + 1, n_split, col_tile);
-        __syncthreads();  // b_s and w_s of the previous item are no longer read
-        for (int i = threadIdx.x; i < g.m; i += blockDim.x) b_s[i] = bblk[(size_t)r * g.m + i];
+        __syncthreads();  // bk_s and w_s of the previous item are no longer read
+        stage_sym_block(g, bblk, r, bk_s);
         __syncthreads();
         const RangeInfo rin = ri[r];
         Stats st;
@@ -746,15 +775,7 @@ __device__ __forceinline__ void list_scans(const Geometry &g, const RangeInfo *r
             const int c = (t0 + ti) * col_tile + part * seg + (i - ti * seg);
             if (c >= ncol) continue;
             const int d = dmap[c >> 3], k = c & 7;
-            const SymFlags sf = sym_flags(k, g.n);
-            const uint16_t *qd = qblk + (size_t)d * g.m;
-            unsigned long long X = 0;
-            for (int y = 0; y < g.n; ++y) {
-                uint32_t acc = 0;  // one row: n products of at most 4P * P, n <= 16
-                for (int x = 0; x < g.n; ++x)
-                    acc += (uint32_t)qd[sym_src_index(sf, g.ln, y, x)] * (uint32_t)b_s[(y << g.ln) + x];
-                X += acc;
-            }
+            const unsigned long long X = cand_cross(g, qblk + (size_t)d * g.m, bk_s + k * (g.m + 1));
             const uint32_t idx = (uint32_t)(d * 8 + k);
             const U er = exact_rational<Wide>(g, st, di[d], (long long)X);
             if (better(er, idx, best_e, best_i)) {
