@@ -617,12 +617,13 @@ __global__ void __launch_bounds__(32 * kRescoreWarps, 4)
 
 
 
-// The range's pixels permuted for each symmetry, staged by the whole block:
-// bk[k*(m+1) + j] is the range pixel that S_k places over contracted-domain
-// pixel j (the layout of stage_sym_pixels).
-__device__ __forceinline__ void stage_sym_block(const Geometry &g, const uint16_t *bblk, int r, int *bk)
+// The range's pixels permuted for each symmetry, staged by the threads
+// first, first + step, ...: bk[k*(m+1) + j] is the range pixel that S_k places
+// over contracted-domain pixel j (the layout of stage_sym_pixels).
+__device__ __forceinline__ void stage_sym_rows(const Geometry &g, const uint16_t *bblk, int r, int *bk, int first,
+                                               int step)
 {
-    for (int i = threadIdx.x; i < g.m; i += blockDim.x) {
+    for (int i = first; i < g.m; i += step) {
         const int b = bblk[(size_t)r * g.m + i];
         const int y = i >> g.ln, x = i & (g.n - 1);
 #pragma unroll
@@ -676,7 +677,7 @@ __device__ __forceinline__ void full_scans(const Geometry &g, const RangeInfo *r
         const int hi = (int)((long long)g.N * (ch + 1) / nch);
         const int r = fb_list[slot];
         __syncthreads();  // bk_s and w_s of the previous item are no longer read
-        stage_sym_block(g, bblk, r, bk_s);
+        stage_sym_rows(g, bblk, r, bk_s, threadIdx.x, blockDim.x);
         __syncthreads();
         const RangeInfo rin = ri[r];
         Stats st;
@@ -733,7 +734,8 @@ __device__ __forceinline__ void full_scans(const Geometry &g, const RangeInfo *r
     }
 }
 
-// Exact scan of the candidates of one failed list (work item (range, list)):
+// Exact scan of the candidates of one failed list (work item (range, list),
+// one block each, for short queues; list_scans_warp below for long ones):
 // list l = split * parts + part of a range holds the columns tile * col_tile
 // + part * seg + [0, seg) of the tiles of its split, exactly as the search
 // assigned them (compacted columns; dmap gives the domain).  Each item writes
@@ -741,7 +743,7 @@ __device__ __forceinline__ void full_scans(const Geometry &g, const RangeInfo *r
 // the finalists' best and writes the winner, flagged as resolved by an exact
 // scan.
 template <bool Wide>
-__device__ __forceinline__ void list_scans(const Geometry &g, const RangeInfo *ri, const DomainInfo *di,
+__device__ __forceinline__ void list_scans_block(const Geometry &g, const RangeInfo *ri, const DomainInfo *di,
                                            const uint16_t *bblk, const uint16_t *qblk, const int *counts,
                                            const int *dmap, int col_tile, int target, int max_split,
                                            int lists_per_split, int max_lists, const SpanBufs &sb, uint32_t *winner,
@@ -762,7 +764,7 @@ __device__ __forceinline__ void list_scans(const Geometry &g, const RangeInfo *r
         const int sp = l / lists_per_split, part = l - sp * lists_per_split;
         const int t0 = split_tile(tiles, sp, n_split, col_tile), t1 = split_tile(tiles, sp + 1, n_split, col_tile);
         __syncthreads();  // bk_s and w_s of the previous item are no longer read
-        stage_sym_block(g, bblk, r, bk_s);
+        stage_sym_rows(g, bblk, r, bk_s, threadIdx.x, blockDim.x);
         __syncthreads();
         const RangeInfo rin = ri[r];
         Stats st;
@@ -818,6 +820,81 @@ __device__ __forceinline__ void list_scans(const Geometry &g, const RangeInfo *r
     }
 }
 
+// The same scan with one warp per item, for long queues (more items than
+// twice the blocks), where a warp rather than a block per item amortises the
+// staging and the reduction.  bk: this warp's 8 (m+1) ints of shared memory;
+// items first, first + stride, ...
+template <bool Wide>
+__device__ __forceinline__ void list_scans_warp(const Geometry &g, const RangeInfo *ri, const DomainInfo *di,
+                                           const uint16_t *bblk, const uint16_t *qblk, const int *counts,
+                                           const int *dmap, int col_tile, int target, int max_split,
+                                           int lists_per_split, int max_lists, const SpanBufs &sb, uint32_t *winner,
+                                           int *bk, int first, int stride)
+{
+    typedef typename Exact<Wide>::U U;
+    const int lane = threadIdx.x & 31;
+    const int count = *sb.count;
+    const int ncol = 8 * counts[2];
+    const int tiles = (ncol + col_tile - 1) / col_tile;
+    const int n_split = active_splits((counts[0] + 127) / 128, tiles, target, max_split, col_tile);
+    const int n_lists = n_split * lists_per_split;
+    const int seg = col_tile / lists_per_split;
+    for (int item = first; item < count; item += stride) {
+        const int code = sb.items[item];
+        const int r = code >> 7, l = code & 127;
+        const int sp = l / lists_per_split, part = l - sp * lists_per_split;
+        const int t0 = split_tile(tiles, sp, n_split, col_tile), t1 = split_tile(tiles, sp + 1, n_split, col_tile);
+        __syncwarp();  // bk of the previous item is no longer read
+        stage_sym_rows(g, bblk, r, bk, lane, 32);
+        __syncwarp();
+        const RangeInfo rin = ri[r];
+        Stats st;
+        st.Sb = rin.Sb;
+        st.Sbb = rin.Sbb;
+        U best_e = ~(U)0;
+        uint32_t best_i = 0xffffffffu;
+        for (int i = lane; i < (t1 - t0) * seg; i += 32) {
+            const int ti = i / seg;
+            const int c = (t0 + ti) * col_tile + part * seg + (i - ti * seg);
+            if (c >= ncol) continue;
+            const int d = dmap[c >> 3], k = c & 7;
+            const unsigned long long X = cand_cross(g, qblk + (size_t)d * g.m, bk + k * (g.m + 1));
+            const uint32_t idx = (uint32_t)(d * 8 + k);
+            const U er = exact_rational<Wide>(g, st, di[d], (long long)X);
+            if (better(er, idx, best_e, best_i)) {
+                best_e = er;
+                best_i = idx;
+            }
+        }
+        warp_argmin(best_e, best_i);
+        if (lane == 0) {
+            Partial *sp_r = sb.part + (size_t)r * max_lists;
+            sp_r[l] = Partial{(unsigned long long)best_e, hi64(best_e), best_i, 0};
+            __threadfence();  // the partial is visible before the count says so
+            if (atomicSub(sb.pending + r, 1) == 1) {
+                __threadfence();
+                Partial bb = sb.cert[r];
+                for (int j = 0; j < n_lists; ++j) {
+                    const Partial *pj = sp_r + j;
+                    const unsigned long long jl = __ldcg(&pj->lo), jh = __ldcg(&pj->hi);
+                    const uint32_t ji = __ldcg(&pj->idx);
+                    const unsigned __int128 ej = ((unsigned __int128)jh << 64) | jl;
+                    const unsigned __int128 eb = ((unsigned __int128)bb.hi << 64) | bb.lo;
+                    if (ji != 0xffffffffu && better(ej, ji, eb, bb.idx)) {
+                        bb.lo = jl;
+                        bb.hi = jh;
+                        bb.idx = ji;
+                    }
+                }
+                winner[r] = bb.idx | 0x80000000u;  // high bit: resolved by an exact scan
+            }
+        }
+    }
+}
+
+// Shared memory of the list scans: 8 (m+1) ints per warp of a 256-thread block.
+__host__ __device__ __forceinline__ size_t list_scan_smem(int m) { return sizeof(int) * 8 * 8 * (size_t)(m + 1); }
+
 // One launch for both exact scans (persistent blocks; usually there is no
 // work and every block returns at once).
 template <bool Wide>
@@ -828,10 +905,17 @@ __global__ void __launch_bounds__(256) k_exact_scans(Geometry g, const RangeInfo
                                                      int max_split, int lists_per_split, int max_lists, SpanBufs sb,
                                                      uint32_t *winner)
 {
+    extern __shared__ int scan_sm[];  // [warps][8 (m+1)]
     grid_dep_sync();
     full_scans<Wide>(g, ri, di, bblk, qblk, fb_list, fb_count, nch, part, done, winner, blockIdx.x, gridDim.x);
-    list_scans<Wide>(g, ri, di, bblk, qblk, counts, dmap, col_tile, target, max_split, lists_per_split, max_lists, sb,
-                     winner, blockIdx.x, gridDim.x);
+    const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (*sb.count > 2 * (int)gridDim.x)  // grid-uniform
+        list_scans_warp<Wide>(g, ri, di, bblk, qblk, counts, dmap, col_tile, target, max_split, lists_per_split,
+                              max_lists, sb, winner, scan_sm + warp * 8 * (g.m + 1), blockIdx.x * nw + warp,
+                              gridDim.x * nw);
+    else
+        list_scans_block<Wide>(g, ri, di, bblk, qblk, counts, dmap, col_tile, target, max_split, lists_per_split,
+                               max_lists, sb, winner, blockIdx.x, gridDim.x);
 }
 
 // Batched: the work items of all slices' queues form one sequence (the
@@ -842,6 +926,7 @@ __global__ void __launch_bounds__(256) k_exact_scans_batch(const SliceCtx *__res
                                                            int lists_per_split, int col_tile)
 {
     __shared__ int fi_s[kMaxBatch + 1], li_s[kMaxBatch + 1];  // item prefixes: full scans, list scans
+    extern __shared__ int scan_sm[];                          // [warps][8 (m+1)]
     grid_dep_sync();
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         const SliceCtx &c = ctx[i];
@@ -873,21 +958,36 @@ __global__ void __launch_bounds__(256) k_exact_scans_batch(const SliceCtx *__res
         if (lane == 0) fi_s[0] = li_s[0] = 0;
     }
     __syncthreads();
+    // full scans: block items b, b + G, ... of the global sequence
     const int b = blockIdx.x, G = gridDim.x;
     for (int s = 0; s < n; ++s) {
-        const int nf = fi_s[s + 1] - fi_s[s], nl = li_s[s + 1] - li_s[s];
-        // this block's first item of the slice in the global sequence b, b + G, ...
-        const int ff = ((b - fi_s[s]) % G + G) % G, fl = ((b - li_s[s]) % G + G) % G;
-        if (ff >= nf && fl >= nl) continue;  // block-uniform
-        const SliceCtx c = ctx[s];
+        const int nf = fi_s[s + 1] - fi_s[s];
+        const int ff = ((b - fi_s[s]) % G + G) % G;  // this block's first item of the slice
+        if (ff >= nf) continue;                      // block-uniform
+        const SliceCtx &c = ctx[s];
         const EncBufs &e = c.b;
-        if (ff < nf)
-            full_scans<Wide>(c.g, e.ri, e.di, e.bblk, e.qblk, e.fb_list, e.fb_count, fallback_chunks(c.g),
-                             reinterpret_cast<Partial *>(e.partial), fallback_done(c.g, e.partial), e.winner, ff, G);
-        if (fl < nl)
-            list_scans<Wide>(c.g, e.ri, e.di, e.bblk, e.qblk, e.cb.counts, e.cb.dmap, col_tile, c.target, c.n_split,
-                             lists_per_split, c.n_lists, span_bufs(c.g, c.n_lists, e.span, e.fb_count + 2), e.winner,
-                             fl, G);
+        full_scans<Wide>(c.g, e.ri, e.di, e.bblk, e.qblk, e.fb_list, e.fb_count, fallback_chunks(c.g),
+                         reinterpret_cast<Partial *>(e.partial), fallback_done(c.g, e.partial), e.winner, ff, G);
+    }
+    // list scans: one warp per item (warp items w, w + W, ... of the global
+    // sequence) when the queues are long, else one block per item
+    const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const bool by_warp = li_s[n] > 2 * G;  // grid-uniform
+    const int w = by_warp ? b * nw + warp : b, W = by_warp ? G * nw : G;
+    for (int s = 0; s < n; ++s) {
+        const int nl = li_s[s + 1] - li_s[s];
+        const int fl = ((w - li_s[s]) % W + W) % W;  // this warp's (block's) first item of the slice
+        if (fl >= nl) continue;                      // warp- (block-) uniform
+        const SliceCtx &c = ctx[s];
+        const EncBufs &e = c.b;
+        const SpanBufs sb = span_bufs(c.g, c.n_lists, e.span, e.fb_count + 2);
+        if (by_warp)
+            list_scans_warp<Wide>(c.g, e.ri, e.di, e.bblk, e.qblk, e.cb.counts, e.cb.dmap, col_tile, c.target,
+                                  c.n_split, lists_per_split, c.n_lists, sb, e.winner, scan_sm + warp * 8 * (c.g.m + 1),
+                                  fl, W);
+        else
+            list_scans_block<Wide>(c.g, e.ri, e.di, e.bblk, e.qblk, e.cb.counts, e.cb.dmap, col_tile, c.target,
+                                   c.n_split, lists_per_split, c.n_lists, sb, e.winner, fl, W);
     }
 }
 
@@ -1052,9 +1152,13 @@ cudaError_t launch_exact_scans(const Geometry &g, const RangeInfo *ri, const Dom
     const int nch = fallback_chunks(g);
     Partial *part = reinterpret_cast<Partial *>(partial);
     const SpanBufs sb = span_bufs(g, max_lists, span, fb_count + 2);
-    return launch_dep(g.wide ? k_exact_scans<true> : k_exact_scans<false>, dim3(2 * n_sm), dim3(256), 0, st, g, ri,
-                      di, bblk, qblk, fb_list, (const int *)fb_count, nch, part, fallback_done(g, partial), counts,
-                      dmap, col_tile, target, max_split, lists_per_split, max_lists, sb, winner);
+    const size_t smem = list_scan_smem(g.m);
+    auto kern = g.wide ? k_exact_scans<true> : k_exact_scans<false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return launch_dep(kern, dim3(2 * n_sm), dim3(256), smem, st, g, ri, di, bblk, qblk, fb_list,
+                      (const int *)fb_count, nch, part, fallback_done(g, partial), counts, dmap, col_tile, target,
+                      max_split, lists_per_split, max_lists, sb, winner);
 }
 
 cudaError_t launch_finalize(const Geometry &g, const RangeInfo *ri, const DomainInfo *di,
@@ -1080,10 +1184,16 @@ cudaError_t launch_rescore_batch(const SliceCtx *ctx, int n, int total_ranges, b
     if (any_wide && (e = launch_dep(k_rescore_batch<true>, dim3(blocks), dim3(32 * kRescoreWarps), smem, st, ctx, n,
                                     total_ranges, lists_per_split, col_tile, exact_scan)) != cudaSuccess)
         return e;
-    if (any_narrow && (e = launch_dep(k_exact_scans_batch<false>, dim3(2 * n_sm), dim3(256), 0, st, ctx, n,
+    const size_t ssm = list_scan_smem(max_m);
+    if ((e = cudaFuncSetAttribute(k_exact_scans_batch<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)ssm)) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(k_exact_scans_batch<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)ssm)) != cudaSuccess)
+        return e;
+    if (any_narrow && (e = launch_dep(k_exact_scans_batch<false>, dim3(2 * n_sm), dim3(256), ssm, st, ctx, n,
                                       lists_per_split, col_tile)) != cudaSuccess)
         return e;
-    if (any_wide && (e = launch_dep(k_exact_scans_batch<true>, dim3(2 * n_sm), dim3(256), 0, st, ctx, n,
+    if (any_wide && (e = launch_dep(k_exact_scans_batch<true>, dim3(2 * n_sm), dim3(256), ssm, st, ctx, n,
                                     lists_per_split, col_tile)) != cudaSuccess)
         return e;
     return cudaSuccess;
