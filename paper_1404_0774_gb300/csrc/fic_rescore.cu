@@ -359,6 +359,9 @@ __device__ __forceinline__ unsigned long long hi64(unsigned __int128 v) { return
 
 constexpr int kRescoreWarps = 4;
 constexpr int kRescoreEnt = 16;  // list entries per lane: up to 512 per range
+// Shared memory of a re-score warp: the symmetry-permuted range pixels
+// (8 rows of m+1) and the finalist list (up to every entry).
+__host__ __device__ constexpr int rescore_warp_ints(int m) { return 8 * (m + 1) + 32 * kRescoreEnt; }
 template <bool Wide>
 __device__ __forceinline__ void rescore_range(const Geometry &g, const EpiConst &ec, const RangeInfo *ri,
                                               const DomainInfo *di, const uint16_t *bblk, const uint16_t *qblk,
@@ -464,36 +467,26 @@ __device__ __forceinline__ void rescore_range(const Geometry &g, const EpiConst 
             best_i = fi;
         }
     }
-    // finalist slots: bit q of qmask when some lane's entry q is a finalist
-    uint32_t qmask = 0, mine = 0;
+    // finalists (entries whose key can still reach the best, but the best
+    // itself), compacted into this warp's list in shared memory, then
+    // re-scored one per lane in a single pass: per-lane exact cross terms
+    // against the symmetry-permuted range pixels, exact rational codes
+    int *fl = bk + 8 * (g.m + 1);
+    int nfin = 0;
+    __syncwarp();  // the list and bk of the warp's previous range are read
 #pragma unroll
     for (int q = 0; q < kRescoreEnt; ++q) {
         const bool fin = ent[q].idx != 0xffffffffu && (ent[q].idx & kIdxMask) != best_i && ent[q].key <= kfin;
-        if (__any_sync(0xffffffffu, fin)) qmask |= 1u << q;
-        mine |= (fin ? 1u : 0u) << q;
+        const unsigned bal = __ballot_sync(0xffffffffu, fin);
+        if (fin) fl[nfin + __popc(bal & ((1u << lane) - 1u))] = (int)(ent[q].idx & kIdxMask);
+        nfin += __popc(bal);
     }
-    bool staged = false;
-    while (qmask) {
-        const int q = __ffs(qmask) - 1;
-        qmask &= qmask - 1;
-        const bool fin = (mine >> q) & 1u;
-        const unsigned mask = __ballot_sync(0xffffffffu, fin);
-        const uint32_t idx = fin ? (L[lane + 32 * q].idx & kIdxMask) : 0u;  // cached reload
-        long long myX = 0;
-        if ((mask & (mask - 1)) == 0) {  // one finalist: the whole warp computes it
-            const uint32_t wi = __shfl_sync(0xffffffffu, idx, __ffs(mask) - 1);
-            long long X, Xd;
-            warp_cross2(g, qblk, wi, wi, b, X, Xd);
-            myX = X;
-        } else {  // several: each lane computes its own
-            if (!staged) {
-                stage_sym_pixels(g, b, bk);
-                staged = true;
-            }
-            if (fin) myX = lane_cross(g, qblk, idx, bk);
-        }
-        if (fin) {  // lanes re-score their own finalists in parallel (integer work)
-            const U er = exact_rational<Wide>(g, st, di[idx >> 3], myX);
+    if (nfin > 0) {  // warp-uniform
+        stage_sym_pixels(g, b, bk);
+        __syncwarp();
+        for (int f = lane; f < nfin; f += 32) {
+            const uint32_t idx = (uint32_t)fl[f];
+            const U er = exact_rational<Wide>(g, st, di[idx >> 3], lane_cross(g, qblk, idx, bk));
             if (better(er, idx, best_e, best_i)) {
                 best_e = er;
                 best_i = idx;
@@ -558,7 +551,7 @@ __device__ __forceinline__ void rescore_blocks(const Geometry &g, const EpiConst
         if (!rkeep[r]) winner[r] = 0;
         fb_done[r] = 0;  // completion counters of the exact fallback
     }
-    int *bk = bk_all + (threadIdx.x >> 5) * 8 * (g.m + 1);
+    int *bk = bk_all + (threadIdx.x >> 5) * rescore_warp_ints(g.m);
     const int nkept = counts[0];
     for (int j = blockIdx.x * kRescoreWarps + (threadIdx.x >> 5); j < nkept; j += gridDim.x * kRescoreWarps)
         rescore_range<Wide>(g, ec, ri, di, bblk, qblk, lists, max_lists, counts, lists_per_split, col_tile, target,
@@ -608,7 +601,7 @@ __global__ void __launch_bounds__(32 * kRescoreWarps, 4)
         const int j = gi - c.r_begin;
         const EncBufs &b = c.b;
         if (j >= b.cb.counts[0]) continue;  // the screened ranges are the first counts[0]
-        int *bk = bk_all + (threadIdx.x >> 5) * 8 * (c.g.m + 1);
+        int *bk = bk_all + (threadIdx.x >> 5) * rescore_warp_ints(c.g.m);
         rescore_range<Wide>(c.g, c.ec, b.ri, b.di, b.bblk, b.qblk, b.lists, c.n_lists, b.cb.counts, lists_per_split,
                             col_tile, c.target, c.n_split, exact_scan, b.winner, b.fb_list, b.fb_count,
                             b.cb.act[j], bk, span_bufs(c.g, c.n_lists, b.span, b.fb_count + 2));
@@ -633,26 +626,6 @@ __device__ __forceinline__ void stage_sym_rows(const Geometry &g, const uint16_t
             bk[k * (g.m + 1) + (sy << g.ln) + sx] = b;
         }
     }
-}
-
-// Exact X of one candidate: its contracted-domain row qd read in natural
-// order, 16 bytes at a time, against the staged row bkk = bk + k*(m+1).
-// Eight products of at most 4P * P < 2^26 per partial: exact in 32 bits.
-__device__ __forceinline__ unsigned long long cand_cross(const Geometry &g, const uint16_t *qd, const int *bkk)
-{
-    const uint4 *q4 = reinterpret_cast<const uint4 *>(qd);
-    unsigned long long X = 0;
-#pragma unroll 4
-    for (int v = 0; v < (g.m >> 3); ++v) {
-        const uint4 w = __ldg(q4 + v);
-        const int *b = bkk + 8 * v;
-        uint32_t acc = (w.x & 0xffffu) * (uint32_t)b[0] + (w.x >> 16) * (uint32_t)b[1];
-        acc += (w.y & 0xffffu) * (uint32_t)b[2] + (w.y >> 16) * (uint32_t)b[3];
-        acc += (w.z & 0xffffu) * (uint32_t)b[4] + (w.z >> 16) * (uint32_t)b[5];
-        acc += (w.w & 0xffffu) * (uint32_t)b[6] + (w.w >> 16) * (uint32_t)b[7];
-        X += acc;
-    }
-    return X;
 }
 
 // Exhaustive exact scan of the ranges that failed certification, as work
@@ -688,7 +661,7 @@ __device__ __forceinline__ void full_scans(const Geometry &g, const RangeInfo *r
         uint32_t best_i = 0xffffffffu;
         for (int idx = lo + threadIdx.x; idx < hi; idx += blockDim.x) {
             const int d = idx >> 3;
-            const unsigned long long X = cand_cross(g, qblk + (size_t)d * g.m, bk_s + (idx & 7) * (g.m + 1));
+            const long long X = lane_cross(g, qblk, (uint32_t)idx, bk_s);
             const U er = exact_rational<Wide>(g, st, di[d], (long long)X);
             if (better(er, (uint32_t)idx, best_e, best_i)) {
                 best_e = er;
@@ -777,8 +750,8 @@ __device__ __forceinline__ void list_scans_block(const Geometry &g, const RangeI
             const int c = (t0 + ti) * col_tile + part * seg + (i - ti * seg);
             if (c >= ncol) continue;
             const int d = dmap[c >> 3], k = c & 7;
-            const unsigned long long X = cand_cross(g, qblk + (size_t)d * g.m, bk_s + k * (g.m + 1));
             const uint32_t idx = (uint32_t)(d * 8 + k);
+            const long long X = lane_cross(g, qblk, idx, bk_s);
             const U er = exact_rational<Wide>(g, st, di[d], (long long)X);
             if (better(er, idx, best_e, best_i)) {
                 best_e = er;
@@ -858,8 +831,8 @@ __device__ __forceinline__ void list_scans_warp(const Geometry &g, const RangeIn
             const int c = (t0 + ti) * col_tile + part * seg + (i - ti * seg);
             if (c >= ncol) continue;
             const int d = dmap[c >> 3], k = c & 7;
-            const unsigned long long X = cand_cross(g, qblk + (size_t)d * g.m, bk + k * (g.m + 1));
             const uint32_t idx = (uint32_t)(d * 8 + k);
+            const long long X = lane_cross(g, qblk, idx, bk);
             const U er = exact_rational<Wide>(g, st, di[d], (long long)X);
             if (better(er, idx, best_e, best_i)) {
                 best_e = er;
@@ -1126,7 +1099,7 @@ cudaError_t launch_rescore(const Geometry &g, const EpiConst &ec, const RangeInf
                            cudaStream_t st)
 {
     const SpanBufs sb = span_bufs(g, max_lists, span, fb_count + 2);
-    const size_t smem = sizeof(int) * kRescoreWarps * 8 * (g.m + 1);
+    const size_t smem = sizeof(int) * kRescoreWarps * rescore_warp_ints(g.m);
     // at most as many blocks as are resident at once (4 per SM at this size)
     const int blocks = std::max(1, std::min((g.R + kRescoreWarps - 1) / kRescoreWarps, 4 * n_sm));
     if (max_lists * kListK > 32 * kRescoreEnt) return cudaErrorInvalidValue;
@@ -1175,7 +1148,7 @@ cudaError_t launch_rescore_batch(const SliceCtx *ctx, int n, int total_ranges, b
                                  int max_m, int lists_per_split, int col_tile, int exact_scan, int n_sm,
                                  cudaStream_t st)
 {
-    const size_t smem = sizeof(int) * kRescoreWarps * 8 * (max_m + 1);
+    const size_t smem = sizeof(int) * kRescoreWarps * rescore_warp_ints(max_m);
     const int blocks = 4 * n_sm;  // resident at once (4 per SM at this size)
     cudaError_t e;
     if (any_narrow && (e = launch_dep(k_rescore_batch<false>, dim3(blocks), dim3(32 * kRescoreWarps), smem, st, ctx, n,
