@@ -110,3 +110,20 @@ def random_image(seed: int, h: int, w: int, bit_depth: int) -> np.ndarray:
     p = (1 << bit_depth) - 1
     dt = np.uint8 if bit_depth <= 8 else np.uint16
     return rng.integers(0, p + 1, (h, w)).astype(dt)
+
+
+def rounding_tie_image(seed: int = 1404077499) -> np.ndarray:
+    """32x32 12-bit image (8x8 ranges, 16x16 domains at stride 16) with two
+    ranges whose best maps sit exactly on a rounding boundary of the 5-bit s /
+    7-bit o quantiser: range 15 (rows/cols 24..31) equals a/2 + 1000 for the
+    2x2 mean a of domain 0 (2x2-constant blocks of even values, so a/2 is an
+    integer: least-squares s = 1/2, s * 15 = 7.5); range 8 (rows 16..23, cols
+    0..7) is a 97/98 checkerboard (every candidate has |s * 15| < 1/2, so the
+    offset is the mean 97.5 and o * 63 / 4095 = 1.5).  Uniform noise elsewhere."""
+    rng = np.random.default_rng(seed)
+    img = rng.integers(0, 4096, size=(32, 32)).astype(np.uint16)
+    w = rng.integers(50, 901, size=(8, 8))
+    img[0:16, 0:16] = np.kron(2 * w, np.ones((2, 2), dtype=np.int64))
+    img[24:32, 24:32] = w + 1000
+    img[16:24, 0:8] = 97 + (np.add.outer(np.arange(8), np.arange(8)) % 2)
+    return img

@@ -297,3 +297,21 @@ def test_failed_lists_rescan_gives_the_exact_maps(fic, orc, search):
     resc = np.nonzero(a["info"] & fic.FIC_MAP_FALLBACK)[0]
     sample = np.unique(np.concatenate([resc[:24], rng.choice(len(a), 24, replace=False)]))
     check_against_oracle(orc, img, a, 8, 4, 12, ranges=sample)
+
+
+
+@pytest.mark.parametrize("search", SEARCH)
+def test_codes_on_exact_rounding_ties(fic, orc, search):
+    # the GPU decides the codes in FP32 from exact integers and defers to the
+    # FP64 operation sequence next to a rounding boundary; here both ties are
+    # exact, so that sequence (and the oracle) must give the rounded-away codes
+    img = fic_synth.rounding_tie_image()
+    ref = orc.encode(img.astype(np.float64), n=8, t=16, bit_depth=12)
+    assert (ref["d"][15], ref["k"][15], ref["c"][15]) == (0, 0, 8) and ref["s_ls"][15] == 0.5
+    assert (ref["d"][8], ref["k"][8], ref["c"][8], ref["e"][8]) == (0, 0, 0, 2) and ref["o_raw"][8] == 97.5
+    p = fic.params(range_size=8, domain_stride=16, bit_depth=12, search=search_code(fic, search))
+    got = gpu_encode(fic, img, p)
+    check_against_oracle(orc, img.astype(np.float64), got, 8, 16, 12)
+    for r in (15, 8):
+        assert (got["domain_idx"][r], got["iso"][r], got["s_code"][r], got["o_code"][r]) == \
+            (ref["d"][r], ref["k"][r], ref["c"][r], ref["e"][r]), r

@@ -310,3 +310,17 @@ def test_scaled_decode_averages_down_to_the_unscaled_decode(orc):
     assert x2.shape == (128, 128) and xh.shape == (32, 32)
     assert np.allclose(down(x2), x1, rtol=0, atol=1e-9 * 4095)
     assert np.allclose(down(x1), xh, rtol=0, atol=1e-9 * 4095)
+
+
+def test_exact_ties_round_half_away_from_zero(orc):
+    # eq 11-12 quantise s and o to the nearest code; on an exact half the
+    # reading is "half away from zero" (C round()).  The two crafted ranges
+    # of rounding_tie_image land exactly on s * Ls = 7.5 and o * Lo / P = 1.5:
+    # the codes must be 8 and 2, and the neighbouring codes must give the
+    # same least-squares distance (the tie is real, not a near miss).
+    img = fic_synth.rounding_tie_image().astype(np.float64)
+    ref = orc.encode(img, n=8, t=16, bit_depth=12)
+    assert (ref["d"][15], ref["k"][15], ref["s_ls"][15], ref["c"][15]) == (0, 0, 0.5, 8)
+    assert (ref["d"][8], ref["k"][8], ref["c"][8], ref["o_raw"][8], ref["e"][8]) == (0, 0, 0, 97.5, 2)
+    assert abs(0.5 * 15 - 8) == abs(0.5 * 15 - 7)
+    assert abs(97.5 * 63 / 4095 - 2) == abs(97.5 * 63 / 4095 - 1)
