@@ -59,7 +59,7 @@ enum {
     FIC_ERR_CAPACITY = -4,  /* output or workspace buffer too small           */
     FIC_ERR_CUDA = -5,      /* a CUDA runtime call failed                     */
     FIC_ERR_TIMEOUT = -6,   /* a bounded device-side wait ran out             */
-    FIC_ERR_UNSUPPORTED = -7 /* valid parameters this build does not handle   */
+    FIC_ERR_UNSUPPORTED = -7 /* valid parameters this library does not handle */
 };
 
 /* Search implementation. */

@@ -1333,7 +1333,7 @@ const char *fic_status_str(int status)
     case FIC_ERR_CAPACITY: return "output or workspace buffer too small";
     case FIC_ERR_CUDA: return "CUDA runtime error";
     case FIC_ERR_TIMEOUT: return "device-side wait timed out";
-    case FIC_ERR_UNSUPPORTED: return "parameters not supported by this build";
+    case FIC_ERR_UNSUPPORTED: return "parameters not supported by this library";
     default: return "unknown status";
     }
 }
