@@ -531,21 +531,22 @@ __global__ void __launch_bounds__(256, kRowsBlocksPerSm) k_rows_batch(const Slic
 }
 
 
-// Seed of the per-range best key: before the search, every range scores 256
-// candidates -- the 8 symmetries of the 5 x 5 domains around it and of 7
-// domains spread over the image -- from their exact cross terms, with the
-// same code decision and key as the search epilogue.  Only clean keys (code
-// not next to a rounding boundary, offset not clamped) are published: each is
-// within the screening allowance of a real candidate's residual, which is all
-// the search's insertion window needs.
+// Seed of the per-range best key: before the search, every range scores the
+// 8 symmetries of a few domains -- the ones around it and 7 spread over the
+// image -- from their exact cross terms, with the same code decision and key
+// as the search epilogue.  Only clean keys (code not next to a rounding
+// boundary, offset not clamped) are published: each is within the screening
+// allowance of a real candidate's residual, which is all the search's
+// insertion window needs.
 //
-// One warp per range, lane = domain slot, all 8 symmetries per lane: bk[k][j]
-// is the range pixel that S_k places over domain pixel j, so X(d, k) =
-// sum_j q_d[j] * bk[k][j]; q2[p][slot] holds the contracted-domain pixels 2p,
-// 2p+1 of the slot's domain (lanes read consecutive words, the bk reads are
-// broadcasts).  Per warp 96 m bytes of shared memory: 8 m ints of bk, m/2 x
-// 32 words of q2.  The loads of a warp are issued together (one round trip
-// after the keep flag for m <= 64).
+// seed_warp (m = 256): one warp per range over 32 domain slots (5 x 5 + 7),
+// lane = slot, all 8 symmetries per lane: bk[k][j] is the range pixel that
+// S_k places over domain pixel j, so X(d, k) = sum_j q_d[j] * bk[k][j];
+// q2[p][slot] holds the contracted-domain pixels 2p, 2p+1 of the slot's
+// domain (lanes read consecutive words, the bk reads are broadcasts); 8 m
+// ints of bk and m/2 x 32 words of q2 per warp.  seed_pair (m <= 64): the
+// same with half a warp per range over 16 slots (3 x 3 + 7).  The loads of a
+// warp are issued together (one round trip after the keep flag).
 __host__ __device__ constexpr int seed_warps(int m) { return m <= 64 ? 16 : 8; }
 // Shared ints per seed warp: one range (m = 256: 8 m of bk, 16 m of q2) or
 // two (m <= 64, see seed_pair: 2 (8 m + 2) of bk, 16 m of q2).
