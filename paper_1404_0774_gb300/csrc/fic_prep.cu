@@ -405,7 +405,7 @@ __device__ __forceinline__ uint4 sym_chunk(const uint16_t *s, const uint16_t *t,
 // (KP and m are multiples of 8, so a chunk never straddles two parts).
 // Domain constants in the same order.
 __device__ __forceinline__ void domain_rows_warp(const Geometry &g, const DomainInfo *di, const uint16_t *qblk,
-                                                 const float4 *dconst, int j, int d, int lane, const uint16_t *kc_s,
+                                                 const float4 *dconst, int j, int d, int lane,
                                                  uint16_t *hi_s, uint16_t *lo_s, uint16_t *hit_s, uint16_t *lot_s,
                                                  float *cb32, __half *cb16, float4 *dconst_c, int *dmap)
 {
@@ -460,19 +460,21 @@ __device__ __forceinline__ void domain_rows_warp(const Geometry &g, const Domain
     const int base = g.split_hilo ? 2 * m : m;
     const uint32_t t0 = __half_as_ushort(__float2half_rn(-1024.0f * (float)fd / (float)m));
     const uint32_t t1 = __half_as_ushort(__float2half_rn(-(float)fd / (float)m));
-    for (int e = lane; e < 8 * nch; e += 32) {
-        const int kc = kc_s[e];
-        const int k = kc >> 8, c = kc & 255;
+    // four lanes per symmetry k = lane / 4, chunks c = lane % 4, + 4, ...:
+    // the symmetry's flags are fixed per lane
+    const int k = lane >> 2;
+    const SymFlags sf = sym_flags(k, g.n);
+    uint4 *row = reinterpret_cast<uint4 *>(cb16 + ((size_t)j * 8 + k) * g.KP);
+    for (int c = lane & 3; c < nch; c += 4) {
         const int col0 = 8 * c;
         uint4 v;
         if (col0 >= base) {
             v = make_uint4(col0 == base ? (t0 | (t1 << 16)) : 0u, 0u, 0u, 0u);
         } else {
             const bool lo_part = col0 >= m;  // second copy (12-bit only)
-            v = sym_chunk(lo_part ? lo_s : hi_s, lo_part ? lot_s : hit_s, sym_flags(k, g.n), g.n, g.ln,
-                          lo_part ? col0 - m : col0);
+            v = sym_chunk(lo_part ? lo_s : hi_s, lo_part ? lot_s : hit_s, sf, g.n, g.ln, lo_part ? col0 - m : col0);
         }
-        reinterpret_cast<uint4 *>(cb16 + ((size_t)j * 8 + k) * g.KP)[c] = v;
+        row[c] = v;
     }
 }
 
@@ -488,12 +490,8 @@ __device__ __forceinline__ void rows_block(const Geometry &g, const RangeInfo *r
                                            __half *ra16, float *cb32, __half *cb16, float4 *dconst_c, int *dmap,
                                            int first, int stride)
 {
-    __shared__ uint16_t kc_s[8 * ((2 * kMaxM + 16) / 8)];
     __shared__ __align__(16) uint16_t hi_s[8][kMaxM], lo_s[8][kMaxM], hit_s[8][kMaxM], lot_s[8][kMaxM];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int nch = g.KP >> 3;
-    for (int e = threadIdx.x; e < 8 * nch; e += blockDim.x) kc_s[e] = (uint16_t)(((e / nch) << 8) | (e % nch));
-    __syncthreads();
     const int nr = counts[0], nd = counts[2];
     const int rgroups = (nr + 7) / 8, groups = rgroups + (nd + 7) / 8;
     for (int vb = first; vb < groups; vb += stride) {
@@ -504,7 +502,7 @@ __device__ __forceinline__ void rows_block(const Geometry &g, const RangeInfo *r
             const int j = (vb - rgroups) * 8 + w;
             if (j < nd) {
                 __syncwarp();  // the warp's staging arrays of its previous domain are read
-                domain_rows_warp(g, di, qblk, dconst, j, dact[j], lane, kc_s, hi_s[w], lo_s[w], hit_s[w], lot_s[w],
+                domain_rows_warp(g, di, qblk, dconst, j, dact[j], lane, hi_s[w], lo_s[w], hit_s[w], lot_s[w],
                                  cb32, cb16, dconst_c, dmap);
             }
         }
