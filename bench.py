@@ -167,26 +167,62 @@ def load_peaks():
         "fallback"
 
 
-def cpu_oracle_sample(img, target_s=12.0, min_ranges=64):
-    """Time the FP64 oracle on an evenly spaced sample of ranges (~target_s seconds)."""
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), for the record."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.strip().lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for ln in fh:
+                if ln.lower().startswith(("model name", "cpu model")):
+                    return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+
+    return platform.processor() or platform.machine()
+
+
+def psnr_db(ref, x, bits):
+    """10 log10(P^2 / MSE) of a decoded image against the original (FP64)."""
+    P = float((1 << bits) - 1)
+    mse = float(np.mean((np.asarray(x, np.float64) - np.asarray(ref, np.float64)) ** 2))
+    return float("inf") if mse == 0.0 else 10.0 * np.log10(P * P / mse)
+
+
+def cpu_oracle_baseline(img):
+    """The FP64 oracle on the host cores: the whole slice (every range, all
+    125000 candidates each; seconds on a many-core host) on all threads, its
+    maps decoded by the oracle decoder (10 iterations from 2^(B-1)) for the
+    PSNR the GPU arms must match; and single-threaded on the 256x256 8-bit
+    MR-like slice (8x8 ranges, domains at stride 8)."""
     import oracle
 
     oracle.build()
     R, D, _ = comparisons()
     cores = os.cpu_count() or 1
-    n = min_ranges
     t0 = time.perf_counter()
-    oracle.encode(img, n=RANGE, t=STRIDE, bit_depth=BITS, ranges=np.linspace(0, R - 1, n).astype(np.int32),
-                  threads=cores)
+    ref = oracle.encode(img, n=RANGE, t=STRIDE, bit_depth=BITS, threads=cores)
     dt = time.perf_counter() - t0
-    n2 = int(min(R, max(n, n * target_s / max(dt, 1e-3))))
-    sel = np.linspace(0, R - 1, n2).astype(np.int32)
-    t0 = time.perf_counter()
-    oracle.encode(img, n=RANGE, t=STRIDE, bit_depth=BITS, ranges=sel, threads=cores)
-    dt = time.perf_counter() - t0
-    return {"value": n2 * D * 8 / dt, "unit": "comparisons/s", "cores": cores, "kind": "oracle",
-            "sample": f"{n2} evenly spaced ranges of the 512x512 slice, all 125000 candidates each, "
-                      f"{dt:.1f} s wall on {cores} threads"}
+    P = float((1 << BITS) - 1)
+    x = oracle.decode(ref["d"], ref["k"], ref["c"] / 15.0, ref["e"] * P / 63.0, N_PIX, N_PIX, n=RANGE, t=STRIDE,
+                      bit_depth=BITS, iters=10)
+    mr = fic_synth.mr_slice()
+    t1 = time.perf_counter()
+    oracle.encode(mr, n=8, t=8, bit_depth=8, threads=1)
+    dt1 = time.perf_counter() - t1
+    r1, d1 = oracle.counts(256, 256, 8, 8)
+    return {"value": R * D * 8 / dt, "unit": "comparisons/s", "cores": cores, "kind": "oracle",
+            "cpu_model": cpu_model(), "ms_per_step": 1e3 * dt,
+            "sample": f"the whole 512x512 slice: {R} ranges x {D * 8} candidates, {dt:.1f} s wall on {cores} threads",
+            "single_thread_mr256": {"ms": 1e3 * dt1, "comparisons_per_s": r1 * d1 * 8 / dt1,
+                                    "workload": "256x256 8-bit MR-like slice, 8x8 ranges, domains at stride 8"}}, \
+        psnr_db(img, x, BITS), ref
 
 
 def run_reference(args):
@@ -210,10 +246,14 @@ def run_reference(args):
     t = float(np.sum(times))
     value = args.steps * per_step * D * 8 / t
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "comparisons/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps * R / per_step,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "sample_ranges_per_step": per_step},
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "step": f"{per_step} ranges of the slice x 125000 candidates each",
+                       "sample_ranges_per_step": per_step,
+                       "ms_per_slice_extrapolated": 1e3 * t / args.steps * R / per_step},
             "cpu_baseline": {"value": value, "unit": "comparisons/s", "cores": cores, "kind": "oracle",
+                             "cpu_model": cpu_model(),
                              "sample": f"{per_step} ranges x 125000 candidates per step"},
             "e2e": {"value": value, "unit": "comparisons/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -619,9 +659,10 @@ def main():
     t_total = max_over_ranks(t_total, ws, dev)
     value = job_rate(ws, args.steps, comps, t_total)
 
-    # dominant kernel: the search, timed alone with events on the launching stream
     stats = fic.last_encode_stats()
     used = {fic.FIC_SEARCH_TC: "tc", fic.FIC_SEARCH_SIMT: "simt"}.get(stats[2], "?")
+    mnp = fic.maps_to_numpy(maps)
+    n_fallback = int((mnp["info"] & fic.FIC_MAP_FALLBACK).sum())
 
     # end to end through the C ABI with pinned host buffers
     h_img = torch.from_numpy(img_np.astype(np.int16)).pin_memory()
@@ -650,26 +691,59 @@ def main():
     e2e_t = max_over_ranks(e2e_t, ws, dev)
     e2e_value = job_rate(ws, args.steps, comps, e2e_t)
 
-    mnp = fic.maps_to_numpy(maps)
-    n_fallback = int((mnp["info"] & fic.FIC_MAP_FALLBACK).sum())
+    def timed_arm(pp, wsp, k):
+        """k steps of the encode with parameters pp (L2 flushed before each),
+        total seconds (max over ranks), after 3 warm-up steps."""
+        for _ in range(3):
+            fic.encode(img, pp, maps=maps, workspace=wsp, stream=stream)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
+        for i in range(k):
+            flush.zero_()
+            evs[i][0].record(stream)
+            fic.encode(img, pp, maps=maps, workspace=wsp, stream=stream)
+            evs[i][1].record(stream)
+        torch.cuda.synchronize()
+        return max_over_ranks(float(np.sum([a.elapsed_time(b) for a, b in evs])) / 1e3, ws, dev)
+
+    def phases_of(pp, wsp):
+        """Median phase times (ms) of the encode with pp: events the library
+        records around each phase on the launching stream, L2 flushed."""
+        pt = fic.params(range_size=RANGE, domain_stride=STRIDE, bit_depth=BITS, search=pp.search,
+                        flags=pp.flags | fic.FIC_FLAG_PHASE_TIMING)
+        ph = []
+        for _ in range(max(5, min(args.steps, 20))):
+            flush.zero_()
+            fic.encode(img, pt, maps=maps, workspace=wsp, stream=stream)
+            ph.append(fic.last_encode_phase_ms())
+        return {k: float(v) for k, v in zip(["prep", "search", "rescore", "fallback", "output"],
+                                            np.median(np.array(ph), axis=0))}
+
+    def decoded_psnr(pp, wsp):
+        """PSNR of this arm's maps decoded on the GPU (fic_decode, 10 Jacobi
+        iterations from 2^(B-1))."""
+        fic.encode(img, pp, maps=maps, workspace=wsp, stream=stream)
+        out = fic.decode(maps, N_PIX, N_PIX, pp, stream=stream)
+        torch.cuda.synchronize()
+        return psnr_db(img_np, out.cpu().numpy(), BITS), fic.maps_to_numpy(maps).copy()
 
     # the same encode with every range and domain screened (FIC_FLAG_DENSE):
     # the default skips shadow ranges and flat domains (Section V), same maps
     pdense = fic.params(range_size=RANGE, domain_stride=STRIDE, bit_depth=BITS, search=search,
                         flags=fic.FIC_FLAG_DENSE)
     wsd = torch.empty(fic.encode_workspace_size(N_PIX, N_PIX, pdense), dtype=torch.uint8, device=dev)
-    for _ in range(3):
-        fic.encode(img, pdense, maps=maps, workspace=wsd, stream=stream)
-    d_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    for i in range(args.steps):
-        flush.zero_()
-        d_ev[i][0].record(stream)
-        fic.encode(img, pdense, maps=maps, workspace=wsd, stream=stream)
-        d_ev[i][1].record(stream)
-    torch.cuda.synchronize()
-    dense_t = float(np.sum([a.elapsed_time(b) for a, b in d_ev])) / 1e3
-    dense_t = max_over_ranks(dense_t, ws, dev)
+    dense_t = timed_arm(pdense, wsd, args.steps)
     dense_value = job_rate(ws, args.steps, comps, dense_t)
+
+    # the plain FP32 CUDA-core search on the same slice (the speed-up baseline)
+    other = fic.FIC_SEARCH_SIMT if used == "tc" else fic.FIC_SEARCH_TC
+    po = fic.params(range_size=RANGE, domain_stride=STRIDE, bit_depth=BITS, search=other)
+    wso = torch.empty(fic.encode_workspace_size(N_PIX, N_PIX, po), dtype=torch.uint8, device=dev)
+    other_t = timed_arm(po, wso, args.steps)
+    podense = fic.params(range_size=RANGE, domain_stride=STRIDE, bit_depth=BITS, search=other,
+                         flags=fic.FIC_FLAG_DENSE)
+    wsod = torch.empty(fic.encode_workspace_size(N_PIX, N_PIX, podense), dtype=torch.uint8, device=dev)
+    other_dense_t = timed_arm(podense, wsod, args.steps)
+
     # what the skips leave to screen (host-side count from the image itself)
     n = RANGE
     blocks = img_np.reshape(N_PIX // n, n, N_PIX // n, n).transpose(0, 2, 1, 3).reshape(-1, n * n)
@@ -684,18 +758,10 @@ def main():
             flat += int(blk.max() == blk.min())
     screened = (R - shadow) * (D - flat) * 8
 
-    # dominant kernel (the search) timed alone: events recorded by the library
-    # around each phase on the launching stream, L2 flushed before each step
-    pt = fic.params(range_size=RANGE, domain_stride=STRIDE, bit_depth=BITS, search=search,
-                    flags=fic.FIC_FLAG_PHASE_TIMING)
-    phases = []
-    for i in range(max(5, min(args.steps, 20))):
-        flush.zero_()
-        fic.encode(img, pt, maps=maps, workspace=work, stream=stream)
-        phases.append(fic.last_encode_phase_ms())
-    phases = np.array(phases)
-    phase_med = {k: float(v) for k, v in zip(["prep", "search", "rescore", "fallback", "output"],
-                                               np.median(phases, axis=0))}
+    phase_med = phases_of(p, work)
+    phase_other = phases_of(po, wso)
+    psnr_main, maps_main = decoded_psnr(p, work)
+    psnr_other, maps_other = decoded_psnr(po, wso)
     peaks, peak_kind = load_peaks()
     clocks = clk.summary()
     clocks["window_s"] = clk_window
@@ -708,16 +774,17 @@ def main():
     # the binding unit of the search is its FP32 epilogue: the launch against
     # the FP32 lane throughput (SMs x 128 lanes x max SM clock)
     alu_peak = sm_count(dev) * 128 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    tensor_tflops = useful / (kern_ms * 1e-3) / 1e12
     if used == "tc":
         alu = screened * EPI_OPS_PER_CANDIDATE / (kern_ms * 1e-3) / 1e12
         executed = screened * 2 * (2 * RANGE * RANGE)  # FP16 MMA flops issued: hi and lo parts
         roof = {"bound": "alu", "achieved": alu, "peak": alu_peak, "unit": "Tops/s",
                 "ops_per_unit": EPI_OPS_PER_CANDIDATE,
-                "tensor": {"bound": "tensor", "achieved": useful / (kern_ms * 1e-3) / 1e12,
+                "tensor": {"bound": "tensor", "achieved": tensor_tflops,
                            "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
-                           "frac": useful / (kern_ms * 1e-3) / 1e12 / peaks["bf16_tflops"],
+                           "frac": tensor_tflops / peaks["bf16_tflops"],
                            "executed": executed / (kern_ms * 1e-3) / 1e12, "flops_per_unit": 2 * RANGE * RANGE,
-                           "note": "the tensor cores are not the binding unit: 10 % busy"}}
+                           "executed_frac": executed / (kern_ms * 1e-3) / 1e12 / peaks["bf16_tflops"]}}
     else:
         # the FP32 search: RANGE^2 FMAs of the cross term plus the screening key per candidate
         ops = RANGE * RANGE + EPI_OPS_PER_CANDIDATE
@@ -730,6 +797,14 @@ def main():
     roof["kernel"] = "search"
     roof["phase_ms"] = phase_med
 
+    arms = {used: {"ms_per_step": 1e3 * t_total / args.steps, "value": value, "search_ms": kern_ms,
+                   "dense_ms_per_step": 1e3 * dense_t / args.steps, "psnr_db": psnr_main},
+            ("simt" if used == "tc" else "tc"): {
+                "ms_per_step": 1e3 * other_t / args.steps, "value": job_rate(ws, args.steps, comps, other_t),
+                "search_ms": phase_other["search"], "dense_ms_per_step": 1e3 * other_dense_t / args.steps,
+                "psnr_db": psnr_other, "phase_ms": phase_other}}
+    same_maps = bool(np.array_equal(maps_main[["domain_idx", "iso", "s_code", "o_code"]],
+                                    maps_other[["domain_idx", "iso", "s_code", "o_code"]]))
     line = {"metric": METRIC, "value": value, "unit": "comparisons/s", "n_gpus": ws, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": 1e3 * t_total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -737,14 +812,31 @@ def main():
             "config": {"workload": WORKLOAD, "search": used, "l2": "flushed (256 MB write) between steps",
                        "comparisons_per_step": comps, "ranges_resolved_by_exact_rescan": n_fallback,
                        "shadow_ranges": shadow, "flat_domains": flat, "comparisons_screened_per_step": screened,
+                       "screened_comparisons_per_s": job_rate(ws, args.steps, screened, t_total),
                        "dense": {"value": dense_value, "ms_per_step": 1e3 * dense_t / args.steps,
                                  "note": "FIC_FLAG_DENSE: every range and domain screened, same maps"}},
+            "tc_over_fp32": arms["simt"]["ms_per_step"] / arms["tc"]["ms_per_step"],
+            "tc_over_fp32_dense": arms["simt"]["dense_ms_per_step"] / arms["tc"]["dense_ms_per_step"],
+            "tc_over_fp32_search": arms["simt"]["search_ms"] / arms["tc"]["search_ms"],
+            "fp32_search": arms["simt"], "tc_search": arms["tc"],
+            "psnr_db": {"tc": arms["tc"]["psnr_db"], "fp32": arms["simt"]["psnr_db"]},
+            "same_maps_tc_fp32": same_maps,
+            "dense_ms_per_step": 1e3 * dense_t / args.steps,
+            "tensor_tflops": tensor_tflops if used == "tc" else None,
+            "tensor_frac": tensor_tflops / peaks["bf16_tflops"] if used == "tc" else None,
             "e2e": {"value": e2e_value, "unit": "comparisons/s",
                     "h2d_bytes_per_step": N_PIX * N_PIX * 2, "d2h_bytes_per_step": R * 40},
             "gpu_launches": launches_per_step * args.steps, "clocks": clocks, "roofline": roof}
+    if abs(arms["tc"]["psnr_db"] - arms["simt"]["psnr_db"]) >= 0.01:
+        raise SystemExit(f"decoded PSNR of the two searches differs: {line['psnr_db']}")
     if rank == 0:
         if ws == 1 and not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_oracle_sample(img_np)
+            cb, psnr_oracle, _ = cpu_oracle_baseline(img_np)
+            line["cpu_baseline"] = cb
+            line["psnr_db"]["oracle"] = psnr_oracle
+            for k in ("tc", "fp32"):
+                if abs(line["psnr_db"][k] - psnr_oracle) >= 0.01:
+                    raise SystemExit(f"decoded PSNR differs from the oracle's maps: {line['psnr_db']}")
         print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()

@@ -212,8 +212,12 @@ int fic_cross_terms(const void *img, int w, int h, int pitch_px, const fic_param
  *     FIC_STATIC_SCRATCH_BYTES are rejected with FIC_ERR_CAPACITY before any
  *     device work; e.g. 256x256 with 8x8 ranges fits, 512x512 at stride 4
  *     does not.
- *   - The first call on each device looks up the array's device address; make
- *     that first call before any stream capture on that device.
+ *   - The first call on each device looks up the array's device address (and
+ *     may load the array onto that device); make that first call before any
+ *     stream capture on that device.  The address is kept per device and
+ *     context: after the device's context is destroyed and created again
+ *     (cudaDeviceReset), the next call looks it up anew, so that call too
+ *     belongs outside a capture.
  *   - Every call on a device shares the one array, which keeps the previous
  *     call's contents (each call initialises what it needs).  Calls whose
  *     work overlaps on the GPU -- concurrent streams, or several host threads
@@ -344,6 +348,23 @@ int fic_refine_backward(const fic_map *maps, int w, int h, const fic_params *p, 
 int fic_refine(const void *img, int w, int h, int pitch_px, const fic_params *p, const fic_map *maps, float *s,
                float *o, int steps, int iters, float lr, float *loss, void *workspace, size_t workspace_bytes,
                void *stream);
+
+/*
+ * fic_set_wait_limit_ns -- wall-clock limit of each bounded device-side wait
+ *   of the tensor-core search (an mbarrier wait for a shared-memory stage, a
+ *   TMEM accumulator or a work item; measured with %globaltimer).  When a
+ *   wait runs out, the CTA records the error, stops, waits (up to 2 s) for the
+ *   copies and MMAs it has already issued, frees its TMEM and exits; the
+ *   affected maps carry FIC_MAP_ERROR and the synchronous calls return
+ *   FIC_ERR_TIMEOUT.  The GPU context stays usable.  ns = 0 restores the
+ *   default of 2e9 (2 s).  Process-wide; applies to launches made after the
+ *   call (a batch graph captured earlier keeps the limit it was captured
+ *   with).  Always returns FIC_OK.  The paper has no counterpart: this
+ *   lets a caller bound how long a stuck search may hold the GPU, and lets
+ *   tests drive the timeout path without any fault.
+ */
+int fic_set_wait_limit_ns(uint64_t ns);
+uint64_t fic_get_wait_limit_ns(void);
 
 /* Phase durations (ms) of the last fic_encode on this host thread that ran
  * with FIC_FLAG_PHASE_TIMING: out[0] prep, out[1] search, out[2] re-score,

@@ -1475,4 +1475,12 @@ int fic_last_encode_stats(int64_t out[4])
     return FIC_OK;
 }
 
+int fic_set_wait_limit_ns(uint64_t ns)
+{
+    fic::set_wait_limit_ns((unsigned long long)ns);
+    return FIC_OK;
+}
+
+uint64_t fic_get_wait_limit_ns(void) { return (uint64_t)fic::wait_limit_ns(); }
+
 }  // extern "C"

@@ -549,6 +549,11 @@ cudaError_t launch_search_simt(const Geometry &g, const EpiConst &ec, const Rang
                                const DomainInfo *di, const CompactBufs &cb, int dense, const float *rs32,
                                const float *cb32, ListEntry *lists, int max_split, int target, int *tbest,
                                float *dump, cudaStream_t st);
+// Wall-clock limit of each bounded pipeline wait of the tensor-core search
+// (2 s unless set; the drain at exit always allows 2 s).
+constexpr unsigned long long kDefaultWaitNs = 2000000000ull;
+unsigned long long wait_limit_ns();
+void set_wait_limit_ns(unsigned long long ns);  // 0: the default
 bool search_tc_supported(const Geometry &g);
 size_t search_tc_smem(const Geometry &g);
 int search_tc_tile();

@@ -380,11 +380,14 @@ __device__ __forceinline__ void rescore_range(const Geometry &g, const EpiConst 
     const int nent = n_lists * kListK;
     // every entry of the range's lists in registers (entry lane + 32 s), the
     // pixels and statistics loaded alongside: one memory latency
+    // (an entry naming no candidate counts as empty: lists a search left
+    // unwritten after a timed-out wait may hold anything)
     ListEntry ent[kRescoreEnt];
 #pragma unroll
     for (int q = 0; q < kRescoreEnt; ++q) {
         const int f = lane + 32 * q;
         ent[q] = f < nent ? L[f] : ListEntry{__int_as_float(0x7f800000), 0xffffffffu};
+        if ((ent[q].idx & kIdxMask) >= (uint32_t)g.N) ent[q] = ListEntry{__int_as_float(0x7f800000), 0xffffffffu};
     }
     const RangeInfo rin = ri[r];
     int b[kMaxM / 32];

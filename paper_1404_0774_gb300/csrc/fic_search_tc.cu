@@ -29,6 +29,8 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <atomic>
+
 #include "fic_internal.cuh"
 
 namespace fic {
@@ -44,7 +46,13 @@ constexpr int LISTS = BN / EPI_COLS;            // epilogue warps per TMEM lane 
 constexpr int EPI_WARPS = 4 * LISTS;
 constexpr int THREADS = 64 + 32 * EPI_WARPS;    // TMA warp, MMA warp, epilogue
 constexpr int DC_WARP = EPI_COLS / 8;           // domains per warp per tile
-constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s per wait
+// Limits of the bounded waits.  A pipeline wait (for a stage, an
+// accumulator, an item) gives up after the run-time limit `wait_ns` (2 s by
+// default, fic_set_wait_limit_ns); the drain at exit, which waits for copies
+// and MMAs already issued (they finish in microseconds), always allows 2 s so
+// that no copy or MMA can still be writing when the CTA frees its shared
+// memory and TMEM.
+constexpr unsigned long long kDrainNs = 2000000000ull;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
@@ -87,17 +95,38 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
     return ok != 0;
 }
 
+// try_wait whose suspension is capped at `hint_ns` (used with short limits).
+__device__ __forceinline__ bool mbar_try_wait_hint(uint64_t *bar, uint32_t parity, uint32_t hint_ns)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(hint_ns)
+        : "memory");
+    return ok != 0;
+}
+
+// Limits below this are honoured to the timer's resolution: each try_wait
+// suspends for at most the limit and the clock is read after every one.
+constexpr unsigned long long kShortWaitNs = 1000000ull;
+
 // Bounded wait for the phase of `parity` to complete.  Returns false when the
-// CTA is aborting (another role timed out) or this wait timed out.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_s, int *err)
+// CTA is aborting (another role timed out) or this wait timed out (after
+// wait_ns of %globaltimer).
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_s, int *err,
+                                          unsigned long long wait_ns)
 {
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = gtimer();
+    const bool short_wait = wait_ns < kShortWaitNs;
     for (uint32_t i = 1;; ++i) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if ((i & 63) == 0) {
+        if (short_wait ? mbar_try_wait_hint(bar, parity, (uint32_t)wait_ns) : mbar_try_wait(bar, parity)) return true;
+        if (short_wait || (i & 63) == 0) {
             if (*abort_s) return false;
-            if (gtimer() - t0 > kWaitNs) {
+            if (gtimer() - t0 > wait_ns) {
                 *abort_s = 1;
                 atomicExch(err, 1);
                 return false;
@@ -273,7 +302,8 @@ __device__ __forceinline__ TcItem tc_item(const SliceCtx *ctx, const int *ip_s, 
 // the same item sequence, so the pipelines run on across item boundaries.
 template <int NBLK, int BW, bool BATCH>
 __device__ __forceinline__ void search_tc_run(const TcMaps &maps, const SliceCtx &one, const SliceCtx *many, int n,
-                                              int dense, float *dump, uint32_t smem_bytes, int *queue)
+                                              int dense, float *dump, uint32_t smem_bytes, int *queue,
+                                              unsigned long long wait_ns)
 {
     // a single search reads its context from the kernel parameters (constant
     // bank operands in the epilogue's inner loop)
@@ -405,7 +435,7 @@ __device__ __forceinline__ void search_tc_run(const TcMaps &maps, const SliceCtx
             // roles in order
             for (int k = 0;; ++k) {
                 const int slot = k % kItemQ;
-                if (!mbar_wait(&q_empty[slot], ((k / kItemQ) & 1) ^ 1, &abort_s, err0)) break;
+                if (!mbar_wait(&q_empty[slot], ((k / kItemQ) & 1) ^ 1, &abort_s, err0, wait_ns)) break;
                 int item = atomicAdd(queue, 1);
                 if (item >= total || *(volatile int *)&abort_s) item = -1;
                 item_q[slot] = item;
@@ -421,7 +451,7 @@ __device__ __forceinline__ void search_tc_run(const TcMaps &maps, const SliceCtx
                     break;
                 }
                 // the previous item's MMAs must be done with A
-                if (kitem > 0 && !mbar_wait(&a_empty, (kitem - 1) & 1, &abort_s, err)) break;
+                if (kitem > 0 && !mbar_wait(&a_empty, (kitem - 1) & 1, &abort_s, err, wait_ns)) break;
                 mbar_expect_tx(&a_full, A_BYTES);
 #pragma unroll
                 for (int b = 0; b < NBLK; ++b) tma_load_2d(sA + b * A_BLK, &maps.a128, BW * b, c.abase + w.r0, &a_full);
@@ -430,7 +460,7 @@ __device__ __forceinline__ void search_tc_run(const TcMaps &maps, const SliceCtx
                 ++kitem;
                 for (int t = w.t_begin; t < w.t_end; ++t, ++bseq) {
                     const int s = bseq % STAGES;
-                    if (!mbar_wait(&empty_bar[s], ((bseq / STAGES) & 1) ^ 1, &abort_s, err)) break;
+                    if (!mbar_wait(&empty_bar[s], ((bseq / STAGES) & 1) ^ 1, &abort_s, err, wait_ns)) break;
                     uint8_t *dst = sB + s * B_BYTES;
                     const int y = c.bbase + t * BN;
                     mbar_expect_tx(&full_bar[s], B_BYTES);
@@ -442,14 +472,14 @@ __device__ __forceinline__ void search_tc_run(const TcMaps &maps, const SliceCtx
             // drain: every issued load must land before the CTA may exit
             if (a_pending && !mbar_try_wait(&a_full, (kitem - 1) & 1)) {
                 const unsigned long long t0 = gtimer();
-                while (!mbar_try_wait(&a_full, (kitem - 1) & 1) && gtimer() - t0 < kWaitNs) {
+                while (!mbar_try_wait(&a_full, (kitem - 1) & 1) && gtimer() - t0 < kDrainNs) {
                 }
             }
             for (uint32_t q = (bseq > STAGES ? bseq - STAGES : 0); q < bseq; ++q) {
                 const int s = q % STAGES;
                 if (mbar_try_wait(&full_bar[s], (q / STAGES) & 1)) continue;
                 const unsigned long long t0 = gtimer();
-                while (!mbar_try_wait(&full_bar[s], (q / STAGES) & 1) && gtimer() - t0 < kWaitNs) {
+                while (!mbar_try_wait(&full_bar[s], (q / STAGES) & 1) && gtimer() - t0 < kDrainNs) {
                 }
             }
         }
@@ -463,19 +493,19 @@ __device__ __forceinline__ void search_tc_run(const TcMaps &maps, const SliceCtx
             bool ok = true;
             for (int k = 0; ok; ++k) {
                 const int slot = k % kItemQ;
-                if (!(ok = mbar_wait(&q_full[slot], (k / kItemQ) & 1, &abort_s, err0))) break;
+                if (!(ok = mbar_wait(&q_full[slot], (k / kItemQ) & 1, &abort_s, err0, wait_ns))) break;
                 const int item = item_q[slot];
                 mbar_arrive(&q_empty[slot]);
                 if (item < 0) break;
                 const TcItem w = tc_item(ctx, ip_s, ns_s, rt_s, n, item);
                 int *err = ctx[w.s].b.err;
-                if (!(ok = mbar_wait(&a_full, kitem & 1, &abort_s, err))) break;
+                if (!(ok = mbar_wait(&a_full, kitem & 1, &abort_s, err, wait_ns))) break;
                 ++kitem;
                 for (int t = w.t_begin; t < w.t_end; ++t, ++bseq, ++aseq) {
                     const int s = bseq % STAGES;
                     const int acc = aseq % NACC;
-                    if (!(ok = mbar_wait(&tempty_bar[acc], ((aseq / NACC) & 1) ^ 1, &abort_s, err))) break;
-                    if (!(ok = mbar_wait(&full_bar[s], (bseq / STAGES) & 1, &abort_s, err))) break;
+                    if (!(ok = mbar_wait(&tempty_bar[acc], ((aseq / NACC) & 1) ^ 1, &abort_s, err, wait_ns))) break;
+                    if (!(ok = mbar_wait(&full_bar[s], (bseq / STAGES) & 1, &abort_s, err, wait_ns))) break;
                     tc_fence_after();
                     const uint32_t b_base = b_base0 + s * B_BYTES;
                     const uint32_t d_tmem = tmem_base + acc * ACC_COLS;
@@ -501,6 +531,17 @@ __device__ __forceinline__ void search_tc_run(const TcMaps &maps, const SliceCtx
                 }
                 umma_commit(&a_empty);  // A free once the item's MMAs finish
             }
+            // drain: the MMAs issued so far must finish before the CTA frees
+            // TMEM and shared memory (after an abort the epilogue no longer
+            // waits for them); the last commit tracks all of them
+            if (aseq > 0) {
+                const uint32_t last = aseq - 1;
+                if (!mbar_try_wait(&tfull_bar[last % NACC], (last / NACC) & 1)) {
+                    const unsigned long long t0 = gtimer();
+                    while (!mbar_try_wait(&tfull_bar[last % NACC], (last / NACC) & 1) && gtimer() - t0 < kDrainNs) {
+                    }
+                }
+            }
         }
     } else {
         // ------------------------------------------------------ epilogue
@@ -516,7 +557,7 @@ __device__ __forceinline__ void search_tc_run(const TcMaps &maps, const SliceCtx
         bool ok = true;
         for (int k = 0; ok; ++k) {
             const int slot = k % kItemQ;
-            if (!(ok = __all_sync(0xffffffffu, mbar_wait(&q_full[slot], (k / kItemQ) & 1, &abort_s, err0)))) break;
+            if (!(ok = __all_sync(0xffffffffu, mbar_wait(&q_full[slot], (k / kItemQ) & 1, &abort_s, err0, wait_ns)))) break;
             const int item = item_q[slot];
             __syncwarp();
             if (lane == 0) mbar_arrive(&q_empty[slot]);
@@ -577,7 +618,7 @@ __device__ __forceinline__ void search_tc_run(const TcMaps &maps, const SliceCtx
                 }
                 __syncwarp();
                 // warp-uniform decision: tcgen05.ld below is .sync.aligned
-                if (!(ok = __all_sync(0xffffffffu, mbar_wait(&tfull_bar[acc], (aseq / NACC) & 1, &abort_s, err))))
+                if (!(ok = __all_sync(0xffffffffu, mbar_wait(&tfull_bar[acc], (aseq / NACC) & 1, &abort_s, err, wait_ns))))
                     break;
                 tc_fence_after();
                 const uint32_t taddr = lane_addr + acc * ACC_COLS;
@@ -652,10 +693,10 @@ __device__ __forceinline__ void search_tc_run(const TcMaps &maps, const SliceCtx
 template <int NBLK, int BW, bool BATCH>
 __global__ void __launch_bounds__(THREADS, 1)
     k_search_tc(const __grid_constant__ TcMaps maps, const __grid_constant__ SliceCtx one, const SliceCtx *many, int n,
-                int dense, float *dump, uint32_t smem_bytes, int *queue)
+                int dense, float *dump, uint32_t smem_bytes, int *queue, unsigned long long wait_ns)
 {
     grid_dep_sync();
-    search_tc_run<NBLK, BW, BATCH>(maps, one, many, n, dense, dump, smem_bytes, queue);
+    search_tc_run<NBLK, BW, BATCH>(maps, one, many, n, dense, dump, smem_bytes, queue, wait_ns);
 }
 
 namespace {
@@ -717,6 +758,14 @@ int search_tc_rows(int rows) { return (rows + BM - 1) / BM * BM; }
 
 int search_tc_cols(int cols) { return (cols + BN - 1) / BN * BN; }
 
+// Limit of the search's pipeline waits (fic_set_wait_limit_ns), read at
+// each launch.
+static std::atomic<unsigned long long> g_wait_ns{kDefaultWaitNs};
+
+unsigned long long wait_limit_ns() { return g_wait_ns.load(std::memory_order_relaxed); }
+
+void set_wait_limit_ns(unsigned long long ns) { g_wait_ns.store(ns ? ns : kDefaultWaitNs, std::memory_order_relaxed); }
+
 static int n_sms()
 {
     int dev = 0, n = 0;
@@ -733,7 +782,7 @@ static cudaError_t launch_tc3(const TcMaps &mp, const SliceCtx &one, const Slice
         cudaFuncSetAttribute(k_search_tc<NBLK, BW, BATCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     return launch_dep(k_search_tc<NBLK, BW, BATCH>, dim3(n_sms()), dim3(THREADS), smem, st, mp, one, many, n, dense,
-                      dump, (uint32_t)smem, queue);
+                      dump, (uint32_t)smem, queue, (unsigned long long)wait_limit_ns());
 }
 
 template <int NBLK, int BW>

@@ -11,6 +11,8 @@
 // allocate one.  This entry point uses instead a static array of
 // FIC_STATIC_SCRATCH_BYTES (32 MiB) that every GPU which loads the library
 // holds until the process exits.
+#include <cuda.h>
+
 #include <mutex>
 
 #include "fic_internal.cuh"
@@ -26,10 +28,49 @@ static __device__ __align__(256) unsigned char g_scratch[kStaticBytes];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
-void *g_addr[kMaxDevices] = {};
+// Per device: the array's device address and the unique id of the context it
+// was looked up in.  A context that is destroyed and created again (e.g.
+// after cudaDeviceReset) has a new id, so the stale address is dropped.
+struct Entry {
+    void *addr;
+    unsigned long long ctx_id;
+};
+Entry g_entry[kMaxDevices] = {};
 
-// Device address of g_scratch on the current device, looked up once per device
-// (with that device current).  Returns nullptr on failure.
+typedef CUresult (*PfnCtxGetCurrent)(CUcontext *);
+typedef CUresult (*PfnCtxGetId)(CUcontext, unsigned long long *);
+
+// Unique id of the calling thread's current context, or 0 if none is
+// current or the driver does not report one.
+unsigned long long current_ctx_id()
+{
+    static PfnCtxGetCurrent get_current = nullptr;
+    static PfnCtxGetId get_id = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *a = nullptr, *b = nullptr;
+        cudaDriverEntryPointQueryResult qa, qb;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &a, 12000, cudaEnableDefault, &qa) == cudaSuccess &&
+            qa == cudaDriverEntryPointSuccess &&
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &b, 12000, cudaEnableDefault, &qb) == cudaSuccess &&
+            qb == cudaDriverEntryPointSuccess) {
+            get_current = reinterpret_cast<PfnCtxGetCurrent>(a);
+            get_id = reinterpret_cast<PfnCtxGetId>(b);
+        }
+        cudaGetLastError();
+    }
+    if (!get_current || !get_id) return 0;
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
+
+// Device address of g_scratch on the current device.  Looked up (with that
+// device current) on the first call for the device and again whenever its
+// context has changed since; a failed lookup leaves no cached entry.  Returns
+// nullptr on failure.
 void *scratch_address()
 {
     int dev = 0;
@@ -38,15 +79,20 @@ void *scratch_address()
         return nullptr;
     }
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_addr[dev]) {
-        void *ptr = nullptr;
-        if (cudaGetSymbolAddress(&ptr, g_scratch) != cudaSuccess || !ptr) {
-            cudaGetLastError();
-            return nullptr;
-        }
-        g_addr[dev] = ptr;
+    Entry &e = g_entry[dev];
+    const unsigned long long id = current_ctx_id();
+    if (e.addr && id != 0 && id == e.ctx_id) return e.addr;
+    e = Entry{nullptr, 0};
+    void *ptr = nullptr;
+    if (cudaGetSymbolAddress(&ptr, g_scratch) != cudaSuccess || !ptr) {
+        cudaGetLastError();
+        return nullptr;
     }
-    return g_addr[dev];
+    // the lookup made the device's context current if none was; without a
+    // context id the address is not cached (looked up on every call)
+    const unsigned long long id2 = current_ctx_id();
+    if (id2 != 0) e = Entry{ptr, id2};
+    return ptr;
 }
 
 }  // namespace

@@ -93,6 +93,9 @@ def lib():
                                           vp, sz, vp]
         L.fic_refine.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, pp, vp, vp, vp, ctypes.c_int,
                                  ctypes.c_int, ctypes.c_float, vp, vp, sz, vp]
+        L.fic_set_wait_limit_ns.argtypes = [ctypes.c_uint64]
+        L.fic_get_wait_limit_ns.argtypes = []
+        L.fic_get_wait_limit_ns.restype = ctypes.c_uint64
         _lib = L
     return _lib
 
@@ -426,6 +429,16 @@ def maps_to_numpy(maps) -> np.ndarray:
     if _is_torch(maps):
         return maps.detach().cpu().numpy().view(MAP_DTYPE)
     return np.asarray(maps, MAP_DTYPE)
+
+
+def set_wait_limit_ns(ns: int) -> None:
+    """Wall-clock limit of each bounded device wait of the tensor-core search
+    (0 restores the default of 2 s); applies to later launches."""
+    _check(lib().fic_set_wait_limit_ns(int(ns)), "fic_set_wait_limit_ns")
+
+
+def get_wait_limit_ns() -> int:
+    return int(lib().fic_get_wait_limit_ns())
 
 
 def last_encode_stats():

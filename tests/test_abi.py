@@ -91,3 +91,13 @@ def test_batch_workspace_size_and_limits(fic):
     assert lib.fic_batch_workspace_size(table([64] * 1025), 1025, ctypes.byref(p), ctypes.byref(size)) == -4
     pt = fic.params(range_size=8, domain_stride=4, bit_depth=12, flags=fic.FIC_FLAG_PHASE_TIMING)
     assert lib.fic_batch_workspace_size(table([64]), 1, ctypes.byref(pt), ctypes.byref(size)) == -1
+
+
+def test_wait_limit_setter_is_host_state(fic):
+    """The search's wait limit is host state read at each launch: setting,
+    reading back and restoring the default need no GPU."""
+    assert fic.get_wait_limit_ns() == 2_000_000_000
+    fic.set_wait_limit_ns(12345)
+    assert fic.get_wait_limit_ns() == 12345
+    fic.set_wait_limit_ns(0)
+    assert fic.get_wait_limit_ns() == 2_000_000_000

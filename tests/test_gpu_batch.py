@@ -1,11 +1,14 @@
 """The batched encode (fic_encode_batch through the C ABI): every slice of a
-mixed-size batch must get exactly the maps fic_encode gives that slice alone
-(which the encode parity tests check against the oracle), on the first call
-(run eagerly) and on graph replays."""
+mixed-size batch must get exactly the maps fic_encode gives that slice alone,
+on the first call (run eagerly) and on graph replays; and the batch's own maps
+of one slice per size of the volume workload are checked against the FP64
+oracle directly (every map re-scored, every range's residual against the
+oracle's per-range minimum)."""
 import numpy as np
 import pytest
 
 import fic_synth
+from parity import check_against_oracle
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -91,3 +94,32 @@ def test_batch_of_one_slice(fic):
     fic.encode_batch(tab, p, ws)
     torch.cuda.synchronize()
     assert np.array_equal(fic.maps_to_numpy(mp), fic.maps_to_numpy(fic.encode(im, p)))
+
+
+@pytest.mark.parametrize("search", ["auto", "simt"])
+def test_batch_maps_match_the_oracle(fic, orc, search):
+    """One CT-like slice of each size of the volume workload (256, 384 and 512
+    pixels square, 8x8 ranges, 16x16 domains at stride 4, 12-bit) in one
+    batch, plus repeats so that the batch forms size groups: the batch's maps
+    of the first slice of each size pass the oracle parity bar on every range
+    (Section V search, eq 8-12), on the eager call and on a graph replay."""
+    seed = fic_synth.CT_SEED + 23
+    sizes = [256, 384, 512, 256, 384]
+    imgs_np = [fic_synth.ct_slice(seed + 1000 + i, s) for i, s in enumerate(sizes)]
+    code = {"auto": fic.FIC_SEARCH_AUTO, "simt": fic.FIC_SEARCH_SIMT}[search]
+    p = fic.params(range_size=8, domain_stride=4, bit_depth=12, search=code)
+    imgs = [torch.from_numpy(a.astype(np.int16)).cuda() for a in imgs_np]
+    maps = [torch.zeros((s // 8) ** 2 * 40, dtype=torch.uint8, device="cuda") for s in sizes]
+    tab = fic.slice_table(imgs, maps)
+    ws = torch.empty(fic.batch_workspace_size(tab, p), dtype=torch.uint8, device="cuda")
+    refs = {}
+    for call in range(2):  # eager run, then a graph replay
+        for m in maps:
+            m.zero_()
+        fic.encode_batch(tab, p, ws)
+        torch.cuda.synchronize()
+        for i in range(3):
+            got = fic.maps_to_numpy(maps[i])
+            if i not in refs:
+                refs[i] = orc.encode(imgs_np[i], n=8, t=4, bit_depth=12)
+            check_against_oracle(orc, imgs_np[i], got, 8, 4, 12, ref=refs[i])

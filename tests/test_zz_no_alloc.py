@@ -39,11 +39,26 @@ CASES = [
 ]
 
 
+STATIC_SCRATCH_BYTES = 32 << 20  # FIC_STATIC_SCRATCH_BYTES in include/fic.h
+
+
+def test_header_states_the_scratch_size():
+    import os
+    import re
+
+    hdr = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "fic.h")
+    with open(hdr) as fh:
+        m = re.search(r"#define FIC_STATIC_SCRATCH_BYTES \((\d+)u << (\d+)\)", fh.read())
+    assert m and int(m.group(1)) << int(m.group(2)) == STATIC_SCRATCH_BYTES
+
+
 @pytest.mark.parametrize("name,make,n,t,B", CASES, ids=[c[0] for c in CASES])
 def test_static_scratch_encode_matches_fic_encode(fic, name, make, n, t, B):
     img_np = make()
     h, w = img_np.shape
     p = fic.params(range_size=n, domain_stride=t, bit_depth=B)
+    # the parity cases must fit the fixed scratch (else they would test the refusal)
+    assert fic.encode_workspace_size(w, h, p) <= STATIC_SCRATCH_BYTES
     R, _ = fic.counts(w, h, p)
     img = torch.from_numpy(img_np.astype(np.int16) if B > 8 else img_np).cuda()
     ref = fic.maps_to_numpy(fic.encode(img, p))
@@ -51,13 +66,24 @@ def test_static_scratch_encode_matches_fic_encode(fic, name, make, n, t, B):
     m, P = n * n, (1 << B) - 1
     lib = fic.lib()
     stream = torch.cuda.current_stream().cuda_stream
-    for call in range(2):
-        maps = torch.full((R * 40,), 0xAB, dtype=torch.uint8, device="cuda")
-        nm = ctypes.c_int()
+    outs = [torch.full((R * 40,), 0xAB, dtype=torch.uint8, device="cuda") for _ in range(3)]
+    nm = ctypes.c_int()
+    # a first call may load the static array onto the device; the calls after
+    # it must take no device memory at all
+    assert lib.fic_encode_static(img.data_ptr(), w, h, w, ctypes.byref(p), outs[0].data_ptr(), R, ctypes.byref(nm),
+                                 stream) == 0
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    reserved0 = torch.cuda.memory_reserved()
+    for call in (1, 2):
+        maps = outs[call]
         rc = lib.fic_encode_static(img.data_ptr(), w, h, w, ctypes.byref(p), maps.data_ptr(), R,
                                    ctypes.byref(nm), stream)
         assert rc == 0, (call, rc)
         torch.cuda.synchronize()
+        # (free memory may only grow: a pool trimmed at the synchronisation)
+        assert torch.cuda.mem_get_info()[0] >= free0, "the call took device memory"
+        assert torch.cuda.memory_reserved() == reserved0
         got = fic.maps_to_numpy(maps)
         assert nm.value == R
         assert np.array_equal(got["range_idx"], np.arange(R))
@@ -72,7 +98,7 @@ def test_static_scratch_rejects_images_beyond_its_size(fic):
     """512x512 at stride 4 needs more than the fixed scratch: refused with
     FIC_ERR_CAPACITY before any device work."""
     p = fic.params(range_size=8, domain_stride=4, bit_depth=12)
-    assert fic.encode_workspace_size(512, 512, p) > 16 << 20
+    assert fic.encode_workspace_size(512, 512, p) > STATIC_SCRATCH_BYTES
     img = torch.zeros((512, 512), dtype=torch.int16, device="cuda")
     maps = torch.empty(4096 * 40, dtype=torch.uint8, device="cuda")
     nm = ctypes.c_int()
