@@ -252,6 +252,86 @@ __device__ __forceinline__ void rare_chunk(const float (&X)[32], uint32_t mask, 
     __syncwarp();
 }
 
+// The column constants of one domain as the tensor-core epilogue reads them
+// (staged in shared memory once per tile): a = (kappa, kappa, -sqz, -sqz),
+// b = (g, g, alpha, 0) with g = Sq/m - round(Sq/m), so that the centring
+// correction of a range with factor e_r is corr = -e_r * g (epi_corr); each
+// pair is one aligned 64-bit operand of the packed arithmetic.
+struct DcPack {
+    float4 a, b;
+};
+
+__device__ __forceinline__ DcPack dc_pack(const float4 &c4, const EpiConst &ec)
+{
+    const float a = c4.w * ec.invm;
+    const float g = a - floorf(a + 0.5f);  // exact: Sq/m has at most 6 fraction bits
+    DcPack d;
+    d.a = make_float4(c4.z, c4.z, -c4.y, -c4.y);
+    d.b = make_float4(g, g, c4.x, 0.0f);
+    return d;
+}
+
+// epi_keys32<true> of fic_internal.cuh (the near-boundary candidates go to the
+// rare pass, the mask is assembled from sign bits) on the packed constants:
+// the keys and the mask are bit-identical to it.  kZero: add the penalty to
+// s-code-0 keys (zp); the caller takes the variant without it when no lane of
+// the warp can list an s-code-0 candidate (the key of every s-code-0
+// candidate of a range is the same value K0; without the penalty those keys
+// stay K0, and K0 >= thr keeps them out of the mask as the penalty would).
+template <bool kZero>
+__device__ __forceinline__ uint32_t epi_keys32_tc(const float (&X)[32], const DcPack *dp, float zb, float rho_lim,
+                                                  f32x2_t er2, const EpiConst &ec, float thr, float zp)
+{
+    uint32_t mask = 0, far = 0;  // bit-reversed masks of k < thr, of |rho| below the band
+    const f32x2_t thr2 = pk2(thr, thr);
+    const float mlim2 = -__fmul_rd(rho_lim, rho_lim);
+    const f32x2_t mlim = pk2(mlim2, mlim2);
+    const f32x2_t two_ls = pk2(ec.two_ls, ec.two_ls), mls = pk2(-ec.ls, -ec.ls);
+    const f32x2_t mag = pk2(kMagic, kMagic), zb2 = pk2(zb, zb), invg = pk2(ec.invG, ec.invG);
+    const f32x2_t mg = pk2(-ec.G, -ec.G), lam = pk2(ec.lambda, ec.lambda), zpp = pk2(zp, zp);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const float4 A = dp[q].a, Bv = dp[q].b;
+        const f32x2_t kap = pk2(A.x, A.y), msqz = pk2(A.z, A.w);
+        const f32x2_t mcorr = mul2(er2, pk2(Bv.x, Bv.y));  // -corr in both halves
+        float mc, mc1;
+        upk2(mcorr, mc, mc1);
+        const float alpha = Bv.z;
+        const float bq = fmaf(-mc, alpha, 0.5f);
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            const int j = q * 8 + 2 * h;
+            const float u0 = __saturatef(fmaf(X[j], alpha, bq));
+            const float u1 = __saturatef(fmaf(X[j + 1], alpha, bq));
+            const f32x2_t x = pk2(X[j], X[j + 1]);
+            const f32x2_t r = fma2(pk2(u0, u1), two_ls, mls);  // Ls * clamp(s, -1, 1)
+            const f32x2_t c = sub2(add2(r, mag), mag);          // rounded code
+            const f32x2_t rho = sub2(r, c);
+            const f32x2_t z = fma2(c, msqz, zb2);
+            const f32x2_t e = sub2(fma2(z, invg, mag), mag);
+            const f32x2_t wv = fma2(e, mg, z);
+            const f32x2_t y = fma2(c, kap, sub2(mcorr, x));
+            const f32x2_t cy = mul2(c, y);
+            f32x2_t k = fma2(mul2(wv, lam), wv, cy);
+            if (kZero) {
+                float c0, c1;
+                upk2(c, c0, c1);
+                const float zero0 = __saturatef(fmaf(c0, -c0, 1.0f));  // 1 for c = 0, else 0
+                const float zero1 = __saturatef(fmaf(c1, -c1, 1.0f));
+                k = fma2(pk2(zero0, zero1), zpp, k);
+            }
+            float d0, d1, t0, t1;
+            upk2(sub2(k, thr2), d0, d1);
+            upk2(fma2(rho, rho, mlim), t0, t1);
+            mask = __funnelshift_l(__float_as_uint(d0), mask, 1);  // (mask << 1) | sign bit
+            mask = __funnelshift_l(__float_as_uint(d1), mask, 1);
+            far = __funnelshift_l(__float_as_uint(t0), far, 1);
+            far = __funnelshift_l(__float_as_uint(t1), far, 1);
+        }
+    }
+    return __brev(mask | ~far);
+}
+
 // Bits of the first nv (1..32) columns of a 32-column chunk.
 __device__ __forceinline__ uint32_t col_mask(int nv) { return nv >= 32 ? 0xffffffffu : (1u << nv) - 1u; }
 
@@ -334,11 +414,14 @@ __device__ __forceinline__ void search_tc_run(const TcMaps &maps, const SliceCtx
     constexpr int ET = 32 * EPI_WARPS;                                // epilogue threads
     float *xsm = reinterpret_cast<float *>(sB + STAGES * B_BYTES);  // [32][ET] cross terms (rare pass)
     float4 *dcs = reinterpret_cast<float4 *>(xsm + 32 * ET);        // [EPI_WARPS][DC_WARP] domain constants
+    // then [EPI_WARPS][DC_WARP] original domain ids, then the packed constants
+    DcPack *dps = reinterpret_cast<DcPack *>(reinterpret_cast<int *>(dcs + EPI_WARPS * DC_WARP) + EPI_WARPS * DC_WARP);
     __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], a_full, a_empty, tfull_bar[NACC],
         tempty_bar[NACC];
     __shared__ uint32_t tmem_base_s;
     __shared__ int abort_s;
-    __shared__ int ip_s[kMaxBatch + 1], ns_s[kMaxBatch], rt_s[kMaxBatch];
+    constexpr int NSL = BATCH ? kMaxBatch : 1;  // slices of the launch
+    __shared__ int ip_s[NSL + 1], ns_s[NSL], rt_s[NSL];
     __shared__ int item_q[kItemQ];
     __shared__ __align__(8) uint64_t q_full[kItemQ], q_empty[kItemQ];
 
@@ -378,7 +461,7 @@ __device__ __forceinline__ void search_tc_run(const TcMaps &maps, const SliceCtx
         // self-check: every TMA box and MMA operand lies inside this CTA's
         // dynamic shared memory
         const uint32_t used = (uint32_t)(smem - smem_raw) + A_BYTES + STAGES * B_BYTES + 32 * ET * 4 +
-                              EPI_WARPS * DC_WARP * (16 + 4);
+                              EPI_WARPS * DC_WARP * (16 + 4 + 32);
         int bad = 0;
         if (used > smem_bytes) bad = 2;
         if (smem_u32(smem) & 1023u) bad = 4;
@@ -552,6 +635,7 @@ __device__ __forceinline__ void search_tc_run(const TcMaps &maps, const SliceCtx
         const int et = ew * 32 + lane;        // staging column of this thread
         float4 *wdc = dcs + ew * DC_WARP;
         int *wod = reinterpret_cast<int *>(dcs + EPI_WARPS * DC_WARP) + ew * DC_WARP;
+        DcPack *wdp = dps + ew * DC_WARP;
         const uint32_t lane_addr = tmem_base + ((uint32_t)(quad * 32) << 16) + part * EPI_COLS;
         uint32_t aseq = 0;
         bool ok = true;
@@ -579,7 +663,11 @@ __device__ __forceinline__ void search_tc_run(const TcMaps &maps, const SliceCtx
             RangeEpi re{};
             if (live) re = range_epi(c.b.ri[r], ec);
             const float er = (PARTS == 2 && live) ? (float)c.b.ri[r].e_r : 0.0f;  // centring correction factor
+            const f32x2_t er2 = pk2(er, er);
             const bool scr = live && (dense || !re.shadow);
+            // the key every s-code-0 candidate of this range gets (one value:
+            // with c = 0 the key is lambda * w^2 of the offset residue of zb)
+            const float K0 = epi_key(0.0f, 0.0f, 0.0f, re.zb, make_float4(0.f, 0.f, 0.f, 0.f), ec);
             ListState L;
             list_init(L);
             const int ntile = w.t_end - w.t_begin;
@@ -602,6 +690,7 @@ __device__ __forceinline__ void search_tc_run(const TcMaps &maps, const SliceCtx
                 if (lane < DC_WARP) {
                     wdc[lane] = dc_next;
                     wod[lane] = od_next;
+                    wdp[lane] = dc_pack(dc_next, ec);
                 }
                 if (scr && !dump) {
                     const float Tg = ord2f(tb_next);  // best key other CTAs found
@@ -662,10 +751,17 @@ __device__ __forceinline__ void search_tc_run(const TcMaps &maps, const SliceCtx
                             if (j >= nv) X[j] = __int_as_float(0x7fc00000);  // NaN: never listed
                     }
                     const float thr = fminf(L.key[kListK - 1], L.tw);
-                    const float zp = L.has_zero ? kZeroPenalty : 0.0f;
-                    const uint32_t mask = scr && nv > 0
-                                              ? epi_keys32<true>(X, dc, re.zb, re.rho_lim, er, ec, thr, zp) & col_mask(nv)
-                                              : 0u;
+                    // s-code-0 candidates need the penalty only where one is
+                    // listed already and their common key K0 is below the
+                    // threshold (rare): the warp takes the plain keys otherwise
+                    const bool zero_pen = __any_sync(0xffffffffu, scr && L.has_zero && K0 < thr);
+                    uint32_t mask = 0u;
+                    if (zero_pen)
+                        mask = epi_keys32_tc<true>(X, wdp, re.zb, re.rho_lim, er2, ec, thr,
+                                                   L.has_zero ? kZeroPenalty : 0.0f);
+                    else
+                        mask = epi_keys32_tc<false>(X, wdp, re.zb, re.rho_lim, er2, ec, thr, 0.0f);
+                    mask = scr && nv > 0 ? mask & col_mask(nv) : 0u;
                     if (__any_sync(0xffffffffu, mask != 0u))
                         rare_chunk(X, mask, od, dc, er, xsm + et, ET, re, ec, L, tbest + r);
                 }
@@ -747,7 +843,7 @@ size_t search_tc_smem(const Geometry &g)
 {
     const int nblk = g.split_hilo ? 2 : 1, bw = tc_block_width(g);
     return 1024 + (size_t)(nblk * BM * bw * 2 + BM * 32) + (size_t)STAGES * (nblk * BN * bw * 2 + BN * 32) +
-           32 * (32 * EPI_WARPS) * 4 + EPI_WARPS * DC_WARP * (16 + 4);
+           32 * (32 * EPI_WARPS) * 4 + EPI_WARPS * DC_WARP * (16 + 4 + 32);
 }
 
 int search_tc_lists_per_split() { return LISTS; }
@@ -800,6 +896,7 @@ static cudaError_t launch_tc_any(const Geometry &g, const __half *ra16, int arow
                                  int *queue, cudaStream_t st)
 {
     if (!search_tc_supported(g) || n < 1 || n > kMaxBatch || !queue) return cudaErrorInvalidValue;
+    if (!many && n != 1) return cudaErrorInvalidValue;  // the single-search kernel sizes its tables for one slice
     TcMaps mp;
     const int nblk = g.split_hilo ? 2 : 1, bw = tc_block_width(g);
     const CUtensorMapSwizzle sw = bw == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_32B;
