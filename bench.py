@@ -167,6 +167,37 @@ def load_peaks():
         "fallback"
 
 
+def shadow_mask(img, n):
+    """Per range (row-major), whether the n x n block is constant (a shadow
+    range: Section V decides it without a search)."""
+    h, w = img.shape
+    b = img.reshape(h // n, n, w // n, n).transpose(0, 2, 1, 3).reshape(-1, n * n)
+    return b.max(1) == b.min(1)
+
+
+def flat_domains(img, n, t):
+    """Number of 2n x 2n domains at stride t whose 2x2-sum block is constant
+    (flat: zero variance, s = 0 for every candidate)."""
+    from numpy.lib.stride_tricks import sliding_window_view
+
+    q = img.astype(np.int64)
+    q = q[0::2, 0::2] + q[1::2, 0::2] + q[0::2, 1::2] + q[1::2, 1::2]
+    win = sliding_window_view(q, (n, n))[:: t // 2, :: t // 2] if t % 2 == 0 else None
+    if win is None:  # odd stride: domains do not start on the 2x2 grid of q
+        h, w = img.shape
+        cnt = 0
+        for v in range((h - 2 * n) // t + 1):
+            for u in range((w - 2 * n) // t + 1):
+                blk = img[v * t: v * t + 2 * n, u * t: u * t + 2 * n].astype(np.int64)
+                qq = blk[0::2, 0::2] + blk[1::2, 0::2] + blk[0::2, 1::2] + blk[1::2, 1::2]
+                cnt += int(qq.max() == qq.min())
+        return cnt
+    nd_y = (img.shape[0] - 2 * n) // t + 1
+    nd_x = (img.shape[1] - 2 * n) // t + 1
+    win = win[:nd_y, :nd_x]
+    return int((win.max(axis=(2, 3)) == win.min(axis=(2, 3))).sum())
+
+
 def cpu_model():
     """The host CPU's model name (lscpu, else /proc/cpuinfo), for the record."""
     try:
@@ -223,6 +254,39 @@ def cpu_oracle_baseline(img):
             "single_thread_mr256": {"ms": 1e3 * dt1, "comparisons_per_s": r1 * d1 * 8 / dt1,
                                     "workload": "256x256 8-bit MR-like slice, 8x8 ranges, domains at stride 8"}}, \
         psnr_db(img, x, BITS), ref
+
+
+def cpu_oracle_volume(stack, target_s=15.0):
+    """The FP64 oracle on the host cores for the stack: per slice size, a
+    sample of ranges of one slice (evenly spaced, all candidates each), scaled
+    to whole slices; value in slices/s of the whole 96-slice mix."""
+    import oracle
+
+    oracle.build()
+    cores = os.cpu_count() or 1
+    sizes = sorted({a.shape[0] for a in stack})
+    per_slice, notes = {}, []
+    for sz in sizes:
+        a = next(x for x in stack if x.shape[0] == sz)
+        R, D = oracle.counts(sz, sz, RANGE, STRIDE)
+        k = 48
+        sel = np.linspace(0, R - 1, k).astype(np.int32)
+        t0 = time.perf_counter()
+        oracle.encode(a, n=RANGE, t=STRIDE, bit_depth=BITS, ranges=sel, threads=cores)
+        dt = time.perf_counter() - t0
+        k2 = int(min(R, max(k, k * (target_s / len(sizes)) / max(dt, 1e-3))))
+        sel = np.linspace(0, R - 1, k2).astype(np.int32)
+        t0 = time.perf_counter()
+        oracle.encode(a, n=RANGE, t=STRIDE, bit_depth=BITS, ranges=sel, threads=cores)
+        dt = time.perf_counter() - t0
+        per_slice[sz] = dt * R / k2
+        notes.append(f"{sz}x{sz}: {k2} of {R} ranges in {dt:.1f} s")
+    counts = {sz: sum(1 for x in stack if x.shape[0] == sz) for sz in sizes}
+    t_stack = sum(counts[sz] * per_slice[sz] for sz in sizes)
+    return {"value": len(stack) / t_stack, "unit": "slices/s", "cores": cores, "kind": "oracle",
+            "cpu_model": cpu_model(), "ms_per_step": 1e3 * t_stack,
+            "sample": "per size, evenly spaced ranges of one slice (all candidates each) scaled to whole slices: "
+                      + "; ".join(notes)}
 
 
 def run_reference(args):
@@ -333,6 +397,48 @@ def run_quadtree(args):
     t_total = float(np.sum([a.elapsed_time(b) for a, b in ev])) / 1e3
     t_total = max_over_ranks(t_total, ws, dev)
     value = job_rate(ws, args.steps, comps, t_total)
+    # the search of each level timed alone: events the library records around
+    # each level's search launch on the stream (FIC_FLAG_PHASE_TIMING)
+    pt = fic.params(range_size=16, domain_stride=16, bit_depth=BITS, flags=fic.FIC_FLAG_PHASE_TIMING)
+    lvl_ms = []
+    for _ in range(max(5, min(args.steps, 20))):
+        flush.zero_()
+        fic.encode_quadtree(img, pt, 4, 8.0, maps=maps, workspace=work, stream=stream)
+        lvl_ms.append(fic.last_quadtree_phase_ms())
+    lvl_ms = np.median(np.array(lvl_ms), axis=0)
+    leaves = fic.qmaps_to_numpy(maps, int(n_leaves))
+    for lvl, d in enumerate(per_level):
+        d["search_ms"] = float(lvl_ms[lvl])
+        # screened candidates of the level: its active ranges that are not
+        # constant (shadow) x its domains that are not flat x 8
+        n = d["range_size"]
+        sh = shadow_mask(img_np, n)
+        nx = N_PIX // n
+        act = np.zeros((N_PIX // n) ** 2, bool)
+        for j in range(lvl, 3):  # leaves at this level and below descend from the level's active ranges
+            sel = leaves[leaves["level"] == j]
+            act[(sel["y"] // n) * nx + sel["x"] // n] = True
+        d["screened"] = int((act & ~sh).sum()) * (d["domains"] - flat_domains(img_np, n, n)) * 8
+    top = int(np.argmax(lvl_ms[: len(per_level)]))
+    peaks, peak_kind = load_peaks()
+    alu_peak = sm_count(dev) * 128 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    d = per_level[top]
+    kern_s = d["search_ms"] * 1e-3
+    if d["search"] == "tc":
+        ops = EPI_OPS_PER_CANDIDATE
+        roof = {"bound": "alu", "achieved": d["screened"] * ops / kern_s / 1e12, "peak": alu_peak, "unit": "Tops/s",
+                "ops_per_unit": ops,
+                "tensor": {"bound": "tensor", "achieved": d["screened"] * 2 * d["range_size"] ** 2 / kern_s / 1e12,
+                           "peak": peaks["bf16_tflops"], "unit": "TFLOP/s", "flops_per_unit": 2 * d["range_size"] ** 2}}
+        roof["tensor"]["frac"] = roof["tensor"]["achieved"] / roof["tensor"]["peak"]
+    else:
+        ops = d["range_size"] ** 2 + EPI_OPS_PER_CANDIDATE
+        roof = {"bound": "alu", "achieved": d["screened"] * ops / kern_s / 1e12, "peak": alu_peak, "unit": "Tops/s",
+                "ops_per_unit": ops}
+    roof.update({"frac": roof["achieved"] / roof["peak"], "units": d["screened"], "traffic": None,
+                 "kernel": f"search of level {top} ({d['range_size']}x{d['range_size']} ranges, {d['search']})",
+                 "peak_source": peak_kind + "; FP32 lanes x max clock for the ALU view",
+                 "search_ms_per_level": [float(x) for x in lvl_ms[: len(per_level)]]})
     # end to end from pinned host memory through the C ABI (image H2D, leaves D2H)
     h_img = torch.from_numpy(img_np.astype(np.int16)).pin_memory()
     h_maps = np.zeros(cap, fic.QMAP_DTYPE)
@@ -358,7 +464,7 @@ def run_quadtree(args):
                     "timing": "host wall clock (the call waits for its stream)"},
             # per level the seven encode kernels and the split test; then the
             # leaf count and the leaf gather
-            "gpu_launches": args.steps * (8 * len(per_level) + 2), "clocks": clocks, "roofline": None}
+            "gpu_launches": args.steps * (8 * len(per_level) + 2), "clocks": clocks, "roofline": roof}
     if rank == 0:
         if ws == 1 and not args.no_cpu_baseline:
             import oracle
@@ -450,10 +556,15 @@ def run_volume(args):
     t_total = max_over_ranks(t_total, ws_n, dev)
     n_sl = len(stack)
     value = job_rate(ws_n, args.steps, n_sl, t_total)
-    # per-slice completion times within a batch (separate runs: reading them waits for the batch)
-    for _ in range(args.steps):
+    # latency of a whole batch (every slice's maps are ready when its batch
+    # is): events around each of >= 20 separate replays, each waited for
+    for _ in range(max(20, args.steps)):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
         fic.encode_batch(tab, p, work, stream)
-        lat.extend(fic.last_batch_slice_ms(n_sl))
+        b.record(stream)
+        b.synchronize()
+        lat.append(a.elapsed_time(b))
     # end to end: pinned host stack -> device, batch, maps -> pinned host
     h_imgs = [torch.from_numpy(a.astype(np.int16)).pin_memory() for a in stack]
     h_maps = [torch.empty(m.numel(), dtype=torch.uint8).pin_memory() for m in maps]
@@ -480,21 +591,45 @@ def run_volume(args):
     clocks["window_s"] = clk_window
     clocks["note"] = "sampled over the timed steps and the identical steps that follow them"
     lat = np.array(lat)
+    # the batch's screened candidates (shadow ranges and flat domains are
+    # decided without a cross term); ALU view of the whole batch: the
+    # screening key's FP32 operations over the batch's time (the search is
+    # the largest stage, not the only one, so this bounds its fraction from below)
+    screened = 0
+    for a in stack:
+        R, D = fic.counts(a.shape[1], a.shape[0], p)
+        screened += (R - int(shadow_mask(a, RANGE).sum())) * (D - flat_domains(a, RANGE, STRIDE)) * 8
+    peaks, peak_kind = load_peaks()
+    alu_peak = sm_count(dev) * 128 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    step_s = t_total / args.steps
+    roof = {"bound": "alu", "achieved": screened * EPI_OPS_PER_CANDIDATE / step_s / 1e12, "peak": alu_peak,
+            "unit": "Tops/s", "ops_per_unit": EPI_OPS_PER_CANDIDATE, "units": screened, "traffic": None,
+            "kernel": "whole batch (one graph replay: statistics, compaction, rows, search, re-score, scans, output)",
+            "peak_source": peak_kind + "; FP32 lanes x max clock",
+            "tensor": {"bound": "tensor", "achieved": screened * 2 * RANGE * RANGE / step_s / 1e12,
+                       "peak": peaks["bf16_tflops"], "unit": "TFLOP/s", "flops_per_unit": 2 * RANGE * RANGE}}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["tensor"]["frac"] = roof["tensor"]["achieved"] / roof["tensor"]["peak"]
     line = {"metric": "slices/s", "value": value, "unit": "slices/s", "n_gpus": ws_n, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": 1e3 * t_total / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "fp16+fp32", "data": "synthetic",
             "config": {"workload": VOL_WORKLOAD, "slices": n_sl, "comparisons_per_step": comps,
                        "comparisons_per_s": job_rate(ws_n, args.steps, comps, t_total),
-                       "slice_completion_ms": {"p50": float(np.percentile(lat, 50)),
-                                               "p99": float(np.percentile(lat, 99)), "max": float(lat.max()),
-                                               "note": "time from the start of the batch to each slice's maps "
-                                                       "(every stage covers all slices: they complete together)"},
+                       "slice_latency_ms": {"p50": float(np.percentile(lat, 50)),
+                                            "p99": float(np.percentile(lat, 99)), "max": float(lat.max()),
+                                            "replays": int(lat.size),
+                                            "note": "per-replay latency of the batch (CUDA events around each "
+                                                    "replay, run one at a time): every stage covers all slices, "
+                                                    "so each slice's maps are ready when its batch is"},
+                       "screened_comparisons_per_step": screened,
                        "l2": "working set of the batch (several GB) is larger than L2"},
             "e2e": {"value": job_rate(ws_n, args.steps, n_sl, e2e_t), "unit": "slices/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": args.steps * batch_launches([a.shape[0] * a.shape[1] for a in stack]), "clocks": clocks,
-            "roofline": None}
+            "roofline": roof}
     if rank == 0:
+        if ws_n == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_oracle_volume(stack)
         print(json.dumps(line), flush=True)
     if ws_n > 1:
         dist.destroy_process_group()
@@ -552,9 +687,49 @@ def run_refine(args):
     t = e0.elapsed_time(e1) / 1e3
     L = loss.cpu().numpy()
     before, after = psnr(s0, o0), psnr(s, o)
+    # end to end: the image, the maps and the starting coefficients copied in
+    # from pinned host memory, the whole refinement, the refined s, o and the
+    # loss curve copied back
+    h_img = torch.from_numpy(img_np.astype(np.int16)).pin_memory()
+    h_maps = maps.cpu().pin_memory()
+    h_s0, h_o0 = s0.cpu().pin_memory(), o0.cpu().pin_memory()
+    h_s, h_o, h_loss = (torch.empty_like(h_s0).pin_memory(), torch.empty_like(h_o0).pin_memory(),
+                        torch.empty(steps + 1, dtype=torch.float32).pin_memory())
+    d_img, d_maps = torch.empty_like(img), torch.empty_like(maps)
+    d_s, d_o = torch.empty_like(s0), torch.empty_like(o0)
+    torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record()
+    d_img.copy_(h_img, non_blocking=True)
+    d_maps.copy_(h_maps, non_blocking=True)
+    d_s.copy_(h_s0, non_blocking=True)
+    d_o.copy_(h_o0, non_blocking=True)
+    lo = fic.refine(d_img, d_maps, d_s, d_o, p, steps=steps, iters=T, lr=lr, workspace=work)
+    h_s.copy_(d_s, non_blocking=True)
+    h_o.copy_(d_o, non_blocking=True)
+    h_loss.copy_(lo, non_blocking=True)
+    f1.record()
+    torch.cuda.synchronize()
+    t_e2e = f0.elapsed_time(f1) / 1e3
+    h2d = h_img.numel() * 2 + h_maps.numel() + 8 * h_s0.numel()
+    d2h = 8 * h_s0.numel() + 4 * (steps + 1)
     clocks = clk.summary()
     clocks["window_s"] = clk_window
     clocks["note"] = "sampled over the timed refinement and identical ones that follow it"
+    # algorithmic bytes of one step (W*H pixels, FP32 iterates): the forward
+    # reads and writes an iterate per iteration (8 T N), the loss reads x_T and
+    # the image and writes dL/dx_T (10 N), the reverse sweep recomputes the odd
+    # iterates from the even checkpoints (4 T N) and per iteration reads x_t
+    # and the adjoint and writes the next adjoint (12 T N)
+    npx = N_PIX * N_PIX
+    step_bytes = (24 * T + 10) * npx
+    peaks, peak_kind = load_peaks()
+    roof = {"bound": "hbm", "achieved": step_bytes / (t / steps) / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "bytes_per_unit": step_bytes, "units": 1, "traffic": None,
+            "kernel": "whole step (one graph replay of 45 launches; the adjoint item kernel is the largest)",
+            "peak_source": peak_kind,
+            "note": "the iterates (1 MB each) stay in L2: the step is bound by launch and latency, not by HBM"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
     line = {"metric": "refinement steps/s", "value": steps / t, "unit": "steps/s", "n_gpus": 1, "steps": steps,
             "warmup": max(3, args.warmup), "ms_per_step": 1e3 * t / steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -563,7 +738,11 @@ def run_refine(args):
                        "loss_first": float(L[0]), "loss_last": float(L[-1])},
             # per step: fill + T forward iterations, 2 loss kernels, T/2 recomputed
             # iterates, T per-range gradients, 3 (T - 1) adjoint kernels, Adam
-            "e2e": None, "gpu_launches": steps * (5 * T + T // 2 + 1), "clocks": clocks, "roofline": None}
+            "psnr_gain_db": after - before, "psnr_refined_db": after,
+            "e2e": {"value": steps / t_e2e, "unit": "steps/s", "h2d_bytes_per_step": h2d / steps,
+                    "d2h_bytes_per_step": d2h / steps,
+                    "timing": "one whole refinement (inputs in, 200 steps, results out), per step"},
+            "gpu_launches": steps * (5 * T + T // 2 + 1), "clocks": clocks, "roofline": roof}
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -745,17 +924,8 @@ def main():
     other_dense_t = timed_arm(podense, wsod, args.steps)
 
     # what the skips leave to screen (host-side count from the image itself)
-    n = RANGE
-    blocks = img_np.reshape(N_PIX // n, n, N_PIX // n, n).transpose(0, 2, 1, 3).reshape(-1, n * n)
-    shadow = int((blocks.max(1) == blocks.min(1)).sum())
-    q = img_np.astype(np.int64)
-    q = q[0::2, 0::2] + q[1::2, 0::2] + q[0::2, 1::2] + q[1::2, 1::2]
-    nd = (N_PIX - 2 * n) // STRIDE + 1
-    flat = 0
-    for v in range(nd):
-        for u in range(nd):
-            blk = q[v * STRIDE // 2: v * STRIDE // 2 + n, u * STRIDE // 2: u * STRIDE // 2 + n]
-            flat += int(blk.max() == blk.min())
+    shadow = int(shadow_mask(img_np, RANGE).sum())
+    flat = flat_domains(img_np, RANGE, STRIDE)
     screened = (R - shadow) * (D - flat) * 8
 
     phase_med = phases_of(p, work)

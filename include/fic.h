@@ -261,7 +261,8 @@ typedef struct {
  *   them.
  *   Sizes: range_size 16 or 8, min_size 4, 8 or 16 with min_size <=
  *   range_size; w and h multiples of range_size, at least 2*range_size.
- *   FIC_FLAG_PHASE_TIMING is rejected.
+ *   FIC_FLAG_PHASE_TIMING: record events around each level's search (read
+ *   them with fic_last_quadtree_phase_ms).
  */
 int fic_encode_quadtree(const void *img, int w, int h, int pitch_px, const fic_params *p, int min_size,
                         float rms_split, fic_qmap *maps, int maps_cap, int *n_maps, void *workspace,
@@ -273,6 +274,11 @@ int fic_quadtree_workspace_size(int w, int h, const fic_params *p, int min_size,
  * (FIC_SEARCH_*), CTA target of its candidate split (waves x SMs), ranges
  * screened (active), leaves kept. */
 int fic_last_quadtree_stats(int64_t out[17]);
+
+/* Search time (ms) of each level of the last fic_encode_quadtree on this host
+ * thread that ran with FIC_FLAG_PHASE_TIMING: out[l] for level l (0 past the
+ * last level).  Waits for those events; FIC_ERR_BAD_ARG if there are none. */
+int fic_last_quadtree_phase_ms(double out[3]);
 
 /* One slice of a batch (fic_encode_batch); every pointer is device memory. */
 typedef struct {

@@ -38,6 +38,25 @@ struct PhaseEvents {
 };
 thread_local PhaseEvents g_phase;
 
+// Events around the search of each quadtree level (fic_encode_quadtree with
+// FIC_FLAG_PHASE_TIMING).
+struct QtPhaseEvents {
+    cudaEvent_t ev[kMaxLevels][2] = {};
+    int levels = 0;
+    bool valid = false;
+    bool ensure()
+    {
+        for (auto &l : ev)
+            for (auto &e : l)
+                if (!e && cudaEventCreate(&e) != cudaSuccess) {
+                    cudaGetLastError();
+                    return false;
+                }
+        return true;
+    }
+};
+thread_local QtPhaseEvents g_qt_phase;
+
 constexpr size_t kAlign = 256;
 size_t align_up(size_t v) { return (v + kAlign - 1) & ~(kAlign - 1); }
 
@@ -351,7 +370,7 @@ EncBufs enc_bufs(const EncLayout &L, char *ws)
 // contraction and write the raw cross terms there.
 cudaError_t encode_pipeline(const Geometry &gd, const fic_params *p, int search, int n_split, int target,
                             const EncLayout &L, char *ws, const void *dimg, const int *active, fic_map *dmaps,
-                            float *dump, bool timed, cudaStream_t st)
+                            float *dump, bool timed, cudaStream_t st, const cudaEvent_t *search_ev = nullptr)
 {
     const EncBufs b = enc_bufs(L, ws);
     const int n_lists = n_split * lists_per_split(search);
@@ -373,12 +392,14 @@ cudaError_t encode_pipeline(const Geometry &gd, const fic_params *p, int search,
     FIC_STEP(launch_prep(gd, dimg, ec, dense, (search == FIC_SEARCH_TC && gd.split_hilo) ? 1 : 0, active, b.ri, b.di, b.dconst, b.bblk, b.qblk, b.rs32, b.cb32, b.ra16,
                          b.cb16, b.tbest, b.cb, b.fb_count, dump ? 0 : 1, st));
     FIC_MARK(1);
+    if (search_ev) FIC_STEP(cudaEventRecord(search_ev[0], st));
     if (search == FIC_SEARCH_TC)
         FIC_STEP(launch_search_tc(gd, ec, b.ri, b.cb, dense, b.ra16, b.cb16, b.lists, n_split, target, b.tbest, dump,
                                   b.err, b.fb_count + 3, st));
     else
         FIC_STEP(launch_search_simt(gd, ec, b.ri, b.di, b.cb, dense, b.rs32, b.cb32, b.lists, n_split, target, b.tbest,
                                     dump, st));
+    if (search_ev) FIC_STEP(cudaEventRecord(search_ev[1], st));
     FIC_MARK(2);
     if (!dump) {
         FIC_STEP(launch_rescore(gd, ec, b.ri, b.di, b.bblk, b.qblk, b.lists, n_lists, b.cb.counts, b.cb.act, b.cb.rkeep,
@@ -508,7 +529,6 @@ int qt_plan(int w, int h, int pitch, const fic_params *p, int min_size, int maps
     if (!p) return FIC_ERR_BAD_ARG;
     int rc = check_params(p);
     if (rc != FIC_OK) return rc;
-    if (p->flags & FIC_FLAG_PHASE_TIMING) return FIC_ERR_BAD_ARG;
     const int nmax = p->range_size;
     if (nmax != 8 && nmax != 16) return FIC_ERR_BAD_ARG;
     if ((min_size != 4 && min_size != 8 && min_size != 16) || min_size > nmax) return FIC_ERR_BAD_ARG;
@@ -522,6 +542,7 @@ int qt_plan(int w, int h, int pitch, const fic_params *p, int min_size, int maps
     Q.enc_bytes = 0;
     for (int l = 0; l < Q.levels; ++l) {
         Q.pl[l] = *p;
+        Q.pl[l].flags &= ~FIC_FLAG_PHASE_TIMING;  // a level's own phases are not recorded
         Q.pl[l].range_size = nmax >> l;
         Q.pl[l].domain_stride = nmax >> l;
         rc = make_geometry(w, h, pitch, &Q.pl[l], Q.g[l]);
@@ -618,6 +639,8 @@ int run_quadtree(const void *img, int w, int h, int pitch_px, const fic_params *
         QtLevels lv;
         lv.levels = Q.levels;
         int list_off = 0;
+        const bool timed = (p->flags & FIC_FLAG_PHASE_TIMING) && g_qt_phase.ensure();
+        g_qt_phase.valid = false;
         g_qt_stats[0] = Q.levels;
         for (int l = 0; l < Q.levels; ++l) {
             Geometry g = Q.g[l];
@@ -635,7 +658,7 @@ int run_quadtree(const void *img, int w, int h, int pitch_px, const fic_params *
             else if (p->search == FIC_SEARCH_TC) ch.search = FIC_SEARCH_TC;
             else ch.search = tc_ok ? FIC_SEARCH_TC : FIC_SEARCH_SIMT;
             if (p->n_split == 0) {
-                const TuneKey key{w, h, g.n, g.B, g.s_bits, g.o_bits, (int)p->flags, p->search};
+                const TuneKey key{w, h, g.n, g.B, g.s_bits, g.o_bits, (int)pl->flags, p->search};
                 bool have = false;
                 {
                     std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -668,7 +691,8 @@ int run_quadtree(const void *img, int w, int h, int pitch_px, const fic_params *
             const int n_split = choose_split(g, pl, ch.search);
             const int target = p->n_split > 0 ? split_target(pl, ch.search) : target_for(ch.search, ch.waves);
             const EncLayout L = enc_layout(g, ch.search, n_split * lists_per_split(ch.search));
-            FIC_CUDA(encode_pipeline(g, pl, ch.search, n_split, target, L, ews, dimg, active, lmaps, nullptr, false, st));
+            FIC_CUDA(encode_pipeline(g, pl, ch.search, n_split, target, L, ews, dimg, active, lmaps, nullptr, false, st,
+                                     timed ? g_qt_phase.ev[l] : nullptr));
             if (l + 1 < Q.levels)
                 FIC_CUDA(cudaMemsetAsync(active_next, 0, sizeof(int) * Q.g[l + 1].R, st));
             FIC_CUDA(launch_qt_split(g.R, g.nx, g.m, lmaps, active, (double)rms_split, l + 1 == Q.levels ? 1 : 0, leaf,
@@ -684,6 +708,8 @@ int run_quadtree(const void *img, int w, int h, int pitch_px, const fic_params *
             g_qt_stats[1 + 4 * l] = ch.search;
             g_qt_stats[2 + 4 * l] = target;
         }
+        g_qt_phase.levels = Q.levels;
+        g_qt_phase.valid = timed;
         fic_qmap *dout = maps_dev ? maps : reinterpret_cast<fic_qmap *>(ws + Q.stage);
         FIC_CUDA(launch_qt_gather(lv, reinterpret_cast<int *>(ws + Q.lists), dout, maps_cap, counts, st));
         int hc[2 + 2 * kMaxLevels];
@@ -1380,6 +1406,24 @@ int fic_last_quadtree_stats(int64_t out[17])
     if (!out) return FIC_ERR_BAD_ARG;
     for (int i = 0; i < 1 + 4 * kMaxLevels; ++i) out[i] = g_qt_stats[i];
     for (int i = 1 + 4 * kMaxLevels; i < 17; ++i) out[i] = 0;
+    return FIC_OK;
+}
+
+int fic_last_quadtree_phase_ms(double out[3])
+{
+    if (!out) return FIC_ERR_BAD_ARG;
+    if (!g_qt_phase.valid) return FIC_ERR_BAD_ARG;
+    for (int l = 0; l < kMaxLevels; ++l) {
+        out[l] = 0.0;
+        if (l >= g_qt_phase.levels) continue;
+        float ms = 0.0f;
+        if (cudaEventSynchronize(g_qt_phase.ev[l][1]) != cudaSuccess ||
+            cudaEventElapsedTime(&ms, g_qt_phase.ev[l][0], g_qt_phase.ev[l][1]) != cudaSuccess) {
+            cudaGetLastError();
+            return FIC_ERR_CUDA;
+        }
+        out[l] = ms;
+    }
     return FIC_OK;
 }
 

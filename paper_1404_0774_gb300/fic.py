@@ -79,6 +79,7 @@ def lib():
                                           ctypes.c_float, vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), vp, sz, vp]
         L.fic_quadtree_workspace_size.argtypes = [ctypes.c_int, ctypes.c_int, pp, ctypes.c_int, ctypes.POINTER(sz)]
         L.fic_last_quadtree_stats.argtypes = [i64p]
+        L.fic_last_quadtree_phase_ms.argtypes = [ctypes.POINTER(ctypes.c_double)]
         L.fic_encode_batch.argtypes = [vp, ctypes.c_int, pp, vp, sz, vp]
         L.fic_batch_workspace_size.argtypes = [vp, ctypes.c_int, pp, ctypes.POINTER(sz)]
         L.fic_last_batch_slice_ms.argtypes = [ctypes.POINTER(ctypes.c_float), ctypes.c_int]
@@ -261,6 +262,14 @@ def last_quadtree_stats():
     """[levels, then per level: search kernel, CTA target, ranges screened, leaves]."""
     out = (ctypes.c_int64 * 17)()
     _check(lib().fic_last_quadtree_stats(out), "fic_last_quadtree_stats")
+    return list(out)
+
+
+def last_quadtree_phase_ms():
+    """Search ms of each level of the last quadtree encode run with
+    FIC_FLAG_PHASE_TIMING (waits for its events)."""
+    out = (ctypes.c_double * 3)()
+    _check(lib().fic_last_quadtree_phase_ms(out), "fic_last_quadtree_phase_ms")
     return list(out)
 
 
