@@ -192,6 +192,18 @@ int split_target(const fic_params *p, int search)
     return (search == FIC_SEARCH_TC ? 3 : 8) * sm_count();
 }
 
+// How the search forms the cross term, for the statistics' error allowances:
+// 0 with the FP32 search or the exact 8-bit tensor-core layout (centring in
+// the MMA), 1 with exact hi/lo tensor-core accumulators (12-bit, K <= 64), 2
+// with tensor-core accumulation over K = 256 per part (16x16 ranges); 1 and 2
+// fold the centring correction into the epilogue.
+int tc_mode_of(const Geometry &g, int search)
+{
+    if (search != FIC_SEARCH_TC) return 0;
+    if (g.m == 256) return 2;
+    return g.split_hilo ? 1 : 0;
+}
+
 int lists_per_split(int search)
 {
     return search == FIC_SEARCH_SIMT ? search_simt_lists_per_split() : search_tc_lists_per_split();
@@ -389,7 +401,7 @@ cudaError_t encode_pipeline(const Geometry &gd, const fic_params *p, int search,
     // whatever they hold only reaches accumulator rows and columns that the
     // epilogue ignores; the exact-scan queue counters are zeroed by k_stats)
     FIC_MARK(0);
-    FIC_STEP(launch_prep(gd, dimg, ec, dense, (search == FIC_SEARCH_TC && gd.split_hilo) ? 1 : 0, active, b.ri, b.di, b.dconst, b.bblk, b.qblk, b.rs32, b.cb32, b.ra16,
+    FIC_STEP(launch_prep(gd, dimg, ec, dense, tc_mode_of(gd, search), active, b.ri, b.di, b.dconst, b.bblk, b.qblk, b.rs32, b.cb32, b.ra16,
                          b.cb16, b.tbest, b.cb, b.fb_count, dump ? 0 : 1, st));
     FIC_MARK(1);
     if (search_ev) FIC_STEP(cudaEventRecord(search_ev[0], st));
@@ -911,7 +923,7 @@ cudaError_t batch_pipeline(const BatchPlan &P, const fic_params *p, char *ws, in
     cudaError_t e = cudaSuccess;
     for (auto &gr : groups)
         if ((e = launch_stats_batch(dctx + gr.first, gr.second, stats_grid(P.sl[P.order[k0 + gr.first]].g), dense,
-                                    (tc && g0.split_hilo) ? 1 : 0, st)) != cudaSuccess)
+                                    tc_mode_of(g0, tc ? FIC_SEARCH_TC : FIC_SEARCH_SIMT), st)) != cudaSuccess)
             return e;
     for (auto &gr : groups)
         if ((e = launch_compact_seed_batch(dctx + gr.first, gr.second, ranges_of(gr.first),

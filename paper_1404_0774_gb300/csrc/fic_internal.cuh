@@ -515,19 +515,22 @@ struct SliceCtx {
 // Number of candidate-dimension splits actually used: enough work items for
 // about `target` (a few waves over the SMs) given the number of row tiles
 // that have ranges to screen, capped by the list layout (max_split) and by
-// kMinSplitTiles candidate tiles per split (so that a work item amortises its
-// setup and its lists see enough candidates to tighten; the persistent
-// tensor-core search, recognised by its column tile, only: the FP32 search
-// launches one short CTA per item and wants the items).
+// a minimum number of candidate tiles per split (so that a work item
+// amortises its setup and its lists see enough candidates to tighten; the
+// persistent tensor-core search, recognised by its column tile, only: the
+// FP32 search launches one short CTA per item and wants the items).  A
+// tensor-core tile of 16x16 ranges (m = 256) is four times the MMA and copy
+// work of one of 8x8 ranges, and the level of a quadtree that uses it has few
+// ranges: there one tile per split suffices.
 constexpr int kMinSplitTiles = 12;
 __host__ __device__ __forceinline__ int active_splits(int row_tiles, int col_tiles, int target, int max_split,
-                                                     int col_tile)
+                                                     int col_tile, int m)
 {
     if (row_tiles <= 0 || col_tiles <= 0) return 1;
     int s = target / row_tiles;
     s = s < 1 ? 1 : s;
     s = s > max_split ? max_split : s;
-    const int by_tiles = col_tile == 96 ? col_tiles / kMinSplitTiles : col_tiles;
+    const int by_tiles = col_tile == 96 ? col_tiles / (m >= 256 ? 1 : kMinSplitTiles) : col_tiles;
     s = s > by_tiles ? by_tiles : s;
     return s < 1 ? 1 : s;
 }
@@ -568,7 +571,7 @@ int search_simt_lists_per_split();
 // launch per stage over the slices (the per-slice stages: once per group of
 // equal slices).
 int stats_grid(const Geometry &g);  // blocks of the statistics launch of one slice
-cudaError_t launch_stats_batch(const SliceCtx *ctx, int n, int blocks, int dense, int tc_split, cudaStream_t st);
+cudaError_t launch_stats_batch(const SliceCtx *ctx, int n, int blocks, int dense, int tc_mode, cudaStream_t st);
 cudaError_t launch_compact_seed_batch(const SliceCtx *ctx, int n, int ranges, int m, cudaStream_t st);
 cudaError_t launch_rows_batch(const SliceCtx *ctx, int n, int blocks, cudaStream_t st);
 cudaError_t launch_search_tc_batch(const Geometry &g, const __half *ra16, int arows, const __half *cb16, int brows,
@@ -613,7 +616,7 @@ __device__ __forceinline__ RangeEpi range_epi(const RangeInfo &ri, const EpiCons
     re.shadow = ri.shadow;
     return re;
 }
-cudaError_t launch_prep(const Geometry &g, const void *img, const EpiConst &ec, int dense, int tc_split,
+cudaError_t launch_prep(const Geometry &g, const void *img, const EpiConst &ec, int dense, int tc_mode,
                         const int *active,
                         RangeInfo *ri, DomainInfo *di, float4 *dconst, uint16_t *bblk, uint16_t *qblk, float *rs32,
                         float *cb32, __half *ra16, __half *cb16, int *tbest, const CompactBufs &cb, int *zero4,

@@ -39,7 +39,7 @@ __device__ __forceinline__ T group_sum(T v, int G)
 // all when dense).  `valid` is false for the lanes of a group past the last
 // range: they take part in the reductions only.
 __device__ __forceinline__ void range_stats(const Geometry &g, const EpiConst &ec, const void *img, int dense,
-                                            int tc_split, const int *active, int r, bool valid, int li, int G,
+                                            int tc_mode, const int *active, int r, bool valid, int li, int G,
                                             RangeInfo *ri, uint16_t *bblk, int *tbest, int *rkeep)
 {
     const int rr = valid ? r : 0;
@@ -92,14 +92,22 @@ __device__ __forceinline__ void range_stats(const Geometry &g, const EpiConst &e
     info.zb = (float)(g.mod_g ? z % g.Gi : z);
     info.bp2 = bp2f;
     // FP32 error of Ls*s: ~1e-6 when the cross term is exact, plus the
-    // accumulation error of high-variance pairs (grows with sum (b-c_r)^2).
-    // With the tensor-core search's separate hi/lo accumulators the cross
-    // term X' is exact but for the rounding of hi + lo and of the folded
-    // correction: relative errors of 2^-23 of (|X'| + |corr|), |corr| <=
-    // |e_r|/2, times alpha <= 2m/(m-1) < 2.1 and 2 Ls.
+    // accumulation error of high-variance pairs (grows with sum (b-c_r)^2):
+    // FP32 sums of integer products are exact below 2^24, so an error needs
+    // |q'| |b'| above it, and is then at most K u |q'| |b'|, which moves Ls*s
+    // by at most ~4 Ls K u^2 |b'|^2 (den ~ m |q'|^2), u = 2^-24, K = m terms.
+    // tc_mode 1 (the tensor-core search's separate hi/lo accumulators, K <=
+    // 64): the cross term X' is exact but for the rounding of hi + lo and of
+    // the folded correction: relative errors of 2^-23 of (|X'| + |corr|),
+    // |corr| <= |e_r|/2, times alpha <= 2m/(m-1) < 2.1 and 2 Ls.  tc_mode 2
+    // (tensor cores with K = 256 per part): both error sources, the
+    // accumulation bound doubled (the hardware's order of the FP32 additions
+    // is not specified).
     const float er_abs = fabsf((float)e_r);
-    const float eta = tc_split ? 1e-5f + 1.2e-7f * g.Ls * (2.0f + 2.1f * er_abs)
-                               : 1e-5f + 12.0f * g.Ls * 64.0f * bp2f * 3.552713678800501e-15f;  // 2^-48
+    const float acc_err = 12.0f * g.Ls * (float)max(64, g.m) * bp2f * 3.552713678800501e-15f;  // 2^-48
+    const float eta = tc_mode == 1   ? 1e-5f + 1.2e-7f * g.Ls * (2.0f + 2.1f * er_abs)
+                      : tc_mode == 2 ? 1e-5f + 2.0f * acc_err + 1.2e-7f * g.Ls * (2.0f + 2.1f * er_abs)
+                                     : 1e-5f + acc_err;
     info.rho_lim = 0.5f - fminf(eta, 0.25f);
     // Screening allowance.  A candidate within reach of the winner has
     // |c| * sqrt(sum (q-q_mean)^2) <= 4*Ls*(sqrt(Sbb_c) + sqrt(R)), R <= Eb; its
@@ -111,12 +119,12 @@ __device__ __forceinline__ void range_stats(const Geometry &g, const EpiConst &e
     const float sb = sqrtf(bp2f);
     const float sqm = sqrtf((float)g.m);
     const float S = (4.0f * g.Ls * (sqrtf(sbbc) + sqrtf(Eb)) + sqm) * sb + (g.split_hilo ? 128.0f * sqm * sb : 0.0f);
-    const bool exact = tc_split || S < 8.0e6f;  // < 2^23 with margin, or exact partial sums
+    const bool exact = tc_mode == 1 || S < 8.0e6f;  // < 2^23 with margin, or exact partial sums
     const float gam = 3.0517578125e-05f;  // 2^-15
+    const float corr_a = tc_mode != 0 ? 9.5367431640625e-07f * g.Ls * er_abs : 0.0f;  // 2^-20: the folded correction
     info.beta_q = exact ? 0.0f : 4.0f * g.Ls * gam * sb;
-    info.beta_a = 3.814697265625e-06f * 2.0f * g.Ls * (sbbc + ec.delta_o) + 1e-3f +
-                  (exact ? (tc_split ? 9.5367431640625e-07f * g.Ls * er_abs : 0.0f)  // 2^-20
-                         : gam * g.Ls * 128.0f * sqm * sb);
+    info.beta_a = 3.814697265625e-06f * 2.0f * g.Ls * (sbbc + ec.delta_o) + 1e-3f + corr_a +
+                  (exact ? 0.0f : gam * g.Ls * 128.0f * sqm * sb);
     info.shadow = bmin == bmax ? 1 : 0;
     info.pad = 0;
     ri[r] = info;
@@ -191,7 +199,7 @@ __device__ __forceinline__ void domain_stats(const Geometry &g, const void *img,
 // Statistics of every range (the first stats_range_blocks blocks) and every
 // domain (the blocks after), one launch; stats_items per block of 256.
 __device__ __forceinline__ void stats_block(const Geometry &g, const EpiConst &ec, const void *img, int dense,
-                                            int tc_split, const int *active, RangeInfo *ri, uint16_t *bblk,
+                                            int tc_mode, const int *active, RangeInfo *ri, uint16_t *bblk,
                                             int *tbest, DomainInfo *di, float4 *dconst, uint16_t *qblk, int *rkeep,
                                             int *dkeep, int *zero4, int bx)
 {
@@ -201,31 +209,31 @@ __device__ __forceinline__ void stats_block(const Geometry &g, const EpiConst &e
     const int item = threadIdx.x / G;  // (warp, group) in order
     if (bx < rbs) {
         const int r = bx * per_block + item;
-        range_stats(g, ec, img, dense, tc_split, active, r, r < g.R, li, G, ri, bblk, tbest, rkeep);
+        range_stats(g, ec, img, dense, tc_mode, active, r, r < g.R, li, G, ri, bblk, tbest, rkeep);
     } else {
         const int d = (bx - rbs) * per_block + item;
         domain_stats(g, img, dense, d, d < g.D, li, G, di, dconst, qblk, dkeep);
     }
 }
 
-__global__ void __launch_bounds__(256) k_stats(Geometry g, EpiConst ec, const void *img, int dense, int tc_split,
+__global__ void __launch_bounds__(256) k_stats(Geometry g, EpiConst ec, const void *img, int dense, int tc_mode,
                                                const int *active, RangeInfo *ri, uint16_t *bblk, int *tbest,
                                                DomainInfo *di, float4 *dconst, uint16_t *qblk, int *rkeep,
                                                int *dkeep, int *zero4)
 {
     grid_dep_sync();
-    stats_block(g, ec, img, dense, tc_split, active, ri, bblk, tbest, di, dconst, qblk, rkeep, dkeep, zero4,
+    stats_block(g, ec, img, dense, tc_mode, active, ri, bblk, tbest, di, dconst, qblk, rkeep, dkeep, zero4,
                 blockIdx.x);
 }
 
 // Batched: blockIdx.y = slice.
-__global__ void __launch_bounds__(256) k_stats_batch(const SliceCtx *__restrict__ ctx, int dense, int tc_split)
+__global__ void __launch_bounds__(256) k_stats_batch(const SliceCtx *__restrict__ ctx, int dense, int tc_mode)
 {
     grid_dep_sync();
     const SliceCtx c = ctx[blockIdx.y];
     if ((int)blockIdx.x >= stats_blocks(c.g)) return;
     const EncBufs &b = c.b;
-    stats_block(c.g, c.ec, c.img, dense, tc_split, nullptr, b.ri, b.bblk, b.tbest, b.di, b.dconst, b.qblk,
+    stats_block(c.g, c.ec, c.img, dense, tc_mode, nullptr, b.ri, b.bblk, b.tbest, b.di, b.dconst, b.qblk,
                 b.cb.rkeep, b.cb.dkeep, b.fb_count, blockIdx.x);
 }
 
@@ -846,14 +854,14 @@ static int prep_sms()
     return n;
 }
 
-cudaError_t launch_prep(const Geometry &g, const void *img, const EpiConst &ec, int dense, int tc_split,
+cudaError_t launch_prep(const Geometry &g, const void *img, const EpiConst &ec, int dense, int tc_mode,
                         const int *active,
                         RangeInfo *ri, DomainInfo *di, float4 *dconst, uint16_t *bblk, uint16_t *qblk, float *rs32,
                         float *cb32, __half *ra16, __half *cb16, int *tbest, const CompactBufs &cb, int *zero4,
                         int seed, cudaStream_t st)
 {
     const int rb = (g.R + 7) / 8, db = (g.D + 7) / 8;
-    cudaError_t e = launch_dep(k_stats, dim3(stats_blocks(g)), dim3(256), 0, st, g, ec, img, dense, tc_split, active,
+    cudaError_t e = launch_dep(k_stats, dim3(stats_blocks(g)), dim3(256), 0, st, g, ec, img, dense, tc_mode, active,
                                ri, bblk, tbest, di, dconst, qblk, cb.rkeep, cb.dkeep, zero4);
     if (e != cudaSuccess) return e;
     const int sw = seed_warps(g.m);
@@ -875,9 +883,9 @@ cudaError_t launch_prep(const Geometry &g, const void *img, const EpiConst &ec, 
 // largest slice's, so a group of equal slices wastes no blocks).
 int stats_grid(const Geometry &g) { return stats_blocks(g); }
 
-cudaError_t launch_stats_batch(const SliceCtx *ctx, int n, int blocks, int dense, int tc_split, cudaStream_t st)
+cudaError_t launch_stats_batch(const SliceCtx *ctx, int n, int blocks, int dense, int tc_mode, cudaStream_t st)
 {
-    return launch_dep(k_stats_batch, dim3(blocks, n), dim3(256), 0, st, ctx, dense, tc_split);
+    return launch_dep(k_stats_batch, dim3(blocks, n), dim3(256), 0, st, ctx, dense, tc_mode);
 }
 
 // ranges, m: the largest of the slices' ranges and their common block size

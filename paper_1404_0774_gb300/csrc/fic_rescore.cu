@@ -375,7 +375,7 @@ __device__ __forceinline__ void rescore_range(const Geometry &g, const EpiConst 
     // lists actually written by the search (its split count follows the kept counts)
     const int n_lists = lists_per_split *
                         active_splits((counts[0] + 127) / 128, (8 * counts[2] + col_tile - 1) / col_tile, target, max_split,
-                                      col_tile);
+                                      col_tile, g.m);
     const ListEntry *L = lists + (size_t)r * max_lists * kListK;
     const int nent = n_lists * kListK;
     // every entry of the range's lists in registers (entry lane + 32 s), the
@@ -731,7 +731,7 @@ __device__ __forceinline__ void list_scans_block(const Geometry &g, const RangeI
     const int count = *sb.count;
     const int ncol = 8 * counts[2];
     const int tiles = (ncol + col_tile - 1) / col_tile;
-    const int n_split = active_splits((counts[0] + 127) / 128, tiles, target, max_split, col_tile);
+    const int n_split = active_splits((counts[0] + 127) / 128, tiles, target, max_split, col_tile, g.m);
     const int n_lists = n_split * lists_per_split;
     const int seg = col_tile / lists_per_split;
     for (int item = first; item < count; item += stride) {
@@ -812,7 +812,7 @@ __device__ __forceinline__ void list_scans_warp(const Geometry &g, const RangeIn
     const int count = *sb.count;
     const int ncol = 8 * counts[2];
     const int tiles = (ncol + col_tile - 1) / col_tile;
-    const int n_split = active_splits((counts[0] + 127) / 128, tiles, target, max_split, col_tile);
+    const int n_split = active_splits((counts[0] + 127) / 128, tiles, target, max_split, col_tile, g.m);
     const int n_lists = n_split * lists_per_split;
     const int seg = col_tile / lists_per_split;
     for (int item = first; item < count; item += stride) {

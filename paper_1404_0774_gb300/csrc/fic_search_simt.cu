@@ -41,7 +41,7 @@ __device__ __forceinline__ void search_simt_cta(const Geometry &g, const EpiCons
     const int split = by;
     // contiguous slice of the candidate dimension, in whole tiles
     const int tiles = (ncol + BN - 1) / BN;
-    const int n_split = active_splits((nrow + BM - 1) / BM, tiles, target, max_split, BN);
+    const int n_split = active_splits((nrow + BM - 1) / BM, tiles, target, max_split, BN, g.m);
     if (r0 >= nrow || split >= n_split) return;  // CTA-uniform: nothing to screen
     const int t_begin = (int)((long long)tiles * split / n_split);
     const int t_end = (int)((long long)tiles * (split + 1) / n_split);

@@ -380,7 +380,7 @@ __device__ __forceinline__ TcItem tc_item(const SliceCtx *ctx, const int *ip_s, 
 // Persistent tensor-core search over the work items of n slices (n = 1: a
 // single encode); every role (TMA producer, MMA issuer, epilogue warps) walks
 // the same item sequence, so the pipelines run on across item boundaries.
-template <int NBLK, int BW, bool BATCH>
+template <int NBLK, int BW, int KB, bool BATCH>
 __device__ __forceinline__ void search_tc_run(const TcMaps &maps, const SliceCtx &one, const SliceCtx *many, int n,
                                               int dense, float *dump, uint32_t smem_bytes, int *queue,
                                               unsigned long long wait_ns)
@@ -393,8 +393,15 @@ __device__ __forceinline__ void search_tc_run(const TcMaps &maps, const SliceCtx
     constexpr int KPB = BW / 16;
     constexpr uint32_t A_BLK = BM * BW * 2;              // bytes of one block, A
     constexpr uint32_t B_BLK = BN * BW * 2;
-    constexpr uint32_t A_BYTES = NBLK * A_BLK + BM * 32;  // + SW32 tail
-    constexpr uint32_t B_BYTES = NBLK * B_BLK + BN * 32;
+    // KB == 1 (4x4 and 8x8 ranges): A holds NBLK copies of the range pixels
+    // and the tail; a B stage holds a whole tile (NBLK blocks and the tail).
+    // KB > 1 (16x16 ranges, K = 256 per part): A holds the range pixels once,
+    // KB boxes of 64 (every part's MMAs read them); a B stage holds one box
+    // of one part, a tile is NBLK * KB stages, and there is no tail (the
+    // centring correction is applied in the epilogue).
+    constexpr uint32_t A_BYTES = KB == 1 ? NBLK * A_BLK + BM * 32 : KB * A_BLK;
+    constexpr uint32_t B_BYTES = KB == 1 ? NBLK * B_BLK + BN * 32 : B_BLK;
+    constexpr int NSTG = KB == 1 ? STAGES : 7;  // stages of the B ring
     constexpr int KSTEPS = NBLK * KPB + 1;
     constexpr uint32_t SBO = BW == 64 ? 1024 : 256, LAYOUT = BW == 64 ? 2 : 6;
     constexpr uint32_t IDESC = instr_desc(BM, BN);
@@ -404,6 +411,9 @@ __device__ __forceinline__ void search_tc_run(const TcMaps &maps, const SliceCtx
     // of the cross term is that of hi + lo.  8-bit: one accumulator, tail
     // columns included.
     constexpr uint32_t PARTS = NBLK == 2 ? 2 : 1;
+    // the centring correction -e_r f_d / m is added in the epilogue (else by
+    // the tail MMA)
+    constexpr bool CORR_EPI = PARTS == 2 || KB > 1;
     constexpr uint32_t ACC_COLS = BN * PARTS;
     constexpr uint32_t TMEM_COLS = ACC_COLS * NACC <= 256 ? 256 : 512;  // allocation: a power of two
 
@@ -412,11 +422,11 @@ __device__ __forceinline__ void search_tc_run(const TcMaps &maps, const SliceCtx
     uint8_t *sA = smem;
     uint8_t *sB = smem + A_BYTES;  // A_BYTES is a multiple of 1024
     constexpr int ET = 32 * EPI_WARPS;                                // epilogue threads
-    float *xsm = reinterpret_cast<float *>(sB + STAGES * B_BYTES);  // [32][ET] cross terms (rare pass)
+    float *xsm = reinterpret_cast<float *>(sB + NSTG * B_BYTES);  // [32][ET] cross terms (rare pass)
     float4 *dcs = reinterpret_cast<float4 *>(xsm + 32 * ET);        // [EPI_WARPS][DC_WARP] domain constants
     // then [EPI_WARPS][DC_WARP] original domain ids, then the packed constants
     DcPack *dps = reinterpret_cast<DcPack *>(reinterpret_cast<int *>(dcs + EPI_WARPS * DC_WARP) + EPI_WARPS * DC_WARP);
-    __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], a_full, a_empty, tfull_bar[NACC],
+    __shared__ __align__(8) uint64_t full_bar[NSTG], empty_bar[NSTG], a_full, a_empty, tfull_bar[NACC],
         tempty_bar[NACC];
     __shared__ uint32_t tmem_base_s;
     __shared__ int abort_s;
@@ -436,7 +446,7 @@ __device__ __forceinline__ void search_tc_run(const TcMaps &maps, const SliceCtx
         const SliceCtx &c = ctx[i];
         const int nrow = c.b.cb.counts[0], ncol = 8 * c.b.cb.counts[2];
         const int rt = (nrow + BM - 1) / BM, tiles = (ncol + BN - 1) / BN;
-        const int ns = rt > 0 && tiles > 0 ? active_splits(rt, tiles, c.target, c.n_split, BN) : 0;
+        const int ns = rt > 0 && tiles > 0 ? active_splits(rt, tiles, c.target, c.n_split, BN, c.g.m) : 0;
         ns_s[i] = ns;
         rt_s[i] = rt;
         ip_s[i + 1] = rt * ns;
@@ -460,14 +470,14 @@ __device__ __forceinline__ void search_tc_run(const TcMaps &maps, const SliceCtx
     if (threadIdx.x == 0) {
         // self-check: every TMA box and MMA operand lies inside this CTA's
         // dynamic shared memory
-        const uint32_t used = (uint32_t)(smem - smem_raw) + A_BYTES + STAGES * B_BYTES + 32 * ET * 4 +
+        const uint32_t used = (uint32_t)(smem - smem_raw) + A_BYTES + NSTG * B_BYTES + 32 * ET * 4 +
                               EPI_WARPS * DC_WARP * (16 + 4 + 32);
         int bad = 0;
         if (used > smem_bytes) bad = 2;
         if (smem_u32(smem) & 1023u) bad = 4;
         abort_s = bad;
         if (bad) atomicExch(err0, bad);
-        for (int s = 0; s < STAGES; ++s) {
+        for (int s = 0; s < NSTG; ++s) {
             mbar_init(&full_bar[s], 1);
             mbar_init(&empty_bar[s], 1);
         }
@@ -536,21 +546,42 @@ __device__ __forceinline__ void search_tc_run(const TcMaps &maps, const SliceCtx
                 // the previous item's MMAs must be done with A
                 if (kitem > 0 && !mbar_wait(&a_empty, (kitem - 1) & 1, &abort_s, err, wait_ns)) break;
                 mbar_expect_tx(&a_full, A_BYTES);
+                if constexpr (KB == 1) {
 #pragma unroll
-                for (int b = 0; b < NBLK; ++b) tma_load_2d(sA + b * A_BLK, &maps.a128, BW * b, c.abase + w.r0, &a_full);
-                tma_load_2d(sA + NBLK * A_BLK, &maps.a32, BW * NBLK, c.abase + w.r0, &a_full);
+                    for (int b = 0; b < NBLK; ++b)
+                        tma_load_2d(sA + b * A_BLK, &maps.a128, BW * b, c.abase + w.r0, &a_full);
+                    tma_load_2d(sA + NBLK * A_BLK, &maps.a32, BW * NBLK, c.abase + w.r0, &a_full);
+                } else {
+#pragma unroll
+                    for (int b = 0; b < KB; ++b) tma_load_2d(sA + b * A_BLK, &maps.a128, BW * b, c.abase + w.r0, &a_full);
+                }
                 a_pending = true;
                 ++kitem;
-                for (int t = w.t_begin; t < w.t_end; ++t, ++bseq) {
-                    const int s = bseq % STAGES;
-                    if (!mbar_wait(&empty_bar[s], ((bseq / STAGES) & 1) ^ 1, &abort_s, err, wait_ns)) break;
-                    uint8_t *dst = sB + s * B_BYTES;
+                bool ok = true;
+                for (int t = w.t_begin; ok && t < w.t_end; ++t) {
                     const int y = c.bbase + t * BN;
-                    mbar_expect_tx(&full_bar[s], B_BYTES);
+                    if constexpr (KB == 1) {
+                        const int s = bseq % NSTG;
+                        if (!(ok = mbar_wait(&empty_bar[s], ((bseq / NSTG) & 1) ^ 1, &abort_s, err, wait_ns))) break;
+                        uint8_t *dst = sB + s * B_BYTES;
+                        mbar_expect_tx(&full_bar[s], B_BYTES);
 #pragma unroll
-                    for (int b = 0; b < NBLK; ++b) tma_load_2d(dst + b * B_BLK, &maps.b128, BW * b, y, &full_bar[s]);
-                    tma_load_2d(dst + NBLK * B_BLK, &maps.b32, BW * NBLK, y, &full_bar[s]);
+                        for (int b = 0; b < NBLK; ++b) tma_load_2d(dst + b * B_BLK, &maps.b128, BW * b, y, &full_bar[s]);
+                        tma_load_2d(dst + NBLK * B_BLK, &maps.b32, BW * NBLK, y, &full_bar[s]);
+                        ++bseq;
+                    } else {
+                        // part p, box b: columns 64 (p KB + b) of the candidate rows
+                        for (int pb = 0; pb < NBLK * KB; ++pb) {
+                            const int s = bseq % NSTG;
+                            if (!(ok = mbar_wait(&empty_bar[s], ((bseq / NSTG) & 1) ^ 1, &abort_s, err, wait_ns)))
+                                break;
+                            mbar_expect_tx(&full_bar[s], B_BYTES);
+                            tma_load_2d(sB + s * B_BYTES, &maps.b128, BW * pb, y, &full_bar[s]);
+                            ++bseq;
+                        }
+                    }
                 }
+                if (!ok) break;
             }
             // drain: every issued load must land before the CTA may exit
             if (a_pending && !mbar_try_wait(&a_full, (kitem - 1) & 1)) {
@@ -558,11 +589,11 @@ __device__ __forceinline__ void search_tc_run(const TcMaps &maps, const SliceCtx
                 while (!mbar_try_wait(&a_full, (kitem - 1) & 1) && gtimer() - t0 < kDrainNs) {
                 }
             }
-            for (uint32_t q = (bseq > STAGES ? bseq - STAGES : 0); q < bseq; ++q) {
-                const int s = q % STAGES;
-                if (mbar_try_wait(&full_bar[s], (q / STAGES) & 1)) continue;
+            for (uint32_t q = (bseq > NSTG ? bseq - NSTG : 0); q < bseq; ++q) {
+                const int s = q % NSTG;
+                if (mbar_try_wait(&full_bar[s], (q / NSTG) & 1)) continue;
                 const unsigned long long t0 = gtimer();
-                while (!mbar_try_wait(&full_bar[s], (q / STAGES) & 1) && gtimer() - t0 < kDrainNs) {
+                while (!mbar_try_wait(&full_bar[s], (q / NSTG) & 1) && gtimer() - t0 < kDrainNs) {
                 }
             }
         }
@@ -572,6 +603,8 @@ __device__ __forceinline__ void search_tc_run(const TcMaps &maps, const SliceCtx
             const uint32_t a_base = smem_u32(sA);
             const uint32_t b_base0 = smem_u32(sB);
             uint32_t bseq = 0, aseq = 0;
+            uint64_t *last_bar = nullptr;  // the barrier of the last commit, and its phase parity
+            uint32_t last_par = 0;
             int kitem = 0;
             bool ok = true;
             for (int k = 0; ok; ++k) {
@@ -584,45 +617,67 @@ __device__ __forceinline__ void search_tc_run(const TcMaps &maps, const SliceCtx
                 int *err = ctx[w.s].b.err;
                 if (!(ok = mbar_wait(&a_full, kitem & 1, &abort_s, err, wait_ns))) break;
                 ++kitem;
-                for (int t = w.t_begin; t < w.t_end; ++t, ++bseq, ++aseq) {
-                    const int s = bseq % STAGES;
+                for (int t = w.t_begin; t < w.t_end; ++t, ++aseq) {
                     const int acc = aseq % NACC;
                     if (!(ok = mbar_wait(&tempty_bar[acc], ((aseq / NACC) & 1) ^ 1, &abort_s, err, wait_ns))) break;
-                    if (!(ok = mbar_wait(&full_bar[s], (bseq / STAGES) & 1, &abort_s, err, wait_ns))) break;
-                    tc_fence_after();
-                    const uint32_t b_base = b_base0 + s * B_BYTES;
                     const uint32_t d_tmem = tmem_base + acc * ACC_COLS;
+                    if constexpr (KB == 1) {
+                        const int s = bseq % NSTG;
+                        if (!(ok = mbar_wait(&full_bar[s], (bseq / NSTG) & 1, &abort_s, err, wait_ns))) break;
+                        tc_fence_after();
+                        const uint32_t b_base = b_base0 + s * B_BYTES;
 #pragma unroll
-                    for (int k = 0; k < KSTEPS; ++k) {
-                        if (PARTS == 2 && k == NBLK * KPB) break;  // the correction is applied in the epilogue
-                        uint64_t ad, bd;
-                        const int blk = k / KPB, sub = k % KPB;
-                        if (k < NBLK * KPB) {
-                            ad = smem_desc(a_base + blk * A_BLK + sub * 32, SBO, LAYOUT);
-                            bd = smem_desc(b_base + blk * B_BLK + sub * 32, SBO, LAYOUT);
-                        } else {
-                            ad = smem_desc(a_base + NBLK * A_BLK, 256, 6);
-                            bd = smem_desc(b_base + NBLK * B_BLK, 256, 6);
+                        for (int k = 0; k < KSTEPS; ++k) {
+                            if (PARTS == 2 && k == NBLK * KPB) break;  // the correction is applied in the epilogue
+                            uint64_t ad, bd;
+                            const int blk = k / KPB, sub = k % KPB;
+                            if (k < NBLK * KPB) {
+                                ad = smem_desc(a_base + blk * A_BLK + sub * 32, SBO, LAYOUT);
+                                bd = smem_desc(b_base + blk * B_BLK + sub * 32, SBO, LAYOUT);
+                            } else {
+                                ad = smem_desc(a_base + NBLK * A_BLK, 256, 6);
+                                bd = smem_desc(b_base + NBLK * B_BLK, 256, 6);
+                            }
+                            if (PARTS == 2)  // block 0 (hi) -> columns [0, BN), block 1 (lo) -> [BN, 2 BN)
+                                umma_f16(d_tmem + blk * BN, ad, bd, IDESC, sub ? 1u : 0u);
+                            else
+                                umma_f16(d_tmem, ad, bd, IDESC, k > 0 ? 1u : 0u);
                         }
-                        if (PARTS == 2)  // block 0 (hi) -> columns [0, BN), block 1 (lo) -> [BN, 2 BN)
-                            umma_f16(d_tmem + blk * BN, ad, bd, IDESC, sub ? 1u : 0u);
-                        else
-                            umma_f16(d_tmem, ad, bd, IDESC, k > 0 ? 1u : 0u);
+                        umma_commit(&empty_bar[s]);  // smem stage free once these MMAs finish
+                        ++bseq;
+                    } else {
+                        // part p accumulates its KB boxes (K = 64 each) into
+                        // columns [p BN, (p + 1) BN) of the accumulator
+                        for (int pb = 0; pb < NBLK * KB; ++pb) {
+                            const int s = bseq % NSTG;
+                            if (!(ok = mbar_wait(&full_bar[s], (bseq / NSTG) & 1, &abort_s, err, wait_ns))) break;
+                            tc_fence_after();
+                            const int p = pb / KB, b = pb % KB;
+                            const uint32_t b_base = b_base0 + s * B_BYTES;
+#pragma unroll
+                            for (int sub = 0; sub < KPB; ++sub)
+                                umma_f16(d_tmem + p * BN, smem_desc(a_base + b * A_BLK + sub * 32, SBO, LAYOUT),
+                                         smem_desc(b_base + sub * 32, SBO, LAYOUT), IDESC, (b | sub) ? 1u : 0u);
+                            umma_commit(&empty_bar[s]);
+                            last_bar = &empty_bar[s];
+                            last_par = (bseq / NSTG) & 1;
+                            ++bseq;
+                        }
+                        if (!ok) break;
                     }
-                    umma_commit(&empty_bar[s]);    // smem stage free once these MMAs finish
                     umma_commit(&tfull_bar[acc]);  // accumulator ready for the epilogue
+                    last_bar = &tfull_bar[acc];
+                    last_par = (aseq / NACC) & 1;
                 }
+                if (!ok) break;
                 umma_commit(&a_empty);  // A free once the item's MMAs finish
             }
             // drain: the MMAs issued so far must finish before the CTA frees
             // TMEM and shared memory (after an abort the epilogue no longer
             // waits for them); the last commit tracks all of them
-            if (aseq > 0) {
-                const uint32_t last = aseq - 1;
-                if (!mbar_try_wait(&tfull_bar[last % NACC], (last / NACC) & 1)) {
-                    const unsigned long long t0 = gtimer();
-                    while (!mbar_try_wait(&tfull_bar[last % NACC], (last / NACC) & 1) && gtimer() - t0 < kDrainNs) {
-                    }
+            if (last_bar && !mbar_try_wait(last_bar, last_par)) {
+                const unsigned long long t0 = gtimer();
+                while (!mbar_try_wait(last_bar, last_par) && gtimer() - t0 < kDrainNs) {
                 }
             }
         }
@@ -662,7 +717,7 @@ __device__ __forceinline__ void search_tc_run(const TcMaps &maps, const SliceCtx
             const int r = live ? c.b.cb.act[jrow] : 0;  // range id
             RangeEpi re{};
             if (live) re = range_epi(c.b.ri[r], ec);
-            const float er = (PARTS == 2 && live) ? (float)c.b.ri[r].e_r : 0.0f;  // centring correction factor
+            const float er = (CORR_EPI && live) ? (float)c.b.ri[r].e_r : 0.0f;  // centring correction factor
             const f32x2_t er2 = pk2(er, er);
             const bool scr = live && (dense || !re.shadow);
             // the key every s-code-0 candidate of this range gets (one value:
@@ -741,7 +796,7 @@ __device__ __forceinline__ void search_tc_run(const TcMaps &maps, const SliceCtx
                 if (dump) {
 #pragma unroll
                     for (int j = 0; j < 32; ++j) {
-                        const float ca = PARTS == 2 ? epi_corr(er, pick4(dc, j >> 3).w, ec) : 0.0f;
+                        const float ca = CORR_EPI ? epi_corr(er, pick4(dc, j >> 3).w, ec) : 0.0f;
                         if (live && j < nv) dump[(size_t)r * g.N + od[j >> 3] * 8 + (j & 7)] = X[j] + ca;
                     }
                 } else {
@@ -786,13 +841,13 @@ __device__ __forceinline__ void search_tc_run(const TcMaps &maps, const SliceCtx
 // One search (one = its slice context, many = nullptr) or a batch of n
 // slices (many: device array) whose operands share the tensor maps' buffers
 // (rows from abase / bbase on); one CTA per SM, persistent.
-template <int NBLK, int BW, bool BATCH>
+template <int NBLK, int BW, int KB, bool BATCH>
 __global__ void __launch_bounds__(THREADS, 1)
     k_search_tc(const __grid_constant__ TcMaps maps, const __grid_constant__ SliceCtx one, const SliceCtx *many, int n,
                 int dense, float *dump, uint32_t smem_bytes, int *queue, unsigned long long wait_ns)
 {
     grid_dep_sync();
-    search_tc_run<NBLK, BW, BATCH>(maps, one, many, n, dense, dump, smem_bytes, queue, wait_ns);
+    search_tc_run<NBLK, BW, KB, BATCH>(maps, one, many, n, dense, dump, smem_bytes, queue, wait_ns);
 }
 
 namespace {
@@ -829,21 +884,24 @@ bool make_map(CUtensorMap *m, const void *base, int rows, int kp, int x_box, int
 
 }  // namespace
 
-// K elements per copy of the pixels: m = 64 (n = 8) in 128B-swizzled blocks,
-// m = 16 (n = 4) in 32B-swizzled ones.
-static int tc_block_width(const Geometry &g) { return g.m == 64 ? 64 : (g.m == 16 ? 16 : 0); }
+// K elements of one TMA box of pixels: m = 64 (n = 8) and m = 256 (n = 16,
+// four boxes per copy of the pixels) in 128B-swizzled boxes of 64, m = 16
+// (n = 4) in 32B-swizzled ones.
+static int tc_block_width(const Geometry &g) { return g.m == 64 || g.m == 256 ? 64 : (g.m == 16 ? 16 : 0); }
 
 bool search_tc_supported(const Geometry &g)
 {
     const int bw = tc_block_width(g);
-    return bw != 0 && g.KP == (g.split_hilo ? 2 : 1) * bw + 16;
+    return bw != 0 && g.KP == (g.split_hilo ? 2 : 1) * g.m + 16;
 }
 
 size_t search_tc_smem(const Geometry &g)
 {
     const int nblk = g.split_hilo ? 2 : 1, bw = tc_block_width(g);
-    return 1024 + (size_t)(nblk * BM * bw * 2 + BM * 32) + (size_t)STAGES * (nblk * BN * bw * 2 + BN * 32) +
-           32 * (32 * EPI_WARPS) * 4 + EPI_WARPS * DC_WARP * (16 + 4 + 32);
+    const size_t epi = 32 * (32 * EPI_WARPS) * 4 + EPI_WARPS * DC_WARP * (16 + 4 + 32);
+    if (g.m == 256)  // the range pixels once (4 boxes), a ring of 7 one-box stages
+        return 1024 + (size_t)4 * BM * bw * 2 + (size_t)7 * BN * bw * 2 + epi;
+    return 1024 + (size_t)(nblk * BM * bw * 2 + BM * 32) + (size_t)STAGES * (nblk * BN * bw * 2 + BN * 32) + epi;
 }
 
 int search_tc_lists_per_split() { return LISTS; }
@@ -870,23 +928,23 @@ static int n_sms()
     return n > 0 ? n : 1;
 }
 
-template <int NBLK, int BW, bool BATCH>
+template <int NBLK, int BW, int KB, bool BATCH>
 static cudaError_t launch_tc3(const TcMaps &mp, const SliceCtx &one, const SliceCtx *many, int n, int dense,
                               float *dump, int *queue, size_t smem, cudaStream_t st)
 {
     cudaError_t e =
-        cudaFuncSetAttribute(k_search_tc<NBLK, BW, BATCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_search_tc<NBLK, BW, KB, BATCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    return launch_dep(k_search_tc<NBLK, BW, BATCH>, dim3(n_sms()), dim3(THREADS), smem, st, mp, one, many, n, dense,
-                      dump, (uint32_t)smem, queue, (unsigned long long)wait_limit_ns());
+    return launch_dep(k_search_tc<NBLK, BW, KB, BATCH>, dim3(n_sms()), dim3(THREADS), smem, st, mp, one, many, n,
+                      dense, dump, (uint32_t)smem, queue, (unsigned long long)wait_limit_ns());
 }
 
-template <int NBLK, int BW>
+template <int NBLK, int BW, int KB>
 static cudaError_t launch_tc(const TcMaps &mp, const SliceCtx &one, const SliceCtx *many, int n, int dense, float *dump,
                              int *queue, size_t smem, cudaStream_t st)
 {
-    return many ? launch_tc3<NBLK, BW, true>(mp, one, many, n, dense, dump, queue, smem, st)
-                : launch_tc3<NBLK, BW, false>(mp, one, many, n, dense, dump, queue, smem, st);
+    return many ? launch_tc3<NBLK, BW, KB, true>(mp, one, many, n, dense, dump, queue, smem, st)
+                : launch_tc3<NBLK, BW, KB, false>(mp, one, many, n, dense, dump, queue, smem, st);
 }
 
 // Tensor maps over an operand pair (arows / brows rows of KP halves) and
@@ -906,11 +964,14 @@ static cudaError_t launch_tc_any(const Geometry &g, const __half *ra16, int arow
         !make_map(&mp.b32, cb16, brows, g.KP, 16, BN, CU_TENSOR_MAP_SWIZZLE_32B))
         return cudaErrorInvalidValue;
     const size_t smem = search_tc_smem(g);
+    if (g.m == 256)
+        return nblk == 2 ? launch_tc<2, 64, 4>(mp, one, many, n, dense, dump, queue, smem, st)
+                         : launch_tc<1, 64, 4>(mp, one, many, n, dense, dump, queue, smem, st);
     if (bw == 64)
-        return nblk == 2 ? launch_tc<2, 64>(mp, one, many, n, dense, dump, queue, smem, st)
-                         : launch_tc<1, 64>(mp, one, many, n, dense, dump, queue, smem, st);
-    return nblk == 2 ? launch_tc<2, 16>(mp, one, many, n, dense, dump, queue, smem, st)
-                     : launch_tc<1, 16>(mp, one, many, n, dense, dump, queue, smem, st);
+        return nblk == 2 ? launch_tc<2, 64, 1>(mp, one, many, n, dense, dump, queue, smem, st)
+                         : launch_tc<1, 64, 1>(mp, one, many, n, dense, dump, queue, smem, st);
+    return nblk == 2 ? launch_tc<2, 16, 1>(mp, one, many, n, dense, dump, queue, smem, st)
+                     : launch_tc<1, 16, 1>(mp, one, many, n, dense, dump, queue, smem, st);
 }
 
 cudaError_t launch_search_tc(const Geometry &g, const EpiConst &ec, const RangeInfo *ri, const CompactBufs &cb,

@@ -5,7 +5,9 @@ Xt[r, c] = (m * X - Sq * Sb) / m with X = sum_i q_i b_i (eq 9's cross term),
 computed here in int64 with numpy's own rotations/flips for the symmetries.
 FP32 accumulation of centred integer products is exact while partial sums
 stay below 2^24; beyond that the error is bounded by a small multiple of
-2^-24 times the magnitude of the centred products.
+2^-24 times the magnitude of the centred products: K = m terms, so for 16x16
+ranges (K = 256, hi and lo parts each) the bound is 3 * 256 * 2^-24 < 2^-14
+of the scale.
 """
 import numpy as np
 import pytest
@@ -71,6 +73,10 @@ CASES = [
     ("mr8_n4", lambda: fic_synth.mr_slice(26, 48), 4, 4, 8),
     ("extremes12", lambda: fic_synth.random_image(27, 64, 64, 1).astype(np.uint16) * 4095, 8, 4, 12),
     ("all4095", lambda: np.full((48, 64), 4095, np.uint16), 8, 4, 12),
+    ("ct12_n16", lambda: fic_synth.ct_slice(28, 64), 16, 8, 12),
+    ("rand12_n16", lambda: fic_synth.random_image(29, 64, 64, 12).astype(np.uint16), 16, 16, 12),
+    ("mr8_n16", lambda: fic_synth.mr_slice(30, 64), 16, 8, 8),
+    ("extremes12_n16", lambda: fic_synth.random_image(31, 64, 64, 1).astype(np.uint16) * 4095, 16, 16, 12),
 ]
 
 
@@ -84,8 +90,8 @@ def test_cross_terms(fic, name, make, n, t, B, search):
     ref, scale = exact_xt(img, n, t)
     err = np.abs(got - ref)
     assert np.isfinite(got).all()
-    assert (err / scale).max() < 2.0 ** -16, (err / scale).max()
-    if B == 8 and search == "tc":
+    assert (err / scale).max() < (2.0 ** -14 if n == 16 else 2.0 ** -16), (err / scale).max()
+    if B == 8 and search == "tc" and n < 16:
         # 8-bit: every product and partial sum of the centred integers is below
         # 2^24, so only the final fractional centring term can round
         assert (err <= np.abs(ref) * 2.0 ** -23 + 2.0 ** -6).all(), err.max()

@@ -72,8 +72,6 @@ def search_code(fic, search):
 @pytest.mark.parametrize("name,make,n,t,B", CASES, ids=[c[0] for c in CASES])
 @pytest.mark.parametrize("search", SEARCH)
 def test_encode_parity_small(fic, orc, name, make, n, t, B, search):
-    if search == "tc" and n not in (4, 8):
-        pytest.skip("the tensor-core search handles 4x4 and 8x8 ranges")
     img = make()
     p = fic.params(range_size=n, domain_stride=t, bit_depth=B, search=search_code(fic, search))
     got = gpu_encode(fic, img, p)
@@ -116,6 +114,17 @@ def test_ct_slice_512_full(fic, orc, ct512_oracle, search):
     got = gpu_encode(fic, img, p)
     same = check_against_oracle(orc, img, got, 8, 4, 12, ref=ref)
     print(f"index agreement with the oracle: {same:.4f}")
+
+
+@pytest.mark.parametrize("t", [16, 8])
+@pytest.mark.parametrize("search", SEARCH)
+def test_ct_slice_512_n16_full(fic, orc, search, t):
+    """16x16 ranges on the 512x512 12-bit CT-like slice (the quadtree's first
+    level at stride 16, and stride 8): K = 256 per part on the tensor cores;
+    every map re-scored, every range's minimum checked."""
+    img = fic_synth.ct_slice()
+    p = fic.params(range_size=16, domain_stride=t, bit_depth=12, search=search_code(fic, search))
+    check_against_oracle(orc, img, gpu_encode(fic, img, p), 16, t, 12)
 
 
 @pytest.mark.parametrize("search", SEARCH)
@@ -253,8 +262,6 @@ def test_exact_scan_gives_the_screened_maps(fic, orc, name, make, n, t, B, searc
     """FIC_FLAG_EXACT_SCAN sends every screened range to the exhaustive exact
     scan (the path uncertified ranges take): the maps must be the screened
     search's, each flagged as resolved by the scan, and meet the oracle bar."""
-    if search == "tc" and n not in (4, 8):
-        pytest.skip("the tensor-core search handles 4x4 and 8x8 ranges")
     img = make()
     p = fic.params(range_size=n, domain_stride=t, bit_depth=B, search=search_code(fic, search))
     px = fic.params(range_size=n, domain_stride=t, bit_depth=B, search=search_code(fic, search),
@@ -274,8 +281,6 @@ def test_exact_scan_gives_the_screened_maps(fic, orc, name, make, n, t, B, searc
 def test_encode_parity_other_code_widths(fic, orc, search, n, sb, ob):
     """s and o quantised to other bit widths (the 8/10-bit and 6/9-bit cases
     need 128-bit exact residuals; 3/4 bits is a coarse grid)."""
-    if search == "tc" and n not in (4, 8):
-        pytest.skip("the tensor-core search handles 4x4 and 8x8 ranges")
     img = fic_synth.ct_slice(23 + n + sb, 64)
     p = fic.params(range_size=n, domain_stride=4, bit_depth=12, s_bits=sb, o_bits=ob, search=search_code(fic, search))
     check_against_oracle(orc, img, gpu_encode(fic, img, p), n, 4, 12, sb=sb, ob=ob)
