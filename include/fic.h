@@ -64,7 +64,7 @@ enum {
 
 /* Search implementation. */
 enum {
-    FIC_SEARCH_AUTO = 0, /* tensor-core search for n = 4 and 8, else SIMT     */
+    FIC_SEARCH_AUTO = 0, /* the tensor-core search (every range size n)       */
     FIC_SEARCH_TC = 1,   /* FP16 tcgen05 tensor-core cross term + FP32 epilogue */
     FIC_SEARCH_SIMT = 2  /* plain FP32 CUDA-core search (the speedup baseline) */
 };

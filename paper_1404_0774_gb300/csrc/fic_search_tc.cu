@@ -12,10 +12,17 @@
 // 16-element SWIZZLE_32B tail block carrying the centring terms.  For 12-bit
 // images the hi and lo blocks go to separate TMEM accumulators, whose sums
 // are exact, and the tail's centring term is folded in by the epilogue.
+// 16x16 ranges (K = 256 per copy): the range pixels are staged once as four
+// 64-element boxes that every part's MMAs read, the candidate rows stream
+// through a ring of one-box stages (a tile is parts x 4 stages), the tail is
+// not used (the centring correction is applied in the epilogue), and the
+// FP32 accumulation over K = 256 may round: the statistics kernel widens the
+// screening allowances for it.
 //
 // CTA = 128 ranges (one per TMEM lane), streaming a contiguous slice of the
 // candidate dimension in tiles of 96:
-//   warp 0        TMA producer (one thread): A once, B tiles into a 3-stage ring
+//   warp 0        TMA producer (one thread): A once per item, B tiles into a
+//                 3-stage ring (16x16 ranges: B boxes into a 7-stage ring)
 //   warp 1        TMEM allocator + MMA issuer (one thread): m/16 tcgen05.mma
 //                 kind::f16 128x96x16 per pixel block (+1 tail for 8-bit)
 //                 per tile into one of two TMEM accumulator sets
