@@ -522,7 +522,7 @@ struct SliceCtx {
 // tensor-core tile of 16x16 ranges (m = 256) is four times the MMA and copy
 // work of one of 8x8 ranges, and the level of a quadtree that uses it has few
 // ranges: there one tile per split suffices.
-constexpr int kMinSplitTiles = 12;
+constexpr int kMinSplitTiles = 6;  // tensor-core super-tiles of 192 columns
 __host__ __device__ __forceinline__ int active_splits(int row_tiles, int col_tiles, int target, int max_split,
                                                      int col_tile, int m)
 {
@@ -530,19 +530,19 @@ __host__ __device__ __forceinline__ int active_splits(int row_tiles, int col_til
     int s = target / row_tiles;
     s = s < 1 ? 1 : s;
     s = s > max_split ? max_split : s;
-    const int by_tiles = col_tile == 96 ? col_tiles / (m >= 256 ? 1 : kMinSplitTiles) : col_tiles;
+    const int by_tiles = col_tile == 192 ? col_tiles / (m >= 256 ? 1 : kMinSplitTiles) : col_tiles;
     s = s > by_tiles ? by_tiles : s;
     return s < 1 ? 1 : s;
 }
 
 // First candidate tile of split s of ns over `tiles` tiles.  The tensor-core
-// search (column tile 96) takes its items split-major from a queue shared by
+// search (column unit 192) takes its items split-major from a queue shared by
 // all CTAs, so its splits shrink from 1.5x to 0.5x the mean size (boundary
 // tiles * (3 s ns - s^2) / (2 ns^2)): the items that start last are short
 // and the SMs run out of work together.  The FP32 search's splits are equal.
 __host__ __device__ __forceinline__ int split_tile(int tiles, int s, int ns, int col_tile)
 {
-    if (col_tile != 96) return (int)((long long)tiles * s / ns);
+    if (col_tile != 192) return (int)((long long)tiles * s / ns);
     return (int)((long long)tiles * (3LL * s * ns - (long long)s * s) / (2LL * ns * ns));
 }
 

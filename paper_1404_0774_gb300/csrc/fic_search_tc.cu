@@ -44,12 +44,21 @@ namespace fic {
 namespace {
 
 constexpr int BM = 128;
-constexpr int BN = 96;                          // candidates per tile
-static_assert(BN == 96, "active_splits recognises the tensor-core search by its 96-column tile");
-constexpr int STAGES = 3;
-constexpr int NACC = 2;
+constexpr int BN = 64;                          // candidates per MMA tile (B rows of one stage)
+constexpr int STAGES = 4;
+constexpr int NACC = 4;                         // accumulator slots (one per MMA tile in flight)
 constexpr int EPI_COLS = 32;                    // columns of a tile per epilogue warp
-constexpr int LISTS = BN / EPI_COLS;            // epilogue warps per TMEM lane quadrant
+// A work item's columns come in super-tiles of LISTS MMA tiles; epilogue
+// part p (one warp per TMEM lane quadrant) takes MMA tile p of every
+// super-tile, both of its 32-column chunks.  The three warps of a scheduler
+// (one per part) so work on different tiles, which the MMA warp produces one
+// after another into a ring of NACC accumulator slots, instead of all
+// waiting for and working on the same tile at the same time; and each of
+// them pays the per-tile wait, staging and release once per two chunks.
+constexpr int LISTS = 3;                        // epilogue warps per TMEM lane quadrant
+constexpr int SUPER = LISTS * BN;               // columns of a super-tile (the split unit)
+static_assert(SUPER == 192, "active_splits and split_tile recognise the tensor-core search by its 192-column unit");
+constexpr int CHUNKS = BN / EPI_COLS;           // chunks of an MMA tile per epilogue warp
 constexpr int EPI_WARPS = 4 * LISTS;
 constexpr int THREADS = 64 + 32 * EPI_WARPS;    // TMA warp, MMA warp, epilogue
 constexpr int DC_WARP = EPI_COLS / 8;           // domains per warp per tile
@@ -377,10 +386,9 @@ __device__ __forceinline__ TcItem tc_item(const SliceCtx *ctx, const int *ip_s, 
     it.split = local / nrt;
     it.r0 = (local - it.split * nrt) * BM;
     const int ncol = 8 * ctx[lo].b.cb.counts[2];
-    const int tiles = (ncol + BN - 1) / BN;
-    static_assert(BN == 96, "split_tile recognises the tensor-core search by its 96-column tile");
-    it.t_begin = split_tile(tiles, it.split, ns, BN);
-    it.t_end = split_tile(tiles, it.split + 1, ns, BN);
+    const int tiles = (ncol + SUPER - 1) / SUPER;
+    it.t_begin = split_tile(tiles, it.split, ns, SUPER);
+    it.t_end = split_tile(tiles, it.split + 1, ns, SUPER);
     return it;
 }
 
@@ -452,8 +460,8 @@ __device__ __forceinline__ void search_tc_run(const TcMaps &maps, const SliceCtx
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         const SliceCtx &c = ctx[i];
         const int nrow = c.b.cb.counts[0], ncol = 8 * c.b.cb.counts[2];
-        const int rt = (nrow + BM - 1) / BM, tiles = (ncol + BN - 1) / BN;
-        const int ns = rt > 0 && tiles > 0 ? active_splits(rt, tiles, c.target, c.n_split, BN, c.g.m) : 0;
+        const int rt = (nrow + BM - 1) / BM, tiles = (ncol + SUPER - 1) / SUPER;
+        const int ns = rt > 0 && tiles > 0 ? active_splits(rt, tiles, c.target, c.n_split, SUPER, c.g.m) : 0;
         ns_s[i] = ns;
         rt_s[i] = rt;
         ip_s[i + 1] = rt * ns;
@@ -496,7 +504,7 @@ __device__ __forceinline__ void search_tc_run(const TcMaps &maps, const SliceCtx
         }
         for (int a = 0; a < NACC; ++a) {
             mbar_init(&tfull_bar[a], 1);
-            mbar_init(&tempty_bar[a], EPI_WARPS);  // one arrival per epilogue warp
+            mbar_init(&tempty_bar[a], 4);  // one arrival per epilogue warp of the tile's part
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -544,8 +552,8 @@ __device__ __forceinline__ void search_tc_run(const TcMaps &maps, const SliceCtx
                 const TcItem w = tc_item(ctx, ip_s, ns_s, rt_s, n, item);
                 const SliceCtx &c = ctx[w.s];
                 int *err = c.b.err;
-                const int rpad = (c.g.R + BM - 1) / BM * BM, npad = (c.g.N + BN - 1) / BN * BN;
-                if (w.r0 + BM > rpad || w.t_end * BN > npad) {  // every box inside the slice's padded operands
+                const int rpad = (c.g.R + BM - 1) / BM * BM, npad = (c.g.N + SUPER - 1) / SUPER * SUPER;
+                if (w.r0 + BM > rpad || w.t_end * SUPER > npad) {  // every box inside the slice's padded operands
                     abort_s = 3;
                     atomicExch(err, 3);
                     break;
@@ -565,7 +573,7 @@ __device__ __forceinline__ void search_tc_run(const TcMaps &maps, const SliceCtx
                 a_pending = true;
                 ++kitem;
                 bool ok = true;
-                for (int t = w.t_begin; ok && t < w.t_end; ++t) {
+                for (int t = w.t_begin * LISTS; ok && t < w.t_end * LISTS; ++t) {  // MMA tiles of the item
                     const int y = c.bbase + t * BN;
                     if constexpr (KB == 1) {
                         const int s = bseq % NSTG;
@@ -624,7 +632,7 @@ __device__ __forceinline__ void search_tc_run(const TcMaps &maps, const SliceCtx
                 int *err = ctx[w.s].b.err;
                 if (!(ok = mbar_wait(&a_full, kitem & 1, &abort_s, err, wait_ns))) break;
                 ++kitem;
-                for (int t = w.t_begin; t < w.t_end; ++t, ++aseq) {
+                for (int t = w.t_begin * LISTS; t < w.t_end * LISTS; ++t, ++aseq) {  // MMA tiles, in order
                     const int acc = aseq % NACC;
                     if (!(ok = mbar_wait(&tempty_bar[acc], ((aseq / NACC) & 1) ^ 1, &abort_s, err, wait_ns))) break;
                     const uint32_t d_tmem = tmem_base + acc * ACC_COLS;
@@ -635,7 +643,7 @@ __device__ __forceinline__ void search_tc_run(const TcMaps &maps, const SliceCtx
                         const uint32_t b_base = b_base0 + s * B_BYTES;
 #pragma unroll
                         for (int k = 0; k < KSTEPS; ++k) {
-                            if (PARTS == 2 && k == NBLK * KPB) break;  // the correction is applied in the epilogue
+                            if (CORR_EPI && k == NBLK * KPB) break;  // the correction is applied in the epilogue
                             uint64_t ad, bd;
                             const int blk = k / KPB, sub = k % KPB;
                             if (k < NBLK * KPB) {
@@ -645,7 +653,7 @@ __device__ __forceinline__ void search_tc_run(const TcMaps &maps, const SliceCtx
                                 ad = smem_desc(a_base + NBLK * A_BLK, 256, 6);
                                 bd = smem_desc(b_base + NBLK * B_BLK, 256, 6);
                             }
-                            if (PARTS == 2)  // block 0 (hi) -> columns [0, BN), block 1 (lo) -> [BN, 2 BN)
+                            if (PARTS == 2)  // block 0 (hi) -> slot columns [0, BN), block 1 (lo) -> [BN, 2 BN)
                                 umma_f16(d_tmem + blk * BN, ad, bd, IDESC, sub ? 1u : 0u);
                             else
                                 umma_f16(d_tmem, ad, bd, IDESC, k > 0 ? 1u : 0u);
@@ -654,7 +662,7 @@ __device__ __forceinline__ void search_tc_run(const TcMaps &maps, const SliceCtx
                         ++bseq;
                     } else {
                         // part p accumulates its KB boxes (K = 64 each) into
-                        // columns [p BN, (p + 1) BN) of the accumulator
+                        // columns [p BN, (p + 1) BN) of the slot
                         for (int pb = 0; pb < NBLK * KB; ++pb) {
                             const int s = bseq % NSTG;
                             if (!(ok = mbar_wait(&full_bar[s], (bseq / NSTG) & 1, &abort_s, err, wait_ns))) break;
@@ -698,7 +706,7 @@ __device__ __forceinline__ void search_tc_run(const TcMaps &maps, const SliceCtx
         float4 *wdc = dcs + ew * DC_WARP;
         int *wod = reinterpret_cast<int *>(dcs + EPI_WARPS * DC_WARP) + ew * DC_WARP;
         DcPack *wdp = dps + ew * DC_WARP;
-        const uint32_t lane_addr = tmem_base + ((uint32_t)(quad * 32) << 16) + part * EPI_COLS;
+        const uint32_t lane_addr = tmem_base + ((uint32_t)(quad * 32) << 16);
         uint32_t aseq = 0;
         bool ok = true;
         for (int k = 0; ok; ++k) {
@@ -732,102 +740,113 @@ __device__ __forceinline__ void search_tc_run(const TcMaps &maps, const SliceCtx
             const float K0 = epi_key(0.0f, 0.0f, 0.0f, re.zb, make_float4(0.f, 0.f, 0.f, 0.f), ec);
             ListState L;
             list_init(L);
-            const int ntile = w.t_end - w.t_begin;
-            // prefetch for the first tile: its 4 domains and the shared best key
+            const int ntile = w.t_end - w.t_begin;  // super-tiles of the item
+            // prefetch for the first chunk: its 4 domains and the shared best key
             float4 dc_next = make_float4(0.f, 0.f, 0.f, 0.f);
             int od_next = 0;
             int tb_next = 0x7f800000;
             if (ntile > 0) {
-                const int jd = ((w.t_begin * BN + part * EPI_COLS) >> 3) + lane;
+                const int jd = ((w.t_begin * SUPER + part * BN) >> 3) + lane;
                 if (lane < DC_WARP && jd < ndom) {
                     dc_next = __ldg(dconst + jd);
                     od_next = __ldg(dmap + jd);
                 }
                 if (scr && !dump) tb_next = __ldcg(tbest + r);
             }
-            for (int it = 0; it < ntile; ++it, ++aseq) {
-                const int acc = aseq % NACC;
-                const int n0 = (w.t_begin + it) * BN + part * EPI_COLS;
-                __syncwarp();  // every lane is done with the previous tile's staged constants
-                if (lane < DC_WARP) {
-                    wdc[lane] = dc_next;
-                    wod[lane] = od_next;
-                    wdp[lane] = dc_pack(dc_next, ec);
-                }
+            for (int it = 0; ok && it < ntile; ++it) {
+                // this part's MMA tile of super-tile it: the item's MMA tile 3 it + part
+                const uint32_t mt = aseq + it * LISTS + part;
+                const int acc = mt % NACC;
                 if (scr && !dump) {
                     const float Tg = ord2f(tb_next);  // best key other CTAs found
                     list_adopt(L, Tg, re, ec);
                     L.Tpub = fminf(L.Tpub, Tg);
                 }
-                if (it + 1 < ntile) {  // prefetch for the next tile
-                    const int jd = ((n0 + BN) >> 3) + lane;
-                    if (lane < DC_WARP && jd < ndom) {
-                        dc_next = __ldg(dconst + jd);
-                        od_next = __ldg(dmap + jd);
-                    }
-                    if (scr && !dump) tb_next = __ldcg(tbest + r);
-                }
-                __syncwarp();
                 // warp-uniform decision: tcgen05.ld below is .sync.aligned
-                if (!(ok = __all_sync(0xffffffffu, mbar_wait(&tfull_bar[acc], (aseq / NACC) & 1, &abort_s, err, wait_ns))))
+                if (!(ok = __all_sync(0xffffffffu, mbar_wait(&tfull_bar[acc], (mt / NACC) & 1, &abort_s, err, wait_ns))))
                     break;
                 tc_fence_after();
-                const uint32_t taddr = lane_addr + acc * ACC_COLS;
-                const int nv = min(32, ncol - n0);  // may be <= 0 in the last tile
-                // the chunk's domain constants stay in shared memory (read where
-                // used, which leaves the registers to the key computation)
-                const int (&od)[4] = *reinterpret_cast<const int (*)[4]>(wod);
-                const float4 (&dc)[4] = *reinterpret_cast<const float4 (*)[4]>(wdc);
-                float X[32];
-                {
-                    uint32_t h[32], l[32];
-                    tmem_ld32(taddr, h);
-                    if (PARTS == 2) {
-                        tmem_ld32(taddr + BN, l);
-                        tmem_wait2(h, l);
+#pragma unroll 1
+                for (int ch = 0; ch < CHUNKS; ++ch) {
+                    const int n0 = (w.t_begin + it) * SUPER + part * BN + ch * EPI_COLS;
+                    __syncwarp();  // every lane is done with the previous chunk's staged constants
+                    if (lane < DC_WARP) {
+                        wdc[lane] = dc_next;
+                        wod[lane] = od_next;
+                        wdp[lane] = dc_pack(dc_next, ec);
+                    }
+                    {  // prefetch for the next chunk: the tile's second, or the next super-tile's first
+                        const int n1 = ch + 1 < CHUNKS ? n0 + EPI_COLS : n0 + SUPER - (CHUNKS - 1) * EPI_COLS;
+                        const bool more = ch + 1 < CHUNKS || it + 1 < ntile;
+                        const int jd = (n1 >> 3) + lane;
+                        if (more && lane < DC_WARP && jd < ndom) {
+                            dc_next = __ldg(dconst + jd);
+                            od_next = __ldg(dmap + jd);
+                        }
+                        if (ch + 1 == CHUNKS && it + 1 < ntile && scr && !dump) tb_next = __ldcg(tbest + r);
+                    }
+                    __syncwarp();
+                    const uint32_t taddr = lane_addr + acc * ACC_COLS + ch * EPI_COLS;
+                    const int nv = min(32, ncol - n0);  // may be <= 0 in the last tile
+                    // the chunk's domain constants stay in shared memory (read where
+                    // used, which leaves the registers to the key computation)
+                    const int (&od)[4] = *reinterpret_cast<const int (*)[4]>(wod);
+                    const float4 (&dc)[4] = *reinterpret_cast<const float4 (*)[4]>(wdc);
+                    float X[32];
+                    {
+                        uint32_t h[32], l[32];
+                        tmem_ld32(taddr, h);
+                        if (PARTS == 2) {
+                            tmem_ld32(taddr + BN, l);
+                            tmem_wait2(h, l);
 #pragma unroll
-                        for (int j = 0; j < 32; j += 2)
-                            upk2(add2(pk2(__uint_as_float(h[j]), __uint_as_float(h[j + 1])),
-                                      pk2(__uint_as_float(l[j]), __uint_as_float(l[j + 1]))), X[j], X[j + 1]);
+                            for (int j = 0; j < 32; j += 2)
+                                upk2(add2(pk2(__uint_as_float(h[j]), __uint_as_float(h[j + 1])),
+                                          pk2(__uint_as_float(l[j]), __uint_as_float(l[j + 1]))), X[j], X[j + 1]);
+                        } else {
+                            tmem_wait(h);
+#pragma unroll
+                            for (int j = 0; j < 32; ++j) X[j] = __uint_as_float(h[j]);
+                        }
+                    }
+                    if (ch + 1 == CHUNKS) {
+                        // the tile's accumulator is in registers: release it to the
+                        // MMA warp now, so that a slow warp holds up the tensor
+                        // cores only by its loads
+                        tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(&tempty_bar[acc]);
+                    }
+                    if (dump) {
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) {
+                            const float ca = CORR_EPI ? epi_corr(er, pick4(dc, j >> 3).w, ec) : 0.0f;
+                            if (live && j < nv) dump[(size_t)r * g.N + od[j >> 3] * 8 + (j & 7)] = X[j] + ca;
+                        }
                     } else {
-                        tmem_wait(h);
+                        if (nv < 32) {
 #pragma unroll
-                        for (int j = 0; j < 32; ++j) X[j] = __uint_as_float(h[j]);
+                            for (int j = 0; j < 32; ++j)
+                                if (j >= nv) X[j] = __int_as_float(0x7fc00000);  // NaN: never listed
+                        }
+                        const float thr = fminf(L.key[kListK - 1], L.tw);
+                        // s-code-0 candidates need the penalty only where one is
+                        // listed already and their common key K0 is below the
+                        // threshold (rare): the warp takes the plain keys otherwise
+                        const bool zero_pen = __any_sync(0xffffffffu, scr && L.has_zero && K0 < thr);
+                        uint32_t mask = 0u;
+                        if (zero_pen)
+                            mask = epi_keys32_tc<true>(X, wdp, re.zb, re.rho_lim, er2, ec, thr,
+                                                       L.has_zero ? kZeroPenalty : 0.0f);
+                        else
+                            mask = epi_keys32_tc<false>(X, wdp, re.zb, re.rho_lim, er2, ec, thr, 0.0f);
+                        mask = scr && nv > 0 ? mask & col_mask(nv) : 0u;
+                        if (__any_sync(0xffffffffu, mask != 0u))
+                            rare_chunk(X, mask, od, dc, er, xsm + et, ET, re, ec, L, tbest + r);
                     }
-                }
-                // the accumulator is in registers: release it to the MMA warp now,
-                // so that a slow warp holds up the tensor cores only by its load
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&tempty_bar[acc]);
-                if (dump) {
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        const float ca = CORR_EPI ? epi_corr(er, pick4(dc, j >> 3).w, ec) : 0.0f;
-                        if (live && j < nv) dump[(size_t)r * g.N + od[j >> 3] * 8 + (j & 7)] = X[j] + ca;
-                    }
-                } else {
-                    if (nv < 32) {
-#pragma unroll
-                        for (int j = 0; j < 32; ++j)
-                            if (j >= nv) X[j] = __int_as_float(0x7fc00000);  // NaN: never listed
-                    }
-                    const float thr = fminf(L.key[kListK - 1], L.tw);
-                    // s-code-0 candidates need the penalty only where one is
-                    // listed already and their common key K0 is below the
-                    // threshold (rare): the warp takes the plain keys otherwise
-                    const bool zero_pen = __any_sync(0xffffffffu, scr && L.has_zero && K0 < thr);
-                    uint32_t mask = 0u;
-                    if (zero_pen)
-                        mask = epi_keys32_tc<true>(X, wdp, re.zb, re.rho_lim, er2, ec, thr,
-                                                   L.has_zero ? kZeroPenalty : 0.0f);
-                    else
-                        mask = epi_keys32_tc<false>(X, wdp, re.zb, re.rho_lim, er2, ec, thr, 0.0f);
-                    mask = scr && nv > 0 ? mask & col_mask(nv) : 0u;
-                    if (__any_sync(0xffffffffu, mask != 0u))
-                        rare_chunk(X, mask, od, dc, er, xsm + et, ET, re, ec, L, tbest + r);
                 }
             }
+            aseq += ntile * LISTS;
             if (ok && scr && !dump) {
                 ListEntry *dst = c.b.lists + (((size_t)r * c.n_split + w.split) * LISTS + part) * kListK;
 #pragma unroll
@@ -913,11 +932,11 @@ size_t search_tc_smem(const Geometry &g)
 
 int search_tc_lists_per_split() { return LISTS; }
 
-int search_tc_tile() { return BN; }
+int search_tc_tile() { return SUPER; }
 
 int search_tc_rows(int rows) { return (rows + BM - 1) / BM * BM; }
 
-int search_tc_cols(int cols) { return (cols + BN - 1) / BN * BN; }
+int search_tc_cols(int cols) { return (cols + SUPER - 1) / SUPER * SUPER; }
 
 // Limit of the search's pipeline waits (fic_set_wait_limit_ns), read at
 // each launch.
