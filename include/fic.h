@@ -374,7 +374,8 @@ uint64_t fic_get_wait_limit_ns(void);
 
 /* Phase durations (ms) of the last fic_encode on this host thread that ran
  * with FIC_FLAG_PHASE_TIMING: out[0] prep, out[1] search, out[2] re-score,
- * out[3] fallback, out[4] map output.  Waits for those events. */
+ * out[3] exact fallback scans and map output (one launch), out[4] 0 (kept
+ * so that the array layout is unchanged).  Waits for those events. */
 int fic_last_encode_phase_ms(double out[5]);
 
 #ifdef __cplusplus

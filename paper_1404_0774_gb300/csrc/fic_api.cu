@@ -419,11 +419,11 @@ cudaError_t encode_pipeline(const Geometry &gd, const fic_params *p, int search,
                                 n_split, sm_count(), (p->flags & FIC_FLAG_EXACT_SCAN) ? 1 : 0, b.winner, b.fb_list,
                                 b.fb_count, b.partial, b.span, st));
         FIC_MARK(3);
-        FIC_STEP(launch_exact_scans(gd, b.ri, b.di, b.bblk, b.qblk, b.fb_list, b.fb_count, b.partial, b.cb.counts,
-                                    b.cb.dmap, search == FIC_SEARCH_TC ? search_tc_tile() : 64, target, n_split,
-                                    lists_per_split(search), n_lists, b.span, b.winner, sm_count(), st));
+        FIC_STEP(launch_scans_finalize(gd, b.ri, b.di, b.bblk, b.qblk, b.fb_list, b.fb_count, b.partial, b.cb.counts,
+                                       b.cb.dmap, search == FIC_SEARCH_TC ? search_tc_tile() : 64, target, n_split,
+                                       lists_per_split(search), n_lists, b.span, b.winner, b.err, dmaps, sm_count(),
+                                       st));
         FIC_MARK(4);
-        FIC_STEP(launch_finalize(gd, b.ri, b.di, b.bblk, b.qblk, b.winner, b.err, dmaps, st));
         FIC_MARK(5);
     }
 #undef FIC_MARK
@@ -922,7 +922,8 @@ cudaError_t batch_pipeline(const BatchPlan &P, const fic_params *p, char *ws, in
     auto ranges_of = [&](int k) { return P.sl[P.order[k0 + k]].g.R; };
     cudaError_t e = cudaSuccess;
     for (auto &gr : groups)
-        if ((e = launch_stats_batch(dctx + gr.first, gr.second, stats_grid(P.sl[P.order[k0 + gr.first]].g), dense,
+        if ((e = launch_stats_batch(P.sl[P.order[k0 + gr.first]].g, dctx + gr.first, gr.second,
+                                    stats_grid(P.sl[P.order[k0 + gr.first]].g), dense,
                                     tc_mode_of(g0, tc ? FIC_SEARCH_TC : FIC_SEARCH_SIMT), st)) != cudaSuccess)
             return e;
     for (auto &gr : groups)
@@ -930,7 +931,7 @@ cudaError_t batch_pipeline(const BatchPlan &P, const fic_params *p, char *ws, in
                                             P.sl[P.order[k0 + gr.first]].g.m, st)) != cudaSuccess)
             return e;
     for (auto &gr : groups)
-        if ((e = launch_rows_batch(dctx + gr.first, gr.second, blocks_of(gr.first), st)) != cudaSuccess) return e;
+        if ((e = launch_rows_batch(P.sl[P.order[k0 + gr.first]].g, dctx + gr.first, gr.second, blocks_of(gr.first), st)) != cudaSuccess) return e;
     if (tc)
         e = launch_search_tc_batch(g0, reinterpret_cast<const __half *>(ws + P.ra_off), P.arows,
                                    reinterpret_cast<const __half *>(ws + P.cb_off), P.brows, dctx, n, dense,

@@ -571,9 +571,10 @@ int search_simt_lists_per_split();
 // launch per stage over the slices (the per-slice stages: once per group of
 // equal slices).
 int stats_grid(const Geometry &g);  // blocks of the statistics launch of one slice
-cudaError_t launch_stats_batch(const SliceCtx *ctx, int n, int blocks, int dense, int tc_mode, cudaStream_t st);
+cudaError_t launch_stats_batch(const Geometry &g, const SliceCtx *ctx, int n, int blocks, int dense, int tc_mode,
+                               cudaStream_t st);
 cudaError_t launch_compact_seed_batch(const SliceCtx *ctx, int n, int ranges, int m, cudaStream_t st);
-cudaError_t launch_rows_batch(const SliceCtx *ctx, int n, int blocks, cudaStream_t st);
+cudaError_t launch_rows_batch(const Geometry &g, const SliceCtx *ctx, int n, int blocks, cudaStream_t st);
 cudaError_t launch_search_tc_batch(const Geometry &g, const __half *ra16, int arows, const __half *cb16, int brows,
                                    const SliceCtx *ctx, int n, int dense, int *queue, cudaStream_t st);
 cudaError_t launch_search_simt_batch(const SliceCtx *ctx, int n, int max_ranges, int max_split, int dense,
@@ -589,16 +590,14 @@ cudaError_t launch_rescore(const Geometry &g, const EpiConst &ec, const RangeInf
                            int exact_scan, uint32_t *winner, int *fb_list, int *fb_count, void *partial, void *span,
                            cudaStream_t st);
 size_t span_bytes(const Geometry &g, int max_lists);
-cudaError_t launch_exact_scans(const Geometry &g, const RangeInfo *ri, const DomainInfo *di, const uint16_t *bblk,
-                               const uint16_t *qblk, const int *fb_list, int *fb_count, void *partial,
-                               const int *counts, const int *dmap, int col_tile, int target, int max_split,
-                               int lists_per_split, int max_lists, void *span, uint32_t *winner, int n_sm,
-                               cudaStream_t st);
+// The exact scans of the ranges the re-score queued and the map output, one
+// launch.
+cudaError_t launch_scans_finalize(const Geometry &g, const RangeInfo *ri, const DomainInfo *di, const uint16_t *bblk,
+                                  const uint16_t *qblk, const int *fb_list, int *fb_count, void *partial,
+                                  const int *counts, const int *dmap, int col_tile, int target, int max_split,
+                                  int lists_per_split, int max_lists, void *span, uint32_t *winner, const int *err,
+                                  fic_map *maps, int n_sm, cudaStream_t st);
 size_t fallback_partial_bytes(const Geometry &g);
-
-cudaError_t launch_finalize(const Geometry &g, const RangeInfo *ri, const DomainInfo *di,
-                            const uint16_t *bblk, const uint16_t *qblk, const uint32_t *winner,
-                            const int *err, fic_map *maps, cudaStream_t st);
 size_t decode_workspace_bytes(const Geometry &g);
 cudaError_t launch_decode(const Geometry &g, const fic_map *maps, float init, int iters, void *ws,
                           float *out, cudaStream_t st);

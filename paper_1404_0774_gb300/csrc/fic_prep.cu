@@ -14,8 +14,8 @@ namespace fic {
 // lane; m = 256 takes the whole warp), so a warp holds 32 / G items whose
 // sums reduce within their lane groups and whose per-item tails run side by
 // side.
-__host__ __device__ __forceinline__ int stats_group(int m) { return m >= 256 ? 32 : m / 8; }
-__host__ __device__ __forceinline__ int stats_items(int m) { return 8 * (32 / stats_group(m)); }  // per block
+__host__ __device__ constexpr int stats_group(int m) { return m >= 256 ? 32 : m / 8; }
+__host__ __device__ constexpr int stats_items(int m) { return 8 * (32 / stats_group(m)); }  // per block
 __host__ __device__ __forceinline__ int stats_range_blocks(const Geometry &g)
 {
     return (g.R + stats_items(g.m) - 1) / stats_items(g.m);
@@ -38,22 +38,23 @@ __device__ __forceinline__ T group_sum(T v, int G)
 // centre, allowances, and the keep flag (every range but shadow ranges, or
 // all when dense).  `valid` is false for the lanes of a group past the last
 // range: they take part in the reductions only.
+template <int LN, bool B8>
 __device__ __forceinline__ void range_stats(const Geometry &g, const EpiConst &ec, const void *img, int dense,
                                             int tc_mode, const int *active, int r, bool valid, int li, int G,
                                             RangeInfo *ri, uint16_t *bblk, int *tbest, int *rkeep)
 {
+    constexpr int n = 1 << LN, m = n * n;
     const int rr = valid ? r : 0;
-    const int ry = (rr / g.nx) * g.n, rx = (rr % g.nx) * g.n;
+    const int ry = (rr / g.nx) * n, rx = (rr % g.nx) * n;
     int bv[8];
     long long Sb = 0, Sbb = 0;
     int bmin = 1 << 30, bmax = -1;
     // every load issued before the first use (no store between them)
-    const bool b8 = g.B <= 8;
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
         const int i = li + G * j;
-        const size_t off = (size_t)(ry + (i >> g.ln)) * g.pitch + rx + (i & (g.n - 1));
-        bv[j] = valid ? (b8 ? (int)((const uint8_t *)img)[off] : (int)((const uint16_t *)img)[off]) : 0;
+        const size_t off = (size_t)(ry + (i >> LN)) * g.pitch + rx + (i & (n - 1));
+        bv[j] = valid ? (B8 ? (int)((const uint8_t *)img)[off] : (int)((const uint16_t *)img)[off]) : 0;
     }
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
@@ -62,7 +63,7 @@ __device__ __forceinline__ void range_stats(const Geometry &g, const EpiConst &e
         Sbb += (long long)b * b;
         bmin = min(bmin, b);
         bmax = max(bmax, b);
-        if (valid) bblk[(size_t)rr * g.m + li + G * j] = (uint16_t)b;
+        if (valid) bblk[(size_t)rr * m + li + G * j] = (uint16_t)b;
     }
     Sb = group_sum(Sb, G);
     Sbb = group_sum(Sbb, G);
@@ -73,12 +74,12 @@ __device__ __forceinline__ void range_stats(const Geometry &g, const EpiConst &e
     if (!valid || li != 0) return;
     // centre: nearest integer to the mean, kept within 2048 of every pixel so
     // that b - c_r is an exact FP16 integer
-    long long cr = (2 * Sb + g.m) >> (2 * g.ln + 1);  // m = 2^(2 ln), Sb >= 0
+    long long cr = (2 * Sb + m) >> (2 * LN + 1);  // m = 2^(2 ln), Sb >= 0
     cr = max((long long)(bmax - 2048), min((long long)(bmin + 2048), cr));
     const int c_r = (int)cr;
-    const int e_r = (int)(Sb - (long long)g.m * c_r);
+    const int e_r = (int)(Sb - (long long)m * c_r);
     // sum (b - c_r)^2, exactly
-    const float bp2f = __ll2float_rn(Sbb - 2 * cr * Sb + (long long)g.m * cr * cr);
+    const float bp2f = __ll2float_rn(Sbb - 2 * cr * Sb + (long long)m * cr * cr);
     // per-range constants: integer arithmetic and FP32 only (the FP64 rate of
     // this part is a small fraction of FP32)
     RangeInfo info;
@@ -86,8 +87,8 @@ __device__ __forceinline__ void range_stats(const Geometry &g, const EpiConst &e
     info.Sbb = Sbb;
     info.c_r = c_r;
     info.e_r = e_r;
-    const float invm = 1.0f / (float)g.m;
-    info.sbbc = (float)((long long)g.m * Sbb - Sb * Sb) * invm;
+    constexpr float invm = 1.0f / (float)m;
+    info.sbbc = (float)((long long)m * Sbb - Sb * Sb) * invm;
     const int z = 4 * g.Ls * (int)Sb;  // < 2^31 for B <= 12, m <= 256, s_bits <= 8
     info.zb = (float)(g.mod_g ? z % g.Gi : z);
     info.bp2 = bp2f;
@@ -104,7 +105,7 @@ __device__ __forceinline__ void range_stats(const Geometry &g, const EpiConst &e
     // accumulation bound doubled (the hardware's order of the FP32 additions
     // is not specified).
     const float er_abs = fabsf((float)e_r);
-    const float acc_err = 12.0f * g.Ls * (float)max(64, g.m) * bp2f * 3.552713678800501e-15f;  // 2^-48
+    const float acc_err = 12.0f * g.Ls * (float)(m > 64 ? m : 64) * bp2f * 3.552713678800501e-15f;  // 2^-48
     const float eta = tc_mode == 1   ? 1e-5f + 1.2e-7f * g.Ls * (2.0f + 2.1f * er_abs)
                       : tc_mode == 2 ? 1e-5f + 2.0f * acc_err + 1.2e-7f * g.Ls * (2.0f + 2.1f * er_abs)
                                      : 1e-5f + acc_err;
@@ -117,7 +118,7 @@ __device__ __forceinline__ void range_stats(const Geometry &g, const EpiConst &e
     const float sbbc = fmaxf(info.sbbc, 0.0f);
     const float Eb = 4.0f * (sbbc + ec.delta_o);
     const float sb = sqrtf(bp2f);
-    const float sqm = sqrtf((float)g.m);
+    const float sqm = n;  // sqrt(m)
     const float S = (4.0f * g.Ls * (sqrtf(sbbc) + sqrtf(Eb)) + sqm) * sb + (g.split_hilo ? 128.0f * sqm * sb : 0.0f);
     const bool exact = tc_mode == 1 || S < 8.0e6f;  // < 2^23 with margin, or exact partial sums
     const float gam = 3.0517578125e-05f;  // 2^-15
@@ -137,24 +138,25 @@ __device__ __forceinline__ void range_stats(const Geometry &g, const EpiConst &e
 // each): the 2x2 sums q (tau as an integer sum, the mean being q/4), Sq, Sqq,
 // centre, the epilogue column constants, and the keep flag (every domain but
 // flat ones, den = 0, or all when dense).
+template <int LN, bool B8>
 __device__ __forceinline__ void domain_stats(const Geometry &g, const void *img, int dense, int d, bool valid,
                                              int li, int G, DomainInfo *di, float4 *dconst, uint16_t *qblk,
                                              int *dkeep)
 {
+    constexpr int n = 1 << LN, m = n * n;
     const int dd0 = valid ? d : 0;
     const int dy = (dd0 / g.U) * g.t, dx = (dd0 % g.U) * g.t;
     long long Sq = 0, Sqq = 0;
     int qv[8];
-    const bool b8 = g.B <= 8;
     // every load issued before the first store
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
         const int i = li + G * j;
-        const int y = i >> g.ln, x = i & (g.n - 1);
+        const int y = i >> LN, x = i & (n - 1);
         const size_t o0 = (size_t)(dy + 2 * y) * g.pitch + dx + 2 * x;
         int q = 0;
         if (valid) {
-            if (b8) {
+            if (B8) {
                 const uint8_t *p8 = (const uint8_t *)img;
                 q = (int)p8[o0] + (int)p8[o0 + 1] + (int)p8[o0 + g.pitch] + (int)p8[o0 + g.pitch + 1];
             } else {
@@ -167,15 +169,14 @@ __device__ __forceinline__ void domain_stats(const Geometry &g, const void *img,
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
         const int q = qv[j];
-        if (valid) qblk[(size_t)d * g.m + li + G * j] = (uint16_t)q;
+        if (valid) qblk[(size_t)d * m + li + G * j] = (uint16_t)q;
         Sq += q;
         Sqq += (long long)q * q;
     }
     Sq = group_sum(Sq, G);
     Sqq = group_sum(Sqq, G);
     if (!valid || li != 0) return;
-    const int m = g.m;
-    const long long cd = (2 * Sq + m) >> (2 * g.ln + 1);  // m = 2^(2 ln), Sq >= 0
+    const long long cd = (2 * Sq + m) >> (2 * LN + 1);  // m = 2^(2 ln), Sq >= 0
     const long long den = (long long)m * Sqq - Sq * Sq;
     DomainInfo info;
     info.Sq = Sq;
@@ -198,43 +199,61 @@ __device__ __forceinline__ void domain_stats(const Geometry &g, const void *img,
 
 // Statistics of every range (the first stats_range_blocks blocks) and every
 // domain (the blocks after), one launch; stats_items per block of 256.
+template <int LN, bool B8>
 __device__ __forceinline__ void stats_block(const Geometry &g, const EpiConst &ec, const void *img, int dense,
                                             int tc_mode, const int *active, RangeInfo *ri, uint16_t *bblk,
                                             int *tbest, DomainInfo *di, float4 *dconst, uint16_t *qblk, int *rkeep,
                                             int *dkeep, int *zero4, int bx)
 {
     if (bx == 0 && threadIdx.x < 4) zero4[threadIdx.x] = 0;  // exact-scan queue counters
-    const int G = stats_group(g.m), per_block = stats_items(g.m), rbs = stats_range_blocks(g);
+    constexpr int G = stats_group(1 << (2 * LN)), per_block = stats_items(1 << (2 * LN));
+    const int rbs = stats_range_blocks(g);
     const int li = threadIdx.x & (G - 1);
     const int item = threadIdx.x / G;  // (warp, group) in order
     if (bx < rbs) {
         const int r = bx * per_block + item;
-        range_stats(g, ec, img, dense, tc_mode, active, r, r < g.R, li, G, ri, bblk, tbest, rkeep);
+        range_stats<LN, B8>(g, ec, img, dense, tc_mode, active, r, r < g.R, li, G, ri, bblk, tbest, rkeep);
     } else {
         const int d = (bx - rbs) * per_block + item;
-        domain_stats(g, img, dense, d, d < g.D, li, G, di, dconst, qblk, dkeep);
+        domain_stats<LN, B8>(g, img, dense, d, d < g.D, li, G, di, dconst, qblk, dkeep);
     }
 }
 
+template <int LN, bool B8>
 __global__ void __launch_bounds__(256) k_stats(Geometry g, EpiConst ec, const void *img, int dense, int tc_mode,
                                                const int *active, RangeInfo *ri, uint16_t *bblk, int *tbest,
                                                DomainInfo *di, float4 *dconst, uint16_t *qblk, int *rkeep,
                                                int *dkeep, int *zero4)
 {
     grid_dep_sync();
-    stats_block(g, ec, img, dense, tc_mode, active, ri, bblk, tbest, di, dconst, qblk, rkeep, dkeep, zero4,
-                blockIdx.x);
+    stats_block<LN, B8>(g, ec, img, dense, tc_mode, active, ri, bblk, tbest, di, dconst, qblk, rkeep, dkeep, zero4,
+                        blockIdx.x);
 }
 
 // Batched: blockIdx.y = slice.
+template <int LN, bool B8>
 __global__ void __launch_bounds__(256) k_stats_batch(const SliceCtx *__restrict__ ctx, int dense, int tc_mode)
 {
     grid_dep_sync();
     const SliceCtx c = ctx[blockIdx.y];
     if ((int)blockIdx.x >= stats_blocks(c.g)) return;
     const EncBufs &b = c.b;
-    stats_block(c.g, c.ec, c.img, dense, tc_mode, nullptr, b.ri, b.bblk, b.tbest, b.di, b.dconst, b.qblk,
+    stats_block<LN, B8>(c.g, c.ec, c.img, dense, tc_mode, nullptr, b.ri, b.bblk, b.tbest, b.di, b.dconst, b.qblk,
                 b.cb.rkeep, b.cb.dkeep, b.fb_count, blockIdx.x);
+}
+
+// The statistics kernels of a geometry (range size and 8-bit pixels are
+// template parameters): calls launch(single, batched).
+template <typename Launch>
+static cudaError_t with_stats_kernel(const Geometry &g, Launch &&launch)
+{
+    const bool b8 = g.B <= 8;
+    switch (g.ln) {
+    case 2: return b8 ? launch(k_stats<2, true>, k_stats_batch<2, true>) : launch(k_stats<2, false>, k_stats_batch<2, false>);
+    case 3: return b8 ? launch(k_stats<3, true>, k_stats_batch<3, true>) : launch(k_stats<3, false>, k_stats_batch<3, false>);
+    case 4: return b8 ? launch(k_stats<4, true>, k_stats_batch<4, true>) : launch(k_stats<4, false>, k_stats_batch<4, false>);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 // Stable compaction of the flagged items by one block of T threads, over
@@ -323,164 +342,180 @@ __device__ __forceinline__ void compact_block(int nr, const int *rflag, int *rac
 }
 
 
-__device__ __forceinline__ uint32_t pack_h2(__half a, __half b)
+// FP16 bit pattern of an integer of magnitude below 2^11 (exact).
+__device__ __forceinline__ uint32_t h16(int v) { return __half_as_ushort(__int2half_rn(v)); }
+
+// Reverses the order of the 8 (4) FP16 values of v when sel = 0x5476 (sel =
+// 0x3210 leaves them): each output word takes the mirrored input word with
+// its halves swapped.
+__device__ __forceinline__ uint4 rev8_sel(uint4 v, uint32_t sel)
 {
-    return (uint32_t)__half_as_ushort(a) | ((uint32_t)__half_as_ushort(b) << 16);
+    return make_uint4(__byte_perm(v.x, v.w, sel), __byte_perm(v.y, v.z, sel), __byte_perm(v.z, v.y, sel),
+                      __byte_perm(v.w, v.x, sel));
 }
 
-// Operand row j (j < count) of the range act[j]: centred pixels b - c_r
-// (twice when q is split into hi/lo parts), then e_hi, e_lo (e_r = 1024 e_hi
-// + e_lo) and zeros.
-__device__ __forceinline__ void range_row(const Geometry &g, const RangeInfo *ri, const uint16_t *bblk, int j, int r,
-                                          int lane, float *rs32, __half *ra16)
+__device__ __forceinline__ uint2 rev4_sel(uint2 v, uint32_t sel)
 {
-    const RangeInfo info = ri[r];
-    constexpr int PPL = kMaxM / 32;
-    int bv[PPL];
-#pragma unroll
-    for (int u = 0; u < PPL; ++u) {  // every load before the first store
-        if (32 * u >= g.m) break;  // warp-uniform
-        const int i = lane + 32 * u;
-        bv[u] = i < g.m ? (int)bblk[(size_t)r * g.m + i] : 0;
-    }
-#pragma unroll
-    for (int u = 0; u < PPL; ++u) {
-        const int i = lane + 32 * u;
-        if (i >= g.m) break;
-        const int bc = bv[u] - info.c_r;
-        if (rs32) rs32[(size_t)j * g.m + i] = (float)bc;
-        if (ra16) {
-            ra16[(size_t)j * g.KP + i] = __int2half_rn(bc);
-            if (g.split_hilo) ra16[(size_t)j * g.KP + g.m + i] = __int2half_rn(bc);
-        }
-    }
+    return make_uint2(__byte_perm(v.x, v.y, sel), __byte_perm(v.y, v.x, sel));
+}
+
+// Operand row shapes for ranges of 2^LN x 2^LN pixels; SPLIT: q' is split
+// into hi/lo FP16 parts (bit depths above 8).
+template <int LN, bool SPLIT>
+struct RowShape {
+    static constexpr int n = 1 << LN, m = n * n;
+    static constexpr int base = SPLIT ? 2 * m : m;  // first column after the pixel parts
+    static constexpr int KP = base + 16;             // FP16 row length (Geometry::KP)
+    static constexpr int nch = KP / 8;               // 16-byte chunks per row
+};
+
+// Operand row j (j < count) of the range r: centred pixels b - c_r (twice
+// when q is split into hi/lo parts), then e_hi, e_lo (e_r = 1024 e_hi + e_lo)
+// and zeros.  FP16 layout: one 16-byte chunk per lane, 8 pixels converted
+// from one 16-byte load of the range's pixels.
+template <int LN, bool SPLIT>
+__device__ __forceinline__ void range_row(const RangeInfo *ri, const uint16_t *bblk, int j, int r, int lane,
+                                          float *rs32, __half *ra16)
+{
+    typedef RowShape<LN, SPLIT> S;
+    const int c_r = ri[r].c_r;
     if (ra16) {
-        const int base = g.split_hilo ? 2 * g.m : g.m;
-        const int e_r = info.e_r;
+        const int e_r = ri[r].e_r;
         const int e_hi = (e_r >= 0) ? (e_r >> 10) : -((-e_r + 1023) >> 10);
         const int e_lo = e_r - 1024 * e_hi;
-        for (int c = base + lane; c < g.KP; c += 32) {
-            const int v = c == base ? e_hi : (c == base + 1 ? e_lo : 0);
-            ra16[(size_t)j * g.KP + c] = __int2half_rn(v);
+        uint4 *row = reinterpret_cast<uint4 *>(ra16 + (size_t)j * S::KP);
+        const uint4 *src = reinterpret_cast<const uint4 *>(bblk + (size_t)r * S::m);
+        for (int c = lane; c < S::nch; c += 32) {
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (c < S::base / 8) {
+                const uint4 w = src[SPLIT && c >= S::m / 8 ? c - S::m / 8 : c];
+                v.x = h16((int)(w.x & 0xffffu) - c_r) | (h16((int)(w.x >> 16) - c_r) << 16);
+                v.y = h16((int)(w.y & 0xffffu) - c_r) | (h16((int)(w.y >> 16) - c_r) << 16);
+                v.z = h16((int)(w.z & 0xffffu) - c_r) | (h16((int)(w.z >> 16) - c_r) << 16);
+                v.w = h16((int)(w.w & 0xffffu) - c_r) | (h16((int)(w.w >> 16) - c_r) << 16);
+            } else if (c == S::base / 8) {
+                v.x = h16(e_hi) | (h16(e_lo) << 16);
+            }
+            row[c] = v;
         }
     }
-}
-
-// 8 (4) FP16 bit patterns in reverse order.
-__device__ __forceinline__ uint4 rev8(uint4 v)
-{
-    return make_uint4(__byte_perm(v.w, 0, 0x1032), __byte_perm(v.z, 0, 0x1032), __byte_perm(v.y, 0, 0x1032),
-                      __byte_perm(v.x, 0, 0x1032));
-}
-
-__device__ __forceinline__ uint2 rev4(uint2 v)
-{
-    return make_uint2(__byte_perm(v.y, 0, 0x1032), __byte_perm(v.x, 0, 0x1032));
-}
-
-// Elements i0 .. i0+7 (i0 a multiple of 8) of S_k applied to an n x n block
-// held row-major in s and transposed in t (16-byte aligned).  Output (y, x)
-// reads s at row u ^ my, column v ^ mx with (u, v) = swap ? (x, y) : (y, x);
-// with the axes swapped that is t at row y ^ mx, column x ^ my.  Either way
-// the 8 elements are a run along one row of s or t, reversed when the column
-// mask is set (n >= 8: one run of 8; n = 4: two runs of 4).
-__device__ __forceinline__ uint4 sym_chunk(const uint16_t *s, const uint16_t *t, const SymFlags &f, int n, int ln,
-                                           int i0)
-{
-    const uint16_t *b = f.swap ? t : s;
-    const int rm = f.swap ? f.mx : f.my, cm = f.swap ? f.my : f.mx;
-    if (n >= 8) {
-        const int y = i0 >> ln, x0 = i0 & (n - 1);
-        const uint4 v = *reinterpret_cast<const uint4 *>(b + ((y ^ rm) << ln) + ((x0 ^ cm) & ~7));
-        return cm ? rev8(v) : v;
+    if (rs32) {
+        for (int i = lane; i < S::m; i += 32) rs32[(size_t)j * S::m + i] = (float)((int)bblk[(size_t)r * S::m + i] - c_r);
     }
-    const int y = i0 >> 2;
-    uint2 r0 = *reinterpret_cast<const uint2 *>(b + ((y ^ rm) << 2));
-    uint2 r1 = *reinterpret_cast<const uint2 *>(b + (((y + 1) ^ rm) << 2));
-    if (cm) {
-        r0 = rev4(r0);
-        r1 = rev4(r1);
-    }
-    return make_uint4(r0.x, r0.y, r1.x, r1.y);
 }
 
-// Candidate rows 8j+k of the domain dact[j]: output pixel i = (y,x) of
+// Per-lane constants of the FP16 domain rows: lane = 4 k + c0 writes chunks
+// c0, c0 + 4, ... of the row of symmetry k, whose flags are fixed per lane.
+struct RowLane {
+    int k;
+    int part;      // staging part read: + 2 m when S_k swaps the axes (transposed copies)
+    int rm, cm;    // row and column masks in the part read
+    uint32_t sel;  // byte selector: reverse the chunk when the column mask is set
+};
+
+template <int LN>
+__device__ __forceinline__ RowLane row_lane(int lane)
+{
+    constexpr int n = 1 << LN, m = n * n;
+    const SymFlags f = sym_flags(lane >> 2, n);
+    RowLane L;
+    L.k = lane >> 2;
+    L.part = f.swap ? 2 * m : 0;
+    L.rm = f.swap ? f.mx : f.my;
+    L.cm = f.swap ? f.my : f.mx;
+    L.sel = L.cm ? 0x5476u : 0x3210u;
+    return L;
+}
+
+// Candidate rows 8j+k of the domain d: output pixel i = (y,x) of
 // S_k(tau(d)) is q at sym_src_index(k, i), centred by c_d.  FP16 row
 // (tensor-core layout): [128*hi | lo (12-bit only) | -1024 f_d/m, -f_d/m,
 // 0...] with q - c_d = 128*hi + lo.  The warp converts the domain's m values
-// once into FP16 bit patterns in shared memory, row-major and transposed, then
-// writes the 16-byte chunks of the 8 rows, each one aligned shared-memory load
-// (KP and m are multiples of 8, so a chunk never straddles two parts).
-// Domain constants in the same order.
-__device__ __forceinline__ void domain_rows_warp(const Geometry &g, const DomainInfo *di, const uint16_t *qblk,
-                                                 const float4 *dconst, int j, int d, int lane,
-                                                 uint16_t *hi_s, uint16_t *lo_s, uint16_t *hit_s, uint16_t *lot_s,
-                                                 float *cb32, __half *cb16, float4 *dconst_c, int *dmap)
+// once into FP16 bit patterns in shared memory (st: hi, lo, then both
+// transposed), then writes the 16-byte chunks of the 8 rows: under S_k the 8
+// values of a chunk are a run along one row of a staged part (of the
+// transposed part when S_k swaps the axes), reversed when S_k flips the
+// columns (n >= 8: one run of 8; n = 4: two runs of 4).  SIMT layout (cb32):
+// the 8 symmetric copies of q - c_d in FP32.  Domain constants in the same
+// order.
+template <int LN, bool SPLIT>
+__device__ __forceinline__ void domain_rows_warp(const DomainInfo *di, const uint16_t *qblk, const float4 *dconst, int j,
+                                                 int d, int lane, const RowLane &rl, uint16_t *st, float *cb32,
+                                                 __half *cb16, float4 *dconst_c, int *dmap)
 {
-    const int m = g.m;
-    const DomainInfo info = di[d];
-    const int c_d = info.c_d, fd = info.f_d;
+    typedef RowShape<LN, SPLIT> S;
+    constexpr int n = S::n, m = S::m;
+    constexpr int QPL = (m + 31) / 32;
+    int qv[QPL];
+#pragma unroll
+    for (int u = 0; u < QPL; ++u) {  // every load before the first store
+        const int i = lane + 32 * u;
+        qv[u] = i < m ? (int)qblk[(size_t)d * m + i] : 0;
+    }
+    const int c_d = di[d].c_d, fd = di[d].f_d;
     if (lane == 0) {
         dconst_c[j] = dconst[d];
         dmap[j] = d;
     }
-    constexpr int QPL = kMaxM / 32;
-    int qv[QPL];
-#pragma unroll
-    for (int u = 0; u < QPL; ++u) {  // every load before the first store
-        if (32 * u >= m) break;  // warp-uniform
-        const int i = lane + 32 * u;
-        qv[u] = i < m ? (int)qblk[(size_t)d * m + i] : 0;
-    }
 #pragma unroll
     for (int u = 0; u < QPL; ++u) {
         const int i = lane + 32 * u;
-        if (i >= m) break;
-        const int qc = qv[u] - c_d;
-        const int it = ((i & (g.n - 1)) << g.ln) + (i >> g.ln);  // transposed position
-        if (cb32) {
-            lo_s[i] = (uint16_t)(qc + 32768);  // SIMT operand: centred value, biased
-        } else if (g.split_hilo) {
-            const int hi = (qc + 64) >> 7;  // floor; |hi| <= 128
-            const uint16_t h = __half_as_ushort(__int2half_rn(128 * hi));
-            const uint16_t l = __half_as_ushort(__int2half_rn(qc - 128 * hi));
-            hi_s[i] = h;
-            hit_s[it] = h;
-            lo_s[i] = l;
-            lot_s[it] = l;
-        } else {
-            const uint16_t h = __half_as_ushort(__int2half_rn(qc));
-            hi_s[i] = h;
-            hit_s[it] = h;
+        if (i < m) {
+            const int qc = qv[u] - c_d;
+            const int it = ((i & (n - 1)) << LN) + (i >> LN);  // transposed position
+            if (cb32) {
+                st[i] = (uint16_t)(qc + 32768);  // SIMT operand: centred value, biased
+            } else if (SPLIT) {
+                const int hi = (qc + 64) >> 7;  // floor; |hi| <= 128
+                const uint16_t h = (uint16_t)h16(128 * hi), l = (uint16_t)h16(qc - 128 * hi);
+                st[i] = h;
+                st[m + i] = l;
+                st[2 * m + it] = h;
+                st[3 * m + it] = l;
+            } else {
+                const uint16_t h = (uint16_t)h16(qc);
+                st[i] = h;
+                st[2 * m + it] = h;
+            }
         }
     }
     __syncwarp();
     if (cb32) {
         for (int k = 0; k < 8; ++k) {
-            const SymFlags f = sym_flags(k, g.n);
+            const SymFlags f = sym_flags(k, n);
             for (int i = lane; i < m; i += 32)
                 cb32[((size_t)j * 8 + k) * m + i] =
-                    (float)((int)lo_s[sym_src_index(f, g.ln, i >> g.ln, i & (g.n - 1))] - 32768);
+                    (float)((int)st[sym_src_index(f, LN, i >> LN, i & (n - 1))] - 32768);
         }
         return;
     }
-    const int nch = g.KP >> 3;  // 16-byte chunks per row
-    const int base = g.split_hilo ? 2 * m : m;
-    const uint32_t t0 = __half_as_ushort(__float2half_rn(-1024.0f * (float)fd / (float)m));
-    const uint32_t t1 = __half_as_ushort(__float2half_rn(-(float)fd / (float)m));
-    // four lanes per symmetry k = lane / 4, chunks c = lane % 4, + 4, ...:
-    // the symmetry's flags are fixed per lane
-    const int k = lane >> 2;
-    const SymFlags sf = sym_flags(k, g.n);
-    uint4 *row = reinterpret_cast<uint4 *>(cb16 + ((size_t)j * 8 + k) * g.KP);
-    for (int c = lane & 3; c < nch; c += 4) {
+    // tail: -f_d/m in the scale of the hi part and of the lo part (m is a
+    // power of two: the products are the exact quotients)
+    const uint32_t tail = (uint32_t)__half_as_ushort(__float2half_rn((float)fd * (-1024.0f / m))) |
+                          ((uint32_t)__half_as_ushort(__float2half_rn((float)fd * (-1.0f / m))) << 16);
+    uint4 *row = reinterpret_cast<uint4 *>(cb16 + ((size_t)j * 8 + rl.k) * S::KP);
+    constexpr int NI = (S::nch + 3) / 4;
+#pragma unroll
+    for (int it = 0; it < NI; ++it) {
+        const int c = (lane & 3) + 4 * it;
+        if (c >= S::nch) break;
         const int col0 = 8 * c;
         uint4 v;
-        if (col0 >= base) {
-            v = make_uint4(col0 == base ? (t0 | (t1 << 16)) : 0u, 0u, 0u, 0u);
+        if (col0 >= S::base) {
+            v = make_uint4(col0 == S::base ? tail : 0u, 0u, 0u, 0u);
         } else {
-            const bool lo_part = col0 >= m;  // second copy (12-bit only)
-            v = sym_chunk(lo_part ? lo_s : hi_s, lo_part ? lot_s : hit_s, sf, g.n, g.ln, lo_part ? col0 - m : col0);
+            const bool lo_part = SPLIT && col0 >= m;  // second copy (12-bit only)
+            const int i0 = lo_part ? col0 - m : col0;
+            const uint16_t *b = st + rl.part + (lo_part ? m : 0);
+            if (n >= 8) {
+                const int y = i0 >> LN, x0 = i0 & (n - 1);
+                v = rev8_sel(*reinterpret_cast<const uint4 *>(b + ((y ^ rl.rm) << LN) + ((x0 ^ rl.cm) & ~7)), rl.sel);
+            } else {
+                const int y = i0 >> 2;
+                const uint2 r0 = rev4_sel(*reinterpret_cast<const uint2 *>(b + ((y ^ rl.rm) << 2)), rl.sel);
+                const uint2 r1 = rev4_sel(*reinterpret_cast<const uint2 *>(b + (((y + 1) ^ rl.rm) << 2)), rl.sel);
+                v = make_uint4(r0.x, r0.y, r1.x, r1.y);
+            }
         }
         row[c] = v;
     }
@@ -491,49 +526,70 @@ __device__ __forceinline__ void domain_rows_warp(const Geometry &g, const Domain
 // warp): first the range groups, then the domain groups, as many as the
 // compaction kept; block `first` takes every stride-th group, so a grid of
 // resident blocks covers them with no block spent on nothing.
-constexpr int kRowsBlocksPerSm = 5;  // resident at 48 registers x 256 threads
-__device__ __forceinline__ void rows_block(const Geometry &g, const RangeInfo *ri, const uint16_t *bblk,
-                                           const DomainInfo *di, const uint16_t *qblk, const float4 *dconst,
-                                           const int *act, const int *dact, const int *counts, float *rs32,
-                                           __half *ra16, float *cb32, __half *cb16, float4 *dconst_c, int *dmap,
-                                           int first, int stride)
+// Resident blocks per SM: 5 at 48 registers x 256 threads; 4 (64 registers)
+// for 16x16 ranges, whose 8 pixels a lane would not fit in 48 without spills.
+__host__ __device__ constexpr int rows_blocks_per_sm(int ln) { return ln == 4 ? 4 : 5; }
+template <int LN, bool SPLIT>
+__device__ __forceinline__ void rows_block(const RangeInfo *ri, const uint16_t *bblk, const DomainInfo *di,
+                                           const uint16_t *qblk, const float4 *dconst, const int *act,
+                                           const int *dact, const int *counts, float *rs32, __half *ra16,
+                                           float *cb32, __half *cb16, float4 *dconst_c, int *dmap, int first,
+                                           int stride)
 {
-    __shared__ __align__(16) uint16_t hi_s[8][kMaxM], lo_s[8][kMaxM], hit_s[8][kMaxM], lot_s[8][kMaxM];
+    constexpr int m = 1 << (2 * LN);
+    __shared__ __align__(16) uint16_t st_s[8][4 * m];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const RowLane rl = row_lane<LN>(lane);
     const int nr = counts[0], nd = counts[2];
     const int rgroups = (nr + 7) / 8, groups = rgroups + (nd + 7) / 8;
     for (int vb = first; vb < groups; vb += stride) {
         if (vb < rgroups) {
             const int j = vb * 8 + w;
-            if (j < nr) range_row(g, ri, bblk, j, act[j], lane, rs32, ra16);
+            if (j < nr) range_row<LN, SPLIT>(ri, bblk, j, act[j], lane, rs32, ra16);
         } else {
             const int j = (vb - rgroups) * 8 + w;
             if (j < nd) {
-                __syncwarp();  // the warp's staging arrays of its previous domain are read
-                domain_rows_warp(g, di, qblk, dconst, j, dact[j], lane, hi_s[w], lo_s[w], hit_s[w], lot_s[w],
-                                 cb32, cb16, dconst_c, dmap);
+                __syncwarp();  // the warp's staging area of its previous domain is read
+                domain_rows_warp<LN, SPLIT>(di, qblk, dconst, j, dact[j], lane, rl, st_s[w], cb32, cb16, dconst_c,
+                                            dmap);
             }
         }
     }
 }
 
-__global__ void __launch_bounds__(256, kRowsBlocksPerSm) k_rows(Geometry g, const RangeInfo *ri, const uint16_t *bblk,
+template <int LN, bool SPLIT>
+__global__ void __launch_bounds__(256, rows_blocks_per_sm(LN)) k_rows(const RangeInfo *ri, const uint16_t *bblk,
                                               const DomainInfo *di, const uint16_t *qblk, const float4 *dconst,
                                               const int *act, const int *dact, const int *counts, float *rs32,
                                               __half *ra16, float *cb32, __half *cb16, float4 *dconst_c, int *dmap)
 {
     grid_dep_sync();
-    rows_block(g, ri, bblk, di, qblk, dconst, act, dact, counts, rs32, ra16, cb32, cb16, dconst_c, dmap, blockIdx.x,
-               gridDim.x);
+    rows_block<LN, SPLIT>(ri, bblk, di, qblk, dconst, act, dact, counts, rs32, ra16, cb32, cb16, dconst_c, dmap,
+                          blockIdx.x, gridDim.x);
 }
 
-__global__ void __launch_bounds__(256, kRowsBlocksPerSm) k_rows_batch(const SliceCtx *__restrict__ ctx)
+template <int LN, bool SPLIT>
+__global__ void __launch_bounds__(256, rows_blocks_per_sm(LN)) k_rows_batch(const SliceCtx *__restrict__ ctx)
 {
     grid_dep_sync();
     const SliceCtx &c = ctx[blockIdx.y];
     const EncBufs &b = c.b;
-    rows_block(c.g, b.ri, b.bblk, b.di, b.qblk, b.dconst, b.cb.act, b.cb.dact, b.cb.counts, b.rs32, b.ra16, b.cb32,
-               b.cb16, b.cb.dconst_c, b.cb.dmap, blockIdx.x, gridDim.x);
+    rows_block<LN, SPLIT>(b.ri, b.bblk, b.di, b.qblk, b.dconst, b.cb.act, b.cb.dact, b.cb.counts, b.rs32, b.ra16,
+                          b.cb32, b.cb16, b.cb.dconst_c, b.cb.dmap, blockIdx.x, gridDim.x);
+}
+
+// The row kernels of a geometry (range size and hi/lo split are template
+// parameters): calls launch(single, batched).
+template <typename Launch>
+static cudaError_t with_rows_kernel(const Geometry &g, Launch &&launch)
+{
+    const bool sp = g.split_hilo != 0;
+    switch (g.ln) {
+    case 2: return sp ? launch(k_rows<2, true>, k_rows_batch<2, true>) : launch(k_rows<2, false>, k_rows_batch<2, false>);
+    case 3: return sp ? launch(k_rows<3, true>, k_rows_batch<3, true>) : launch(k_rows<3, false>, k_rows_batch<3, false>);
+    case 4: return sp ? launch(k_rows<4, true>, k_rows_batch<4, true>) : launch(k_rows<4, false>, k_rows_batch<4, false>);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 
@@ -861,8 +917,10 @@ cudaError_t launch_prep(const Geometry &g, const void *img, const EpiConst &ec, 
                         int seed, cudaStream_t st)
 {
     const int rb = (g.R + 7) / 8, db = (g.D + 7) / 8;
-    cudaError_t e = launch_dep(k_stats, dim3(stats_blocks(g)), dim3(256), 0, st, g, ec, img, dense, tc_mode, active,
-                               ri, bblk, tbest, di, dconst, qblk, cb.rkeep, cb.dkeep, zero4);
+    cudaError_t e = with_stats_kernel(g, [&](auto one, auto) {
+        return launch_dep(one, dim3(stats_blocks(g)), dim3(256), 0, st, g, ec, img, dense, tc_mode, active, ri, bblk,
+                          tbest, di, dconst, qblk, cb.rkeep, cb.dkeep, zero4);
+    });
     if (e != cudaSuccess) return e;
     const int sw = seed_warps(g.m);
     e = with_seed_shape(g.m, [&](auto one, auto, int threads) {
@@ -873,19 +931,23 @@ cudaError_t launch_prep(const Geometry &g, const void *img, const EpiConst &ec, 
                           (const int *)cb.dkeep, cb.act, cb.dact, cb.counts, tbest);
     });
     if (e != cudaSuccess) return e;
-    const int blocks = std::max(1, std::min(rb + db, kRowsBlocksPerSm * prep_sms()));
-    return launch_dep(k_rows, dim3(blocks), dim3(256), 0, st, g, (const RangeInfo *)ri, (const uint16_t *)bblk,
-                      (const DomainInfo *)di, (const uint16_t *)qblk, (const float4 *)dconst, (const int *)cb.act,
-                      (const int *)cb.dact, (const int *)cb.counts, rs32, ra16, cb32, cb16, cb.dconst_c, cb.dmap);
+    const int blocks = std::max(1, std::min(rb + db, rows_blocks_per_sm(g.ln) * prep_sms()));
+    return with_rows_kernel(g, [&](auto one, auto) {
+        return launch_dep(one, dim3(blocks), dim3(256), 0, st, (const RangeInfo *)ri, (const uint16_t *)bblk,
+                          (const DomainInfo *)di, (const uint16_t *)qblk, (const float4 *)dconst, (const int *)cb.act,
+                          (const int *)cb.dact, (const int *)cb.counts, rs32, ra16, cb32, cb16, cb.dconst_c, cb.dmap);
+    });
 }
 
 // Batched prep stages of n slices (ctx: device array; blocks / ranges: the
 // largest slice's, so a group of equal slices wastes no blocks).
 int stats_grid(const Geometry &g) { return stats_blocks(g); }
 
-cudaError_t launch_stats_batch(const SliceCtx *ctx, int n, int blocks, int dense, int tc_mode, cudaStream_t st)
+cudaError_t launch_stats_batch(const Geometry &g, const SliceCtx *ctx, int n, int blocks, int dense, int tc_mode,
+                               cudaStream_t st)
 {
-    return launch_dep(k_stats_batch, dim3(blocks, n), dim3(256), 0, st, ctx, dense, tc_mode);
+    return with_stats_kernel(
+        g, [&](auto, auto many) { return launch_dep(many, dim3(blocks, n), dim3(256), 0, st, ctx, dense, tc_mode); });
 }
 
 // ranges, m: the largest of the slices' ranges and their common block size
@@ -898,10 +960,12 @@ cudaError_t launch_compact_seed_batch(const SliceCtx *ctx, int n, int ranges, in
     });
 }
 
-cudaError_t launch_rows_batch(const SliceCtx *ctx, int n, int blocks, cudaStream_t st)
+// g: the geometry of the group's slices (range size and bit depth are
+// common to all slices of a batch)
+cudaError_t launch_rows_batch(const Geometry &g, const SliceCtx *ctx, int n, int blocks, cudaStream_t st)
 {
-    const int x = std::max(1, std::min(blocks, kRowsBlocksPerSm * prep_sms() / std::max(1, n)));
-    return launch_dep(k_rows_batch, dim3(x, n), dim3(256), 0, st, ctx);
+    const int x = std::max(1, std::min(blocks, rows_blocks_per_sm(g.ln) * prep_sms() / std::max(1, n)));
+    return with_rows_kernel(g, [&](auto, auto many) { return launch_dep(many, dim3(x, n), dim3(256), 0, st, ctx); });
 }
 
 

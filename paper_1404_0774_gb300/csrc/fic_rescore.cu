@@ -357,6 +357,12 @@ __host__ __device__ inline int *fallback_done(const Geometry &g, void *partial)
 __device__ __forceinline__ unsigned long long hi64(unsigned long long) { return 0ull; }
 __device__ __forceinline__ unsigned long long hi64(unsigned __int128 v) { return (unsigned long long)(v >> 64); }
 
+// Winner words the re-score leaves for ranges whose winner an exact scan
+// decides (never a resolved winner: those are index | 2^31 with index < 2^31 - 8).
+constexpr uint32_t kWinScan = 0xffffffffu;   // queued for the full exact scan
+constexpr uint32_t kWinLists = 0xfffffffeu;  // lists queued for exact re-scans
+__device__ __forceinline__ bool win_pending(uint32_t w) { return w >= kWinLists; }
+
 constexpr int kRescoreWarps = 4;
 constexpr int kRescoreEnt = 16;  // list entries per lane: up to 512 per range
 // Shared memory of a re-score warp: the symmetry-permuted range pixels
@@ -421,7 +427,7 @@ __device__ __forceinline__ void rescore_range(const Geometry &g, const EpiConst 
     }
     if (ib == 0xffffffffu || exact_scan) {  // no candidate was listed (or asked): exact scan
         if (lane == 0) {
-            winner[r] = 0xffffffffu;
+            winner[r] = kWinScan;
             fb_list[atomicAdd(fb_count, 1)] = r;
         }
         return;
@@ -527,7 +533,7 @@ __device__ __forceinline__ void rescore_range(const Geometry &g, const EpiConst 
     if (lane == 0) {
         sb.cert[r] = Partial{(unsigned long long)best_e, hi64(best_e), best_i, 0};
         sb.pending[r] = nfail;
-        winner[r] = best_i;  // provisional: the last list scan replaces it
+        winner[r] = kWinLists;  // the last list scan writes the winner
     }
     while (failing) {
         const int q = __ffs(failing) - 1;
@@ -613,6 +619,63 @@ __global__ void __launch_bounds__(32 * kRescoreWarps, 4)
 
 
 
+// The map of range r from its winner word wj (candidate index, bit 31: the
+// winner came from an exact scan) and the exact statistics of the pair: codes
+// decided as fp64_codes decides them (the FP32 shortcut where it provably
+// agrees), the eq 8 residual exact in integers and rounded once to FP64.
+__device__ __forceinline__ void write_map(const Geometry &g, const Stats &st, int r, uint32_t wj, const int *err,
+                                          fic_map *maps)
+{
+    uint32_t ij = wj & 0x7fffffffu;
+    if (ij >= (uint32_t)g.N) ij = 0;  // unreachable: every range has a winner
+    int c, e;
+    float sf, of;
+    if (fast_codes(g, st, c, e)) {
+        sf = s_hat_f(g, c);
+        of = o_hat_f(g, e);
+    } else {  // next to a rounding boundary: the FP64 sequence decides
+        double sh, oh;
+        fp64_codes(g, st, c, e, sh, oh);
+        sf = (float)sh;
+        of = (float)oh;
+    }
+    const double invD2 = 1.0 / ((double)(4 * g.Ls * g.Lo) * (double)(4 * g.Ls * g.Lo));
+    fic_map mp;
+    mp.range_idx = (uint32_t)r;
+    mp.domain_idx = ij >> 3;
+    mp.iso = ij & 7;
+    mp.s_code = c;
+    mp.o_code = e;
+    mp.s = sf;
+    mp.o = of;
+    mp.info = ((wj & 0x80000000u) ? FIC_MAP_FALLBACK : 0u) | (*err ? FIC_MAP_ERROR : 0u);
+    mp.err = u128_to_double((unsigned __int128)exact_err<true>(g, st, c, e)) * invD2;
+    maps[r] = mp;
+}
+
+// The map of one range whose winner an exact scan has just decided, by the
+// calling warp (exact cross term over the lanes, the rest on lane 0).
+__device__ void finalize_range_warp(const Geometry &g, const RangeInfo *ri, const DomainInfo *di,
+                                    const uint16_t *bblk, const uint16_t *qblk, int r, uint32_t wj, const int *err,
+                                    fic_map *maps)
+{
+    const int lane = threadIdx.x & 31;
+    uint32_t idx = wj & 0x7fffffffu;
+    if (idx >= (uint32_t)g.N) idx = 0;
+    const int d = idx >> 3;
+    const SymFlags sf = sym_flags(idx & 7, g.n);
+    long long X = 0;
+    for (int i = lane; i < g.m; i += 32)
+        X += (long long)qblk[(size_t)d * g.m + sym_src_index(sf, g.ln, i >> g.ln, i & (g.n - 1))] *
+             bblk[(size_t)r * g.m + i];
+    for (int off = 16; off > 0; off >>= 1) X += __shfl_xor_sync(0xffffffffu, X, off);
+    if (lane == 0) {
+        const RangeInfo rin = ri[r];
+        const DomainInfo dd = di[d];
+        write_map(g, Stats{dd.Sq, dd.Sqq, rin.Sb, rin.Sbb, X}, r, wj, err, maps);
+    }
+}
+
 // The range's pixels permuted for each symmetry, staged by the threads
 // first, first + step, ...: bk[k*(m+1) + j] is the range pixel that S_k places
 // over contracted-domain pixel j (the layout of stage_sym_pixels).
@@ -641,11 +704,12 @@ template <bool Wide>
 __device__ __forceinline__ void full_scans(const Geometry &g, const RangeInfo *ri, const DomainInfo *di,
                                            const uint16_t *bblk, const uint16_t *qblk, const int *fb_list,
                                            const int *fb_count, int nch, Partial *part, int *done, uint32_t *winner,
-                                           int first, int stride)
+                                           int first, int stride, const int *err, fic_map *maps)
 {
     __shared__ int bk_s[8 * (kMaxM + 1)];
     __shared__ Partial w_s[8];
     __shared__ int last_s;
+    __shared__ uint32_t fin_w;
     const int count = *fb_count;
     for (int item = first; item < count * nch; item += stride) {
         const int slot = item / nch, ch = item - slot * nch;
@@ -705,7 +769,12 @@ __device__ __forceinline__ void full_scans(const Geometry &g, const RangeInfo *r
                     }
                 }
                 winner[r] = bb.idx | 0x80000000u;  // high bit: resolved by the fallback
+                fin_w = bb.idx | 0x80000000u;
             }
+        }
+        if (maps) {  // the map of a range whose last chunk this was
+            __syncthreads();
+            if (last_s && threadIdx.x < 32) finalize_range_warp(g, ri, di, bblk, qblk, r, fin_w, err, maps);
         }
     }
 }
@@ -723,11 +792,13 @@ __device__ __forceinline__ void list_scans_block(const Geometry &g, const RangeI
                                            const uint16_t *bblk, const uint16_t *qblk, const int *counts,
                                            const int *dmap, int col_tile, int target, int max_split,
                                            int lists_per_split, int max_lists, const SpanBufs &sb, uint32_t *winner,
-                                           int first, int stride)
+                                           int first, int stride, const int *err, fic_map *maps)
 {
     typedef typename Exact<Wide>::U U;
     __shared__ int bk_s[8 * (kMaxM + 1)];
     __shared__ Partial w_s[8];
+    __shared__ int fin_s;
+    __shared__ uint32_t fin_w;
     const int count = *sb.count;
     const int ncol = 8 * counts[2];
     const int tiles = (ncol + col_tile - 1) / col_tile;
@@ -775,6 +846,7 @@ __device__ __forceinline__ void list_scans_block(const Geometry &g, const RangeI
             Partial *sp_r = sb.part + (size_t)r * max_lists;
             sp_r[l] = b;
             __threadfence();  // the partial is visible before the count says so
+            fin_s = 0;
             if (atomicSub(sb.pending + r, 1) == 1) {
                 __threadfence();
                 Partial bb = sb.cert[r];
@@ -791,7 +863,13 @@ __device__ __forceinline__ void list_scans_block(const Geometry &g, const RangeI
                     }
                 }
                 winner[r] = bb.idx | 0x80000000u;  // high bit: resolved by an exact scan
+                fin_s = 1;
+                fin_w = bb.idx | 0x80000000u;
             }
+        }
+        if (maps) {  // the map of a range whose last list this was
+            __syncthreads();
+            if (fin_s && threadIdx.x < 32) finalize_range_warp(g, ri, di, bblk, qblk, r, fin_w, err, maps);
         }
     }
 }
@@ -805,7 +883,7 @@ __device__ __forceinline__ void list_scans_warp(const Geometry &g, const RangeIn
                                            const uint16_t *bblk, const uint16_t *qblk, const int *counts,
                                            const int *dmap, int col_tile, int target, int max_split,
                                            int lists_per_split, int max_lists, const SpanBufs &sb, uint32_t *winner,
-                                           int *bk, int first, int stride)
+                                           int *bk, int first, int stride, const int *err, fic_map *maps)
 {
     typedef typename Exact<Wide>::U U;
     const int lane = threadIdx.x & 31;
@@ -843,6 +921,7 @@ __device__ __forceinline__ void list_scans_warp(const Geometry &g, const RangeIn
             }
         }
         warp_argmin(best_e, best_i);
+        uint32_t fin_w = 0;  // lane 0: the winner when this was the range's last list
         if (lane == 0) {
             Partial *sp_r = sb.part + (size_t)r * max_lists;
             sp_r[l] = Partial{(unsigned long long)best_e, hi64(best_e), best_i, 0};
@@ -863,107 +942,11 @@ __device__ __forceinline__ void list_scans_warp(const Geometry &g, const RangeIn
                     }
                 }
                 winner[r] = bb.idx | 0x80000000u;  // high bit: resolved by an exact scan
+                fin_w = bb.idx | 0x80000000u;
             }
         }
-    }
-}
-
-// Shared memory of the list scans: 8 (m+1) ints per warp of a 256-thread block.
-__host__ __device__ __forceinline__ size_t list_scan_smem(int m) { return sizeof(int) * 8 * 8 * (size_t)(m + 1); }
-
-// One launch for both exact scans (persistent blocks; usually there is no
-// work and every block returns at once).
-template <bool Wide>
-__global__ void __launch_bounds__(256) k_exact_scans(Geometry g, const RangeInfo *ri, const DomainInfo *di,
-                                                     const uint16_t *bblk, const uint16_t *qblk, const int *fb_list,
-                                                     const int *fb_count, int nch, Partial *part, int *done,
-                                                     const int *counts, const int *dmap, int col_tile, int target,
-                                                     int max_split, int lists_per_split, int max_lists, SpanBufs sb,
-                                                     uint32_t *winner)
-{
-    extern __shared__ int scan_sm[];  // [warps][8 (m+1)]
-    grid_dep_sync();
-    full_scans<Wide>(g, ri, di, bblk, qblk, fb_list, fb_count, nch, part, done, winner, blockIdx.x, gridDim.x);
-    const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    if (*sb.count > 2 * (int)gridDim.x)  // grid-uniform
-        list_scans_warp<Wide>(g, ri, di, bblk, qblk, counts, dmap, col_tile, target, max_split, lists_per_split,
-                              max_lists, sb, winner, scan_sm + warp * 8 * (g.m + 1), blockIdx.x * nw + warp,
-                              gridDim.x * nw);
-    else
-        list_scans_block<Wide>(g, ri, di, bblk, qblk, counts, dmap, col_tile, target, max_split, lists_per_split,
-                               max_lists, sb, winner, blockIdx.x, gridDim.x);
-}
-
-// Batched: the work items of all slices' queues form one sequence (the
-// queue lengths of every slice are read at once, then prefix-summed), spread
-// over the persistent blocks like a single queue.
-template <bool Wide>
-__global__ void __launch_bounds__(256) k_exact_scans_batch(const SliceCtx *__restrict__ ctx, int n,
-                                                           int lists_per_split, int col_tile)
-{
-    __shared__ int fi_s[kMaxBatch + 1], li_s[kMaxBatch + 1];  // item prefixes: full scans, list scans
-    extern __shared__ int scan_sm[];                          // [warps][8 (m+1)]
-    grid_dep_sync();
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        const SliceCtx &c = ctx[i];
-        const bool mine = c.g.wide == Wide;
-        fi_s[i + 1] = mine ? c.b.fb_count[0] * fallback_chunks(c.g) : 0;
-        li_s[i + 1] = mine ? c.b.fb_count[2] : 0;
-    }
-    __syncthreads();
-    if (threadIdx.x < 32) {  // inclusive scans, 32 slices at a time
-        const int lane = threadIdx.x;
-        int cf = 0, cl = 0;
-        for (int i0 = 0; i0 < n; i0 += 32) {
-            const int i = i0 + lane;
-            int vf = i < n ? fi_s[i + 1] : 0, vl = i < n ? li_s[i + 1] : 0;
-            for (int o = 1; o < 32; o <<= 1) {
-                const int yf = __shfl_up_sync(0xffffffffu, vf, o), yl = __shfl_up_sync(0xffffffffu, vl, o);
-                if (lane >= o) {
-                    vf += yf;
-                    vl += yl;
-                }
-            }
-            if (i < n) {
-                fi_s[i + 1] = cf + vf;
-                li_s[i + 1] = cl + vl;
-            }
-            cf += __shfl_sync(0xffffffffu, vf, 31);
-            cl += __shfl_sync(0xffffffffu, vl, 31);
-        }
-        if (lane == 0) fi_s[0] = li_s[0] = 0;
-    }
-    __syncthreads();
-    // full scans: block items b, b + G, ... of the global sequence
-    const int b = blockIdx.x, G = gridDim.x;
-    for (int s = 0; s < n; ++s) {
-        const int nf = fi_s[s + 1] - fi_s[s];
-        const int ff = ((b - fi_s[s]) % G + G) % G;  // this block's first item of the slice
-        if (ff >= nf) continue;                      // block-uniform
-        const SliceCtx &c = ctx[s];
-        const EncBufs &e = c.b;
-        full_scans<Wide>(c.g, e.ri, e.di, e.bblk, e.qblk, e.fb_list, e.fb_count, fallback_chunks(c.g),
-                         reinterpret_cast<Partial *>(e.partial), fallback_done(c.g, e.partial), e.winner, ff, G);
-    }
-    // list scans: one warp per item (warp items w, w + W, ... of the global
-    // sequence) when the queues are long, else one block per item
-    const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const bool by_warp = li_s[n] > 2 * G;  // grid-uniform
-    const int w = by_warp ? b * nw + warp : b, W = by_warp ? G * nw : G;
-    for (int s = 0; s < n; ++s) {
-        const int nl = li_s[s + 1] - li_s[s];
-        const int fl = ((w - li_s[s]) % W + W) % W;  // this warp's (block's) first item of the slice
-        if (fl >= nl) continue;                      // warp- (block-) uniform
-        const SliceCtx &c = ctx[s];
-        const EncBufs &e = c.b;
-        const SpanBufs sb = span_bufs(c.g, c.n_lists, e.span, e.fb_count + 2);
-        if (by_warp)
-            list_scans_warp<Wide>(c.g, e.ri, e.di, e.bblk, e.qblk, e.cb.counts, e.cb.dmap, col_tile, c.target,
-                                  c.n_split, lists_per_split, c.n_lists, sb, e.winner, scan_sm + warp * 8 * (c.g.m + 1),
-                                  fl, W);
-        else
-            list_scans_block<Wide>(c.g, e.ri, e.di, e.bblk, e.qblk, e.cb.counts, e.cb.dmap, col_tile, c.target,
-                                   c.n_split, lists_per_split, c.n_lists, sb, e.winner, fl, W);
+        fin_w = __shfl_sync(0xffffffffu, fin_w, 0);
+        if (maps && fin_w != 0) finalize_range_warp(g, ri, di, bblk, qblk, r, fin_w, err, maps);
     }
 }
 
@@ -1047,41 +1030,124 @@ __device__ __forceinline__ void finalize_block(const Geometry &g, const RangeInf
     long long X = 0;
 #pragma unroll
     for (int w = 0; w < kFinWarps; ++w) X += x_s[w][jr];
-    Stats st{st_s[0][jr], st_s[1][jr], st_s[2][jr], st_s[3][jr], X};
     const uint32_t wj = w_s[jr];
-    uint32_t ij = wj & 0x7fffffffu;
-    if (ij >= (uint32_t)g.N) ij = 0;
-    int c, e;
-    float sf, of;
-    if (fast_codes(g, st, c, e)) {
-        sf = s_hat_f(g, c);
-        of = o_hat_f(g, e);
-    } else {  // next to a rounding boundary: the FP64 sequence decides
-        double sh, oh;
-        fp64_codes(g, st, c, e, sh, oh);
-        sf = (float)sh;
-        of = (float)oh;
-    }
-    const double invD2 = 1.0 / ((double)(4 * g.Ls * g.Lo) * (double)(4 * g.Ls * g.Lo));
-    fic_map mp;
-    mp.range_idx = (uint32_t)(r0 + jr);
-    mp.domain_idx = ij >> 3;
-    mp.iso = ij & 7;
-    mp.s_code = c;
-    mp.o_code = e;
-    mp.s = sf;
-    mp.o = of;
-    mp.info = ((wj & 0x80000000u) ? FIC_MAP_FALLBACK : 0u) | (*err ? FIC_MAP_ERROR : 0u);
-    mp.err = u128_to_double((unsigned __int128)exact_err<true>(g, st, c, e)) * invD2;
-    maps[r0 + jr] = mp;
+    if (win_pending(wj)) return;  // an exact scan decides it (and writes the map)
+    write_map(g, Stats{st_s[0][jr], st_s[1][jr], st_s[2][jr], st_s[3][jr], X}, r0 + jr, wj, err, maps);
 }
 
-__global__ void __launch_bounds__(32 * kFinWarps) k_finalize(Geometry g, const RangeInfo *ri, const DomainInfo *di,
-                                                             const uint16_t *bblk, const uint16_t *qblk,
-                                                             const uint32_t *winner, const int *err, fic_map *maps)
+// Shared memory of the list scans: 8 (m+1) ints per warp.
+__host__ __device__ __forceinline__ size_t list_scan_smem(int m, int warps)
 {
+    return sizeof(int) * 8 * (size_t)warps * (size_t)(m + 1);
+}
+
+// The exact scans and the map output in one launch (persistent blocks of
+// kFinWarps warps).  Each block first writes the maps of its groups of 32
+// ranges whose winner the re-score settled, then takes exact-scan work items
+// (usually there are none); the item that completes a range's scans writes
+// its map.  A range's map is thus written once its winner is final, by
+// whichever side sees it final (both write the same map).
+template <bool Wide>
+__global__ void __launch_bounds__(32 * kFinWarps) k_scans_finalize(Geometry g, const RangeInfo *ri,
+                                                                   const DomainInfo *di, const uint16_t *bblk,
+                                                                   const uint16_t *qblk, const int *fb_list,
+                                                                   const int *fb_count, int nch, Partial *part,
+                                                                   int *done, const int *counts, const int *dmap,
+                                                                   int col_tile, int target, int max_split,
+                                                                   int lists_per_split, int max_lists, SpanBufs sb,
+                                                                   uint32_t *winner, const int *err, fic_map *maps)
+{
+    extern __shared__ int scan_sm[];  // [warps][8 (m+1)]
     grid_dep_sync();
-    finalize_block(g, ri, di, bblk, qblk, winner, err, maps, blockIdx.x);
+    const int groups = (g.R + kFinRanges - 1) / kFinRanges;
+    for (int gb = blockIdx.x; gb < groups; gb += gridDim.x) {
+        finalize_block(g, ri, di, bblk, qblk, winner, err, maps, gb);
+        __syncthreads();  // the block's staging is reused by its next group
+    }
+    full_scans<Wide>(g, ri, di, bblk, qblk, fb_list, fb_count, nch, part, done, winner, blockIdx.x, gridDim.x, err,
+                     maps);
+    const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (*sb.count > 2 * (int)gridDim.x)  // grid-uniform
+        list_scans_warp<Wide>(g, ri, di, bblk, qblk, counts, dmap, col_tile, target, max_split, lists_per_split,
+                              max_lists, sb, winner, scan_sm + warp * 8 * (g.m + 1), blockIdx.x * nw + warp,
+                              gridDim.x * nw, err, maps);
+    else
+        list_scans_block<Wide>(g, ri, di, bblk, qblk, counts, dmap, col_tile, target, max_split, lists_per_split,
+                               max_lists, sb, winner, blockIdx.x, gridDim.x, err, maps);
+}
+
+// Batched: the work items of all slices' queues form one sequence (the
+// queue lengths of every slice are read at once, then prefix-summed), spread
+// over the persistent blocks like a single queue.
+template <bool Wide>
+__global__ void __launch_bounds__(256) k_exact_scans_batch(const SliceCtx *__restrict__ ctx, int n,
+                                                           int lists_per_split, int col_tile)
+{
+    __shared__ int fi_s[kMaxBatch + 1], li_s[kMaxBatch + 1];  // item prefixes: full scans, list scans
+    extern __shared__ int scan_sm[];                          // [warps][8 (m+1)]
+    grid_dep_sync();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const SliceCtx &c = ctx[i];
+        const bool mine = c.g.wide == Wide;
+        fi_s[i + 1] = mine ? c.b.fb_count[0] * fallback_chunks(c.g) : 0;
+        li_s[i + 1] = mine ? c.b.fb_count[2] : 0;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {  // inclusive scans, 32 slices at a time
+        const int lane = threadIdx.x;
+        int cf = 0, cl = 0;
+        for (int i0 = 0; i0 < n; i0 += 32) {
+            const int i = i0 + lane;
+            int vf = i < n ? fi_s[i + 1] : 0, vl = i < n ? li_s[i + 1] : 0;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int yf = __shfl_up_sync(0xffffffffu, vf, o), yl = __shfl_up_sync(0xffffffffu, vl, o);
+                if (lane >= o) {
+                    vf += yf;
+                    vl += yl;
+                }
+            }
+            if (i < n) {
+                fi_s[i + 1] = cf + vf;
+                li_s[i + 1] = cl + vl;
+            }
+            cf += __shfl_sync(0xffffffffu, vf, 31);
+            cl += __shfl_sync(0xffffffffu, vl, 31);
+        }
+        if (lane == 0) fi_s[0] = li_s[0] = 0;
+    }
+    __syncthreads();
+    // full scans: block items b, b + G, ... of the global sequence
+    const int b = blockIdx.x, G = gridDim.x;
+    for (int s = 0; s < n; ++s) {
+        const int nf = fi_s[s + 1] - fi_s[s];
+        const int ff = ((b - fi_s[s]) % G + G) % G;  // this block's first item of the slice
+        if (ff >= nf) continue;                      // block-uniform
+        const SliceCtx &c = ctx[s];
+        const EncBufs &e = c.b;
+        full_scans<Wide>(c.g, e.ri, e.di, e.bblk, e.qblk, e.fb_list, e.fb_count, fallback_chunks(c.g),
+                         reinterpret_cast<Partial *>(e.partial), fallback_done(c.g, e.partial), e.winner, ff, G,
+                         nullptr, nullptr);
+    }
+    // list scans: one warp per item (warp items w, w + W, ... of the global
+    // sequence) when the queues are long, else one block per item
+    const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const bool by_warp = li_s[n] > 2 * G;  // grid-uniform
+    const int w = by_warp ? b * nw + warp : b, W = by_warp ? G * nw : G;
+    for (int s = 0; s < n; ++s) {
+        const int nl = li_s[s + 1] - li_s[s];
+        const int fl = ((w - li_s[s]) % W + W) % W;  // this warp's (block's) first item of the slice
+        if (fl >= nl) continue;                      // warp- (block-) uniform
+        const SliceCtx &c = ctx[s];
+        const EncBufs &e = c.b;
+        const SpanBufs sb = span_bufs(c.g, c.n_lists, e.span, e.fb_count + 2);
+        if (by_warp)
+            list_scans_warp<Wide>(c.g, e.ri, e.di, e.bblk, e.qblk, e.cb.counts, e.cb.dmap, col_tile, c.target,
+                                  c.n_split, lists_per_split, c.n_lists, sb, e.winner, scan_sm + warp * 8 * (c.g.m + 1),
+                                  fl, W, nullptr, nullptr);
+        else
+            list_scans_block<Wide>(c.g, e.ri, e.di, e.bblk, e.qblk, e.cb.counts, e.cb.dmap, col_tile, c.target,
+                                   c.n_split, lists_per_split, c.n_lists, sb, e.winner, fl, W, nullptr, nullptr);
+    }
 }
 
 __global__ void __launch_bounds__(32 * kFinWarps) k_finalize_batch(const SliceCtx *__restrict__ ctx)
@@ -1119,30 +1185,25 @@ size_t fallback_partial_bytes(const Geometry &g)
 }
 
 
-cudaError_t launch_exact_scans(const Geometry &g, const RangeInfo *ri, const DomainInfo *di, const uint16_t *bblk,
-                               const uint16_t *qblk, const int *fb_list, int *fb_count, void *partial,
-                               const int *counts, const int *dmap, int col_tile, int target, int max_split,
-                               int lists_per_split, int max_lists, void *span, uint32_t *winner, int n_sm,
-                               cudaStream_t st)
+cudaError_t launch_scans_finalize(const Geometry &g, const RangeInfo *ri, const DomainInfo *di, const uint16_t *bblk,
+                                  const uint16_t *qblk, const int *fb_list, int *fb_count, void *partial,
+                                  const int *counts, const int *dmap, int col_tile, int target, int max_split,
+                                  int lists_per_split, int max_lists, void *span, uint32_t *winner, const int *err,
+                                  fic_map *maps, int n_sm, cudaStream_t st)
 {
     const int nch = fallback_chunks(g);
     Partial *part = reinterpret_cast<Partial *>(partial);
     const SpanBufs sb = span_bufs(g, max_lists, span, fb_count + 2);
-    const size_t smem = list_scan_smem(g.m);
-    auto kern = g.wide ? k_exact_scans<true> : k_exact_scans<false>;
+    const size_t smem = list_scan_smem(g.m, kFinWarps);
+    auto kern = g.wide ? k_scans_finalize<true> : k_scans_finalize<false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    return launch_dep(kern, dim3(2 * n_sm), dim3(256), smem, st, g, ri, di, bblk, qblk, fb_list,
+    // resident at once (the scans' work items are taken by stride); at least
+    // one block per group of 32 ranges
+    const int blocks = std::max((g.R + kFinRanges - 1) / kFinRanges, 3 * n_sm);
+    return launch_dep(kern, dim3(blocks), dim3(32 * kFinWarps), smem, st, g, ri, di, bblk, qblk, fb_list,
                       (const int *)fb_count, nch, part, fallback_done(g, partial), counts, dmap, col_tile, target,
-                      max_split, lists_per_split, max_lists, sb, winner);
-}
-
-cudaError_t launch_finalize(const Geometry &g, const RangeInfo *ri, const DomainInfo *di,
-                            const uint16_t *bblk, const uint16_t *qblk, const uint32_t *winner,
-                            const int *err, fic_map *maps, cudaStream_t st)
-{
-    return launch_dep(k_finalize, dim3((g.R + kFinRanges - 1) / kFinRanges), dim3(32 * kFinWarps), 0, st, g, ri, di,
-                      bblk, qblk, winner, err, maps);
+                      max_split, lists_per_split, max_lists, sb, winner, err, maps);
 }
 
 // Batched re-score and exact scans of n slices (max_m: the pixels per range,
@@ -1160,7 +1221,7 @@ cudaError_t launch_rescore_batch(const SliceCtx *ctx, int n, int total_ranges, b
     if (any_wide && (e = launch_dep(k_rescore_batch<true>, dim3(blocks), dim3(32 * kRescoreWarps), smem, st, ctx, n,
                                     total_ranges, lists_per_split, col_tile, exact_scan)) != cudaSuccess)
         return e;
-    const size_t ssm = list_scan_smem(max_m);
+    const size_t ssm = list_scan_smem(max_m, 8);
     if ((e = cudaFuncSetAttribute(k_exact_scans_batch<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)ssm)) != cudaSuccess ||
         (e = cudaFuncSetAttribute(k_exact_scans_batch<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
