@@ -606,13 +606,14 @@ static cudaError_t with_rows_kernel(const Geometry &g, Launch &&launch)
 // S_k places over domain pixel j, so X(d, k) = sum_j q_d[j] * bk[k][j];
 // q2[p][slot] holds the contracted-domain pixels 2p, 2p+1 of the slot's
 // domain (lanes read consecutive words, the bk reads are broadcasts); 8 m
-// ints of bk and m/2 x 32 words of q2 per warp.  seed_pair (m <= 64): the
-// same with half a warp per range over 16 slots (3 x 3 + 7).  The loads of a
-// warp are issued together (one round trip after the keep flag).
+// ints of bk and m/2 x 32 words of q2 per warp.  seed_range (m <= 64): the
+// same over 16 slots (3 x 3 + 7), the warp's two halves taking four
+// symmetries each.  The loads of a warp are issued together (one round trip
+// after the keep flag).
 __host__ __device__ constexpr int seed_warps(int m) { return m <= 64 ? 16 : 8; }
-// Shared ints per seed warp: one range (m = 256: 8 m of bk, 16 m of q2) or
-// two (m <= 64, see seed_pair: 2 (8 m + 2) of bk, 16 m of q2).
-__host__ __device__ constexpr int seed_warp_ints(int m) { return m <= 64 ? 32 * m + 4 : 24 * m; }
+// Shared ints per seed warp: one range (m = 256: 8 m of bk, 16 m of q2;
+// m <= 64, see seed_range: 8 (m + 2) of bk, 8 m of q2).
+__host__ __device__ constexpr int seed_warp_ints(int m) { return m <= 64 ? 16 * m + 16 : 24 * m; }
 __host__ __device__ constexpr size_t seed_smem(int m) { return sizeof(int) * (size_t)seed_warps(m) * seed_warp_ints(m); }
 
 template <int PPL>  // range pixels per lane, at least m / 32
@@ -715,106 +716,100 @@ __device__ __forceinline__ void seed_warp(const Geometry &g, const EpiConst &ec,
     if (lane == 0 && best != 0x7fffffff) atomicMin(tbest + r, best);
 }
 
-// The seed of two ranges per warp (m <= 64), half a warp each: the same
-// scoring as seed_warp over 16 domain slots per range -- the 3 x 3 domains
-// around it and 7 spread over the image -- so that a warp does half the work
-// per range and the seeds of all ranges fit one wave of blocks.  bk holds the
-// two ranges' symmetry-permuted pixels (row 8 m + 2 apart, so that the two
-// halves' broadcast reads fall in different banks), q2 the slots' domain
-// pixel pairs as in seed_warp.  Cross terms sum in 32 bits: m <= 64 products
-// of at most 4P * P < 2^26 stay below 2^32.
-__device__ __forceinline__ void seed_pair(const Geometry &g, const EpiConst &ec, const RangeInfo *ri,
-                                          const DomainInfo *di, const float4 *dconst, const uint16_t *bblk,
-                                          const uint16_t *qblk, const int *rkeep, int *tbest, int rA, int rB,
-                                          int lane, int *bk, uint32_t *q2)
+// The seed of one range (m <= 64) by a whole warp: the same scoring as
+// seed_warp over 16 domain slots -- the 3 x 3 domains around the range and 7
+// spread over the image -- with lane = (symmetry half h, slot sl): the lane
+// scores symmetries 4h .. 4h+3 of its slot's domain.  bk holds the range's
+// symmetry-permuted pixels (rows of m + 2 ints, so that the two halves'
+// broadcast reads fall in different banks), q2[p][slot] the slots' domain
+// pixel pairs (each slot row loaded by its two lanes, half each).  Cross
+// terms sum in 32 bits: m <= 64 products of at most 4P * P < 2^26 stay below
+// 2^32.
+__device__ __forceinline__ void seed_range(const Geometry &g, const EpiConst &ec, const RangeInfo *ri,
+                                           const DomainInfo *di, const float4 *dconst, const uint16_t *bblk,
+                                           const uint16_t *qblk, int *tbest, int r, int lane, int *bk, uint32_t *q2)
 {
-    const int hg = lane >> 4, sl = lane & 15;
-    const int r = hg ? rB : rA;
-    const bool live = r >= 0 && r < g.R && rkeep[r] != 0;
-    if (!__any_sync(0xffffffffu, live)) return;
-    __syncwarp();  // bk and q2 of the warp's previous pair are read
-    int d = 0;
-    if (live) {
-        if (sl < 9) {
-            const int ry = (r / g.nx) * g.n, rx = (r % g.nx) * g.n;
-            const int v0 = min(max((ry - g.n / 2) / g.t, 0), g.V - 1);
-            const int u0 = min(max((rx - g.n / 2) / g.t, 0), g.U - 1);
-            const int v = min(max(v0 + sl / 3 - 1, 0), g.V - 1);
-            const int u = min(max(u0 + sl % 3 - 1, 0), g.U - 1);
-            d = v * g.U + u;
-        } else {
-            d = (int)(((long long)r * 2654435761LL + (long long)(sl - 9) * 40503LL) % g.D);
-        }
+    const int h = lane >> 4, sl = lane & 15;
+    int d;
+    if (sl < 9) {
+        const int ry = (r / g.nx) * g.n, rx = (r % g.nx) * g.n;
+        const int v0 = min(max((ry - g.n / 2) / g.t, 0), g.V - 1);
+        const int u0 = min(max((rx - g.n / 2) / g.t, 0), g.U - 1);
+        const int v = min(max(v0 + sl / 3 - 1, 0), g.V - 1);
+        const int u = min(max(u0 + sl % 3 - 1, 0), g.U - 1);
+        d = v * g.U + u;
+    } else {
+        d = (int)(((long long)r * 2654435761LL + (long long)(sl - 9) * 40503LL) % g.D);
     }
     // every load issued together
-    int bv[4];
+    int bv[2];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const int i = sl + 16 * j;
-        bv[j] = live && i < g.m ? (int)bblk[(size_t)r * g.m + i] : 0;
+    for (int j = 0; j < 2; ++j) {
+        const int i = lane + 32 * j;
+        bv[j] = i < g.m ? (int)bblk[(size_t)r * g.m + i] : 0;
     }
     const uint4 *qrow = reinterpret_cast<const uint4 *>(qblk + (size_t)d * g.m);
-    const int nv = g.m >> 3;  // <= 8
-    uint4 qv[8];
+    const int nv = g.m >> 3;  // 16-byte vectors of a domain row, <= 8
+    uint4 qv[4];              // vectors 2 v + h of the slot's row
 #pragma unroll
-    for (int v = 0; v < 8; ++v) qv[v] = v < nv ? __ldg(qrow + v) : make_uint4(0, 0, 0, 0);
-    const RangeInfo rin = ri[live ? r : 0];
+    for (int v = 0; v < 4; ++v) qv[v] = 2 * v + h < nv ? __ldg(qrow + 2 * v + h) : make_uint4(0, 0, 0, 0);
+    const RangeInfo rin = ri[r];
     const DomainInfo dd = di[d];
     const float4 c4 = dconst[d];
-    int *bkh = bk + hg * (8 * g.m + 2);
+    const int bp = g.m + 2;  // bk row pitch (ints)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const int i = sl + 16 * j;
+    for (int j = 0; j < 2; ++j) {
+        const int i = lane + 32 * j;
         if (i < g.m) {
             const int y = i >> g.ln, x = i & (g.n - 1);
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
                 int sy, sx;
                 sym_src(k, g.n, y, x, sy, sx);
-                bkh[k * g.m + (sy << g.ln) + sx] = bv[j];
+                bk[k * bp + (sy << g.ln) + sx] = bv[j];
             }
         }
     }
 #pragma unroll
-    for (int v = 0; v < 8; ++v) {
-        if (v < nv) {
-            q2[(4 * v + 0) * 32 + lane] = qv[v].x;
-            q2[(4 * v + 1) * 32 + lane] = qv[v].y;
-            q2[(4 * v + 2) * 32 + lane] = qv[v].z;
-            q2[(4 * v + 3) * 32 + lane] = qv[v].w;
+    for (int v = 0; v < 4; ++v) {
+        const int vv = 2 * v + h;
+        if (vv < nv) {
+            q2[(4 * vv + 0) * 16 + sl] = qv[v].x;
+            q2[(4 * vv + 1) * 16 + sl] = qv[v].y;
+            q2[(4 * vv + 2) * 16 + sl] = qv[v].z;
+            q2[(4 * vv + 3) * 16 + sl] = qv[v].w;
         }
     }
     __syncwarp();
-    uint32_t X[8];
+    const int *bkh = bk + 4 * h * bp;
+    uint32_t X[4];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) X[k] = 0;
+    for (int k = 0; k < 4; ++k) X[k] = 0;
     for (int p = 0; p < (g.m >> 1); ++p) {
-        const uint32_t w = q2[p * 32 + lane];
+        const uint32_t w = q2[p * 16 + sl];  // the two halves of a slot read the same word
         const uint32_t qa = w & 0xffffu, qb = w >> 16;
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const int2 b2 = *reinterpret_cast<const int2 *>(bkh + k * g.m + 2 * p);
+        for (int k = 0; k < 4; ++k) {
+            const int2 b2 = *reinterpret_cast<const int2 *>(bkh + k * bp + 2 * p);
             X[k] += qa * (uint32_t)b2.x + qb * (uint32_t)b2.y;
         }
     }
+    const RangeEpi re = range_epi(rin, ec);
+    const long long sqsb = dd.Sq * rin.Sb;
     int best = 0x7fffffff;
-    if (live) {
-        const RangeEpi re = range_epi(rin, ec);
-        const long long sqsb = dd.Sq * rin.Sb;
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const long long num = (long long)g.m * (long long)X[k] - sqsb;  // exact
-            const float Xt = __ll2float_rn(num) * ec.invm;
-            float rho;
-            const float c = epi_code(Xt, c4.x, 0.5f, ec, rho);
-            if (fabsf(rho) > re.rho_lim) continue;
-            const float ostar = (re.Sb - c * c4.w * ec.inv4ls) * ec.invm;
-            if (!(ostar < ec.pmax)) continue;
-            best = min(best, f2ord(epi_key(Xt, -0.0f, c, re.zb, c4, ec)));
-        }
+    for (int k = 0; k < 4; ++k) {
+        const long long num = (long long)g.m * (long long)X[k] - sqsb;  // exact
+        const float Xt = __ll2float_rn(num) * ec.invm;
+        float rho;
+        const float c = epi_code(Xt, c4.x, 0.5f, ec, rho);
+        if (fabsf(rho) > re.rho_lim) continue;
+        const float ostar = (re.Sb - c * c4.w * ec.inv4ls) * ec.invm;
+        if (!(ostar < ec.pmax)) continue;
+        best = min(best, f2ord(epi_key(Xt, -0.0f, c, re.zb, c4, ec)));
     }
-    for (int off = 8; off > 0; off >>= 1) best = min(best, __shfl_xor_sync(0xffffffffu, best, off));
-    if (sl == 0 && live && best != 0x7fffffff) atomicMin(tbest + r, best);
+    best = __reduce_min_sync(0xffffffffu, best);
+    if (lane == 0 && best != 0x7fffffff) atomicMin(tbest + r, best);
 }
 
 // Compaction (blocks 0 and 1: ranges, domains) and, when seed != 0, the
@@ -837,12 +832,18 @@ __device__ __forceinline__ void compact_seed_block(const Geometry &g, const EpiC
     // (which cluster in the image) spread evenly over the blocks
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int *bk = seed_sm + warp * seed_warp_ints(g.m);
-    if (T == 512) {  // m <= 64: two ranges per warp
-        const int per = 2 * (T / 32), nb = (g.R + per - 1) / per;
-        if (bx - 2 >= nb) return;
-        const int rA = (2 * warp) * nb + (bx - 2), rB = rA + nb;
-        seed_pair(g, ec, ri, di, dconst, bblk, qblk, rkeep, tbest, rA, rB, lane, bk,
-                  reinterpret_cast<uint32_t *>(bk + 2 * (8 * g.m + 2)));
+    if (T == 512) {  // m <= 64: a warp per screened range among the block's 16
+        // block b takes ranges b, b + nb, ..., b + 15 nb; its warps take the
+        // screened ones in order (every warp reads the 16 keep flags)
+        const int nb = (g.R + 15) / 16, b = bx - 2;
+        if (b >= nb) return;
+        const int rl = lane < 16 ? lane * nb + b : g.R;
+        unsigned kept = __ballot_sync(0xffffffffu, rl < g.R && rkeep[rl] != 0);
+        if (warp >= __popc(kept)) return;  // warp-uniform
+        for (int t = 0; t < warp; ++t) kept &= kept - 1;
+        const int r = (__ffs(kept) - 1) * nb + b;
+        seed_range(g, ec, ri, di, dconst, bblk, qblk, tbest, r, lane, bk,
+                   reinterpret_cast<uint32_t *>(bk + 8 * (g.m + 2)));
     } else {
         const int nb = (g.R + T / 32 - 1) / (T / 32);
         if (bx - 2 >= nb) return;
@@ -854,7 +855,7 @@ __device__ __forceinline__ void compact_seed_block(const Geometry &g, const EpiC
 }
 
 template <int T>
-__global__ void __launch_bounds__(T, 1) k_compact_seed(Geometry g, EpiConst ec, int seed, const RangeInfo *ri,
+__global__ void __launch_bounds__(T, T == 512 ? 2 : 1) k_compact_seed(Geometry g, EpiConst ec, int seed, const RangeInfo *ri,
                                                     const DomainInfo *di, const float4 *dconst,
                                                     const uint16_t *bblk, const uint16_t *qblk, const int *rkeep,
                                                     const int *dkeep, int *act, int *dact, int *counts, int *tbest)
@@ -865,7 +866,7 @@ __global__ void __launch_bounds__(T, 1) k_compact_seed(Geometry g, EpiConst ec, 
 }
 
 template <int T>
-__global__ void __launch_bounds__(T, 1) k_compact_seed_batch(const SliceCtx *__restrict__ ctx)
+__global__ void __launch_bounds__(T, T == 512 ? 2 : 1) k_compact_seed_batch(const SliceCtx *__restrict__ ctx)
 {
     grid_dep_sync();
     const SliceCtx &c = ctx[blockIdx.y];
@@ -924,7 +925,7 @@ cudaError_t launch_prep(const Geometry &g, const void *img, const EpiConst &ec, 
     if (e != cudaSuccess) return e;
     const int sw = seed_warps(g.m);
     e = with_seed_shape(g.m, [&](auto one, auto, int threads) {
-        const int per = g.m <= 64 ? 2 * sw : sw;  // ranges per seed block
+        const int per = sw;  // ranges per seed block
         return launch_dep(one, dim3(2 + (seed ? (g.R + per - 1) / per : 0)), dim3(threads), seed ? seed_smem(g.m) : 0,
                           st, g, ec, seed, (const RangeInfo *)ri, (const DomainInfo *)di, (const float4 *)dconst,
                           (const uint16_t *)bblk, (const uint16_t *)qblk, (const int *)cb.rkeep,
@@ -955,7 +956,7 @@ cudaError_t launch_compact_seed_batch(const SliceCtx *ctx, int n, int ranges, in
 {
     const int sw = seed_warps(m);
     return with_seed_shape(m, [&](auto, auto many, int threads) {
-        const int per = m <= 64 ? 2 * sw : sw;  // ranges per seed block
+        const int per = sw;  // ranges per seed block
         return launch_dep(many, dim3(2 + (ranges + per - 1) / per, n), dim3(threads), seed_smem(m), st, ctx);
     });
 }
