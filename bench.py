@@ -462,9 +462,11 @@ def run_quadtree(args):
             "e2e": {"value": job_rate(ws, args.steps, comps, e2e_t), "unit": "comparisons/s",
                     "h2d_bytes_per_step": N_PIX * N_PIX * 2, "d2h_bytes_per_step": int(n_leaves) * 56,
                     "timing": "host wall clock (the call waits for its stream)"},
-            # per level the six encode kernels and the split test; then the
-            # leaf count and the leaf gather
-            "gpu_launches": args.steps * (7 * len(per_level) + 2), "clocks": clocks, "roofline": roof}
+            # per level the encode kernels (five; six for 16x16 ranges, whose
+            # compaction and seed keep a launch of their own) and the split
+            # test; then the leaf count and the leaf gather
+            "gpu_launches": args.steps * (sum((7 if d["range_size"] == 16 else 6) for d in per_level) + 2),
+            "clocks": clocks, "roofline": roof}
     if rank == 0:
         if ws == 1 and not args.no_cpu_baseline:
             import oracle
@@ -808,7 +810,7 @@ def main():
     for _ in range(max(3, args.warmup)):
         step()
     torch.cuda.synchronize()
-    launches_per_step = 6  # statistics, compaction + seed, operand rows, search, re-score, exact scans + output
+    launches_per_step = 5  # statistics, compaction + operand rows + seed, search, re-score, exact scans + output
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     if ws > 1:

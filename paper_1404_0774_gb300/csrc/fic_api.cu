@@ -211,7 +211,7 @@ int lists_per_split(int search)
 
 struct EncLayout {
     size_t img, ri, di, dconst, bblk, qblk, rs32, cb32, ra16, cb16, lists, winner, fb_list, fb_count, span,
-        tbest, partial, maps, rkeep, dkeep, act, dact, counts, dconst_c, dmap, total;
+        tbest, partial, maps, rkeep, dkeep, act, dact, counts, dconst_c, dmap, bmask, bcount, total;
 };
 
 // tc_operands = false: the tensor-core operand rows live elsewhere (a
@@ -252,6 +252,8 @@ EncLayout enc_layout(const Geometry &g, int search, int n_lists, bool tc_operand
     L.counts = take(sizeof(int) * 4);
     L.dconst_c = take(sizeof(float4) * g.D);
     L.dmap = take(sizeof(int) * g.D);
+    L.bmask = take(sizeof(uint4) * stats_grid(g));
+    L.bcount = take(sizeof(int) * stats_grid(g));
     L.total = o;
     return L;
 }
@@ -371,6 +373,8 @@ EncBufs enc_bufs(const EncLayout &L, char *ws)
     b.cb.counts = reinterpret_cast<int *>(ws + L.counts);
     b.cb.dconst_c = reinterpret_cast<float4 *>(ws + L.dconst_c);
     b.cb.dmap = reinterpret_cast<int *>(ws + L.dmap);
+    b.cb.bmask = reinterpret_cast<uint4 *>(ws + L.bmask);
+    b.cb.bcount = reinterpret_cast<int *>(ws + L.bcount);
     return b;
 }
 

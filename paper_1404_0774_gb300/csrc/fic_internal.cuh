@@ -478,6 +478,8 @@ struct CompactBufs {
     int *counts;          // 4 ints, see above
     float4 *dconst_c;     // epilogue constants of the kept domains, in order
     int *dmap;            // kept domain j -> original domain id
+    uint4 *bmask;         // per statistics block: keep flags of its items (bit i of word i / 32)
+    int *bcount;          // per statistics block: kept items
 };
 // Device buffers of one encode (sub-buffers of its workspace).
 struct EncBufs {

@@ -39,7 +39,7 @@ __device__ __forceinline__ T group_sum(T v, int G)
 // all when dense).  `valid` is false for the lanes of a group past the last
 // range: they take part in the reductions only.
 template <int LN, bool B8>
-__device__ __forceinline__ void range_stats(const Geometry &g, const EpiConst &ec, const void *img, int dense,
+__device__ __forceinline__ bool range_stats(const Geometry &g, const EpiConst &ec, const void *img, int dense,
                                             int tc_mode, const int *active, int r, bool valid, int li, int G,
                                             RangeInfo *ri, uint16_t *bblk, int *tbest, int *rkeep)
 {
@@ -71,7 +71,7 @@ __device__ __forceinline__ void range_stats(const Geometry &g, const EpiConst &e
         bmin = min(bmin, __shfl_xor_sync(0xffffffffu, bmin, off));
         bmax = max(bmax, __shfl_xor_sync(0xffffffffu, bmax, off));
     }
-    if (!valid || li != 0) return;
+    if (!valid || li != 0) return false;
     // centre: nearest integer to the mean, kept within 2048 of every pixel so
     // that b - c_r is an exact FP16 integer
     long long cr = (2 * Sb + m) >> (2 * LN + 1);  // m = 2^(2 ln), Sb >= 0
@@ -130,7 +130,9 @@ __device__ __forceinline__ void range_stats(const Geometry &g, const EpiConst &e
     info.pad = 0;
     ri[r] = info;
     tbest[r] = 0x7f800000;  // +inf in the ordered-integer encoding of floats
-    rkeep[r] = (!active || active[r]) && (dense || !info.shadow);
+    const bool keep = (!active || active[r]) && (dense || !info.shadow);
+    rkeep[r] = keep;
+    return keep;
 }
 
 
@@ -139,7 +141,7 @@ __device__ __forceinline__ void range_stats(const Geometry &g, const EpiConst &e
 // centre, the epilogue column constants, and the keep flag (every domain but
 // flat ones, den = 0, or all when dense).
 template <int LN, bool B8>
-__device__ __forceinline__ void domain_stats(const Geometry &g, const void *img, int dense, int d, bool valid,
+__device__ __forceinline__ bool domain_stats(const Geometry &g, const void *img, int dense, int d, bool valid,
                                              int li, int G, DomainInfo *di, float4 *dconst, uint16_t *qblk,
                                              int *dkeep)
 {
@@ -175,7 +177,7 @@ __device__ __forceinline__ void domain_stats(const Geometry &g, const void *img,
     }
     Sq = group_sum(Sq, G);
     Sqq = group_sum(Sqq, G);
-    if (!valid || li != 0) return;
+    if (!valid || li != 0) return false;
     const long long cd = (2 * Sq + m) >> (2 * LN + 1);  // m = 2^(2 ln), Sq >= 0
     const long long den = (long long)m * Sqq - Sq * Sq;
     DomainInfo info;
@@ -194,7 +196,9 @@ __device__ __forceinline__ void domain_stats(const Geometry &g, const void *img,
     c4.z = denf / (8.0f * m * g.Ls);
     c4.w = (float)Sq;
     dconst[d] = c4;
-    dkeep[d] = dense || den != 0;
+    const bool keep = dense || den != 0;
+    dkeep[d] = keep;
+    return keep;
 }
 
 // Statistics of every range (the first stats_range_blocks blocks) and every
@@ -203,19 +207,41 @@ template <int LN, bool B8>
 __device__ __forceinline__ void stats_block(const Geometry &g, const EpiConst &ec, const void *img, int dense,
                                             int tc_mode, const int *active, RangeInfo *ri, uint16_t *bblk,
                                             int *tbest, DomainInfo *di, float4 *dconst, uint16_t *qblk, int *rkeep,
-                                            int *dkeep, int *zero4, int bx)
+                                            int *dkeep, int *zero4, uint4 *bmask, int *bcount, int bx)
 {
     if (bx == 0 && threadIdx.x < 4) zero4[threadIdx.x] = 0;  // exact-scan queue counters
     constexpr int G = stats_group(1 << (2 * LN)), per_block = stats_items(1 << (2 * LN));
+    static_assert(per_block <= 128, "the keep mask of a block is four words");
     const int rbs = stats_range_blocks(g);
     const int li = threadIdx.x & (G - 1);
     const int item = threadIdx.x / G;  // (warp, group) in order
+    bool keep;
     if (bx < rbs) {
         const int r = bx * per_block + item;
-        range_stats<LN, B8>(g, ec, img, dense, tc_mode, active, r, r < g.R, li, G, ri, bblk, tbest, rkeep);
+        keep = range_stats<LN, B8>(g, ec, img, dense, tc_mode, active, r, r < g.R, li, G, ri, bblk, tbest, rkeep);
     } else {
         const int d = (bx - rbs) * per_block + item;
-        domain_stats<LN, B8>(g, img, dense, d, d < g.D, li, G, di, dconst, qblk, dkeep);
+        keep = domain_stats<LN, B8>(g, img, dense, d, d < g.D, li, G, di, dconst, qblk, dkeep);
+    }
+    if (!bmask) return;
+    // the block's keep flags in item order (bit i of word i / 32) and their
+    // count, for the compaction that follows without a scan launch
+    __shared__ int keep_s[per_block];
+    if (li == 0) keep_s[item] = keep ? 1 : 0;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        uint32_t w[4];
+        int total = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int it = 32 * k + threadIdx.x;
+            w[k] = __ballot_sync(0xffffffffu, it < per_block && keep_s[it] != 0);
+            total += __popc(w[k]);
+        }
+        if (threadIdx.x == 0) {
+            bmask[bx] = make_uint4(w[0], w[1], w[2], w[3]);
+            bcount[bx] = total;
+        }
     }
 }
 
@@ -223,11 +249,11 @@ template <int LN, bool B8>
 __global__ void __launch_bounds__(256) k_stats(Geometry g, EpiConst ec, const void *img, int dense, int tc_mode,
                                                const int *active, RangeInfo *ri, uint16_t *bblk, int *tbest,
                                                DomainInfo *di, float4 *dconst, uint16_t *qblk, int *rkeep,
-                                               int *dkeep, int *zero4)
+                                               int *dkeep, int *zero4, uint4 *bmask, int *bcount)
 {
     grid_dep_sync();
     stats_block<LN, B8>(g, ec, img, dense, tc_mode, active, ri, bblk, tbest, di, dconst, qblk, rkeep, dkeep, zero4,
-                        blockIdx.x);
+                        bmask, bcount, blockIdx.x);
 }
 
 // Batched: blockIdx.y = slice.
@@ -239,7 +265,7 @@ __global__ void __launch_bounds__(256) k_stats_batch(const SliceCtx *__restrict_
     if ((int)blockIdx.x >= stats_blocks(c.g)) return;
     const EncBufs &b = c.b;
     stats_block<LN, B8>(c.g, c.ec, c.img, dense, tc_mode, nullptr, b.ri, b.bblk, b.tbest, b.di, b.dconst, b.qblk,
-                b.cb.rkeep, b.cb.dkeep, b.fb_count, blockIdx.x);
+                        b.cb.rkeep, b.cb.dkeep, b.fb_count, nullptr, nullptr, blockIdx.x);
 }
 
 // The statistics kernels of a geometry (range size and 8-bit pixels are
@@ -876,6 +902,195 @@ __global__ void __launch_bounds__(T, T == 512 ? 2 : 1) k_compact_seed_batch(cons
                           cb.counts, b.tbest, blockIdx.x);
 }
 
+// ---------------------------------------------------------------------------
+// Compaction, operand rows and seeds in one launch (ranges of at most 8 x 8).
+// The statistics kernel left per block a keep mask and its count (block i of
+// the ranges covers items i * per .. i * per + per - 1, then the domains'
+// blocks).  Every block of this launch prefix-sums those counts itself, so
+// the j-th kept range (domain) is found from the sums by a binary search and
+// a bit count in its block's mask, and no launch is spent on the compaction:
+// the order is the original one, as a stable compaction gives.
+constexpr int kRsWarps = 16;             // warps per block (two blocks per SM)
+constexpr int kRsMaxStatBlocks = 8192;   // statistics blocks a block can scan
+
+__host__ __device__ constexpr int rows_seed_ints(int m, int nsb)
+{
+    return kRsWarps * seed_warp_ints(m) + nsb + 1 + 2 * kRsWarps + 2;
+}
+
+// Position of the t-th (from 0) set bit of x (t < popc(x)).
+__device__ __forceinline__ int nth_set_bit(uint32_t x, int t)
+{
+    int pos = 0;
+#pragma unroll
+    for (int sh = 16; sh > 0; sh >>= 1) {
+        const uint32_t lo = x & ((1u << sh) - 1u);
+        const int c = __popc(lo);
+        if (t >= c) {
+            t -= c;
+            x >>= sh;
+            pos += sh;
+        } else {
+            x = lo;
+        }
+    }
+    return pos;
+}
+
+// Item of rank j among the kept items of statistics blocks [lo, hi): E holds
+// the exclusive prefix sums of the blocks' counts (E[k] <= E[lo] + j <
+// E[hi]); per items a block.
+__device__ __forceinline__ int kept_item(const int *E, int lo, int hi, int j, const uint4 *bmask, int per)
+{
+    const int T = E[lo] + j;
+    int a = lo, b = hi - 1;  // last k in [lo, hi) with E[k] <= T
+    while (a < b) {
+        const int mid = (a + b + 1) >> 1;
+        if (E[mid] <= T) a = mid;
+        else b = mid - 1;
+    }
+    int t = T - E[a];
+    const uint4 mk = bmask[a];
+    const uint32_t w[4] = {mk.x, mk.y, mk.z, mk.w};
+    int base = (a - lo) * per;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int c = __popc(w[k]);
+        if (t < c) return base + nth_set_bit(w[k], t);
+        t -= c;
+        base += 32;
+    }
+    return -1;  // unreachable when the counts and masks agree
+}
+
+template <int LN, bool SPLIT>
+__global__ void __launch_bounds__(32 * kRsWarps, 2)
+    k_rows_seed(Geometry g, EpiConst ec, int seed, const RangeInfo *ri, const uint16_t *bblk, const DomainInfo *di,
+                const uint16_t *qblk, const float4 *dconst, const int *rkeep, const uint4 *bmask,
+                const int *bcount, int *tbest, int *act, int *dact, int *counts, float *rs32, __half *ra16,
+                float *cb32, __half *cb16, float4 *dconst_c, int *dmap)
+{
+    extern __shared__ __align__(16) int rs_sm[];
+    constexpr int m = 1 << (2 * LN);
+    constexpr int per = stats_items(m);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int rbs = stats_range_blocks(g), nsb = stats_blocks(g);
+    int *wsm = rs_sm + warp * seed_warp_ints(m);  // the warp's seed area, then its row staging
+    int *E = rs_sm + kRsWarps * seed_warp_ints(m);
+    int *wsum = E + nsb + 1;
+    int *first = wsum + 2 * kRsWarps;
+    grid_dep_sync();
+    // exclusive prefix sums of the statistics blocks' keep counts (each
+    // thread a contiguous run of blocks)
+    const int run = (nsb + 32 * kRsWarps - 1) / (32 * kRsWarps);
+    const int k0 = min(nsb, (int)threadIdx.x * run), k1 = min(nsb, k0 + run);
+    int sum = 0;
+    for (int k = k0; k < k1; ++k) sum += bcount[k];
+    int x = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[warp] = x;
+    if (threadIdx.x < 2) first[threadIdx.x] = 0x7fffffff;
+    __syncthreads();
+    if (warp == 0) {
+        const int v = lane < kRsWarps ? wsum[lane] : 0;
+        int xs = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, xs, o);
+            if (lane >= o) xs += y;
+        }
+        if (lane < kRsWarps) wsum[kRsWarps + lane] = xs - v;  // exclusive warp offsets
+    }
+    __syncthreads();
+    int acc = wsum[kRsWarps + warp] + x - sum;
+    for (int k = k0; k < k1; ++k) {
+        E[k] = acc;
+        acc += bcount[k];
+    }
+    if (k1 == nsb && k0 < k1) E[nsb] = acc;
+    if (nsb == 0 && threadIdx.x == 0) E[0] = 0;
+    __syncthreads();
+    const int nr = E[rbs], nd = E[nsb] - E[rbs];
+    if (blockIdx.x == 0) {
+        // the first range (domain) that is not kept, as the compaction
+        // reports it: blocks whose count is below their valid items
+        for (int k = threadIdx.x; k < nsb; k += blockDim.x) {
+            const bool dom = k >= rbs;
+            const int lo_item = (dom ? k - rbs : k) * per;
+            const int valid = min(per, (dom ? g.D : g.R) - lo_item);
+            if (bcount[k] < valid) {
+                const uint4 mk = bmask[k];
+                const uint32_t w[4] = {mk.x, mk.y, mk.z, mk.w};
+                int f = -1;
+                for (int q = 0; q < 4 && f < 0; ++q) {
+                    const int nv = min(32, valid - 32 * q);
+                    if (nv <= 0) break;
+                    const uint32_t vm = nv >= 32 ? 0xffffffffu : ((1u << nv) - 1u);
+                    const uint32_t z = ~w[q] & vm;
+                    if (z) f = 32 * q + __ffs(z) - 1;
+                }
+                if (f >= 0) atomicMin(first + (dom ? 1 : 0), lo_item + f);
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            counts[0] = nr;
+            counts[1] = first[0] == 0x7fffffff ? -1 : first[0];
+            counts[2] = nd;
+            counts[3] = first[1] == 0x7fffffff ? -1 : first[1];
+        }
+    }
+    // seeds: block b takes ranges b, b + G, ..., b + 15 G, its warps the
+    // screened ones in order
+    if (seed) {
+        const int G = gridDim.x, b = blockIdx.x;
+        const int rl = lane < 16 ? lane * G + b : g.R;
+        unsigned kept = __ballot_sync(0xffffffffu, rl < g.R && rkeep[rl] != 0);
+        if (warp < __popc(kept)) {  // warp-uniform
+            for (int t = 0; t < warp; ++t) kept &= kept - 1;
+            const int r = (__ffs(kept) - 1) * G + b;
+            seed_range(g, ec, ri, di, dconst, bblk, qblk, tbest, r, lane, wsm,
+                       reinterpret_cast<uint32_t *>(wsm + 8 * (m + 2)));
+            __syncwarp();  // the seed area becomes the row staging
+        }
+    }
+    // operand rows: warp units over the grid, the kept ranges' rows first
+    const RowLane rl = row_lane<LN>(lane);
+    uint16_t *st = reinterpret_cast<uint16_t *>(wsm);
+    const int W = gridDim.x * kRsWarps;
+    for (int u = blockIdx.x * kRsWarps + warp; u < nr + nd; u += W) {
+        if (u < nr) {
+            const int r = kept_item(E, 0, rbs, u, bmask, per);
+            if (r < 0) continue;  // unreachable: counts and masks come from one statistics launch
+            if (lane == 0) act[u] = r;
+            range_row<LN, SPLIT>(ri, bblk, u, r, lane, rs32, ra16);
+        } else {
+            const int j = u - nr;
+            const int d = kept_item(E, rbs, nsb, j, bmask, per);
+            if (d < 0) continue;
+            if (lane == 0) dact[j] = d;
+            __syncwarp();  // the staging of the warp's previous domain is read
+            domain_rows_warp<LN, SPLIT>(di, qblk, dconst, j, d, lane, rl, st, cb32, cb16, dconst_c, dmap);
+        }
+    }
+}
+
+// The fused kernels of a geometry (ranges of at most 8 x 8).
+template <typename Launch>
+static cudaError_t with_rows_seed_kernel(const Geometry &g, Launch &&launch)
+{
+    const bool sp = g.split_hilo != 0;
+    switch (g.ln) {
+    case 2: return sp ? launch(k_rows_seed<2, true>) : launch(k_rows_seed<2, false>);
+    case 3: return sp ? launch(k_rows_seed<3, true>) : launch(k_rows_seed<3, false>);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
 // Launch shape of the compaction + seed launch: T/32 seeded ranges per block.
 template <typename Launch>
 static cudaError_t with_seed_shape(int m, Launch &&launch)
@@ -918,11 +1133,32 @@ cudaError_t launch_prep(const Geometry &g, const void *img, const EpiConst &ec, 
                         int seed, cudaStream_t st)
 {
     const int rb = (g.R + 7) / 8, db = (g.D + 7) / 8;
+    const int nsb = stats_blocks(g);
+    // ranges of at most 8 x 8 (the seed's shared memory per warp is small
+    // there) and statistics blocks whose counts fit a block's shared memory:
+    // compaction, operand rows and seeds in one launch after the statistics
+    const bool fused = g.m <= 64 && nsb <= kRsMaxStatBlocks && cb.bmask;
     cudaError_t e = with_stats_kernel(g, [&](auto one, auto) {
-        return launch_dep(one, dim3(stats_blocks(g)), dim3(256), 0, st, g, ec, img, dense, tc_mode, active, ri, bblk,
-                          tbest, di, dconst, qblk, cb.rkeep, cb.dkeep, zero4);
+        return launch_dep(one, dim3(nsb), dim3(256), 0, st, g, ec, img, dense, tc_mode, active, ri, bblk, tbest, di,
+                          dconst, qblk, cb.rkeep, cb.dkeep, zero4, fused ? cb.bmask : nullptr,
+                          fused ? cb.bcount : nullptr);
     });
     if (e != cudaSuccess) return e;
+    if (fused) {
+        const size_t smem = sizeof(int) * (size_t)rows_seed_ints(g.m, nsb);
+        // every range in some block's 16 seed slots; at least the resident
+        // blocks (two per SM) for the rows
+        const int blocks = std::max((g.R + 15) / 16, 2 * prep_sms());
+        return with_rows_seed_kernel(g, [&](auto kern) {
+            cudaError_t e2 = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e2 != cudaSuccess) return e2;
+            return launch_dep(kern, dim3(blocks), dim3(32 * kRsWarps), smem, st, g, ec, seed, (const RangeInfo *)ri,
+                              (const uint16_t *)bblk, (const DomainInfo *)di, (const uint16_t *)qblk,
+                              (const float4 *)dconst, (const int *)cb.rkeep, (const uint4 *)cb.bmask,
+                              (const int *)cb.bcount, tbest, cb.act, cb.dact, cb.counts, rs32, ra16, cb32, cb16,
+                              cb.dconst_c, cb.dmap);
+        });
+    }
     const int sw = seed_warps(g.m);
     e = with_seed_shape(g.m, [&](auto one, auto, int threads) {
         const int per = sw;  // ranges per seed block
