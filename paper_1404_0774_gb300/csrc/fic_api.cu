@@ -948,7 +948,7 @@ cudaError_t batch_pipeline(const BatchPlan &P, const fic_params *p, char *ws, in
                                   st)) != cudaSuccess)
         return e;
     for (auto &gr : groups)
-        if ((e = launch_finalize_batch(dctx + gr.first, gr.second, ranges_of(gr.first), st)) != cudaSuccess) return e;
+        if ((e = launch_finalize_batch(dctx + gr.first, gr.second, ranges_of(gr.first), P.any_wide, st)) != cudaSuccess) return e;
     return cudaSuccess;
 }
 

@@ -584,7 +584,7 @@ cudaError_t launch_search_simt_batch(const SliceCtx *ctx, int n, int max_ranges,
 cudaError_t launch_rescore_batch(const SliceCtx *ctx, int n, int total_ranges, bool any_wide, bool any_narrow,
                                  int max_m, int lists_per_split, int col_tile, int exact_scan, int n_sm,
                                  cudaStream_t st);
-cudaError_t launch_finalize_batch(const SliceCtx *ctx, int n, int ranges, cudaStream_t st);
+cudaError_t launch_finalize_batch(const SliceCtx *ctx, int n, int ranges, bool wide, cudaStream_t st);
 cudaError_t launch_rescore(const Geometry &g, const EpiConst &ec, const RangeInfo *ri,
                            const DomainInfo *di, const uint16_t *bblk, const uint16_t *qblk,
                            const ListEntry *lists, int max_lists, const int *counts, const int *act,

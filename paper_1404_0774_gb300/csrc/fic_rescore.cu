@@ -622,7 +622,9 @@ __global__ void __launch_bounds__(32 * kRescoreWarps, 4)
 // The map of range r from its winner word wj (candidate index, bit 31: the
 // winner came from an exact scan) and the exact statistics of the pair: codes
 // decided as fp64_codes decides them (the FP32 shortcut where it provably
-// agrees), the eq 8 residual exact in integers and rounded once to FP64.
+// agrees), the eq 8 residual exact in integers (64-bit unless the geometry
+// needs 128, as in the re-score) and rounded once to FP64.
+template <bool Wide>
 __device__ __forceinline__ void write_map(const Geometry &g, const Stats &st, int r, uint32_t wj, const int *err,
                                           fic_map *maps)
 {
@@ -649,12 +651,14 @@ __device__ __forceinline__ void write_map(const Geometry &g, const Stats &st, in
     mp.s = sf;
     mp.o = of;
     mp.info = ((wj & 0x80000000u) ? FIC_MAP_FALLBACK : 0u) | (*err ? FIC_MAP_ERROR : 0u);
-    mp.err = u128_to_double((unsigned __int128)exact_err<true>(g, st, c, e)) * invD2;
+    mp.err = (Wide ? u128_to_double((unsigned __int128)exact_err<true>(g, st, c, e))
+                   : (double)(unsigned long long)exact_err<false>(g, st, c, e)) * invD2;
     maps[r] = mp;
 }
 
 // The map of one range whose winner an exact scan has just decided, by the
 // calling warp (exact cross term over the lanes, the rest on lane 0).
+template <bool Wide>
 __device__ void finalize_range_warp(const Geometry &g, const RangeInfo *ri, const DomainInfo *di,
                                     const uint16_t *bblk, const uint16_t *qblk, int r, uint32_t wj, const int *err,
                                     fic_map *maps)
@@ -672,7 +676,7 @@ __device__ void finalize_range_warp(const Geometry &g, const RangeInfo *ri, cons
     if (lane == 0) {
         const RangeInfo rin = ri[r];
         const DomainInfo dd = di[d];
-        write_map(g, Stats{dd.Sq, dd.Sqq, rin.Sb, rin.Sbb, X}, r, wj, err, maps);
+        write_map<Wide>(g, Stats{dd.Sq, dd.Sqq, rin.Sb, rin.Sbb, X}, r, wj, err, maps);
     }
 }
 
@@ -774,7 +778,7 @@ __device__ __forceinline__ void full_scans(const Geometry &g, const RangeInfo *r
         }
         if (maps) {  // the map of a range whose last chunk this was
             __syncthreads();
-            if (last_s && threadIdx.x < 32) finalize_range_warp(g, ri, di, bblk, qblk, r, fin_w, err, maps);
+            if (last_s && threadIdx.x < 32) finalize_range_warp<Wide>(g, ri, di, bblk, qblk, r, fin_w, err, maps);
         }
     }
 }
@@ -869,7 +873,7 @@ __device__ __forceinline__ void list_scans_block(const Geometry &g, const RangeI
         }
         if (maps) {  // the map of a range whose last list this was
             __syncthreads();
-            if (fin_s && threadIdx.x < 32) finalize_range_warp(g, ri, di, bblk, qblk, r, fin_w, err, maps);
+            if (fin_s && threadIdx.x < 32) finalize_range_warp<Wide>(g, ri, di, bblk, qblk, r, fin_w, err, maps);
         }
     }
 }
@@ -946,7 +950,7 @@ __device__ __forceinline__ void list_scans_warp(const Geometry &g, const RangeIn
             }
         }
         fin_w = __shfl_sync(0xffffffffu, fin_w, 0);
-        if (maps && fin_w != 0) finalize_range_warp(g, ri, di, bblk, qblk, r, fin_w, err, maps);
+        if (maps && fin_w != 0) finalize_range_warp<Wide>(g, ri, di, bblk, qblk, r, fin_w, err, maps);
     }
 }
 
@@ -960,6 +964,7 @@ __device__ __forceinline__ void list_scans_warp(const Geometry &g, const RangeIn
 // pixel rows of the exact cross term.
 constexpr int kFinRanges = 32;
 constexpr int kFinWarps = 4;
+template <bool Wide>
 __device__ __forceinline__ void finalize_block(const Geometry &g, const RangeInfo *ri, const DomainInfo *di,
                                                const uint16_t *bblk, const uint16_t *qblk, const uint32_t *winner,
                                                const int *err, fic_map *maps, int bx)
@@ -1032,7 +1037,7 @@ __device__ __forceinline__ void finalize_block(const Geometry &g, const RangeInf
     for (int w = 0; w < kFinWarps; ++w) X += x_s[w][jr];
     const uint32_t wj = w_s[jr];
     if (win_pending(wj)) return;  // an exact scan decides it (and writes the map)
-    write_map(g, Stats{st_s[0][jr], st_s[1][jr], st_s[2][jr], st_s[3][jr], X}, r0 + jr, wj, err, maps);
+    write_map<Wide>(g, Stats{st_s[0][jr], st_s[1][jr], st_s[2][jr], st_s[3][jr], X}, r0 + jr, wj, err, maps);
 }
 
 // Shared memory of the list scans: 8 (m+1) ints per warp.
@@ -1061,7 +1066,7 @@ __global__ void __launch_bounds__(32 * kFinWarps) k_scans_finalize(Geometry g, c
     grid_dep_sync();
     const int groups = (g.R + kFinRanges - 1) / kFinRanges;
     for (int gb = blockIdx.x; gb < groups; gb += gridDim.x) {
-        finalize_block(g, ri, di, bblk, qblk, winner, err, maps, gb);
+        finalize_block<Wide>(g, ri, di, bblk, qblk, winner, err, maps, gb);
         __syncthreads();  // the block's staging is reused by its next group
     }
     full_scans<Wide>(g, ri, di, bblk, qblk, fb_list, fb_count, nch, part, done, winner, blockIdx.x, gridDim.x, err,
@@ -1150,13 +1155,14 @@ __global__ void __launch_bounds__(256) k_exact_scans_batch(const SliceCtx *__res
     }
 }
 
+template <bool Wide>
 __global__ void __launch_bounds__(32 * kFinWarps) k_finalize_batch(const SliceCtx *__restrict__ ctx)
 {
     grid_dep_sync();
     const SliceCtx c = ctx[blockIdx.y];
     if ((int)blockIdx.x * kFinRanges >= c.g.R) return;
     const EncBufs &b = c.b;
-    finalize_block(c.g, b.ri, b.di, b.bblk, b.qblk, b.winner, b.err, c.maps, blockIdx.x);
+    finalize_block<Wide>(c.g, b.ri, b.di, b.bblk, b.qblk, b.winner, b.err, c.maps, blockIdx.x);
 }
 
 
@@ -1236,10 +1242,12 @@ cudaError_t launch_rescore_batch(const SliceCtx *ctx, int n, int total_ranges, b
     return cudaSuccess;
 }
 
-cudaError_t launch_finalize_batch(const SliceCtx *ctx, int n, int ranges, cudaStream_t st)
+// wide: some slice's residuals need 128-bit integers (128-bit arithmetic is
+// exact for the others too)
+cudaError_t launch_finalize_batch(const SliceCtx *ctx, int n, int ranges, bool wide, cudaStream_t st)
 {
-    return launch_dep(k_finalize_batch, dim3((ranges + kFinRanges - 1) / kFinRanges, n), dim3(32 * kFinWarps), 0, st,
-                      ctx);
+    return launch_dep(wide ? k_finalize_batch<true> : k_finalize_batch<false>,
+                      dim3((ranges + kFinRanges - 1) / kFinRanges, n), dim3(32 * kFinWarps), 0, st, ctx);
 }
 
 }  // namespace fic
