@@ -220,34 +220,21 @@ __device__ __forceinline__ typename Exact<Wide>::U exact_rational(const Geometry
     return (typename Exact<Wide>::U)exact_err<Wide>(g, st, c, e);
 }
 
-// Exact X of two candidates for a range whose pixels b[] are spread over the
-// warp (lane l holds pixels l, l+32, ...); every lane gets both sums.
-__device__ void warp_cross2(const Geometry &g, const uint16_t *qblk, uint32_t i0, uint32_t i1,
-                            const int (&b)[kMaxM / 32], long long &x0, long long &x1)
+// Exact sum over the warp of q[j] * b[j] (lane l holds the terms of pixels
+// l, l + 32, ...); every lane gets the sum.
+__device__ __forceinline__ long long warp_dot(const int (&q)[kMaxM / 32], const int (&b)[kMaxM / 32])
 {
-    const int d0 = i0 >> 3, k0 = i0 & 7, d1 = i1 >> 3, k1 = i1 & 7;
-    const int lane = threadIdx.x & 31;
-    long long a0 = 0, a1 = 0;
+    long long a = 0;
 #pragma unroll
-    for (int j = 0; j < kMaxM / 32; ++j) {
-        const int i = lane + 32 * j;
-        if (i < g.m) {
-            int sy, sx;
-            sym_src(k0, g.n, i >> g.ln, i & (g.n - 1), sy, sx);
-            const int q0 = qblk[(size_t)d0 * g.m + (sy << g.ln) + sx];
-            sym_src(k1, g.n, i >> g.ln, i & (g.n - 1), sy, sx);
-            const int q1 = qblk[(size_t)d1 * g.m + (sy << g.ln) + sx];
-            a0 += (long long)q0 * b[j];
-            a1 += (long long)q1 * b[j];
-        }
-    }
-    for (int off = 16; off > 0; off >>= 1) {
-        a0 += __shfl_xor_sync(0xffffffffu, a0, off);
-        a1 += __shfl_xor_sync(0xffffffffu, a1, off);
-    }
-    x0 = a0;
-    x1 = a1;
+    for (int j = 0; j < kMaxM / 32; ++j) a += (long long)q[j] * b[j];
+    for (int off = 16; off > 0; off >>= 1) a += __shfl_xor_sync(0xffffffffu, a, off);
+    return a;
 }
+
+// Finalists up to which the re-score takes them one at a time over the whole
+// warp (latency of one gather each) rather than one per lane (staging of the
+// permuted range pixels and a serial row per lane).
+constexpr int kCoopFinalists = 4;
 
 // The range's pixels permuted for each symmetry: bk[k*(m+1) + j] is the
 // range pixel that S_k places over contracted-domain pixel j, so that
@@ -432,6 +419,21 @@ __device__ __forceinline__ void rescore_range(const Geometry &g, const EpiConst 
         }
         return;
     }
+    // the best-key candidate's domain pixels, gathered through its symmetry
+    // (lane l: those over range pixels l, l + 32, ...), and its domain's
+    // statistics: loaded now, under the threshold work below, for its exact
+    // cross term (it is nearly always the only finalist)
+    int qb[kMaxM / 32];
+    {
+        const int d = ib >> 3;
+        const SymFlags sf = sym_flags(ib & 7, g.n);
+#pragma unroll
+        for (int j = 0; j < kMaxM / 32; ++j) {
+            const int i = lane + 32 * j;
+            qb[j] = i < g.m ? (int)qblk[(size_t)d * g.m + sym_src_index(sf, g.ln, i >> g.ln, i & (g.n - 1))] : 0;
+        }
+    }
+    const DomainInfo dib = di[ib >> 3];
     Stats st;
     st.Sb = rin.Sb;
     st.Sbb = rin.Sbb;
@@ -446,9 +448,7 @@ __device__ __forceinline__ void rescore_range(const Geometry &g, const EpiConst 
     if (kc < __int_as_float(0x7f800000)) {
         Ub = __fadd_ru(rin.sbbc, __fdiv_ru(__fadd_ru(kc, beta_key(re, kc, ec)), ec.two_ls));
     } else {
-        long long X, Xd;
-        warp_cross2(g, qblk, ib, ib, b, X, Xd);
-        best_e = exact_rational<Wide>(g, st, di[ib >> 3], X);  // integer work, same on every lane
+        best_e = exact_rational<Wide>(g, st, dib, warp_dot(qb, b));  // integer work, same on every lane
         best_i = ib;
         Ub = __fmul_ru(to_float_ru(best_e), ec.invD2_up);
     }
@@ -490,7 +490,37 @@ __device__ __forceinline__ void rescore_range(const Geometry &g, const EpiConst 
         if (fin) fl[nfin + __popc(bal & ((1u << lane) - 1u))] = (int)(ent[q].idx & kIdxMask);
         nfin += __popc(bal);
     }
-    if (nfin > 0) {  // warp-uniform
+    if (nfin > 0 && nfin <= kCoopFinalists) {  // warp-uniform: the usual case
+        // each finalist's cross term over the whole warp (gathered pixels,
+        // shuffle sum), the best-key candidate's from the loads made above
+        __syncwarp();
+        for (int f = 0; f < nfin; ++f) {
+            const uint32_t idx = (uint32_t)fl[f];
+            long long X;
+            DomainInfo dd;
+            if (idx == ib) {
+                X = warp_dot(qb, b);
+                dd = dib;
+            } else {
+                const int d = idx >> 3;
+                const SymFlags sf = sym_flags(idx & 7, g.n);
+                int qf[kMaxM / 32];
+#pragma unroll
+                for (int j = 0; j < kMaxM / 32; ++j) {
+                    const int i = lane + 32 * j;
+                    qf[j] = i < g.m ? (int)qblk[(size_t)d * g.m + sym_src_index(sf, g.ln, i >> g.ln, i & (g.n - 1))]
+                                    : 0;
+                }
+                dd = di[d];
+                X = warp_dot(qf, b);
+            }
+            const U er = exact_rational<Wide>(g, st, dd, X);  // same on every lane
+            if (better(er, idx, best_e, best_i)) {
+                best_e = er;
+                best_i = idx;
+            }
+        }
+    } else if (nfin > 0) {  // many finalists: one per lane
         stage_sym_pixels(g, b, bk);
         __syncwarp();
         for (int f = lane; f < nfin; f += 32) {
