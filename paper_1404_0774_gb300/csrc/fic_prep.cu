@@ -638,8 +638,8 @@ static cudaError_t with_rows_kernel(const Geometry &g, Launch &&launch)
 // after the keep flag).
 __host__ __device__ constexpr int seed_warps(int m) { return m <= 64 ? 16 : 8; }
 // Shared ints per seed warp: one range (m = 256: 8 m of bk, 16 m of q2;
-// m <= 64, see seed_range: 8 (m + 2) of bk, 8 m of q2).
-__host__ __device__ constexpr int seed_warp_ints(int m) { return m <= 64 ? 16 * m + 16 : 24 * m; }
+// m <= 64, see seed_range: 8 (m + 4) of bk, 8 m of q2).
+__host__ __device__ constexpr int seed_warp_ints(int m) { return m <= 64 ? 16 * m + 32 : 24 * m; }
 __host__ __device__ constexpr size_t seed_smem(int m) { return sizeof(int) * (size_t)seed_warps(m) * seed_warp_ints(m); }
 
 template <int PPL>  // range pixels per lane, at least m / 32
@@ -746,14 +746,15 @@ __device__ __forceinline__ void seed_warp(const Geometry &g, const EpiConst &ec,
 // seed_warp over 16 domain slots -- the 3 x 3 domains around the range and 7
 // spread over the image -- with lane = (symmetry half h, slot sl): the lane
 // scores symmetries 4h .. 4h+3 of its slot's domain.  bk holds the range's
-// symmetry-permuted pixels (rows of m + 2 ints, so that the two halves'
-// broadcast reads fall in different banks), q2[p][slot] the slots' domain
-// pixel pairs (each slot row loaded by its two lanes, half each).  Cross
-// terms sum in 32 bits: m <= 64 products of at most 4P * P < 2^26 stay below
-// 2^32.
+// symmetry-permuted pixels (rows of m + 4 ints: 16-byte aligned, and the two
+// halves' broadcast reads fall in different banks), q2[pp][slot] the slots'
+// domain pixels 4 pp .. 4 pp + 3 as two words (each slot row loaded by its
+// two lanes, half each): one 8-byte and four 16-byte shared loads per 16
+// products.  Cross terms sum in 32 bits: m <= 64 products of at most
+// 4P * P < 2^26 stay below 2^32.
 __device__ __forceinline__ void seed_range(const Geometry &g, const EpiConst &ec, const RangeInfo *ri,
                                            const DomainInfo *di, const float4 *dconst, const uint16_t *bblk,
-                                           const uint16_t *qblk, int *tbest, int r, int lane, int *bk, uint32_t *q2)
+                                           const uint16_t *qblk, int *tbest, int r, int lane, int *bk, uint2 *q2)
 {
     const int h = lane >> 4, sl = lane & 15;
     int d;
@@ -782,7 +783,7 @@ __device__ __forceinline__ void seed_range(const Geometry &g, const EpiConst &ec
     const RangeInfo rin = ri[r];
     const DomainInfo dd = di[d];
     const float4 c4 = dconst[d];
-    const int bp = g.m + 2;  // bk row pitch (ints)
+    const int bp = g.m + 4;  // bk row pitch (ints)
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
         const int i = lane + 32 * j;
@@ -800,10 +801,8 @@ __device__ __forceinline__ void seed_range(const Geometry &g, const EpiConst &ec
     for (int v = 0; v < 4; ++v) {
         const int vv = 2 * v + h;
         if (vv < nv) {
-            q2[(4 * vv + 0) * 16 + sl] = qv[v].x;
-            q2[(4 * vv + 1) * 16 + sl] = qv[v].y;
-            q2[(4 * vv + 2) * 16 + sl] = qv[v].z;
-            q2[(4 * vv + 3) * 16 + sl] = qv[v].w;
+            q2[(2 * vv + 0) * 16 + sl] = make_uint2(qv[v].x, qv[v].y);
+            q2[(2 * vv + 1) * 16 + sl] = make_uint2(qv[v].z, qv[v].w);
         }
     }
     __syncwarp();
@@ -811,13 +810,13 @@ __device__ __forceinline__ void seed_range(const Geometry &g, const EpiConst &ec
     uint32_t X[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) X[k] = 0;
-    for (int p = 0; p < (g.m >> 1); ++p) {
-        const uint32_t w = q2[p * 16 + sl];  // the two halves of a slot read the same word
-        const uint32_t qa = w & 0xffffu, qb = w >> 16;
+    for (int pp = 0; pp < (g.m >> 2); ++pp) {
+        const uint2 w = q2[pp * 16 + sl];  // the two halves of a slot read the same words
+        const uint32_t qa = w.x & 0xffffu, qb = w.x >> 16, qc = w.y & 0xffffu, qd = w.y >> 16;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            const int2 b2 = *reinterpret_cast<const int2 *>(bkh + k * bp + 2 * p);
-            X[k] += qa * (uint32_t)b2.x + qb * (uint32_t)b2.y;
+            const int4 b4 = *reinterpret_cast<const int4 *>(bkh + k * bp + 4 * pp);
+            X[k] += qa * (uint32_t)b4.x + qb * (uint32_t)b4.y + qc * (uint32_t)b4.z + qd * (uint32_t)b4.w;
         }
     }
     const RangeEpi re = range_epi(rin, ec);
@@ -869,7 +868,7 @@ __device__ __forceinline__ void compact_seed_block(const Geometry &g, const EpiC
         for (int t = 0; t < warp; ++t) kept &= kept - 1;
         const int r = (__ffs(kept) - 1) * nb + b;
         seed_range(g, ec, ri, di, dconst, bblk, qblk, tbest, r, lane, bk,
-                   reinterpret_cast<uint32_t *>(bk + 8 * (g.m + 2)));
+                   reinterpret_cast<uint2 *>(bk + 8 * (g.m + 4)));
     } else {
         const int nb = (g.R + T / 32 - 1) / (T / 32);
         if (bx - 2 >= nb) return;
@@ -1054,7 +1053,7 @@ __global__ void __launch_bounds__(32 * kRsWarps, 2)
             for (int t = 0; t < warp; ++t) kept &= kept - 1;
             const int r = (__ffs(kept) - 1) * G + b;
             seed_range(g, ec, ri, di, dconst, bblk, qblk, tbest, r, lane, wsm,
-                       reinterpret_cast<uint32_t *>(wsm + 8 * (m + 2)));
+                       reinterpret_cast<uint2 *>(wsm + 8 * (m + 4)));
             __syncwarp();  // the seed area becomes the row staging
         }
     }
