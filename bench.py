@@ -642,6 +642,42 @@ REF_WORKLOAD = ("512x512 12-bit CT-like synthetic slice encoded as the slice wor
                 "kernels, iterates checkpointed every 2")
 
 
+def cpu_oracle_refine(img_np, maps, fic, s0, o0, iters, lr, budget_s=8.0):
+    """The FP64 oracle's refinement step on the host: the loss of the unrolled
+    decode and its gradient by the adjoint (oracle.refine_grad, one thread),
+    then the same Adam update in numpy, repeated for about budget_s seconds
+    from the encode's coefficients.  Returns the cpu_baseline record."""
+    import oracle
+
+    oracle.build()
+    m = fic.maps_to_numpy(maps)
+    dom = m["domain_idx"].astype(np.int32)
+    sym = m["iso"].astype(np.int32)
+    s = s0.double().cpu().numpy().copy()
+    o = o0.double().cpu().numpy().copy()
+    P = float((1 << BITS) - 1)
+    ref = img_np.astype(np.float64)
+    ms, vs = np.zeros_like(s), np.zeros_like(s)
+    mo, vo = np.zeros_like(o), np.zeros_like(o)
+    b1, b2, eps = 0.9, 0.999, 1e-8
+    k, t0 = 0, time.time()
+    while k < 3 or time.time() - t0 < budget_s:
+        _, gs, go = oracle.refine_grad(dom, sym, s, o, ref, n=RANGE, t=STRIDE, bit_depth=BITS, iters=iters)
+        k += 1
+        go = go * P  # the offset is optimised as o / P
+        ms = b1 * ms + (1 - b1) * gs
+        vs = b2 * vs + (1 - b2) * gs * gs
+        mo = b1 * mo + (1 - b1) * go
+        vo = b2 * vo + (1 - b2) * go * go
+        s -= lr * (ms / (1 - b1 ** k)) / (np.sqrt(vs / (1 - b2 ** k)) + eps)
+        o -= P * lr * (mo / (1 - b1 ** k)) / (np.sqrt(vo / (1 - b2 ** k)) + eps)
+    dt = time.time() - t0
+    return {"value": k / dt, "unit": "steps/s", "cores": 1, "kind": "oracle", "cpu_model": cpu_model(),
+            "ms_per_step": 1e3 * dt / k,
+            "sample": "%d refinement steps of the slice (FP64 loss and adjoint gradient of the %d-iteration "
+                      "unrolled decode, Adam in numpy), %.1f s on one thread" % (k, iters, dt)}
+
+
 def run_refine(args):
     """Differentiable refinement: one step = forward (8 unrolled iterations),
     loss, reverse sweep (adjoint), Adam update -- one CUDA graph replay."""
@@ -745,6 +781,8 @@ def run_refine(args):
                     "d2h_bytes_per_step": d2h / steps,
                     "timing": "one whole refinement (inputs in, 200 steps, results out), per step"},
             "gpu_launches": steps * (5 * T + T // 2 + 1), "clocks": clocks, "roofline": roof}
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_oracle_refine(img_np, maps, fic, s0, o0, T, lr)
     if rank == 0:
         print(json.dumps(line), flush=True)
 

@@ -425,8 +425,8 @@ cudaError_t encode_pipeline(const Geometry &gd, const fic_params *p, int search,
         FIC_MARK(3);
         FIC_STEP(launch_scans_finalize(gd, b.ri, b.di, b.bblk, b.qblk, b.fb_list, b.fb_count, b.partial, b.cb.counts,
                                        b.cb.dmap, search == FIC_SEARCH_TC ? search_tc_tile() : 64, target, n_split,
-                                       lists_per_split(search), n_lists, b.span, b.winner, b.err, dmaps, sm_count(),
-                                       st));
+                                       lists_per_split(search), n_lists, b.span, b.winner, b.err, dmaps, ec, b.dconst,
+                                       sm_count(), st));
         FIC_MARK(4);
         FIC_MARK(5);
     }

@@ -598,7 +598,8 @@ cudaError_t launch_scans_finalize(const Geometry &g, const RangeInfo *ri, const 
                                   const uint16_t *qblk, const int *fb_list, int *fb_count, void *partial,
                                   const int *counts, const int *dmap, int col_tile, int target, int max_split,
                                   int lists_per_split, int max_lists, void *span, uint32_t *winner, const int *err,
-                                  fic_map *maps, int n_sm, cudaStream_t st);
+                                  fic_map *maps, const EpiConst &ec, const float4 *dconst, int n_sm,
+                                  cudaStream_t st);
 size_t fallback_partial_bytes(const Geometry &g);
 size_t decode_workspace_bytes(const Geometry &g);
 cudaError_t launch_decode(const Geometry &g, const fic_map *maps, float init, int iters, void *ws,

@@ -813,6 +813,35 @@ __device__ __forceinline__ void full_scans(const Geometry &g, const RangeInfo *r
     }
 }
 
+// Whether a re-scanned candidate (domain statistics dd and screening
+// constants c4, exact cross term X) can be left out: with its code decided
+// away from a rounding boundary, its FP32 screening key less the key's
+// allowance lies above kcert, the certification's bound for the finalists'
+// best residual, so its own residual exceeds that best and it can neither
+// beat nor tie the winner (the test the certification applies to a list's
+// last key).  Candidates next to a rounding boundary are always scored.
+__device__ __forceinline__ bool scan_skip(const Geometry &g, const EpiConst &ec, const RangeEpi &re, long long Sb,
+                                          const DomainInfo &dd, const float4 &c4, long long X, float kcert)
+{
+    const long long num = (long long)g.m * X - dd.Sq * Sb;  // exact
+    const float Xt = __ll2float_rn(num) * ec.invm;
+    float rho;
+    const float c = epi_code(Xt, c4.x, 0.5f, ec, rho);
+    if (fabsf(rho) > re.rho_lim) return false;
+    const float key = epi_key(Xt, -0.0f, c, re.zb, c4, ec);
+    return __fsub_rd(key, beta_key(re, key, ec)) > kcert;
+}
+
+// kcert of range r from the finalists' best exact residual the re-score left
+// in sb.cert (rounded outward as in the certification).
+template <bool Wide>
+__device__ __forceinline__ float scan_kcert(const EpiConst &ec, const RangeInfo &rin, const Partial &cp)
+{
+    typedef typename Exact<Wide>::U U;
+    const U e = Wide ? (U)(((unsigned __int128)cp.hi << 64) | cp.lo) : (U)cp.lo;
+    return __fmul_ru(__fsub_ru(__fmul_ru(to_float_ru(e), ec.invD2_up), rin.sbbc), ec.two_ls);
+}
+
 // Exact scan of the candidates of one failed list (work item (range, list),
 // one block each, for short queues; list_scans_warp below for long ones):
 // list l = split * parts + part of a range holds the columns tile * col_tile
@@ -822,7 +851,8 @@ __device__ __forceinline__ void full_scans(const Geometry &g, const RangeInfo *r
 // the finalists' best and writes the winner, flagged as resolved by an exact
 // scan.
 template <bool Wide>
-__device__ __forceinline__ void list_scans_block(const Geometry &g, const RangeInfo *ri, const DomainInfo *di,
+__device__ __forceinline__ void list_scans_block(const Geometry &g, const EpiConst &ec, const RangeInfo *ri,
+                                           const DomainInfo *di, const float4 *dconst,
                                            const uint16_t *bblk, const uint16_t *qblk, const int *counts,
                                            const int *dmap, int col_tile, int target, int max_split,
                                            int lists_per_split, int max_lists, const SpanBufs &sb, uint32_t *winner,
@@ -851,6 +881,8 @@ __device__ __forceinline__ void list_scans_block(const Geometry &g, const RangeI
         Stats st;
         st.Sb = rin.Sb;
         st.Sbb = rin.Sbb;
+        const RangeEpi re = range_epi(rin, ec);
+        const float kcert = scan_kcert<Wide>(ec, rin, sb.cert[r]);
         U best_e = ~(U)0;
         uint32_t best_i = 0xffffffffu;
         for (int i = threadIdx.x; i < (t1 - t0) * seg; i += blockDim.x) {
@@ -860,7 +892,9 @@ __device__ __forceinline__ void list_scans_block(const Geometry &g, const RangeI
             const int d = dmap[c >> 3], k = c & 7;
             const uint32_t idx = (uint32_t)(d * 8 + k);
             const long long X = lane_cross(g, qblk, idx, bk_s);
-            const U er = exact_rational<Wide>(g, st, di[d], (long long)X);
+            const DomainInfo dd = di[d];
+            if (scan_skip(g, ec, re, st.Sb, dd, dconst[d], X, kcert)) continue;
+            const U er = exact_rational<Wide>(g, st, dd, (long long)X);
             if (better(er, idx, best_e, best_i)) {
                 best_e = er;
                 best_i = idx;
@@ -913,7 +947,8 @@ __device__ __forceinline__ void list_scans_block(const Geometry &g, const RangeI
 // staging and the reduction.  bk: this warp's 8 (m+1) ints of shared memory;
 // items first, first + stride, ...
 template <bool Wide>
-__device__ __forceinline__ void list_scans_warp(const Geometry &g, const RangeInfo *ri, const DomainInfo *di,
+__device__ __forceinline__ void list_scans_warp(const Geometry &g, const EpiConst &ec, const RangeInfo *ri,
+                                           const DomainInfo *di, const float4 *dconst,
                                            const uint16_t *bblk, const uint16_t *qblk, const int *counts,
                                            const int *dmap, int col_tile, int target, int max_split,
                                            int lists_per_split, int max_lists, const SpanBufs &sb, uint32_t *winner,
@@ -939,6 +974,8 @@ __device__ __forceinline__ void list_scans_warp(const Geometry &g, const RangeIn
         Stats st;
         st.Sb = rin.Sb;
         st.Sbb = rin.Sbb;
+        const RangeEpi re = range_epi(rin, ec);
+        const float kcert = scan_kcert<Wide>(ec, rin, sb.cert[r]);
         U best_e = ~(U)0;
         uint32_t best_i = 0xffffffffu;
         for (int i = lane; i < (t1 - t0) * seg; i += 32) {
@@ -948,7 +985,9 @@ __device__ __forceinline__ void list_scans_warp(const Geometry &g, const RangeIn
             const int d = dmap[c >> 3], k = c & 7;
             const uint32_t idx = (uint32_t)(d * 8 + k);
             const long long X = lane_cross(g, qblk, idx, bk);
-            const U er = exact_rational<Wide>(g, st, di[d], (long long)X);
+            const DomainInfo dd = di[d];
+            if (scan_skip(g, ec, re, st.Sb, dd, dconst[d], X, kcert)) continue;
+            const U er = exact_rational<Wide>(g, st, dd, (long long)X);
             if (better(er, idx, best_e, best_i)) {
                 best_e = er;
                 best_i = idx;
@@ -1090,7 +1129,8 @@ __global__ void __launch_bounds__(32 * kFinWarps) k_scans_finalize(Geometry g, c
                                                                    int *done, const int *counts, const int *dmap,
                                                                    int col_tile, int target, int max_split,
                                                                    int lists_per_split, int max_lists, SpanBufs sb,
-                                                                   uint32_t *winner, const int *err, fic_map *maps)
+                                                                   uint32_t *winner, const int *err, fic_map *maps,
+                                                                   EpiConst ec, const float4 *dconst)
 {
     extern __shared__ int scan_sm[];  // [warps][8 (m+1)]
     grid_dep_sync();
@@ -1103,11 +1143,11 @@ __global__ void __launch_bounds__(32 * kFinWarps) k_scans_finalize(Geometry g, c
                      maps);
     const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     if (*sb.count > 2 * (int)gridDim.x)  // grid-uniform
-        list_scans_warp<Wide>(g, ri, di, bblk, qblk, counts, dmap, col_tile, target, max_split, lists_per_split,
+        list_scans_warp<Wide>(g, ec, ri, di, dconst, bblk, qblk, counts, dmap, col_tile, target, max_split, lists_per_split,
                               max_lists, sb, winner, scan_sm + warp * 8 * (g.m + 1), blockIdx.x * nw + warp,
                               gridDim.x * nw, err, maps);
     else
-        list_scans_block<Wide>(g, ri, di, bblk, qblk, counts, dmap, col_tile, target, max_split, lists_per_split,
+        list_scans_block<Wide>(g, ec, ri, di, dconst, bblk, qblk, counts, dmap, col_tile, target, max_split, lists_per_split,
                                max_lists, sb, winner, blockIdx.x, gridDim.x, err, maps);
 }
 
@@ -1176,11 +1216,11 @@ __global__ void __launch_bounds__(256) k_exact_scans_batch(const SliceCtx *__res
         const EncBufs &e = c.b;
         const SpanBufs sb = span_bufs(c.g, c.n_lists, e.span, e.fb_count + 2);
         if (by_warp)
-            list_scans_warp<Wide>(c.g, e.ri, e.di, e.bblk, e.qblk, e.cb.counts, e.cb.dmap, col_tile, c.target,
+            list_scans_warp<Wide>(c.g, c.ec, e.ri, e.di, e.dconst, e.bblk, e.qblk, e.cb.counts, e.cb.dmap, col_tile, c.target,
                                   c.n_split, lists_per_split, c.n_lists, sb, e.winner, scan_sm + warp * 8 * (c.g.m + 1),
                                   fl, W, nullptr, nullptr);
         else
-            list_scans_block<Wide>(c.g, e.ri, e.di, e.bblk, e.qblk, e.cb.counts, e.cb.dmap, col_tile, c.target,
+            list_scans_block<Wide>(c.g, c.ec, e.ri, e.di, e.dconst, e.bblk, e.qblk, e.cb.counts, e.cb.dmap, col_tile, c.target,
                                    c.n_split, lists_per_split, c.n_lists, sb, e.winner, fl, W, nullptr, nullptr);
     }
 }
@@ -1225,7 +1265,7 @@ cudaError_t launch_scans_finalize(const Geometry &g, const RangeInfo *ri, const 
                                   const uint16_t *qblk, const int *fb_list, int *fb_count, void *partial,
                                   const int *counts, const int *dmap, int col_tile, int target, int max_split,
                                   int lists_per_split, int max_lists, void *span, uint32_t *winner, const int *err,
-                                  fic_map *maps, int n_sm, cudaStream_t st)
+                                  fic_map *maps, const EpiConst &ec, const float4 *dconst, int n_sm, cudaStream_t st)
 {
     const int nch = fallback_chunks(g);
     Partial *part = reinterpret_cast<Partial *>(partial);
@@ -1239,7 +1279,7 @@ cudaError_t launch_scans_finalize(const Geometry &g, const RangeInfo *ri, const 
     const int blocks = std::max((g.R + kFinRanges - 1) / kFinRanges, 3 * n_sm);
     return launch_dep(kern, dim3(blocks), dim3(32 * kFinWarps), smem, st, g, ri, di, bblk, qblk, fb_list,
                       (const int *)fb_count, nch, part, fallback_done(g, partial), counts, dmap, col_tile, target,
-                      max_split, lists_per_split, max_lists, sb, winner, err, maps);
+                      max_split, lists_per_split, max_lists, sb, winner, err, maps, ec, dconst);
 }
 
 // Batched re-score and exact scans of n slices (max_m: the pixels per range,
