@@ -141,6 +141,21 @@ def test_ct_slice_1024_sampled(fic, orc, search):
     check_against_oracle(orc, img, got, 8, 4, 12, ranges=sample)
 
 
+@pytest.mark.parametrize("search", SEARCH)
+def test_ct_slice_1024_stride2_sampled(fic, orc, search):
+    """1024x1024 12-bit CT-like, 8x8 ranges, domains at stride 2 (16384 ranges
+    x 255025 domains): more statistics blocks (8482) than one block of the
+    fused compaction + rows + seed launch can prefix-sum, so this size takes
+    the separate compaction + seed and rows launches.  Every map re-scored,
+    the minimum checked on sampled ranges."""
+    img = fic_synth.ct_slice(fic_synth.CT_SEED + 4, 1024)
+    p = fic.params(range_size=8, domain_stride=2, bit_depth=12, search=search_code(fic, search))
+    got = gpu_encode(fic, img, p)
+    rng = np.random.default_rng(2)
+    sample = np.sort(rng.choice(16384, 24, replace=False))
+    check_against_oracle(orc, img, got, 8, 2, 12, ranges=sample)
+
+
 DENSE_CASES = [
     ("ct128", lambda: fic_synth.ct_slice(16, 128), 8, 4, 12),
     ("mr128", lambda: fic_synth.mr_slice(17, 128), 8, 4, 8),
