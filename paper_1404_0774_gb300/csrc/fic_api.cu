@@ -210,7 +210,7 @@ int lists_per_split(int search)
 }
 
 struct EncLayout {
-    size_t img, ri, di, dconst, bblk, qblk, rs32, cb32, ra16, cb16, lists, winner, fb_list, fb_count, span,
+    size_t img, ri, di, dconst, bblk, qblk, rs32, cb32, ra16, cb16, lists, winner, winx, fb_list, fb_count, span,
         tbest, partial, maps, rkeep, dkeep, act, dact, counts, dconst_c, dmap, bmask, bcount, total;
 };
 
@@ -239,6 +239,7 @@ EncLayout enc_layout(const Geometry &g, int search, int n_lists, bool tc_operand
     L.cb16 = simt || !tc_operands ? 0 : take(sizeof(__half) * (size_t)search_tc_cols(g.N) * g.KP);
     L.lists = take(sizeof(ListEntry) * (size_t)g.R * n_lists * kListK);
     L.winner = take(sizeof(uint32_t) * g.R);
+    L.winx = take(sizeof(long long) * g.R);
     L.fb_list = take(sizeof(int) * g.R);
     L.fb_count = take(sizeof(int) * 4);  // full-scan count, error flag, list-scan count, search work items
     L.span = take(span_bytes(g, n_lists));
@@ -360,6 +361,7 @@ EncBufs enc_bufs(const EncLayout &L, char *ws)
     b.cb16 = L.cb16 ? reinterpret_cast<__half *>(ws + L.cb16) : nullptr;
     b.lists = reinterpret_cast<ListEntry *>(ws + L.lists);
     b.winner = reinterpret_cast<uint32_t *>(ws + L.winner);
+    b.winx = reinterpret_cast<long long *>(ws + L.winx);
     b.fb_list = reinterpret_cast<int *>(ws + L.fb_list);
     b.fb_count = reinterpret_cast<int *>(ws + L.fb_count);
     b.err = b.fb_count + 1;
@@ -420,13 +422,13 @@ cudaError_t encode_pipeline(const Geometry &gd, const fic_params *p, int search,
     if (!dump) {
         FIC_STEP(launch_rescore(gd, ec, b.ri, b.di, b.bblk, b.qblk, b.lists, n_lists, b.cb.counts, b.cb.act, b.cb.rkeep,
                                 lists_per_split(search), search == FIC_SEARCH_TC ? search_tc_tile() : 64, target,
-                                n_split, sm_count(), (p->flags & FIC_FLAG_EXACT_SCAN) ? 1 : 0, b.winner, b.fb_list,
+                                n_split, sm_count(), (p->flags & FIC_FLAG_EXACT_SCAN) ? 1 : 0, b.winner, b.winx, b.fb_list,
                                 b.fb_count, b.partial, b.span, st));
         FIC_MARK(3);
         FIC_STEP(launch_scans_finalize(gd, b.ri, b.di, b.bblk, b.qblk, b.fb_list, b.fb_count, b.partial, b.cb.counts,
                                        b.cb.dmap, search == FIC_SEARCH_TC ? search_tc_tile() : 64, target, n_split,
-                                       lists_per_split(search), n_lists, b.span, b.winner, b.err, dmaps, ec, b.dconst,
-                                       sm_count(), st));
+                                       lists_per_split(search), n_lists, b.span, b.winner, b.winx, b.err, dmaps, ec,
+                                       b.dconst, sm_count(), st));
         FIC_MARK(4);
         FIC_MARK(5);
     }

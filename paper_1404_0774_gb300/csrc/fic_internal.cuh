@@ -491,6 +491,7 @@ struct EncBufs {
     __half *ra16, *cb16;
     ListEntry *lists;
     uint32_t *winner;
+    long long *winx;      // the winner's exact cross term (kNoCross where unknown)
     int *fb_list, *fb_count, *err, *tbest;
     void *partial, *span;
     CompactBufs cb;
@@ -589,17 +590,17 @@ cudaError_t launch_rescore(const Geometry &g, const EpiConst &ec, const RangeInf
                            const DomainInfo *di, const uint16_t *bblk, const uint16_t *qblk,
                            const ListEntry *lists, int max_lists, const int *counts, const int *act,
                            const int *rkeep, int lists_per_split, int col_tile, int target, int max_split, int n_sm,
-                           int exact_scan, uint32_t *winner, int *fb_list, int *fb_count, void *partial, void *span,
-                           cudaStream_t st);
+                           int exact_scan, uint32_t *winner, long long *winx, int *fb_list, int *fb_count,
+                           void *partial, void *span, cudaStream_t st);
 size_t span_bytes(const Geometry &g, int max_lists);
 // The exact scans of the ranges the re-score queued and the map output, one
 // launch.
 cudaError_t launch_scans_finalize(const Geometry &g, const RangeInfo *ri, const DomainInfo *di, const uint16_t *bblk,
                                   const uint16_t *qblk, const int *fb_list, int *fb_count, void *partial,
                                   const int *counts, const int *dmap, int col_tile, int target, int max_split,
-                                  int lists_per_split, int max_lists, void *span, uint32_t *winner, const int *err,
-                                  fic_map *maps, const EpiConst &ec, const float4 *dconst, int n_sm,
-                                  cudaStream_t st);
+                                  int lists_per_split, int max_lists, void *span, uint32_t *winner,
+                                  const long long *winx, const int *err, fic_map *maps, const EpiConst &ec,
+                                  const float4 *dconst, int n_sm, cudaStream_t st);
 size_t fallback_partial_bytes(const Geometry &g);
 size_t decode_workspace_bytes(const Geometry &g);
 cudaError_t launch_decode(const Geometry &g, const fic_map *maps, float init, int iters, void *ws,

@@ -163,7 +163,35 @@ __device__ __forceinline__ void warp_argmin(U &err, uint32_t &idx)
     }
 }
 
+// Warp argmin over (err, idx) carrying the winner's cross term x.
+template <typename U>
+__device__ __forceinline__ void warp_argmin_x(U &err, uint32_t &idx, long long &x)
+{
+    for (int off = 16; off > 0; off >>= 1) {
+        const U oe = shfl_xor_u(err, off);
+        const uint32_t oi = __shfl_xor_sync(0xffffffffu, idx, off);
+        const long long ox = __shfl_xor_sync(0xffffffffu, x, off);
+        if (better(oe, oi, err, idx)) {
+            err = oe;
+            idx = oi;
+            x = ox;
+        }
+    }
+}
+
 }  // namespace
+
+// Cross-term word of a range whose winner's cross term the map output must
+// compute itself (a range the search did not screen and that is not constant).
+constexpr long long kNoCross = (long long)0x8000000000000000ull;
+
+// The cross term of candidate 0 (domain 0, identity) for a range the search
+// did not screen: for a constant range (pixel value Sb/m) it is Sb/m * Sq of
+// domain 0; otherwise (a range the caller left out) unknown.
+__device__ __forceinline__ long long unscreened_cross(const Geometry &g, const RangeInfo &rin, const DomainInfo *di)
+{
+    return rin.shadow ? (rin.Sb >> (2 * g.ln)) * di[0].Sq : kNoCross;
+}
 
 __device__ __forceinline__ double u128_to_double(unsigned __int128 v)
 {
@@ -360,7 +388,8 @@ __device__ __forceinline__ void rescore_range(const Geometry &g, const EpiConst 
                                               const DomainInfo *di, const uint16_t *bblk, const uint16_t *qblk,
                                               const ListEntry *lists, int max_lists, const int *counts,
                                               int lists_per_split, int col_tile, int target, int max_split,
-                                              int exact_scan, uint32_t *winner, int *fb_list, int *fb_count, int r,
+                                              int exact_scan, uint32_t *winner, long long *winx, int *fb_list,
+                                              int *fb_count, int r,
                                               int *bk, const SpanBufs &sb)
 {
     typedef typename Exact<Wide>::U U;
@@ -440,6 +469,7 @@ __device__ __forceinline__ void rescore_range(const Geometry &g, const EpiConst 
     const RangeEpi re = range_epi(rin, ec);
     U best_e = ~(U)0;
     uint32_t best_i = 0xffffffffu;
+    long long best_x = 0;  // the cross term of best_i (for the map output)
     // Ub >= the best exact residual, rounded up; every threshold below is an
     // FP32 bound rounded outward.  A clean entry gives it without exact work:
     // its residual is at most sbbc + (key + beta(key)) / (2 Ls).  Otherwise
@@ -448,7 +478,8 @@ __device__ __forceinline__ void rescore_range(const Geometry &g, const EpiConst 
     if (kc < __int_as_float(0x7f800000)) {
         Ub = __fadd_ru(rin.sbbc, __fdiv_ru(__fadd_ru(kc, beta_key(re, kc, ec)), ec.two_ls));
     } else {
-        best_e = exact_rational<Wide>(g, st, dib, warp_dot(qb, b));  // integer work, same on every lane
+        best_x = warp_dot(qb, b);
+        best_e = exact_rational<Wide>(g, st, dib, best_x);  // integer work, same on every lane
         best_i = ib;
         Ub = __fmul_ru(to_float_ru(best_e), ec.invD2_up);
     }
@@ -474,6 +505,7 @@ __device__ __forceinline__ void rescore_range(const Geometry &g, const EpiConst 
         if (better(fe, fi, best_e, best_i)) {
             best_e = fe;
             best_i = fi;
+            best_x = 0;  // unused: with s = 0 the cross term drops out
         }
     }
     // finalists (entries whose key can still reach the best, but the best
@@ -518,6 +550,7 @@ __device__ __forceinline__ void rescore_range(const Geometry &g, const EpiConst 
             if (better(er, idx, best_e, best_i)) {
                 best_e = er;
                 best_i = idx;
+                best_x = X;
             }
         }
     } else if (nfin > 0) {  // many finalists: one per lane
@@ -525,14 +558,16 @@ __device__ __forceinline__ void rescore_range(const Geometry &g, const EpiConst 
         __syncwarp();
         for (int f = lane; f < nfin; f += 32) {
             const uint32_t idx = (uint32_t)fl[f];
-            const U er = exact_rational<Wide>(g, st, di[idx >> 3], lane_cross(g, qblk, idx, bk));
+            const long long X = lane_cross(g, qblk, idx, bk);
+            const U er = exact_rational<Wide>(g, st, di[idx >> 3], X);
             if (better(er, idx, best_e, best_i)) {
                 best_e = er;
                 best_i = idx;
+                best_x = X;
             }
         }
     }
-    warp_argmin(best_e, best_i);
+    warp_argmin_x(best_e, best_i, best_x);
     // certified list: sbbc + (last - beta(last))/(2Ls) > E*, tested as
     // round-down(last - beta) > round-up((E* - sbbc) * 2Ls).  A full list's
     // unlisted candidates have residual >= its last key less the allowance at
@@ -555,7 +590,10 @@ __device__ __forceinline__ void rescore_range(const Geometry &g, const EpiConst 
     int nfail = __popc(failing);
     for (int off = 16; off > 0; off >>= 1) nfail += __shfl_xor_sync(0xffffffffu, nfail, off);
     if (nfail == 0) {
-        if (lane == 0) winner[r] = best_i;
+        if (lane == 0) {
+            winner[r] = best_i;
+            winx[r] = best_x;
+        }
         return;
     }
     Partial *sp = sb.part + (size_t)r * max_lists;
@@ -583,18 +621,22 @@ __device__ __forceinline__ void rescore_blocks(const Geometry &g, const EpiConst
                                                const ListEntry *lists, int max_lists, const int *counts,
                                                const int *act, const int *rkeep, int lists_per_split, int col_tile,
                                                int target, int max_split, int exact_scan, uint32_t *winner,
-                                               int *fb_list, int *fb_count, int *fb_done, const SpanBufs &sb)
+                                               long long *winx, int *fb_list, int *fb_count, int *fb_done,
+                                               const SpanBufs &sb)
 {
     extern __shared__ int bk_all[];  // [warps][8][m+1]
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < g.R; r += gridDim.x * blockDim.x) {
-        if (!rkeep[r]) winner[r] = 0;
+        if (!rkeep[r]) {
+            winner[r] = 0;
+            winx[r] = unscreened_cross(g, ri[r], di);
+        }
         fb_done[r] = 0;  // completion counters of the exact fallback
     }
     int *bk = bk_all + (threadIdx.x >> 5) * rescore_warp_ints(g.m);
     const int nkept = counts[0];
     for (int j = blockIdx.x * kRescoreWarps + (threadIdx.x >> 5); j < nkept; j += gridDim.x * kRescoreWarps)
         rescore_range<Wide>(g, ec, ri, di, bblk, qblk, lists, max_lists, counts, lists_per_split, col_tile, target,
-                            max_split, exact_scan, winner, fb_list, fb_count, act[j], bk, sb);
+                            max_split, exact_scan, winner, winx, fb_list, fb_count, act[j], bk, sb);
 }
 
 template <bool Wide>
@@ -602,11 +644,11 @@ __global__ void __launch_bounds__(32 * kRescoreWarps, 4)
     k_rescore(Geometry g, EpiConst ec, const RangeInfo *ri, const DomainInfo *di, const uint16_t *bblk,
               const uint16_t *qblk, const ListEntry *lists, int max_lists, const int *counts, const int *act,
               const int *rkeep, int lists_per_split, int col_tile, int target, int max_split, int exact_scan,
-              uint32_t *winner, int *fb_list, int *fb_count, int *fb_done, SpanBufs sb)
+              uint32_t *winner, long long *winx, int *fb_list, int *fb_count, int *fb_done, SpanBufs sb)
 {
     grid_dep_sync();
     rescore_blocks<Wide>(g, ec, ri, di, bblk, qblk, lists, max_lists, counts, act, rkeep, lists_per_split, col_tile,
-                         target, max_split, exact_scan, winner, fb_list, fb_count, fb_done, sb);
+                         target, max_split, exact_scan, winner, winx, fb_list, fb_count, fb_done, sb);
 }
 
 // Batched: one grid of persistent blocks over the ranges of all slices (in
@@ -627,7 +669,10 @@ __global__ void __launch_bounds__(32 * kRescoreWarps, 4)
             while (s + 1 < n && gi >= ctx[s + 1].r_begin) ++s;
             const EncBufs &b = ctx[s].b;
             const int r = gi - ctx[s].r_begin;
-            if (!b.cb.rkeep[r]) b.winner[r] = 0;
+            if (!b.cb.rkeep[r]) {
+                b.winner[r] = 0;
+                b.winx[r] = unscreened_cross(ctx[s].g, b.ri[r], b.di);
+            }
             fallback_done(ctx[s].g, b.partial)[r] = 0;
         }
     }
@@ -642,7 +687,7 @@ __global__ void __launch_bounds__(32 * kRescoreWarps, 4)
         if (j >= b.cb.counts[0]) continue;  // the screened ranges are the first counts[0]
         int *bk = bk_all + (threadIdx.x >> 5) * rescore_warp_ints(c.g.m);
         rescore_range<Wide>(c.g, c.ec, b.ri, b.di, b.bblk, b.qblk, b.lists, c.n_lists, b.cb.counts, lists_per_split,
-                            col_tile, c.target, c.n_split, exact_scan, b.winner, b.fb_list, b.fb_count,
+                            col_tile, c.target, c.n_split, exact_scan, b.winner, b.winx, b.fb_list, b.fb_count,
                             b.cb.act[j], bk, span_bufs(c.g, c.n_lists, b.span, b.fb_count + 2));
     }
 }
@@ -1033,14 +1078,23 @@ __device__ __forceinline__ void list_scans_warp(const Geometry &g, const EpiCons
 // pixel rows of the exact cross term.
 constexpr int kFinRanges = 32;
 constexpr int kFinWarps = 4;
+//
+// When the re-score left every settled winner's cross term (winx) for the
+// group, the maps need only the statistics (no staging): the usual case.
+// scans_write: the exact scans write the maps of the ranges they resolve
+// (winner bit 31), so this block leaves those out; otherwise (the batch,
+// whose scans ran before) their cross terms are computed here.
 template <bool Wide>
 __device__ __forceinline__ void finalize_block(const Geometry &g, const RangeInfo *ri, const DomainInfo *di,
                                                const uint16_t *bblk, const uint16_t *qblk, const uint32_t *winner,
-                                               const int *err, fic_map *maps, int bx)
+                                               const long long *winx, bool scans_write, const int *err,
+                                               fic_map *maps, int bx)
 {
     __shared__ uint32_t b_s[kFinRanges][(kMaxM + 2) / 2];
     __shared__ uint32_t q_s[kFinRanges][(kMaxM + 2) / 2];
     __shared__ uint32_t w_s[kFinRanges];
+    __shared__ long long xw_s[kFinRanges];
+    __shared__ int known_s;
     __shared__ long long x_s[kFinWarps][kFinRanges];
     __shared__ long long st_s[4][kFinRanges];  // Sq, Sqq of the winner's domain; Sb, Sbb of the range
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -1048,8 +1102,31 @@ __device__ __forceinline__ void finalize_block(const Geometry &g, const RangeInf
     const int nr = min(kFinRanges, g.R - r0);
     const int r = r0 + lane;
     const bool live = lane < nr;
-    if (warp == 0) w_s[lane] = live ? winner[r] : 0u;
+    if (warp == 0) {
+        const uint32_t w0 = live ? winner[r] : 0u;
+        const long long x0 = live ? winx[r] : 0;
+        w_s[lane] = w0;
+        xw_s[lane] = x0;
+        // no cross term needed here: no range, a winner the scans will decide
+        // (and write), one they resolved when they write it; else it must be known
+        const bool known = !live || win_pending(w0) || ((w0 & 0x80000000u) ? scans_write : x0 != kNoCross);
+        const unsigned all = __ballot_sync(0xffffffffu, known);
+        if (lane == 0) known_s = all == 0xffffffffu;
+    }
     __syncthreads();
+    if (known_s) {  // block-uniform
+        constexpr int kPer = kFinRanges / kFinWarps;
+        const int jr = warp * kPer + lane;
+        if (lane >= kPer || jr >= nr) return;
+        const uint32_t wj = w_s[jr];
+        if (win_pending(wj) || (wj & 0x80000000u)) return;  // the scans write it
+        uint32_t ij = wj;
+        if (ij >= (uint32_t)g.N) ij = 0;  // unreachable: every range has a winner
+        const RangeInfo rin = ri[r0 + jr];
+        const DomainInfo dd = di[ij >> 3];
+        write_map<Wide>(g, Stats{dd.Sq, dd.Sqq, rin.Sb, rin.Sbb, xw_s[jr]}, r0 + jr, wj, err, maps);
+        return;
+    }
     const uint32_t wv = w_s[lane];
     uint32_t idx = wv & 0x7fffffffu;
     if (idx >= (uint32_t)g.N) idx = 0;  // unreachable: every range has a winner
@@ -1129,14 +1206,15 @@ __global__ void __launch_bounds__(32 * kFinWarps) k_scans_finalize(Geometry g, c
                                                                    int *done, const int *counts, const int *dmap,
                                                                    int col_tile, int target, int max_split,
                                                                    int lists_per_split, int max_lists, SpanBufs sb,
-                                                                   uint32_t *winner, const int *err, fic_map *maps,
-                                                                   EpiConst ec, const float4 *dconst)
+                                                                   uint32_t *winner, const long long *winx,
+                                                                   const int *err, fic_map *maps, EpiConst ec,
+                                                                   const float4 *dconst)
 {
     extern __shared__ int scan_sm[];  // [warps][8 (m+1)]
     grid_dep_sync();
     const int groups = (g.R + kFinRanges - 1) / kFinRanges;
     for (int gb = blockIdx.x; gb < groups; gb += gridDim.x) {
-        finalize_block<Wide>(g, ri, di, bblk, qblk, winner, err, maps, gb);
+        finalize_block<Wide>(g, ri, di, bblk, qblk, winner, winx, true, err, maps, gb);
         __syncthreads();  // the block's staging is reused by its next group
     }
     full_scans<Wide>(g, ri, di, bblk, qblk, fb_list, fb_count, nch, part, done, winner, blockIdx.x, gridDim.x, err,
@@ -1232,7 +1310,7 @@ __global__ void __launch_bounds__(32 * kFinWarps) k_finalize_batch(const SliceCt
     const SliceCtx c = ctx[blockIdx.y];
     if ((int)blockIdx.x * kFinRanges >= c.g.R) return;
     const EncBufs &b = c.b;
-    finalize_block<Wide>(c.g, b.ri, b.di, b.bblk, b.qblk, b.winner, b.err, c.maps, blockIdx.x);
+    finalize_block<Wide>(c.g, b.ri, b.di, b.bblk, b.qblk, b.winner, b.winx, false, b.err, c.maps, blockIdx.x);
 }
 
 
@@ -1240,8 +1318,8 @@ cudaError_t launch_rescore(const Geometry &g, const EpiConst &ec, const RangeInf
                            const DomainInfo *di, const uint16_t *bblk, const uint16_t *qblk,
                            const ListEntry *lists, int max_lists, const int *counts, const int *act,
                            const int *rkeep, int lists_per_split, int col_tile, int target, int max_split, int n_sm,
-                           int exact_scan, uint32_t *winner, int *fb_list, int *fb_count, void *partial, void *span,
-                           cudaStream_t st)
+                           int exact_scan, uint32_t *winner, long long *winx, int *fb_list, int *fb_count,
+                           void *partial, void *span, cudaStream_t st)
 {
     const SpanBufs sb = span_bufs(g, max_lists, span, fb_count + 2);
     const size_t smem = sizeof(int) * kRescoreWarps * rescore_warp_ints(g.m);
@@ -1250,7 +1328,7 @@ cudaError_t launch_rescore(const Geometry &g, const EpiConst &ec, const RangeInf
     if (max_lists * kListK > 32 * kRescoreEnt) return cudaErrorInvalidValue;
     return launch_dep(g.wide ? k_rescore<true> : k_rescore<false>, dim3(blocks), dim3(32 * kRescoreWarps), smem, st,
                       g, ec, ri, di, bblk, qblk, lists, max_lists, counts, act, rkeep, lists_per_split, col_tile,
-                      target, max_split, exact_scan, winner, fb_list, fb_count, fallback_done(g, partial), sb);
+                      target, max_split, exact_scan, winner, winx, fb_list, fb_count, fallback_done(g, partial), sb);
 }
 
 
@@ -1264,8 +1342,9 @@ size_t fallback_partial_bytes(const Geometry &g)
 cudaError_t launch_scans_finalize(const Geometry &g, const RangeInfo *ri, const DomainInfo *di, const uint16_t *bblk,
                                   const uint16_t *qblk, const int *fb_list, int *fb_count, void *partial,
                                   const int *counts, const int *dmap, int col_tile, int target, int max_split,
-                                  int lists_per_split, int max_lists, void *span, uint32_t *winner, const int *err,
-                                  fic_map *maps, const EpiConst &ec, const float4 *dconst, int n_sm, cudaStream_t st)
+                                  int lists_per_split, int max_lists, void *span, uint32_t *winner,
+                                  const long long *winx, const int *err, fic_map *maps, const EpiConst &ec,
+                                  const float4 *dconst, int n_sm, cudaStream_t st)
 {
     const int nch = fallback_chunks(g);
     Partial *part = reinterpret_cast<Partial *>(partial);
@@ -1279,7 +1358,7 @@ cudaError_t launch_scans_finalize(const Geometry &g, const RangeInfo *ri, const 
     const int blocks = std::max((g.R + kFinRanges - 1) / kFinRanges, 3 * n_sm);
     return launch_dep(kern, dim3(blocks), dim3(32 * kFinWarps), smem, st, g, ri, di, bblk, qblk, fb_list,
                       (const int *)fb_count, nch, part, fallback_done(g, partial), counts, dmap, col_tile, target,
-                      max_split, lists_per_split, max_lists, sb, winner, err, maps, ec, dconst);
+                      max_split, lists_per_split, max_lists, sb, winner, winx, err, maps, ec, dconst);
 }
 
 // Batched re-score and exact scans of n slices (max_m: the pixels per range,
