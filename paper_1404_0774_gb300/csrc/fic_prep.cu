@@ -912,9 +912,13 @@ __global__ void __launch_bounds__(T, T == 512 ? 2 : 1) k_compact_seed_batch(cons
 constexpr int kRsWarps = 16;             // warps per block (two blocks per SM)
 constexpr int kRsMaxStatBlocks = 8192;   // statistics blocks a block can scan
 
-__host__ __device__ constexpr int rows_seed_ints(int m, int nsb)
+// Shared ints of a block: the seed areas, the prefix sums, scan scratch, the
+// items of the block's row units (rounds: an upper bound of the units per
+// block and warp, from the largest possible number of kept items) and the
+// list of its screened ranges to seed (seeds: the ranges a block owns).
+__host__ __device__ constexpr int rows_seed_ints(int m, int nsb, int rounds, int seeds)
 {
-    return kRsWarps * seed_warp_ints(m) + nsb + 1 + 2 * kRsWarps + 2;
+    return kRsWarps * seed_warp_ints(m) + nsb + 1 + 2 * kRsWarps + 2 + kRsWarps * rounds + seeds;
 }
 
 // Position of the t-th (from 0) set bit of x (t < popc(x)).
@@ -1014,6 +1018,40 @@ __global__ void __launch_bounds__(32 * kRsWarps, 2)
     if (nsb == 0 && threadIdx.x == 0) E[0] = 0;
     __syncthreads();
     const int nr = E[rbs], nd = E[nsb] - E[rbs];
+    // the block owns row units u = b kRsWarps + i + k W (i < kRsWarps, warp i
+    // takes them); their items (range or domain ids) are found once here, a
+    // thread per unit, rather than by each warp per unit
+    const int W = gridDim.x * kRsWarps;
+    const int T = nr + nd;
+    int *items = first + 2;
+    int *slist = items + kRsWarps * ((g.R + g.D + W - 1) / W);  // screened ranges to seed
+    __shared__ int nseed_s;
+    if (seed && warp == 0) {
+        // the block's ranges b, b + G, b + 2 G, ...: the screened ones, in order
+        int cnt = 0;
+        for (int r0 = blockIdx.x; r0 < g.R; r0 += 32 * gridDim.x) {
+            const int r = r0 + lane * gridDim.x;
+            const bool k = r < g.R && rkeep[r] != 0;
+            const unsigned bal = __ballot_sync(0xffffffffu, k);
+            if (k) slist[cnt + __popc(bal & ((1u << lane) - 1u))] = r;
+            cnt += __popc(bal);
+        }
+        if (lane == 0) nseed_s = cnt;
+    }
+    {
+        const int u0 = blockIdx.x * kRsWarps;
+        const int K = T > u0 ? (T - u0 + W - 1) / W : 0;
+        for (int q = threadIdx.x; q < K * kRsWarps; q += blockDim.x) {
+            const int u = u0 + (q % kRsWarps) + (q / kRsWarps) * W;
+            int it = -1;
+            if (u < nr)
+                it = kept_item(E, 0, rbs, u, bmask, per);
+            else if (u < T)
+                it = kept_item(E, rbs, nsb, u - nr, bmask, per);
+            items[q] = it;
+        }
+    }
+    __syncthreads();
     if (blockIdx.x == 0) {
         // the first range (domain) that is not kept, as the compaction
         // reports it: blocks whose count is below their valid items
@@ -1043,34 +1081,32 @@ __global__ void __launch_bounds__(32 * kRsWarps, 2)
             counts[3] = first[1] == 0x7fffffff ? -1 : first[1];
         }
     }
-    // seeds: block b takes ranges b, b + G, ..., b + 15 G, its warps the
-    // screened ones in order
+    // seeds: the block's screened ranges (listed above), warp w takes
+    // entries w, w + kRsWarps, ...
     if (seed) {
-        const int G = gridDim.x, b = blockIdx.x;
-        const int rl = lane < 16 ? lane * G + b : g.R;
-        unsigned kept = __ballot_sync(0xffffffffu, rl < g.R && rkeep[rl] != 0);
-        if (warp < __popc(kept)) {  // warp-uniform
-            for (int t = 0; t < warp; ++t) kept &= kept - 1;
-            const int r = (__ffs(kept) - 1) * G + b;
-            seed_range(g, ec, ri, di, dconst, bblk, qblk, tbest, r, lane, wsm,
+        const int ns = nseed_s;
+        for (int e = warp; e < ns; e += kRsWarps) {
+            __syncwarp();  // the warp's previous seed area is read
+            seed_range(g, ec, ri, di, dconst, bblk, qblk, tbest, slist[e], lane, wsm,
                        reinterpret_cast<uint2 *>(wsm + 8 * (m + 4)));
-            __syncwarp();  // the seed area becomes the row staging
         }
+        __syncwarp();  // the seed area becomes the row staging
     }
     // operand rows: warp units over the grid, the kept ranges' rows first
     const RowLane rl = row_lane<LN>(lane);
     uint16_t *st = reinterpret_cast<uint16_t *>(wsm);
-    const int W = gridDim.x * kRsWarps;
-    for (int u = blockIdx.x * kRsWarps + warp; u < nr + nd; u += W) {
+    for (int k = 0;; ++k) {
+        const int u = blockIdx.x * kRsWarps + warp + k * W;
+        if (u >= T) break;
+        const int it = items[k * kRsWarps + warp];
+        if (it < 0) continue;  // unreachable: counts and masks come from one statistics launch
         if (u < nr) {
-            const int r = kept_item(E, 0, rbs, u, bmask, per);
-            if (r < 0) continue;  // unreachable: counts and masks come from one statistics launch
+            const int r = it;
             if (lane == 0) act[u] = r;
             range_row<LN, SPLIT>(ri, bblk, u, r, lane, rs32, ra16);
         } else {
             const int j = u - nr;
-            const int d = kept_item(E, rbs, nsb, j, bmask, per);
-            if (d < 0) continue;
+            const int d = it;
             if (lane == 0) dact[j] = d;
             __syncwarp();  // the staging of the warp's previous domain is read
             domain_rows_warp<LN, SPLIT>(di, qblk, dconst, j, d, lane, rl, st, cb32, cb16, dconst_c, dmap);
@@ -1144,10 +1180,12 @@ cudaError_t launch_prep(const Geometry &g, const void *img, const EpiConst &ec, 
     });
     if (e != cudaSuccess) return e;
     if (fused) {
-        const size_t smem = sizeof(int) * (size_t)rows_seed_ints(g.m, nsb);
-        // every range in some block's 16 seed slots; at least the resident
-        // blocks (two per SM) for the rows
-        const int blocks = std::max((g.R + 15) / 16, 2 * prep_sms());
+        // one wave: the resident blocks (two per SM)
+        const int blocks = 2 * prep_sms();
+        const int W = blocks * kRsWarps;
+        const int rounds = (g.R + g.D + W - 1) / W;  // row units a warp takes, at most
+        const int seeds = (g.R + blocks - 1) / blocks;  // ranges a block owns
+        const size_t smem = sizeof(int) * (size_t)rows_seed_ints(g.m, nsb, rounds, seeds);
         return with_rows_seed_kernel(g, [&](auto kern) {
             cudaError_t e2 = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e2 != cudaSuccess) return e2;
