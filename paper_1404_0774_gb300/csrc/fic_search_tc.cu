@@ -11,7 +11,9 @@
 // 64 elements, SWIZZLE_128B; 4x4 ranges: 16 elements, SWIZZLE_32B) plus one
 // 16-element SWIZZLE_32B tail block carrying the centring terms.  For 12-bit
 // images the hi and lo blocks go to separate TMEM accumulators, whose sums
-// are exact, and the tail's centring term is folded in by the epilogue.
+// are exact (one MMA of 2 x 64 candidate rows per K step: a B stage holds the
+// tile's hi rows and then its lo rows), and the tail's centring term is
+// folded in by the epilogue.
 // 16x16 ranges (K = 256 per copy): the range pixels are staged once as four
 // 64-element boxes that every part's MMAs read, the candidate rows stream
 // through a ring of one-box stages (a tile is parts x 4 stages), the tail is
@@ -19,16 +21,18 @@
 // FP32 accumulation over K = 256 may round: the statistics kernel widens the
 // screening allowances for it.
 //
-// CTA = 128 ranges (one per TMEM lane), streaming a contiguous slice of the
-// candidate dimension in tiles of 96:
-//   warp 0        TMA producer (one thread): A once per item, B tiles into a
-//                 3-stage ring (16x16 ranges: B boxes into a 7-stage ring)
-//   warp 1        TMEM allocator + MMA issuer (one thread): m/16 tcgen05.mma
-//                 kind::f16 128x96x16 per pixel block (+1 tail for 8-bit)
-//                 per tile into one of two TMEM accumulator sets
+// Persistent CTA, one per SM.  A work item is a row tile of 128 screened
+// ranges (one per TMEM lane) against one split of the candidate columns,
+// streamed in 192-column super-tiles of three 64-column MMA tiles:
+//   warp 0        TMA producer (one thread): the item queue, A once per item,
+//                 B tiles into a 4-stage ring (16x16 ranges: B boxes into a
+//                 7-stage ring)
+//   warp 1        TMEM allocator + MMA issuer (one thread): tcgen05.mma
+//                 kind::f16 128xNx16 per K step of every MMA tile into a ring
+//                 of four TMEM accumulator slots
 //   warps 2..13   epilogue, three per TMEM lane quadrant (three per scheduler
-//                 with the register budget of 14 warps): each takes 32
-//                 columns of every tile, FP32 screening (eq 8-12 with
+//                 with the register budget of 14 warps): part p takes MMA
+//                 tile p of every super-tile, FP32 screening (eq 8-12 with
 //                 quantisation), per-range candidate lists
 // Every mbarrier wait is bounded by a wall-clock limit; on expiry the CTA sets
 // an error flag, stops, drains its outstanding TMA loads (bounded), frees its
@@ -111,7 +115,7 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
     return ok != 0;
 }
 
-// try_wait whose suspension is capped at `hint_ns` (used with short limits).
+// try_wait whose suspension is capped at `hint_ns`.
 __device__ __forceinline__ bool mbar_try_wait_hint(uint64_t *bar, uint32_t parity, uint32_t hint_ns)
 {
     uint32_t ok;
@@ -125,8 +129,16 @@ __device__ __forceinline__ bool mbar_try_wait_hint(uint64_t *bar, uint32_t parit
     return ok != 0;
 }
 
+// Longest suspension of one try_wait in a pipeline wait.  The thread wakes
+// as soon as the phase completes, so the hint costs nothing in latency; it
+// keeps a waiting role from re-issuing try_wait in a loop, which takes issue
+// slots from the epilogue warps on the same scheduler (measured: 2 us less
+// search time on the 512x512 slice than unhinted try_wait).
+constexpr uint32_t kSuspendHintNs = 50000u;
+
 // Limits below this are honoured to the timer's resolution: each try_wait
-// suspends for at most the limit and the clock is read after every one.
+// suspends for at most the limit and the clock is read after every one
+// (otherwise after every 64th).
 constexpr unsigned long long kShortWaitNs = 1000000ull;
 
 // Bounded wait for the phase of `parity` to complete.  Returns false when the
@@ -139,7 +151,9 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volati
     const unsigned long long t0 = gtimer();
     const bool short_wait = wait_ns < kShortWaitNs;
     for (uint32_t i = 1;; ++i) {
-        if (short_wait ? mbar_try_wait_hint(bar, parity, (uint32_t)wait_ns) : mbar_try_wait(bar, parity)) return true;
+        if (short_wait ? mbar_try_wait_hint(bar, parity, (uint32_t)wait_ns)
+                       : mbar_try_wait_hint(bar, parity, kSuspendHintNs))
+            return true;
         if (short_wait || (i & 63) == 0) {
             if (*abort_s) return false;
             if (gtimer() - t0 > wait_ns) {
@@ -420,6 +434,7 @@ __device__ __forceinline__ void search_tc_run(const TcMaps &maps, const SliceCtx
     constexpr int KSTEPS = NBLK * KPB + 1;
     constexpr uint32_t SBO = BW == 64 ? 1024 : 256, LAYOUT = BW == 64 ? 2 : 6;
     constexpr uint32_t IDESC = instr_desc(BM, BN);
+    constexpr uint32_t IDESC2 = instr_desc(BM, 2 * BN);  // 12-bit: a stage's hi and lo rows as one operand
     // 12-bit: the hi and lo parts of q' accumulate separately (each sum is
     // exact in FP32: multiples of 128 below 2^31, integers below 2^23) and the
     // centring correction is folded into the epilogue, so the only rounding
@@ -430,6 +445,11 @@ __device__ __forceinline__ void search_tc_run(const TcMaps &maps, const SliceCtx
     // the tail MMA)
     constexpr bool CORR_EPI = PARTS == 2 || KB > 1;
     constexpr uint32_t ACC_COLS = BN * PARTS;
+    // bytes the MMAs read (the expected transaction counts): 12-bit items load
+    // only A block 0 (both parts multiply the same range pixels) and no tail
+    // boxes (the correction is the epilogue's)
+    constexpr uint32_t A_TX = KB > 1 ? KB * A_BLK : (PARTS == 2 ? A_BLK : NBLK * A_BLK + BM * 32);
+    constexpr uint32_t B_TX = KB > 1 ? B_BLK : (CORR_EPI ? NBLK * B_BLK : NBLK * B_BLK + BN * 32);
     constexpr uint32_t TMEM_COLS = ACC_COLS * NACC <= 256 ? 256 : 512;  // allocation: a power of two
 
     extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -560,8 +580,10 @@ __device__ __forceinline__ void search_tc_run(const TcMaps &maps, const SliceCtx
                 }
                 // the previous item's MMAs must be done with A
                 if (kitem > 0 && !mbar_wait(&a_empty, (kitem - 1) & 1, &abort_s, err, wait_ns)) break;
-                mbar_expect_tx(&a_full, A_BYTES);
-                if constexpr (KB == 1) {
+                mbar_expect_tx(&a_full, A_TX);
+                if constexpr (KB == 1 && PARTS == 2) {
+                    tma_load_2d(sA, &maps.a128, 0, c.abase + w.r0, &a_full);
+                } else if constexpr (KB == 1) {
 #pragma unroll
                     for (int b = 0; b < NBLK; ++b)
                         tma_load_2d(sA + b * A_BLK, &maps.a128, BW * b, c.abase + w.r0, &a_full);
@@ -579,10 +601,10 @@ __device__ __forceinline__ void search_tc_run(const TcMaps &maps, const SliceCtx
                         const int s = bseq % NSTG;
                         if (!(ok = mbar_wait(&empty_bar[s], ((bseq / NSTG) & 1) ^ 1, &abort_s, err, wait_ns))) break;
                         uint8_t *dst = sB + s * B_BYTES;
-                        mbar_expect_tx(&full_bar[s], B_BYTES);
+                        mbar_expect_tx(&full_bar[s], B_TX);
 #pragma unroll
                         for (int b = 0; b < NBLK; ++b) tma_load_2d(dst + b * B_BLK, &maps.b128, BW * b, y, &full_bar[s]);
-                        tma_load_2d(dst + NBLK * B_BLK, &maps.b32, BW * NBLK, y, &full_bar[s]);
+                        if constexpr (!CORR_EPI) tma_load_2d(dst + NBLK * B_BLK, &maps.b32, BW * NBLK, y, &full_bar[s]);
                         ++bseq;
                     } else {
                         // part p, box b: columns 64 (p KB + b) of the candidate rows
@@ -590,7 +612,7 @@ __device__ __forceinline__ void search_tc_run(const TcMaps &maps, const SliceCtx
                             const int s = bseq % NSTG;
                             if (!(ok = mbar_wait(&empty_bar[s], ((bseq / NSTG) & 1) ^ 1, &abort_s, err, wait_ns)))
                                 break;
-                            mbar_expect_tx(&full_bar[s], B_BYTES);
+                            mbar_expect_tx(&full_bar[s], B_TX);
                             tma_load_2d(sB + s * B_BYTES, &maps.b128, BW * pb, y, &full_bar[s]);
                             ++bseq;
                         }
@@ -641,22 +663,28 @@ __device__ __forceinline__ void search_tc_run(const TcMaps &maps, const SliceCtx
                         if (!(ok = mbar_wait(&full_bar[s], (bseq / NSTG) & 1, &abort_s, err, wait_ns))) break;
                         tc_fence_after();
                         const uint32_t b_base = b_base0 + s * B_BYTES;
+                        if constexpr (PARTS == 2) {
+                            // The stage's hi block (candidate rows 0..BN-1) and lo block (the same
+                            // candidates' lo parts, rows BN..2BN-1) lie one after the other in whole
+                            // 8-row groups, so they are one operand of 2 BN rows against the range
+                            // pixels (A block 0): one MMA per K step puts hi in slot columns [0, BN)
+                            // and lo in [BN, 2 BN), half the MMA instructions of a pair per block.
 #pragma unroll
-                        for (int k = 0; k < KSTEPS; ++k) {
-                            if (CORR_EPI && k == NBLK * KPB) break;  // the correction is applied in the epilogue
-                            uint64_t ad, bd;
-                            const int blk = k / KPB, sub = k % KPB;
-                            if (k < NBLK * KPB) {
-                                ad = smem_desc(a_base + blk * A_BLK + sub * 32, SBO, LAYOUT);
-                                bd = smem_desc(b_base + blk * B_BLK + sub * 32, SBO, LAYOUT);
-                            } else {
-                                ad = smem_desc(a_base + NBLK * A_BLK, 256, 6);
-                                bd = smem_desc(b_base + NBLK * B_BLK, 256, 6);
-                            }
-                            if (PARTS == 2)  // block 0 (hi) -> slot columns [0, BN), block 1 (lo) -> [BN, 2 BN)
-                                umma_f16(d_tmem + blk * BN, ad, bd, IDESC, sub ? 1u : 0u);
-                            else
+                            for (int sub = 0; sub < KPB; ++sub)
+                                umma_f16(d_tmem, smem_desc(a_base + sub * 32, SBO, LAYOUT),
+                                         smem_desc(b_base + sub * 32, SBO, LAYOUT), IDESC2, sub ? 1u : 0u);
+                        } else {
+                            // 8-bit: the q' block, then the tail block with the centring terms
+#pragma unroll
+                            for (int k = 0; k < KSTEPS; ++k) {
+                                const bool tail = k == NBLK * KPB;
+                                const int blk = k / KPB, sub = k % KPB;
+                                const uint64_t ad = tail ? smem_desc(a_base + NBLK * A_BLK, 256, 6)
+                                                         : smem_desc(a_base + blk * A_BLK + sub * 32, SBO, LAYOUT);
+                                const uint64_t bd = tail ? smem_desc(b_base + NBLK * B_BLK, 256, 6)
+                                                         : smem_desc(b_base + blk * B_BLK + sub * 32, SBO, LAYOUT);
                                 umma_f16(d_tmem, ad, bd, IDESC, k > 0 ? 1u : 0u);
+                            }
                         }
                         umma_commit(&empty_bar[s]);  // smem stage free once these MMAs finish
                         ++bseq;
