@@ -151,6 +151,11 @@ EpiConst make_epi(const Geometry &g)
     ec.near_slack = (float)((32.0 * g.Ls * g.Ls + 16.0 * g.Ls) * 5.9604644775390625e-08);  // 2^-24
     const double dd = 4.0 * g.Ls * g.Lo;
     ec.invD2_up = std::nextafter((float)(1.0 / (dd * dd)), INFINITY);
+    // the residue w = z - round(z/G) G of the FP32 key: |w| <= G/2 plus the
+    // rounding of z*invG (2^-23 |z|, taken as 2^-22 zmax), lambda w^2 then
+    // rounded once more
+    const double wmax = 0.5 * g.G + zmax * 2.384185791015625e-07;
+    ec.qmax = (float)(lambda * wmax * wmax * 1.001 + 1.0);
     return ec;
 }
 

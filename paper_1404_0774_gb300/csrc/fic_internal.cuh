@@ -121,6 +121,7 @@ struct EpiConst {
     float inv4ls, invm, pmax;  // 1/(4*Ls), 1/m, P (offset clamp detection)
     float near_slack;   // kappa * near_slack bounds how far below c*y the key of the other code can fall
     float invD2_up;     // FP32 upper bound of 1/(4*Ls*Lo)^2 (exact residuals are integers / D^2)
+    float qmax;         // upper bound of the offset term lambda*w^2 of any candidate's key (w the o-grid residue)
 };
 
 // Per-thread constants of the range the thread screens.

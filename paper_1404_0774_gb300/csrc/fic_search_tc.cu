@@ -302,8 +302,16 @@ __device__ __forceinline__ DcPack dc_pack(const float4 &c4, const EpiConst &ec)
 }
 
 // epi_keys32<true> of fic_internal.cuh (the near-boundary candidates go to the
-// rare pass, the mask is assembled from sign bits) on the packed constants:
-// the keys and the mask are bit-identical to it.  kZero: add the penalty to
+// rare pass, the mask is assembled from sign bits) on the packed constants,
+// with the threshold folded into the key: the sign of
+// lambda w^2 + (c y - thr') replaces that of (c y + lambda w^2) - thr, one
+// instruction less per pair of candidates.  The mask only chooses what the
+// rare pass visits (which recomputes each key as epi_key does), so it may hold
+// more candidates, never fewer: with P = c y and Q = (lambda w) w exact, the
+// key k = RN(Q + RN(P)) is below thr only if P + Q < thr + u(|P| + |thr|);
+// near the sign change |P| <= |thr'| + qmax, so thr' = thr + 2^-21 (|thr| +
+// qmax) exceeds every rounding of both forms (u = 2^-24) and
+// RN(Q + RN(P - thr')) < 0 whenever k < thr.  kZero: add the penalty to
 // s-code-0 keys (zp); the caller takes the variant without it when no lane of
 // the warp can list an s-code-0 candidate (the key of every s-code-0
 // candidate of a range is the same value K0; without the penalty those keys
@@ -313,7 +321,8 @@ __device__ __forceinline__ uint32_t epi_keys32_tc(const float (&X)[32], const Dc
                                                   f32x2_t er2, const EpiConst &ec, float thr, float zp)
 {
     uint32_t mask = 0, far = 0;  // bit-reversed masks of k < thr, of |rho| below the band
-    const f32x2_t thr2 = pk2(thr, thr);
+    const float thr_up = __fadd_ru(thr, __fmul_ru(__fadd_ru(fabsf(thr), ec.qmax), 4.76837158203125e-07f));  // 2^-21
+    const f32x2_t mthr = pk2(-thr_up, -thr_up);
     const float mlim2 = -__fmul_rd(rho_lim, rho_lim);
     const f32x2_t mlim = pk2(mlim2, mlim2);
     const f32x2_t two_ls = pk2(ec.two_ls, ec.two_ls), mls = pk2(-ec.ls, -ec.ls);
@@ -341,17 +350,16 @@ __device__ __forceinline__ uint32_t epi_keys32_tc(const float (&X)[32], const Dc
             const f32x2_t e = sub2(fma2(z, invg, mag), mag);
             const f32x2_t wv = fma2(e, mg, z);
             const f32x2_t y = fma2(c, kap, sub2(mcorr, x));
-            const f32x2_t cy = mul2(c, y);
-            f32x2_t k = fma2(mul2(wv, lam), wv, cy);
+            f32x2_t d = fma2(mul2(wv, lam), wv, fma2(c, y, mthr));  // key - thr'
             if (kZero) {
                 float c0, c1;
                 upk2(c, c0, c1);
                 const float zero0 = __saturatef(fmaf(c0, -c0, 1.0f));  // 1 for c = 0, else 0
                 const float zero1 = __saturatef(fmaf(c1, -c1, 1.0f));
-                k = fma2(pk2(zero0, zero1), zpp, k);
+                d = fma2(pk2(zero0, zero1), zpp, d);
             }
             float d0, d1, t0, t1;
-            upk2(sub2(k, thr2), d0, d1);
+            upk2(d, d0, d1);
             upk2(fma2(rho, rho, mlim), t0, t1);
             mask = __funnelshift_l(__float_as_uint(d0), mask, 1);  // (mask << 1) | sign bit
             mask = __funnelshift_l(__float_as_uint(d1), mask, 1);
