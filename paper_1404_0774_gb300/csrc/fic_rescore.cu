@@ -578,13 +578,29 @@ __device__ __forceinline__ void rescore_range(const Geometry &g, const EpiConst 
     // a list that fails the test is re-scanned exactly over its own candidates
     // (the columns the search gave it); the winner is then the best of those
     // scans and of the finalists above
-    uint32_t failing = 0;  // bit q: this lane's list (lane/4 + 8q) failed
-    if ((lane & (kListK - 1)) == kListK - 1) {
+    // The last entries sit on lanes 3, 7, ..., 31 (8 of them for each q); each
+    // lane takes those of 4 values of q, gathered by shuffles, so that all 32
+    // lanes test 4 lists instead of 8 lanes testing 16.  Lane l tests, for
+    // q = l/8 + 4t, the list (l % 8) + 8q held by lane 4 (l % 8) + 3.
+    static_assert(kListK == 4 && kRescoreEnt == 16, "certification: 8 list ends per entry row, 4 rows a lane");
+    uint32_t failing = 0;  // bit q: list (lane % 8) + 8q failed
+    {
+        const int src = 4 * (lane & 7) + kListK - 1, q0 = lane >> 3;
+        float lk[4];
+        uint32_t li[4];
 #pragma unroll
         for (int q = 0; q < kRescoreEnt; ++q) {
-            const ListEntry last = ent[q];
-            if (last.idx == 0xffffffffu) continue;  // list not full (or past the end)
-            if (!(__fsub_rd(last.key, beta_key(re, last.key, ec)) > kcert)) failing |= 1u << q;
+            const float k = __shfl_sync(0xffffffffu, ent[q].key, src);
+            const uint32_t i = __shfl_sync(0xffffffffu, ent[q].idx, src);
+            if ((q & 3) == q0) {
+                lk[q >> 2] = k;
+                li[q >> 2] = i;
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            if (li[t] == 0xffffffffu) continue;  // list not full (or past the end)
+            if (!(__fsub_rd(lk[t], beta_key(re, lk[t], ec)) > kcert)) failing |= 1u << (q0 + 4 * t);
         }
     }
     int nfail = __popc(failing);
@@ -606,7 +622,7 @@ __device__ __forceinline__ void rescore_range(const Geometry &g, const EpiConst 
     while (failing) {
         const int q = __ffs(failing) - 1;
         failing &= failing - 1;
-        const int l = (lane >> 2) + 8 * q;
+        const int l = (lane & 7) + 8 * q;
         sb.items[atomicAdd(sb.count, 1)] = (r << 7) | l;
     }
 }
