@@ -33,6 +33,10 @@ WORKLOAD = ("512x512 12-bit CT-like synthetic slice; 8x8 ranges (4096); 16x16 do
             "(15625) x 8 symmetries; s 5-bit, o 7-bit")
 METRIC = "range-domain comparisons/s"
 CLOCK_WINDOW_S = 1.0
+# untimed warm-up: the W steps asked for, and more of the same step until this
+# much wall time has passed (a fresh process's first fraction of a second of
+# GPU work runs slower than the steady state)
+WARMUP_MIN_S = 0.3
 # FP32 operations of the screening key per candidate (the epilogue's
 # algorithmic work): s code 4 (scale + saturate, map to the code grid, round
 # by magic add, subtract), o residue 4 (z, e: scale + round, w), key 4
@@ -51,6 +55,19 @@ def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
+
+
+def warm_up(step, w, sync):
+    """W untimed steps (at least 3), continued until WARMUP_MIN_S of wall time
+    has passed; returns the number of steps run."""
+    n, t0 = 0, time.time()
+    while n < max(3, w) or time.time() - t0 < WARMUP_MIN_S:
+        step()
+        n += 1
+        if n % 16 == 0:
+            sync()
+    sync()
+    return n
 
 
 def rank_seed(rank):
@@ -373,9 +390,8 @@ def run_quadtree(args):
     def step():
         return fic.encode_quadtree(img, p, 4, 8.0, maps=maps, workspace=work, stream=stream)[1]
 
-    for _ in range(max(3, args.warmup)):  # the first call also times the launch shapes of each level
-        step()
-    torch.cuda.synchronize()
+    # the first call also times the launch shapes of each level
+    n_warm = warm_up(step, args.warmup, torch.cuda.synchronize)
     comps, per_level = quadtree_comparisons(fic, fic.last_quadtree_stats())
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     if ws > 1:
@@ -458,7 +474,8 @@ def run_quadtree(args):
             "warmup": max(3, args.warmup), "ms_per_step": 1e3 * t_total / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "fp16+fp32", "data": "synthetic",
             "config": {"workload": QT_WORKLOAD, "leaves": int(n_leaves), "comparisons_per_step": comps,
-                       "levels": per_level, "l2": "flushed (256 MB write) between steps"},
+                       "levels": per_level, "l2": "flushed (256 MB write) between steps",
+                       "warmup_untimed": {"steps": n_warm, "min_s": WARMUP_MIN_S}},
             "e2e": {"value": job_rate(ws, args.steps, comps, e2e_t), "unit": "comparisons/s",
                     "h2d_bytes_per_step": N_PIX * N_PIX * 2, "d2h_bytes_per_step": int(n_leaves) * 56,
                     "timing": "host wall clock (the call waits for its stream)"},
@@ -535,9 +552,8 @@ def run_volume(args):
     for a in stack:
         R, D = fic.counts(a.shape[1], a.shape[0], p)
         comps += R * D * 8
-    for _ in range(max(3, args.warmup)):  # the first call runs eagerly and captures the graph
-        fic.encode_batch(tab, p, work, stream)
-    torch.cuda.synchronize()
+    # the first call runs eagerly and captures the graph
+    n_warm = warm_up(lambda: fic.encode_batch(tab, p, work, stream), args.warmup, torch.cuda.synchronize)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     lat = []
     if ws_n > 1:
@@ -616,6 +632,7 @@ def run_volume(args):
             "warmup": max(3, args.warmup), "ms_per_step": 1e3 * t_total / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "fp16+fp32", "data": "synthetic",
             "config": {"workload": VOL_WORKLOAD, "slices": n_sl, "comparisons_per_step": comps,
+                       "warmup_untimed": {"steps": n_warm, "min_s": WARMUP_MIN_S},
                        "comparisons_per_s": job_rate(ws_n, args.steps, comps, t_total),
                        "slice_latency_ms": {"p50": float(np.percentile(lat, 50)),
                                             "p99": float(np.percentile(lat, 99)), "max": float(lat.max()),
@@ -845,9 +862,7 @@ def main():
     def step():
         fic.encode(img, p, maps=maps, workspace=work, stream=stream)
 
-    for _ in range(max(3, args.warmup)):
-        step()
-    torch.cuda.synchronize()
+    n_warm = warm_up(step, args.warmup, torch.cuda.synchronize)
     launches_per_step = 5  # statistics, compaction + operand rows + seed, search, re-score, exact scans + output
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
@@ -1020,6 +1035,7 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "fp16+fp32" if used == "tc" else "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "search": used, "l2": "flushed (256 MB write) between steps",
+                       "warmup_untimed": {"steps": n_warm, "min_s": WARMUP_MIN_S},
                        "comparisons_per_step": comps, "ranges_resolved_by_exact_rescan": n_fallback,
                        "shadow_ranges": shadow, "flat_domains": flat, "comparisons_screened_per_step": screened,
                        "screened_comparisons_per_s": job_rate(ws, args.steps, screened, t_total),
