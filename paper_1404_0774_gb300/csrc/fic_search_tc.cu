@@ -480,6 +480,49 @@ __device__ __forceinline__ void search_tc_run(const TcMaps &maps, const SliceCtx
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
+
+    // A single search runs the set-up that reads nothing an earlier kernel
+    // writes -- the barriers, the TMEM allocation, the tensor-map descriptors
+    // -- before the wait for that kernel, so that it overlaps its tail (slice
+    // encode 2.6 us shorter).  A batch waits first: its search shares the SMs
+    // with the other pipelines of the graph (measured 4.6 % slower otherwise).
+    if constexpr (BATCH) grid_dep_sync();
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NSTG; ++s) {
+            mbar_init(&full_bar[s], 1);
+            mbar_init(&empty_bar[s], 1);
+        }
+        mbar_init(&a_full, 1);
+        mbar_init(&a_empty, 1);
+        for (int q = 0; q < kItemQ; ++q) {
+            mbar_init(&q_full[q], 1);
+            mbar_init(&q_empty[q], 1 + EPI_WARPS);  // the MMA thread and every epilogue warp
+        }
+        for (int a = 0; a < NACC; ++a) {
+            mbar_init(&tfull_bar[a], 1);
+            mbar_init(&tempty_bar[a], 4);  // one arrival per epilogue warp of the tile's part
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&maps.a128)) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&maps.b128)) : "memory");
+        if constexpr (!CORR_EPI) {  // the tail boxes (8-bit)
+            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&maps.a32)) : "memory");
+            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&maps.b32)) : "memory");
+        }
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&tmem_base_s)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = tmem_base_s;
+
+    if constexpr (!BATCH) grid_dep_sync();  // the operand rows, statistics and counts are written
     int *err0 = ctx[0].b.err;
 
     // items per slice: row tiles of the kept ranges x active candidate
@@ -509,53 +552,29 @@ __device__ __forceinline__ void search_tc_run(const TcMaps &maps, const SliceCtx
         }
         if (lane == 0) ip_s[0] = 0;
     }
-
     if (threadIdx.x == 0) {
         // self-check: every TMA box and MMA operand lies inside this CTA's
-        // dynamic shared memory
+        // dynamic shared memory, and the TMEM allocation is lane field 0,
+        // columns [base, base + TMEM_COLS) within the 512 of the SM
         const uint32_t used = (uint32_t)(smem - smem_raw) + A_BYTES + NSTG * B_BYTES + 32 * ET * 4 +
                               EPI_WARPS * DC_WARP * (16 + 4 + 32);
         int bad = 0;
         if (used > smem_bytes) bad = 2;
         if (smem_u32(smem) & 1023u) bad = 4;
+        if ((tmem_base >> 16) != 0 || (tmem_base & 0xFFFFu) + TMEM_COLS > 512) bad = 5;
         abort_s = bad;
         if (bad) atomicExch(err0, bad);
-        for (int s = 0; s < NSTG; ++s) {
-            mbar_init(&full_bar[s], 1);
-            mbar_init(&empty_bar[s], 1);
-        }
-        mbar_init(&a_full, 1);
-        mbar_init(&a_empty, 1);
-        for (int q = 0; q < kItemQ; ++q) {
-            mbar_init(&q_full[q], 1);
-            mbar_init(&q_empty[q], 1 + EPI_WARPS);  // the MMA thread and every epilogue warp
-        }
-        for (int a = 0; a < NACC; ++a) {
-            mbar_init(&tfull_bar[a], 1);
-            mbar_init(&tempty_bar[a], 4);  // one arrival per epilogue warp of the tile's part
-        }
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
     const int total = ip_s[n];
-    if ((int)blockIdx.x >= total) return;  // CTA-uniform: no work (nothing allocated yet)
-    if (warp == 1) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                         smem_u32(&tmem_base_s)),
-                     "r"(TMEM_COLS)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    if ((int)blockIdx.x >= total) {  // CTA-uniform: no work
+        if (warp == 1) {
+            __syncwarp();
+            asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS)
+                         : "memory");
+        }
+        return;
     }
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    const uint32_t tmem_base = tmem_base_s;
-    // TMEM: lane field 0, columns [base, base + TMEM_COLS) within the 512 of the SM
-    if (threadIdx.x == 0 && ((tmem_base >> 16) != 0 || (tmem_base & 0xFFFFu) + TMEM_COLS > 512)) {
-        abort_s = 5;
-        atomicExch(err0, 5);
-    }
-    __syncthreads();
     const bool run = abort_s == 0;
 
     if (!run) {
@@ -908,7 +927,6 @@ __global__ void __launch_bounds__(THREADS, 1)
     k_search_tc(const __grid_constant__ TcMaps maps, const __grid_constant__ SliceCtx one, const SliceCtx *many, int n,
                 int dense, float *dump, uint32_t smem_bytes, int *queue, unsigned long long wait_ns)
 {
-    grid_dep_sync();
     search_tc_run<NBLK, BW, KB, BATCH>(maps, one, many, n, dense, dump, smem_bytes, queue, wait_ns);
 }
 
