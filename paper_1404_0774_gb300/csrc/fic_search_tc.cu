@@ -591,7 +591,9 @@ __device__ __forceinline__ void search_tc_run(const TcMaps &maps, const SliceCtx
             for (int k = 0;; ++k) {
                 const int slot = k % kItemQ;
                 if (!mbar_wait(&q_empty[slot], ((k / kItemQ) & 1) ^ 1, &abort_s, err0, wait_ns)) break;
-                int item = atomicAdd(queue, 1);
+                // the first item of CTA b is item b (every CTA takes one), the
+                // later ones come from the counter: items gridDim.x, gridDim.x + 1, ...
+                int item = k == 0 ? (int)blockIdx.x : (int)gridDim.x + atomicAdd(queue, 1);
                 if (item >= total || *(volatile int *)&abort_s) item = -1;
                 item_q[slot] = item;
                 mbar_arrive(&q_full[slot]);
