@@ -34,10 +34,14 @@
  *    half away from zero to e*P/Lo, Lo = 2^(o_bits-1) - 1.  Collage error
  *    R = sum (s_hat*a_i + o_hat - b_i)^2 (eq 8).
  *  - Pointers may be host or device memory; the library detects which
- *    (cudaPointerGetAttributes) and copies host data itself.  The caller owns
- *    every buffer.  `stream` is a cudaStream_t (NULL = legacy default stream).
- *    Calls on one stream are ordered; the host-pointer variants synchronise
- *    the stream before returning.
+ *    (cudaPointerGetAttributes) and moves host data itself: fic_encode reads a
+ *    page-locked host image with a copy kernel (16-byte aligned, rows
+ *    contiguous; otherwise, and for pageable memory, by a copy-engine
+ *    transfer) and its map output kernel writes page-locked host maps in
+ *    place (pageable maps are copied back).  The caller owns every buffer.
+ *    `stream` is a cudaStream_t (NULL = legacy default stream).  Calls on one
+ *    stream are ordered; the host-pointer variants synchronise the stream
+ *    before returning.
  *  - Errors: every call returns FIC_OK (0) or a negative FIC_ERR_* code and
  *    never aborts; fic_status_str() gives a message.
  */

@@ -274,6 +274,64 @@ bool is_device_ptr(const void *ptr)
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// Where a caller's buffer lives: device (or managed) memory, page-locked host
+// memory that kernels can address (its device address in *dev), or other
+// host memory, which only the copy engines reach.
+enum class Mem { Device, PinnedHost, Host };
+
+Mem classify(const void *ptr, void **dev)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return Mem::Host;
+    }
+    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return Mem::Device;
+    if (a.type == cudaMemoryTypeHost && a.devicePointer) {
+        *dev = a.devicePointer;
+        return Mem::PinnedHost;
+    }
+    return Mem::Host;
+}
+
+// The image from page-locked host memory into the workspace, 16 bytes a
+// thread: for half a megabyte a kernel over the chip-to-chip link costs a
+// few microseconds, a copy-engine transfer about twelve (most of it the
+// operation's fixed latency).  The loads go first, the stores after the wait
+// for the stream's previous kernel.
+__global__ void __launch_bounds__(256) k_copy_in(const uint4 *__restrict__ src, uint4 *__restrict__ dst, size_t n16)
+{
+    const size_t i0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x, step = (size_t)gridDim.x * blockDim.x;
+    uint4 v[4];
+    int k = 0;
+    for (size_t i = i0; i < n16 && k < 4; i += step, ++k) v[k] = __ldcs(src + i);
+    grid_dep_sync();
+    k = 0;
+    for (size_t i = i0; i < n16 && k < 4; i += step, ++k) dst[i] = v[k];
+    for (size_t i = i0 + 4 * step; i < n16; i += step) dst[i] = __ldcs(src + i);
+}
+
+// A pinned host word of this thread for reading the device error flag back
+// after a call with host buffers (allocated on the thread's first such call
+// and kept; a pageable destination would route the 4-byte copy through a
+// staging buffer).  Null when it cannot be had or when the caller may not
+// allocate (fic_encode_static): the copy then goes to a stack word.
+thread_local bool g_no_alloc = false;
+
+int *pinned_flag()
+{
+    thread_local int *flag = nullptr;
+    thread_local bool tried = false;
+    if (!flag && !tried && !g_no_alloc) {
+        tried = true;
+        if (cudaMallocHost(reinterpret_cast<void **>(&flag), sizeof(int)) != cudaSuccess) {
+            cudaGetLastError();
+            flag = nullptr;
+        }
+    }
+    return g_no_alloc ? nullptr : flag;
+}
+
 // FIC_DEBUG=1 in the environment: synchronise after every call on the
 // encode/decode paths and report the first failing one on stderr.
 bool debug_mode()
@@ -471,30 +529,53 @@ int run_encode(const void *img, int w, int h, int pitch_px, const fic_params *p,
         owned = true;
     }
     {
-        const bool img_dev = is_device_ptr(img);
-        const bool maps_dev = dump ? true : is_device_ptr(maps);
+        void *img_alias = nullptr, *maps_alias = nullptr;
+        const Mem img_mem = classify(img, &img_alias);
+        const Mem maps_mem = dump ? Mem::Device : classify(maps, &maps_alias);
+        const bool img_dev = img_mem == Mem::Device, maps_dev = maps_mem == Mem::Device;
         const size_t elem = g.B <= 8 ? 1 : 2;
         const void *dimg = img;
         Geometry gd = g;
         if (!img_dev) {
-            FIC_CUDA(cudaMemcpy2DAsync(ws + L.img, (size_t)w * elem, img, (size_t)pitch_px * elem,
-                                       (size_t)w * elem, h, cudaMemcpyHostToDevice, st));
+            const size_t bytes = (size_t)w * h * elem;
+            if (img_mem == Mem::PinnedHost && pitch_px == w && bytes % 16 == 0 &&
+                (reinterpret_cast<uintptr_t>(img_alias) & 15) == 0) {
+                const size_t n16 = bytes / 16;
+                const int blocks = (int)std::min<size_t>((n16 + 255) / 256, (size_t)4 * sm_count());
+                FIC_CUDA(launch_dep(k_copy_in, dim3(blocks), dim3(256), 0, st, (const uint4 *)img_alias,
+                                    reinterpret_cast<uint4 *>(ws + L.img), n16));
+            } else if (pitch_px == w) {  // one contiguous copy
+                FIC_CUDA(cudaMemcpyAsync(ws + L.img, img, bytes, cudaMemcpyHostToDevice, st));
+            } else {
+                FIC_CUDA(cudaMemcpy2DAsync(ws + L.img, (size_t)w * elem, img, (size_t)pitch_px * elem,
+                                           (size_t)w * elem, h, cudaMemcpyHostToDevice, st));
+            }
             dimg = ws + L.img;
             gd.pitch = w;
         }
-        fic_map *dmaps = maps_dev ? maps : reinterpret_cast<fic_map *>(ws + L.maps);
+        // maps in page-locked host memory are written there by the map output
+        // kernel itself (no copy back); every map carries FIC_MAP_ERROR when
+        // the search set the error word, so the host reads it from map 0
+        const bool maps_direct = maps_mem == Mem::PinnedHost;
+        fic_map *dmaps = maps_dev ? maps
+                                  : (maps_direct ? static_cast<fic_map *>(maps_alias)
+                                                 : reinterpret_cast<fic_map *>(ws + L.maps));
         const bool timed = !dump && (p->flags & FIC_FLAG_PHASE_TIMING) && g_phase.ensure();
         g_phase.valid = false;
         FIC_CUDA(encode_pipeline(gd, p, search, n_split, split_target(p, search), L, ws, dimg, nullptr, dmaps, dump,
                                  timed, st));
         g_phase.valid = timed;
         const bool sync = dump || !maps_dev || !img_dev || debug_mode();
-        if (!dump && !maps_dev)
+        if (!dump && !maps_dev && !maps_direct)
             FIC_CUDA(cudaMemcpyAsync(maps, dmaps, sizeof(fic_map) * g.R, cudaMemcpyDeviceToHost, st));
         if (sync) {
-            int herr = 0;
-            FIC_CUDA(cudaMemcpyAsync(&herr, enc_bufs(L, ws).err, sizeof(int), cudaMemcpyDeviceToHost, st));
+            int herr_stack = 0;
+            int *hf = maps_direct ? nullptr : pinned_flag();
+            int *dst = hf ? hf : &herr_stack;
+            if (!maps_direct)
+                FIC_CUDA(cudaMemcpyAsync(dst, enc_bufs(L, ws).err, sizeof(int), cudaMemcpyDeviceToHost, st));
             FIC_CUDA(cudaStreamSynchronize(st));
+            const int herr = maps_direct ? (int)((maps[0].info & FIC_MAP_ERROR) != 0) : *dst;
             if (herr) {
                 rc = FIC_ERR_TIMEOUT;
                 if (debug_mode()) fprintf(stderr, "libfic: device error flag %d\n", herr);
@@ -1323,8 +1404,11 @@ int encode_with_workspace(const void *img, int w, int h, int pitch_px, const fic
                           int maps_cap, int *n_maps, void *workspace, size_t workspace_bytes, void *stream)
 {
     if (!maps || !workspace) return FIC_ERR_BAD_ARG;
-    return run_encode(img, w, h, pitch_px, p, maps, maps_cap, n_maps, workspace, workspace_bytes, stream,
-                      nullptr);
+    g_no_alloc = true;  // the caller may not allocate, not even pinned host memory
+    const int rc = run_encode(img, w, h, pitch_px, p, maps, maps_cap, n_maps, workspace, workspace_bytes, stream,
+                              nullptr);
+    g_no_alloc = false;
+    return rc;
 }
 }  // namespace fic
 

@@ -49,3 +49,21 @@ def check_against_oracle(orc, img, got, n, t, B, sb=5, ob=7, ranges=None, ref=No
     if ref is None:
         ref = orc.encode(img, n=n, t=t, bit_depth=B, s_bits=sb, o_bits=ob, ranges=sel)
     return check_minima(got, ref, sel, n, B)
+
+
+def encode_pinned(fic, img, p):
+    """fic_encode through the C ABI with the image and the maps in page-locked
+    host memory: the image is read by a copy kernel, the maps are written by
+    the map output kernel straight into the host buffer."""
+    import ctypes
+
+    import torch
+
+    h, w = img.shape
+    R, _ = fic.counts(w, h, p)
+    h_img = torch.from_numpy(img.astype(np.int16) if img.dtype == np.uint16 else img.copy()).pin_memory()
+    h_maps = torch.full((R * 40,), 0xAB, dtype=torch.uint8).pin_memory()
+    nm = ctypes.c_int()
+    rc = fic.lib().fic_encode(h_img.data_ptr(), w, h, w, ctypes.byref(p), h_maps.data_ptr(), R, ctypes.byref(nm),
+                              None, 0, torch.cuda.current_stream().cuda_stream)
+    return rc, h_maps.numpy().view(fic.MAP_DTYPE).copy()

@@ -17,7 +17,7 @@ import numpy as np
 import pytest
 
 import fic_synth
-from parity import check_against_oracle
+from parity import check_against_oracle, encode_pinned
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -187,6 +187,16 @@ def test_host_and_device_pointers_agree(fic):
     dev = gpu_encode(fic, img, p)
     host = fic.encode(img, p)
     assert np.array_equal(dev, host)
+
+
+@pytest.mark.parametrize("B,n,t", [(12, 8, 4), (8, 8, 8)])
+def test_pinned_host_buffers_agree(fic, B, n, t):
+    img = fic_synth.ct_slice(14, 64) if B == 12 else fic_synth.mr_slice(size=64)
+    p = fic.params(range_size=n, domain_stride=t, bit_depth=B)
+    rc, got = encode_pinned(fic, img, p)
+    assert rc == 0
+    assert np.array_equal(got, gpu_encode(fic, img, p))
+    assert np.array_equal(got, fic.encode(img, p))  # pageable host buffers: copy-engine path
 
 
 @pytest.mark.parametrize("B,n,t", [(8, 8, 8), (12, 8, 4)])

@@ -14,7 +14,7 @@ import numpy as np
 import pytest
 
 import fic_synth
-from parity import check_against_oracle
+from parity import check_against_oracle, encode_pinned
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -55,6 +55,20 @@ def test_expired_waits_return_timeout_and_leave_the_gpu_usable(fic, orc, n, t):
     # a wait for the first accumulator spans a TMA copy and the MMAs: far
     # longer than 1 ns, so the limit runs out
     assert fired >= 1
+    # page-locked host maps are written by the map output kernel directly; the
+    # call takes the error from the maps' flags
+    fired_pinned = 0
+    try:
+        fic.set_wait_limit_ns(1)
+        for _ in range(3):
+            rc, pm = encode_pinned(fic, img, p)
+            if rc != 0:
+                assert rc == -6
+                assert np.all(pm["info"] & FIC_MAP_ERROR)
+                fired_pinned += 1
+    finally:
+        fic.set_wait_limit_ns(0)
+    assert fired_pinned >= 1
     assert fic.get_wait_limit_ns() == 2_000_000_000
     # the context is intact and the search runs normally again
     got = fic.encode(img, p)
