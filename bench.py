@@ -455,16 +455,20 @@ def run_quadtree(args):
                  "kernel": f"search of level {top} ({d['range_size']}x{d['range_size']} ranges, {d['search']})",
                  "peak_source": peak_kind + "; FP32 lanes x max clock for the ALU view",
                  "search_ms_per_level": [float(x) for x in lvl_ms[: len(per_level)]]})
-    # end to end from pinned host memory through the C ABI (image H2D, leaves D2H)
-    h_img = torch.from_numpy(img_np.astype(np.int16)).pin_memory()
-    h_maps = np.zeros(cap, fic.QMAP_DTYPE)
+    # end to end from pinned host memory through the C ABI (image in, leaves out;
+    # uint16 views of the pinned buffers, so that the binding passes them as
+    # they are)
+    h_img_t = torch.from_numpy(img_np.astype(np.int16)).pin_memory()
+    h_img = h_img_t.numpy().view(np.uint16)
+    h_maps_t = torch.zeros(cap * fic.QMAP_DTYPE.itemsize, dtype=torch.uint8).pin_memory()
+    h_maps = h_maps_t.numpy().view(fic.QMAP_DTYPE)
     for _ in range(2):
-        fic.encode_quadtree(h_img.numpy(), p, 4, 8.0, maps=h_maps, workspace=work, stream=stream)
+        fic.encode_quadtree(h_img, p, 4, 8.0, maps=h_maps, workspace=work, stream=stream)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(args.steps):
         flush.zero_()
-        fic.encode_quadtree(h_img.numpy(), p, 4, 8.0, maps=h_maps, workspace=work, stream=stream)
+        fic.encode_quadtree(h_img, p, 4, 8.0, maps=h_maps, workspace=work, stream=stream)
     torch.cuda.synchronize()
     e2e_t = time.perf_counter() - t0
     clocks = clk.summary()

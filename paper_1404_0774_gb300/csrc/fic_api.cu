@@ -332,6 +332,22 @@ int *pinned_flag()
     return g_no_alloc ? nullptr : flag;
 }
 
+// Pinned host words of this thread for reading n ints back (as pinned_flag;
+// null when they cannot be had).
+int *pinned_words(int n)
+{
+    thread_local int *buf = nullptr;
+    thread_local int have = 0;
+    if (have < n && !g_no_alloc) {
+        if (buf) cudaFreeHost(buf);
+        buf = nullptr;
+        have = 0;
+        if (cudaMallocHost(reinterpret_cast<void **>(&buf), sizeof(int) * n) == cudaSuccess) have = n;
+        else cudaGetLastError();
+    }
+    return have >= n ? buf : nullptr;
+}
+
 // FIC_DEBUG=1 in the environment: synchronise after every call on the
 // encode/decode paths and report the first failing one on stderr.
 bool debug_mode()
@@ -726,14 +742,24 @@ int run_quadtree(const void *img, int w, int h, int pitch_px, const fic_params *
         owned = true;
     }
     {
-        const bool img_dev = is_device_ptr(img);
-        const bool maps_dev = is_device_ptr(maps);
+        void *img_alias = nullptr, *maps_alias = nullptr;
+        const Mem img_mem = classify(img, &img_alias), maps_mem = classify(maps, &maps_alias);
+        const bool maps_dev = maps_mem == Mem::Device;
         const size_t elem = Q.g[0].B <= 8 ? 1 : 2;
         const void *dimg = img;
         int pitch = pitch_px;
-        if (!img_dev) {
-            FIC_CUDA(cudaMemcpy2DAsync(ws + Q.img, (size_t)w * elem, img, (size_t)pitch_px * elem, (size_t)w * elem, h,
-                                       cudaMemcpyHostToDevice, st));
+        if (img_mem != Mem::Device) {
+            const size_t bytes = (size_t)w * h * elem;
+            if (img_mem == Mem::PinnedHost && pitch_px == w && bytes % 16 == 0 &&
+                (reinterpret_cast<uintptr_t>(img_alias) & 15) == 0) {
+                const size_t n16 = bytes / 16;
+                const int blocks = (int)std::min<size_t>((n16 + 255) / 256, (size_t)4 * sm_count());
+                FIC_CUDA(launch_dep(k_copy_in, dim3(blocks), dim3(256), 0, st, (const uint4 *)img_alias,
+                                    reinterpret_cast<uint4 *>(ws + Q.img), n16));
+            } else {
+                FIC_CUDA(cudaMemcpy2DAsync(ws + Q.img, (size_t)w * elem, img, (size_t)pitch_px * elem,
+                                           (size_t)w * elem, h, cudaMemcpyHostToDevice, st));
+            }
             dimg = ws + Q.img;
             pitch = w;
         }
@@ -814,12 +840,19 @@ int run_quadtree(const void *img, int w, int h, int pitch_px, const fic_params *
         }
         g_qt_phase.levels = Q.levels;
         g_qt_phase.valid = timed;
-        fic_qmap *dout = maps_dev ? maps : reinterpret_cast<fic_qmap *>(ws + Q.stage);
+        // page-locked host leaves are written in place by the gather kernel
+        const bool maps_direct = maps_mem == Mem::PinnedHost;
+        fic_qmap *dout = maps_dev ? maps
+                                  : (maps_direct ? static_cast<fic_qmap *>(maps_alias)
+                                                 : reinterpret_cast<fic_qmap *>(ws + Q.stage));
         FIC_CUDA(launch_qt_gather(lv, reinterpret_cast<int *>(ws + Q.lists), dout, maps_cap, counts, st));
-        int hc[2 + 2 * kMaxLevels];
-        FIC_CUDA(cudaMemcpyAsync(hc, counts, sizeof hc, cudaMemcpyDeviceToHost, st));
+        constexpr int kCounts = 2 + 2 * kMaxLevels;
+        int hc_stack[kCounts];
+        int *hp = pinned_words(kCounts);
+        int *hc = hp ? hp : hc_stack;
+        FIC_CUDA(cudaMemcpyAsync(hc, counts, sizeof(int) * kCounts, cudaMemcpyDeviceToHost, st));
         FIC_CUDA(cudaStreamSynchronize(st));
-        if (!maps_dev && hc[0] > 0) {
+        if (!maps_dev && !maps_direct && hc[0] > 0) {
             FIC_CUDA(cudaMemcpyAsync(maps, dout, sizeof(fic_qmap) * (size_t)hc[0], cudaMemcpyDeviceToHost, st));
             FIC_CUDA(cudaStreamSynchronize(st));
         }

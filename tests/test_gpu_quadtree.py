@@ -84,6 +84,21 @@ def test_quadtree_host_and_device_agree(fic):
     assert np.array_equal(a, b)
 
 
+def test_quadtree_pinned_host_buffers_agree(fic):
+    """A page-locked host image (read by a copy kernel) and page-locked host
+    leaves (written in place by the gather kernel) give the device path's leaves."""
+    img = fic_synth.ct_slice(45, 64)
+    p = fic.params(range_size=16, domain_stride=16, bit_depth=12)
+    a = gpu_quadtree(fic, img, p, 4, 8.0, device=True)
+    h_img = torch.from_numpy(img.astype(np.int16)).pin_memory()
+    cap = (64 // 4) ** 2
+    h_maps = torch.zeros(cap * fic.QMAP_DTYPE.itemsize, dtype=torch.uint8).pin_memory()
+    leaves, n = fic.encode_quadtree(h_img.numpy().view(np.uint16), p, 4, 8.0,
+                                    maps=h_maps.numpy().view(fic.QMAP_DTYPE))
+    assert n == len(a)
+    assert np.array_equal(np.asarray(leaves), a)
+
+
 def test_quadtree_rejects_bad_sizes(fic):
     img = np.zeros((64, 64), np.uint8)
     with pytest.raises(fic.FicError):
