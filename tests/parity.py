@@ -51,19 +51,35 @@ def check_against_oracle(orc, img, got, n, t, B, sb=5, ob=7, ranges=None, ref=No
     return check_minima(got, ref, sel, n, B)
 
 
-def encode_pinned(fic, img, p):
+def encode_pinned(fic, img, p, layout="contiguous"):
     """fic_encode through the C ABI with the image and the maps in page-locked
-    host memory: the image is read by a copy kernel, the maps are written by
-    the map output kernel straight into the host buffer."""
+    host memory: a contiguous, 16-byte aligned image is read by a copy kernel
+    (layout "pitched": rows 8 elements longer than the image is wide, "unaligned":
+    an image starting 2 bytes past an aligned address -- both go through the
+    copy engines), and the maps are written by the map output kernel straight
+    into the host buffer."""
     import ctypes
 
     import torch
 
     h, w = img.shape
     R, _ = fic.counts(w, h, p)
-    h_img = torch.from_numpy(img.astype(np.int16) if img.dtype == np.uint16 else img.copy()).pin_memory()
+    src = img.astype(np.int16) if img.dtype == np.uint16 else img
+    elem = src.dtype.itemsize
+    if layout == "pitched":
+        buf = torch.zeros((h, w + 8), dtype=torch.from_numpy(src[:1, :1].copy()).dtype).pin_memory()
+        buf[:, :w] = torch.from_numpy(src.copy())
+        ptr, pitch = buf.data_ptr(), w + 8
+    elif layout == "unaligned":
+        buf = torch.zeros(h * w + 16 // elem, dtype=torch.from_numpy(src[:1, :1].copy()).dtype).pin_memory()
+        off = 2 // elem if elem == 2 else 2
+        buf[off:off + h * w] = torch.from_numpy(src.copy().ravel())
+        ptr, pitch = buf.data_ptr() + off * elem, w
+    else:
+        buf = torch.from_numpy(src.copy()).pin_memory()
+        ptr, pitch = buf.data_ptr(), w
     h_maps = torch.full((R * 40,), 0xAB, dtype=torch.uint8).pin_memory()
     nm = ctypes.c_int()
-    rc = fic.lib().fic_encode(h_img.data_ptr(), w, h, w, ctypes.byref(p), h_maps.data_ptr(), R, ctypes.byref(nm),
+    rc = fic.lib().fic_encode(ptr, w, h, pitch, ctypes.byref(p), h_maps.data_ptr(), R, ctypes.byref(nm),
                               None, 0, torch.cuda.current_stream().cuda_stream)
     return rc, h_maps.numpy().view(fic.MAP_DTYPE).copy()

@@ -189,11 +189,12 @@ def test_host_and_device_pointers_agree(fic):
     assert np.array_equal(dev, host)
 
 
+@pytest.mark.parametrize("layout", ["contiguous", "pitched", "unaligned"])
 @pytest.mark.parametrize("B,n,t", [(12, 8, 4), (8, 8, 8)])
-def test_pinned_host_buffers_agree(fic, B, n, t):
+def test_pinned_host_buffers_agree(fic, B, n, t, layout):
     img = fic_synth.ct_slice(14, 64) if B == 12 else fic_synth.mr_slice(size=64)
     p = fic.params(range_size=n, domain_stride=t, bit_depth=B)
-    rc, got = encode_pinned(fic, img, p)
+    rc, got = encode_pinned(fic, img, p, layout)
     assert rc == 0
     assert np.array_equal(got, gpu_encode(fic, img, p))
     assert np.array_equal(got, fic.encode(img, p))  # pageable host buffers: copy-engine path
