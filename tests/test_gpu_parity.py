@@ -116,6 +116,27 @@ def test_ct_slice_512_full(fic, orc, ct512_oracle, search):
     print(f"index agreement with the oracle: {same:.4f}")
 
 
+@pytest.fixture(scope="module")
+def ct512_n4_oracle(orc):
+    """The oracle's exhaustive search of every 4x4 range of the 512x512 slice
+    (16384 ranges x 16129 domains x 8 = 2.1e9 comparisons)."""
+    img = fic_synth.ct_slice()
+    return img, orc.encode(img, n=4, t=4, bit_depth=12)
+
+
+@pytest.mark.parametrize("search", SEARCH)
+def test_ct_slice_512_n4_full(fic, orc, ct512_n4_oracle, search):
+    """4x4 ranges on the 512x512 12-bit CT-like slice, 8x8 domains at stride 4
+    (the geometry of the quadtree's last level): many near-ties, so lists
+    fail certification and the exact re-scans decide; every map re-scored by
+    the oracle, every range's residual checked against its minimum."""
+    img, ref = ct512_n4_oracle
+    p = fic.params(range_size=4, domain_stride=4, bit_depth=12, search=search_code(fic, search))
+    got = gpu_encode(fic, img, p)
+    check_against_oracle(orc, img, got, 4, 4, 12, ref=ref)
+    print(f"maps resolved by exact re-scans: {int((got['info'] & fic.FIC_MAP_FALLBACK != 0).sum())}")
+
+
 @pytest.mark.parametrize("t", [16, 8])
 @pytest.mark.parametrize("search", SEARCH)
 def test_ct_slice_512_n16_full(fic, orc, search, t):
