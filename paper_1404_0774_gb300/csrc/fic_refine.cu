@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(1024) k_ref_loss_final(int nb, int N, const do
 
 // dL/ds_r, dL/do_r contributions of one reverse step: warp per range.
 __global__ void k_ref_grad_range(RefineGeo rg, const int *roff, const int *rsym, const float *xt, const float *g1,
-                                 float *ds, float *dof)
+                                 float *ds, float *dof, int first)
 {
     const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
@@ -202,9 +202,9 @@ __global__ void k_ref_grad_range(RefineGeo rg, const int *roff, const int *rsym,
         gs += __shfl_xor_sync(0xffffffffu, gs, o);
         go += __shfl_xor_sync(0xffffffffu, go, o);
     }
-    if (lane == 0) {
-        ds[r] += gs;
-        dof[r] += go;
+    if (lane == 0) {  // the first reverse step starts the sums
+        ds[r] = first ? gs : ds[r] + gs;
+        dof[r] = first ? go : dof[r] + go;
     }
 }
 
@@ -343,8 +343,6 @@ cudaError_t refine_backward(const RefineGeo &rg, const RefineBufs &b, const floa
 {
     const int N = rg.w * rg.h;
     cudaError_t e;
-    if ((e = cudaMemsetAsync(ds, 0, sizeof(float) * rg.R, st)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(dof, 0, sizeof(float) * rg.R, st)) != cudaSuccess) return e;
     const float *g1 = grad_x;
     for (int t = iters - 1; t >= 0; --t) {
         const float *xt;
@@ -355,7 +353,7 @@ cudaError_t refine_backward(const RefineGeo &rg, const RefineBufs &b, const floa
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
             xt = b.tmp;
         }
-        k_ref_grad_range<<<blocks(rg.R, 8), 256, 0, st>>>(rg, b.roff, b.rsym, xt, g1, ds, dof);
+        k_ref_grad_range<<<blocks(rg.R, 8), 256, 0, st>>>(rg, b.roff, b.rsym, xt, g1, ds, dof, t == iters - 1 ? 1 : 0);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if (t > 0) {
             float *g0 = (g1 == b.g[0]) ? b.g[1] : b.g[0];
