@@ -337,13 +337,18 @@ int *pinned_flag()
 int *pinned_words(int n)
 {
     thread_local int *buf = nullptr;
-    thread_local int have = 0;
-    if (have < n && !g_no_alloc) {
+    thread_local int have = 0, failed_at = 0;  // failed_at: a request of this size could not be met
+    if (have < n && !g_no_alloc && (failed_at == 0 || n < failed_at)) {
         if (buf) cudaFreeHost(buf);
         buf = nullptr;
         have = 0;
-        if (cudaMallocHost(reinterpret_cast<void **>(&buf), sizeof(int) * n) == cudaSuccess) have = n;
-        else cudaGetLastError();
+        if (cudaMallocHost(reinterpret_cast<void **>(&buf), sizeof(int) * n) == cudaSuccess) {
+            have = n;
+        } else {
+            cudaGetLastError();
+            buf = nullptr;
+            failed_at = n;
+        }
     }
     return have >= n ? buf : nullptr;
 }
