@@ -265,6 +265,29 @@ def test_decode_iterates_contract(orc):
         assert b <= smax * a * (1 + 1e-12) + 1e-9
 
 
+@pytest.mark.parametrize("s,o,init", [(0.5, 4000.0, 100.0), (0.75, -300.0, 2048.0), (-0.5, 1000.0, 0.0)])
+def test_decode_of_uniform_maps_closed_form(orc, s, o, init):
+    """With one (s, o) for every range, a flat image stays flat whatever the
+    domains and symmetries (the 2x2 mean of a constant is the constant), so
+    x_t = s^t x_0 + o (1 - s^t) / (1 - s).  The first two cases leave [0, P]
+    (towards 8000 and -1200 for P = 4095): the clamped decode is the clip of
+    that value, the unclamped decode the value itself."""
+    h = w = 32
+    n, t, B, T = 8, 4, 12, 9
+    R = (h // n) * (w // n)
+    U = (w - 2 * n) // t + 1
+    rng = np.random.default_rng(5)
+    dom = rng.integers(0, U * U, R).astype(np.int32)
+    sym = rng.integers(0, 8, R).astype(np.int32)
+    sv, ov = np.full(R, s), np.full(R, o)
+    want = s ** T * init + o * (1 - s ** T) / (1 - s)
+    raw = orc.decode(dom, sym, sv, ov, h, w, n=n, t=t, bit_depth=B, iters=T, init=init, clamp=False)
+    assert np.allclose(raw, want, rtol=0, atol=1e-9 * (abs(want) + abs(o)))
+    got = orc.decode(dom, sym, sv, ov, h, w, n=n, t=t, bit_depth=B, iters=T, init=init)
+    assert np.array_equal(got, np.clip(raw, 0, (1 << B) - 1))
+    assert np.all((got >= 0) & (got <= (1 << B) - 1))
+
+
 def test_psnr_closed_form(orc):
     ref = np.zeros((16, 16))
     assert orc.psnr(ref, ref + 1.0, 8) == pytest.approx(20 * np.log10(255.0), rel=1e-14)
