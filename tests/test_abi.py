@@ -101,3 +101,41 @@ def test_wait_limit_setter_is_host_state(fic):
     assert fic.get_wait_limit_ns() == 12345
     fic.set_wait_limit_ns(0)
     assert fic.get_wait_limit_ns() == 2_000_000_000
+
+
+def test_missing_library_raises_instead_of_falling_back(fic, monkeypatch, tmp_path):
+    """Without libfic.so every entry point raises: there is no CPU path."""
+    import numpy as np
+
+    monkeypatch.setattr(fic, "_LIB_PATH", str(tmp_path / "libfic.so"))
+    monkeypatch.setattr(fic, "_lib", None)
+    img = np.zeros((64, 64), np.uint16)
+    p = fic.params(range_size=8, domain_stride=8, bit_depth=12)
+    with pytest.raises(ImportError):
+        fic.encode(img, p)
+    with pytest.raises(ImportError):
+        fic.decode(np.zeros(64, fic.MAP_DTYPE), 64, 64, p)
+    with pytest.raises(ImportError):
+        fic.lib()
+
+
+def test_product_sources_never_reach_the_oracle():
+    """The library, its binding and its build name nothing of the oracle
+    package (no import, include, link or call): the CUDA path and the oracle
+    share no code."""
+    import os
+    import re
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    pat = re.compile(r"\boracle\b|\borc_\w+|fic_oracle", re.I)
+    seen = 0
+    for top in ("paper_1404_0774_gb300", "include"):
+        for dirpath, dirnames, files in os.walk(os.path.join(root, top)):
+            dirnames[:] = [d for d in dirnames if d not in ("_lib", "_build", "__pycache__")]
+            for f in files:
+                if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp", ".c")):
+                    seen += 1
+                    with open(os.path.join(dirpath, f)) as fh:
+                        hits = [ln for ln in fh if pat.search(ln)]
+                    assert not hits, (f, hits[:3])
+    assert seen >= 5
