@@ -529,8 +529,9 @@ def batch_launches(sizes, parts=6):
 
 def run_volume(args):
     """Batched volume: one step = fic_encode_batch of the whole 96-slice stack
-    (a replay of its CUDA graph).  Reports slices/s and the per-slice
-    completion times within a batch (p50/p99)."""
+    (a replay of its CUDA graph).  Reports slices/s and the latency of one
+    batch replay over the timed replays (p50/p99): every stage covers all
+    slices, so a slice's maps are ready when its batch is."""
     import torch
 
     import __graft_entry__
