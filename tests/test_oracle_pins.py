@@ -154,6 +154,30 @@ def test_quantised_codes_are_grid_optimal(orc, bits):
         assert f["err"] == pytest.approx(res, rel=1e-12, abs=1e-9)
 
 
+@pytest.mark.parametrize("slope,mb,c_end,e_end", [(3.0, 128.0, 15, None), (-3.0, 128.0, -15, None),
+                                                  (-2.0, 200.0, -15, 63)])
+def test_codes_at_the_grid_ends(orc, slope, mb, c_end, e_end):
+    """Planted blocks whose fit lies outside the code grids: a slope of +-3
+    clamps s to +-1, and with s = -1 an offset mean(b) + mean(a) ~ 400 > P = 255
+    clamps o to P.  The codes are the grid ends and equal the brute-force grid
+    fit; the residual is that of the clamped codes."""
+    n, t, B, sb, ob = 4, 4, 8, 5, 7
+    rng = np.random.default_rng(int(10 * slope + mb))
+    img = rng.uniform(0, 255, (32, 32))
+    dom = 200.0 + rng.uniform(-10, 10, (2 * n, 2 * n))
+    img[:2 * n, :2 * n] = dom
+    a = np_tau(dom)
+    img[16:16 + n, 16:16 + n] = slope * (a - a.mean()) + mb
+    r = (16 // n) * (32 // n) + 16 // n
+    f = orc.fit_candidate(img, r, 0, 0, n=n, t=t, bit_depth=B, s_bits=sb, o_bits=ob)
+    c, e, res = grid_fit(a, np_range(img, r, n), B, sb, ob)
+    assert (f["c"], f["e"]) == (c, e)
+    assert f["c"] == c_end and f["s_hat"] == c_end / 15
+    if e_end is not None:
+        assert f["e"] == e_end and f["o_hat"] == 255.0 and f["o_raw"] > 255.0
+    assert f["err"] == pytest.approx(res, rel=1e-12, abs=1e-9)
+
+
 def test_nearest_s_level_is_optimal_for_free_offset():
     """With o free, the residual is a convex quadratic in s, so the nearest grid
     level to the least-squares slope is the best level (brute force over levels)."""
